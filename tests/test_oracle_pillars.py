@@ -1,0 +1,299 @@
+"""Pins of the pillar oracle against hand-counted clouds, brute force, closed forms,
+invariants and library routines.  CPU only."""
+import dataclasses
+import math
+import struct
+
+import numpy as np
+import pytest
+
+from oracle import pillars as O
+from pp_synth import GEOM_SMALL, Geometry, uniform_cloud, clustered_cloud, GEOM_FULL
+
+TINY = Geometry(0.0, 1.28, -0.32, 0.64, -1.0, 1.0, 0.32, 0.32, 4, 3, 5)
+
+
+def _cloud(rows):
+    return np.array(rows, dtype=np.float32).reshape(-1, 4)
+
+
+# ---------------------------------------------------------------- hand-counted clouds
+
+def test_hand_cloud_edges():
+    pts = _cloud([
+        (0.0, -0.32, 0.0, 0.5),     # 0: x = xmin, y = ymin          -> cell 0
+        (0.32, 0.0, 0.0, 0.1),      # 1: exactly on the ix=1, iy=1 edges -> cell 5
+        (1.28, 0.0, 0.0, 0.0),      # 2: x = xmax                    -> dropped
+        (1.2799, 0.1, 0.0, 0.0),    # 3: just inside xmax            -> cell 7
+        (0.5, 0.63, 0.99, 0.0),     # 4: iy = 2                       -> cell 9
+        (0.5, 0.64, 0.0, 0.0),      # 5: y = ymax                    -> dropped
+        (0.5, 0.0, 1.0, 0.0),       # 6: z = zmax                    -> dropped
+        (0.5, 0.0, -1.0, 0.0),      # 7: z = zmin (kept)             -> cell 5
+        (-1e-6, 0.0, 0.0, 0.0),     # 8: x < xmin                    -> dropped
+        (float("nan"), 0.0, 0.0, 0.0),  # 9: NaN                     -> dropped
+        (0.64, 0.32, 0.0, 0.0),     # 10: on the ix=2, iy=2 edges    -> cell 10
+        (0.31999, -0.01, 0.0, 0.0),  # 11: just below both edges     -> cell 0
+    ])
+    v = O.voxelise(pts, TINY)
+    assert v["cell"].tolist() == [0, 5, -1, 7, 9, -1, -1, 5, -1, -1, 10, 0]
+    assert v["num_pillars"] == 5
+    assert v["coord"].tolist() == [0, 5, 7, 9, 10]
+    assert v["npts"].tolist() == [2, 2, 1, 1, 1]
+    assert v["pt_idx"][:, :2].tolist() == [[0, 11], [1, 7], [3, -1], [4, -1], [10, -1]]
+    assert v["cnt"].tolist() == [2, 0, 0, 0, 0, 2, 0, 1, 0, 1, 1, 0]
+    assert v["pillar_of_cell"].tolist() == [0, -1, -1, -1, -1, 1, -1, 2, -1, 3, 4, -1]
+    np.testing.assert_array_equal(v["pts"][1, 1], pts[7])
+    assert not v["pts"][2, 1:].any()   # zero padding
+
+
+def test_hand_cloud_cap_keeps_lowest_cells():
+    # 8 occupied cells (P + 3), listed in scrambled order: the cap keeps the 5 lowest
+    centres = {11: (3, 2), 3: (3, 0), 7: (3, 1), 0: (0, 0), 9: (1, 2), 2: (2, 0), 10: (2, 2), 5: (1, 1)}
+    rows = []
+    for cell in [11, 3, 7, 0, 9, 2, 10, 5]:
+        ix, iy = centres[cell]
+        rows.append((0.16 + 0.32 * ix, -0.16 + 0.32 * iy, 0.0, 0.0))
+    v = O.voxelise(_cloud(rows), TINY)
+    assert v["num_pillars"] == 5
+    assert v["coord"].tolist() == [0, 2, 3, 5, 7]
+    assert v["pt_idx"][:, 0].tolist() == [3, 5, 1, 7, 2]
+    assert v["pillar_of_cell"][[9, 10, 11]].tolist() == [-1, -1, -1]
+
+
+def test_hand_cloud_first_32_by_index():
+    rng = np.random.default_rng(3)
+    n = 60
+    in_cell = sorted(rng.choice(n, 40, replace=False).tolist())   # 40 points in cell 6
+    rows = []
+    for i in range(n):
+        if i in in_cell:
+            rows.append((0.64 + 0.3 * rng.random(), 0.0 + 0.3 * rng.random(), 0.0, 0.0))
+        else:
+            rows.append((0.0 + 0.3 * rng.random(), -0.32 + 0.3 * rng.random(), 0.0, 0.0))
+    v = O.voxelise(_cloud(rows), TINY)
+    assert v["coord"].tolist() == [0, 6]
+    assert v["npts"].tolist() == [20, 32]
+    assert v["pt_idx"][1].tolist() == in_cell[:32]
+    assert int(v["cnt"][6]) == 40
+
+
+def test_empty_and_all_dropped():
+    v = O.voxelise(np.zeros((0, 4), np.float32), TINY)
+    assert v["num_pillars"] == 0 and v["coord"].size == 0 and v["cell"].size == 0
+    assert v["pts"].shape == (0, 32, 4)
+    v = O.voxelise(_cloud([(5.0, 0, 0, 0), (0.1, 0.1, 3.0, 0), (0.1, 9.0, 0.0, 0)]), TINY)
+    assert v["num_pillars"] == 0 and v["cell"].tolist() == [-1, -1, -1]
+    assert not v["cnt"].any()
+
+
+# ---------------------------------------------------------------- brute force
+
+def _fl32(v: float) -> float:
+    return struct.unpack("f", struct.pack("f", v))[0]
+
+
+def _brute_voxelise(pts, g):
+    """Per-point loop: binary32 ops emulated through float64 and a rounding to binary32
+    (double rounding is innocuous for +, -, / from 53 to 24 bits), dict grouping."""
+    groups = {}
+    cells = []
+    lo = [_fl32(g.xmin), _fl32(g.ymin), _fl32(g.zmin)]
+    hi = [_fl32(g.xmax), _fl32(g.ymax), _fl32(g.zmax)]
+    for i, (x, y, z, _r) in enumerate(pts.tolist()):
+        ok = all(lo[k] <= c < hi[k] for k, c in enumerate((x, y, z)))
+        if ok:
+            ix = math.floor(_fl32(_fl32(x - lo[0]) / _fl32(g.vx)))
+            iy = math.floor(_fl32(_fl32(y - lo[1]) / _fl32(g.vy)))
+            ok = 0 <= ix < g.nx and 0 <= iy < g.ny
+        if not ok:
+            cells.append(-1)
+            continue
+        c = iy * g.nx + ix
+        cells.append(c)
+        groups.setdefault(c, []).append(i)
+    kept = sorted(groups)[: g.max_pillars]
+    return cells, kept, [groups[c][: g.max_pts] for c in kept]
+
+
+def _edge_cloud(n, g, seed):
+    rng = np.random.default_rng(seed)
+    pts = uniform_cloud(n, seed, g)
+    k = n // 3
+    # a third of the points sit exactly on cell edges (and on the max edges)
+    pts[:k, 0] = (rng.integers(0, g.nx + 1, k) * np.float32(g.vx) + np.float32(g.xmin)).astype(np.float32)
+    pts[:k, 1] = (rng.integers(0, g.ny + 1, k) * np.float32(g.vy) + np.float32(g.ymin)).astype(np.float32)
+    pts[k:k + 20, 2] = np.float32(g.zmax)
+    pts[k + 20:k + 40, 2] = np.float32(g.zmin)
+    return pts[rng.permutation(n)]
+
+
+CAPPED = dataclasses.replace(GEOM_SMALL, max_pillars=700, max_pts=4)
+
+
+@pytest.mark.parametrize("g,n,seed", [(TINY, 300, 1), (GEOM_SMALL, 3000, 2), (CAPPED, 4000, 5)])
+def test_brute_force(g, n, seed):
+    pts = _edge_cloud(n, g, seed)
+    # a dense cell so the point cap binds
+    pts[:50, 0] = np.float32(g.xmin) + np.float32(0.01)
+    pts[:50, 1] = np.float32(g.ymin) + np.float32(0.01)
+    pts[:50, 2] = 0.0
+    cells, kept, members = _brute_voxelise(pts, g)
+    v = O.voxelise(pts, g)
+    assert v["cell"].tolist() == cells
+    assert v["coord"].tolist() == kept
+    for p, m in enumerate(members):
+        assert v["pt_idx"][p, : len(m)].tolist() == m
+        assert v["npts"][p] == len(m)
+        assert (v["pt_idx"][p, len(m):] == -1).all()
+        np.testing.assert_array_equal(v["pts"][p, : len(m)], pts[m])
+
+
+def test_invariants_and_permutation():
+    pts = clustered_cloud(30000, 11, GEOM_FULL)
+    v = O.voxelise(pts, GEOM_FULL)
+    cnt = v["cnt"]
+    assert v["num_pillars"] == min(GEOM_FULL.max_pillars, int((cnt > 0).sum()))
+    assert (np.diff(v["coord"]) > 0).all()
+    assert int(v["npts"].sum()) == int(np.minimum(cnt[v["coord"]], 32).sum())
+    assert int(cnt.sum()) == int((v["cell"] >= 0).sum())
+    # permutation invariance after re-indexing
+    perm = np.random.default_rng(0).permutation(len(pts))
+    w = O.voxelise(pts[perm], GEOM_FULL)
+    np.testing.assert_array_equal(w["coord"], v["coord"])
+    np.testing.assert_array_equal(w["cnt"], v["cnt"])
+    # every pillar with fewer points than the cap holds the same set of points
+    full = v["npts"] < 32
+    a = np.sort(np.where(v["pt_idx"] >= 0, v["pt_idx"], -1)[full], axis=1)
+    b = np.sort(np.where(w["pt_idx"] >= 0, perm[np.maximum(w["pt_idx"], 0)], -1)[full], axis=1)
+    np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------- PointNet
+
+def _ident_bn(c=64, beta=0.0):
+    return np.stack([np.ones(c), np.full(c, beta), np.zeros(c), np.full(c, 1.0 - O.BN_EPS)]).astype(np.float64)
+
+
+def test_pointnet_feature_columns():
+    """Channel j of an identity-like Linear picks feature j: its output is the max over valid
+    points of ReLU(f_j + 10) -- plain maxima of the inputs, checked with numpy.max."""
+    g = GEOM_SMALL
+    pts = uniform_cloud(5000, 4, g)
+    pts[:, 2] -= 2.0  # z mostly negative: padding slots fed as zeros would win the max
+    v = O.voxelise(pts, g)
+    W = np.zeros((64, 9))
+    for j in range(9):
+        W[j, j] = 1.0
+    feat = O.pointnet(v["pts"], v["npts"], v["coord"], W, _ident_bn(64, 10.0), g)
+    for p in range(0, v["num_pillars"], 37):
+        q = v["pts"][p, : v["npts"][p]].astype(np.float64)
+        ix, iy = v["coord"][p] % g.nx, v["coord"][p] // g.nx
+        xc = np.float32(g.xmin) + (ix + 0.5) * np.float64(np.float32(g.vx))
+        yc = np.float32(g.ymin) + (iy + 0.5) * np.float64(np.float32(g.vy))
+        m = q[:, :3].mean(axis=0)
+        want = [q[:, 0].max(), q[:, 1].max(), q[:, 2].max(), q[:, 3].max(),
+                q[:, 0].max() - m[0], q[:, 1].max() - m[1], q[:, 2].max() - m[2],
+                q[:, 0].max() - xc, q[:, 1].max() - yc]
+        got = feat[p, :9] - 10.0
+        np.testing.assert_allclose(got, np.maximum(np.array(want) + 10.0, 0) - 10.0, rtol=0, atol=1e-9)
+        assert (feat[p, 9:] == 10.0).all()   # zero weight rows -> ReLU(BN(0)) = beta
+
+
+def test_pointnet_single_point_closed_form():
+    """A single-point pillar has zero mean offsets: weights on features 4..6 cannot matter."""
+    g = GEOM_SMALL
+    rng = np.random.default_rng(5)
+    pts = np.zeros((3, 32, 4), np.float32)
+    pts[:, 0] = [(1.0, 2.0, -0.5, 0.3), (40.0, -10.0, 0.2, 0.9), (69.0, 39.0, -2.9, 0.0)]
+    npts = np.array([1, 1, 1], np.int32)
+    coord = np.array([0, 5000, 53000], np.int32)
+    W = rng.normal(size=(64, 9))
+    bn = np.stack([rng.uniform(0.5, 1.5, 64), rng.uniform(-1, 1, 64), rng.normal(size=64),
+                   rng.uniform(0.5, 2, 64)])
+    a = O.pointnet(pts, npts, coord, W, bn, g)
+    W2 = W.copy()
+    W2[:, 4:7] = rng.normal(size=(64, 3)) * 100
+    b = O.pointnet(pts, npts, coord, W2, bn, g)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_pointnet_permutation_invariant():
+    g = GEOM_SMALL
+    pts = clustered_cloud(8000, 6, g)
+    v = O.voxelise(pts, g)
+    rng = np.random.default_rng(1)
+    W = rng.normal(size=(64, 9))
+    bn = np.stack([rng.uniform(0.5, 1.5, 64), rng.uniform(-1, 1, 64), rng.normal(size=64) * 5,
+                   rng.uniform(10, 400, 64)])
+    a = O.pointnet(v["pts"], v["npts"], v["coord"], W, bn, g)
+    shuffled = v["pts"].copy()
+    for p in range(v["num_pillars"]):
+        k = v["npts"][p]
+        shuffled[p, :k] = shuffled[p, rng.permutation(k)]
+    b = O.pointnet(shuffled, v["npts"], v["coord"], W, bn, g)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- scatter
+
+def test_scatter_positions():
+    g = GEOM_SMALL
+    v = O.voxelise(uniform_cloud(6000, 8, g), g)
+    feat = np.random.default_rng(2).normal(size=(v["num_pillars"], 64))
+    canvas = O.scatter(feat, v["coord"], g)
+    assert canvas.shape == (g.ny, g.nx, 64)
+    nz = np.argwhere(np.abs(canvas).sum(axis=2) > 0)
+    assert len(nz) == v["num_pillars"]
+    for p, c in enumerate(v["coord"].tolist()):
+        assert (canvas[c // g.nx, c % g.nx] == feat[p]).all()
+
+
+# ---------------------------------------------------------------- conv backbone
+
+def test_conv_identity_kernel():
+    rng = np.random.default_rng(9)
+    x = np.abs(rng.normal(size=(7, 9, 16)))
+    w = np.zeros((16, 16, 3, 3))
+    w[:, :, 1, 1] = np.eye(16)
+    out = O.conv3x3_bn_relu(x, w, _ident_bn(16), 1)
+    np.testing.assert_allclose(out, x, rtol=1e-12)
+    out2 = O.conv3x3_bn_relu(x, w, _ident_bn(16), 2)
+    np.testing.assert_allclose(out2, x[::2, ::2], rtol=1e-12)
+
+
+@pytest.mark.parametrize("H,W,cin,cout,s", [(6, 5, 8, 4, 1), (7, 9, 8, 16, 2), (8, 8, 16, 8, 2)])
+def test_conv_vs_torch(H, W, cin, cout, s):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(H * W + s)
+    x = rng.normal(size=(H, W, cin))
+    w = rng.normal(size=(cout, cin, 3, 3))
+    bn = np.stack([rng.uniform(0.5, 1.5, cout), rng.uniform(-0.1, 0.1, cout),
+                   rng.normal(size=cout), rng.uniform(0.5, 2.0, cout)])
+    out = O.conv3x3_bn_relu(x, w, bn, s)
+    t = torch.nn.functional.conv2d(torch.from_numpy(x.transpose(2, 0, 1)[None]),
+                                   torch.from_numpy(w), stride=s, padding=1)[0].numpy()
+    t = bn[0][:, None, None] * (t - bn[2][:, None, None]) / np.sqrt(bn[3][:, None, None] + 1e-3) \
+        + bn[1][:, None, None]
+    np.testing.assert_allclose(out, np.maximum(t, 0).transpose(1, 2, 0), rtol=1e-10, atol=1e-10)
+
+
+def test_conv_brute_force_loop():
+    rng = np.random.default_rng(12)
+    H, W, cin, cout, s = 5, 6, 3, 2, 2
+    x = rng.normal(size=(H, W, cin))
+    w = rng.normal(size=(cout, cin, 3, 3))
+    bn = _ident_bn(cout, 0.0)
+    Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
+    out = O.conv3x3_bn_relu(x, w, bn, s)
+    assert out.shape == (Ho, Wo, cout)
+    for oy in range(Ho):
+        for ox in range(Wo):
+            for co in range(cout):
+                acc = 0.0
+                for ky in range(3):
+                    for kx in range(3):
+                        iy, ix = oy * s + ky - 1, ox * s + kx - 1
+                        if 0 <= iy < H and 0 <= ix < W:
+                            for ci in range(cin):
+                                acc += w[co, ci, ky, kx] * x[iy, ix, ci]
+                assert abs(out[oy, ox, co] - max(acc, 0.0)) < 1e-12

@@ -1,0 +1,230 @@
+"""Pins of the scheduling oracle: Table 2's printed urgencies and priorities, hand-computed
+batch boundaries, levels and delays, the miss-ratio metric (Eq. 3) on hand-made logs, and the
+discrete-event simulation against exhaustive enumeration of 3-chain instances.  CPU only."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sched as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table2.txt")
+
+
+def _table2():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        c, per, D, ec, eg, ul, pri = line.split()
+        rows.append((int(c), float(per), float(D), float(ec), float(eg), float(ul), int(pri)))
+    return rows
+
+
+def _trunc4(v):
+    return math.floor(v * 1e4) / 1e4
+
+
+def test_table2_urgency_values():
+    rows = _table2()
+    for c, _per, D, ec, eg, ul, _pri in rows:
+        got = _trunc4(S.table2_urgency(D, ec, eg))
+        if c == 10:
+            assert abs(got - 0.0056) < 1e-12 and ul == 0.0050   # misprinted row
+        else:
+            assert abs(got - ul) < 1e-12, (c, got, ul)
+
+
+def test_table2_priority_ranks():
+    rows = _table2()
+    uls = [S.table2_urgency(D, ec, eg) for _c, _p, D, ec, eg, _u, _r in rows]
+    pri = S.priority_ranks(uls)
+    printed = [r[6] for r in rows]
+    for c in range(len(rows)):
+        if c in (2, 7):
+            continue
+        assert pri[c] == printed[c], c
+    # C2 and C7 have equal urgency; the table ranks the higher id first, the rule the lower
+    assert {pri[2], pri[7]} == {printed[2], printed[7]} == {4, 5}
+    assert pri[2] < pri[7]
+
+
+def test_batch_boundaries_hand():
+    assert S.batch_boundaries([0.2, 0.2, 0.2, 0.1, 0.4, 0.05], 0.5) == [2, 4]
+    assert S.batch_boundaries([0.5, 0.5], 0.5) == [0, 1]
+    assert S.batch_boundaries([0.1] * 4, 0.5) == []
+    assert S.batch_boundaries([], 0.5) == []
+    assert S.batch_boundaries([0.3, 0.3, 0.3], 0.0) == [0, 1, 2]
+
+
+def test_batch_gate_overlap():
+    g = S.BatchGate(500.0)
+    assert not g.launched(0, 200.0)
+    assert g.launched(1, 300.0)          # 500 >= 500: batch {0, 1} closes
+    assert g.pending == 1
+    assert g.launched(2, 600.0)          # batch {2} closes
+    assert g.pending == 2                # overlapped mode (max_closed = 2) must now wait
+    g.finished(0)
+    assert g.pending == 2
+    g.finished(1)
+    assert g.pending == 1
+    g.finished(2)
+    assert g.pending == 0
+
+
+def test_miss_ratio_hand_log():
+    assert abs(S.overall_miss_ratio({0: (1, 4), 1: (0, 2), 2: (3, 3)}) - (0.25 + 0 + 1) / 3) < 1e-15
+    assert S.overall_miss_ratio({0: (0, 0), 1: (1, 2)}) == 0.5
+    assert S.overall_miss_ratio({}) == 0.0
+
+
+def _R(fid, chain, t_arr, D, est, prec=0, util=1.0):
+    return S.Ready(fid, chain, t_arr, t_arr + D, est, 0.0, prec, util)
+
+
+def test_decide_levels_and_reservation():
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, th_urgent=1 / 100.0, num_pri=6)
+    # slack 50 -> UL 0.02 > TH 0.01: reserved level 0
+    d = S.decide(0.0, [_R(1, 0, 0, 150, 100)], [], 0, cfg)
+    assert (d.kind, d.frames, d.level) == (S.RELEASE, [1], 0)
+    # slack 1000 -> UL 0.001; active non-urgent ULs 0.002, 0.0005; urgent one ignored
+    act = [S.Active(5, 0.002), S.Active(6, 0.0005), S.Active(7, 0.5)]
+    d = S.decide(0.0, [_R(2, 1, 0, 1100, 100)], act[:2], 0, cfg)
+    # r = 1 (0.002 > 0.001), n = 3 -> 1 + floor(1*5/3) = 2
+    assert d.level == 2
+    # an urgent active unit of another chain holds the release (Section 4.4.4) ...
+    d = S.decide(0.0, [_R(2, 1, 0, 1100, 100)], act, 0, cfg)
+    assert d.kind == S.DELAY
+    # ... unless the candidate is exempt by low utilisation, or the urgent unit is its own chain
+    d = S.decide(0.0, [_R(2, 1, 0, 1100, 100, util=0.05)], act, 0, cfg)
+    assert d.kind == S.RELEASE and d.level == 2
+    d = S.decide(0.0, [_R(2, 7, 0, 1100, 100)], act, 0, cfg)
+    assert d.kind == S.RELEASE
+
+
+def test_decide_order_batch_drop_wait():
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=3, th_urgent=0.0)
+    ready = [_R(1, 0, 0, 1000, 100), _R(2, 1, 10, 500, 100), _R(3, 2, 5, 2000, 100, prec=1),
+             _R(4, 3, 0, 50, 100), _R(5, 4, 0, 900, 100)]
+    d = S.decide(20.0, ready, [], 0, cfg)
+    assert d.drops == [4]                         # slack 50 - 100 - 20 < 0: early exit
+    assert d.frames == [2, 5, 1]                  # slack 390, 780, 880; precision 0 only
+    d = S.decide(20.0, ready, [], 2, cfg)
+    assert d.kind == S.WAIT and d.drops == [4]
+    fifo = S.PolicyConfig(policy=S.POLICY_FIFO, max_batch=1, num_pri=6)
+    d = S.decide(20.0, ready, [], 0, fifo)
+    assert d.frames == [1] and d.drops == [] and d.level == 5    # (t_arr 0, chain 0) first
+
+
+# ---------------------------------------------------------------- DES vs enumeration
+
+def _instance(seed):
+    """3 chains, 1-3 frames each, 1-3 units per frame; at most 8 units in total so that the
+    enumeration stays small."""
+    rng = np.random.default_rng(seed)
+    frames = []
+    fid, units = 0, 0
+    for c in range(3):
+        t_arr = float(rng.integers(0, 20))
+        for k in range(int(rng.integers(1, 4))):
+            n_st = int(rng.integers(1, 4))
+            if units + n_st > 8 - (2 - c):       # leave at least one unit for later chains
+                break
+            stages = [float(rng.integers(3, 15)) for _ in range(n_st)]
+            D = float(rng.integers(20, 90))
+            frames.append(S.SimFrame(fid, c, t_arr, t_arr + D, stages))
+            fid += 1
+            units += n_st
+            t_arr += float(rng.integers(5, 40))
+    return frames
+
+
+def _enumerate(frames):
+    """Every schedule of one non-preemptive server that starts a ready unit whenever it is
+    idle (units of a frame in order; a frame is ready from its arrival).  Yields
+    (list of (t_start, frame, stage), finish times)."""
+    by = {f.frame_id: f for f in frames}
+
+    def rec(t, nxt, trace, fin):
+        ready = [f for f in frames if f.t_arr <= t and nxt[f.frame_id] < len(f.stages)]
+        if not ready:
+            future = [f.t_arr for f in frames if f.t_arr > t and nxt[f.frame_id] < len(f.stages)]
+            if not future:
+                yield list(trace), dict(fin)
+                return
+            yield from rec(min(future), nxt, trace, fin)
+            return
+        for f in ready:
+            k = nxt[f.frame_id]
+            te = t + f.stages[k]
+            nxt[f.frame_id] += 1
+            trace.append((t, f.frame_id, k))
+            if nxt[f.frame_id] == len(f.stages):
+                fin[f.frame_id] = te
+            yield from rec(te, nxt, trace, fin)
+            trace.pop()
+            fin.pop(f.frame_id, None)
+            nxt[f.frame_id] -= 1
+
+    yield from rec(0.0, {f.frame_id: 0 for f in frames}, [], {})
+
+
+def _is_least_slack(trace, frames):
+    by = {f.frame_id: f for f in frames}
+    nxt = {f.frame_id: 0 for f in frames}
+    for t, fid, k in trace:
+        ready = [f for f in frames if f.t_arr <= t and nxt[f.frame_id] < len(f.stages)]
+        key = lambda f: (f.deadline - sum(f.stages[nxt[f.frame_id]:]) - t, f.chain_id, f.t_arr,
+                         f.frame_id)
+        if min(ready, key=key).frame_id != fid:
+            return False
+        nxt[fid] += 1
+    return True
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_des_matches_enumeration(seed):
+    frames = _instance(seed)
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, delta_eval_us=0.0, max_closed=1,
+                         th_urgent=0.0, early_exit=False)
+    res = S.simulate(frames, cfg)
+    greedy = []
+    best_miss = None
+    for trace, fin in _enumerate(frames):
+        misses = sum(fin[f.frame_id] > f.deadline for f in frames)
+        best_miss = misses if best_miss is None else min(best_miss, misses)
+        if _is_least_slack(trace, frames):
+            greedy.append((trace, fin))
+    assert len(greedy) == 1
+    trace, fin = greedy[0]
+    assert [(t, m[0][0], m[0][1]) for t, m, _lvl in res.releases] == trace
+    assert res.done == fin
+    assert sum(res.missed.values()) >= best_miss     # least slack is not optimal in general
+
+
+def test_des_early_exit_and_batching_invariants():
+    rng = np.random.default_rng(4)
+    frames = []
+    for i in range(200):
+        c = i % 5
+        t = float(i * 40 + rng.integers(0, 30))
+        frames.append(S.SimFrame(i, c, t, t + float(rng.choice([150, 300, 600])),
+                                 [float(rng.integers(20, 120))], precision=c % 2))
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=4, delta_eval_us=100.0,
+                         max_closed=2, th_urgent=0.0)
+    res = S.simulate(frames, cfg, unit_time=lambda ds: 10.0 + 0.5 * sum(ds))
+    assert set(res.done) | set(res.dropped) == {f.frame_id for f in frames}
+    assert not set(res.done) & set(res.dropped)
+    for _t, members, _lvl in res.releases:
+        assert 1 <= len(members) <= 4
+        assert len({frames[fid].precision for fid, _ in members}) == 1
+    for fid, t in res.dropped.items():        # dropped only when hopeless at that time
+        f = frames[fid]
+        assert f.deadline - f.stages[0] - t < 0
+    fifo = S.simulate(frames, S.PolicyConfig(policy=S.POLICY_FIFO, max_batch=1, max_closed=0),
+                      unit_time=lambda ds: 10.0 + 0.5 * sum(ds))
+    assert not fifo.dropped and len(fifo.done) == len(frames)
+    assert [m[0][0] for _t, m, _l in fifo.releases] == [f.frame_id for f in
+                                                        sorted(frames, key=lambda f: (f.t_arr, f.chain_id))]
