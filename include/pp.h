@@ -1,0 +1,320 @@
+/*
+ * pp.h -- C ABI of the urgency-served LiDAR pillar front end for NVIDIA GB300 (sm_103a).
+ *
+ * Two layers:
+ *   1. Stage entry points (pp_voxelize, pp_pointnet, pp_scatter, pp_conv3x3, ...): one step of
+ *      the pillar front end on device buffers the caller owns, enqueued on a caller stream.
+ *   2. The serving runtime (pp_create ... pp_destroy, declared further below): chains, frame
+ *      admission under an HBM budget, urgency-ordered batched release, completion polling.
+ *
+ * Conventions for every function here:
+ *   - Return value is a pp_status: PP_OK (0) or a negative error.  Nothing aborts, throws or
+ *     exits across this boundary.  A CUDA error seen while enqueueing returns PP_EDEVICE.
+ *   - "device" pointers are CUDA device (or managed) addresses on the current device; "host"
+ *     pointers are ordinary process memory.  No function takes ownership of a caller buffer.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Stage
+ *     entry points only enqueue work; they never synchronise the stream.
+ *   - Points are float4 (x, y, z, intensity) in metres, float32.  A batch of B frames is laid
+ *     out as [B][cap_points][4] floats; frame b holds n_points[b] <= cap_points valid rows.
+ *   - Activations are "padded NHWC": [B][H+2][W+2][C] with a one-pixel border that must be
+ *     zero; ops write only the interior of their output unless stated otherwise.
+ *
+ * The method: the paper's 3D-perception chains (Section 6, Table 4: PointPillars, 22k-25k
+ * points) are run here as a pillar front end -- voxelise, PointNet, BEV scatter, conv3x3
+ * backbone -- and released by the urgency rules of Section 4 (Eq. 2, Sections 4.3-4.4.5).
+ */
+#ifndef PP_H_
+#define PP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PP_OK = 0,
+  PP_EINVAL = -1,     /* bad argument: null pointer, size out of range, unsupported shape   */
+  PP_ENOMEM = -2,     /* device or host allocation failed                                    */
+  PP_EAGAIN = -3,     /* not admitted now: HBM budget or frame slots exhausted; retry later  */
+  PP_ETIMEDOUT = -4,  /* a bounded wait ran out                                              */
+  PP_EDEVICE = -5,    /* a CUDA call failed, or a kernel reported a device-side error        */
+  PP_ESTATE = -6      /* call not valid in the object's current state                        */
+} pp_status;
+
+enum { PP_F32 = 0, PP_BF16 = 1 };
+
+/* Pillar grid.  Ranges are half-open [min, max).  nx * vx must span x, ny * vy must span y.
+ * max_pts must be 32.  Cell index of a point (binary32 arithmetic, round to nearest even, no
+ * contraction): ix = floor((x - xmin) / vx), iy = floor((y - ymin) / vy); the point is kept iff
+ * it lies inside all three ranges and 0 <= ix < nx, 0 <= iy < ny; cell = iy * nx + ix. */
+typedef struct {
+  float xmin, xmax, ymin, ymax, zmin, zmax, vx, vy;
+  int32_t nx, ny, max_pillars, max_pts;
+} pp_geometry;
+
+/* Library version string, e.g. "pp 0.1 sm_103a". Never NULL. */
+const char* pp_version(void);
+
+/* Text of the last error recorded by this thread (empty string if none). Never NULL. */
+const char* pp_last_error(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Stage 1: voxelisation (point -> pillar).                                                  */
+/*                                                                                           */
+/* For each frame b: cell index per point (-1 = dropped); per-cell point counts via           */
+/* warp-aggregated atomics; pillars = occupied cells in ascending cell order, at most         */
+/* max_pillars of them; each pillar keeps the max_pts (32) points with the lowest input       */
+/* indices, in ascending index order, gathered into pts (zero padded).  The result does not   */
+/* depend on thread timing: it is bit-identical run to run.                                  */
+/*                                                                                           */
+/* Outputs (device, written for every frame; G = nx*ny, P = max_pillars):                    */
+/*   cell           int32 [B][cap_points]   cell per point, -1 if dropped (rows >= n unset)   */
+/*   cnt            uint32[B][G]            points per cell                                   */
+/*   pillar_of_cell int32 [B][G]            pillar id of the cell, -1 if not a kept pillar    */
+/*   coord          int32 [B][P]            cell of pillar p (p < num_pillars[b])             */
+/*   npts           int32 [B][P]            min(count, 32) of pillar p                        */
+/*   num_pillars    int32 [B]                                                                 */
+/*   pts            float [B][P][32][4]     kept points of pillar p, zero rows after npts     */
+/* Entries for p >= num_pillars[b] are unspecified.  n_points is a DEVICE array [B] so that a */
+/* captured CUDA graph can be replayed with new counts; each value must be in [0, cap_points];*/
+/* a value outside that range makes the frame empty and sets the error word in the workspace  */
+/* (reported by pp_voxelize_check).                                                          */
+/* workspace: device scratch of pp_voxelize_workspace_bytes() bytes, 256-byte aligned.        */
+size_t pp_voxelize_workspace_bytes(const pp_geometry* g, int32_t batch, int32_t cap_points);
+int pp_voxelize(const pp_geometry* g, int32_t batch, int32_t cap_points,
+                const float* points, const int32_t* n_points,
+                int32_t* cell, uint32_t* cnt, int32_t* pillar_of_cell,
+                int32_t* coord, int32_t* npts, int32_t* num_pillars, float* pts,
+                void* workspace, size_t workspace_bytes, void* stream);
+/* Synchronises `stream`, then reads the workspace's error word: PP_OK or PP_EINVAL (a
+ * n_points value was out of range). */
+int pp_voxelize_check(const void* workspace, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Stage 2: PointNet.  Per pillar p < num_pillars[b] and channel c < 64:                     */
+/*   features f = (x, y, z, r, x-mx, y-my, z-mz, x-xc, y-yc) per kept point, where (mx,my,mz)*/
+/*   is the mean of the pillar's kept points and (xc, yc) = (xmin + (ix+.5) vx,              */
+/*   ymin + (iy+.5) vy) is its cell centre;                                                  */
+/*   feat[b][p][c] = max over the kept points of ReLU(scale[c] * (W[c] . f) + shift[c]).     */
+/* pfn_w: device float [64][9] (Linear weight, no bias).  scale_shift: device float [2][64]  */
+/* (inference BN folded, see pp_bn_fold).  feat: device float [B][P][64]; rows p >=           */
+/* num_pillars[b] are unspecified.  Computed in FP32.                                        */
+int pp_pointnet(const pp_geometry* g, int32_t batch, const float* pts, const int32_t* npts,
+                const int32_t* coord, const int32_t* num_pillars, const float* pfn_w,
+                const float* scale_shift, float* feat, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Stage 3: BEV scatter.  Writes the WHOLE padded canvas [B][ny+2][nx+2][64] (dtype PP_F32   */
+/* or PP_BF16, round to nearest even): interior pixel (iy, ix) gets feat[b][p] if            */
+/* pillar_of_cell[b][iy*nx+ix] = p >= 0, else zeros; the border is zero.  One coalesced pass, */
+/* so no separate clear is needed.                                                           */
+int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
+               const int32_t* pillar_of_cell, void* canvas, int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Stage 4: one backbone layer, conv3x3 (zero pad 1, stride 1 or 2, no bias) + folded BN +    */
+/* ReLU, implicit GEMM over padded NHWC.                                                     */
+/*   in : [B][H+2][W+2][cin]  of dtype, border zero                                          */
+/*   out: [B][Ho+2][Wo+2][cout] of dtype, Ho = (H-1)/stride + 1, Wo = (W-1)/stride + 1; only  */
+/*        the interior is written (the border must already be zero).                          */
+/*   w  : packed weights from pp_conv_pack_weights for the same dtype.                       */
+/*   scale_shift: device float [2][cout].                                                    */
+/* PP_F32: CUDA-core FP32 FMA.  PP_BF16: tcgen05 tensor cores, BF16 x BF16 -> FP32 in TMEM,   */
+/* BF16 output.  cin, cout must be multiples of 64; stride 2 needs even H and W.              */
+/* tile: -1 = library choice (autotuned table when present), else an index into the tile     */
+/* list of pp_conv_tile_count(dtype).                                                        */
+int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
+               int32_t dtype, const void* in, const void* w, const float* scale_shift,
+               void* out, int32_t tile, void* stream);
+int pp_conv_tile_count(int32_t dtype);
+
+/* Repacks float OIHW weights [cout][cin][3][3] (device) into the layout pp_conv3x3 expects
+ * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,
+ * PP_BF16 -> [cout][9*cin] bf16 (round to nearest even), K index = (ky*3+kx)*cin + ci. */
+size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype);
+int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t dtype,
+                         void* w_packed, void* stream);
+
+/* Host helper: folds inference BN rows (gamma, beta, mean, var) [4][c] (host float) into
+ * scale = gamma / sqrt(var + eps), shift = beta - mean * scale, written to out [2][c] (host
+ * float), computed in double.  eps is the BN epsilon (1e-3 for this network). */
+int pp_bn_fold(const float* bn, int32_t c, float eps, float* out);
+
+/* Reads the library's sticky device error word (bit 1: a TMA producer wait timed out, bit 2: an
+ * MMA wait timed out, bit 4: an epilogue wait timed out in the tensor-core conv; the kernel
+ * that hit it skipped its stores).  Synchronous (device-wide copy).  clear != 0 resets it. */
+int pp_device_error(uint32_t* code, int32_t clear);
+
+/* ======================================================================================== */
+/* Serving runtime.                                                                          */
+/*                                                                                           */
+/* Chains release frames periodically (Section 4.1); each frame runs the pillar front end and */
+/* must finish by its absolute deadline.  The runtime admits frames under a fixed HBM budget, */
+/* keeps admitted frames on the host until release, and a dispatcher thread releases them in  */
+/* units of up to max_batch frames (one CUDA-graph launch per unit) following the paper's     */
+/* rules: urgency UL = 1/slack (Eq. 2), early exit of frames whose slack is negative          */
+/* (Section 4.3), task-level stream binding with a reserved top priority (Section 4.4.3),     */
+/* delayed launching behind urgent units of other chains (Section 4.4.4), and batched launch  */
+/* synchronisation with overlap (Section 4.4.5).  Policy PP_POLICY_FIFO is the plain baseline:*/
+/* every frame launched on arrival on its chain's default-priority stream, kernel by kernel,  */
+/* no graph, no batching, no urgency.                                                        */
+/* Times are microseconds on the host monotonic clock (pp_now_us).                           */
+/* Threading: every entry point may be called from any thread; one internal dispatcher       */
+/* thread does the rest.                                                                     */
+
+enum { PP_POLICY_FIFO = 0, PP_POLICY_URGENCY = 1 };
+enum { PP_FRAME_DONE = 0, PP_FRAME_DROPPED = 1, PP_FRAME_ERROR = 2 };
+#define PP_MAX_BLOCKS 4
+#define PP_MAX_CHAINS 64
+
+typedef struct {
+  pp_geometry geom;
+  /* backbone: block b has convs[b] conv3x3 layers of chans[b] channels, the first one with
+   * stride strides[b] (the others stride 1).  Input channels of the first layer: 64. */
+  int32_t n_blocks, convs[PP_MAX_BLOCKS], chans[PP_MAX_BLOCKS], strides[PP_MAX_BLOCKS];
+  /* weights, host float, copied by pp_create: pfn_w [64][9]; pfn_bn [4][64]; per layer
+   * conv_w[l] [cout][cin][3][3] and conv_bn[l] [4][cout].  BN rows: gamma, beta, mean, var;
+   * epsilon 1e-3. */
+  const float* pfn_w;
+  const float* pfn_bn;
+  const float* const* conv_w;
+  const float* const* conv_bn;
+  int32_t max_batch;            /* frames per release unit, 1..8                              */
+  int32_t cap_points;           /* maximum points per frame                                   */
+  int32_t precisions;           /* bit 0: FP32 units, bit 1: BF16 units                       */
+  int32_t units;                /* units per precision; 0 = as many as the budget allows (16) */
+  uint64_t hbm_budget_bytes;    /* device memory the context may hold (units + staging)       */
+  int32_t policy;               /* PP_POLICY_FIFO or PP_POLICY_URGENCY                        */
+  int32_t use_graphs;           /* replay one CUDA graph per unit launch                      */
+  double delta_eval_us;         /* batch closes when its estimated GPU time reaches this      */
+  int32_t max_closed;           /* closed batches allowed in flight: 2 overlapped, 1 sync,    */
+                                /* 0 = no synchronisation                                     */
+  double delay_quantum_us;      /* re-check period of a delayed release                       */
+  double th_urgent;             /* UL threshold (1/us); 0 = calibrate, < 0 = off              */
+  int32_t th_calib_frames;      /* frames sampled for the calibration (p95 of max UL)         */
+  double util_exempt;           /* units below this utilisation are never delayed             */
+  int32_t early_exit;           /* drop frames whose slack is negative                        */
+  int32_t num_streams;          /* stream priority levels per chain; 0 = device range         */
+} pp_config;
+
+/* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
+ * max_batch 8, delta_eval 500 us, max_closed 2, delay quantum 1000 us, th_urgent 0 (calibrate
+ * over 64 frames), util_exempt 0.1, early_exit 1, graphs on, both precisions, budget 20 GiB). */
+void pp_config_defaults(pp_config* cfg);
+
+typedef struct pp_ctx pp_ctx;
+
+/* Creates a context on the current CUDA device: uploads weights, allocates the units (each
+ * holding buffers for max_batch frames), captures their graphs, starts the dispatcher.
+ * PP_ENOMEM if one unit per enabled precision does not fit the budget. */
+int pp_create(const pp_config* cfg, pp_ctx** out);
+
+/* Declares a chain.  period/deadline in milliseconds (informational/default deadline);
+ * precision PP_F32 or PP_BF16 (needs that precision enabled).  Up to PP_MAX_CHAINS ids,
+ * 0 <= chain_id < PP_MAX_CHAINS. */
+int pp_register_chain(pp_ctx* ctx, int32_t chain_id, double period_ms, double rel_deadline_ms,
+                      int32_t precision);
+
+/* Submits one frame of `n_points` float4 points.  is_device_ptr = 0: host memory, copied
+ * before the call returns; 1: device memory, borrowed until the frame's result is polled.
+ * t_arrival_us / abs_deadline_us on the pp_now_us clock (abs_deadline_us <= 0: arrival +
+ * the chain's deadline).  PP_EAGAIN when admitting the frame would exceed the HBM budget. */
+int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_points,
+                    int32_t is_device_ptr, double t_arrival_us, double abs_deadline_us,
+                    uint64_t* frame_id_out);
+
+typedef struct {
+  uint64_t frame_id;
+  int32_t chain_id;
+  int32_t status;               /* PP_FRAME_DONE / PP_FRAME_DROPPED / PP_FRAME_ERROR          */
+  double t_arr_us, t_release_us, t_done_us, deadline_us;
+  int32_t missed;               /* t_done > deadline, or dropped                              */
+  int32_t num_pillars;
+  int32_t batch;                /* frames in the unit this frame ran in                       */
+  int32_t level;                /* stream priority level it was released on (0 = highest)     */
+  const void* out_dev;          /* last backbone layer, padded NHWC [out_h+2][out_w+2][out_c] */
+  int32_t out_c, out_h, out_w, out_dtype;
+  const void* block_dev[PP_MAX_BLOCKS];  /* output of each block, same layout                 */
+  int32_t block_c[PP_MAX_BLOCKS], block_h[PP_MAX_BLOCKS], block_w[PP_MAX_BLOCKS];
+} pp_result;
+
+/* Drains up to `max` completed frames into out[]; waits up to timeout_us for the first one
+ * (0 = do not wait).  *n_out = number written (0 on timeout, return PP_OK).  Output buffers
+ * stay valid until pp_result_release(frame_id). */
+int pp_poll(pp_ctx* ctx, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us);
+int pp_result_release(pp_ctx* ctx, uint64_t frame_id);
+
+typedef struct {
+  uint64_t submitted, done, dropped, missed, rejected;
+  double overall_miss_ratio;     /* Eq. 3: mean over chains of misses / frames               */
+  double lat_p50_us, lat_p99_us, lat_mean_us;
+  double frames_per_s;           /* completed frames / (last done - first arrival)           */
+  uint64_t units_launched;
+  double mean_batch;
+  uint64_t delayed_releases;
+  double delayed_us;
+  uint64_t collisions;           /* launches made while another chain's urgent unit ran      */
+  double sched_us_per_decision;
+  double th_urgent;              /* threshold in use (1/us)                                  */
+  uint64_t chain_frames[PP_MAX_CHAINS], chain_missed[PP_MAX_CHAINS];
+  double chain_p99_us[PP_MAX_CHAINS];
+} pp_stats;
+
+int pp_get_stats(pp_ctx* ctx, pp_stats* out);
+/* Stops the dispatcher, waits (bounded, 10 s) for in-flight units, frees everything.
+ * PP_ETIMEDOUT if the device did not finish in time (resources are then leaked, not freed). */
+int pp_destroy(pp_ctx* ctx);
+/* Host monotonic clock in microseconds. */
+double pp_now_us(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* One release unit without the runtime: buffers for `max_batch` frames of one precision,    */
+/* the whole front end as plain launches or one CUDA graph per batch size.                   */
+typedef struct pp_pipeline pp_pipeline;
+int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** out);
+/* frames: host array of n pointers to each frame's points (host or device memory, copied into
+ * the unit's slots on `stream`); counts: host array of n point counts.  Enqueues everything on
+ * `stream` and returns without waiting. */
+int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames,
+                    const int32_t* counts, int32_t use_graph, void* stream);
+/* Device pointer to block `block`'s output for frame slot i (padded NHWC) and its shape; pass
+ * block = -1 for the number of pillars (int32 device pointer, dims unset). */
+int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** dev,
+                       int32_t* c, int32_t* h, int32_t* w);
+size_t pp_pipeline_bytes(pp_pipeline* p);
+int pp_pipeline_destroy(pp_pipeline* p);
+
+/* ---------------------------------------------------------------------------------------- */
+/* The release rule as a pure function (what the dispatcher calls on every decision), exported */
+/* so that decisions can be replayed against an independent implementation.                  */
+typedef struct {
+  uint64_t frame_id;
+  int32_t chain_id, precision;
+  double t_arr_us, deadline_us, est_gpu_us, est_cpu_us, util;
+} pp_policy_frame;
+typedef struct {
+  int32_t chain_id;
+  double ul;                     /* urgency of an active unit when it was released (1/us)     */
+} pp_policy_active;
+typedef struct {
+  int32_t policy, max_batch, max_closed, num_pri, early_exit;
+  double th_urgent, util_exempt;
+} pp_policy_config;
+enum { PP_DECIDE_NONE = 0, PP_DECIDE_RELEASE = 1, PP_DECIDE_WAIT = 2, PP_DECIDE_DELAY = 3 };
+typedef struct {
+  int32_t kind, level, n_frames, n_drops;
+  uint64_t frames[8];            /* released frame ids (kind RELEASE), most urgent first     */
+} pp_policy_decision;
+/* drops: caller array of drops_cap entries receiving the ids of frames to drop (early exit);
+ * n_drops counts them all even if more than drops_cap. */
+int pp_policy_decide(const pp_policy_config* cfg, double t_us, const pp_policy_frame* ready,
+                     int32_t n_ready, const pp_policy_active* active, int32_t n_active,
+                     int32_t closed_pending, pp_policy_decision* out, uint64_t* drops,
+                     int32_t drops_cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PP_H_ */

@@ -1,0 +1,436 @@
+// BF16 conv3x3 + folded BN + ReLU on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// Implicit GEMM over padded NHWC bf16:  M = output pixels, N = cout, K = 9*cin in (ky, kx, ci)
+// order.  One CTA computes a 128 x BN output tile whose 128 pixels form a bh x bw box of one
+// frame (bh*bw = 128), so one tiled TMA copy fetches the whole A operand of a (tap, 64-channel)
+// K block: the zero border of the padded layout supplies the halo, and stride 2 is expressed
+// by viewing each padded row/column pair as (index/2, index%2) in a 5-D tensor map.  The
+// weights ([cout][9*cin] bf16) come in by a 2-D tensor map.  Both land in shared memory in the
+// 128-byte-swizzled K-major layout that tcgen05.mma reads directly.
+//
+// Warp roles (128 threads):  warp 0 lane 0 issues TMA into a STAGES-deep ring (full/empty
+// mbarriers); warp 1 lane 0 issues tcgen05.mma (M=128, N=BN, K=16) accumulating in TMEM and
+// frees each stage with tcgen05.commit; then all four warps read the accumulator back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows), apply BN + ReLU in FP32, round
+// to bf16 and store.  Every mbarrier wait is bounded (%globaltimer); on timeout the kernel sets
+// the library's device error word, skips its stores, frees its TMEM and returns.
+#include "pp_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace pp {
+
+__device__ unsigned g_tc_error;  // sticky device error word of the tensor-core conv
+
+namespace {
+
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr int kBM = 128;
+constexpr int kBK = 64;                              // channels per K block (128 bytes)
+constexpr uint32_t kABytes = kBM * kBK * 2;          // 16 KiB
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned tc_error_now() {
+  return *reinterpret_cast<volatile unsigned*>(&g_tc_error);
+}
+// Bounded wait; false on timeout (after recording `code` in the device error word) or as soon
+// as another CTA has recorded an error, so that one failure does not cost a timeout per CTA.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned code) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (!mbar_try(bar, parity)) {
+    if (tc_error_now() != 0u) return false;
+    if (now_ns() - t0 > kTimeoutNs) {
+      atomicOr(&g_tc_error, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0,
+                                       int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tma_5d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0,
+                                       int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0,
+                                       int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)(16u >> 4) << 16;             // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, M=128, N=BN.
+template <int BN>
+__device__ __forceinline__ uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  ConvShape c;
+  int bh, bw, tiles_x, tiles_y;
+  const float* ss;
+  __nv_bfloat16* out;
+};
+
+template <int BN, int STAGES, bool S2>
+__global__ void __launch_bounds__(128, 1)
+conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           TcArgs args) {
+  constexpr uint32_t kBBytes = BN * kBK * 2;
+  constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // power of two >= 32 (BN is 64/128/256)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kBBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  float* s_ss = reinterpret_cast<float*>(tmem_slot + 4);  // [2][BN]
+
+  const ConvShape& c = args.c;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx = blockIdx.x;
+  const int tx = bx % args.tiles_x;
+  const int ty = (bx / args.tiles_x) % args.tiles_y;
+  const int b = bx / (args.tiles_x * args.tiles_y);
+  const int n0 = blockIdx.y * BN;
+  const int oy0 = ty * args.bh, ox0 = tx * args.bw;
+
+  // a previous failure (sticky until the host clears it) turns every later CTA into a no-op
+  __shared__ unsigned s_abort;
+  if (threadIdx.x == 0) s_abort = tc_error_now();
+  __syncthreads();
+  if (s_abort != 0u) return;
+  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+    s_ss[i] = args.ss[n0 + i];
+    s_ss[BN + i] = args.ss[c.cout + n0 + i];
+  }
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], 1);
+      }
+      mbar_init(accum, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int kchunks = c.cin / kBK;
+  const int KB = 9 * kchunks;
+  const int Hp2 = (c.H + 2) / 2;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) break;
+      const int tap = kb / kchunks, cc = kb % kchunks;
+      const int ky = tap / 3, kx = tap % 3;
+      mbar_expect_tx(&full[s], kABytes + kBBytes);
+      if (S2)
+        tma_5d(sA + s * kABytes, &tmA, &full[s], cc * kBK, kx & 1, ox0 + (kx >> 1), ky & 1,
+               b * Hp2 + oy0 + (ky >> 1));
+      else
+        tma_3d(sA + s * kABytes, &tmA, &full[s], cc * kBK, ox0 + kx, b * (c.H + 2) + oy0 + ky);
+      tma_2d(sB + s * kBBytes, &tmB, &full[s], tap * c.cin + cc * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t id = idesc<BN>();
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, 2u)) break;
+      tc_fence_after();
+      const uint8_t* a = sA + s * kABytes;
+      const uint8_t* bb = sB + s * kBBytes;
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k)
+        mma_bf16(tmem, sdesc(a + k * 32), sdesc(bb + k * 32), id, (kb | k) != 0);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accum);
+  }
+  __syncwarp();
+
+  // epilogue: TMEM -> registers -> BN + ReLU -> bf16 -> global
+  const bool ok = mbar_wait(accum, 0u, 4u);
+  __syncwarp();
+  tc_fence_after();
+  const int r = warp * 32 + lane;
+  const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
+  const bool store = ok && oy < c.Ho && ox < c.Wo;
+  __nv_bfloat16* o = args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0;
+#pragma unroll 1
+  for (int j = 0; j < BN / 16; ++j) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 16), v);
+    if (store) {
+      uint32_t pk[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = j * 16 + 2 * i;
+        const float a0 = fmaxf(fmaf(v[2 * i], s_ss[n], s_ss[BN + n]), 0.f);
+        const float a1 = fmaxf(fmaf(v[2 * i + 1], s_ss[n + 1], s_ss[BN + n + 1]), 0.f);
+        __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+        pk[i] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(o + j * 16);
+      dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+// ---------------------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct TileTC {
+  int bh, bw, bn, stages;
+};
+// bh*bw must be 128.  The table is the autotuner's search space.
+constexpr TileTC kTilesTC[] = {
+    {8, 16, 64, 4},  {4, 32, 64, 4},  {16, 8, 64, 4},  {2, 64, 64, 4}, {1, 128, 64, 4},
+    {8, 16, 128, 4}, {4, 32, 128, 4}, {16, 8, 128, 4}, {8, 16, 256, 3}, {4, 32, 256, 3},
+    {16, 8, 256, 3}, {8, 16, 64, 6},
+};
+
+template <int BN, int STAGES>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)STAGES * (kABytes + BN * kBK * 2) + (2 * STAGES + 1) * 8 + 16 +
+         2 * BN * sizeof(float);
+}
+
+template <int BN, int STAGES, bool S2>
+int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, dim3 grid,
+              cudaStream_t s) {
+  constexpr size_t bytes = smem_bytes<BN, STAGES>();
+  static bool attr_set = false;  // per instantiation, set once (same device for the process)
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc<BN, STAGES, S2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e, "conv tc smem attribute");
+    attr_set = true;
+  }
+  conv3x3_tc<BN, STAGES, S2><<<grid, 128, bytes, s>>>(a, w, args);
+  return cuda_status(cudaGetLastError(), "conv tc launch");
+}
+
+int pick_tile(const ConvShape& c) {
+  // least padded work, then the wider N tile (fewer A re-reads), then fewer CTAs
+  int best = -1;
+  double best_cost = 1e30;
+  for (int i = 0; i < (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])); ++i) {
+    const TileTC& t = kTilesTC[i];
+    if (c.cout % t.bn || t.stages != (t.bn == 256 ? 3 : 4)) continue;
+    const double tiles = (double)((c.Ho + t.bh - 1) / t.bh) * ((c.Wo + t.bw - 1) / t.bw);
+    const double cost = tiles * 128.0 * (1.0 + 0.25 * 64.0 / t.bn);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = i; }
+  }
+  return best;
+}
+
+}  // namespace
+
+int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])); }
+
+int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w,
+                     const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  if (tile < 0) tile = pick_tile(c);
+  if (tile < 0 || tile >= conv_bf16_tile_count() || c.cout % kTilesTC[tile].bn)
+    return fail(PP_EINVAL, "conv bf16: tile %d unsupported for cout %d", tile, c.cout);
+  const TileTC t = kTilesTC[tile];
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
+    return fail(PP_EINVAL, "conv bf16: operands must be 16-byte aligned");
+  const int Hp = c.H + 2, Wp = c.W + 2;
+  CUtensorMap ta, tw;
+  CUresult r;
+  if (c.stride == 1) {
+    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 2, (cuuint64_t)Wp * c.cin * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(in), dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
+    cuuint64_t strides[4] = {(cuuint64_t)c.cin * 2, (cuuint64_t)c.cin * 4,
+                             (cuuint64_t)Wp * c.cin * 2, (cuuint64_t)Wp * c.cin * 4};
+    cuuint32_t box[5] = {(cuuint32_t)kBK, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(in), dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv bf16: activation tensor map (%d)", (int)r);
+  {
+    const int K = 9 * c.cin;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c.cout};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)t.bn};
+    cuuint32_t es[2] = {1, 1};
+    r = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(w), dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv bf16: weight tensor map (%d)", (int)r);
+  TcArgs args;
+  args.c = c;
+  args.bh = t.bh;
+  args.bw = t.bw;
+  args.tiles_x = (c.Wo + t.bw - 1) / t.bw;
+  args.tiles_y = (c.Ho + t.bh - 1) / t.bh;
+  args.ss = ss;
+  args.out = out;
+  const dim3 grid((unsigned)(args.tiles_x * args.tiles_y * c.batch), (unsigned)(c.cout / t.bn));
+  const bool s2 = c.stride == 2;
+#define PP_TC_CASE(BN, ST)                                                       \
+  if (t.bn == BN && t.stages == ST)                                              \
+    return s2 ? launch_tc<BN, ST, true>(ta, tw, args, grid, s)                   \
+              : launch_tc<BN, ST, false>(ta, tw, args, grid, s);
+  PP_TC_CASE(64, 4)
+  PP_TC_CASE(64, 6)
+  PP_TC_CASE(128, 4)
+  PP_TC_CASE(256, 3)
+#undef PP_TC_CASE
+  return fail(PP_EINVAL, "conv bf16: no kernel for tile %d", tile);
+}
+
+int tc_error_read(unsigned* code, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(code, g_tc_error, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_status(e, "read device error word");
+  if (clear && *code) {
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_status(e, "clear device error word");
+  }
+  return PP_OK;
+}
+
+}  // namespace pp

@@ -1,0 +1,176 @@
+// PointNet (PFN) over pillars and the BEV scatter, batched over frames (PointPillars front end
+// of the paper's 3D-perception chains, Section 6 / Table 4).
+//
+// pfn_fused: one warp per pillar.  Lane j builds the 9 features of point j into shared memory
+// (pillar mean by warp shuffles), then lane c owns channels c and c+32 and runs
+// Linear(9->64) + folded BN + ReLU over the valid points, keeping a running max in registers.
+// The 9x64 weights and the BN scale/shift are staged in shared memory once per block.
+//
+// bev_scatter: a single gather pass over the whole padded canvas -- every 16-byte chunk of every
+// pixel is written exactly once (feature row of the pillar at that cell, zeros elsewhere and on
+// the border), so no separate clear is needed and all stores are coalesced 16-byte vectors.
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;
+
+__global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restrict__ pts,
+                                                 const int* __restrict__ npts,
+                                                 const int* __restrict__ coord,
+                                                 const int* __restrict__ num_pillars,
+                                                 const float* __restrict__ pfn_w,
+                                                 const float* __restrict__ ss,
+                                                 float* __restrict__ feat) {
+  __shared__ float w_s[9][64];          // transposed: w_s[k][c] = W[c][k]
+  __shared__ float sc_s[64], sh_s[64];
+  __shared__ float f_s[kWarps][32][10];  // features per point (+1 pad)
+  for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
+    const int c = i / 9, k = i % 9;
+    w_s[k][c] = pfn_w[i];
+  }
+  if (threadIdx.x < 64) {
+    sc_s[threadIdx.x] = ss[threadIdx.x];
+    sh_s[threadIdx.x] = ss[64 + threadIdx.x];
+  }
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.x * kWarps + wid;
+  if (p >= num_pillars[b]) return;  // warp-uniform; no block barrier follows
+  const size_t q = (size_t)b * g.P + p;
+  const int n = npts[q];
+  const float4 v = pts[q * 32 + lane];
+  const bool valid = lane < n;
+  float sx = valid ? v.x : 0.f, sy = valid ? v.y : 0.f, sz = valid ? v.z : 0.f;
+  for (int o = 16; o; o >>= 1) {
+    sx += __shfl_xor_sync(kFull, sx, o);
+    sy += __shfl_xor_sync(kFull, sy, o);
+    sz += __shfl_xor_sync(kFull, sz, o);
+  }
+  const float inv = 1.f / (float)n;
+  const float mx = sx * inv, my = sy * inv, mz = sz * inv;
+  const int cell = coord[q];
+  const int ix = cell % g.nx, iy = cell / g.nx;
+  const float xc = g.xmin + ((float)ix + 0.5f) * g.vx;
+  const float yc = g.ymin + ((float)iy + 0.5f) * g.vy;
+  float* f = f_s[wid][lane];
+  f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+  f[4] = v.x - mx; f[5] = v.y - my; f[6] = v.z - mz;
+  f[7] = v.x - xc; f[8] = v.y - yc;
+  __syncwarp();
+  const float s0 = sc_s[lane], s1 = sc_s[lane + 32];
+  const float h0 = sh_s[lane], h1 = sh_s[lane + 32];
+  float m0 = 0.f, m1 = 0.f;  // ReLU outputs are >= 0 and every pillar has >= 1 point
+  for (int j = 0; j < n; ++j) {
+    const float* fj = f_s[wid][j];
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      a0 = fmaf(fj[k], w_s[k][lane], a0);
+      a1 = fmaf(fj[k], w_s[k][lane + 32], a1);
+    }
+    m0 = fmaxf(m0, fmaxf(fmaf(a0, s0, h0), 0.f));
+    m1 = fmaxf(m1, fmaxf(fmaf(a1, s1, h1), 0.f));
+  }
+  feat[q * 64 + lane] = m0;
+  feat[q * 64 + lane + 32] = m1;
+}
+
+// FP32 canvas: 16 chunks of 4 channels per pixel.
+__global__ void bev_scatter_f32(Geom g, int batch, const float4* __restrict__ feat,
+                                const int* __restrict__ pillar_of_cell,
+                                float4* __restrict__ canvas) {
+  const int Wp = g.nx + 2, Hp = g.ny + 2;
+  const size_t total = (size_t)batch * Hp * Wp * 16;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 15);
+    const size_t pix = t >> 4;
+    const int x = (int)(pix % Wp);
+    const size_t r = pix / Wp;
+    const int y = (int)(r % Hp);
+    const int b = (int)(r / Hp);
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x >= 1 && x <= g.nx && y >= 1 && y <= g.ny) {
+      const int p = pillar_of_cell[(size_t)b * g.G + (size_t)(y - 1) * g.nx + (x - 1)];
+      if (p >= 0) val = feat[((size_t)b * g.P + p) * 16 + chunk];
+    }
+    canvas[t] = val;
+  }
+}
+
+// BF16 canvas: 8 chunks of 8 channels (16 bytes) per pixel, round to nearest even.
+__global__ void bev_scatter_bf16(Geom g, int batch, const float4* __restrict__ feat,
+                                 const int* __restrict__ pillar_of_cell,
+                                 uint4* __restrict__ canvas) {
+  const int Wp = g.nx + 2, Hp = g.ny + 2;
+  const size_t total = (size_t)batch * Hp * Wp * 8;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 7);
+    const size_t pix = t >> 3;
+    const int x = (int)(pix % Wp);
+    const size_t r = pix / Wp;
+    const int y = (int)(r % Hp);
+    const int b = (int)(r / Hp);
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (x >= 1 && x <= g.nx && y >= 1 && y <= g.ny) {
+      const int p = pillar_of_cell[(size_t)b * g.G + (size_t)(y - 1) * g.nx + (x - 1)];
+      if (p >= 0) {
+        const float4* src = feat + ((size_t)b * g.P + p) * 16 + chunk * 2;
+        const float4 a = src[0], c = src[1];
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(a.z, a.w);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(c.x, c.y);
+        __nv_bfloat162 h3 = __floats2bfloat162_rn(c.z, c.w);
+        val.x = *reinterpret_cast<unsigned*>(&h0);
+        val.y = *reinterpret_cast<unsigned*>(&h1);
+        val.z = *reinterpret_cast<unsigned*>(&h2);
+        val.w = *reinterpret_cast<unsigned*>(&h3);
+      }
+    }
+    canvas[t] = val;
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+}  // namespace
+
+int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,
+               const int* num_pillars, const float* pfn_w, const float* ss, float* feat,
+               cudaStream_t s) {
+  pfn_fused<<<dim3((g.P + kWarps - 1) / kWarps, batch), kWarps * 32, 0, s>>>(
+      g, pts, npts, coord, num_pillars, pfn_w, ss, feat);
+  return cuda_status(cudaGetLastError(), "pointnet launch");
+}
+
+int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
+                   void* canvas, int dtype, cudaStream_t s) {
+  const size_t pixels = (size_t)batch * (g.ny + 2) * (g.nx + 2);
+  const size_t chunks = pixels * (dtype == PP_F32 ? 16 : 8);
+  size_t blocks = (chunks + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  if (dtype == PP_F32)
+    bev_scatter_f32<<<(unsigned)blocks, 256, 0, s>>>(g, batch, (const float4*)feat,
+                                                     pillar_of_cell, (float4*)canvas);
+  else
+    bev_scatter_bf16<<<(unsigned)blocks, 256, 0, s>>>(g, batch, (const float4*)feat,
+                                                      pillar_of_cell, (uint4*)canvas);
+  return cuda_status(cudaGetLastError(), "scatter launch");
+}
+
+}  // namespace pp

@@ -1,0 +1,66 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pp.h"
+
+namespace pp {
+
+// Records `msg` as this thread's last error and returns `code` (for `return fail(...)`).
+int fail(int code, const char* fmt, ...);
+// Maps a CUDA error to PP_EDEVICE with a message naming `what`; PP_OK for cudaSuccess.
+int cuda_status(cudaError_t e, const char* what);
+void clear_error();
+const char* last_error();
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Kernel-side copy of the geometry with derived sizes.
+struct Geom {
+  float xmin, xmax, ymin, ymax, zmin, zmax, vx, vy;
+  int nx, ny, G, P;
+};
+
+int check_geometry(const pp_geometry* g, Geom* out);
+
+// ---- voxelisation (vox.cu)
+struct VoxWork {
+  int* err;          // [1] sticky error word
+  int* slot;         // [B][cap] arrival slot of a point inside its cell
+  int* csr;          // [B][cap] point indices grouped by kept pillar
+  int* pillar_start; // [B][P]
+  int* pillar_cnt;   // [B][P]
+  int2* tile_sums;   // [B][ntiles] (occupied cells, points) per tile of cells
+  int ntiles;
+};
+constexpr int kVoxTile = 2048;        // cells per scan tile (256 threads x 8)
+size_t vox_workspace_bytes(const Geom& g, int batch, int cap);
+VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
+int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
+               int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
+               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s);
+
+// ---- PointNet and scatter (pfn.cu)
+int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,
+               const int* num_pillars, const float* pfn_w, const float* scale_shift,
+               float* feat, cudaStream_t s);
+int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
+                   void* canvas, int dtype, cudaStream_t s);
+
+// ---- conv (conv_simt.cu, conv_tc.cu)
+struct ConvShape {
+  int batch, H, W, cin, cout, stride, Ho, Wo;
+};
+int conv_f32_launch(const ConvShape& c, const float* in, const float* w_kn, const float* ss,
+                    float* out, int tile, cudaStream_t s);
+int conv_f32_tile_count();
+int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w_nk,
+                     const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s);
+int conv_bf16_tile_count();
+int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
+
+}  // namespace pp

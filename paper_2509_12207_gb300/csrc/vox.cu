@@ -1,0 +1,297 @@
+// Voxelisation of LiDAR points into pillars (point -> cell -> pillar), batched over frames.
+//
+// The paper's 3D-perception chains run PointPillars (Section 6, Table 4); this is its first
+// stage, made deterministic: pillars are the occupied cells in ascending cell order (at most
+// P), and each keeps its 32 lowest-index points in ascending index order.
+//
+// Five launches per batch, gridDim.y = frame:
+//   1. vox_cell_count   cell per point; warp-aggregated atomic count per cell, which also hands
+//                       each point an arrival slot inside its cell (order arbitrary)
+//   2. vox_tile_sums    per tile of 2048 cells: (occupied cells, points)
+//   3. vox_scan         exclusive scans over cells -> pillar id (rank of occupied cell, kept if
+//                       < P), pillar's first point offset; writes coord / npts / num_pillars
+//   4. vox_bucket       point i -> csr[pillar_start + slot]: points grouped by kept pillar
+//   5. vox_select       one warp per pillar: the 32 smallest point indices of its group, sorted
+//                       by warp bitonic sort/merge, gathered into pts (zero padded)
+// Nothing depends on the order in which atomics land, so the output is bit-identical across
+// runs.  The cell index follows the binary32 contract of pp.h (__fsub_rn / __fdiv_rn, floorf).
+#include "pp_internal.h"
+
+#include <climits>
+
+namespace pp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int frame_points(const int* n_points, int b, int cap, int* err) {
+  int n = n_points[b];
+  if (n < 0 || n > cap) {
+    if (err && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(err, 1);
+    return 0;
+  }
+  return n;
+}
+
+__global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
+                               const int* __restrict__ n_points, int* __restrict__ cell,
+                               int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
+  const int b = blockIdx.y;
+  const int n = frame_points(n_points, b, cap, err);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x >= n) return;  // whole block idle (uniform exit)
+  const size_t row = (size_t)b * cap + i;
+  int c = -1;
+  if (i < n) {
+    const float4 p = points[row];
+    bool ok = p.x >= g.xmin && p.x < g.xmax && p.y >= g.ymin && p.y < g.ymax &&
+              p.z >= g.zmin && p.z < g.zmax;
+    if (ok) {
+      const float qx = floorf(__fdiv_rn(__fsub_rn(p.x, g.xmin), g.vx));
+      const float qy = floorf(__fdiv_rn(__fsub_rn(p.y, g.ymin), g.vy));
+      ok = qx >= 0.f && qx < (float)g.nx && qy >= 0.f && qy < (float)g.ny;
+      if (ok) c = (int)qy * g.nx + (int)qx;
+    }
+    cell[row] = c;
+  }
+  const unsigned valid = __ballot_sync(kFull, c >= 0);
+  if (c >= 0) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(valid, c);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&cnt[(size_t)b * g.G + c], (unsigned)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    slot[row] = (int)base + __popc(peers & ((1u << lane) - 1u));
+  }
+}
+
+// Sums of (occupied, points) over one tile of kVoxTile cells; 256 threads.
+__global__ void vox_tile_sums(Geom g, const unsigned* __restrict__ cnt, int2* __restrict__ sums,
+                              int ntiles) {
+  const int b = blockIdx.y;
+  const unsigned* c = cnt + (size_t)b * g.G;
+  const int base = blockIdx.x * kVoxTile;
+  int occ = 0, pts = 0;
+  for (int j = threadIdx.x; j < kVoxTile; j += blockDim.x) {
+    const int k = base + j;
+    const unsigned v = k < g.G ? c[k] : 0u;
+    occ += v != 0u;
+    pts += (int)v;
+  }
+  for (int o = 16; o; o >>= 1) {
+    occ += __shfl_xor_sync(kFull, occ, o);
+    pts += __shfl_xor_sync(kFull, pts, o);
+  }
+  __shared__ int2 red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_int2(occ, pts);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int2 t = make_int2(0, 0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t.x += red[w].x; t.y += red[w].y; }
+    sums[(size_t)b * ntiles + blockIdx.x] = t;
+  }
+}
+
+// Exclusive block scan of a pair of ints over 256 threads; returns the prefix, sets *total.
+__device__ __forceinline__ int2 block_scan2(int2 v, int2* total) {
+  __shared__ int2 warp_tot[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int a = __shfl_up_sync(kFull, inc.x, o);
+    const int c = __shfl_up_sync(kFull, inc.y, o);
+    if (lane >= o) { inc.x += a; inc.y += c; }
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  int2 off = make_int2(0, 0), tot = make_int2(0, 0);
+  for (int w = 0; w < 8; ++w) {
+    if (w < wid) { off.x += warp_tot[w].x; off.y += warp_tot[w].y; }
+    tot.x += warp_tot[w].x; tot.y += warp_tot[w].y;
+  }
+  __syncthreads();
+  *total = tot;
+  return make_int2(off.x + inc.x - v.x, off.y + inc.y - v.y);
+}
+
+__global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restrict__ cnt,
+                                                const int2* __restrict__ sums, int ntiles,
+                                                int* __restrict__ pillar_of_cell,
+                                                int* __restrict__ coord, int* __restrict__ npts,
+                                                int* __restrict__ pillar_start,
+                                                int* __restrict__ pillar_cnt,
+                                                int* __restrict__ num_pillars) {
+  const int b = blockIdx.y;
+  const unsigned* c = cnt + (size_t)b * g.G;
+  const int base = blockIdx.x * kVoxTile;
+  __shared__ unsigned tile[kVoxTile];
+  __shared__ int2 pre_red[8];
+  // prefix of the preceding tiles' sums
+  int2 pre = make_int2(0, 0);
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) {
+    const int2 s = sums[(size_t)b * ntiles + t];
+    pre.x += s.x; pre.y += s.y;
+  }
+  for (int o = 16; o; o >>= 1) {
+    pre.x += __shfl_xor_sync(kFull, pre.x, o);
+    pre.y += __shfl_xor_sync(kFull, pre.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) pre_red[threadIdx.x >> 5] = pre;
+  for (int j = threadIdx.x; j < kVoxTile; j += blockDim.x) {
+    const int k = base + j;
+    tile[j] = k < g.G ? c[k] : 0u;
+  }
+  __syncthreads();
+  pre = make_int2(0, 0);
+  for (int w = 0; w < 8; ++w) { pre.x += pre_red[w].x; pre.y += pre_red[w].y; }
+  // 8 consecutive cells per thread
+  unsigned v[8];
+  int2 loc = make_int2(0, 0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[j] = tile[threadIdx.x * 8 + j];
+    loc.x += v[j] != 0u;
+    loc.y += (int)v[j];
+  }
+  int2 tot;
+  int2 ex = block_scan2(loc, &tot);
+  int rank = pre.x + ex.x, start = pre.y + ex.y;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = base + threadIdx.x * 8 + j;
+    if (k >= g.G) break;
+    int pid = -1;
+    if (v[j] != 0u) {
+      if (rank < g.P) {
+        pid = rank;
+        const size_t q = (size_t)b * g.P + rank;
+        coord[q] = k;
+        npts[q] = v[j] < 32u ? (int)v[j] : 32;
+        pillar_start[q] = start;
+        pillar_cnt[q] = (int)v[j];
+      }
+      ++rank;
+      start += (int)v[j];
+    }
+    pillar_of_cell[(size_t)b * g.G + k] = pid;
+  }
+  if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) {
+    const int all = pre.x + tot.x;
+    num_pillars[b] = all < g.P ? all : g.P;
+  }
+}
+
+__global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
+                           const int* __restrict__ cell, const int* __restrict__ slot,
+                           const int* __restrict__ pillar_of_cell,
+                           const int* __restrict__ pillar_start, int* __restrict__ csr) {
+  const int b = blockIdx.y;
+  const int n = frame_points(n_points, b, cap, nullptr);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t row = (size_t)b * cap + i;
+  const int c = cell[row];
+  if (c < 0) return;
+  const int p = pillar_of_cell[(size_t)b * g.G + c];
+  if (p < 0) return;
+  csr[(size_t)b * cap + pillar_start[(size_t)b * g.P + p] + slot[row]] = i;
+}
+
+// Ascending bitonic sort of one int per lane across a warp.
+__device__ __forceinline__ int warp_sort(int v, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int o = __shfl_xor_sync(kFull, v, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      v = keep_min ? min(v, o) : max(v, o);
+    }
+  }
+  return v;
+}
+
+// Sorts a bitonic sequence held one per lane into ascending order.
+__device__ __forceinline__ int warp_bitonic_merge(int v, int lane) {
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const int o = __shfl_xor_sync(kFull, v, j);
+    v = (lane & j) == 0 ? min(v, o) : max(v, o);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
+                                                  const float4* __restrict__ points,
+                                                  const int* __restrict__ csr,
+                                                  const int* __restrict__ pillar_start,
+                                                  const int* __restrict__ pillar_cnt,
+                                                  const int* __restrict__ num_pillars,
+                                                  float4* __restrict__ pts) {
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= num_pillars[b]) return;  // warp-uniform
+  const size_t q = (size_t)b * g.P + p;
+  const int count = pillar_cnt[q];
+  const int* seg = csr + (size_t)b * cap + pillar_start[q];
+  int best = warp_sort(lane < count ? seg[lane] : INT_MAX, lane);
+  for (int k = 32; k < count; k += 32) {
+    int v = warp_sort(k + lane < count ? seg[k + lane] : INT_MAX, lane);
+    v = __shfl_sync(kFull, v, 31 - lane);          // reversed: best ++ v is bitonic
+    best = warp_bitonic_merge(min(best, v), lane);  // lower half = 32 smallest of the union
+  }
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < count) out = points[(size_t)b * cap + best];
+  pts[q * 32 + lane] = out;
+}
+
+}  // namespace
+
+size_t vox_workspace_bytes(const Geom& g, int batch, int cap) {
+  const int ntiles = (g.G + kVoxTile - 1) / kVoxTile;
+  size_t s = 256;                                            // err
+  s += align_up((size_t)batch * cap * sizeof(int), 256) * 2;  // slot, csr
+  s += align_up((size_t)batch * g.P * sizeof(int), 256) * 2;  // pillar_start, pillar_cnt
+  s += align_up((size_t)batch * ntiles * sizeof(int2), 256);
+  return s;
+}
+
+VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
+  VoxWork w;
+  char* p = static_cast<char*>(ws);
+  w.ntiles = (g.G + kVoxTile - 1) / kVoxTile;
+  w.err = reinterpret_cast<int*>(p);
+  p += 256;
+  w.slot = reinterpret_cast<int*>(p);
+  p += align_up((size_t)batch * cap * sizeof(int), 256);
+  w.csr = reinterpret_cast<int*>(p);
+  p += align_up((size_t)batch * cap * sizeof(int), 256);
+  w.pillar_start = reinterpret_cast<int*>(p);
+  p += align_up((size_t)batch * g.P * sizeof(int), 256);
+  w.pillar_cnt = reinterpret_cast<int*>(p);
+  p += align_up((size_t)batch * g.P * sizeof(int), 256);
+  w.tile_sums = reinterpret_cast<int2*>(p);
+  return w;
+}
+
+int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
+               int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
+               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_status(e, "memset cnt");
+  const dim3 pg((cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, batch);
+  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, n_points, cell, w.slot, cnt, w.err);
+  vox_tile_sums<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles);
+  vox_scan<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles, pillar_of_cell,
+                                                 coord, npts, w.pillar_start, w.pillar_cnt,
+                                                 num_pillars);
+  vox_bucket<<<pg, 256, 0, s>>>(g, cap, n_points, cell, w.slot, pillar_of_cell, w.pillar_start,
+                                w.csr);
+  vox_select<<<dim3((g.P + 7) / 8, batch), 256, 0, s>>>(g, cap, points, w.csr, w.pillar_start,
+                                                        w.pillar_cnt, num_pillars, pts);
+  return cuda_status(cudaGetLastError(), "voxelize launch");
+}
+
+}  // namespace pp

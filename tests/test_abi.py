@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function include/*.h
+declares; host-only entry points behave as documented.  CPU only (no compute calls)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(pp_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_12207_gb300 import _build
+    _build.build()
+    import paper_2509_12207_gb300 as pp
+    return pp.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 10
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    import paper_2509_12207_gb300 as pp
+    assert set(pp.declared_symbols()) <= _declared()
+    assert _declared() <= set(pp.declared_symbols())
+
+
+def test_version_and_errors(lib):
+    import paper_2509_12207_gb300 as pp
+    assert b"sm_103a" in lib.pp_version()
+    # argument validation runs on the host and records a message
+    g = pp.Geometry(0, 1, 0, 1, 0, 1, 0.5, 0.5, 2, 2, 4, 16)   # max_pts != 32
+    assert lib.pp_voxelize_workspace_bytes(ctypes.byref(g), 1, 10) == 0
+    rc = lib.pp_conv3x3(1, 8, 8, 48, 64, 1, 0, 16, 16, 16, 16, -1, None)
+    assert rc == pp.PP_EINVAL and b"multiples of 64" in lib.pp_last_error()
+    rc = lib.pp_conv3x3(1, 7, 8, 64, 64, 2, 0, 16, 16, 16, 16, -1, None)
+    assert rc == pp.PP_EINVAL and b"even" in lib.pp_last_error()
+    assert lib.pp_conv_packed_bytes(64, 128, 1) == 9 * 64 * 128 * 2
+
+
+def test_bn_fold_matches_definition(lib):
+    import paper_2509_12207_gb300 as pp
+    rng = np.random.default_rng(0)
+    bn = np.stack([rng.uniform(0.5, 1.5, 64), rng.uniform(-1, 1, 64), rng.normal(size=64),
+                   rng.uniform(0.1, 3, 64)]).astype(np.float32)
+    ss = pp.bn_fold(bn)
+    h = rng.normal(size=(100, 64)) * 3
+    want = bn[0] * (h - bn[2]) / np.sqrt(bn[3].astype(np.float64) + 1e-3) + bn[1]
+    np.testing.assert_allclose(h * ss[0] + ss[1], want, rtol=1e-6, atol=1e-6)

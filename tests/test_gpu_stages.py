@@ -1,0 +1,255 @@
+"""Parity of each stage entry point (through the C ABI) with the FP64 oracle.
+
+Integer outputs (cells, counts, pillar ids, coords, npts, gathered points, canvas positions)
+must match bit for bit; FP32 features and conv outputs within 1e-4 of the oracle (rel_err);
+the BF16 conv within 2e-2 of the oracle with unrounded weights, and within 8e-3 of the oracle
+fed the same bf16-rounded operands (only FP32 accumulation order and the output rounding
+differ there)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import pillars as O
+from pp_synth import (GEOM_FULL, GEOM_SMALL, Geometry, clustered_cloud, config_points,
+                      pillar_weights, uniform_cloud, BACKBONE_SMALL)
+from tests._util import BF16_TOL, FP32_TOL, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+import paper_2509_12207_gb300 as pp  # noqa: E402
+
+DEV = "cuda:0"
+TINY = Geometry(0.0, 1.28, -0.32, 0.64, -1.0, 1.0, 0.32, 0.32, 4, 3, 5)
+
+
+def _batch(clouds, cap=None):
+    cap = cap or max(1, max(len(c) for c in clouds))
+    pts = np.zeros((len(clouds), cap, 4), np.float32)
+    for i, c in enumerate(clouds):
+        pts[i, : len(c)] = c
+    n = np.array([len(c) for c in clouds], np.int32)
+    return torch.from_numpy(pts).to(DEV), torch.from_numpy(n).to(DEV)
+
+
+def _check_vox(g, clouds, v, b):
+    ref = O.voxelise(clouds[b], g)
+    n = len(clouds[b])
+    num = int(v["num_pillars"][b])
+    assert num == ref["num_pillars"]
+    np.testing.assert_array_equal(v["cell"][b, :n].cpu().numpy(), ref["cell"])
+    np.testing.assert_array_equal(v["cnt"][b].cpu().numpy(), ref["cnt"])
+    np.testing.assert_array_equal(v["pillar_of_cell"][b].cpu().numpy(), ref["pillar_of_cell"])
+    np.testing.assert_array_equal(v["coord"][b, :num].cpu().numpy(), ref["coord"])
+    np.testing.assert_array_equal(v["npts"][b, :num].cpu().numpy(), ref["npts"])
+    got = v["pts"][b, :num].cpu().numpy()
+    assert got.tobytes() == ref["pts"].tobytes()  # bit-exact, including zero padding
+    return ref
+
+
+def _edge_cloud(g, n, seed):
+    rng = np.random.default_rng(seed)
+    pts = uniform_cloud(n, seed, g)
+    k = n // 3
+    pts[:k, 0] = (rng.integers(0, g.nx + 1, k) * np.float32(g.vx) + np.float32(g.xmin)).astype(np.float32)
+    pts[:k, 1] = (rng.integers(0, g.ny + 1, k) * np.float32(g.vy) + np.float32(g.ymin)).astype(np.float32)
+    pts[k:k + 10, 2] = np.float32(g.zmax)
+    pts[k + 10:k + 20, 0] = np.nan
+    pts[k + 20:k + 30, 1] = np.float32(g.ymax)
+    pts[:200, 0] = np.float32(g.xmin) + np.float32(0.05)   # one crowded cell (> 32 points)
+    pts[:200, 1] = np.float32(g.ymin) + np.float32(0.05)
+    pts[:200, 2] = 0.0
+    return pts[rng.permutation(n)]
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "edges", "tiny"])
+def test_voxelize_single(name):
+    if name == "cfg1":
+        g, clouds = GEOM_SMALL, [config_points(1, 0)]
+    elif name == "cfg2":
+        g, clouds = GEOM_FULL, [config_points(2, 0)]
+    elif name == "edges":
+        g, clouds = GEOM_SMALL, [_edge_cloud(GEOM_SMALL, 30000, 3)]
+    else:
+        g, clouds = TINY, [_edge_cloud(TINY, 500, 4)]
+    pts, n = _batch(clouds)
+    v = pp.voxelize(pts, n, g)
+    torch.cuda.synchronize()
+    pp.voxelize_check(v)
+    _check_vox(g, clouds, v, 0)
+
+
+def test_voxelize_batched_uneven_and_degenerate():
+    g = GEOM_SMALL
+    clouds = [config_points(3, 0, 150000), np.zeros((0, 4), np.float32), config_points(3, 1, 31000),
+              uniform_cloud(50, 9, g) + np.float32(500.0),  # every point dropped
+              clustered_cloud(90000, 5, g)]
+    pts, n = _batch(clouds, cap=150000)
+    v = pp.voxelize(pts, n, g)
+    torch.cuda.synchronize()
+    for b in range(len(clouds)):
+        ref = _check_vox(g, clouds, v, b)
+        if b == 0:
+            assert ref["num_pillars"] == g.max_pillars   # the cap binds at 150k points
+    # determinism: a second run is bit-identical
+    w = pp.voxelize(pts, n, g)
+    torch.cuda.synchronize()
+    assert torch.equal(v["pillar_of_cell"], w["pillar_of_cell"])
+    assert torch.equal(v["num_pillars"], w["num_pillars"])
+    for b in range(len(clouds)):
+        num = int(v["num_pillars"][b])       # entries past num_pillars are unspecified
+        for k in ("coord", "npts", "pts"):
+            assert torch.equal(v[k][b, :num], w[k][b, :num])
+
+
+def test_voxelize_bad_count_reported():
+    g = GEOM_SMALL
+    pts, n = _batch([uniform_cloud(100, 1, g)])
+    n.fill_(1000)  # > cap: the frame is treated as empty and the error word is set
+    v = pp.voxelize(pts, n, g)
+    with pytest.raises(pp.PPError):
+        pp.voxelize_check(v)
+    assert int(v["num_pillars"][0]) == 0
+
+
+def _pfn_params(seed=7):
+    pfn_w, pfn_bn, _, _ = pillar_weights(BACKBONE_SMALL, seed)
+    ss = pp.bn_fold(pfn_bn)
+    return pfn_w, pfn_bn, torch.from_numpy(pfn_w).to(DEV), torch.from_numpy(ss).to(DEV)
+
+
+@pytest.mark.parametrize("g,cfg", [(GEOM_SMALL, 1), (GEOM_FULL, 2)])
+def test_pointnet_and_scatter(g, cfg):
+    cloud = config_points(cfg, 1)
+    pts, n = _batch([cloud])
+    v = pp.voxelize(pts, n, g)
+    pfn_w, pfn_bn, w_d, ss_d = _pfn_params()
+    feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], w_d, ss_d, g)
+    torch.cuda.synchronize()
+    ref = O.voxelise(cloud, g)
+    num = ref["num_pillars"]
+    rf = O.pointnet(ref["pts"], ref["npts"], ref["coord"], pfn_w, pfn_bn, g)
+    assert rel_err(feat[0, :num].cpu().numpy(), rf) <= FP32_TOL
+    # scatter positions are exact: feed the GPU features, compare with the oracle scatter of them
+    f32 = feat[0, :num].cpu().numpy().astype(np.float64)
+    canvas_ref = O.scatter(f32, ref["coord"], g)
+    for dt in (pp.PP_F32, pp.PP_BF16):
+        canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=dt)
+        torch.cuda.synchronize()
+        c = canvas[0].float().cpu().numpy()
+        assert not c[0].any() and not c[-1].any() and not c[:, 0].any() and not c[:, -1].any()
+        want = torch.from_numpy(canvas_ref).to(torch.float32)
+        if dt == pp.PP_BF16:
+            want = want.to(torch.bfloat16).float()
+        assert np.array_equal(c[1:-1, 1:-1], want.numpy())
+
+
+def test_scatter_batched_bf16_rounding():
+    g = GEOM_SMALL
+    clouds = [config_points(3, 2, 40000), config_points(3, 3, 120000)]
+    pts, n = _batch(clouds)
+    v = pp.voxelize(pts, n, g)
+    feat = torch.randn((2, g.max_pillars, 64), device=DEV) * 3
+    canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=pp.PP_BF16)
+    torch.cuda.synchronize()
+    for b in range(2):
+        num = int(v["num_pillars"][b])
+        coord = v["coord"][b, :num].long()
+        inner = canvas[b, 1:-1, 1:-1].reshape(-1, 64)
+        assert torch.equal(inner[coord], feat[b, :num].to(torch.bfloat16))
+        mask = torch.ones(inner.shape[0], dtype=torch.bool, device=DEV)
+        mask[coord] = False
+        assert not inner[mask].any()
+
+
+# ------------------------------------------------------------------ conv
+
+def _conv_case(B, H, W, cin, cout, s, seed, density=0.5):
+    rng = np.random.default_rng(seed)
+    x = np.maximum(rng.normal(size=(B, H, W, cin)), 0) * (rng.random((B, H, W, 1)) < density)
+    w = rng.normal(0, np.sqrt(2.0 / (9 * cin)), (cout, cin, 3, 3)).astype(np.float32)
+    bn = np.stack([rng.uniform(0.5, 1.5, cout), rng.uniform(-0.1, 0.1, cout),
+                   rng.normal(0, 0.1, cout), rng.uniform(0.5, 2.0, cout)]).astype(np.float32)
+    xp = np.zeros((B, H + 2, W + 2, cin), np.float32)
+    xp[:, 1:-1, 1:-1] = x
+    return xp, w, bn
+
+
+SHAPES = [(2, 20, 18, 64, 64, 1), (2, 20, 18, 64, 64, 2), (1, 34, 46, 128, 128, 1),
+          (1, 26, 30, 64, 128, 2), (1, 14, 10, 256, 256, 1), (1, 16, 18, 128, 256, 2),
+          (3, 9, 17, 64, 64, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_conv_f32(shape):
+    B, H, W, cin, cout, s = shape
+    xp, w, bn = _conv_case(B, H, W, cin, cout, s, seed=H * W + cin)
+    x_d = torch.from_numpy(xp).to(DEV)
+    wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_F32)
+    ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
+    refs = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
+    for tile in range(pp.conv_tile_count(pp.PP_F32)):
+        if cout % (64 if tile in (0, 1) else 128):
+            continue
+        out = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32, tile=tile)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        for b in range(B):
+            assert rel_err(o[b, 1:-1, 1:-1], refs[b]) <= FP32_TOL, (tile, b)
+            assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+TC_TILES = [(8, 16, 64), (4, 32, 64), (16, 8, 64), (2, 64, 64), (1, 128, 64), (8, 16, 128),
+            (4, 32, 128), (16, 8, 128), (8, 16, 256), (4, 32, 256), (16, 8, 256), (8, 16, 64)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_conv_bf16(shape):
+    B, H, W, cin, cout, s = shape
+    xp, w, bn = _conv_case(B, H, W, cin, cout, s, seed=H * W + cin + 1)
+    xb = _bf16(xp)
+    x_d = xb.to(DEV)
+    wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_BF16)
+    ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
+    x_r = xb.float().numpy().astype(np.float64)
+    w_r = torch.from_numpy(w).to(torch.bfloat16).float().numpy().astype(np.float64)
+    loose = [O.conv3x3_bn_relu(x_r[b, 1:-1, 1:-1], w, bn, s) for b in range(B)]
+    tight = [O.conv3x3_bn_relu(x_r[b, 1:-1, 1:-1], w_r, bn, s) for b in range(B)]
+    assert pp.conv_tile_count(pp.PP_BF16) == len(TC_TILES)
+    for tile, (_bh, _bw, bn_) in enumerate(TC_TILES):
+        if cout % bn_:
+            continue
+        out = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_BF16, tile=tile)
+        torch.cuda.synchronize()
+        assert pp.device_error() == 0
+        o = out.float().cpu().numpy()
+        for b in range(B):
+            assert rel_err(o[b, 1:-1, 1:-1], tight[b]) <= 8e-3, (tile, b)
+            assert rel_err(o[b, 1:-1, 1:-1], loose[b]) <= BF16_TOL, (tile, b)
+            assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
+
+
+def test_frame_config1_fp32_end_to_end():
+    g, bb = GEOM_SMALL, BACKBONE_SMALL
+    cloud = config_points(1, 0)
+    weights = pillar_weights(bb, 7)
+    ref = O.frame(cloud, g, bb, weights)
+    pfn_w, pfn_bn, conv_w, conv_bn = weights
+    pts, n = _batch([cloud])
+    v = pp.voxelize(pts, n, g)
+    feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
+                       torch.from_numpy(pfn_w).to(DEV), torch.from_numpy(pp.bn_fold(pfn_bn)).to(DEV), g)
+    x = pp.scatter(feat, v["pillar_of_cell"], g, dtype=pp.PP_F32)
+    for (ci, co, s), w, bn in zip(bb.layers(64), conv_w, conv_bn):
+        x = pp.conv3x3(x, pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_F32),
+                       torch.from_numpy(pp.bn_fold(bn)).to(DEV), co, s, dtype=pp.PP_F32)
+    torch.cuda.synchronize()
+    got = x[0, 1:-1, 1:-1].cpu().numpy()
+    assert got.shape == ref["blocks"][-1].shape
+    assert rel_err(got, ref["blocks"][-1]) <= FP32_TOL
