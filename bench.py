@@ -1,0 +1,397 @@
+"""Benchmark of the pillar front end on GB300 through the library's public C ABI.
+
+Default workload: full-size single frame, FP32 -- 120,000 points (70 % in 40 Gaussian blobs),
+0.16 m grid 432 x 496, 12,000 pillars x 32 points, PointNet 9->64, backbone 64/128/256 channels
+x 4/6/6 conv3x3 at strides 2/2/2.  One step = one frame through the whole hot path: admission
+(pp_submit_frame), release by the urgency rule, one graph launch (voxelise, PointNet, scatter,
+16 convs), completion (pp_poll) and release of the result.
+
+Prints one JSON line: frames/s with inputs resident in HBM (value), the same through host
+buffers with the H2D copy and a D2H read of the result inside the timed region (e2e), the conv
+kernels' roofline (FP32 FMA bound), the oracle's CPU baseline, clocks seen during the run.
+Multi-GPU: replicas only (frames are independent); rank 0 prints the aggregate.
+``--impl reference`` times the FP64 CPU oracle on the same workload (one frame per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cfg2-fp32": "full-size single frame FP32: 120k clustered points, 432x496 grid, 12000 pillars, "
+                 "backbone 64/128/256 x 4/6/6 conv3x3 strides 2/2/2",
+    "cfg1-fp32": "single frame FP32: 20k uniform points, 216x248 grid, 4000 pillars, 3 conv3x3 64ch",
+    "cfg3-bf16": "batched BF16: 8 frames of 30k-150k uniform points per unit, 216x248 grid, 3 conv3x3 64ch",
+}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2-fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def _workload(name):
+    from pp_synth import (BACKBONE_FULL, BACKBONE_SMALL, GEOM_FULL, GEOM_SMALL, batched_counts,
+                          config_points, pillar_weights)
+    if name == "cfg2-fp32":
+        g, bb, prec, batch, cap = GEOM_FULL, BACKBONE_FULL, 0, 1, 120000
+        frames = [config_points(2, k) for k in range(4)]
+    elif name == "cfg1-fp32":
+        g, bb, prec, batch, cap = GEOM_SMALL, BACKBONE_SMALL, 0, 1, 20000
+        frames = [config_points(1, k) for k in range(4)]
+    else:
+        g, bb, prec, batch, cap = GEOM_SMALL, BACKBONE_SMALL, 1, 8, 150000
+        counts = batched_counts(3)
+        frames = [config_points(3, k, n) for k, n in enumerate(counts)]
+    return g, bb, prec, batch, cap, frames, pillar_weights(bb, 7)
+
+
+def _conv_flops(g, bb):
+    tot = 0
+    H, W = g.ny, g.nx
+    for ci, co, s in bb.layers(64):
+        Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
+        tot += 2 * Ho * Wo * co * 9 * ci
+        H, W = Ho, Wo
+    return tot
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline)
+
+def _oracle_seconds(name, frames_to_run):
+    """Times the FP64 oracle on ``frames_to_run`` frames of the workload (this process)."""
+    from oracle import pillars as O
+    g, bb, _prec, _batch, _cap, frames, w = _workload(name)
+    t0 = time.perf_counter()
+    for k in range(frames_to_run):
+        O.frame(frames[k % len(frames)], g, bb, w)
+    return time.perf_counter() - t0
+
+
+def _cpu_baseline(name, n_frames=1):
+    """Runs the oracle single-threaded in a child process (BLAS pinned to one thread)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "%s:%d" % (name, n_frames),
+                          "--workload", name], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return {"value": None, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + out.stderr[-300:]}
+    secs = float(out.stdout.strip().splitlines()[-1])
+    return {"value": n_frames / secs, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full frame(s) of the workload through the FP64 NumPy oracle, one thread, %.1f s"
+                      % (n_frames, secs)}
+
+
+# ------------------------------------------------------------------ clocks
+
+def _die_with_parent():
+    """Child-side: ask Linux to SIGTERM this process when its parent exits (PR_SET_PDEATHSIG)."""
+    try:
+        import ctypes
+        import signal
+        ctypes.CDLL("libc.so.6", use_errno=True).prctl(1, signal.SIGTERM, 0, 0, 0)
+    except OSError:
+        pass
+
+
+class _Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs.
+    Always stopped by the caller (try/finally); the child also dies with this process and is
+    killed by a watchdog after `max_s` seconds."""
+
+    def __init__(self, gpu_index, enabled=True, max_s=600.0):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        if not enabled:
+            return
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL,
+                preexec_fn=_die_with_parent)
+            import threading
+            self.timer = threading.Timer(max_s, self._kill)
+            self.timer.daemon = True
+            self.timer.start()
+            time.sleep(0.5)  # let the sampler start before the timed region
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def _kill(self):
+        if self.p is not None and self.p.poll() is None:
+            self.p.kill()
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        self.timer.cancel()
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            self.p.wait(5)
+        self.f.close()
+        self.p = None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ measurements
+
+def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=10):
+    """Average duration of each conv layer's kernel, launched through pp_conv3x3 on the current
+    stream and timed with CUDA events around `reps` launches of it."""
+    dt = torch.float32 if prec == pp.PP_F32 else torch.bfloat16
+    H, W = g.ny, g.nx
+    x = torch.rand((batch, H + 2, W + 2, 64), device="cuda").to(dt)
+    x[:, 0] = 0; x[:, -1] = 0; x[:, :, 0] = 0; x[:, :, -1] = 0
+    per_layer = []
+    stream = torch.cuda.current_stream()
+    for (ci, co, s), wt, bn in zip(bb.layers(64), w[2], w[3]):
+        wp = pp.pack_conv_weights(torch.from_numpy(wt).cuda(), prec)
+        ss = torch.from_numpy(pp.bn_fold(bn)).cuda()
+        Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
+        out = torch.zeros((batch, Ho + 2, Wo + 2, co), dtype=dt, device="cuda")
+        pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        flops = 2.0 * batch * Ho * Wo * co * 9 * ci
+        per_layer.append((e0.elapsed_time(e1) / reps * 1e-3, flops))
+        x, H, W = out, Ho, Wo
+    return per_layer
+
+
+def _time_stages(pp, torch, g, frames_dev, w, prec, reps=10):
+    """Average duration of the voxelise / PointNet / scatter launches for one frame."""
+    stream = torch.cuda.current_stream()
+    pts = frames_dev[0][None].contiguous()
+    n = torch.tensor([pts.shape[1]], dtype=torch.int32, device="cuda")
+    pfn_w = torch.from_numpy(w[0]).cuda()
+    pfn_ss = torch.from_numpy(pp.bn_fold(w[1])).cuda()
+    v = pp.voxelize(pts, n, g)
+    feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], pfn_w, pfn_ss, g)
+    canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec)
+    out = {}
+    for name, fn in (("voxelize", lambda: pp.voxelize(pts, n, g)),
+                     ("pointnet", lambda: pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
+                                                      pfn_w, pfn_ss, g)),
+                     ("scatter", lambda: pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec))):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / reps
+    canvas_bytes = canvas.numel() * canvas.element_size()
+    return out, canvas_bytes, int(v["num_pillars"][0])
+
+
+def _run_ours(a, rank, world, dist):
+    import numpy as np
+    import torch
+    import paper_2509_12207_gb300 as pp
+
+    dev = rank % max(1, torch.cuda.device_count())
+    torch.cuda.set_device(dev)
+    g, bb, prec, batch, cap, frames, w = _workload(a.workload)
+    # throughput run: no deadline pressure (early exit off, 10 s deadline), so a slow run (a
+    # profiler) still completes every frame
+    cfg, keep = pp.make_config(g, bb, w, max_batch=batch, cap_points=cap, precisions=1 << prec, units=2,
+                               th_urgent=-1.0, early_exit=0)
+    ctx = pp.Context(cfg)
+    ctx.register_chain(0, 10000.0, 10000.0, prec)
+    frames_dev = [torch.from_numpy(f).cuda() for f in frames]
+    frames_host = [torch.from_numpy(f).pin_memory() for f in frames]
+    n_frames = batch
+
+    def step(k, host):
+        ids = []
+        for j in range(n_frames):
+            f = (frames_host if host else frames_dev)[(k * n_frames + j) % len(frames)]
+            rc, fid = ctx.submit(0, f.numpy() if host else f)
+            assert rc == pp.PP_OK, rc
+            ids.append(fid)
+        got = []
+        while len(got) < n_frames:
+            got += ctx.poll(16, timeout_us=1000000)
+        for r in got:
+            assert r.status == pp.PP_FRAME_DONE
+            if host:
+                # D2H read of the step's result (the last backbone layer)
+                nbytes = r.out_c * (r.out_h + 2) * (r.out_w + 2) * (4 if r.out_dtype == pp.PP_F32 else 2)
+                step.d2h += nbytes
+                step.sink = pp.result_tensor(r).cpu()
+            ctx.release(r.frame_id)
+    step.d2h = 0
+
+    def timed(host):
+        for k in range(a.warmup):
+            step(k, host)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t0 = time.perf_counter()
+        step.d2h = 0
+        for k in range(a.steps):
+            step(k, host)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        el = e0.elapsed_time(e1) * 1e-3
+        if dist is not None:
+            t = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        return el, wall
+
+    clocks = _Clocks(dev, enabled=not a.no_clocks)
+    try:
+        el, wall = timed(host=False)
+    finally:
+        clk = clocks.stop()
+    st = ctx.stats()
+    e2e_el, _ = timed(host=True)
+    h2d = sum(int(frames[(k * n_frames + j) % len(frames)].nbytes) for k in range(a.steps)
+              for j in range(n_frames)) // a.steps
+    d2h = step.d2h // a.steps
+    ctx.destroy()
+
+    # kernel roofline: the conv kernels dominate the step
+    layers = _time_conv_kernels(pp, torch, g, bb, w, prec, batch)
+    conv_s = sum(t for t, _ in layers)
+    conv_flops = sum(f for _, f in layers)
+    stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w, prec)
+    sm_max = (clk.get("sm_max_mhz") or 2070.0)
+    if prec == pp.PP_F32:
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # FP32 FMA lanes x 2 flops x clock
+        bound, peak_note = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_max
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        bound, peak_note = "tensor", "bf16 dense, of measured" if peaks else "bf16 dense, of fallback"
+    achieved = conv_flops / conv_s / 1e12
+    frames_done = a.steps * n_frames * world
+    res = {
+        "metric": "pillar frames/s", "value": frames_done / el, "unit": "frames/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOADS[a.workload], "frames_per_step": n_frames, "points_per_frame":
+                   [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
+                         % (canvas_bytes // 2 ** 20)},
+        "e2e": {"value": frames_done / e2e_el, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "conv3x3 (%s), all layers"
+                     % ("CUDA-core FP32" if prec == 0 else "tcgen05 BF16"), "peak_source": peak_note,
+                     "conv_ms_per_frame": conv_s * 1e3 / n_frames},
+        "stage_ms": {k: v for k, v in stages.items()},
+        "serving": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
+                    "sched_us_per_decision": st["sched_us_per_decision"], "units": st["units_launched"]},
+        "gpu_launches": a.steps * (5 + 1 + 1 + len(bb.layers(64))) * (1 if n_frames else 0),
+        "clocks": clk,
+        "num_pillars": num_p,
+        "wall_s": wall,
+    }
+    return res
+
+
+def _run_reference(a):
+    g, bb, prec, batch, cap, frames, w = _workload(a.workload)
+    from oracle import pillars as O
+    for k in range(a.warmup):
+        O.frame(frames[k % len(frames)], g, bb, w)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        for j in range(batch):
+            O.frame(frames[(k * batch + j) % len(frames)], g, bb, w)
+    secs = time.perf_counter() - t0
+    v = a.steps * batch / secs
+    cores = os.cpu_count()
+    return {"impl": "reference", "metric": "pillar frames/s", "value": v, "unit": "frames/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": secs / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[a.workload], "frames_per_step": batch},
+            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": "one full frame per step through the FP64 NumPy oracle (BLAS threads as "
+                                       "installed, up to %d cores)" % cores},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = _args()
+    if a.cpu_worker:
+        name, n = a.cpu_worker.split(":")
+        print(_oracle_seconds(name, int(n)))
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps(_run_reference(a)))
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    res = _run_ours(a, rank, world, dist)
+    if rank == 0:
+        if not a.no_cpu_baseline:
+            res["cpu_baseline"] = _cpu_baseline(a.workload, 1)
+        print(json.dumps(res))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,9 @@ typedef struct {
   double util_exempt;           /* units below this utilisation are never delayed             */
   int32_t early_exit;           /* drop frames whose slack is negative                        */
   int32_t num_streams;          /* stream priority levels per chain; 0 = device range         */
+  int32_t max_admitted;         /* admitted-but-unreleased frames per precision (each holds a  */
+                                /* result slot in HBM); 0 = as many as the budget allows, the  */
+                                /* library caps it at 128                                      */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
@@ -207,8 +210,10 @@ void pp_config_defaults(pp_config* cfg);
 typedef struct pp_ctx pp_ctx;
 
 /* Creates a context on the current CUDA device: uploads weights, allocates the units (each
- * holding buffers for max_batch frames), captures their graphs, starts the dispatcher.
- * PP_ENOMEM if one unit per enabled precision does not fit the budget. */
+ * holding buffers for max_batch frames), captures their graphs, carves one result slot per
+ * admissible frame out of what is left of the budget, and starts the dispatcher.  A unit is
+ * reusable as soon as it completes: it copies its frames' block outputs into their result
+ * slots.  PP_ENOMEM if one unit per enabled precision and one result slot do not fit. */
 int pp_create(const pp_config* cfg, pp_ctx** out);
 
 /* Declares a chain.  period/deadline in milliseconds (informational/default deadline);
@@ -242,7 +247,9 @@ typedef struct {
 
 /* Drains up to `max` completed frames into out[]; waits up to timeout_us for the first one
  * (0 = do not wait).  *n_out = number written (0 on timeout, return PP_OK).  Output buffers
- * stay valid until pp_result_release(frame_id). */
+ * (the frame's result slot) stay valid until pp_result_release(frame_id), which returns the
+ * slot to the budget.  A frame dropped by early exit carries no outputs (out_dev NULL) and
+ * gives its slot back at once; releasing it only forgets the record. */
 int pp_poll(pp_ctx* ctx, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us);
 int pp_result_release(pp_ctx* ctx, uint64_t frame_id);
 

@@ -37,6 +37,89 @@ class Geometry(ctypes.Structure):
                    g.nx, g.ny, g.max_pillars, getattr(g, "max_pts", 32))
 
 
+MAX_BLOCKS = 4
+MAX_CHAINS = 64
+PP_POLICY_FIFO, PP_POLICY_URGENCY = 0, 1
+PP_FRAME_DONE, PP_FRAME_DROPPED, PP_FRAME_ERROR = 0, 1, 2
+PP_DECIDE_NONE, PP_DECIDE_RELEASE, PP_DECIDE_WAIT, PP_DECIDE_DELAY = 0, 1, 2, 3
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("geom", Geometry),
+        ("n_blocks", ctypes.c_int32), ("convs", ctypes.c_int32 * MAX_BLOCKS),
+        ("chans", ctypes.c_int32 * MAX_BLOCKS), ("strides", ctypes.c_int32 * MAX_BLOCKS),
+        ("pfn_w", ctypes.c_void_p), ("pfn_bn", ctypes.c_void_p),
+        ("conv_w", ctypes.c_void_p), ("conv_bn", ctypes.c_void_p),
+        ("max_batch", ctypes.c_int32), ("cap_points", ctypes.c_int32),
+        ("precisions", ctypes.c_int32), ("units", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+        ("policy", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+        ("delta_eval_us", ctypes.c_double), ("max_closed", ctypes.c_int32),
+        ("delay_quantum_us", ctypes.c_double), ("th_urgent", ctypes.c_double),
+        ("th_calib_frames", ctypes.c_int32), ("util_exempt", ctypes.c_double),
+        ("early_exit", ctypes.c_int32), ("num_streams", ctypes.c_int32),
+        ("max_admitted", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("frame_id", ctypes.c_uint64), ("chain_id", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("t_arr_us", ctypes.c_double), ("t_release_us", ctypes.c_double),
+        ("t_done_us", ctypes.c_double), ("deadline_us", ctypes.c_double),
+        ("missed", ctypes.c_int32), ("num_pillars", ctypes.c_int32),
+        ("batch", ctypes.c_int32), ("level", ctypes.c_int32),
+        ("out_dev", ctypes.c_void_p), ("out_c", ctypes.c_int32), ("out_h", ctypes.c_int32),
+        ("out_w", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+        ("block_dev", ctypes.c_void_p * MAX_BLOCKS), ("block_c", ctypes.c_int32 * MAX_BLOCKS),
+        ("block_h", ctypes.c_int32 * MAX_BLOCKS), ("block_w", ctypes.c_int32 * MAX_BLOCKS),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64), ("done", ctypes.c_uint64), ("dropped", ctypes.c_uint64),
+        ("missed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+        ("overall_miss_ratio", ctypes.c_double), ("lat_p50_us", ctypes.c_double),
+        ("lat_p99_us", ctypes.c_double), ("lat_mean_us", ctypes.c_double),
+        ("frames_per_s", ctypes.c_double), ("units_launched", ctypes.c_uint64),
+        ("mean_batch", ctypes.c_double), ("delayed_releases", ctypes.c_uint64),
+        ("delayed_us", ctypes.c_double), ("collisions", ctypes.c_uint64),
+        ("sched_us_per_decision", ctypes.c_double), ("th_urgent", ctypes.c_double),
+        ("chain_frames", ctypes.c_uint64 * MAX_CHAINS), ("chain_missed", ctypes.c_uint64 * MAX_CHAINS),
+        ("chain_p99_us", ctypes.c_double * MAX_CHAINS),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("chain_")}
+        d["chain_frames"] = list(self.chain_frames)
+        d["chain_missed"] = list(self.chain_missed)
+        d["chain_p99_us"] = list(self.chain_p99_us)
+        return d
+
+
+class PolicyFrame(ctypes.Structure):
+    _fields_ = [("frame_id", ctypes.c_uint64), ("chain_id", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("t_arr_us", ctypes.c_double), ("deadline_us", ctypes.c_double),
+                ("est_gpu_us", ctypes.c_double), ("est_cpu_us", ctypes.c_double), ("util", ctypes.c_double)]
+
+
+class PolicyActive(ctypes.Structure):
+    _fields_ = [("chain_id", ctypes.c_int32), ("ul", ctypes.c_double)]
+
+
+class PolicyConfig(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_closed", ctypes.c_int32),
+                ("num_pri", ctypes.c_int32), ("early_exit", ctypes.c_int32),
+                ("th_urgent", ctypes.c_double), ("util_exempt", ctypes.c_double)]
+
+
+class PolicyDecision(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("n_frames", ctypes.c_int32),
+                ("n_drops", ctypes.c_int32), ("frames", ctypes.c_uint64 * 8)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 _P = ctypes.c_void_p
@@ -59,6 +142,27 @@ _SIGS = {
     "pp_conv_pack_weights": (ctypes.c_int, [_P, _I, _I, _I, _P, _P]),
     "pp_bn_fold": (ctypes.c_int, [_P, _I, ctypes.c_float, _P]),
     "pp_device_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), _I]),
+    "pp_config_defaults": (None, [ctypes.POINTER(Config)]),
+    "pp_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "pp_register_chain": (ctypes.c_int, [_P, _I, ctypes.c_double, ctypes.c_double, _I]),
+    "pp_submit_frame": (ctypes.c_int, [_P, _I, _P, ctypes.c_int64, _I, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "pp_poll": (ctypes.c_int, [_P, ctypes.POINTER(Result), _I, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]),
+    "pp_result_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "pp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "pp_destroy": (ctypes.c_int, [_P]),
+    "pp_now_us": (ctypes.c_double, []),
+    "pp_pipeline_create": (ctypes.c_int, [ctypes.POINTER(Config), _I, ctypes.POINTER(ctypes.c_void_p)]),
+    "pp_pipeline_run": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int32),
+                                       _I, _P]),
+    "pp_pipeline_output": (ctypes.c_int, [_P, _I, _I, ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "pp_pipeline_bytes": (_SZ, [_P]),
+    "pp_pipeline_destroy": (ctypes.c_int, [_P]),
+    "pp_policy_decide": (ctypes.c_int, [ctypes.POINTER(PolicyConfig), ctypes.c_double, ctypes.POINTER(PolicyFrame),
+                                        _I, ctypes.POINTER(PolicyActive), _I, _I, ctypes.POINTER(PolicyDecision),
+                                        ctypes.POINTER(ctypes.c_uint64), _I]),
 }
 
 
@@ -211,3 +315,181 @@ def device_error(clear: bool = True) -> int:
     v = ctypes.c_uint32(0)
     _check(lib().pp_device_error(ctypes.byref(v), 1 if clear else 0))
     return int(v.value)
+
+
+# ------------------------------------------------------------------ runtime, pipeline, policy
+
+def make_config(geom, backbone, weights, **knobs):
+    """Builds a pp_config (defaults from pp_config_defaults) for ``geom`` / ``backbone``
+    (objects with the pp_synth Geometry/Backbone fields) and ``weights`` =
+    (pfn_w [64,9], pfn_bn [4,64], conv_w list, conv_bn list) as float32 arrays.  Returns the
+    config and the list of arrays it points into (keep it alive while the config is used)."""
+    import numpy as np
+    cfg = Config()
+    lib().pp_config_defaults(ctypes.byref(cfg))
+    cfg.geom = Geometry.of(geom)
+    cfg.n_blocks = len(backbone.convs)
+    for i, (n, c, st) in enumerate(zip(backbone.convs, backbone.chans, backbone.strides)):
+        cfg.convs[i], cfg.chans[i], cfg.strides[i] = n, c, st
+    pfn_w, pfn_bn, conv_w, conv_bn = weights
+    keep = [np.ascontiguousarray(pfn_w, dtype=np.float32), np.ascontiguousarray(pfn_bn, dtype=np.float32)]
+    cw = [np.ascontiguousarray(w, dtype=np.float32) for w in conv_w]
+    cb = [np.ascontiguousarray(b, dtype=np.float32) for b in conv_bn]
+    arr_w = (ctypes.c_void_p * len(cw))(*[a.ctypes.data for a in cw])
+    arr_b = (ctypes.c_void_p * len(cb))(*[a.ctypes.data for a in cb])
+    keep += cw + cb + [arr_w, arr_b]
+    cfg.pfn_w, cfg.pfn_bn = keep[0].ctypes.data, keep[1].ctypes.data
+    cfg.conv_w = ctypes.cast(arr_w, ctypes.c_void_p)
+    cfg.conv_bn = ctypes.cast(arr_b, ctypes.c_void_p)
+    for k, v in knobs.items():
+        if not hasattr(cfg, k):
+            raise PPError(PP_EINVAL, "unknown config field %s" % k)
+        setattr(cfg, k, v)
+    return cfg, keep
+
+
+class Context:
+    """A serving context (pp_create ... pp_destroy)."""
+
+    def __init__(self, cfg):
+        h = ctypes.c_void_p()
+        _check(lib().pp_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+
+    def register_chain(self, chain_id, period_ms, deadline_ms, precision):
+        _check(lib().pp_register_chain(self.h, chain_id, period_ms, deadline_ms, precision))
+
+    def submit(self, chain_id, points, t_arrival_us=None, abs_deadline_us=0.0, n_points=None):
+        """points: numpy float32 [N, 4] (host; copied) or a CUDA tensor [N, 4] (device; borrowed
+        until the frame is polled).  Returns (status, frame_id); status PP_EAGAIN when not
+        admitted."""
+        fid = ctypes.c_uint64(0)
+        t = now_us() if t_arrival_us is None else t_arrival_us
+        if hasattr(points, "is_cuda"):
+            n = int(points.shape[0]) if n_points is None else n_points
+            rc = lib().pp_submit_frame(self.h, chain_id, _ptr(points), n, 1, t, abs_deadline_us, ctypes.byref(fid))
+        else:
+            import numpy as np
+            a = np.ascontiguousarray(points, dtype=np.float32)
+            n = int(a.shape[0]) if n_points is None else n_points
+            rc = lib().pp_submit_frame(self.h, chain_id, a.ctypes.data if n else None, n, 0, t, abs_deadline_us,
+                                       ctypes.byref(fid))
+        if rc not in (PP_OK, PP_EAGAIN):
+            _check(rc)
+        return rc, int(fid.value)
+
+    def poll(self, max_results=64, timeout_us=0):
+        buf = (Result * max_results)()
+        n = ctypes.c_int32(0)
+        _check(lib().pp_poll(self.h, buf, max_results, ctypes.byref(n), int(timeout_us)))
+        return [buf[i] for i in range(n.value)]
+
+    def release(self, frame_id):
+        _check(lib().pp_result_release(self.h, ctypes.c_uint64(frame_id)))
+
+    def stats(self):
+        s = Stats()
+        _check(lib().pp_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def destroy(self):
+        if self.h:
+            rc = lib().pp_destroy(self.h)
+            self.h = None
+            _check(rc)
+
+
+def now_us() -> float:
+    return float(lib().pp_now_us())
+
+
+def result_tensor(r, block=None):
+    """Wraps a result's output (the last layer, or block ``block``) as a torch tensor view of
+    the padded NHWC device buffer [h+2, w+2, c] (valid until the frame is released)."""
+    import torch
+    if not r.out_dev:
+        raise PPError(PP_ESTATE, "frame %d has no output (status %d)" % (r.frame_id, r.status))
+    if block is None:
+        ptr, c, h, w = r.out_dev, r.out_c, r.out_h, r.out_w
+    else:
+        ptr, c, h, w = r.block_dev[block], r.block_c[block], r.block_h[block], r.block_w[block]
+    dt = torch.float32 if r.out_dtype == PP_F32 else torch.bfloat16
+    return _device_view(ptr, (h + 2, w + 2, c), dt)
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ exporter for a device buffer the library owns."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _device_view(ptr, shape, dtype):
+    """Copy of the device buffer of ``shape``/``dtype`` at ``ptr`` as a new CUDA tensor."""
+    import torch
+    if dtype == torch.bfloat16:
+        t = torch.as_tensor(_CudaArray(ptr, shape, "<i2"), device="cuda").view(torch.bfloat16)
+    elif dtype == torch.float32:
+        t = torch.as_tensor(_CudaArray(ptr, shape, "<f4"), device="cuda")
+    elif dtype == torch.int32:
+        t = torch.as_tensor(_CudaArray(ptr, shape, "<i4"), device="cuda")
+    else:
+        raise PPError(PP_EINVAL, "unsupported dtype %s" % dtype)
+    return t.clone()
+
+
+class Pipeline:
+    """One release unit without the runtime (pp_pipeline_*)."""
+
+    def __init__(self, cfg, precision):
+        h = ctypes.c_void_p()
+        _check(lib().pp_pipeline_create(ctypes.byref(cfg), precision, ctypes.byref(h)))
+        self.h = h
+        self.precision = precision
+
+    def run(self, frames, counts=None, use_graph=True, stream=None):
+        """frames: list of CUDA tensors [N_i, 4] (or host numpy arrays)."""
+        n = len(frames)
+        ptrs = (ctypes.c_void_p * n)(*[(_ptr(f) if hasattr(f, "data_ptr") else f.ctypes.data) for f in frames])
+        cnt = (ctypes.c_int32 * n)(*[int(f.shape[0]) for f in frames] if counts is None else counts)
+        _check(lib().pp_pipeline_run(self.h, n, ptrs, cnt, 1 if use_graph else 0, _stream(stream)))
+
+    def output(self, i, block):
+        d = ctypes.c_void_p()
+        c, h, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().pp_pipeline_output(self.h, i, block, ctypes.byref(d), ctypes.byref(c), ctypes.byref(h),
+                                        ctypes.byref(w)))
+        return d.value, c.value, h.value, w.value
+
+    def output_tensor(self, i, block):
+        import torch
+        ptr, c, h, w = self.output(i, block)
+        dt = torch.float32 if self.precision == PP_F32 else torch.bfloat16
+        return _device_view(ptr, (h + 2, w + 2, c), dt)
+
+    def num_pillars(self, i):
+        import torch
+        ptr, _, _, _ = self.output(i, -1)
+        return int(_device_view(ptr, (1,), torch.int32)[0])
+
+    def bytes(self):
+        return int(lib().pp_pipeline_bytes(self.h))
+
+    def destroy(self):
+        if self.h:
+            lib().pp_pipeline_destroy(self.h)
+            self.h = None
+
+
+def policy_decide(cfg, t_us, ready, active, closed_pending):
+    """Calls pp_policy_decide.  ready: list of dicts with PolicyFrame fields; active: list of
+    (chain_id, ul).  Returns (kind, frame ids, level, drop ids)."""
+    pc = PolicyConfig(**cfg)
+    rf = (PolicyFrame * max(1, len(ready)))(*[PolicyFrame(**r) for r in ready])
+    ac = (PolicyActive * max(1, len(active)))(*[PolicyActive(c, u) for c, u in active])
+    d = PolicyDecision()
+    drops = (ctypes.c_uint64 * max(1, len(ready)))()
+    _check(lib().pp_policy_decide(ctypes.byref(pc), float(t_us), rf, len(ready), ac, len(active),
+                                  int(closed_pending), ctypes.byref(d), drops, len(ready)))
+    return d.kind, [int(d.frames[i]) for i in range(d.n_frames)], d.level, [int(drops[i]) for i in range(d.n_drops)]

@@ -1,0 +1,313 @@
+// Release unit: device buffers for up to B frames, the whole pillar front end as one launch
+// sequence (voxelise -> PointNet -> scatter -> conv3x3 layers), and one CUDA graph per batch
+// size 1..B so that a unit launch costs one cudaGraphLaunch.  Per-frame point counts live in
+// device memory, so a graph replays any mix of uneven frames: grids are sized for the unit's
+// capacity and blocks past a frame's count exit at once.
+#include "pipeline.h"
+
+#include <cstring>
+#include <new>
+
+namespace pp {
+
+namespace {
+int layers_of(const pp_config* cfg, std::vector<LayerSpec>* out, std::vector<int>* block_end,
+              int H0, int W0) {
+  if (cfg->n_blocks <= 0 || cfg->n_blocks > PP_MAX_BLOCKS)
+    return fail(PP_EINVAL, "config: n_blocks must be 1..%d", PP_MAX_BLOCKS);
+  int cin = 64, H = H0, W = W0;
+  for (int b = 0; b < cfg->n_blocks; ++b) {
+    if (cfg->convs[b] <= 0 || cfg->convs[b] > 16 || cfg->chans[b] <= 0 || cfg->chans[b] % 64 ||
+        cfg->chans[b] > 1024 || (cfg->strides[b] != 1 && cfg->strides[b] != 2))
+      return fail(PP_EINVAL, "config: block %d: convs 1..16, chans multiple of 64, stride 1/2", b);
+    for (int i = 0; i < cfg->convs[b]; ++i) {
+      LayerSpec l;
+      l.cin = cin;
+      l.cout = cfg->chans[b];
+      l.stride = i == 0 ? cfg->strides[b] : 1;
+      if (l.stride == 2 && ((H & 1) || (W & 1)))
+        return fail(PP_EINVAL, "config: stride 2 on an odd map (%d x %d)", H, W);
+      l.H = H;
+      l.W = W;
+      l.Ho = (H - 1) / l.stride + 1;
+      l.Wo = (W - 1) / l.stride + 1;
+      out->push_back(l);
+      cin = l.cout;
+      H = l.Ho;
+      W = l.Wo;
+    }
+    block_end->push_back((int)out->size() - 1);
+  }
+  return PP_OK;
+}
+}  // namespace
+
+int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
+  int st = check_geometry(&cfg->geom, &g);
+  if (st) return st;
+  precision = prec;
+  layers.clear();
+  block_end.clear();
+  st = layers_of(cfg, &layers, &block_end, g.ny, g.nx);
+  if (st) return st;
+  if (!cfg->pfn_w || !cfg->pfn_bn || !cfg->conv_w || !cfg->conv_bn)
+    return fail(PP_EINVAL, "config: NULL weights");
+  auto dev_alloc = [&](void** p, size_t n) -> int {
+    if (cudaMalloc(p, n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PP_ENOMEM, "cudaMalloc(%zu) for weights failed", n);
+    }
+    bytes += n;
+    return PP_OK;
+  };
+  float ss[2 * 1024];
+  if ((st = dev_alloc((void**)&pfn_w, 64 * 9 * sizeof(float)))) return st;
+  if ((st = dev_alloc((void**)&pfn_ss, 2 * 64 * sizeof(float)))) return st;
+  if ((st = pp_bn_fold(cfg->pfn_bn, 64, 1e-3f, ss))) return st;
+  if ((st = cuda_status(cudaMemcpy(pfn_w, cfg->pfn_w, 64 * 9 * sizeof(float), cudaMemcpyHostToDevice), "upload pfn_w"))) return st;
+  if ((st = cuda_status(cudaMemcpy(pfn_ss, ss, 2 * 64 * sizeof(float), cudaMemcpyHostToDevice), "upload pfn_ss"))) return st;
+  for (size_t l = 0; l < layers.size(); ++l) {
+    const LayerSpec& L = layers[l];
+    if (!cfg->conv_w[l] || !cfg->conv_bn[l]) return fail(PP_EINVAL, "config: NULL layer %zu weights", l);
+    const size_t wbytes = (size_t)L.cout * L.cin * 9 * sizeof(float);
+    float* tmp = nullptr;
+    if ((st = cuda_status(cudaMalloc(&tmp, wbytes), "weights staging"))) return st;
+    void* packed = nullptr;
+    float* ssd = nullptr;
+    st = dev_alloc(&packed, pp_conv_packed_bytes(L.cin, L.cout, prec));
+    if (!st) st = dev_alloc((void**)&ssd, 2 * L.cout * sizeof(float));
+    if (!st) st = cuda_status(cudaMemcpy(tmp, cfg->conv_w[l], wbytes, cudaMemcpyHostToDevice), "upload conv_w");
+    if (!st) st = conv_pack_launch(tmp, L.cin, L.cout, prec, packed, s);
+    if (!st) st = cuda_status(cudaStreamSynchronize(s), "pack weights");
+    if (!st) st = pp_bn_fold(cfg->conv_bn[l], L.cout, 1e-3f, ss);
+    if (!st) st = cuda_status(cudaMemcpy(ssd, ss, 2 * L.cout * sizeof(float), cudaMemcpyHostToDevice), "upload conv_ss");
+    cudaFree(tmp);
+    conv_w.push_back(packed);
+    conv_ss.push_back(ssd);
+    if (st) return st;
+  }
+  return PP_OK;
+}
+
+void Model::release() {
+  cudaFree(pfn_w);
+  cudaFree(pfn_ss);
+  for (void* p : conv_w) cudaFree(p);
+  for (float* p : conv_ss) cudaFree(p);
+  pfn_w = pfn_ss = nullptr;
+  conv_w.clear();
+  conv_ss.clear();
+}
+
+int Pipeline::alloc(void** p, size_t n) {
+  n = align_up(n < 256 ? 256 : n, 256);
+  if (cudaMalloc(p, n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PP_ENOMEM, "cudaMalloc(%zu) failed", n);
+  }
+  allocs_.push_back(*p);
+  bytes_ += n;
+  return PP_OK;
+}
+
+int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, cudaStream_t s) {
+  m_ = m;
+  B_ = max_batch;
+  cap_ = cap_points;
+  const Geom& g = m->g;
+  const size_t elt = m->precision == PP_F32 ? 4 : 2;
+  int st = PP_OK;
+#define PP_ALLOC(ptr, n) \
+  if ((st = alloc(reinterpret_cast<void**>(&ptr), (n)))) return st
+  PP_ALLOC(points_, (size_t)B_ * cap_ * sizeof(float4));
+  PP_ALLOC(n_dev_, (size_t)B_ * sizeof(int));
+  PP_ALLOC(cell_, (size_t)B_ * cap_ * sizeof(int));
+  PP_ALLOC(cnt_, (size_t)B_ * g.G * sizeof(unsigned));
+  PP_ALLOC(poc_, (size_t)B_ * g.G * sizeof(int));
+  PP_ALLOC(coord_, (size_t)B_ * g.P * sizeof(int));
+  PP_ALLOC(npts_, (size_t)B_ * g.P * sizeof(int));
+  PP_ALLOC(num_, (size_t)B_ * sizeof(int));
+  PP_ALLOC(pts_, (size_t)B_ * g.P * 32 * sizeof(float4));
+  PP_ALLOC(vox_ws_, vox_workspace_bytes(g, B_, cap_));
+  PP_ALLOC(feat_, (size_t)B_ * g.P * 64 * sizeof(float));
+  PP_ALLOC(canvas_, (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt);
+  for (const LayerSpec& L : m->layers) {
+    void* a = nullptr;
+    const size_t n = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
+    PP_ALLOC(a, n);
+    act_.push_back(a);
+    // borders stay zero forever: convs write interiors only
+    if ((st = cuda_status(cudaMemsetAsync(a, 0, n, s), "clear activations"))) return st;
+  }
+#undef PP_ALLOC
+  if ((st = cuda_status(cudaMemsetAsync(vox_ws_, 0, 256, s), "clear vox error word"))) return st;
+  if ((st = cuda_status(cudaMemsetAsync(n_dev_, 0, (size_t)B_ * sizeof(int), s), "clear counts"))) return st;
+  if ((st = cuda_status(cudaMallocHost(&n_host_, (size_t)B_ * sizeof(int)), "pinned counts"))) return st;
+  memset(n_host_, 0, (size_t)B_ * sizeof(int));
+  if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)B_ * sizeof(int)), "pinned pillar counts"))) return st;
+  memset(num_host_, 0, (size_t)B_ * sizeof(int));
+  vw_ = vox_carve(vox_ws_, g, B_, cap_);
+  // one eager pass sets kernel attributes and validates every launch before capture
+  if ((st = enqueue(B_, s))) return st;
+  if ((st = cuda_status(cudaStreamSynchronize(s), "pipeline warm-up"))) return st;
+  graphs_.assign(B_ + 1, nullptr);
+  if (graphs) {
+    cudaStream_t cs;
+    if ((st = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream"))) return st;
+    for (int b = 1; b <= B_ && st == PP_OK; ++b) {
+      cudaGraph_t graph = nullptr;
+      st = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+      if (st) break;
+      const int est = enqueue(b, cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      if (est) { st = est; if (graph) cudaGraphDestroy(graph); break; }
+      if ((st = cuda_status(ee, "end capture"))) break;
+      st = cuda_status(cudaGraphInstantiate(&graphs_[b], graph, 0), "instantiate graph");
+      cudaGraphDestroy(graph);
+    }
+    cudaStreamDestroy(cs);
+    if (st) return st;
+  }
+  return PP_OK;
+}
+
+void Pipeline::release() {
+  for (cudaGraphExec_t g : graphs_)
+    if (g) cudaGraphExecDestroy(g);
+  graphs_.clear();
+  for (void* p : allocs_) cudaFree(p);
+  allocs_.clear();
+  act_.clear();
+  if (n_host_) cudaFreeHost(n_host_);
+  if (num_host_) cudaFreeHost(num_host_);
+  n_host_ = num_host_ = nullptr;
+  bytes_ = 0;
+}
+
+int Pipeline::enqueue(int n, cudaStream_t s) {
+  const Model& m = *m_;
+  const Geom& g = m.g;
+  int st = vox_launch(g, n, cap_, points_, n_dev_, cell_, cnt_, poc_, coord_, npts_, num_, pts_, vw_, s);
+  if (!st) st = pfn_launch(g, n, pts_, npts_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
+  if (!st) st = scatter_launch(g, n, feat_, poc_, canvas_, m.precision, s);
+  const void* x = canvas_;
+  for (size_t l = 0; l < m.layers.size() && !st; ++l) {
+    const LayerSpec& L = m.layers[l];
+    ConvShape c{n, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
+    if (m.precision == PP_F32)
+      st = conv_f32_launch(c, (const float*)x, (const float*)m.conv_w[l], m.conv_ss[l],
+                           (float*)act_[l], -1, s);
+    else
+      st = conv_bf16_launch(c, (const __nv_bfloat16*)x, (const __nv_bfloat16*)m.conv_w[l],
+                            m.conv_ss[l], (__nv_bfloat16*)act_[l], -1, s);
+    x = act_[l];
+  }
+  return st;
+}
+
+int Pipeline::run(int n, const float* const* frames, const int* counts, bool use_graph,
+                  cudaStream_t s) {
+  if (n <= 0 || n > B_) return fail(PP_EINVAL, "pipeline run: batch %d outside 1..%d", n, B_);
+  for (int i = 0; i < n; ++i) {
+    if (counts[i] < 0 || counts[i] > cap_)
+      return fail(PP_EINVAL, "pipeline run: frame %d has %d points (cap %d)", i, counts[i], cap_);
+    if (counts[i] > 0 && !frames[i]) return fail(PP_EINVAL, "pipeline run: NULL frame %d", i);
+  }
+  for (int i = 0; i < n; ++i) {
+    n_host_[i] = counts[i];
+    if (counts[i] > 0) {
+      int st = cuda_status(cudaMemcpyAsync(points_ + (size_t)i * cap_, frames[i],
+                                           (size_t)counts[i] * sizeof(float4), cudaMemcpyDefault, s),
+                           "stage points");
+      if (st) return st;
+    }
+  }
+  int st = cuda_status(cudaMemcpyAsync(n_dev_, n_host_, (size_t)n * sizeof(int),
+                                       cudaMemcpyHostToDevice, s), "stage counts");
+  if (st) return st;
+  if (use_graph && graphs_.size() > (size_t)n && graphs_[n])
+    st = cuda_status(cudaGraphLaunch(graphs_[n], s), "graph launch");
+  else
+    st = enqueue(n, s);
+  if (st) return st;
+  return cuda_status(cudaMemcpyAsync(num_host_, num_, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s),
+                     "read back pillar counts");
+}
+
+const void* Pipeline::layer_out(int layer, int i) const {
+  const LayerSpec& L = m_->layers[layer];
+  const size_t elt = m_->precision == PP_F32 ? 4 : 2;
+  return static_cast<const char*>(act_[layer]) + (size_t)i * (L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
+}
+
+}  // namespace pp
+
+// ------------------------------------------------------------------ C ABI
+
+struct pp_pipeline {
+  pp::Model model;
+  pp::Pipeline pipe;
+};
+
+using namespace pp;
+
+extern "C" {
+
+int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** out) {
+  if (!cfg || !out) return fail(PP_EINVAL, "pipeline_create: NULL argument");
+  if (precision != PP_F32 && precision != PP_BF16) return fail(PP_EINVAL, "pipeline_create: bad precision");
+  if (cfg->max_batch < 1 || cfg->max_batch > 8 || cfg->cap_points < 1 || cfg->cap_points > (1 << 24))
+    return fail(PP_EINVAL, "pipeline_create: max_batch 1..8, cap_points 1..2^24");
+  pp_pipeline* p = new (std::nothrow) pp_pipeline();
+  if (!p) return fail(PP_ENOMEM, "pipeline_create: host allocation");
+  cudaStream_t s;
+  int st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+  if (!st) st = p->model.upload(cfg, precision, s);
+  if (!st) st = p->pipe.init(&p->model, cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, s);
+  if (!st) st = cuda_status(cudaStreamSynchronize(s), "pipeline init");
+  cudaStreamDestroy(s);
+  if (st) {
+    p->pipe.release();
+    p->model.release();
+    delete p;
+    return st;
+  }
+  *out = p;
+  return PP_OK;
+}
+
+int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames, const int32_t* counts,
+                    int32_t use_graph, void* stream) {
+  if (!p || !frames || !counts) return fail(PP_EINVAL, "pipeline_run: NULL argument");
+  return p->pipe.run(n, frames, counts, use_graph != 0, static_cast<cudaStream_t>(stream));
+}
+
+int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** dev, int32_t* c,
+                       int32_t* h, int32_t* w) {
+  if (!p || !dev || i < 0 || i >= p->pipe.max_batch()) return fail(PP_EINVAL, "pipeline_output: bad argument");
+  if (block == -1) {
+    *dev = p->pipe.num_pillars_dev() + i;
+    return PP_OK;
+  }
+  if (block < 0 || block >= (int)p->model.block_end.size()) return fail(PP_EINVAL, "pipeline_output: bad block");
+  const int l = p->model.block_end[block];
+  const LayerSpec& L = p->model.layers[l];
+  *dev = p->pipe.layer_out(l, i);
+  if (c) *c = L.cout;
+  if (h) *h = L.Ho;
+  if (w) *w = L.Wo;
+  return PP_OK;
+}
+
+size_t pp_pipeline_bytes(pp_pipeline* p) { return p ? p->pipe.bytes() + p->model.bytes : 0; }
+
+int pp_pipeline_destroy(pp_pipeline* p) {
+  if (!p) return PP_OK;
+  cudaDeviceSynchronize();
+  p->pipe.release();
+  p->model.release();
+  delete p;
+  return PP_OK;
+}
+
+}  // extern "C"

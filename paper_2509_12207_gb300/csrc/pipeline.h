@@ -46,6 +46,8 @@ class Pipeline {
   float4* points_dev() const { return points_; }
   int* counts_dev() const { return n_dev_; }
   int* counts_host() const { return n_host_; }
+  // pinned copy of num_pillars, written at the end of every run (valid once it completes)
+  const int* num_pillars_host() const { return num_host_; }
 
  private:
   const Model* m_ = nullptr;
@@ -53,7 +55,8 @@ class Pipeline {
   size_t bytes_ = 0;
   float4* points_ = nullptr;
   int* n_dev_ = nullptr;
-  int* n_host_ = nullptr;  // pinned [B]
+  int* n_host_ = nullptr;    // pinned [B]
+  int* num_host_ = nullptr;  // pinned [B]
   int *cell_ = nullptr, *poc_ = nullptr, *coord_ = nullptr, *npts_ = nullptr, *num_ = nullptr;
   unsigned* cnt_ = nullptr;
   float4* pts_ = nullptr;

@@ -1,0 +1,811 @@
+// Serving runtime: chains, frame admission under an HBM budget, and a dispatcher thread that
+// releases frames in units (one graph launch each) by the rule in policy.cpp.
+//
+// Mapping of the paper's mechanisms (Section 4):
+//  * urgency evaluation (Eq. 2) at frame arrival and at every release decision; remaining GPU
+//    time comes from a lookup table of measured unit durations keyed by (precision, frames in
+//    the unit), each entry the mean of its last 8 measurements (Section 4.2, Table 1); the
+//    table is seeded by timing every unit size once at creation (the offline profiling stage);
+//  * the active kernel buffer (Section 4.4.2) is the list of in-flight units with the chain and
+//    urgency they were released with;
+//  * task-level stream binding with reservation (Section 4.4.3): every chain owns one stream per
+//    priority level; a unit goes to its head frame's chain pool at the level the rule chose;
+//  * TH_urgent (Section 4.4.3) is the 95th percentile of the highest urgency seen at each
+//    decision during the first frames, unless given;
+//  * delayed launching (Section 4.4.4): the dispatcher holds the release and re-checks after the
+//    delay quantum or at the next completion;
+//  * batched launching with overlap (Section 4.4.5): launches accumulate estimated GPU time into
+//    the open batch; when it reaches Delta_eval the batch closes (an event), and releases pause
+//    while max_closed closed batches are unfinished;
+//  * early chain exit (Section 4.3): frames with negative slack are dropped before release.
+// Completion times come from CUDA events (GPU timestamps mapped to the host clock), so latency
+// does not depend on how quickly the dispatcher notices a completion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "pipeline.h"
+
+namespace pp {
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+constexpr int kLutWindow = 8;
+constexpr int kMaxAdmitted = 128;  // admitted-but-unreleased frames per precision, at most
+
+struct Lut {
+  double v[kLutWindow] = {0};
+  int n = 0, next = 0;
+  void add(double x) {
+    v[next] = x;
+    next = (next + 1) % kLutWindow;
+    if (n < kLutWindow) ++n;
+  }
+  double mean(double dflt) const {
+    if (!n) return dflt;
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += v[i];
+    return s / n;
+  }
+};
+
+struct Frame {
+  uint64_t id = 0;
+  int chain = 0, precision = 0;
+  double t_arr = 0, deadline = 0, t_release = 0;
+  int64_t n = 0;
+  const float* src = nullptr;  // device pointer (borrowed) or pinned staging slot
+  int staging = -1;
+  int rslot = -1;              // result pool slot (reserved at admission)
+  int unit = -1, slot = -1;
+  bool dropped = false, done = false, polled = false;
+  double delay_start = -1;
+};
+
+struct Unit {
+  Pipeline pipe;
+  int precision = 0;
+  bool busy = false, running = false;
+  int nf = 0, level = 0, head_chain = 0;
+  uint64_t frames[8] = {0};
+  cudaEvent_t start = nullptr, done = nullptr;
+  double ul = 0, est = 0, t_launch = 0;
+};
+
+struct Chain {
+  bool used = false;
+  double period_ms = 0, deadline_ms = 0;
+  int precision = 0;
+  std::vector<cudaStream_t> streams;  // one per priority level, level 0 highest
+  uint64_t frames = 0, missed = 0;
+  std::vector<double> lat;
+};
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+struct pp_ctx {
+  pp_config cfg{};
+  int device = 0;
+  int num_pri = 1, prio_greatest = 0;
+  Model models[2];
+  bool have[2] = {false, false};
+  std::vector<Unit*> units;
+  int capacity[2] = {0, 0}, admitted[2] = {0, 0};
+  Chain chains[PP_MAX_CHAINS];
+  std::map<uint64_t, Frame*> frames;
+  std::vector<Frame*> ready;
+  std::deque<pp_result> completed;
+  std::vector<float*> staging;
+  std::vector<int> staging_free;
+  // per-precision result pools: every admitted frame owns one slot until it is released, so
+  // units are free again as soon as they complete
+  struct Pool {
+    void* base = nullptr;
+    size_t slot_bytes = 0;
+    std::vector<size_t> block_off;
+    std::vector<int> free;
+  } pool[2];
+  Lut lut[2][9];
+  // batched synchronisation gate
+  double open_sum = 0;
+  std::vector<int> open_units;
+  std::deque<std::vector<int>> closed;
+  // urgency threshold
+  double th = -1;
+  std::vector<double> th_samples;
+  bool calibrating = false;
+  // timing reference: GPU event <-> host clock
+  cudaEvent_t ref_event = nullptr;
+  double ref_host = 0;
+  cudaStream_t aux = nullptr;
+  // stats
+  uint64_t submitted = 0, n_done = 0, n_dropped = 0, n_missed = 0, rejected = 0, launched = 0;
+  uint64_t batch_frames = 0, delayed = 0, collisions = 0, decisions = 0;
+  double delayed_us = 0, sched_us = 0, first_arr = -1, last_done = -1;
+  std::vector<double> lat_all;
+  uint64_t next_id = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread dispatcher;
+  std::atomic<bool> stop{false};
+  bool device_error = false;
+};
+
+namespace {
+
+double unit_est(pp_ctx* c, int prec, int nf) {
+  return c->lut[prec][nf].mean(c->lut[prec][1].mean(1000.0) * nf);
+}
+
+void CUDART_CB notify_cb(void* p) {
+  pp_ctx* c = static_cast<pp_ctx*>(p);
+  c->cv_work.notify_one();
+}
+
+double event_host_time(pp_ctx* c, cudaEvent_t e) {
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, c->ref_event, e) != cudaSuccess) {
+    cudaGetLastError();
+    return now_us();
+  }
+  return c->ref_host + (double)ms * 1000.0;
+}
+
+void push_result(pp_ctx* c, Frame* f, int status, double t_done) {
+  pp_result r;
+  memset(&r, 0, sizeof(r));
+  r.frame_id = f->id;
+  r.chain_id = f->chain;
+  r.status = status;
+  r.t_arr_us = f->t_arr;
+  r.t_release_us = f->t_release;
+  r.t_done_us = t_done;
+  r.deadline_us = f->deadline;
+  r.missed = status != PP_FRAME_DONE || t_done > f->deadline;
+  Chain& ch = c->chains[f->chain];
+  ch.frames++;
+  if (r.missed) {
+    ch.missed++;
+    c->n_missed++;
+  }
+  if (status == PP_FRAME_DONE) {
+    const double lat = t_done - f->t_arr;
+    ch.lat.push_back(lat);
+    c->lat_all.push_back(lat);
+    c->n_done++;
+    if (t_done > c->last_done) c->last_done = t_done;
+    Unit* u = c->units[f->unit];
+    const Model* m = u->pipe.model();
+    const pp_ctx::Pool& pl = c->pool[f->precision];
+    char* base = static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
+    r.batch = u->nf;
+    r.level = u->level;
+    r.out_dtype = m->precision;
+    for (size_t b = 0; b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
+      const LayerSpec& L = m->layers[m->block_end[b]];
+      r.block_dev[b] = base + pl.block_off[b];
+      r.block_c[b] = L.cout;
+      r.block_h[b] = L.Ho;
+      r.block_w[b] = L.Wo;
+      r.out_dev = r.block_dev[b];
+      r.out_c = L.cout;
+      r.out_h = L.Ho;
+      r.out_w = L.Wo;
+    }
+    r.num_pillars = u->pipe.num_pillars_host()[f->slot];
+  } else {
+    c->n_dropped += status == PP_FRAME_DROPPED;
+  }
+  f->done = true;
+  c->completed.push_back(r);
+  c->cv_done.notify_all();
+}
+
+void free_staging(pp_ctx* c, Frame* f) {
+  if (f->staging >= 0) {
+    c->staging_free.push_back(f->staging);
+    f->staging = -1;
+  }
+}
+
+void free_result(pp_ctx* c, Frame* f) {
+  if (f->rslot >= 0) {
+    c->pool[f->precision].free.push_back(f->rslot);
+    f->rslot = -1;
+  }
+}
+
+// Completed units: results, estimate table, batch gate.  The unit is free again at once.
+void reap(pp_ctx* c) {
+  for (size_t ui = 0; ui < c->units.size(); ++ui) {
+    Unit* u = c->units[ui];
+    if (!u->running) continue;
+    const cudaError_t q = cudaEventQuery(u->done);
+    if (q == cudaErrorNotReady) continue;
+    u->running = false;
+    u->busy = false;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      c->device_error = true;
+    }
+    const double t_done = q == cudaSuccess ? event_host_time(c, u->done) : now_us();
+    float ms = 0;
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess)
+      c->lut[u->precision][u->nf].add(ms * 1000.0);
+    else
+      cudaGetLastError();
+    for (int i = 0; i < u->nf; ++i) {
+      Frame* f = c->frames[u->frames[i]];
+      free_staging(c, f);
+      push_result(c, f, q == cudaSuccess ? PP_FRAME_DONE : PP_FRAME_ERROR, t_done);
+    }
+    // batch gate: closed batches finish in launch order
+    const int id = (int)ui;
+    for (auto& b : c->closed) b.erase(std::remove(b.begin(), b.end(), id), b.end());
+    while (!c->closed.empty() && c->closed.front().empty()) c->closed.pop_front();
+    c->open_units.erase(std::remove(c->open_units.begin(), c->open_units.end(), id), c->open_units.end());
+  }
+}
+
+int closed_pending(pp_ctx* c) {
+  int n = 0;
+  for (auto& b : c->closed) n += !b.empty();
+  return n;
+}
+
+int free_unit(pp_ctx* c, int prec) {
+  for (size_t i = 0; i < c->units.size(); ++i)
+    if (!c->units[i]->busy && c->units[i]->precision == prec) return (int)i;
+  return -1;
+}
+
+pp_policy_config policy_cfg(pp_ctx* c) {
+  pp_policy_config p;
+  p.policy = c->cfg.policy;
+  p.max_batch = c->cfg.max_batch;
+  p.max_closed = c->cfg.max_closed;
+  p.num_pri = c->num_pri;
+  p.early_exit = c->cfg.early_exit;
+  p.th_urgent = c->th;
+  p.util_exempt = c->cfg.util_exempt;
+  return p;
+}
+
+int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
+  Frame* head = c->frames[d.frames[0]];
+  const int prec = head->precision;
+  const int ui = free_unit(c, prec);
+  if (ui < 0) return 1;  // every unit of this precision is busy: wait for a completion/release
+  Unit* u = c->units[ui];
+  const float* srcs[8];
+  int counts[8];
+  u->nf = d.n_frames;
+  u->level = d.level;
+  u->head_chain = head->chain;
+  const double slack = head->deadline - unit_est(c, prec, 1) - t;
+  u->ul = slack > 0 ? 1.0 / slack : -INFINITY;
+  u->est = unit_est(c, prec, d.n_frames);
+  for (int i = 0; i < d.n_frames; ++i) {
+    Frame* f = c->frames[d.frames[i]];
+    u->frames[i] = f->id;
+    f->unit = ui;
+    f->slot = i;
+    f->t_release = t;
+    srcs[i] = f->src;
+    counts[i] = (int)f->n;
+    if (f->delay_start >= 0) {
+      c->delayed_us += t - f->delay_start;
+      f->delay_start = -1;
+    }
+    c->ready.erase(std::remove(c->ready.begin(), c->ready.end(), f), c->ready.end());
+  }
+  // collision: a launch while another chain's urgent unit is in flight (or this one is urgent)
+  if (c->th > 0) {
+    for (Unit* o : c->units)
+      if (o->running && o->head_chain != u->head_chain && (o->ul > c->th || u->ul > c->th)) {
+        c->collisions++;
+        break;
+      }
+  }
+  const int lvl = std::min(std::max(d.level, 0), c->num_pri - 1);
+  cudaStream_t s = c->chains[head->chain].streams[lvl];
+  u->busy = true;
+  u->running = true;
+  u->t_launch = t;
+  int st = cuda_status(cudaEventRecord(u->start, s), "record start");
+  if (!st) st = u->pipe.run(d.n_frames, srcs, counts, c->cfg.use_graphs != 0, s);
+  const pp_ctx::Pool& pl = c->pool[prec];
+  const Model* m = u->pipe.model();
+  for (int i = 0; i < d.n_frames && !st; ++i) {
+    char* dst = static_cast<char*>(pl.base) + (size_t)c->frames[d.frames[i]]->rslot * pl.slot_bytes;
+    for (size_t b = 0; b < m->block_end.size() && !st; ++b) {
+      const int l = m->block_end[b];
+      const LayerSpec& L = m->layers[l];
+      const size_t n = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (prec == PP_F32 ? 4 : 2);
+      st = cuda_status(cudaMemcpyAsync(dst + pl.block_off[b], u->pipe.layer_out(l, i), n,
+                                       cudaMemcpyDeviceToDevice, s), "copy result");
+    }
+  }
+  if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
+  if (!st) st = cuda_status(cudaLaunchHostFunc(s, notify_cb, c), "host notify");
+  if (st) c->device_error = true;
+  c->launched++;
+  c->batch_frames += d.n_frames;
+  // batched synchronisation bookkeeping
+  c->open_units.push_back(ui);
+  c->open_sum += u->est;
+  if (c->open_sum >= c->cfg.delta_eval_us) {
+    c->closed.push_back(c->open_units);
+    c->open_units.clear();
+    c->open_sum = 0;
+  }
+  return 0;
+}
+
+void calibrate(pp_ctx* c, double t) {
+  if (!c->calibrating) return;
+  double mx = -INFINITY;
+  for (Frame* f : c->ready) {
+    const double s = f->deadline - unit_est(c, f->precision, 1) - t;
+    if (s > 0) mx = std::max(mx, 1.0 / s);
+  }
+  for (Unit* u : c->units)
+    if (u->running) mx = std::max(mx, u->ul);
+  if (std::isfinite(mx)) c->th_samples.push_back(mx);
+  if ((int64_t)c->n_done >= c->cfg.th_calib_frames && c->th_samples.size() >= 8) {
+    std::vector<double> v = c->th_samples;
+    std::sort(v.begin(), v.end());
+    c->th = v[(size_t)std::floor(0.95 * (double)(v.size() - 1))];
+    c->calibrating = false;
+  }
+}
+
+// One pass of decisions; returns the time (us) until the dispatcher should look again.
+double decide_all(pp_ctx* c) {
+  double wake = 1e9;
+  for (int guard = 0; guard < 1024; ++guard) {
+    const double t = now_us();
+    calibrate(c, t);
+    std::vector<pp_policy_frame> rf;
+    rf.reserve(c->ready.size());
+    for (Frame* f : c->ready) {
+      pp_policy_frame p;
+      p.frame_id = f->id;
+      p.chain_id = f->chain;
+      p.precision = f->precision;
+      p.t_arr_us = f->t_arr;
+      p.deadline_us = f->deadline;
+      p.est_gpu_us = unit_est(c, f->precision, 1);
+      p.est_cpu_us = 0.0;
+      p.util = 1.0;
+      rf.push_back(p);
+    }
+    std::vector<pp_policy_active> act;
+    for (Unit* u : c->units)
+      if (u->running) act.push_back({u->head_chain, u->ul});
+    pp_policy_config pc = policy_cfg(c);
+    pp_policy_decision d;
+    std::vector<uint64_t> drops(rf.size() + 1);
+    pp_policy_decide(&pc, t, rf.data(), (int)rf.size(), act.data(), (int)act.size(),
+                     closed_pending(c), &d, drops.data(), (int)drops.size());
+    for (int i = 0; i < d.n_drops; ++i) {
+      Frame* f = c->frames[drops[i]];
+      c->ready.erase(std::remove(c->ready.begin(), c->ready.end(), f), c->ready.end());
+      f->dropped = true;
+      free_staging(c, f);
+      free_result(c, f);
+      c->admitted[f->precision]--;
+      push_result(c, f, PP_FRAME_DROPPED, t);
+    }
+    c->decisions++;
+    if (d.kind == PP_DECIDE_RELEASE) {
+      if (launch_unit(c, d, t)) return 200.0;  // no free unit
+      c->sched_us += now_us() - t;
+      continue;
+    }
+    c->sched_us += now_us() - t;
+    if (d.kind == PP_DECIDE_DELAY) {
+      for (Frame* f : c->ready)
+        if (f->delay_start < 0) {
+          f->delay_start = t;
+          c->delayed++;
+        }
+      wake = std::min(wake, c->cfg.delay_quantum_us);
+    } else if (d.kind == PP_DECIDE_WAIT) {
+      wake = std::min(wake, 200.0);
+    }
+    break;
+  }
+  bool running = false;
+  for (Unit* u : c->units) running |= u->running;
+  if (running) wake = std::min(wake, 500.0);
+  return wake;
+}
+
+void dispatcher_main(pp_ctx* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (!c->stop.load()) {
+    reap(c);
+    const double wake = decide_all(c);
+    c->cv_work.wait_for(lk, std::chrono::microseconds((int64_t)std::max(20.0, std::min(wake, 1e6))));
+  }
+}
+
+void destroy_units(pp_ctx* c) {
+  for (Unit* u : c->units) {
+    u->pipe.release();
+    if (u->start) cudaEventDestroy(u->start);
+    if (u->done) cudaEventDestroy(u->done);
+    delete u;
+  }
+  c->units.clear();
+  for (int p = 0; p < 2; ++p)
+    if (c->have[p]) c->models[p].release();
+  for (float* s : c->staging) cudaFreeHost(s);
+  c->staging.clear();
+  for (auto& pl : c->pool)
+    if (pl.base) cudaFree(pl.base);
+  for (auto& ch : c->chains)
+    for (cudaStream_t s : ch.streams) cudaStreamDestroy(s);
+  if (c->ref_event) cudaEventDestroy(c->ref_event);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  for (auto& kv : c->frames) delete kv.second;
+  c->frames.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+double pp_now_us(void) { return now_us(); }
+
+void pp_config_defaults(pp_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->max_batch = 8;
+  cfg->cap_points = 150000;
+  cfg->precisions = 3;
+  cfg->units = 0;
+  cfg->hbm_budget_bytes = 20ull << 30;
+  cfg->policy = PP_POLICY_URGENCY;
+  cfg->use_graphs = 1;
+  cfg->delta_eval_us = 500.0;
+  cfg->max_closed = 2;
+  cfg->delay_quantum_us = 1000.0;
+  cfg->th_urgent = 0.0;
+  cfg->th_calib_frames = 64;
+  cfg->util_exempt = 0.1;
+  cfg->early_exit = 1;
+  cfg->num_streams = 0;
+}
+
+int pp_create(const pp_config* cfg, pp_ctx** out) {
+  if (!cfg || !out) return fail(PP_EINVAL, "create: NULL argument");
+  if (cfg->max_batch < 1 || cfg->max_batch > 8) return fail(PP_EINVAL, "create: max_batch must be 1..8");
+  if (cfg->cap_points < 1 || cfg->cap_points > (1 << 24)) return fail(PP_EINVAL, "create: cap_points 1..2^24");
+  if ((cfg->precisions & 3) == 0) return fail(PP_EINVAL, "create: no precision enabled");
+  if (cfg->policy != PP_POLICY_FIFO && cfg->policy != PP_POLICY_URGENCY) return fail(PP_EINVAL, "create: bad policy");
+  if (cfg->units < 0 || cfg->units > 64 || cfg->max_closed < 0 || !(cfg->delta_eval_us >= 0) ||
+      cfg->max_admitted < 0 ||
+      !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0)
+    return fail(PP_EINVAL, "create: bad runtime knob");
+  pp_ctx* c = new (std::nothrow) pp_ctx();
+  if (!c) return fail(PP_ENOMEM, "create: host allocation");
+  c->cfg = *cfg;
+  c->cfg.pfn_w = c->cfg.pfn_bn = nullptr;  // not retained: weights are copied to the device
+  c->cfg.conv_w = c->cfg.conv_bn = nullptr;
+  int st = cuda_status(cudaGetDevice(&c->device), "get device");
+  int least = 0, greatest = 0;
+  if (!st) st = cuda_status(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
+  c->prio_greatest = greatest;
+  c->num_pri = least - greatest + 1;
+  if (cfg->num_streams > 0) c->num_pri = std::min(c->num_pri, cfg->num_streams);
+  if (!st) st = cuda_status(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "aux stream");
+  uint64_t used = 0;
+  for (int p = 0; p < 2 && !st; ++p) {
+    if (!(cfg->precisions & (1 << p))) continue;
+    st = c->models[p].upload(cfg, p, c->aux);
+    c->have[p] = st == PP_OK;
+    used += c->models[p].bytes;
+  }
+  // units: round-robin over precisions while the budget allows
+  const int want = cfg->units > 0 ? cfg->units : 16;
+  for (int k = 0; k < want && !st; ++k) {
+    for (int p = 0; p < 2 && !st; ++p) {
+      if (!c->have[p]) continue;
+      Unit* u = new (std::nothrow) Unit();
+      if (!u) { st = fail(PP_ENOMEM, "create: host allocation"); break; }
+      u->precision = p;
+      st = u->pipe.init(&c->models[p], cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, c->aux);
+      if (!st) st = cuda_status(cudaEventCreate(&u->start), "event");
+      if (!st) st = cuda_status(cudaEventCreate(&u->done), "event");
+      if (!st && used + u->pipe.bytes() > cfg->hbm_budget_bytes) {
+        u->pipe.release();
+        cudaEventDestroy(u->start);
+        cudaEventDestroy(u->done);
+        delete u;
+        if (c->capacity[p] == 0) st = fail(PP_ENOMEM, "create: one unit (precision %d) exceeds the HBM budget", p);
+        k = want;  // budget exhausted
+        break;
+      }
+      if (st) { u->pipe.release(); delete u; break; }
+      used += u->pipe.bytes();
+      c->units.push_back(u);
+      c->capacity[p] += cfg->max_batch;
+    }
+  }
+  // result pools: one slot per admissible frame, from what is left of the budget
+  for (int p = 0; p < 2 && !st; ++p) {
+    if (!c->have[p] || c->capacity[p] == 0) continue;
+    pp_ctx::Pool& pl = c->pool[p];
+    const Model& m = c->models[p];
+    size_t off = 0;
+    for (int l : m.block_end) {
+      const LayerSpec& L = m.layers[l];
+      pl.block_off.push_back(off);
+      off += align_up((size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (p == PP_F32 ? 4 : 2), 256);
+    }
+    pl.slot_bytes = off;
+    c->capacity[p] = 0;
+  }
+  {
+    const uint64_t left = cfg->hbm_budget_bytes > used ? cfg->hbm_budget_bytes - used : 0;
+    const uint64_t per = c->pool[0].slot_bytes + c->pool[1].slot_bytes;
+    const uint64_t cap = cfg->max_admitted > 0 ? (uint64_t)std::min(cfg->max_admitted, kMaxAdmitted)
+                                               : (uint64_t)kMaxAdmitted;
+    int n = per ? (int)std::min<uint64_t>(left / per, cap) : 0;
+    for (int p = 0; p < 2 && !st; ++p) {
+      pp_ctx::Pool& pl = c->pool[p];
+      if (!pl.slot_bytes) continue;
+      if (n < 1) st = fail(PP_ENOMEM, "create: no room for a result slot in the budget");
+      if (!st) st = cuda_status(cudaMalloc(&pl.base, pl.slot_bytes * (size_t)n), "result pool");
+      for (int i = 0; i < n && !st; ++i) pl.free.push_back(n - 1 - i);
+      c->capacity[p] = n;
+      used += pl.slot_bytes * (size_t)n;
+    }
+  }
+  // pinned staging for host submissions: one slot per admissible frame
+  const int slots = c->capacity[0] + c->capacity[1];
+  for (int i = 0; i < slots && !st; ++i) {
+    float* s = nullptr;
+    st = cuda_status(cudaMallocHost(&s, (size_t)cfg->cap_points * 16), "pinned staging");
+    if (!st) {
+      c->staging.push_back(s);
+      c->staging_free.push_back(i);
+    }
+  }
+  // offline profiling: time every unit size once to seed the estimate table
+  for (int p = 0; p < 2 && !st; ++p) {
+    const int ui = free_unit(c, p);
+    if (ui < 0) continue;
+    Unit* u = c->units[ui];
+    const float* srcs[8] = {nullptr};
+    int counts[8] = {0};
+    for (int b = 1; b <= cfg->max_batch && !st; ++b) {
+      for (int rep = 0; rep < 2 && !st; ++rep) {
+        st = cuda_status(cudaEventRecord(u->start, c->aux), "profile");
+        if (!st) st = u->pipe.run(b, srcs, counts, cfg->use_graphs != 0, c->aux);
+        if (!st) st = cuda_status(cudaEventRecord(u->done, c->aux), "profile");
+        if (!st) st = cuda_status(cudaEventSynchronize(u->done), "profile");
+        float ms = 0;
+        if (!st && rep == 1 && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess)
+          c->lut[p][b].add(ms * 1000.0);
+      }
+    }
+  }
+  if (!st) st = cuda_status(cudaEventCreate(&c->ref_event), "ref event");
+  if (!st) st = cuda_status(cudaEventRecord(c->ref_event, c->aux), "ref event");
+  if (!st) st = cuda_status(cudaEventSynchronize(c->ref_event), "ref event");
+  c->ref_host = now_us();
+  if (st) {
+    destroy_units(c);
+    delete c;
+    return st;
+  }
+  c->th = cfg->th_urgent > 0 ? cfg->th_urgent : -1.0;
+  c->calibrating = cfg->th_urgent == 0.0 && cfg->policy == PP_POLICY_URGENCY;
+  c->dispatcher = std::thread(dispatcher_main, c);
+  *out = c;
+  return PP_OK;
+}
+
+int pp_register_chain(pp_ctx* c, int32_t chain_id, double period_ms, double rel_deadline_ms,
+                      int32_t precision) {
+  if (!c || chain_id < 0 || chain_id >= PP_MAX_CHAINS || !(rel_deadline_ms > 0) || !(period_ms > 0))
+    return fail(PP_EINVAL, "register_chain: bad argument");
+  if (precision != PP_F32 && precision != PP_BF16) return fail(PP_EINVAL, "register_chain: bad precision");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->have[precision]) return fail(PP_EINVAL, "register_chain: precision %d not enabled", precision);
+  Chain& ch = c->chains[chain_id];
+  if (ch.used) return fail(PP_ESTATE, "register_chain: chain %d already registered", chain_id);
+  for (int l = 0; l < c->num_pri; ++l) {
+    cudaStream_t s;
+    int st = cuda_status(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, c->prio_greatest + l),
+                         "chain stream");
+    if (st) return st;
+    ch.streams.push_back(s);
+  }
+  ch.used = true;
+  ch.period_ms = period_ms;
+  ch.deadline_ms = rel_deadline_ms;
+  ch.precision = precision;
+  return PP_OK;
+}
+
+int pp_submit_frame(pp_ctx* c, int32_t chain_id, const float* xyzr, int64_t n_points,
+                    int32_t is_device_ptr, double t_arrival_us, double abs_deadline_us,
+                    uint64_t* frame_id_out) {
+  if (!c || chain_id < 0 || chain_id >= PP_MAX_CHAINS) return fail(PP_EINVAL, "submit: bad chain");
+  if (n_points < 0 || n_points > c->cfg.cap_points || (n_points > 0 && !xyzr))
+    return fail(PP_EINVAL, "submit: n_points outside [0, cap_points] or NULL points");
+  if (is_device_ptr && (reinterpret_cast<uintptr_t>(xyzr) & 15u))
+    return fail(PP_EINVAL, "submit: device points must be 16-byte aligned");
+  std::unique_lock<std::mutex> lk(c->mu);
+  Chain& ch = c->chains[chain_id];
+  if (!ch.used) return fail(PP_ESTATE, "submit: chain %d not registered", chain_id);
+  const int p = ch.precision;
+  if (c->admitted[p] >= c->capacity[p] || c->pool[p].free.empty() ||
+      (!is_device_ptr && c->staging_free.empty())) {
+    c->rejected++;
+    return fail(PP_EAGAIN, "submit: HBM budget full");
+  }
+  Frame* f = new (std::nothrow) Frame();
+  if (!f) return fail(PP_ENOMEM, "submit: host allocation");
+  f->id = c->next_id++;
+  f->chain = chain_id;
+  f->precision = p;
+  f->t_arr = t_arrival_us;
+  f->deadline = abs_deadline_us > 0 ? abs_deadline_us : t_arrival_us + ch.deadline_ms * 1000.0;
+  f->n = n_points;
+  f->rslot = c->pool[p].free.back();
+  c->pool[p].free.pop_back();
+  if (is_device_ptr) {
+    f->src = xyzr;
+  } else {
+    f->staging = c->staging_free.back();
+    c->staging_free.pop_back();
+    float* dst = c->staging[f->staging];
+    lk.unlock();  // the copy runs outside the lock; the slot is already ours
+    if (n_points > 0) memcpy(dst, xyzr, (size_t)n_points * 16);
+    lk.lock();
+    f->src = dst;
+  }
+  c->admitted[p]++;
+  c->submitted++;
+  if (c->first_arr < 0 || f->t_arr < c->first_arr) c->first_arr = f->t_arr;
+  c->frames[f->id] = f;
+  c->ready.push_back(f);
+  if (frame_id_out) *frame_id_out = f->id;
+  lk.unlock();
+  c->cv_work.notify_one();
+  return PP_OK;
+}
+
+int pp_poll(pp_ctx* c, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us) {
+  if (!c || !out || max <= 0 || !n_out) return fail(PP_EINVAL, "poll: bad argument");
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (c->completed.empty() && timeout_us > 0)
+    c->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [c] { return !c->completed.empty(); });
+  int n = 0;
+  while (n < max && !c->completed.empty()) {
+    out[n] = c->completed.front();
+    c->completed.pop_front();
+    auto it = c->frames.find(out[n].frame_id);
+    if (it != c->frames.end()) it->second->polled = true;
+    ++n;
+  }
+  *n_out = n;
+  return c->device_error ? fail(PP_EDEVICE, "a unit failed on the device") : PP_OK;
+}
+
+int pp_result_release(pp_ctx* c, uint64_t frame_id) {
+  if (!c) return fail(PP_EINVAL, "release: NULL context");
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->frames.find(frame_id);
+  if (it == c->frames.end()) return fail(PP_EINVAL, "release: unknown frame %llu", (unsigned long long)frame_id);
+  Frame* f = it->second;
+  if (!f->done) return fail(PP_ESTATE, "release: frame %llu not completed", (unsigned long long)frame_id);
+  if (!f->dropped) {
+    free_result(c, f);
+    c->admitted[f->precision]--;
+  }
+  c->frames.erase(it);
+  delete f;
+  lk.unlock();
+  c->cv_work.notify_one();
+  return PP_OK;
+}
+
+int pp_get_stats(pp_ctx* c, pp_stats* s) {
+  if (!c || !s) return fail(PP_EINVAL, "stats: NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  memset(s, 0, sizeof(*s));
+  s->submitted = c->submitted;
+  s->done = c->n_done;
+  s->dropped = c->n_dropped;
+  s->missed = c->n_missed;
+  s->rejected = c->rejected;
+  double sum = 0;
+  int nch = 0;
+  for (int i = 0; i < PP_MAX_CHAINS; ++i) {
+    const Chain& ch = c->chains[i];
+    s->chain_frames[i] = ch.frames;
+    s->chain_missed[i] = ch.missed;
+    if (ch.frames) {
+      sum += (double)ch.missed / (double)ch.frames;
+      ++nch;
+      std::vector<double> v = ch.lat;
+      if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        s->chain_p99_us[i] = v[(size_t)std::floor(0.99 * (double)(v.size() - 1))];
+      }
+    }
+  }
+  s->overall_miss_ratio = nch ? sum / nch : 0.0;
+  if (!c->lat_all.empty()) {
+    std::vector<double> v = c->lat_all;
+    std::sort(v.begin(), v.end());
+    s->lat_p50_us = v[(size_t)std::floor(0.50 * (double)(v.size() - 1))];
+    s->lat_p99_us = v[(size_t)std::floor(0.99 * (double)(v.size() - 1))];
+    double m = 0;
+    for (double x : v) m += x;
+    s->lat_mean_us = m / (double)v.size();
+  }
+  if (c->n_done && c->last_done > c->first_arr)
+    s->frames_per_s = (double)c->n_done / ((c->last_done - c->first_arr) * 1e-6);
+  s->units_launched = c->launched;
+  s->mean_batch = c->launched ? (double)c->batch_frames / (double)c->launched : 0.0;
+  s->delayed_releases = c->delayed;
+  s->delayed_us = c->delayed_us;
+  s->collisions = c->collisions;
+  s->sched_us_per_decision = c->decisions ? c->sched_us / (double)c->decisions : 0.0;
+  s->th_urgent = c->th;
+  return PP_OK;
+}
+
+int pp_destroy(pp_ctx* c) {
+  if (!c) return PP_OK;
+  c->stop.store(true);
+  c->cv_work.notify_all();
+  if (c->dispatcher.joinable()) c->dispatcher.join();
+  const double t0 = now_us();
+  bool busy = true;
+  while (busy && now_us() - t0 < 10e6) {
+    busy = false;
+    for (Unit* u : c->units)
+      if (u->running && cudaEventQuery(u->done) == cudaErrorNotReady) busy = true;
+    if (busy) std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  cudaGetLastError();
+  if (busy) return fail(PP_ETIMEDOUT, "destroy: units still running after 10 s");
+  // every unit's completion event has fired; what may remain on a chain stream is the host
+  // notification queued after it, which touches this context: let it finish first
+  for (auto& ch : c->chains)
+    for (cudaStream_t s : ch.streams) cudaStreamSynchronize(s);
+  cudaGetLastError();
+  destroy_units(c);
+  delete c;
+  return PP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+"""Whole front end through the C ABI: a release unit (pp_pipeline_*) with plain launches and
+with its CUDA graphs, and the serving runtime (pp_create ... pp_destroy), checked against the
+FP64 oracle; a frame's result is bit-identical alone and in a mixed batch; admission under the
+HBM budget, early exit and shutdown with work in flight."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import pillars as O
+from pp_synth import (BACKBONE_FULL, BACKBONE_SMALL, GEOM_FULL, GEOM_SMALL, config_points,
+                      pillar_weights, uniform_cloud)
+from tests._util import BF16_TOL, FP32_TOL, bf16_emulated_backbone, max_norm_err, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+import paper_2509_12207_gb300 as pp  # noqa: E402
+
+DEV = "cuda:0"
+W_SMALL = pillar_weights(BACKBONE_SMALL, 7)
+
+
+def _ref(cloud, g=GEOM_SMALL, bb=BACKBONE_SMALL, w=W_SMALL):
+    return O.frame(cloud, g, bb, w)
+
+
+def _interior(t):
+    return t[1:-1, 1:-1].float().cpu().numpy()
+
+
+def _check_out(got, ref, prec, w=W_SMALL, bb=BACKBONE_SMALL):
+    """FP32: per-element error (rel_err) <= 1e-4.  BF16: max error relative to the output's
+    largest magnitude <= 2e-2 against the FP64 oracle with unrounded weights, and <= 8e-3
+    against the oracle with the BF16 path's roundings emulated (a canvas value that sits on a
+    bf16 rounding boundary may round one ulp apart on the two sides)."""
+    if prec == pp.PP_F32:
+        assert rel_err(got, ref["blocks"][-1]) <= FP32_TOL
+    else:
+        assert max_norm_err(got, ref["blocks"][-1]) <= BF16_TOL
+        emu = bf16_emulated_backbone(ref["canvas"], w[2], w[3], bb.layers(64))
+        assert max_norm_err(got, emu) <= 8e-3
+
+
+@pytest.fixture(scope="module")
+def small_clouds():
+    return [config_points(3, 0, 61000), config_points(1, 0), config_points(3, 1, 150000)]
+
+
+@pytest.mark.parametrize("prec", [pp.PP_F32, pp.PP_BF16])
+def test_pipeline_batch_and_graph(prec, small_clouds):
+    cfg, keep = pp.make_config(GEOM_SMALL, BACKBONE_SMALL, W_SMALL, max_batch=4, cap_points=150000)
+    p = pp.Pipeline(cfg, prec)
+    try:
+        frames = [torch.from_numpy(c).to(DEV) for c in small_clouds]
+        refs = [_ref(c) for c in small_clouds]
+        outs = {}
+        for use_graph in (False, True):
+            p.run(frames, use_graph=use_graph)
+            torch.cuda.synchronize()
+            for i, r in enumerate(refs):
+                assert p.num_pillars(i) == r["vox"]["num_pillars"]
+                o = p.output_tensor(i, 0)
+                _check_out(_interior(o), r, prec)
+                if use_graph:
+                    assert torch.equal(o, outs[i])     # graph replay == plain launches, bitwise
+                else:
+                    outs[i] = o
+        # the same frame alone (batch of 1) is bit-identical to its result in the batch
+        p.run([frames[2]], use_graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(p.output_tensor(0, 0), outs[2])
+    finally:
+        p.destroy()
+
+
+def test_pipeline_full_size_fp32():
+    w = pillar_weights(BACKBONE_FULL, 11)
+    cloud = config_points(2, 0)
+    ref = O.frame(cloud, GEOM_FULL, BACKBONE_FULL, w)
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000)
+    p = pp.Pipeline(cfg, pp.PP_F32)
+    try:
+        p.run([torch.from_numpy(cloud).to(DEV)])
+        torch.cuda.synchronize()
+        assert p.num_pillars(0) == ref["vox"]["num_pillars"] == GEOM_FULL.max_pillars
+        for b in range(3):
+            assert rel_err(_interior(p.output_tensor(0, b)), ref["blocks"][b]) <= FP32_TOL, b
+    finally:
+        p.destroy()
+
+
+def _ctx(**kw):
+    knobs = dict(max_batch=4, cap_points=150000, units=2, th_urgent=-1.0)
+    knobs.update(kw)
+    cfg, keep = pp.make_config(GEOM_SMALL, BACKBONE_SMALL, W_SMALL, **knobs)
+    ctx = pp.Context(cfg)
+    return ctx, keep
+
+
+def _drain(ctx, n, timeout_s=30.0):
+    got = []
+    t0 = time.time()
+    while len(got) < n and time.time() - t0 < timeout_s:
+        got += ctx.poll(64, timeout_us=100000)
+    assert len(got) == n, (len(got), n)
+    return got
+
+
+def test_runtime_serves_frames_exactly(small_clouds):
+    ctx, keep = _ctx()
+    try:
+        ctx.register_chain(0, 50.0, 50.0, pp.PP_F32)
+        ctx.register_chain(1, 100.0, 100.0, pp.PP_BF16)
+        ids = {}
+        dev_frames = [torch.from_numpy(c).to(DEV) for c in small_clouds]
+        for i, c in enumerate(small_clouds):
+            rc, fid = ctx.submit(0, c)                    # host memory, copied
+            assert rc == pp.PP_OK
+            ids[fid] = (0, i)
+            rc, fid = ctx.submit(1, dev_frames[i])        # device memory, borrowed
+            assert rc == pp.PP_OK
+            ids[fid] = (1, i)
+        res = _drain(ctx, len(ids))
+        refs = [_ref(c) for c in small_clouds]
+        for r in res:
+            chain, i = ids[r.frame_id]
+            assert r.status == pp.PP_FRAME_DONE and r.chain_id == chain
+            assert r.num_pillars == refs[i]["vox"]["num_pillars"]
+            assert r.t_done_us > r.t_release_us >= r.t_arr_us
+            _check_out(_interior(pp.result_tensor(r)), refs[i], pp.PP_F32 if chain == 0 else pp.PP_BF16)
+            ctx.release(r.frame_id)
+        st = ctx.stats()
+        assert st["done"] == len(ids) and st["dropped"] == 0
+        assert st["chain_frames"][0] == 3 and st["chain_frames"][1] == 3
+    finally:
+        ctx.destroy()
+
+
+def test_runtime_alone_vs_mix(small_clouds):
+    # synchronous batches (each release waits for the previous one) so frames that arrive
+    # while a unit runs accumulate and are released together
+    ctx, keep = _ctx(delta_eval_us=0.0, max_closed=1)
+    try:
+        ctx.register_chain(3, 100.0, 100.0, pp.PP_BF16)
+        ctx.register_chain(4, 100.0, 100.0, pp.PP_BF16)
+        probe = small_clouds[1]
+        rc, fid = ctx.submit(3, probe)
+        (r,) = _drain(ctx, 1)
+        assert r.batch == 1
+        alone = pp.result_tensor(r)
+        ctx.release(r.frame_id)
+        others = [uniform_cloud(n, 50 + n, GEOM_SMALL) for n in (30000, 90000, 140000, 60000, 120000, 45000, 80000)]
+        want = None
+        # the probe among other frames: units fill up, later frames share units
+        dev = [torch.from_numpy(c).to(DEV) for c in others]
+        probe_dev = torch.from_numpy(probe).to(DEV)
+        torch.cuda.synchronize()
+        for k, c in enumerate(dev):
+            ctx.submit(4, c)
+            if k == 3:
+                _, want = ctx.submit(3, probe_dev)
+        res = _drain(ctx, len(others) + 1)
+        mix = [r for r in res if r.frame_id == want][0]
+        assert mix.status == pp.PP_FRAME_DONE
+        assert torch.equal(pp.result_tensor(mix), alone)
+        assert max(r.batch for r in res) > 1       # some frames did share a unit
+        for r in res:
+            ctx.release(r.frame_id)
+    finally:
+        ctx.destroy()
+
+
+def test_runtime_admission_budget_and_early_exit():
+    ctx, keep = _ctx(units=1, precisions=1, max_admitted=4)   # FP32 only, 4 result slots
+    try:
+        ctx.register_chain(0, 50.0, 50.0, pp.PP_F32)
+        cloud = uniform_cloud(30000, 3, GEOM_SMALL)
+        ids = []
+        for _ in range(4):
+            rc, fid = ctx.submit(0, cloud)
+            assert rc == pp.PP_OK
+            ids.append(fid)
+        rc, _ = ctx.submit(0, cloud)
+        assert rc == pp.PP_EAGAIN                 # budget: 4 admitted, none released yet
+        res = _drain(ctx, 4)
+        assert all(r.status == pp.PP_FRAME_DONE for r in res)   # one unit, reused at completion
+        rc, _ = ctx.submit(0, cloud)
+        assert rc == pp.PP_EAGAIN                 # results still held
+        for r in res:
+            ctx.release(r.frame_id)
+        # a frame whose deadline has already passed is dropped before release (early exit)
+        now = pp.now_us()
+        rc, late = ctx.submit(0, cloud, t_arrival_us=now - 5000.0, abs_deadline_us=now - 1000.0)
+        assert rc == pp.PP_OK
+        (r,) = _drain(ctx, 1)
+        assert r.frame_id == late and r.status == pp.PP_FRAME_DROPPED and r.missed
+        ctx.release(late)
+        st = ctx.stats()
+        assert st["rejected"] == 2 and st["dropped"] == 1
+    finally:
+        ctx.destroy()
+
+
+def test_runtime_fifo_baseline_and_destroy_in_flight():
+    ctx, keep = _ctx(policy=pp.PP_POLICY_FIFO, max_batch=1, use_graphs=0, max_closed=0, units=4)
+    ctx.register_chain(0, 50.0, 50.0, pp.PP_F32)
+    ctx.register_chain(1, 50.0, 50.0, pp.PP_BF16)
+    for k in range(6):
+        ctx.submit(k % 2, uniform_cloud(40000, k, GEOM_SMALL))
+    ctx.destroy()          # bounded wait for in-flight units, then frees everything

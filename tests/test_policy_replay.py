@@ -1,0 +1,102 @@
+"""Decision replay: the library's release rule (pp_policy_decide, C++) and the oracle's
+decide() (Python) must take the same decision on every state -- same kind, same frames in the
+same order, same stream level, same drops.  Pure host code: runs on the CPU."""
+import numpy as np
+import pytest
+
+from oracle import sched as S
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_2509_12207_gb300 import _build
+    _build.build()
+    import paper_2509_12207_gb300 as m
+    return m
+
+
+def _random_state(rng):
+    t = float(rng.uniform(0, 1e5))
+    n = int(rng.integers(0, 14))
+    ready = []
+    for i in range(n):
+        # coarse grids make ties in slack, chain and arrival common
+        t_arr = t - float(rng.choice([0, 100, 250, 1000, 5000]))
+        D = float(rng.choice([500, 1000, 2000, 5000, 50000]))
+        est = float(rng.choice([100, 400, 900, 3000]))
+        ready.append(dict(frame_id=int(1000 + i * 7 % 13 + 20 * i), chain_id=int(rng.integers(0, 6)),
+                          precision=int(rng.integers(0, 2)), t_arr_us=t_arr, deadline_us=t_arr + D,
+                          est_gpu_us=est, est_cpu_us=float(rng.choice([0.0, 50.0])),
+                          util=float(rng.choice([0.05, 0.1, 0.5, 1.0]))))
+    active = [(int(rng.integers(0, 6)), float(rng.choice([-np.inf, 1e-5, 1e-4, 5e-4, 2e-3, 1e-2])))
+              for _ in range(int(rng.integers(0, 6)))]
+    cfg = dict(policy=int(rng.integers(0, 2)), max_batch=int(rng.integers(1, 9)),
+               max_closed=int(rng.integers(0, 3)), num_pri=int(rng.integers(1, 7)),
+               early_exit=int(rng.integers(0, 2)),
+               th_urgent=float(rng.choice([0.0, -1.0, 1e-4, 1e-3])), util_exempt=0.1)
+    return t, ready, active, int(rng.integers(0, 4)), cfg
+
+
+def _oracle(t, ready, active, closed, cfg):
+    oc = S.PolicyConfig(policy=cfg["policy"], max_batch=cfg["max_batch"], max_closed=cfg["max_closed"],
+                        th_urgent=cfg["th_urgent"], util_exempt=cfg["util_exempt"],
+                        early_exit=bool(cfg["early_exit"]), num_pri=cfg["num_pri"])
+    rr = [S.Ready(r["frame_id"], r["chain_id"], r["t_arr_us"], r["deadline_us"], r["est_gpu_us"],
+                  r["est_cpu_us"], r["precision"], r["util"]) for r in ready]
+    aa = [S.Active(c, u) for c, u in active]
+    return S.decide(t, rr, aa, closed, oc)
+
+
+def test_replay_random_states(pp):
+    rng = np.random.default_rng(2024)
+    kinds = {}
+    for _ in range(6000):
+        t, ready, active, closed, cfg = _random_state(rng)
+        kind, frames, level, drops = pp.policy_decide(cfg, t, ready, active, closed)
+        d = _oracle(t, ready, active, closed, cfg)
+        assert kind == d.kind, (cfg, ready, active, closed)
+        assert drops == d.drops
+        if kind == S.RELEASE:
+            assert frames == d.frames
+            assert level == d.level
+        kinds[kind] = kinds.get(kind, 0) + 1
+    # every kind of decision was exercised
+    assert set(kinds) == {S.NONE, S.RELEASE, S.WAIT, S.DELAY}, kinds
+
+
+def test_replay_des_trace(pp):
+    """Replays every decision point of a discrete-event simulation through the library."""
+    rng = np.random.default_rng(5)
+    frames = []
+    for i in range(300):
+        t = float(i * 30 + rng.integers(0, 25))
+        frames.append(S.SimFrame(i, i % 7, t, t + float(rng.choice([200, 400, 900])),
+                                 [float(rng.integers(20, 150))], precision=(i % 7) % 2))
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=4, delta_eval_us=150.0, max_closed=2,
+                         th_urgent=1.0 / 150.0, num_pri=6)
+    calls = []
+    orig = S.decide
+
+    def spy(t, ready, active, closed, c):
+        d = orig(t, ready, active, closed, c)
+        calls.append((t, list(ready), list(active), closed, d))
+        return d
+
+    S.decide = spy
+    try:
+        S.simulate(frames, cfg, delay_quantum_us=50.0, unit_time=lambda ds: 15.0 + 0.6 * sum(ds))
+    finally:
+        S.decide = orig
+    assert len(calls) > 300
+    pc = dict(policy=cfg.policy, max_batch=cfg.max_batch, max_closed=cfg.max_closed, num_pri=cfg.num_pri,
+              early_exit=int(cfg.early_exit), th_urgent=cfg.th_urgent, util_exempt=cfg.util_exempt)
+    seen = set()
+    for t, ready, active, closed, d in calls:
+        rr = [dict(frame_id=r.frame_id, chain_id=r.chain_id, precision=r.precision, t_arr_us=r.t_arr,
+                   deadline_us=r.deadline, est_gpu_us=r.est_gpu, est_cpu_us=r.est_cpu, util=r.util) for r in ready]
+        kind, fr, level, drops = pp.policy_decide(pc, t, rr, [(a.chain_id, a.ul) for a in active], closed)
+        assert (kind, drops) == (d.kind, d.drops)
+        if kind == S.RELEASE:
+            assert (fr, level) == (d.frames, d.level)
+        seen.add(kind)
+    assert S.RELEASE in seen and S.WAIT in seen
