@@ -92,6 +92,29 @@ int pp_voxelize(const pp_geometry* g, int32_t batch, int32_t cap_points,
  * n_points value was out of range). */
 int pp_voxelize_check(const void* workspace, void* stream);
 
+/* Same operation and outputs as pp_voxelize, for callers that cannot allocate device memory:
+ * the paper has no counterpart; this entry point exists for deployments such as real-time
+ * task threads that may not call the CUDA allocator once they run (cudaMalloc/cudaFree can
+ * block or synchronise the whole device) and hosts whose device memory is owned by another
+ * framework.  It takes no workspace: its scratch is a file-scope device array of
+ * PP_VOX_STATIC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library holds until
+ * the process exits.  Calls needing more scratch than that (pp_voxelize_workspace_bytes() >
+ * PP_VOX_STATIC_SCRATCH_BYTES, e.g. batch 8 x 150,000 points fits, 16 x 150,000 does not)
+ * return PP_EINVAL with a message and enqueue nothing.  It allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current and caches it; make
+ * that first call before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents (the call clears the part that must start at zero): calls whose
+ * work overlaps on the GPU (concurrent streams, or threads) race on it and must be
+ * serialised by the caller.  A n_points value outside [0, cap_points] makes that frame empty
+ * (this variant has no error word to report it). */
+#define PP_VOX_STATIC_SCRATCH_BYTES (16u << 20)
+int pp_voxelize_static(const pp_geometry* g, int32_t batch, int32_t cap_points,
+                       const float* points, const int32_t* n_points,
+                       int32_t* cell, uint32_t* cnt, int32_t* pillar_of_cell,
+                       int32_t* coord, int32_t* npts, int32_t* num_pillars, float* pts,
+                       void* stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Stage 2: PointNet.  Per pillar p < num_pillars[b] and channel c < 64:                     */
 /*   features f = (x, y, z, r, x-mx, y-my, z-mz, x-xc, y-yc) per kept point, where (mx,my,mz)*/

@@ -134,6 +134,7 @@ _SIGS = {
     "pp_voxelize_workspace_bytes": (_SZ, [_GP, _I, _I]),
     "pp_voxelize": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "pp_voxelize_check": (ctypes.c_int, [_P, _P]),
+    "pp_voxelize_static": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_pointnet": (ctypes.c_int, [_GP, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_scatter": (ctypes.c_int, [_GP, _I, _P, _P, _P, _I, _P]),
     "pp_conv3x3": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P]),
@@ -238,6 +239,32 @@ def voxelize(points, n_points, geom, stream=None) -> Dict[str, object]:
                              _ptr(out["npts"]), _ptr(out["num_pillars"]), _ptr(out["pts"]),
                              ws_ptr, ws_bytes, s))
     out["_workspace"] = (ws, ws_ptr)
+    return out
+
+
+def voxelize_static(points, n_points, geom, stream=None) -> Dict[str, object]:
+    """pp_voxelize_static: same outputs as voxelize(), scratch in the library's static device
+    array instead of a workspace (for callers that cannot allocate device memory; the output
+    tensors here are still allocated by torch on the caller's side)."""
+    import torch
+    _need_cuda(points, n_points)
+    g = Geometry.of(geom)
+    B, cap = int(points.shape[0]), int(points.shape[1])
+    dev = points.device
+    G, P = g.nx * g.ny, g.max_pillars
+    out = {
+        "cell": torch.empty((B, cap), dtype=torch.int32, device=dev),
+        "cnt": torch.empty((B, G), dtype=torch.int32, device=dev),
+        "pillar_of_cell": torch.empty((B, G), dtype=torch.int32, device=dev),
+        "coord": torch.empty((B, P), dtype=torch.int32, device=dev),
+        "npts": torch.empty((B, P), dtype=torch.int32, device=dev),
+        "num_pillars": torch.empty((B,), dtype=torch.int32, device=dev),
+        "pts": torch.empty((B, P, 32, 4), dtype=torch.float32, device=dev),
+    }
+    _check(lib().pp_voxelize_static(ctypes.byref(g), B, cap, _ptr(points), _ptr(n_points), _ptr(out["cell"]),
+                                    _ptr(out["cnt"]), _ptr(out["pillar_of_cell"]), _ptr(out["coord"]),
+                                    _ptr(out["npts"]), _ptr(out["num_pillars"]), _ptr(out["pts"]),
+                                    _stream(stream)))
     return out
 
 
