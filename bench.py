@@ -42,6 +42,10 @@ def _args():
     ap.add_argument("--workload", default="cfg2-fp32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
+    ap.add_argument("--serve-sweep", default=None,
+                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed]")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -178,7 +182,7 @@ class _Clocks:
 def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=10):
     """Average duration of each conv layer's kernel, launched through pp_conv3x3 on the current
     stream and timed with CUDA events around `reps` launches of it."""
-    dt = torch.float32 if prec == pp.PP_F32 else torch.bfloat16
+    dt = torch.bfloat16 if prec == pp.PP_BF16 else torch.float32
     H, W = g.ny, g.nx
     x = torch.rand((batch, H + 2, W + 2, 64), device="cuda").to(dt)
     x[:, 0] = 0; x[:, -1] = 0; x[:, :, 0] = 0; x[:, :, -1] = 0
@@ -242,7 +246,7 @@ def _run_ours(a, rank, world, dist):
     # throughput run: no deadline pressure (early exit off, 10 s deadline), so a slow run (a
     # profiler) still completes every frame
     cfg, keep = pp.make_config(g, bb, w, max_batch=batch, cap_points=cap, precisions=1 << prec, units=2,
-                               th_urgent=-1.0, early_exit=0)
+                               th_urgent=-1.0, early_exit=0, fp32_cuda_cores=1 if a.fp32_cuda_cores else 0)
     ctx = pp.Context(cfg)
     ctx.register_chain(0, 10000.0, 10000.0, prec)
     frames_dev = [torch.from_numpy(f).cuda() for f in frames]
@@ -304,19 +308,27 @@ def _run_ours(a, rank, world, dist):
     ctx.destroy()
 
     # kernel roofline: the conv kernels dominate the step
-    layers = _time_conv_kernels(pp, torch, g, bb, w, prec, batch)
+    conv_dtype = prec if (prec == pp.PP_BF16 or a.fp32_cuda_cores) else pp.PP_F32_TC
+    layers = _time_conv_kernels(pp, torch, g, bb, w, conv_dtype, batch)
     conv_s = sum(t for t, _ in layers)
     conv_flops = sum(f for _, f in layers)
     stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w, prec)
-    sm_max = (clk.get("sm_max_mhz") or 2070.0)
-    if prec == pp.PP_F32:
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    src = "of measured" if peaks else "of fallback"
+    if prec == pp.PP_F32 and a.fp32_cuda_cores:
+        sm_max = (clk.get("sm_max_mhz") or 2070.0)
         peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # FP32 FMA lanes x 2 flops x clock
         bound, peak_note = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_max
+    elif prec == pp.PP_F32:
+        # 3xTF32: every FP32 FLOP costs three TF32 tensor FLOPs; TF32 dense = bf16 x 1.1/2.25
+        peak = bf16 * (1.1 / 2.25) / 3.0
+        bound, peak_note = "tensor", ("FP32-equivalent via 3 TF32 passes: bf16 dense %s x 1.1/2.25 "
+                                      "(nominal TF32/BF16) / 3" % src)
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        peak = float(peaks.get("bf16_tflops", 1900.0))
-        bound, peak_note = "tensor", "bf16 dense, of measured" if peaks else "bf16 dense, of fallback"
+        peak = bf16
+        bound, peak_note = "tensor", "bf16 dense, %s" % src
     achieved = conv_flops / conv_s / 1e12
     frames_done = a.steps * n_frames * world
     res = {
@@ -332,10 +344,11 @@ def _run_ours(a, rank, world, dist):
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "conv3x3 (%s), all layers"
-                     % ("CUDA-core FP32" if prec == 0 else "tcgen05 BF16"), "peak_source": peak_note,
+                     % {pp.PP_F32: "CUDA-core FP32", pp.PP_F32_TC: "tcgen05 3xTF32", pp.PP_BF16: "tcgen05 BF16"}[conv_dtype],
+                     "peak_source": peak_note,
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames},
         "stage_ms": {k: v for k, v in stages.items()},
-        "serving": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
+        "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
                     "sched_us_per_decision": st["sched_us_per_decision"], "units": st["units_launched"]},
         "gpu_launches": a.steps * (5 + 1 + 1 + len(bb.layers(64))) * (1 if n_frames else 0),
         "clocks": clk,
@@ -343,6 +356,80 @@ def _run_ours(a, rank, world, dist):
         "wall_s": wall,
     }
     return res
+
+
+# ------------------------------------------------------------------ serving (chains with deadlines)
+
+def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0):
+    """Replays periodic chains in real time against one context and returns its statistics.
+
+    mode "urgency": the paper's release rules (urgency order, early exit, stream binding,
+    delayed launch, overlapped batched sync) with continuous batching of up to 8 frames per
+    graph launch; chains BF16 (``mixed``: odd chains BF16, even FP32).  mode "plain": every
+    frame launched on arrival, kernel by kernel, FP32, on its chain's default-priority stream.
+    Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
+    frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
+    f_a and f_d).  A frame the budget cannot admit counts as a miss."""
+    from pp_synth import BACKBONE_SMALL, GEOM_SMALL, arrival_times, pillar_weights, serving_chains
+    g, bb = GEOM_SMALL, BACKBONE_SMALL
+    w = pillar_weights(bb, 7)
+    chains = serving_chains(n_chains, mixed=mixed)
+    if mode == "urgency":
+        knobs = dict(policy=pp.PP_POLICY_URGENCY, max_batch=8, use_graphs=1, max_closed=2,
+                     delta_eval_us=500.0, th_urgent=0.0, th_calib_frames=64, early_exit=1, units=8)
+        prec = [c.precision for c in chains]
+    else:
+        knobs = dict(policy=pp.PP_POLICY_FIFO, max_batch=1, use_graphs=0, max_closed=0, early_exit=0,
+                     th_urgent=-1.0, units=16)
+        prec = [pp.PP_F32] * n_chains
+    need = (1 if pp.PP_F32 in prec else 0) | (2 if pp.PP_BF16 in prec else 0)
+    cfg, keep = pp.make_config(g, bb, w, cap_points=150000, precisions=need, **knobs)
+    ctx = pp.Context(cfg)
+    try:
+        for c, p in zip(chains, prec):
+            ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
+        ev = arrival_times(chains, duration_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed)
+        rejected = {}
+        t0 = pp.now_us() + 20000.0
+        i, outstanding = 0, 0
+        while i < len(ev) or outstanding:
+            now = pp.now_us()
+            while i < len(ev) and t0 + ev[i][0] * 1000.0 <= now:
+                t_ms, cid, n = ev[i]
+                t_arr = t0 + t_ms * 1000.0
+                rc, _fid = ctx.submit(cid, clouds[i % len(clouds)][:n], t_arrival_us=t_arr)
+                if rc == pp.PP_OK:
+                    outstanding += 1
+                else:
+                    rejected[cid] = rejected.get(cid, 0) + 1
+                i += 1
+            wait = 2000.0 if i >= len(ev) else max(0.0, t0 + ev[i][0] * 1000.0 - pp.now_us())
+            for r in ctx.poll(256, timeout_us=int(min(wait, 2000.0))):
+                ctx.release(r.frame_id)
+                outstanding -= 1
+        st = ctx.stats()
+    finally:
+        ctx.destroy()
+    per = {}
+    for c in chains:
+        n = st["chain_frames"][c.chain_id] + rejected.get(c.chain_id, 0)
+        m = st["chain_missed"][c.chain_id] + rejected.get(c.chain_id, 0)
+        if n:
+            per[c.chain_id] = (m, n)
+    miss = sum(m / n for m, n in per.values()) / max(1, len(per))
+    return {"mode": mode, "chains": n_chains, "rate": rate, "deadline_factor": dfac, "mixed": mixed,
+            "frames": len(ev),
+            "done": st["done"], "dropped": st["dropped"], "rejected": sum(rejected.values()),
+            "miss_ratio": miss, "lat_p50_ms": st["lat_p50_us"] / 1e3, "lat_p99_ms": st["lat_p99_us"] / 1e3,
+            "frames_per_s": st["done"] / duration_s, "mean_batch": st["mean_batch"],
+            "delayed": st["delayed_releases"], "collisions": st["collisions"],
+            "th_urgent_per_ms": st["th_urgent"] * 1e3 if st["th_urgent"] > 0 else None,
+            "sched_us_per_decision": st["sched_us_per_decision"]}
+
+
+def _serving_clouds(torch):
+    from pp_synth import GEOM_SMALL, uniform_cloud
+    return [torch.from_numpy(uniform_cloud(150000, 7000 + k, GEOM_SMALL)).cuda() for k in range(16)]
 
 
 def _run_reference(a):
@@ -379,12 +466,39 @@ def main():
         if rank == 0:
             print(json.dumps(_run_reference(a)))
         return
+    if a.serve_sweep:
+        import torch
+        import paper_2509_12207_gb300 as pp
+        torch.cuda.set_device(0)
+        clouds = _serving_clouds(torch)
+        out = []
+        for item in a.serve_sweep.split(","):
+            parts = item.split(":")
+            n, rate, secs = int(parts[0]), float(parts[1]), float(parts[2])
+            mixed = len(parts) > 3 and parts[3] == "mixed"
+            dfac = float(parts[4]) if len(parts) > 4 else 1.0
+            for mode in ("urgency", "plain"):
+                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac))
+                print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+        print(json.dumps({"metric": "deadline-miss ratio and p99 chain latency, urgency-served batched "
+                          "vs plain per-frame launches", "serving": out}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     res = _run_ours(a, rank, world, dist)
+    if rank == 0 and not a.no_serving:
+        import torch
+        import paper_2509_12207_gb300 as pp
+        clouds = _serving_clouds(torch)
+        res["serving"] = {
+            "config4_11_chains_1x": [_serve(pp, torch, m, 11, 1.0, 4.0, False, clouds=clouds)
+                                     for m in ("urgency", "plain")],
+            "config5_33_chains_40x": [_serve(pp, torch, m, 33, 40.0, 4.0, True, clouds=clouds)
+                                      for m in ("urgency", "plain")],
+        }
     if rank == 0:
         if not a.no_cpu_baseline:
             res["cpu_baseline"] = _cpu_baseline(a.workload, 1)

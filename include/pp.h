@@ -43,7 +43,10 @@ typedef enum {
   PP_ESTATE = -6      /* call not valid in the object's current state                        */
 } pp_status;
 
-enum { PP_F32 = 0, PP_BF16 = 1 };
+/* Arithmetic types.  PP_F32 / PP_BF16 name a precision everywhere; PP_F32_TC is accepted only
+ * by pp_conv3x3 / pp_conv_pack_weights / pp_conv_packed_bytes / pp_conv_tile_count and selects
+ * the FP32 conv on the tensor cores (3xTF32 split, FP32 activations and outputs). */
+enum { PP_F32 = 0, PP_BF16 = 1, PP_F32_TC = 2 };
 
 /* Pillar grid.  Ranges are half-open [min, max).  nx * vx must span x, ny * vy must span y.
  * max_pts must be 32.  Cell index of a point (binary32 arithmetic, round to nearest even, no
@@ -145,7 +148,9 @@ int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
 /*   w  : packed weights from pp_conv_pack_weights for the same dtype.                       */
 /*   scale_shift: device float [2][cout].                                                    */
 /* PP_F32: CUDA-core FP32 FMA.  PP_BF16: tcgen05 tensor cores, BF16 x BF16 -> FP32 in TMEM,   */
-/* BF16 output.  cin, cout must be multiples of 64; stride 2 needs even H and W.              */
+/* BF16 output.  PP_F32_TC: FP32 in and out on the tcgen05 tensor cores: each operand split   */
+/* into a TF32 part and an FP32 remainder, three kind::tf32 products accumulated in FP32     */
+/* (error of the order of FP32 rounding).  cin, cout multiples of 64; stride 2 needs even H, W.*/
 /* tile: -1 = library choice (autotuned table when present), else an index into the tile     */
 /* list of pp_conv_tile_count(dtype).                                                        */
 int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
@@ -155,7 +160,9 @@ int pp_conv_tile_count(int32_t dtype);
 
 /* Repacks float OIHW weights [cout][cin][3][3] (device) into the layout pp_conv3x3 expects
  * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,
- * PP_BF16 -> [cout][9*cin] bf16 (round to nearest even), K index = (ky*3+kx)*cin + ci. */
+ * PP_BF16 -> [cout][9*cin] bf16 (round to nearest even), PP_F32_TC -> [2][cout][9*cin] float
+ * (plane 0: weight with the 13 low mantissa bits cleared, plane 1: the remainder);
+ * K index = (ky*3+kx)*cin + ci. */
 size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype);
 int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t dtype,
                          void* w_packed, void* stream);
@@ -223,6 +230,8 @@ typedef struct {
   int32_t max_admitted;         /* admitted-but-unreleased frames per precision (each holds a  */
                                 /* result slot in HBM); 0 = as many as the budget allows, the  */
                                 /* library caps it at 128                                      */
+  int32_t fp32_cuda_cores;      /* FP32 convs on CUDA cores (1) or on the tensor cores with the */
+                                /* 3xTF32 split (0, default)                                   */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,

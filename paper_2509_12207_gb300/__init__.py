@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpp.so")
 
 PP_OK, PP_EINVAL, PP_ENOMEM, PP_EAGAIN, PP_ETIMEDOUT, PP_EDEVICE, PP_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PP_F32, PP_BF16 = 0, 1
+PP_F32, PP_BF16, PP_F32_TC = 0, 1, 2
 BN_EPS = 1e-3
 
 
@@ -59,7 +59,7 @@ class Config(ctypes.Structure):
         ("delay_quantum_us", ctypes.c_double), ("th_urgent", ctypes.c_double),
         ("th_calib_frames", ctypes.c_int32), ("util_exempt", ctypes.c_double),
         ("early_exit", ctypes.c_int32), ("num_streams", ctypes.c_int32),
-        ("max_admitted", ctypes.c_int32),
+        ("max_admitted", ctypes.c_int32), ("fp32_cuda_cores", ctypes.c_int32),
     ]
 
 
@@ -303,8 +303,8 @@ def pack_conv_weights(w_oihw, dtype, stream=None):
     _need_cuda(w_oihw)
     cout, cin = int(w_oihw.shape[0]), int(w_oihw.shape[1])
     n = lib().pp_conv_packed_bytes(cin, cout, dtype)
-    dst = torch.empty(n // (4 if dtype == PP_F32 else 2),
-                      dtype=torch.float32 if dtype == PP_F32 else torch.bfloat16, device=w_oihw.device)
+    f32 = dtype in (PP_F32, PP_F32_TC)
+    dst = torch.empty(n // (4 if f32 else 2), dtype=torch.float32 if f32 else torch.bfloat16, device=w_oihw.device)
     _check(lib().pp_conv_pack_weights(_ptr(w_oihw.contiguous()), cin, cout, dtype, _ptr(dst), _stream(stream)))
     return dst
 
@@ -320,7 +320,7 @@ def bn_fold(bn):
 
 
 def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=None, stream=None):
-    """x: padded NHWC [B, H+2, W+2, cin] (float32 for PP_F32, bfloat16 for PP_BF16).
+    """x: padded NHWC [B, H+2, W+2, cin] (float32 for PP_F32 / PP_F32_TC, bfloat16 for PP_BF16).
     Returns the padded output [B, Ho+2, Wo+2, cout] (border zero)."""
     import torch
     _need_cuda(x, w_packed, scale_shift)

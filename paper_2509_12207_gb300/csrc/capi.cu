@@ -159,21 +159,28 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
     return conv_bf16_launch(c, static_cast<const __nv_bfloat16*>(in),
                             static_cast<const __nv_bfloat16*>(w), scale_shift,
                             static_cast<__nv_bfloat16*>(out), tile, s);
+  if (dtype == PP_F32_TC)
+    return conv_f32tc_launch(c, static_cast<const float*>(in), static_cast<const float*>(w),
+                             scale_shift, static_cast<float*>(out), tile, s);
   return fail(PP_EINVAL, "conv3x3: bad dtype");
 }
 
 int pp_conv_tile_count(int32_t dtype) {
-  return dtype == PP_F32 ? conv_f32_tile_count() : dtype == PP_BF16 ? conv_bf16_tile_count() : 0;
+  return dtype == PP_F32 ? conv_f32_tile_count()
+       : dtype == PP_BF16 ? conv_bf16_tile_count()
+       : dtype == PP_F32_TC ? conv_f32tc_tile_count() : 0;
 }
 
 size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype) {
   if (cin <= 0 || cout <= 0) return 0;
+  if (dtype == PP_F32_TC) return (size_t)2 * 9 * cin * cout * 4;
   return (size_t)9 * cin * cout * (dtype == PP_F32 ? 4 : 2);
 }
 
 int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t dtype,
                          void* w_packed, void* stream) {
-  if (!w_oihw || !w_packed || cin <= 0 || cout <= 0 || (dtype != PP_F32 && dtype != PP_BF16))
+  if (!w_oihw || !w_packed || cin <= 0 || cout <= 0 ||
+      (dtype != PP_F32 && dtype != PP_BF16 && dtype != PP_F32_TC))
     return fail(PP_EINVAL, "pack_weights: bad argument");
   return conv_pack_launch(w_oihw, cin, cout, dtype, w_packed, static_cast<cudaStream_t>(stream));
 }

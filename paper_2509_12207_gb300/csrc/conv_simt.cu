@@ -166,10 +166,17 @@ __global__ void pack_weights(const float* __restrict__ w, int cin, int cout, int
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int kx = i % 3, ky = (i / 3) % 3, ci = (i / 9) % cin, co = i / (9 * cin);
     const int k = (ky * 3 + kx) * cin + ci;
-    if (dtype == PP_F32)
+    if (dtype == PP_F32) {
       static_cast<float*>(dst)[(size_t)k * cout + co] = w[i];
-    else
+    } else if (dtype == PP_F32_TC) {
+      // hi: the value with its 13 low mantissa bits cleared (a TF32 value); lo: the rest
+      const float hi = __uint_as_float(__float_as_uint(w[i]) & 0xFFFFE000u);
+      float* d = static_cast<float*>(dst);
+      d[(size_t)co * 9 * cin + k] = hi;
+      d[(size_t)cout * 9 * cin + (size_t)co * 9 * cin + k] = w[i] - hi;
+    } else {
       static_cast<__nv_bfloat16*>(dst)[(size_t)co * 9 * cin + k] = __float2bfloat16_rn(w[i]);
+    }
   }
 }
 

@@ -292,6 +292,238 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   }
 }
 
+// ---------------------------------------------------------------------------- FP32 via 3xTF32
+//
+// The same implicit GEMM for FP32 activations, on the tensor cores with FP32-level accuracy:
+// every operand x is split into hi = x with its 13 low mantissa bits cleared (exactly a TF32
+// value) and lo = x - hi (exact in FP32, < 2^-10 |x|), and the product is accumulated as
+// hi*hi' + hi*lo' + lo*hi' (the dropped lo*lo' term is < 2^-20 of the product).  Weights come
+// pre-split from packing ([2][cout][9*cin]: hi plane, lo plane).  Activations are split in
+// shared memory: four converter warps wait for each TMA'd A tile (128 pixels x 32 channels,
+// 128-byte swizzle), rewrite it in place as hi and write lo at the same offsets of a second
+// buffer (an elementwise map, so the swizzle is preserved), fence the async proxy and arrive on
+// the stage's "converted" barrier; the MMA thread issues 3 tcgen05.mma.kind::tf32 (K=8) per
+// K step.  The tensor core's FP32 accumulation is not round-to-nearest, so long accumulation
+// chains drift: the MMA thread accumulates only `fold` K blocks into one of two TMEM buffers,
+// and four reducer warps add each finished buffer into FP32 registers (round to nearest) while
+// the MMAs fill the other buffer; the reducers then run the epilogue and store FP32.
+// 320 threads: warp 0 TMA, warp 1 TMEM allocation + MMA, warps 2-5 convert, warps 6-9 reduce
+// (TMEM lane quarters 2, 3, 0, 1).
+
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+struct TcArgsF32 {
+  ConvShape c;
+  int bh, bw, tiles_x, tiles_y, fold;
+  const float* ss;
+  float* out;
+};
+
+constexpr int kBK32 = 32;                        // fp32 channels per K block (128 bytes)
+constexpr uint32_t kA32Bytes = kBM * kBK32 * 4;  // 16 KiB
+
+template <int BN, int STAGES, bool S2>
+__global__ void __launch_bounds__(320, 1)
+conv3x3_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               TcArgsF32 args) {
+  constexpr uint32_t kBBytes = BN * kBK32 * 4;  // one plane
+  constexpr uint32_t kCols = 2 * BN;            // two accumulator buffers
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ unsigned s_abort;
+  if (threadIdx.x == 0) s_abort = tc_error_now();
+  __syncthreads();
+  if (s_abort != 0u) return;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = smem;                              // [STAGES][16K]  fp32, becomes hi
+  uint8_t* sAlo = sA + STAGES * kA32Bytes;         // [STAGES][16K]
+  uint8_t* sB = sAlo + STAGES * kA32Bytes;         // [STAGES][2][BN*128]  hi, lo
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * 2 * kBBytes);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* kdone = empty + STAGES;   // [2] a TMEM buffer holds a finished group of K blocks
+  uint64_t* kfree = kdone + 2;        // [2] the reducers have read that buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + 2);
+  float* s_ss = reinterpret_cast<float*>(tmem_slot + 4);  // [2][BN]
+
+  const ConvShape& c = args.c;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx = blockIdx.x;
+  const int tx = bx % args.tiles_x;
+  const int ty = (bx / args.tiles_x) % args.tiles_y;
+  const int b = bx / (args.tiles_x * args.tiles_y);
+  const int n0 = blockIdx.y * BN;
+  const int oy0 = ty * args.bh, ox0 = tx * args.bw;
+  const int fold = args.fold;
+
+  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+    s_ss[i] = args.ss[n0 + i];
+    s_ss[BN + i] = args.ss[c.cout + n0 + i];
+  }
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&kdone[i], 1);
+      mbar_init(&kfree[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int kchunks = c.cin / kBK32;
+  const int KB = 9 * kchunks;
+  const int groups = (KB + fold - 1) / fold;
+  const int Hp2 = (c.H + 2) / 2;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) break;
+        const int tap = kb / kchunks, cc = kb % kchunks;
+        const int ky = tap / 3, kx = tap % 3;
+        mbar_expect_tx(&full[s], kA32Bytes + 2 * kBBytes);
+        if (S2)
+          tma_5d(sA + s * kA32Bytes, &tmA, &full[s], cc * kBK32, kx & 1, ox0 + (kx >> 1), ky & 1,
+                 b * Hp2 + oy0 + (ky >> 1));
+        else
+          tma_3d(sA + s * kA32Bytes, &tmA, &full[s], cc * kBK32, ox0 + kx,
+                 b * (c.H + 2) + oy0 + ky);
+        const int kk = tap * c.cin + cc * kBK32;
+        tma_3d(sB + s * 2 * kBBytes, &tmB, &full[s], kk, n0, 0);
+        tma_3d(sB + s * 2 * kBBytes + kBBytes, &tmB, &full[s], kk, n0, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc_tf32<BN>();
+      bool ok = true;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        const int g = kb / fold, buf = g & 1;
+        const bool first = kb % fold == 0;
+        if (first && g >= 2 && !mbar_wait(&kfree[buf], (uint32_t)((g >> 1) - 1) & 1u, 16u)) break;
+        if (!mbar_wait(&conv[s], ph, 2u)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        const uint8_t* ahi = sA + s * kA32Bytes;
+        const uint8_t* alo = sAlo + s * kA32Bytes;
+        const uint8_t* bhi = sB + s * 2 * kBBytes;
+        const uint8_t* blo = bhi + kBBytes;
+#pragma unroll
+        for (int k = 0; k < kBK32 / 8; ++k) {
+          const uint64_t dahi = sdesc(ahi + k * 32), dalo = sdesc(alo + k * 32);
+          const uint64_t dbhi = sdesc(bhi + k * 32), dblo = sdesc(blo + k * 32);
+          mma_tf32(d, dahi, dbhi, id, (first && k == 0) ? 0u : 1u);
+          mma_tf32(d, dahi, dblo, id, 1u);
+          mma_tf32(d, dalo, dbhi, id, 1u);
+        }
+        mma_commit(&empty[s]);
+        if (kb % fold == fold - 1 || kb == KB - 1) mma_commit(&kdone[buf]);
+      }
+    }
+  } else if (warp < 6) {
+    // converters: 128 threads, 8 x 16 B of each 16 KiB A tile per thread
+    const int ct = threadIdx.x - 64;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, 8u)) break;
+      uint4* a = reinterpret_cast<uint4*>(sA + s * kA32Bytes);
+      uint4* lo = reinterpret_cast<uint4*>(sAlo + s * kA32Bytes);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int q = ct + 128 * i;
+        uint4 v = a[q];
+        uint4 h = make_uint4(v.x & 0xFFFFE000u, v.y & 0xFFFFE000u, v.z & 0xFFFFE000u, v.w & 0xFFFFE000u);
+        uint4 l;
+        l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+        l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+        l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+        l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+        a[q] = h;
+        lo[q] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+    }
+  } else {
+    // reducers: fold each finished TMEM buffer into FP32 registers, then the epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    float acc[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int g = 0; g < groups && ok; ++g) {
+      const int buf = g & 1;
+      ok = mbar_wait(&kdone[buf], (uint32_t)(g >> 1) & 1u, 4u);
+      __syncwarp();
+      tc_fence_after();
+#pragma unroll
+      for (int j = 0; j < BN / 16; ++j) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + j * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[j * 16 + i] += v[i];
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
+    }
+    const int r = q * 32 + lane;
+    const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
+    if (ok && oy < c.Ho && ox < c.Wo) {
+      float4* dst = reinterpret_cast<float4*>(
+          args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0);
+#pragma unroll
+      for (int i = 0; i < BN / 4; ++i) {
+        const int n = 4 * i;
+        float4 t;
+        t.x = fmaxf(fmaf(acc[n + 0], s_ss[n + 0], s_ss[BN + n + 0]), 0.f);
+        t.y = fmaxf(fmaf(acc[n + 1], s_ss[n + 1], s_ss[BN + n + 1]), 0.f);
+        t.z = fmaxf(fmaf(acc[n + 2], s_ss[n + 2], s_ss[BN + n + 2]), 0.f);
+        t.w = fmaxf(fmaf(acc[n + 3], s_ss[n + 3], s_ss[BN + n + 3]), 0.f);
+        dst[i] = t;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
 // ---------------------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -420,6 +652,117 @@ int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfl
   PP_TC_CASE(256, 3)
 #undef PP_TC_CASE
   return fail(PP_EINVAL, "conv bf16: no kernel for tile %d", tile);
+}
+
+namespace {
+
+struct TileF32TC {
+  int bh, bw, bn, stages;
+};
+// bh*bw must be 128; stage = 32 KiB of A (fp32 + lo) + 2 x BN x 128 B of B (hi, lo).
+constexpr TileF32TC kTilesF32TC[] = {
+    {8, 16, 64, 4}, {4, 32, 64, 4}, {16, 8, 64, 4}, {2, 64, 64, 4}, {1, 128, 64, 4},
+    {8, 16, 128, 3}, {4, 32, 128, 3}, {16, 8, 128, 3},
+};
+
+template <int BN, int STAGES>
+constexpr size_t smem_bytes_f32() {
+  return 1024 + (size_t)STAGES * (2 * kA32Bytes + 2 * BN * kBK32 * 4) + (3 * STAGES + 4) * 8 + 16 +
+         2 * BN * sizeof(float);
+}
+
+template <int BN, int STAGES, bool S2>
+int launch_tf32x3(const CUtensorMap& a, const CUtensorMap& w, const TcArgsF32& args, dim3 grid,
+                  cudaStream_t s) {
+  constexpr size_t bytes = smem_bytes_f32<BN, STAGES>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tf32x3<BN, STAGES, S2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e, "conv tf32x3 smem attribute");
+    attr_set = true;
+  }
+  conv3x3_tf32x3<BN, STAGES, S2><<<grid, 320, bytes, s>>>(a, w, args);
+  return cuda_status(cudaGetLastError(), "conv tf32x3 launch");
+}
+
+int pick_tile_f32(const ConvShape& c) {
+  int best = -1;
+  double best_cost = 1e30;
+  for (int i = 0; i < (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])); ++i) {
+    const TileF32TC& t = kTilesF32TC[i];
+    if (c.cout % t.bn) continue;
+    const double tiles = (double)((c.Ho + t.bh - 1) / t.bh) * ((c.Wo + t.bw - 1) / t.bw);
+    const double cost = tiles * 128.0 * (1.0 + 0.25 * 64.0 / t.bn);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = i; }
+  }
+  return best;
+}
+
+}  // namespace
+
+int conv_f32tc_tile_count() { return (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])); }
+
+int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
+                      float* out, int tile, cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  if (c.cin % kBK32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
+  if (tile < 0) tile = pick_tile_f32(c);
+  if (tile < 0 || tile >= conv_f32tc_tile_count() || c.cout % kTilesF32TC[tile].bn)
+    return fail(PP_EINVAL, "conv f32 tensor: tile %d unsupported for cout %d", tile, c.cout);
+  const TileF32TC t = kTilesF32TC[tile];
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w_split)) & 15u)
+    return fail(PP_EINVAL, "conv f32 tensor: operands must be 16-byte aligned");
+  const int Hp = c.H + 2, Wp = c.W + 2;
+  CUtensorMap ta, tw;
+  CUresult r;
+  if (c.stride == 1) {
+    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 4, (cuuint64_t)Wp * c.cin * 4};
+    cuuint32_t box[3] = {(cuuint32_t)kBK32, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
+    cuuint64_t strides[4] = {(cuuint64_t)c.cin * 4, (cuuint64_t)c.cin * 8,
+                             (cuuint64_t)Wp * c.cin * 4, (cuuint64_t)Wp * c.cin * 8};
+    cuuint32_t box[5] = {(cuuint32_t)kBK32, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv f32 tensor: activation tensor map (%d)", (int)r);
+  {
+    const int K = 9 * c.cin;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)c.cout, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * c.cout * 4};
+    cuuint32_t box[3] = {(cuuint32_t)kBK32, (cuuint32_t)t.bn, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(w_split), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv f32 tensor: weight tensor map (%d)", (int)r);
+  TcArgsF32 args;
+  args.c = c;
+  args.bh = t.bh;
+  args.bw = t.bw;
+  args.tiles_x = (c.Wo + t.bw - 1) / t.bw;
+  args.tiles_y = (c.Ho + t.bh - 1) / t.bh;
+  args.fold = 2;  // K blocks per TMEM accumulation chain (each is 3 x 4 MMAs)
+  args.ss = ss;
+  args.out = out;
+  const dim3 grid((unsigned)(args.tiles_x * args.tiles_y * c.batch), (unsigned)(c.cout / t.bn));
+  const bool s2 = c.stride == 2;
+  if (t.bn == 64 && t.stages == 4)
+    return s2 ? launch_tf32x3<64, 4, true>(ta, tw, args, grid, s) : launch_tf32x3<64, 4, false>(ta, tw, args, grid, s);
+  if (t.bn == 128 && t.stages == 3)
+    return s2 ? launch_tf32x3<128, 3, true>(ta, tw, args, grid, s) : launch_tf32x3<128, 3, false>(ta, tw, args, grid, s);
+  return fail(PP_EINVAL, "conv f32 tensor: no kernel for tile %d", tile);
 }
 
 int tc_error_read(unsigned* code, bool clear) {

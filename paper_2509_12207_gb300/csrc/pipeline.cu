@@ -46,6 +46,7 @@ int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
   int st = check_geometry(&cfg->geom, &g);
   if (st) return st;
   precision = prec;
+  conv_dtype = prec == PP_BF16 ? PP_BF16 : (cfg->fp32_cuda_cores ? PP_F32 : PP_F32_TC);
   layers.clear();
   block_end.clear();
   st = layers_of(cfg, &layers, &block_end, g.ny, g.nx);
@@ -74,10 +75,10 @@ int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
     if ((st = cuda_status(cudaMalloc(&tmp, wbytes), "weights staging"))) return st;
     void* packed = nullptr;
     float* ssd = nullptr;
-    st = dev_alloc(&packed, pp_conv_packed_bytes(L.cin, L.cout, prec));
+    st = dev_alloc(&packed, pp_conv_packed_bytes(L.cin, L.cout, conv_dtype));
     if (!st) st = dev_alloc((void**)&ssd, 2 * L.cout * sizeof(float));
     if (!st) st = cuda_status(cudaMemcpy(tmp, cfg->conv_w[l], wbytes, cudaMemcpyHostToDevice), "upload conv_w");
-    if (!st) st = conv_pack_launch(tmp, L.cin, L.cout, prec, packed, s);
+    if (!st) st = conv_pack_launch(tmp, L.cin, L.cout, conv_dtype, packed, s);
     if (!st) st = cuda_status(cudaStreamSynchronize(s), "pack weights");
     if (!st) st = pp_bn_fold(cfg->conv_bn[l], L.cout, 1e-3f, ss);
     if (!st) st = cuda_status(cudaMemcpy(ssd, ss, 2 * L.cout * sizeof(float), cudaMemcpyHostToDevice), "upload conv_ss");
@@ -194,9 +195,12 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];
     ConvShape c{n, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
-    if (m.precision == PP_F32)
+    if (m.conv_dtype == PP_F32)
       st = conv_f32_launch(c, (const float*)x, (const float*)m.conv_w[l], m.conv_ss[l],
                            (float*)act_[l], -1, s);
+    else if (m.conv_dtype == PP_F32_TC)
+      st = conv_f32tc_launch(c, (const float*)x, (const float*)m.conv_w[l], m.conv_ss[l],
+                             (float*)act_[l], -1, s);
     else
       st = conv_bf16_launch(c, (const __nv_bfloat16*)x, (const __nv_bfloat16*)m.conv_w[l],
                             m.conv_ss[l], (__nv_bfloat16*)act_[l], -1, s);

@@ -17,6 +17,7 @@ struct Model {
   std::vector<LayerSpec> layers;
   std::vector<int> block_end;  // index of the last layer of each block
   int precision;               // PP_F32 / PP_BF16
+  int conv_dtype;              // PP_F32 (CUDA cores), PP_F32_TC (3xTF32) or PP_BF16
   // device weights
   float* pfn_w = nullptr;        // [64][9]
   float* pfn_ss = nullptr;       // [2][64]

@@ -61,6 +61,9 @@ int conv_f32_tile_count();
 int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w_nk,
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s);
 int conv_bf16_tile_count();
+int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
+                      float* out, int tile, cudaStream_t s);
+int conv_f32tc_tile_count();
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
 
 }  // namespace pp

@@ -75,11 +75,14 @@ def test_pipeline_batch_and_graph(prec, small_clouds):
         p.destroy()
 
 
-def test_pipeline_full_size_fp32():
+@pytest.mark.parametrize("cuda_cores", [0, 1])
+def test_pipeline_full_size_fp32(cuda_cores):
+    """The full-size FP32 frame, with the convs on the tensor cores (3xTF32) and on CUDA cores."""
     w = pillar_weights(BACKBONE_FULL, 11)
     cloud = config_points(2, 0)
     ref = O.frame(cloud, GEOM_FULL, BACKBONE_FULL, w)
-    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000)
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000,
+                               fp32_cuda_cores=cuda_cores)
     p = pp.Pipeline(cfg, pp.PP_F32)
     try:
         p.run([torch.from_numpy(cloud).to(DEV)])

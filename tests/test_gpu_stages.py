@@ -201,6 +201,29 @@ def test_conv_f32(shape):
             assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
 
 
+@pytest.mark.parametrize("shape", SHAPES)
+def test_conv_f32_tensor_cores(shape):
+    """FP32 conv on the tensor cores (3xTF32 split) meets the FP32 tolerance on every tile."""
+    B, H, W, cin, cout, s = shape
+    xp, w, bn = _conv_case(B, H, W, cin, cout, s, seed=H * W + cin + 2)
+    x_d = torch.from_numpy(xp).to(DEV)
+    wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_F32_TC)
+    ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
+    refs = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
+    n_tiles = pp.conv_tile_count(pp.PP_F32_TC)
+    assert n_tiles == 8
+    for tile in range(n_tiles):
+        if cout % (64 if tile < 5 else 128):
+            continue
+        out = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32_TC, tile=tile)
+        torch.cuda.synchronize()
+        assert pp.device_error() == 0
+        o = out.cpu().numpy()
+        for b in range(B):
+            assert rel_err(o[b, 1:-1, 1:-1], refs[b]) <= FP32_TOL, (tile, b)
+            assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
+
+
 def _bf16(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
 
