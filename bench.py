@@ -346,7 +346,9 @@ def _run_ours(a, rank, world, dist):
                      "frac": achieved / peak, "traffic": None, "kernel": "conv3x3 (%s), all layers"
                      % {pp.PP_F32: "CUDA-core FP32", pp.PP_F32_TC: "tcgen05 3xTF32", pp.PP_BF16: "tcgen05 BF16"}[conv_dtype],
                      "peak_source": peak_note,
-                     "conv_ms_per_frame": conv_s * 1e3 / n_frames},
+                     "conv_ms_per_frame": conv_s * 1e3 / n_frames,
+                     "layers_us": [round(t * 1e6, 2) for t, _ in layers],
+                     "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
         "stage_ms": {k: v for k, v in stages.items()},
         "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
                     "sched_us_per_decision": st["sched_us_per_decision"], "units": st["units_launched"]},

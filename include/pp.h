@@ -157,6 +157,12 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
                int32_t dtype, const void* in, const void* w, const float* scale_shift,
                void* out, int32_t tile, void* stream);
 int pp_conv_tile_count(int32_t dtype);
+/* Shape of conv tile `tile` of `dtype`: output box bh x bw pixels (bh*bw = 128 on the tensor
+ * cores; CUDA-core tiles report bh = 1, bw = pixels per tile), bn output channels, and whether
+ * the kernel is persistent (one CTA per SM walking the tiles, TMA ring and two TMEM
+ * accumulators carried across tiles; the default for the tensor-core dtypes). */
+int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
+                      int32_t* persistent);
 
 /* Repacks float OIHW weights [cout][cin][3][3] (device) into the layout pp_conv3x3 expects
  * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,

@@ -140,6 +140,8 @@ _SIGS = {
     "pp_conv3x3": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P]),
     "pp_conv_tile_count": (ctypes.c_int, [_I]),
     "pp_conv_packed_bytes": (_SZ, [_I, _I, _I]),
+    "pp_conv_tile_info": (ctypes.c_int, [_I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pp_conv_pack_weights": (ctypes.c_int, [_P, _I, _I, _I, _P, _P]),
     "pp_bn_fold": (ctypes.c_int, [_P, _I, ctypes.c_float, _P]),
     "pp_device_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), _I]),
@@ -336,6 +338,13 @@ def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=N
 
 def conv_tile_count(dtype) -> int:
     return int(lib().pp_conv_tile_count(dtype))
+
+
+def conv_tile_info(dtype, tile):
+    """(bh, bw, bn, persistent) of conv tile ``tile``."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().pp_conv_tile_info(dtype, tile, *[ctypes.byref(x) for x in v]))
+    return tuple(int(x.value) for x in v)
 
 
 def device_error(clear: bool = True) -> int:

@@ -171,6 +171,20 @@ int pp_conv_tile_count(int32_t dtype) {
        : dtype == PP_F32_TC ? conv_f32tc_tile_count() : 0;
 }
 
+int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
+                      int32_t* persistent) {
+  if (!bh || !bw || !bn || !persistent) return fail(PP_EINVAL, "conv_tile_info: NULL argument");
+  if (dtype == PP_F32) {
+    static const int tiles[4][2] = {{128, 64}, {64, 64}, {128, 128}, {64, 128}};
+    if (tile < 0 || tile >= 4) return fail(PP_EINVAL, "conv_tile_info: bad tile");
+    *bh = 1; *bw = tiles[tile][0]; *bn = tiles[tile][1]; *persistent = 0;
+    return PP_OK;
+  }
+  if (conv_tc_tile_info(dtype, tile, bh, bw, bn, persistent) != PP_OK)
+    return fail(PP_EINVAL, "conv_tile_info: bad dtype or tile");
+  return PP_OK;
+}
+
 size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype) {
   if (cin <= 0 || cout <= 0) return 0;
   if (dtype == PP_F32_TC) return (size_t)2 * 9 * cin * cout * 4;

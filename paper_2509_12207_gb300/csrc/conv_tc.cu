@@ -61,19 +61,26 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ unsigned tc_error_now() {
   return *reinterpret_cast<volatile unsigned*>(&g_tc_error);
 }
-// Bounded wait; false on timeout (after recording `code` in the device error word) or as soon
-// as another CTA has recorded an error, so that one failure does not cost a timeout per CTA.
+// Bounded wait; false on timeout (after recording `code` in the device error word) or once
+// another CTA has recorded an error, so that one failure does not cost a timeout per CTA.  The
+// barrier is polled in a tight loop; the clock and the error word (a global load) are looked at
+// only every 256 polls, so a completed phase is seen within one poll.
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned code) {
   if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = now_ns();
-  while (!mbar_try(bar, parity)) {
-    if (tc_error_now() != 0u) return false;
-    if (now_ns() - t0 > kTimeoutNs) {
-      atomicOr(&g_tc_error, code);
-      return false;
+  uint64_t t0 = 0;
+  for (uint32_t n = 1;; ++n) {
+    if (mbar_try(bar, parity)) return true;
+    if ((n & 255u) == 0u) {
+      if (tc_error_now() != 0u) return false;
+      const uint64_t t = now_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kTimeoutNs) {
+        atomicOr(&g_tc_error, code);
+        return false;
+      }
     }
   }
-  return true;
 }
 
 __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* m, uint64_t* bar, int c0,
@@ -151,6 +158,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes into v[0..31]; no wait (see tmem_wait).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 struct TcArgs {
@@ -524,6 +548,309 @@ conv3x3_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// ---------------------------------------------------------------------------- persistent
+//
+// Persistent form of both tensor-core convs: one CTA per SM walks the output tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (N tile innermost, so CTAs sharing an A tile run
+// side by side and the second read hits L2).  The TMA ring, the converters (3xTF32) and the
+// MMA thread run over the concatenated K blocks of all the CTA's tiles without draining, and
+// accumulation goes to two TMEM buffers in turn: while the reducer warps read one buffer (and,
+// at the end of a tile, apply BN + ReLU and store), the MMAs fill the other.  For BF16 a buffer
+// holds a whole tile's accumulation and a ring stage carries KPS = 2 K blocks (8 MMAs per
+// handshake); for 3xTF32 a buffer holds `fold` K blocks, which the reducers add into FP32
+// registers, and each K step is two MMAs: A_hi x [B_hi | B_lo] (N = 2 BN, the two products land
+// side by side in TMEM) and A_lo x B_hi (N = BN, into the first half); the reducers sum the
+// halves.  Loop counters advance incrementally (no division in the steady state) and shared
+// memory descriptors are built once and offset by addition.
+
+struct PArgs {
+  ConvShape c;
+  int bh, bw, tiles_x, tiles_y, tiles_n, total, fold;
+  const float* ss;
+  void* out;
+};
+
+template <int MODE, int BN, int STAGES, int KPS, bool S2>
+__global__ void __launch_bounds__(MODE == 1 ? 320 : 192, 1)
+conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            PArgs args) {
+  constexpr int BK = MODE == 1 ? 32 : 64;                  // channels per K block (128 B rows)
+  constexpr uint32_t kA = 128 * 128;                       // A tile bytes of one K block
+  constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
+  constexpr uint32_t kAK = MODE == 1 ? 2 * kA : kA;        // per K block: A (+ lo)
+  constexpr uint32_t kBK = MODE == 1 ? 2 * kB : kB;        // per K block: B (+ lo plane)
+  constexpr uint32_t kStageA = KPS * kAK;
+  constexpr uint32_t kStageB = KPS * kBK;
+  constexpr int NACC = MODE == 1 ? 2 * BN : BN;            // TMEM columns per accumulator buffer
+  constexpr uint32_t kCols = 2 * NACC;
+  constexpr int kRed0 = MODE == 1 ? 6 : 2;                 // first reducer warp
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ unsigned s_abort;
+  if (threadIdx.x == 0) s_abort = tc_error_now();
+  __syncthreads();
+  if (s_abort != 0u) return;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + STAGES * kStageA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* kdone = empty + STAGES;
+  uint64_t* kfree = kdone + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + 2);
+  float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);  // [cout] folded BN scale
+  float* s_shift = s_scale + args.c.cout;                    // [cout] folded BN shift
+
+  const ConvShape& c = args.c;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kchunks = c.cin / BK;
+  const int KB = 9 * kchunks;
+  const int fold = MODE == 1 ? args.fold : KB;
+  const int Hp2 = (c.H + 2) / 2;
+
+  for (int i = threadIdx.x; i < c.cout; i += blockDim.x) {
+    s_scale[i] = args.ss[i];
+    s_shift[i] = args.ss[c.cout + i];
+  }
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&kdone[i], 1);
+      mbar_init(&kfree[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto decode = [&](int t, int& b, int& oy0, int& ox0, int& n0) {
+    const int nt = t % args.tiles_n;
+    const int r = t / args.tiles_n;
+    const int tx = r % args.tiles_x;
+    const int ty = (r / args.tiles_x) % args.tiles_y;
+    b = r / (args.tiles_x * args.tiles_y);
+    oy0 = ty * args.bh;
+    ox0 = tx * args.bw;
+    n0 = nt * BN;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+        int b, oy0, ox0, n0;
+        decode(t, b, oy0, ox0, n0);
+        int cc = 0, kx = 0, ky = 0, kk = 0;  // channel chunk, tap, K offset of the next K block
+        for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
+          const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
+          if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
+          mbar_expect_tx(&full[s], (uint32_t)nk * (kA + kBK));
+          for (int j = 0; j < nk; ++j) {
+            uint8_t* a = sA + s * kStageA + j * kAK;
+            if (S2)
+              tma_5d(a, &tmA, &full[s], cc * BK, kx & 1, ox0 + (kx >> 1), ky & 1,
+                     b * Hp2 + oy0 + (ky >> 1));
+            else
+              tma_3d(a, &tmA, &full[s], cc * BK, ox0 + kx, b * (c.H + 2) + oy0 + ky);
+            uint8_t* bb = sB + s * kStageB + j * kBK;
+            if (MODE == 1) {
+              tma_3d(bb, &tmB, &full[s], kk, n0, 0);
+              tma_3d(bb + kB, &tmB, &full[s], kk, n0, 1);
+            } else {
+              tma_2d(bb, &tmB, &full[s], kk, n0);
+            }
+            kk += BK;
+            if (++cc == kchunks) {
+              cc = 0;
+              if (++kx == 3) { kx = 0; ++ky; }
+            }
+          }
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = MODE == 1 ? idesc_tf32<2 * BN>() : idesc<BN>();
+      const uint32_t id2 = idesc_tf32<BN>();
+      const uint64_t dA0 = sdesc(sA), dB0 = sdesc(sB);
+      int s = 0, gg = 0, inq = 0;  // inq: K blocks already in the current group
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+        for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
+          const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
+          const int buf = gg & 1;
+          if (inq == 0 && gg >= 2 && !mbar_wait(&kfree[buf], (uint32_t)((gg >> 1) - 1) & 1u, 16u)) { ok = false; break; }
+          if (!mbar_wait(MODE == 1 ? &conv[s] : &full[s], ph, 2u)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * NACC);
+          const uint64_t da = dA0 + ((uint64_t)(s * kStageA) >> 4);
+          const uint64_t db = dB0 + ((uint64_t)(s * kStageB) >> 4);
+#pragma unroll
+          for (int j = 0; j < KPS; ++j) {
+            if (j < nk) {
+              const bool fresh = inq == 0 && j == 0;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const uint64_t a_k = da + (uint64_t)((j * kAK + k * 32) >> 4);
+                const uint64_t b_k = db + (uint64_t)((j * kBK + k * 32) >> 4);
+                if (MODE == 1) {
+                  mma_tf32(d, a_k, b_k, id, (fresh && k == 0) ? 0u : 1u);           // A_hi x [B_hi|B_lo]
+                  mma_tf32(d, a_k + (kA >> 4), b_k, id2, 1u);                      // A_lo x B_hi
+                } else {
+                  mma_bf16(d, a_k, b_k, id, (fresh && k == 0) ? 0u : 1u);
+                }
+              }
+            }
+          }
+          mma_commit(&empty[s]);
+          inq += nk;
+          if (inq >= fold || kb0 + nk == KB) {
+            mma_commit(&kdone[buf]);
+            ++gg;
+            inq = 0;
+          }
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+    }
+  } else if (MODE == 1 && warp < kRed0) {
+    const int ct = threadIdx.x - 64;
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+      for (int kb = 0; kb < KB; ++kb) {
+        if (!mbar_wait(&full[s], ph, 8u)) { ok = false; break; }
+        uint4* a = reinterpret_cast<uint4*>(sA + s * kStageA);
+        uint4* lo = reinterpret_cast<uint4*>(sA + s * kStageA + kA);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int q = ct + 128 * i;
+          uint4 v = a[q];
+          uint4 h = make_uint4(v.x & 0xFFFFE000u, v.y & 0xFFFFE000u, v.z & 0xFFFFE000u, v.w & 0xFFFFE000u);
+          uint4 l;
+          l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+          l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+          l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+          l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+          a[q] = h;
+          lo[q] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+        if (++s == STAGES) { s = 0; ph ^= 1u; }
+      }
+    }
+  } else if (warp >= kRed0) {
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    const int r = q * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    const int gpt = (KB + fold - 1) / fold;  // accumulation groups per tile
+    int gg = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+      int b, oy0, ox0, n0;
+      decode(t, b, oy0, ox0, n0);
+      const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
+      const bool in_range = oy < c.Ho && ox < c.Wo;
+      const size_t pix = ((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1;
+      if (MODE == 1) {
+        float acc[BN];
+#pragma unroll
+        for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+        for (int g = 0; g < gpt; ++g, ++gg) {
+          const int buf = gg & 1;
+          ok = mbar_wait(&kdone[buf], (uint32_t)(gg >> 1) & 1u, 4u);
+          __syncwarp();
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int j = 0; j < BN / 32; ++j) {
+            uint32_t v[32], w[32];
+            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 32), v);
+            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + BN + j * 32), w);
+            tmem_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[j * 32 + i] += __uint_as_float(v[i]) + __uint_as_float(w[i]);
+          }
+          tc_fence_before();
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
+        }
+        if (ok && in_range) {
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(args.out) + pix * c.cout + n0);
+#pragma unroll
+          for (int i = 0; i < BN / 4; ++i) {
+            const int n = n0 + 4 * i;
+            float4 u;
+            u.x = fmaxf(fmaf(acc[4 * i + 0], s_scale[n + 0], s_shift[n + 0]), 0.f);
+            u.y = fmaxf(fmaf(acc[4 * i + 1], s_scale[n + 1], s_shift[n + 1]), 0.f);
+            u.z = fmaxf(fmaf(acc[4 * i + 2], s_scale[n + 2], s_shift[n + 2]), 0.f);
+            u.w = fmaxf(fmaf(acc[4 * i + 3], s_scale[n + 3], s_shift[n + 3]), 0.f);
+            dst[i] = u;
+          }
+        }
+      } else {
+        const int buf = gg & 1;
+        ok = mbar_wait(&kdone[buf], (uint32_t)(gg >> 1) & 1u, 4u);
+        __syncwarp();
+        if (!ok) break;
+        tc_fence_after();
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(args.out) + pix * c.cout + n0;
+#pragma unroll 1
+        for (int j = 0; j < BN / 64; ++j) {
+          uint32_t v[64];
+          tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 64), v);
+          tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 64 + 32), v + 32);
+          tmem_wait();
+          if (in_range) {
+            uint32_t pk[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int n = n0 + j * 64 + 2 * i;
+              const float a0 = fmaxf(fmaf(__uint_as_float(v[2 * i]), s_scale[n], s_shift[n]), 0.f);
+              const float a1 = fmaxf(fmaf(__uint_as_float(v[2 * i + 1]), s_scale[n + 1], s_shift[n + 1]), 0.f);
+              __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+              pk[i] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(o + j * 64);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+          }
+        }
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
+        ++gg;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
 // ---------------------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -571,29 +898,21 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
   return cuda_status(cudaGetLastError(), "conv tc launch");
 }
 
-int pick_tile(const ConvShape& c) {
-  // least padded work, then the wider N tile (fewer A re-reads), then fewer CTAs
-  int best = -1;
-  double best_cost = 1e30;
-  for (int i = 0; i < (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])); ++i) {
-    const TileTC& t = kTilesTC[i];
-    if (c.cout % t.bn || t.stages != (t.bn == 256 ? 3 : 4)) continue;
-    const double tiles = (double)((c.Ho + t.bh - 1) / t.bh) * ((c.Wo + t.bw - 1) / t.bw);
-    const double cost = tiles * 128.0 * (1.0 + 0.25 * 64.0 / t.bn);
-    if (cost < best_cost - 1e-9) { best_cost = cost; best = i; }
-  }
-  return best;
-}
+
 
 }  // namespace
 
-int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])); }
+int conv_tcp_tile_count(int mode);
+int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
+                    void* out, int ptile, cudaStream_t s);
+int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0); }
 
 int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w,
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
-  if (tile < 0) tile = pick_tile(c);
+  const int n_old = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
+  if (tile < 0 || tile >= n_old) return conv_tcp_launch(0, c, in, w, ss, out, tile < 0 ? -1 : tile - n_old, s);
   if (tile < 0 || tile >= conv_bf16_tile_count() || c.cout % kTilesTC[tile].bn)
     return fail(PP_EINVAL, "conv bf16: tile %d unsupported for cout %d", tile, c.cout);
   const TileTC t = kTilesTC[tile];
@@ -686,29 +1005,19 @@ int launch_tf32x3(const CUtensorMap& a, const CUtensorMap& w, const TcArgsF32& a
   return cuda_status(cudaGetLastError(), "conv tf32x3 launch");
 }
 
-int pick_tile_f32(const ConvShape& c) {
-  int best = -1;
-  double best_cost = 1e30;
-  for (int i = 0; i < (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])); ++i) {
-    const TileF32TC& t = kTilesF32TC[i];
-    if (c.cout % t.bn) continue;
-    const double tiles = (double)((c.Ho + t.bh - 1) / t.bh) * ((c.Wo + t.bw - 1) / t.bw);
-    const double cost = tiles * 128.0 * (1.0 + 0.25 * 64.0 / t.bn);
-    if (cost < best_cost - 1e-9) { best_cost = cost; best = i; }
-  }
-  return best;
-}
+
 
 }  // namespace
 
-int conv_f32tc_tile_count() { return (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])); }
+int conv_f32tc_tile_count() { return (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])) + conv_tcp_tile_count(1); }
 
 int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
                       float* out, int tile, cudaStream_t s) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
   if (c.cin % kBK32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
-  if (tile < 0) tile = pick_tile_f32(c);
+  const int n_old = (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0]));
+  if (tile < 0 || tile >= n_old) return conv_tcp_launch(1, c, in, w_split, ss, out, tile < 0 ? -1 : tile - n_old, s);
   if (tile < 0 || tile >= conv_f32tc_tile_count() || c.cout % kTilesF32TC[tile].bn)
     return fail(PP_EINVAL, "conv f32 tensor: tile %d unsupported for cout %d", tile, c.cout);
   const TileF32TC t = kTilesF32TC[tile];
@@ -763,6 +1072,175 @@ int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split,
   if (t.bn == 128 && t.stages == 3)
     return s2 ? launch_tf32x3<128, 3, true>(ta, tw, args, grid, s) : launch_tf32x3<128, 3, false>(ta, tw, args, grid, s);
   return fail(PP_EINVAL, "conv f32 tensor: no kernel for tile %d", tile);
+}
+
+namespace {
+
+struct TileP {
+  int bh, bw, bn;
+};
+// Persistent tiles (bh*bw = 128).  Stages fill ~192 KiB of shared memory: BF16 stage = 16 KiB A
+// + BN x 128 B; 3xTF32 stage = 32 KiB A (+lo) + 2 x BN x 128 B.
+constexpr TileP kTilesPB[] = {{8, 16, 64}, {4, 32, 64}, {16, 8, 64}, {2, 64, 64}, {8, 16, 128},
+                              {4, 32, 128}, {16, 8, 128}, {8, 16, 256}, {4, 32, 256}};
+constexpr TileP kTilesPF[] = {{8, 16, 64}, {4, 32, 64}, {16, 8, 64}, {2, 64, 64}, {8, 16, 128},
+                              {4, 32, 128}, {16, 8, 128}};
+constexpr int kNPB = (int)(sizeof(kTilesPB) / sizeof(kTilesPB[0]));
+constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
+
+// Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
+// stage = 32 KiB A (+lo) + 2 x BN x 128 B.  Both fill ~192 KiB of shared memory.
+template <int MODE, int BN>
+constexpr int p_kps() {
+  return MODE == 1 ? 1 : 2;
+}
+template <int MODE, int BN>
+constexpr int p_stages() {
+  return MODE == 1 ? (BN == 64 ? 4 : 3) : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+}
+template <int MODE, int BN>
+constexpr size_t p_smem() {
+  return 1024 + (size_t)p_stages<MODE, BN>() * p_kps<MODE, BN>() *
+                    ((MODE == 1 ? 2 : 1) * 16384 + (MODE == 1 ? 2 : 1) * BN * 128) +
+         (3 * p_stages<MODE, BN>() + 4) * 8 + 16;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+template <int MODE, int BN, bool S2>
+int launch_p(const CUtensorMap& a, const CUtensorMap& w, const PArgs& args, cudaStream_t s) {
+  constexpr int ST = p_stages<MODE, BN>();
+  constexpr int KPS = p_kps<MODE, BN>();
+  constexpr size_t bytes = p_smem<MODE, BN>() + 2 * 1024 * sizeof(float);  // + folded BN (cout <= 1024)
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e, "persistent conv smem attribute");
+    attr_set = true;
+  }
+  const int grid = args.total < num_sms() ? args.total : num_sms();
+  conv3x3_tcp<MODE, BN, ST, KPS, S2><<<grid, MODE == 1 ? 320 : 192, bytes, s>>>(a, w, args);
+  return cuda_status(cudaGetLastError(), "persistent conv launch");
+}
+
+// Persistent tile choice: fewest "waves" of tile work over the SMs, each tile costing its MMA
+// time plus a fixed per-tile overhead.
+int pick_tile_p(const ConvShape& c, const TileP* tiles, int n) {
+  int best = -1;
+  double best_cost = 1e30;
+  for (int i = 0; i < n; ++i) {
+    const TileP& t = tiles[i];
+    if (c.cout % t.bn) continue;
+    const double tx = (c.Wo + t.bw - 1) / t.bw, ty = (c.Ho + t.bh - 1) / t.bh;
+    const double total = tx * ty * c.batch * (c.cout / t.bn);
+    const double per_sm = ceil(total / num_sms());
+    const double cost = per_sm * (t.bn + 48.0);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = i; }
+  }
+  return best;
+}
+
+}  // namespace
+
+// mode 0: BF16 in/out, weights [cout][9cin] bf16; mode 1: FP32 in/out via 3xTF32, weights
+// [2][cout][9cin] fp32 (hi, lo planes).
+int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
+                    void* out, int ptile, cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
+  const int n = mode == 1 ? kNPF : kNPB;
+  if (ptile < 0) ptile = pick_tile_p(c, tiles, n);
+  if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn)
+    return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
+  const TileP t = tiles[ptile];
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
+    return fail(PP_EINVAL, "persistent conv: operands must be 16-byte aligned");
+  const int BK = mode == 1 ? 32 : 64;
+  const size_t el = mode == 1 ? 4 : 2;
+  const CUtensorMapDataType dt = mode == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const int Hp = c.H + 2, Wp = c.W + 2;
+  CUtensorMap ta, tw;
+  CUresult r;
+  if (c.stride == 1) {
+    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
+    cuuint64_t strides[2] = {(cuuint64_t)c.cin * el, (cuuint64_t)Wp * c.cin * el};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&ta, dt, 3, const_cast<void*>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
+    cuuint64_t strides[4] = {(cuuint64_t)c.cin * el, (cuuint64_t)c.cin * 2 * el,
+                             (cuuint64_t)Wp * c.cin * el, (cuuint64_t)Wp * c.cin * 2 * el};
+    cuuint32_t box[5] = {(cuuint32_t)BK, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    r = enc(&ta, dt, 5, const_cast<void*>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: activation tensor map (%d)", (int)r);
+  {
+    const int K = 9 * c.cin;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)c.cout, (cuuint64_t)(mode == 1 ? 2 : 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)K * el, (cuuint64_t)K * c.cout * el};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bn, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&tw, dt, mode == 1 ? 3 : 2, const_cast<void*>(w), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: weight tensor map (%d)", (int)r);
+  PArgs args;
+  args.c = c;
+  args.bh = t.bh;
+  args.bw = t.bw;
+  args.tiles_x = (c.Wo + t.bw - 1) / t.bw;
+  args.tiles_y = (c.Ho + t.bh - 1) / t.bh;
+  args.tiles_n = c.cout / t.bn;
+  args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
+  args.fold = 2;
+  args.ss = ss;
+  args.out = out;
+  const bool s2 = c.stride == 2;
+  if (mode == 1) {
+    if (t.bn == 64) return s2 ? launch_p<1, 64, true>(ta, tw, args, s) : launch_p<1, 64, false>(ta, tw, args, s);
+    if (t.bn == 128) return s2 ? launch_p<1, 128, true>(ta, tw, args, s) : launch_p<1, 128, false>(ta, tw, args, s);
+  } else {
+    if (t.bn == 64) return s2 ? launch_p<0, 64, true>(ta, tw, args, s) : launch_p<0, 64, false>(ta, tw, args, s);
+    if (t.bn == 128) return s2 ? launch_p<0, 128, true>(ta, tw, args, s) : launch_p<0, 128, false>(ta, tw, args, s);
+    if (t.bn == 256) return s2 ? launch_p<0, 256, true>(ta, tw, args, s) : launch_p<0, 256, false>(ta, tw, args, s);
+  }
+  return fail(PP_EINVAL, "persistent conv: no kernel for tile %d", ptile);
+}
+
+int conv_tcp_tile_count(int mode) { return mode == 1 ? kNPF : kNPB; }
+
+int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent) {
+  if (dtype == PP_BF16) {
+    const int n0 = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
+    if (tile < 0 || tile >= n0 + kNPB) return PP_EINVAL;
+    if (tile < n0) { *bh = kTilesTC[tile].bh; *bw = kTilesTC[tile].bw; *bn = kTilesTC[tile].bn; *persistent = 0; }
+    else { const TileP& t = kTilesPB[tile - n0]; *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1; }
+    return PP_OK;
+  }
+  if (dtype == PP_F32_TC) {
+    const int n0 = (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0]));
+    if (tile < 0 || tile >= n0 + kNPF) return PP_EINVAL;
+    if (tile < n0) { *bh = kTilesF32TC[tile].bh; *bw = kTilesF32TC[tile].bw; *bn = kTilesF32TC[tile].bn; *persistent = 0; }
+    else { const TileP& t = kTilesPF[tile - n0]; *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1; }
+    return PP_OK;
+  }
+  return PP_EINVAL;
 }
 
 int tc_error_read(unsigned* code, bool clear) {

@@ -64,6 +64,7 @@ int conv_bf16_tile_count();
 int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
                       float* out, int tile, cudaStream_t s);
 int conv_f32tc_tile_count();
+int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent);
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
 
 }  // namespace pp
