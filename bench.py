@@ -179,9 +179,10 @@ class _Clocks:
 
 # ------------------------------------------------------------------ measurements
 
-def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=10):
-    """Average duration of each conv layer's kernel, launched through pp_conv3x3 on the current
-    stream and timed with CUDA events around `reps` launches of it."""
+def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=20, tile=-1):
+    """Average duration of each conv layer's kernel: `reps` launches through pp_conv3x3 are
+    captured into a CUDA graph (tensor maps encoded once, at capture), and one replay of that
+    graph is timed with CUDA events on the replay stream, so host launch cost is not counted."""
     dt = torch.bfloat16 if prec == pp.PP_BF16 else torch.float32
     H, W = g.ny, g.nx
     x = torch.rand((batch, H + 2, W + 2, 64), device="cuda").to(dt)
@@ -193,12 +194,17 @@ def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=10):
         ss = torch.from_numpy(pp.bn_fold(bn)).cuda()
         Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
         out = torch.zeros((batch, Ho + 2, Wo + 2, co), dtype=dt, device="cuda")
-        pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile)
         torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
-            pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out)
+        graph.replay()
         e1.record(stream)
         torch.cuda.synchronize()
         flops = 2.0 * batch * Ho * Wo * co * 9 * ci

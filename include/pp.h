@@ -159,8 +159,11 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
 int pp_conv_tile_count(int32_t dtype);
 /* Shape of conv tile `tile` of `dtype`: output box bh x bw pixels (bh*bw = 128 on the tensor
  * cores; CUDA-core tiles report bh = 1, bw = pixels per tile), bn output channels, and whether
- * the kernel is persistent (one CTA per SM walking the tiles, TMA ring and two TMEM
- * accumulators carried across tiles; the default for the tensor-core dtypes). */
+ * the kernel is persistent: 1 = one CTA per SM walking the tiles, TMA ring and two TMEM
+ * accumulators carried across tiles (the default for the tensor-core dtypes); 2 = the BF16
+ * row-streaming kernel for 64 -> 64 channel layers (the default there: weights resident in
+ * shared memory, each input row loaded once and every tap read as a row-shifted view; tile
+ * reports the 128-pixel output row segment). */
 int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
                       int32_t* persistent);
 

@@ -746,14 +746,14 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int q = ct + 128 * i;
-          uint4 v = a[q];
-          uint4 h = make_uint4(v.x & 0xFFFFE000u, v.y & 0xFFFFE000u, v.z & 0xFFFFE000u, v.w & 0xFFFFE000u);
+          // the tensor core reads a TF32 operand from an FP32 word by dropping its 13 low
+          // mantissa bits, so the untouched tile already is A_hi; only the remainder is written
+          const uint4 v = a[q];
           uint4 l;
-          l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
-          l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
-          l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
-          l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
-          a[q] = h;
+          l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(v.x & 0xFFFFE000u));
+          l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(v.y & 0xFFFFE000u));
+          l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(v.z & 0xFFFFE000u));
+          l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(v.w & 0xFFFFE000u));
           lo[q] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -851,6 +851,228 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
 }
 
+// ---------------------------------------------------------------------------- row streaming
+//
+// BF16 conv for 64 input and 64 output channels that moves each input row into shared memory
+// once.  A tensor-core A operand in the 128-byte-swizzled K-major layout may start at any
+// 128-byte row of a swizzled buffer (the swizzle follows the absolute address), so the nine
+// taps of an output row are nine row-shifted views of three resident input rows.  A CTA owns a
+// strip of output rows (frame, up to 126 (stride 1) or 127 (stride 2) output columns, a run of
+// rows): all 9 weight taps (72 KiB) stay resident, input rows stream through an 8-slot ring of
+// 128-pixel rows (stride 2 keeps the even and odd input columns as two planes, so a tap is
+// plane kx & 1 shifted by kx >> 1), and each output row is 9 taps x 4 MMAs (M = 128 output
+// pixels, N = 64, K = 16) into one of two TMEM buffers while the epilogue warps drain the
+// other.  Per output row the ring takes one new input row (two at stride 2) instead of nine
+// 16 KiB A tiles and nine weight tiles.
+
+struct RArgs {
+  ConvShape c;
+  int pv, nseg, rc, nchunks, units;  // valid outputs per segment, segments, rows per chunk
+  const float* ss;
+  __nv_bfloat16* out;
+};
+
+template <bool S2>
+__global__ void __launch_bounds__(192, 1)
+conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             RArgs args) {
+  constexpr int NS = 8;                 // ring slots of one 128-pixel x 64-channel row plane
+  constexpr uint32_t kRow = 128 * 128;  // 16 KiB
+  constexpr uint32_t kTap = 64 * 128;   // one tap of the 64 x 64 weights, 8 KiB
+  constexpr int kPlanes = S2 ? 2 : 1;   // ring slots per input row
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ unsigned s_abort;
+  if (threadIdx.x == 0) s_abort = tc_error_now();
+  __syncthreads();
+  if (s_abort != 0u) return;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sW = smem;                    // [9][64 rows][128 B]
+  uint8_t* sR = sW + 9 * kTap;           // [NS][128 rows][128 B]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sR + NS * kRow);
+  uint64_t* empty = full + NS;
+  uint64_t* wbar = empty + NS;
+  uint64_t* kdone = wbar + 1;
+  uint64_t* kfree = kdone + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + 2);
+  float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);
+  float* s_shift = s_scale + 64;
+
+  const ConvShape& c = args.c;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < 64) {
+    s_scale[threadIdx.x] = args.ss[threadIdx.x];
+    s_shift[threadIdx.x] = args.ss[64 + threadIdx.x];
+  }
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(wbar, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&kdone[i], 1);
+      mbar_init(&kfree[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(128u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int Hp = c.H + 2, Hp2 = Hp / 2;
+
+  auto decode = [&](int u, int& b, int& ox0, int& r0, int& r1) {
+    const int ch = u % args.nchunks;
+    const int r = u / args.nchunks;
+    const int seg = r % args.nseg;
+    b = r / args.nseg;
+    ox0 = seg * args.pv;
+    r0 = ch * args.rc;
+    r1 = r0 + args.rc < c.Ho ? r0 + args.rc : c.Ho;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(wbar, 9 * kTap);
+      for (int t = 0; t < 9; ++t) tma_2d(sW + t * kTap, &tmB, wbar, t * 64, 0);
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+        int b, ox0, r0, r1;
+        decode(u, b, ox0, r0, r1);
+        const int in0 = r0 * (S2 ? 2 : 1);
+        const int nin = S2 ? 2 * (r1 - r0) + 1 : (r1 - r0) + 2;
+        for (int i = 0; i < nin && ok; ++i) {
+          const int ir = in0 + i;  // padded input row
+          for (int p = 0; p < kPlanes; ++p) {
+            if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
+            mbar_expect_tx(&full[s], kRow);
+            if (S2)
+              tma_5d(sR + s * kRow, &tmA, &full[s], 0, p, ox0, ir & 1, b * Hp2 + (ir >> 1));
+            else
+              tma_3d(sR + s * kRow, &tmA, &full[s], 0, ox0, b * Hp + ir);
+            if (++s == NS) { s = 0; ph ^= 1u; }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc<64>();
+      const uint64_t dW = sdesc(sW), dR = sdesc(sR);
+      bool ok = mbar_wait(wbar, 0u, 2u);
+      int fw = 0, fr = 0;  // ring fills waited / released so far (fill order)
+      int gg = 0;
+      for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+        int b, ox0, r0, r1;
+        decode(u, b, ox0, r0, r1);
+        const int base = fw;  // fill index of this unit's first row plane
+        for (int oy = r0; oy < r1 && ok; ++oy) {
+          const int li = oy - r0;
+          // planes this output row needs: rows li..li+2 (stride 1) or 2li..2li+2 (stride 2)
+          const int last = S2 ? (2 * li + 2) * 2 + 1 : li + 2;
+          while (ok && fw <= base + last) {
+            ok = mbar_wait(&full[fw % NS], (uint32_t)(fw / NS) & 1u, 2u);
+            ++fw;
+          }
+          const int buf = gg & 1;
+          if (ok && gg >= 2) ok = mbar_wait(&kfree[buf], (uint32_t)((gg >> 1) - 1) & 1u, 16u);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * 64);
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+              const int plane = S2 ? base + (2 * li + ky) * 2 + (kx & 1) : base + li + ky;
+              const int shift = S2 ? (kx >> 1) : kx;
+              const uint64_t a0 = dR + (uint64_t)(((plane % NS) * kRow + shift * 128) >> 4);
+              const uint64_t b0 = dW + (uint64_t)(((ky * 3 + kx) * kTap) >> 4);
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_bf16(d, a0 + (uint64_t)(k * 2), b0 + (uint64_t)(k * 2), id,
+                         (ky | kx | k) != 0 ? 1u : 0u);
+            }
+            // an input row's planes go back to the ring right after the last tap that reads
+            // them (the commit fires once those MMAs are done): stride 1 frees row li after
+            // ky = 0, stride 2 frees rows 2li and 2li+1 after ky = 0 and ky = 1
+            const int upto = S2 ? (ky < 2 ? base + (2 * li + ky + 1) * 2 : fr)
+                                : (ky == 0 ? base + li + 1 : fr);
+            while (fr < upto) {
+              mma_commit(&empty[fr % NS]);
+              ++fr;
+            }
+          }
+          mma_commit(&kdone[buf]);
+          ++gg;
+          if (oy + 1 == r1) {  // end of the strip: the remaining rows are not needed any more
+            while (fr < fw) {
+              mma_commit(&empty[fr % NS]);
+              ++fr;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    int gg = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+      int b, ox0, r0, r1;
+      decode(u, b, ox0, r0, r1);
+      const int ox = ox0 + r;
+      const bool col_ok = r < args.pv && ox < c.Wo;
+      for (int oy = r0; oy < r1; ++oy, ++gg) {
+        const int buf = gg & 1;
+        ok = mbar_wait(&kdone[buf], (uint32_t)(gg >> 1) & 1u, 4u);
+        __syncwarp();
+        if (!ok) break;
+        tc_fence_after();
+        uint32_t v[64];
+        tmem_ld32_nowait(trow + (uint32_t)(buf * 64), v);
+        tmem_ld32_nowait(trow + (uint32_t)(buf * 64 + 32), v + 32);
+        tmem_wait();
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
+        if (col_ok) {
+          uint32_t pk[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float a0 = fmaxf(fmaf(__uint_as_float(v[2 * i]), s_scale[2 * i], s_shift[2 * i]), 0.f);
+            const float a1 = fmaxf(fmaf(__uint_as_float(v[2 * i + 1]), s_scale[2 * i + 1], s_shift[2 * i + 1]), 0.f);
+            __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+            pk[i] = *reinterpret_cast<uint32_t*>(&h);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(
+              args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * 64);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+  }
+}
+
 // ---------------------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -905,13 +1127,18 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
 int conv_tcp_tile_count(int mode);
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
                     void* out, int ptile, cudaStream_t s);
-int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0); }
+int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
+                     cudaStream_t s);
+int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0) + 1; }
 
 int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w,
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
   const int n_old = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
+  const int n_p = conv_tcp_tile_count(0);
+  if ((tile < 0 && c.cin == 64 && c.cout == 64) || tile == n_old + n_p)
+    return conv_rows_launch(c, in, w, ss, out, s);
   if (tile < 0 || tile >= n_old) return conv_tcp_launch(0, c, in, w, ss, out, tile < 0 ? -1 : tile - n_old, s);
   if (tile < 0 || tile >= conv_bf16_tile_count() || c.cout % kTilesTC[tile].bn)
     return fail(PP_EINVAL, "conv bf16: tile %d unsupported for cout %d", tile, c.cout);
@@ -1223,12 +1450,88 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   return fail(PP_EINVAL, "persistent conv: no kernel for tile %d", ptile);
 }
 
+// Row-streaming BF16 conv (64 -> 64 channels).
+int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
+                     cudaStream_t s) {
+  auto enc = encode_fn();
+  if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  if (c.cin != 64 || c.cout != 64) return fail(PP_EINVAL, "row conv: needs 64 input and 64 output channels");
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
+    return fail(PP_EINVAL, "row conv: operands must be 16-byte aligned");
+  const int Hp = c.H + 2, Wp = c.W + 2;
+  CUtensorMap ta, tw;
+  CUresult r;
+  if (c.stride == 1) {
+    cuuint64_t dims[3] = {64, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
+    cuuint64_t strides[2] = {128, (cuuint64_t)Wp * 128};
+    cuuint32_t box[3] = {64, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[5] = {64, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
+    cuuint64_t strides[4] = {128, 256, (cuuint64_t)Wp * 128, (cuuint64_t)Wp * 256};
+    cuuint32_t box[5] = {64, 1, 128, 1, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "row conv: activation tensor map (%d)", (int)r);
+  {
+    cuuint64_t dims[2] = {9 * 64, 64};
+    cuuint64_t strides[1] = {9 * 64 * 2};
+    cuuint32_t box[2] = {64, 64};
+    cuuint32_t es[2] = {1, 1};
+    r = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(w), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "row conv: weight tensor map (%d)", (int)r);
+  RArgs a;
+  a.c = c;
+  a.pv = c.stride == 2 ? 127 : 126;
+  a.nseg = (c.Wo + a.pv - 1) / a.pv;
+  const int sms = num_sms();
+  const long rows = (long)c.batch * a.nseg * c.Ho;
+  int rc = (int)((rows + 2L * sms - 1) / (2L * sms));
+  if (rc < 4) rc = 4;
+  if (rc > c.Ho) rc = c.Ho;
+  a.rc = rc;
+  a.nchunks = (c.Ho + rc - 1) / rc;
+  a.units = c.batch * a.nseg * a.nchunks;
+  a.ss = ss;
+  a.out = static_cast<__nv_bfloat16*>(out);
+  constexpr size_t bytes = 1024 + 9 * 64 * 128 + 8 * 128 * 128 + (2 * 8 + 5) * 8 + 16 + 2 * 64 * 4;
+  const int grid = a.units < sms ? a.units : sms;
+  if (c.stride == 2) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(conv3x3_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
+      attr = true;
+    }
+    conv3x3_rows<true><<<grid, 192, bytes, s>>>(ta, tw, a);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(conv3x3_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
+      attr = true;
+    }
+    conv3x3_rows<false><<<grid, 192, bytes, s>>>(ta, tw, a);
+  }
+  return cuda_status(cudaGetLastError(), "row conv launch");
+}
+
 int conv_tcp_tile_count(int mode) { return mode == 1 ? kNPF : kNPB; }
 
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent) {
   if (dtype == PP_BF16) {
     const int n0 = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
-    if (tile < 0 || tile >= n0 + kNPB) return PP_EINVAL;
+    if (tile < 0 || tile > n0 + kNPB) return PP_EINVAL;
+    if (tile == n0 + kNPB) { *bh = 1; *bw = 128; *bn = 64; *persistent = 2; return PP_OK; }  // row streaming
     if (tile < n0) { *bh = kTilesTC[tile].bh; *bw = kTilesTC[tile].bw; *bn = kTilesTC[tile].bn; *persistent = 0; }
     else { const TileP& t = kTilesPB[tile - n0]; *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1; }
     return PP_OK;
