@@ -167,6 +167,25 @@ int pp_conv_tile_count(int32_t dtype);
 int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
                       int32_t* persistent);
 
+/* Conv tile autotuner (this library's; the tile choice of the layers is not from the paper).
+ * Runs every tile of `dtype` that supports the shape on the given buffers (same meaning as
+ * pp_conv3x3; `out` holds a valid result afterwards), timing `reps` launches of each by one
+ * replay of a captured CUDA graph, and records the fastest for this (dtype, shape): from then
+ * on tile = -1 in pp_conv3x3 and in release units means that tile.  Synchronous (uses and
+ * destroys a private stream).  *best_us (may be NULL) = device time per launch. */
+int pp_conv_autotune(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                     int32_t stride, int32_t dtype, const void* in, const void* w,
+                     const float* scale_shift, void* out, int32_t reps, int32_t* best_tile,
+                     float* best_us);
+/* Writes the autotuned table as text ("dtype batch H W cin cout stride tile us" per line). */
+int pp_conv_tune_save(const char* path);
+/* Reads a table written by pp_conv_tune_save (host only, no GPU needed); returns the number of
+ * entries loaded (>= 0) or a negative pp_status.  Lines naming a tile that does not exist are
+ * skipped. */
+int pp_conv_tune_load(const char* path);
+/* Forgets every autotuned entry. */
+void pp_conv_tune_clear(void);
+
 /* Repacks float OIHW weights [cout][cin][3][3] (device) into the layout pp_conv3x3 expects
  * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,
  * PP_BF16 -> [cout][9*cin] bf16 (round to nearest even), PP_F32_TC -> [2][cout][9*cin] float
@@ -241,6 +260,8 @@ typedef struct {
                                 /* library caps it at 128                                      */
   int32_t fp32_cuda_cores;      /* FP32 convs on CUDA cores (1) or on the tensor cores with the */
                                 /* 3xTF32 split (0, default)                                   */
+  int32_t autotune;             /* autotune every conv layer for each unit size at creation     */
+                                /* (pp_conv_autotune; default 1)                               */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,

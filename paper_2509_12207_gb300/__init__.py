@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("th_calib_frames", ctypes.c_int32), ("util_exempt", ctypes.c_double),
         ("early_exit", ctypes.c_int32), ("num_streams", ctypes.c_int32),
         ("max_admitted", ctypes.c_int32), ("fp32_cuda_cores", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -144,6 +145,11 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pp_conv_pack_weights": (ctypes.c_int, [_P, _I, _I, _I, _P, _P]),
     "pp_bn_fold": (ctypes.c_int, [_P, _I, ctypes.c_float, _P]),
+    "pp_conv_autotune": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+    "pp_conv_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "pp_conv_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "pp_conv_tune_clear": (None, []),
     "pp_device_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), _I]),
     "pp_config_defaults": (None, [ctypes.POINTER(Config)]),
     "pp_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
@@ -334,6 +340,30 @@ def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=N
     _check(lib().pp_conv3x3(B, H, W, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
                             _ptr(out), tile, _stream(stream)))
     return out
+
+
+def conv_autotune(x, w_packed, scale_shift, cout, stride, dtype, out, reps=5):
+    """pp_conv_autotune on the layer shape of ``x`` (padded NHWC) -> (best tile, us per launch)."""
+    B, Hp, Wp, cin = (int(v) for v in x.shape)
+    t, us = ctypes.c_int32(-1), ctypes.c_float(0)
+    _check(lib().pp_conv_autotune(B, Hp - 2, Wp - 2, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed),
+                                  _ptr(scale_shift), _ptr(out), reps, ctypes.byref(t), ctypes.byref(us)))
+    return int(t.value), float(us.value)
+
+
+def conv_tune_save(path):
+    _check(lib().pp_conv_tune_save(str(path).encode()))
+
+
+def conv_tune_load(path) -> int:
+    n = lib().pp_conv_tune_load(str(path).encode())
+    if n < 0:
+        _check(n)
+    return int(n)
+
+
+def conv_tune_clear():
+    lib().pp_conv_tune_clear()
 
 
 def conv_tile_count(dtype) -> int:

@@ -203,6 +203,7 @@ int conv_f32_tile_count() { return (int)(sizeof(kTiles) / sizeof(kTiles[0])); }
 int conv_f32_launch(const ConvShape& c, const float* in, const float* w, const float* ss,
                     float* out, int tile, cudaStream_t s) {
   const int M = c.Ho * c.Wo;
+  if (tile < 0) tile = tuned_tile(PP_F32, c);
   if (tile < 0) {
     // fewest waves of (CTAs per SM ~ 2) first, then larger tiles
     int best = 0;

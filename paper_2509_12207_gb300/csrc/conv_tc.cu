@@ -1135,6 +1135,7 @@ int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfl
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  if (tile < 0) tile = tuned_tile(PP_BF16, c);
   const int n_old = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
   const int n_p = conv_tcp_tile_count(0);
   if ((tile < 0 && c.cin == 64 && c.cout == 64) || tile == n_old + n_p)
@@ -1243,6 +1244,7 @@ int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split,
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
   if (c.cin % kBK32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
+  if (tile < 0) tile = tuned_tile(PP_F32_TC, c);
   const int n_old = (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0]));
   if (tile < 0 || tile >= n_old) return conv_tcp_launch(1, c, in, w_split, ss, out, tile < 0 ? -1 : tile - n_old, s);
   if (tile < 0 || tile >= conv_f32tc_tile_count() || c.cout % kTilesF32TC[tile].bn)

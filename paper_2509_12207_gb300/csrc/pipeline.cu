@@ -111,7 +111,7 @@ int Pipeline::alloc(void** p, size_t n) {
   return PP_OK;
 }
 
-int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, cudaStream_t s) {
+int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, cudaStream_t s) {
   m_ = m;
   B_ = max_batch;
   cap_ = cap_points;
@@ -148,6 +148,22 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, c
   if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)B_ * sizeof(int)), "pinned pillar counts"))) return st;
   memset(num_host_, 0, (size_t)B_ * sizeof(int));
   vw_ = vox_carve(vox_ws_, g, B_, cap_);
+  if (tune) {
+    // time every conv tile of every layer for each unit size on this unit's own buffers; the
+    // launches below (and the captured graphs) then use the fastest
+    if ((st = cuda_status(cudaStreamSynchronize(s), "pre-tune sync"))) return st;
+    for (int b = 1; b <= B_ && st == PP_OK; ++b) {
+      const void* x = canvas_;
+      for (size_t l = 0; l < m->layers.size() && st == PP_OK; ++l) {
+        const LayerSpec& L = m->layers[l];
+        int best = -1;
+        st = pp_conv_autotune(b, L.H, L.W, L.cin, L.cout, L.stride, m->conv_dtype, x, m->conv_w[l],
+                              m->conv_ss[l], act_[l], 5, &best, nullptr);
+        x = act_[l];
+      }
+    }
+    if (st) return st;
+  }
   // one eager pass sets kernel attributes and validates every launch before capture
   if ((st = enqueue(B_, s))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s), "pipeline warm-up"))) return st;
@@ -267,7 +283,7 @@ int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** ou
   cudaStream_t s;
   int st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
   if (!st) st = p->model.upload(cfg, precision, s);
-  if (!st) st = p->pipe.init(&p->model, cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, s);
+  if (!st) st = p->pipe.init(&p->model, cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, cfg->autotune != 0, s);
   if (!st) st = cuda_status(cudaStreamSynchronize(s), "pipeline init");
   cudaStreamDestroy(s);
   if (st) {

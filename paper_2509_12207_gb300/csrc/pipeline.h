@@ -30,7 +30,8 @@ struct Model {
 
 class Pipeline {
  public:
-  int init(const Model* m, int max_batch, int cap_points, bool graphs, cudaStream_t s);
+  // tune: autotune every conv layer for unit sizes 1..max_batch before capturing the graphs
+  int init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, cudaStream_t s);
   void release();
   // Stages `n` frames (device or host pointers, cudaMemcpyDefault) into slots 0..n-1 and
   // enqueues the whole front end for them on `s` (graph or plain launches).

@@ -65,6 +65,8 @@ int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split,
                       float* out, int tile, cudaStream_t s);
 int conv_f32tc_tile_count();
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent);
+// Tile the autotuner found fastest for this dtype and shape, or -1 (tune.cu).
+int tuned_tile(int dtype, const ConvShape& c);
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
 
 }  // namespace pp

@@ -497,6 +497,7 @@ void pp_config_defaults(pp_config* cfg) {
   cfg->util_exempt = 0.1;
   cfg->early_exit = 1;
   cfg->num_streams = 0;
+  cfg->autotune = 1;
 }
 
 int pp_create(const pp_config* cfg, pp_ctx** out) {
@@ -536,7 +537,9 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       Unit* u = new (std::nothrow) Unit();
       if (!u) { st = fail(PP_ENOMEM, "create: host allocation"); break; }
       u->precision = p;
-      st = u->pipe.init(&c->models[p], cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, c->aux);
+      // the first unit of each precision tunes the conv tiles; later units reuse the table
+      st = u->pipe.init(&c->models[p], cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0,
+                        cfg->autotune != 0 && k == 0, c->aux);
       if (!st) st = cuda_status(cudaEventCreate(&u->start), "event");
       if (!st) st = cuda_status(cudaEventCreate(&u->done), "event");
       if (!st && used + u->pipe.bytes() > cfg->hbm_budget_bytes) {

@@ -64,3 +64,26 @@ def test_bn_fold_matches_definition(lib):
     h = rng.normal(size=(100, 64)) * 3
     want = bn[0] * (h - bn[2]) / np.sqrt(bn[3].astype(np.float64) + 1e-3) + bn[1]
     np.testing.assert_allclose(h * ss[0] + ss[1], want, rtol=1e-6, atol=1e-6)
+
+
+def test_tune_table_save_load(lib, tmp_path):
+    import paper_2509_12207_gb300 as pp
+    pp.conv_tune_clear()
+    f = tmp_path / "tiles.txt"
+    n_bf16 = pp.conv_tile_count(pp.PP_BF16)
+    f.write_text("# comment\n"
+                 "1 8 248 216 64 64 2 %d 20.5\n"   # valid
+                 "1 8 124 108 64 64 1 999 1.0\n"   # tile does not exist: skipped
+                 "garbage line\n"
+                 "0 1 496 432 64 64 2 1 40.0\n" % (n_bf16 - 1))
+    assert pp.conv_tune_load(f) == 2
+    out = tmp_path / "saved.txt"
+    pp.conv_tune_save(out)
+    lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert sorted(l.split()[:8] for l in lines) == sorted([
+        ["0", "1", "496", "432", "64", "64", "2", "1"], ["1", "8", "248", "216", "64", "64", "2", str(n_bf16 - 1)]])
+    pp.conv_tune_clear()
+    pp.conv_tune_save(out)
+    assert [l for l in out.read_text().splitlines() if not l.startswith("#")] == []
+    with pytest.raises(pp.PPError):
+        pp.conv_tune_load(tmp_path / "missing.txt")

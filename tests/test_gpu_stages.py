@@ -273,3 +273,32 @@ def test_frame_config1_fp32_end_to_end():
     got = x[0, 1:-1, 1:-1].cpu().numpy()
     assert got.shape == ref["blocks"][-1].shape
     assert rel_err(got, ref["blocks"][-1]) <= FP32_TOL
+
+
+@pytest.mark.parametrize("dtype", [pp.PP_BF16, pp.PP_F32_TC])
+def test_conv_autotune_then_library_choice(dtype):
+    """The autotuner picks a tile that supports the shape; afterwards tile = -1 uses it and the
+    result is bit-identical to an explicit launch of that tile (and still meets tolerance)."""
+    pp.conv_tune_clear()
+    B, H, W, cin, cout, s = 2, 30, 44, 64, 64, 2
+    xp, w, bn = _conv_case(B, H, W, cin, cout, s, seed=77)
+    if dtype == pp.PP_BF16:
+        x_d = _bf16(xp).to(DEV)
+    else:
+        x_d = torch.from_numpy(xp).to(DEV)
+    wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), dtype)
+    ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
+    Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
+    out = torch.zeros((B, Ho + 2, Wo + 2, cout), dtype=x_d.dtype, device=DEV)
+    tile, us = pp.conv_autotune(x_d, wp, ss, cout, s, dtype, out)
+    assert 0 <= tile < pp.conv_tile_count(dtype) and us > 0
+    explicit = pp.conv3x3(x_d, wp, ss, cout, s, dtype=dtype, tile=tile)
+    chosen = pp.conv3x3(x_d, wp, ss, cout, s, dtype=dtype, tile=-1)
+    torch.cuda.synchronize()
+    assert torch.equal(explicit, chosen)
+    ref = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
+    o = chosen.float().cpu().numpy()
+    for b in range(B):
+        tol = FP32_TOL if dtype == pp.PP_F32_TC else BF16_TOL
+        assert rel_err(o[b, 1:-1, 1:-1], ref[b]) <= tol
+    pp.conv_tune_clear()
