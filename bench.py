@@ -44,6 +44,10 @@ def _args():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
+    ap.add_argument("--depth", type=int, default=2, help="steps in flight (1 = each step waits for the last)")
+    ap.add_argument("--tune-table", default=None,
+                    help="conv tile table: loaded (no autotuning) if the file exists, else written after "
+                         "autotuning, so that a profiled run launches the same tiles as a plain one")
     ap.add_argument("--serve-sweep", default=None,
                     help="run only the serving sweep: comma list of chains:rate:seconds[:mixed]")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
@@ -213,30 +217,43 @@ def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=20, tile=-1):
     return per_layer
 
 
-def _time_stages(pp, torch, g, frames_dev, w, prec, reps=10):
-    """Average duration of the voxelise / PointNet / scatter launches for one frame."""
-    stream = torch.cuda.current_stream()
-    pts = frames_dev[0][None].contiguous()
-    n = torch.tensor([pts.shape[1]], dtype=torch.int32, device="cuda")
+def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
+    """Device time of the voxelise / PointNet / scatter stages for one step's batch of frames,
+    each stage captured in a CUDA graph (so that only the device work is timed) and replayed."""
+    fs = [frames_dev[j % len(frames_dev)] for j in range(batch)]
+    cap = max(int(f.shape[0]) for f in fs)
+    pts = torch.zeros((batch, cap, 4), dtype=torch.float32, device="cuda")
+    for j, f in enumerate(fs):
+        pts[j, :f.shape[0]] = f
+    n = torch.tensor([int(f.shape[0]) for f in fs], dtype=torch.int32, device="cuda")
     pfn_w = torch.from_numpy(w[0]).cuda()
     pfn_ss = torch.from_numpy(pp.bn_fold(w[1])).cuda()
-    v = pp.voxelize(pts, n, g)
-    feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], pfn_w, pfn_ss, g)
-    canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        v = pp.voxelize(pts, n, g)
+        feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], pfn_w, pfn_ss, g)
+        canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
     out = {}
     for name, fn in (("voxelize", lambda: pp.voxelize(pts, n, g)),
                      ("pointnet", lambda: pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
                                                       pfn_w, pfn_ss, g)),
                      ("scatter", lambda: pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec))):
-        fn()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            keep = fn()  # noqa: F841  (outputs live in the graph's pool)
+        graph.replay()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record(stream)
+        e0.record()
         for _ in range(reps):
-            fn()
-        e1.record(stream)
+            graph.replay()
+        e1.record()
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / reps
+        del graph
     canvas_bytes = canvas.numel() * canvas.element_size()
     return out, canvas_bytes, int(v["num_pillars"][0])
 
@@ -251,46 +268,58 @@ def _run_ours(a, rank, world, dist):
     g, bb, prec, batch, cap, frames, w = _workload(a.workload)
     # throughput run: no deadline pressure (early exit off, 10 s deadline), so a slow run (a
     # profiler) still completes every frame
-    cfg, keep = pp.make_config(g, bb, w, max_batch=batch, cap_points=cap, precisions=1 << prec, units=2,
-                               th_urgent=-1.0, early_exit=0, fp32_cuda_cores=1 if a.fp32_cuda_cores else 0)
+    tuned = bool(a.tune_table) and os.path.exists(a.tune_table) and pp.conv_tune_load(a.tune_table) > 0
+    cfg, keep = pp.make_config(g, bb, w, max_batch=batch, cap_points=cap, precisions=1 << prec,
+                               units=max(2, a.depth), max_admitted=2 * a.depth * batch,
+                               th_urgent=-1.0, early_exit=0, fp32_cuda_cores=1 if a.fp32_cuda_cores else 0,
+                               autotune=0 if tuned else 1)
     ctx = pp.Context(cfg)
+    if a.tune_table and not tuned:
+        pp.conv_tune_save(a.tune_table)
     ctx.register_chain(0, 10000.0, 10000.0, prec)
     frames_dev = [torch.from_numpy(f).cuda() for f in frames]
     frames_host = [torch.from_numpy(f).pin_memory() for f in frames]
     n_frames = batch
 
-    def step(k, host):
-        ids = []
-        for j in range(n_frames):
-            f = (frames_host if host else frames_dev)[(k * n_frames + j) % len(frames)]
-            rc, fid = ctx.submit(0, f.numpy() if host else f)
-            assert rc == pp.PP_OK, rc
-            ids.append(fid)
-        got = []
-        while len(got) < n_frames:
-            got += ctx.poll(16, timeout_us=1000000)
-        for r in got:
-            assert r.status == pp.PP_FRAME_DONE
-            if host:
-                # D2H read of the step's result (the last backbone layer)
-                nbytes = r.out_c * (r.out_h + 2) * (r.out_w + 2) * (4 if r.out_dtype == pp.PP_F32 else 2)
-                step.d2h += nbytes
-                step.sink = pp.result_tensor(r).cpu()
-            ctx.release(r.frame_id)
-    step.d2h = 0
+    def submit(k, host):
+        fs = [(frames_host if host else frames_dev)[(k * n_frames + j) % len(frames)] for j in range(n_frames)]
+        # the step's frames arrive together (one submission), so they share one release unit
+        rc, ids = ctx.submit_many([0] * n_frames, [f.numpy() for f in fs] if host else fs)
+        assert rc == pp.PP_OK and len(ids) == n_frames, rc
+
+    def run_steps(steps, host):
+        """Runs `steps` steps with up to `depth` of them in flight (continuous batching: a step
+        is submitted as soon as an earlier one's results have been read and released)."""
+        k = done = inflight = 0
+        while done < steps * n_frames:
+            while k < steps and inflight < a.depth * n_frames:
+                submit(k, host)
+                k += 1
+                inflight += n_frames
+            got = ctx.poll(64, timeout_us=1000000)
+            for r in got:
+                assert r.status == pp.PP_FRAME_DONE
+                if host:
+                    # D2H read of the frame's result (the last backbone layer)
+                    nbytes = r.out_c * (r.out_h + 2) * (r.out_w + 2) * (4 if r.out_dtype == pp.PP_F32 else 2)
+                    run_steps.d2h += nbytes
+                    run_steps.sink = pp.result_tensor(r).cpu()
+            ctx.release_many([r.frame_id for r in got])
+            inflight -= len(got)
+            done += len(got)
+    run_steps.d2h = 0
 
     def timed(host):
-        for k in range(a.warmup):
-            step(k, host)
+        run_steps(a.warmup, host)
+        timed.units_before = ctx.stats()["units_launched"]
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         t0 = time.perf_counter()
-        step.d2h = 0
-        for k in range(a.steps):
-            step(k, host)
+        run_steps.d2h = 0
+        run_steps(a.steps, host)
         e1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -307,10 +336,12 @@ def _run_ours(a, rank, world, dist):
     finally:
         clk = clocks.stop()
     st = ctx.stats()
+    # units launched inside the timed region (the warm-up steps ran before it)
+    timed_units = st["units_launched"] - timed.units_before
     e2e_el, _ = timed(host=True)
     h2d = sum(int(frames[(k * n_frames + j) % len(frames)].nbytes) for k in range(a.steps)
               for j in range(n_frames)) // a.steps
-    d2h = step.d2h // a.steps
+    d2h = run_steps.d2h // a.steps
     ctx.destroy()
 
     # kernel roofline: the conv kernels dominate the step
@@ -318,7 +349,7 @@ def _run_ours(a, rank, world, dist):
     layers = _time_conv_kernels(pp, torch, g, bb, w, conv_dtype, batch)
     conv_s = sum(t for t, _ in layers)
     conv_flops = sum(f for _, f in layers)
-    stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w, prec)
+    stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w, prec, n_frames)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
@@ -342,7 +373,7 @@ def _run_ours(a, rank, world, dist):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOADS[a.workload], "frames_per_step": n_frames, "points_per_frame":
+        "config": {"workload": WORKLOADS[a.workload], "frames_per_step": n_frames, "steps_in_flight": a.depth, "points_per_frame":
                    [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
                          % (canvas_bytes // 2 ** 20)},
@@ -355,10 +386,12 @@ def _run_ours(a, rank, world, dist):
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames,
                      "layers_us": [round(t * 1e6, 2) for t, _ in layers],
                      "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
-        "stage_ms": {k: v for k, v in stages.items()},
+        "stage_ms_per_step": {k: v for k, v in stages.items()},
         "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
-                    "sched_us_per_decision": st["sched_us_per_decision"], "units": st["units_launched"]},
-        "gpu_launches": a.steps * (5 + 1 + 1 + len(bb.layers(64))) * (1 if n_frames else 0),
+                    "sched_us_per_decision": st["sched_us_per_decision"], "units": timed_units,
+                    "frames_per_unit": a.steps * n_frames / max(1, timed_units)},
+        # per unit: 5 voxelisation kernels, PointNet, scatter, one per conv layer, result copy
+        "gpu_launches": timed_units * (5 + 1 + 1 + len(bb.layers(64)) + 1),
         "clocks": clk,
         "num_pillars": num_p,
         "wall_s": wall,
@@ -398,6 +431,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
         ev = arrival_times(chains, duration_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed)
         rejected = {}
+        slow = []  # frames slower than 5 ms: where the time went
         t0 = pp.now_us() + 20000.0
         i, outstanding = 0, 0
         while i < len(ev) or outstanding:
@@ -412,9 +446,15 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
                     rejected[cid] = rejected.get(cid, 0) + 1
                 i += 1
             wait = 2000.0 if i >= len(ev) else max(0.0, t0 + ev[i][0] * 1000.0 - pp.now_us())
-            for r in ctx.poll(256, timeout_us=int(min(wait, 2000.0))):
-                ctx.release(r.frame_id)
-                outstanding -= 1
+            got = ctx.poll(256, timeout_us=int(min(wait, 2000.0)))
+            for r in got:
+                if r.t_done_us - r.t_arr_us > 5000.0 and len(slow) < 8:
+                    slow.append({"chain": r.chain_id, "status": r.status, "batch": r.batch, "level": r.level,
+                                 "t_ms": round((r.t_arr_us - t0) / 1e3, 3),
+                                 "wait_ms": round((r.t_release_us - r.t_arr_us) / 1e3, 3),
+                                 "run_ms": round((r.t_done_us - r.t_release_us) / 1e3, 3)})
+            ctx.release_many([r.frame_id for r in got])
+            outstanding -= len(got)
         st = ctx.stats()
     finally:
         ctx.destroy()
@@ -432,7 +472,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             "frames_per_s": st["done"] / duration_s, "mean_batch": st["mean_batch"],
             "delayed": st["delayed_releases"], "collisions": st["collisions"],
             "th_urgent_per_ms": st["th_urgent"] * 1e3 if st["th_urgent"] > 0 else None,
-            "sched_us_per_decision": st["sched_us_per_decision"]}
+            "sched_us_per_decision": st["sched_us_per_decision"], "slow_frames": slow}
 
 
 def _serving_clouds(torch):

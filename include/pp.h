@@ -292,6 +292,18 @@ int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_
                     int32_t is_device_ptr, double t_arrival_us, double abs_deadline_us,
                     uint64_t* frame_id_out);
 
+/* Submits n (1..PP_MAX_SUBMIT) frames at once, all arriving at t_arrival_us: they become ready
+ * together, so that one release decision can batch them into a single unit (uneven point
+ * counts share the unit's graph).  chain_ids / xyzr / n_points: host arrays of n entries, same
+ * meaning as in pp_submit_frame; abs_deadline_us: n deadlines, or NULL for each chain's own.
+ * Frames are admitted in order until one cannot be: *n_admitted (may be NULL) receives how
+ * many were, frame_ids_out (may be NULL) their ids, and the call returns PP_EAGAIN (budget
+ * full) or PP_ENOMEM for the first frame left out.  Argument errors admit no frame. */
+#define PP_MAX_SUBMIT 64
+int pp_submit_frames(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
+                     const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
+                     const double* abs_deadline_us, uint64_t* frame_ids_out, int32_t* n_admitted);
+
 typedef struct {
   uint64_t frame_id;
   int32_t chain_id;
@@ -314,6 +326,9 @@ typedef struct {
  * gives its slot back at once; releasing it only forgets the record. */
 int pp_poll(pp_ctx* ctx, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us);
 int pp_result_release(pp_ctx* ctx, uint64_t frame_id);
+/* pp_result_release for n frames under one lock; every id is tried, and the first error met
+ * (unknown or not completed) is returned. */
+int pp_result_release_many(pp_ctx* ctx, int32_t n, const uint64_t* frame_ids);
 
 typedef struct {
   uint64_t submitted, done, dropped, missed, rejected;

@@ -157,7 +157,12 @@ _SIGS = {
     "pp_submit_frame": (ctypes.c_int, [_P, _I, _P, ctypes.c_int64, _I, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_uint64)]),
     "pp_poll": (ctypes.c_int, [_P, ctypes.POINTER(Result), _I, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]),
+    "pp_submit_frames": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_int64), _I, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_int32)]),
     "pp_result_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "pp_result_release_many": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "pp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "pp_destroy": (ctypes.c_int, [_P]),
     "pp_now_us": (ctypes.c_double, []),
@@ -443,6 +448,36 @@ class Context:
         if rc not in (PP_OK, PP_EAGAIN):
             _check(rc)
         return rc, int(fid.value)
+
+    def submit_many(self, chain_ids, frames, t_arrival_us=None, abs_deadlines_us=None):
+        """Submits frames that arrive together (one pp_submit_frames call): ``frames`` are all
+        CUDA tensors [N, 4] (borrowed) or all host arrays (copied).  Returns (status, ids of the
+        admitted frames, in order)."""
+        n = len(frames)
+        t = now_us() if t_arrival_us is None else t_arrival_us
+        dev = n > 0 and hasattr(frames[0], "is_cuda")
+        keep = []
+        if dev:
+            ptrs = [_ptr(f) for f in frames]
+        else:
+            import numpy as np
+            keep = [np.ascontiguousarray(f, dtype=np.float32) for f in frames]
+            ptrs = [a.ctypes.data if a.shape[0] else None for a in keep]
+        cids = (ctypes.c_int32 * n)(*chain_ids)
+        parr = (ctypes.c_void_p * n)(*ptrs)
+        cnt = (ctypes.c_int64 * n)(*[int(f.shape[0]) for f in frames])
+        dls = (ctypes.c_double * n)(*abs_deadlines_us) if abs_deadlines_us is not None else None
+        ids = (ctypes.c_uint64 * n)()
+        got = ctypes.c_int32(0)
+        rc = lib().pp_submit_frames(self.h, n, cids, parr, cnt, 1 if dev else 0, t, dls, ids, ctypes.byref(got))
+        if rc not in (PP_OK, PP_EAGAIN):
+            _check(rc)
+        return rc, [int(ids[i]) for i in range(got.value)]
+
+    def release_many(self, frame_ids):
+        n = len(frame_ids)
+        if n:
+            _check(lib().pp_result_release_many(self.h, n, (ctypes.c_uint64 * n)(*frame_ids)))
 
     def poll(self, max_results=64, timeout_us=0):
         buf = (Result * max_results)()

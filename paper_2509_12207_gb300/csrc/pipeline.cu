@@ -5,12 +5,47 @@
 // capacity and blocks past a frame's count exit at once.
 #include "pipeline.h"
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 
 namespace pp {
 
 namespace {
+
+// Where the block outputs of slot 0 are, how far apart the slots lie, and where each block goes
+// inside a result slot.
+struct ResultCopy {
+  int nblocks;
+  const char* src[PP_MAX_BLOCKS];
+  size_t bytes[PP_MAX_BLOCKS];  // one slot's block output = the distance between slots
+  size_t off[PP_MAX_BLOCKS];
+};
+
+// Copies every frame's block outputs into its result slot (tab->dst[frame]); gridDim.y = frame.
+// Pure 16-byte streaming copy (all sizes are multiples of 128 bytes, all bases 16-byte aligned).
+__global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTable* __restrict__ tab) {
+  const int f = blockIdx.y;
+  char* dst = tab->dst[f];
+  if (!dst) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int b = 0; b < rc.nblocks; ++b) {
+    const uint4* s = reinterpret_cast<const uint4*>(rc.src[b] + (size_t)f * rc.bytes[b]);
+    uint4* d = reinterpret_cast<uint4*>(dst + rc.off[b]);
+    const size_t n = rc.bytes[b] / 16;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      const uint4 v0 = __ldcs(s + i), v1 = __ldcs(s + i + stride);
+      const uint4 v2 = __ldcs(s + i + 2 * stride), v3 = __ldcs(s + i + 3 * stride);
+      d[i] = v0;
+      d[i + stride] = v1;
+      d[i + 2 * stride] = v2;
+      d[i + 3 * stride] = v3;
+    }
+    for (; i < n; i += stride) d[i] = __ldcs(s + i);
+  }
+}
+
 int layers_of(const pp_config* cfg, std::vector<LayerSpec>* out, std::vector<int>* block_end,
               int H0, int W0) {
   if (cfg->n_blocks <= 0 || cfg->n_blocks > PP_MAX_BLOCKS)
@@ -90,6 +125,18 @@ int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
   return PP_OK;
 }
 
+size_t Model::result_layout(std::vector<size_t>* block_off) const {
+  const size_t elt = precision == PP_F32 ? 4 : 2;
+  size_t off = 0;
+  block_off->clear();
+  for (int l : block_end) {
+    const LayerSpec& L = layers[l];
+    block_off->push_back(off);
+    off += align_up((size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * elt, 256);
+  }
+  return off;
+}
+
 void Model::release() {
   cudaFree(pfn_w);
   cudaFree(pfn_ss);
@@ -120,8 +167,9 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   int st = PP_OK;
 #define PP_ALLOC(ptr, n) \
   if ((st = alloc(reinterpret_cast<void**>(&ptr), (n)))) return st
+  if (B_ < 1 || B_ > kMaxUnit) return fail(PP_EINVAL, "pipeline: max_batch 1..%d", kMaxUnit);
   PP_ALLOC(points_, (size_t)B_ * cap_ * sizeof(float4));
-  PP_ALLOC(n_dev_, (size_t)B_ * sizeof(int));
+  PP_ALLOC(tab_dev_, sizeof(UnitTable));
   PP_ALLOC(cell_, (size_t)B_ * cap_ * sizeof(int));
   PP_ALLOC(cnt_, (size_t)B_ * g.G * sizeof(unsigned));
   PP_ALLOC(poc_, (size_t)B_ * g.G * sizeof(int));
@@ -142,9 +190,16 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   }
 #undef PP_ALLOC
   if ((st = cuda_status(cudaMemsetAsync(vox_ws_, 0, 256, s), "clear vox error word"))) return st;
-  if ((st = cuda_status(cudaMemsetAsync(n_dev_, 0, (size_t)B_ * sizeof(int), s), "clear counts"))) return st;
-  if ((st = cuda_status(cudaMallocHost(&n_host_, (size_t)B_ * sizeof(int)), "pinned counts"))) return st;
-  memset(n_host_, 0, (size_t)B_ * sizeof(int));
+  if ((st = cuda_status(cudaMemsetAsync(tab_dev_, 0, sizeof(UnitTable), s), "clear unit table"))) return st;
+  if ((st = cuda_status(cudaMallocHost(&tab_host_, sizeof(UnitTable)), "pinned unit table"))) return st;
+  memset(tab_host_, 0, sizeof(UnitTable));
+  if ((st = cuda_status(cudaEventCreateWithFlags(&tab_ev_, cudaEventDisableTiming), "table event"))) return st;
+  m->result_layout(&res_off_);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if ((st = cuda_status(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return st;
+  }
   if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)B_ * sizeof(int)), "pinned pillar counts"))) return st;
   memset(num_host_, 0, (size_t)B_ * sizeof(int));
   vw_ = vox_carve(vox_ws_, g, B_, cap_);
@@ -195,16 +250,20 @@ void Pipeline::release() {
   for (void* p : allocs_) cudaFree(p);
   allocs_.clear();
   act_.clear();
-  if (n_host_) cudaFreeHost(n_host_);
+  if (tab_host_) cudaFreeHost(tab_host_);
   if (num_host_) cudaFreeHost(num_host_);
-  n_host_ = num_host_ = nullptr;
+  if (tab_ev_) cudaEventDestroy(tab_ev_);
+  tab_host_ = nullptr;
+  num_host_ = nullptr;
+  tab_ev_ = nullptr;
   bytes_ = 0;
 }
 
 int Pipeline::enqueue(int n, cudaStream_t s) {
   const Model& m = *m_;
   const Geom& g = m.g;
-  int st = vox_launch(g, n, cap_, points_, n_dev_, cell_, cnt_, poc_, coord_, npts_, num_, pts_, vw_, s);
+  int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
+                      pts_, vw_, s, tab_dev_->src);
   if (!st) st = pfn_launch(g, n, pts_, npts_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
   if (!st) st = scatter_launch(g, n, feat_, poc_, canvas_, m.precision, s);
   const void* x = canvas_;
@@ -222,28 +281,52 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
                             m.conv_ss[l], (__nv_bfloat16*)act_[l], -1, s);
     x = act_[l];
   }
-  return st;
+  if (st) return st;
+  ResultCopy rc{};
+  rc.nblocks = (int)m.block_end.size();
+  for (int b = 0; b < rc.nblocks; ++b) {
+    const int l = m.block_end[b];
+    const LayerSpec& L = m.layers[l];
+    rc.src[b] = static_cast<const char*>(act_[l]);
+    rc.bytes[b] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
+    rc.off[b] = res_off_[b];
+  }
+  result_copy<<<dim3(std::max(1, 8 * sms_ / n), n), 256, 0, s>>>(rc, tab_dev_);
+  return cuda_status(cudaGetLastError(), "result copy");
 }
 
-int Pipeline::run(int n, const float* const* frames, const int* counts, bool use_graph,
-                  cudaStream_t s) {
+int Pipeline::run(int n, const float* const* frames, const int* counts, const bool* direct,
+                  char* const* dst, bool use_graph, cudaStream_t s) {
   if (n <= 0 || n > B_) return fail(PP_EINVAL, "pipeline run: batch %d outside 1..%d", n, B_);
   for (int i = 0; i < n; ++i) {
     if (counts[i] < 0 || counts[i] > cap_)
       return fail(PP_EINVAL, "pipeline run: frame %d has %d points (cap %d)", i, counts[i], cap_);
     if (counts[i] > 0 && !frames[i]) return fail(PP_EINVAL, "pipeline run: NULL frame %d", i);
+    if (direct && direct[i] && (reinterpret_cast<uintptr_t>(frames[i]) & 15u))
+      return fail(PP_EINVAL, "pipeline run: frame %d is not 16-byte aligned", i);
   }
+  // the pinned table may still be in flight from the previous run on this unit
+  int st = cuda_status(cudaEventSynchronize(tab_ev_), "unit table reuse");
+  if (st) return st;
+  UnitTable& t = *tab_host_;
+  memset(&t, 0, sizeof(t));
   for (int i = 0; i < n; ++i) {
-    n_host_[i] = counts[i];
-    if (counts[i] > 0) {
-      int st = cuda_status(cudaMemcpyAsync(points_ + (size_t)i * cap_, frames[i],
-                                           (size_t)counts[i] * sizeof(float4), cudaMemcpyDefault, s),
-                           "stage points");
-      if (st) return st;
+    t.counts[i] = counts[i];
+    t.dst[i] = dst ? dst[i] : nullptr;
+    if (direct && direct[i]) {
+      t.src[i] = reinterpret_cast<const float4*>(frames[i]);
+      continue;
     }
+    t.src[i] = points_ + (size_t)i * cap_;
+    if (counts[i] > 0 &&
+        (st = cuda_status(cudaMemcpyAsync(points_ + (size_t)i * cap_, frames[i],
+                                          (size_t)counts[i] * sizeof(float4), cudaMemcpyDefault, s),
+                          "stage points")))
+      return st;
   }
-  int st = cuda_status(cudaMemcpyAsync(n_dev_, n_host_, (size_t)n * sizeof(int),
-                                       cudaMemcpyHostToDevice, s), "stage counts");
+  st = cuda_status(cudaMemcpyAsync(tab_dev_, tab_host_, sizeof(UnitTable), cudaMemcpyHostToDevice, s),
+                   "unit table");
+  if (!st) st = cuda_status(cudaEventRecord(tab_ev_, s), "unit table event");
   if (st) return st;
   if (use_graph && graphs_.size() > (size_t)n && graphs_[n])
     st = cuda_status(cudaGraphLaunch(graphs_[n], s), "graph launch");
@@ -299,7 +382,7 @@ int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** ou
 int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames, const int32_t* counts,
                     int32_t use_graph, void* stream) {
   if (!p || !frames || !counts) return fail(PP_EINVAL, "pipeline_run: NULL argument");
-  return p->pipe.run(n, frames, counts, use_graph != 0, static_cast<cudaStream_t>(stream));
+  return p->pipe.run(n, frames, counts, nullptr, nullptr, use_graph != 0, static_cast<cudaStream_t>(stream));
 }
 
 int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** dev, int32_t* c,

@@ -12,6 +12,17 @@ struct LayerSpec {
   int cin, cout, stride, H, W, Ho, Wo;
 };
 
+constexpr int kMaxUnit = 8;  // frames per release unit
+
+// Per-launch table a unit's kernels read from device memory, so that one captured graph serves
+// any frames: counts, where each frame's points are, where its block outputs go.
+struct UnitTable {
+  int32_t counts[kMaxUnit];
+  int32_t pad[kMaxUnit];
+  const float4* src[kMaxUnit];  // frame's points (a borrowed device buffer or a staging row)
+  char* dst[kMaxUnit];          // frame's result slot (NULL: leave outputs in the unit)
+};
+
 struct Model {
   Geom g;
   std::vector<LayerSpec> layers;
@@ -25,6 +36,8 @@ struct Model {
   std::vector<float*> conv_ss;   // [2][cout]
   size_t bytes = 0;
   int upload(const pp_config* cfg, int precision, cudaStream_t s);
+  // Result slot layout: every block's padded NHWC output, each at a 256-byte aligned offset.
+  size_t result_layout(std::vector<size_t>* block_off) const;
   void release();
 };
 
@@ -33,9 +46,12 @@ class Pipeline {
   // tune: autotune every conv layer for unit sizes 1..max_batch before capturing the graphs
   int init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, cudaStream_t s);
   void release();
-  // Stages `n` frames (device or host pointers, cudaMemcpyDefault) into slots 0..n-1 and
-  // enqueues the whole front end for them on `s` (graph or plain launches).
-  int run(int n, const float* const* frames, const int* counts, bool use_graph, cudaStream_t s);
+  // Enqueues the whole front end for `n` frames on `s` (graph or plain launches).  Frame i is
+  // read in place when direct[i] (a 16-byte aligned device buffer), else staged into slot i
+  // (host or device pointer, cudaMemcpyDefault).  When dst[i] is set, the blocks' outputs are
+  // copied to it (result_layout) inside the same graph.  direct / dst may be NULL.
+  int run(int n, const float* const* frames, const int* counts, const bool* direct,
+          char* const* dst, bool use_graph, cudaStream_t s);
   // Enqueues the kernels for slots 0..n-1 (points and counts already in place).
   int enqueue(int n, cudaStream_t s);
   size_t bytes() const { return bytes_; }
@@ -45,9 +61,6 @@ class Pipeline {
   const void* layer_out(int layer, int i) const;
   const Model* model() const { return m_; }
   int* num_pillars_dev() const { return num_; }
-  float4* points_dev() const { return points_; }
-  int* counts_dev() const { return n_dev_; }
-  int* counts_host() const { return n_host_; }
   // pinned copy of num_pillars, written at the end of every run (valid once it completes)
   const int* num_pillars_host() const { return num_host_; }
 
@@ -56,9 +69,12 @@ class Pipeline {
   int B_ = 0, cap_ = 0;
   size_t bytes_ = 0;
   float4* points_ = nullptr;
-  int* n_dev_ = nullptr;
-  int* n_host_ = nullptr;    // pinned [B]
-  int* num_host_ = nullptr;  // pinned [B]
+  UnitTable* tab_dev_ = nullptr;
+  UnitTable* tab_host_ = nullptr;  // pinned; rewritten only once the previous run completed
+  int* num_host_ = nullptr;        // pinned [B]
+  cudaEvent_t tab_ev_ = nullptr;   // after the table's H2D copy of the last run
+  std::vector<size_t> res_off_;
+  int sms_ = 1;
   int *cell_ = nullptr, *poc_ = nullptr, *coord_ = nullptr, *npts_ = nullptr, *num_ = nullptr;
   unsigned* cnt_ = nullptr;
   float4* pts_ = nullptr;

@@ -40,9 +40,12 @@ struct VoxWork {
 constexpr int kVoxTile = 2048;        // cells per scan tile (256 threads x 8)
 size_t vox_workspace_bytes(const Geom& g, int batch, int cap);
 VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
+// srcs: optional device table of per-frame point pointers (frame b reads srcs[b][0..n));
+// NULL = frame b is row b of `points` ([batch][cap]).
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
-               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s);
+               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
+               const float4* const* srcs = nullptr);
 
 // ---- PointNet and scatter (pfn.cu)
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,

@@ -65,6 +65,8 @@ struct Lut {
   }
 };
 
+constexpr int kMaxSubmit = PP_MAX_SUBMIT;
+
 struct Frame {
   uint64_t id = 0;
   int chain = 0, precision = 0;
@@ -296,8 +298,11 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   const int ui = free_unit(c, prec);
   if (ui < 0) return 1;  // every unit of this precision is busy: wait for a completion/release
   Unit* u = c->units[ui];
-  const float* srcs[8];
-  int counts[8];
+  const float* srcs[kMaxUnit];
+  int counts[kMaxUnit];
+  bool direct[kMaxUnit];
+  char* dsts[kMaxUnit];
+  const pp_ctx::Pool& pl = c->pool[prec];
   u->nf = d.n_frames;
   u->level = d.level;
   u->head_chain = head->chain;
@@ -312,6 +317,8 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     f->t_release = t;
     srcs[i] = f->src;
     counts[i] = (int)f->n;
+    direct[i] = f->staging < 0;  // a borrowed device buffer is read in place
+    dsts[i] = static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
     if (f->delay_start >= 0) {
       c->delayed_us += t - f->delay_start;
       f->delay_start = -1;
@@ -332,19 +339,8 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   u->running = true;
   u->t_launch = t;
   int st = cuda_status(cudaEventRecord(u->start, s), "record start");
-  if (!st) st = u->pipe.run(d.n_frames, srcs, counts, c->cfg.use_graphs != 0, s);
-  const pp_ctx::Pool& pl = c->pool[prec];
-  const Model* m = u->pipe.model();
-  for (int i = 0; i < d.n_frames && !st; ++i) {
-    char* dst = static_cast<char*>(pl.base) + (size_t)c->frames[d.frames[i]]->rslot * pl.slot_bytes;
-    for (size_t b = 0; b < m->block_end.size() && !st; ++b) {
-      const int l = m->block_end[b];
-      const LayerSpec& L = m->layers[l];
-      const size_t n = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (prec == PP_F32 ? 4 : 2);
-      st = cuda_status(cudaMemcpyAsync(dst + pl.block_off[b], u->pipe.layer_out(l, i), n,
-                                       cudaMemcpyDeviceToDevice, s), "copy result");
-    }
-  }
+  // the unit's graph also copies every frame's block outputs into its result slot
+  if (!st) st = u->pipe.run(d.n_frames, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s);
   if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
   if (!st) st = cuda_status(cudaLaunchHostFunc(s, notify_cb, c), "host notify");
   if (st) c->device_error = true;
@@ -561,14 +557,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   for (int p = 0; p < 2 && !st; ++p) {
     if (!c->have[p] || c->capacity[p] == 0) continue;
     pp_ctx::Pool& pl = c->pool[p];
-    const Model& m = c->models[p];
-    size_t off = 0;
-    for (int l : m.block_end) {
-      const LayerSpec& L = m.layers[l];
-      pl.block_off.push_back(off);
-      off += align_up((size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (p == PP_F32 ? 4 : 2), 256);
-    }
-    pl.slot_bytes = off;
+    pl.slot_bytes = c->models[p].result_layout(&pl.block_off);
     c->capacity[p] = 0;
   }
   {
@@ -602,12 +591,16 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
     const int ui = free_unit(c, p);
     if (ui < 0) continue;
     Unit* u = c->units[ui];
-    const float* srcs[8] = {nullptr};
-    int counts[8] = {0};
+    const float* srcs[kMaxUnit] = {nullptr};
+    int counts[kMaxUnit] = {0};
+    char* dsts[kMaxUnit];  // free result slots: the timing includes the result copies
+    const pp_ctx::Pool& pl = c->pool[p];
+    for (int i = 0; i < kMaxUnit; ++i)
+      dsts[i] = static_cast<char*>(pl.base) + (size_t)(i % c->capacity[p]) * pl.slot_bytes;
     for (int b = 1; b <= cfg->max_batch && !st; ++b) {
       for (int rep = 0; rep < 2 && !st; ++rep) {
         st = cuda_status(cudaEventRecord(u->start, c->aux), "profile");
-        if (!st) st = u->pipe.run(b, srcs, counts, cfg->use_graphs != 0, c->aux);
+        if (!st) st = u->pipe.run(b, srcs, counts, nullptr, dsts, cfg->use_graphs != 0, c->aux);
         if (!st) st = cuda_status(cudaEventRecord(u->done, c->aux), "profile");
         if (!st) st = cuda_status(cudaEventSynchronize(u->done), "profile");
         float ms = 0;
@@ -655,53 +648,84 @@ int pp_register_chain(pp_ctx* c, int32_t chain_id, double period_ms, double rel_
   return PP_OK;
 }
 
+int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
+                     const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
+                     const double* abs_deadline_us, uint64_t* frame_ids_out, int32_t* n_admitted) {
+  if (n_admitted) *n_admitted = 0;
+  if (!c || n < 1 || n > kMaxSubmit || !chain_ids || !xyzr || !n_points)
+    return fail(PP_EINVAL, "submit: bad argument (n 1..%d, non-NULL arrays)", kMaxSubmit);
+  for (int i = 0; i < n; ++i) {
+    if (chain_ids[i] < 0 || chain_ids[i] >= PP_MAX_CHAINS) return fail(PP_EINVAL, "submit: bad chain");
+    if (n_points[i] < 0 || n_points[i] > c->cfg.cap_points || (n_points[i] > 0 && !xyzr[i]))
+      return fail(PP_EINVAL, "submit: n_points outside [0, cap_points] or NULL points");
+    if (is_device_ptr && (reinterpret_cast<uintptr_t>(xyzr[i]) & 15u))
+      return fail(PP_EINVAL, "submit: device points must be 16-byte aligned");
+  }
+  Frame* fs[kMaxSubmit];
+  int k = 0, st = PP_OK;
+  std::unique_lock<std::mutex> lk(c->mu);
+  for (int i = 0; i < n; ++i)
+    if (!c->chains[chain_ids[i]].used) return fail(PP_ESTATE, "submit: chain %d not registered", chain_ids[i]);
+  // reserve, in order, a result slot (and a staging slot for host points) per frame
+  for (; k < n; ++k) {
+    const Chain& ch = c->chains[chain_ids[k]];
+    const int p = ch.precision;
+    if (c->admitted[p] >= c->capacity[p] || c->pool[p].free.empty() ||
+        (!is_device_ptr && c->staging_free.empty())) {
+      c->rejected += n - k;
+      st = fail(PP_EAGAIN, "submit: HBM budget full");
+      break;
+    }
+    Frame* f = new (std::nothrow) Frame();
+    if (!f) {
+      st = fail(PP_ENOMEM, "submit: host allocation");
+      break;
+    }
+    f->id = c->next_id++;
+    f->chain = chain_ids[k];
+    f->precision = p;
+    f->t_arr = t_arrival_us;
+    const double dl = abs_deadline_us ? abs_deadline_us[k] : 0.0;
+    f->deadline = dl > 0 ? dl : t_arrival_us + ch.deadline_ms * 1000.0;
+    f->n = n_points[k];
+    f->rslot = c->pool[p].free.back();
+    c->pool[p].free.pop_back();
+    c->admitted[p]++;
+    if (is_device_ptr) {
+      f->src = xyzr[k];
+    } else {
+      f->staging = c->staging_free.back();
+      c->staging_free.pop_back();
+      f->src = c->staging[f->staging];
+    }
+    fs[k] = f;
+  }
+  if (!is_device_ptr && k > 0) {
+    lk.unlock();  // the copies run outside the lock; the slots are already ours
+    for (int i = 0; i < k; ++i)
+      if (n_points[i] > 0) memcpy(const_cast<float*>(fs[i]->src), xyzr[i], (size_t)n_points[i] * 16);
+    lk.lock();
+  }
+  // the admitted frames become ready together, so one decision can batch all of them
+  for (int i = 0; i < k; ++i) {
+    Frame* f = fs[i];
+    c->submitted++;
+    if (c->first_arr < 0 || f->t_arr < c->first_arr) c->first_arr = f->t_arr;
+    c->frames[f->id] = f;
+    c->ready.push_back(f);
+    if (frame_ids_out) frame_ids_out[i] = f->id;
+  }
+  if (n_admitted) *n_admitted = k;
+  lk.unlock();
+  if (k > 0) c->cv_work.notify_one();
+  return st;
+}
+
 int pp_submit_frame(pp_ctx* c, int32_t chain_id, const float* xyzr, int64_t n_points,
                     int32_t is_device_ptr, double t_arrival_us, double abs_deadline_us,
                     uint64_t* frame_id_out) {
-  if (!c || chain_id < 0 || chain_id >= PP_MAX_CHAINS) return fail(PP_EINVAL, "submit: bad chain");
-  if (n_points < 0 || n_points > c->cfg.cap_points || (n_points > 0 && !xyzr))
-    return fail(PP_EINVAL, "submit: n_points outside [0, cap_points] or NULL points");
-  if (is_device_ptr && (reinterpret_cast<uintptr_t>(xyzr) & 15u))
-    return fail(PP_EINVAL, "submit: device points must be 16-byte aligned");
-  std::unique_lock<std::mutex> lk(c->mu);
-  Chain& ch = c->chains[chain_id];
-  if (!ch.used) return fail(PP_ESTATE, "submit: chain %d not registered", chain_id);
-  const int p = ch.precision;
-  if (c->admitted[p] >= c->capacity[p] || c->pool[p].free.empty() ||
-      (!is_device_ptr && c->staging_free.empty())) {
-    c->rejected++;
-    return fail(PP_EAGAIN, "submit: HBM budget full");
-  }
-  Frame* f = new (std::nothrow) Frame();
-  if (!f) return fail(PP_ENOMEM, "submit: host allocation");
-  f->id = c->next_id++;
-  f->chain = chain_id;
-  f->precision = p;
-  f->t_arr = t_arrival_us;
-  f->deadline = abs_deadline_us > 0 ? abs_deadline_us : t_arrival_us + ch.deadline_ms * 1000.0;
-  f->n = n_points;
-  f->rslot = c->pool[p].free.back();
-  c->pool[p].free.pop_back();
-  if (is_device_ptr) {
-    f->src = xyzr;
-  } else {
-    f->staging = c->staging_free.back();
-    c->staging_free.pop_back();
-    float* dst = c->staging[f->staging];
-    lk.unlock();  // the copy runs outside the lock; the slot is already ours
-    if (n_points > 0) memcpy(dst, xyzr, (size_t)n_points * 16);
-    lk.lock();
-    f->src = dst;
-  }
-  c->admitted[p]++;
-  c->submitted++;
-  if (c->first_arr < 0 || f->t_arr < c->first_arr) c->first_arr = f->t_arr;
-  c->frames[f->id] = f;
-  c->ready.push_back(f);
-  if (frame_id_out) *frame_id_out = f->id;
-  lk.unlock();
-  c->cv_work.notify_one();
-  return PP_OK;
+  return pp_submit_frames(c, 1, &chain_id, &xyzr, &n_points, is_device_ptr, t_arrival_us,
+                          &abs_deadline_us, frame_id_out, nullptr);
 }
 
 int pp_poll(pp_ctx* c, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us) {
@@ -721,22 +745,36 @@ int pp_poll(pp_ctx* c, pp_result* out, int32_t max, int32_t* n_out, int64_t time
   return c->device_error ? fail(PP_EDEVICE, "a unit failed on the device") : PP_OK;
 }
 
-int pp_result_release(pp_ctx* c, uint64_t frame_id) {
-  if (!c) return fail(PP_EINVAL, "release: NULL context");
+int pp_result_release_many(pp_ctx* c, int32_t n, const uint64_t* frame_ids) {
+  if (!c || n < 0 || (n > 0 && !frame_ids)) return fail(PP_EINVAL, "release: bad argument");
   std::unique_lock<std::mutex> lk(c->mu);
-  auto it = c->frames.find(frame_id);
-  if (it == c->frames.end()) return fail(PP_EINVAL, "release: unknown frame %llu", (unsigned long long)frame_id);
-  Frame* f = it->second;
-  if (!f->done) return fail(PP_ESTATE, "release: frame %llu not completed", (unsigned long long)frame_id);
-  if (!f->dropped) {
-    free_result(c, f);
-    c->admitted[f->precision]--;
+  int st = PP_OK;
+  for (int i = 0; i < n; ++i) {
+    auto it = c->frames.find(frame_ids[i]);
+    if (it == c->frames.end()) {
+      st = fail(PP_EINVAL, "release: unknown frame %llu", (unsigned long long)frame_ids[i]);
+      continue;
+    }
+    Frame* f = it->second;
+    if (!f->done) {
+      st = fail(PP_ESTATE, "release: frame %llu not completed", (unsigned long long)frame_ids[i]);
+      continue;
+    }
+    if (!f->dropped) {
+      free_result(c, f);
+      c->admitted[f->precision]--;
+    }
+    c->frames.erase(it);
+    delete f;
   }
-  c->frames.erase(it);
-  delete f;
   lk.unlock();
   c->cv_work.notify_one();
-  return PP_OK;
+  return st;
+}
+
+int pp_result_release(pp_ctx* c, uint64_t frame_id) {
+  if (!c) return fail(PP_EINVAL, "release: NULL context");
+  return pp_result_release_many(c, 1, &frame_id);
 }
 
 int pp_get_stats(pp_ctx* c, pp_stats* s) {

@@ -33,7 +33,14 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
   return n;
 }
 
+// Frame b's points: srcs[b] when a per-frame pointer table is given, else row b of the batch.
+__device__ __forceinline__ const float4* frame_src(const float4* points,
+                                                   const float4* const* srcs, int b, int cap) {
+  return srcs ? srcs[b] : points + (size_t)b * cap;
+}
+
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
+                               const float4* const* __restrict__ srcs,
                                const int* __restrict__ n_points, int* __restrict__ cell,
                                int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
   const int b = blockIdx.y;
@@ -43,7 +50,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   const size_t row = (size_t)b * cap + i;
   int c = -1;
   if (i < n) {
-    const float4 p = points[row];
+    const float4 p = frame_src(points, srcs, b, cap)[i];
     bool ok = p.x >= g.xmin && p.x < g.xmax && p.y >= g.ymin && p.y < g.ymax &&
               p.z >= g.zmin && p.z < g.zmax;
     if (ok) {
@@ -224,6 +231,7 @@ __device__ __forceinline__ int warp_bitonic_merge(int v, int lane) {
 
 __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
                                                   const float4* __restrict__ points,
+                                                  const float4* const* __restrict__ srcs,
                                                   const int* __restrict__ csr,
                                                   const int* __restrict__ pillar_start,
                                                   const int* __restrict__ pillar_cnt,
@@ -243,7 +251,7 @@ __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
     best = warp_bitonic_merge(min(best, v), lane);  // lower half = 32 smallest of the union
   }
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (lane < count) out = points[(size_t)b * cap + best];
+  if (lane < count) out = frame_src(points, srcs, b, cap)[best];
   pts[q * 32 + lane] = out;
 }
 
@@ -278,18 +286,19 @@ VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
 
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
-               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s) {
+               int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
+               const float4* const* srcs) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
   const dim3 pg((cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, batch);
-  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, n_points, cell, w.slot, cnt, w.err);
+  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, n_points, cell, w.slot, cnt, w.err);
   vox_tile_sums<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles);
   vox_scan<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles, pillar_of_cell,
                                                  coord, npts, w.pillar_start, w.pillar_cnt,
                                                  num_pillars);
   vox_bucket<<<pg, 256, 0, s>>>(g, cap, n_points, cell, w.slot, pillar_of_cell, w.pillar_start,
                                 w.csr);
-  vox_select<<<dim3((g.P + 7) / 8, batch), 256, 0, s>>>(g, cap, points, w.csr, w.pillar_start,
+  vox_select<<<dim3((g.P + 7) / 8, batch), 256, 0, s>>>(g, cap, points, srcs, w.csr, w.pillar_start,
                                                         w.pillar_cnt, num_pillars, pts);
   return cuda_status(cudaGetLastError(), "voxelize launch");
 }

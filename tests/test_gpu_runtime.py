@@ -75,12 +75,17 @@ def test_pipeline_batch_and_graph(prec, small_clouds):
         p.destroy()
 
 
-@pytest.mark.parametrize("cuda_cores", [0, 1])
-def test_pipeline_full_size_fp32(cuda_cores):
-    """The full-size FP32 frame, with the convs on the tensor cores (3xTF32) and on CUDA cores."""
+@pytest.fixture(scope="module")
+def full_frame():
     w = pillar_weights(BACKBONE_FULL, 11)
     cloud = config_points(2, 0)
-    ref = O.frame(cloud, GEOM_FULL, BACKBONE_FULL, w)
+    return w, cloud, O.frame(cloud, GEOM_FULL, BACKBONE_FULL, w)
+
+
+@pytest.mark.parametrize("cuda_cores", [0, 1])
+def test_pipeline_full_size_fp32(cuda_cores, full_frame):
+    """The full-size FP32 frame, with the convs on the tensor cores (3xTF32) and on CUDA cores."""
+    w, cloud, ref = full_frame
     cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000,
                                fp32_cuda_cores=cuda_cores)
     p = pp.Pipeline(cfg, pp.PP_F32)
@@ -92,6 +97,31 @@ def test_pipeline_full_size_fp32(cuda_cores):
             assert rel_err(_interior(p.output_tensor(0, b)), ref["blocks"][b]) <= FP32_TOL, b
     finally:
         p.destroy()
+
+
+def test_runtime_full_size_all_blocks(full_frame):
+    """The full-size frame through the serving runtime: every block's output, as copied into
+    the frame's result slot by the unit's graph, matches the oracle."""
+    w, cloud, ref = full_frame
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=2, cap_points=120000,
+                               precisions=1, units=1, th_urgent=-1.0)
+    ctx = pp.Context(cfg)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        rc, ids = ctx.submit_many([0], [cloud])          # host memory, staged
+        assert rc == pp.PP_OK
+        dev_cloud = torch.from_numpy(cloud).to(DEV)
+        rc, fid = ctx.submit(0, dev_cloud)              # device memory, read in place
+        assert rc == pp.PP_OK
+        res = _drain(ctx, 2)
+        for r in res:
+            assert r.num_pillars == ref["vox"]["num_pillars"]
+            for b in range(3):
+                assert rel_err(_interior(pp.result_tensor(r, b)), ref["blocks"][b]) <= FP32_TOL, b
+        assert torch.equal(pp.result_tensor(res[0]), pp.result_tensor(res[1]))
+        ctx.release_many([r.frame_id for r in res])
+    finally:
+        ctx.destroy()
 
 
 def _ctx(**kw):
@@ -213,3 +243,48 @@ def test_runtime_fifo_baseline_and_destroy_in_flight():
     for k in range(6):
         ctx.submit(k % 2, uniform_cloud(40000, k, GEOM_SMALL))
     ctx.destroy()          # bounded wait for in-flight units, then frees everything
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_runtime_submit_many_one_unit(host):
+    """Frames submitted together (pp_submit_frames) become ready together and run as one unit
+    of uneven point counts; their result copies (made inside the unit's graph) are exact, and
+    they are returned in one pp_result_release_many."""
+    ctx, keep = _ctx(max_batch=8, delta_eval_us=0.0, max_closed=1)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        clouds = [uniform_cloud(n, 70 + i, GEOM_SMALL)
+                  for i, n in enumerate((30000, 150000, 0, 61000, 90000, 1, 120000, 45000))]
+        frames = clouds if host else [torch.from_numpy(c).to(DEV) for c in clouds]
+        torch.cuda.synchronize()
+        rc, ids = ctx.submit_many([0] * 8, frames)
+        assert rc == pp.PP_OK and len(ids) == 8
+        res = {r.frame_id: r for r in _drain(ctx, 8)}
+        assert sorted(res) == sorted(ids)
+        assert all(r.status == pp.PP_FRAME_DONE and r.batch == 8 for r in res.values())
+        for i in (1, 2, 5, 7):
+            ref = _ref(clouds[i])
+            r = res[ids[i]]
+            assert r.num_pillars == ref["vox"]["num_pillars"]
+            for b in range(len(BACKBONE_SMALL.convs)):
+                assert rel_err(_interior(pp.result_tensor(r, b)), ref["blocks"][b]) <= FP32_TOL, (i, b)
+        ctx.release_many(ids)
+        with pytest.raises(pp.PPError):
+            ctx.release_many(ids[:1])           # already released
+    finally:
+        ctx.destroy()
+
+
+def test_runtime_submit_many_partial_admission():
+    ctx, keep = _ctx(units=1, precisions=1, max_admitted=4)
+    try:
+        ctx.register_chain(0, 50.0, 50.0, pp.PP_F32)
+        cloud = uniform_cloud(20000, 5, GEOM_SMALL)
+        rc, ids = ctx.submit_many([0] * 6, [cloud] * 6)
+        assert rc == pp.PP_EAGAIN and len(ids) == 4   # admitted in order until the budget is full
+        res = _drain(ctx, 4)
+        assert sorted(r.frame_id for r in res) == sorted(ids)
+        ctx.release_many(ids)
+        assert ctx.stats()["rejected"] == 2
+    finally:
+        ctx.destroy()
