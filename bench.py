@@ -70,6 +70,26 @@ def _workload(name):
     return g, bb, prec, batch, cap, frames, pillar_weights(bb, 7)
 
 
+# DRAM bytes (read + write) of all conv launches of one step, from one-pass ncu captures
+# (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
+# reports null until it is captured again.
+CONV_TRAFFIC = {
+    "cfg2-fp32": (206.5e6, "72fd56f864ae962dc6c7253f51fd32cced8094d918aa446bd7f7eec3b51ff75a"),
+    "cfg3-bf16": (84.5e6, "72fd56f864ae962dc6c7253f51fd32cced8094d918aa446bd7f7eec3b51ff75a"),
+}
+
+
+def _conv_traffic(workload):
+    import hashlib
+    ent = CONV_TRAFFIC.get(workload)
+    if ent is None:
+        return None
+    src = os.path.join(ROOT, "paper_2509_12207_gb300", "csrc", "conv_tc.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    return ent[0] if digest == ent[1] else None
+
+
 def _conv_flops(g, bb):
     tot = 0
     H, W = g.ny, g.nx
@@ -191,13 +211,16 @@ def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=20, tile=-1):
     H, W = g.ny, g.nx
     x = torch.rand((batch, H + 2, W + 2, 64), device="cuda").to(dt)
     x[:, 0] = 0; x[:, -1] = 0; x[:, :, 0] = 0; x[:, :, -1] = 0
+    planes = ()
+    if prec == pp.PP_F32_TC:  # 3xTF32 operands are split FP32 (value and remainder planes)
+        x, planes = pp.split_f32(x), (2,)
     per_layer = []
     stream = torch.cuda.current_stream()
     for (ci, co, s), wt, bn in zip(bb.layers(64), w[2], w[3]):
         wp = pp.pack_conv_weights(torch.from_numpy(wt).cuda(), prec)
         ss = torch.from_numpy(pp.bn_fold(bn)).cuda()
         Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
-        out = torch.zeros((batch, Ho + 2, Wo + 2, co), dtype=dt, device="cuda")
+        out = torch.zeros(planes + (batch, Ho + 2, Wo + 2, co), dtype=dt, device="cuda")
         pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile)
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
@@ -367,6 +390,7 @@ def _run_ours(a, rank, world, dist):
         peak = bf16
         bound, peak_note = "tensor", "bf16 dense, %s" % src
     achieved = conv_flops / conv_s / 1e12
+    traffic = _conv_traffic(a.workload) if conv_dtype != pp.PP_F32 else None
     frames_done = a.steps * n_frames * world
     res = {
         "metric": "pillar frames/s", "value": frames_done / el, "unit": "frames/s", "n_gpus": world,
@@ -380,7 +404,8 @@ def _run_ours(a, rank, world, dist):
         "e2e": {"value": frames_done / e2e_el, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "conv3x3 (%s), all layers"
+                     "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per step, all conv launches",
+                     "kernel": "conv3x3 (%s), all layers"
                      % {pp.PP_F32: "CUDA-core FP32", pp.PP_F32_TC: "tcgen05 3xTF32", pp.PP_BF16: "tcgen05 BF16"}[conv_dtype],
                      "peak_source": peak_note,
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames,

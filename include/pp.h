@@ -44,8 +44,10 @@ typedef enum {
 } pp_status;
 
 /* Arithmetic types.  PP_F32 / PP_BF16 name a precision everywhere; PP_F32_TC is accepted only
- * by pp_conv3x3 / pp_conv_pack_weights / pp_conv_packed_bytes / pp_conv_tile_count and selects
- * the FP32 conv on the tensor cores (3xTF32 split, FP32 activations and outputs). */
+ * by pp_scatter and the pp_conv_* calls and selects the FP32 conv on the tensor cores (3xTF32).
+ * Its activations are "split FP32": two planes [2][B][H+2][W+2][C] of float, plane 0 the values
+ * and plane 1 their TF32 remainders (x minus x with its 13 low mantissa bits cleared; see
+ * pp_tf32_split), so that the conv reads both parts of its A operand by TMA. */
 enum { PP_F32 = 0, PP_BF16 = 1, PP_F32_TC = 2 };
 
 /* Pillar grid.  Ranges are half-open [min, max).  nx * vx must span x, ny * vy must span y.
@@ -135,16 +137,19 @@ int pp_pointnet(const pp_geometry* g, int32_t batch, const float* pts, const int
 /* Stage 3: BEV scatter.  Writes the WHOLE padded canvas [B][ny+2][nx+2][64] (dtype PP_F32   */
 /* or PP_BF16, round to nearest even): interior pixel (iy, ix) gets feat[b][p] if            */
 /* pillar_of_cell[b][iy*nx+ix] = p >= 0, else zeros; the border is zero.  One coalesced pass, */
-/* so no separate clear is needed.                                                           */
+/* so no separate clear is needed.  PP_F32_TC writes the split FP32 canvas: the PP_F32 canvas */
+/* as plane 0 and its TF32 remainders as plane 1 ([2][B][ny+2][nx+2][64]).                   */
 int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
                const int32_t* pillar_of_cell, void* canvas, int32_t dtype, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Stage 4: one backbone layer, conv3x3 (zero pad 1, stride 1 or 2, no bias) + folded BN +    */
 /* ReLU, implicit GEMM over padded NHWC.                                                     */
-/*   in : [B][H+2][W+2][cin]  of dtype, border zero                                          */
+/*   in : [B][H+2][W+2][cin]  of dtype, border zero (PP_F32_TC: [2][B][H+2][W+2][cin] split  */
+/*        FP32, see PP_F32_TC)                                                               */
 /*   out: [B][Ho+2][Wo+2][cout] of dtype, Ho = (H-1)/stride + 1, Wo = (W-1)/stride + 1; only  */
-/*        the interior is written (the border must already be zero).                          */
+/*        the interior is written (the border must already be zero).  PP_F32_TC: both planes */
+/*        [2][B][Ho+2][Wo+2][cout] are written, plane 1 = TF32 remainders of plane 0.         */
 /*   w  : packed weights from pp_conv_pack_weights for the same dtype.                       */
 /*   scale_shift: device float [2][cout].                                                    */
 /* PP_F32: CUDA-core FP32 FMA.  PP_BF16: tcgen05 tensor cores, BF16 x BF16 -> FP32 in TMEM,   */
@@ -159,7 +164,7 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
 int pp_conv_tile_count(int32_t dtype);
 /* Shape of conv tile `tile` of `dtype`: output box bh x bw pixels (bh*bw = 128 on the tensor
  * cores; CUDA-core tiles report bh = 1, bw = pixels per tile), bn output channels, and whether
- * the kernel is persistent: 1 = one CTA per SM walking the tiles, TMA ring and two TMEM
+ * the kernel is persistent: 1 = one CTA per SM walking the tiles, TMA ring and TMEM
  * accumulators carried across tiles (the default for the tensor-core dtypes); 2 = the BF16
  * row-streaming kernel for 64 -> 64 channel layers (the default there: weights resident in
  * shared memory, each input row loaded once and every tap read as a row-shifted view; tile
@@ -185,6 +190,11 @@ int pp_conv_tune_save(const char* path);
 int pp_conv_tune_load(const char* path);
 /* Forgets every autotuned entry. */
 void pp_conv_tune_clear(void);
+
+/* TF32 remainder plane of n floats (device): lo[i] = x[i] - (x[i] with its 13 low mantissa
+ * bits cleared), exact in FP32 (the part a TF32 read of x[i] drops).  Turns an FP32 tensor into
+ * the split FP32 form of PP_F32_TC (x as plane 0, lo as plane 1).  x and lo may not overlap. */
+int pp_tf32_split(const float* x, float* lo, int64_t n, void* stream);
 
 /* Repacks float OIHW weights [cout][cin][3][3] (device) into the layout pp_conv3x3 expects
  * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,

@@ -147,6 +147,7 @@ _SIGS = {
     "pp_bn_fold": (ctypes.c_int, [_P, _I, ctypes.c_float, _P]),
     "pp_conv_autotune": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I,
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+    "pp_tf32_split": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "pp_conv_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "pp_conv_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "pp_conv_tune_clear": (None, []),
@@ -298,13 +299,15 @@ def pointnet(pts, npts, coord, num_pillars, pfn_w, scale_shift, geom, stream=Non
 
 
 def scatter(feat, pillar_of_cell, geom, dtype=PP_F32, stream=None):
-    """Returns the padded NHWC canvas [B, ny+2, nx+2, 64] (float32 or bfloat16)."""
+    """Returns the padded NHWC canvas [B, ny+2, nx+2, 64] (float32 or bfloat16); for
+    PP_F32_TC the split FP32 canvas [2, B, ny+2, nx+2, 64] (values, TF32 remainders)."""
     import torch
     _need_cuda(feat, pillar_of_cell)
     g = Geometry.of(geom)
     B = int(feat.shape[0])
-    tdt = torch.float32 if dtype == PP_F32 else torch.bfloat16
-    canvas = torch.empty((B, g.ny + 2, g.nx + 2, 64), dtype=tdt, device=feat.device)
+    tdt = torch.bfloat16 if dtype == PP_BF16 else torch.float32
+    shape = (B, g.ny + 2, g.nx + 2, 64)
+    canvas = torch.empty(((2,) if dtype == PP_F32_TC else ()) + shape, dtype=tdt, device=feat.device)
     _check(lib().pp_scatter(ctypes.byref(g), B, _ptr(feat), _ptr(pillar_of_cell), _ptr(canvas), dtype,
                             _stream(stream)))
     return canvas
@@ -332,24 +335,49 @@ def bn_fold(bn):
     return out
 
 
+def tf32_split(x, stream=None):
+    """pp_tf32_split: the TF32 remainder plane of a float32 CUDA tensor (same shape)."""
+    import torch
+    _need_cuda(x)
+    x = x.contiguous()
+    lo = torch.empty_like(x)
+    _check(lib().pp_tf32_split(_ptr(x), _ptr(lo), x.numel(), _stream(stream)))
+    return lo
+
+
+def split_f32(x, stream=None):
+    """A float32 tensor as split FP32 (the PP_F32_TC operand form): [2, *x.shape], plane 0 = x,
+    plane 1 = its TF32 remainders (computed by pp_tf32_split)."""
+    import torch
+    out = torch.empty((2,) + tuple(x.shape), dtype=torch.float32, device=x.device)
+    out[0].copy_(x)
+    _check(lib().pp_tf32_split(_ptr(out[0]), _ptr(out[1]), x.numel(), _stream(stream)))
+    return out
+
+
 def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=None, stream=None):
-    """x: padded NHWC [B, H+2, W+2, cin] (float32 for PP_F32 / PP_F32_TC, bfloat16 for PP_BF16).
-    Returns the padded output [B, Ho+2, Wo+2, cout] (border zero)."""
+    """x: padded NHWC [B, H+2, W+2, cin] (float32 for PP_F32, bfloat16 for PP_BF16; for
+    PP_F32_TC split FP32 [2, B, H+2, W+2, cin], see split_f32).  Returns the padded output
+    [B, Ho+2, Wo+2, cout] (border zero; [2, B, ...] split FP32 for PP_F32_TC)."""
     import torch
     _need_cuda(x, w_packed, scale_shift)
-    B, Hp, Wp, cin = (int(v) for v in x.shape)
+    split = dtype == PP_F32_TC
+    if split and x.dim() != 5:
+        raise PPError(PP_EINVAL, "PP_F32_TC conv takes split FP32 [2, B, H+2, W+2, cin]")
+    B, Hp, Wp, cin = (int(v) for v in x.shape[-4:])
     H, W = Hp - 2, Wp - 2
     Ho, Wo = (H - 1) // stride + 1, (W - 1) // stride + 1
     if out is None:
-        out = torch.zeros((B, Ho + 2, Wo + 2, cout), dtype=x.dtype, device=x.device)
+        out = torch.zeros(((2,) if split else ()) + (B, Ho + 2, Wo + 2, cout), dtype=x.dtype, device=x.device)
     _check(lib().pp_conv3x3(B, H, W, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
                             _ptr(out), tile, _stream(stream)))
     return out
 
 
 def conv_autotune(x, w_packed, scale_shift, cout, stride, dtype, out, reps=5):
-    """pp_conv_autotune on the layer shape of ``x`` (padded NHWC) -> (best tile, us per launch)."""
-    B, Hp, Wp, cin = (int(v) for v in x.shape)
+    """pp_conv_autotune on the layer shape of ``x`` (padded NHWC; split FP32 [2, B, ...] for
+    PP_F32_TC) -> (best tile, us per launch)."""
+    B, Hp, Wp, cin = (int(v) for v in x.shape[-4:])
     t, us = ctypes.c_int32(-1), ctypes.c_float(0)
     _check(lib().pp_conv_autotune(B, Hp - 2, Wp - 2, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed),
                                   _ptr(scale_shift), _ptr(out), reps, ctypes.byref(t), ctypes.byref(us)))

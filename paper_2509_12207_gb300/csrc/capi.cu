@@ -126,12 +126,21 @@ int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
   int st = check_geometry(g, &gg);
   if (st) return st;
   if (batch <= 0 || batch > 4096) return fail(PP_EINVAL, "scatter: batch out of range");
-  if (dtype != PP_F32 && dtype != PP_BF16) return fail(PP_EINVAL, "scatter: bad dtype");
+  if (dtype != PP_F32 && dtype != PP_BF16 && dtype != PP_F32_TC) return fail(PP_EINVAL, "scatter: bad dtype");
   if (!feat || !pillar_of_cell || !canvas) return fail(PP_EINVAL, "scatter: NULL buffer");
   if (!aligned16(feat) || !aligned16(canvas))
     return fail(PP_EINVAL, "scatter: feat and canvas must be 16-byte aligned");
   return scatter_launch(gg, batch, feat, pillar_of_cell, canvas, dtype,
                         static_cast<cudaStream_t>(stream));
+}
+
+int pp_tf32_split(const float* x, float* lo, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !lo))) return fail(PP_EINVAL, "tf32_split: bad argument");
+  if (n == 0) return PP_OK;
+  if (!aligned16(x) || !aligned16(lo)) return fail(PP_EINVAL, "tf32_split: x and lo must be 16-byte aligned");
+  const char *a = reinterpret_cast<const char*>(x), *b = reinterpret_cast<const char*>(lo);
+  if (a < b + n * 4 && b < a + n * 4) return fail(PP_EINVAL, "tf32_split: x and lo overlap");
+  return tf32_split_launch(x, lo, (size_t)n, static_cast<cudaStream_t>(stream));
 }
 
 int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,

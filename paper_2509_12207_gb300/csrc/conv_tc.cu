@@ -321,18 +321,24 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // The same implicit GEMM for FP32 activations, on the tensor cores with FP32-level accuracy:
 // every operand x is split into hi = x with its 13 low mantissa bits cleared (exactly a TF32
 // value) and lo = x - hi (exact in FP32, < 2^-10 |x|), and the product is accumulated as
-// hi*hi' + hi*lo' + lo*hi' (the dropped lo*lo' term is < 2^-20 of the product).  Weights come
-// pre-split from packing ([2][cout][9*cin]: hi plane, lo plane).  Activations are split in
-// shared memory: four converter warps wait for each TMA'd A tile (128 pixels x 32 channels,
-// 128-byte swizzle), rewrite it in place as hi and write lo at the same offsets of a second
-// buffer (an elementwise map, so the swizzle is preserved), fence the async proxy and arrive on
-// the stage's "converted" barrier; the MMA thread issues 3 tcgen05.mma.kind::tf32 (K=8) per
-// K step.  The tensor core's FP32 accumulation is not round-to-nearest, so long accumulation
-// chains drift: the MMA thread accumulates only `fold` K blocks into one of two TMEM buffers,
-// and four reducer warps add each finished buffer into FP32 registers (round to nearest) while
-// the MMAs fill the other buffer; the reducers then run the epilogue and store FP32.
-// 320 threads: warp 0 TMA, warp 1 TMEM allocation + MMA, warps 2-5 convert, warps 6-9 reduce
-// (TMEM lane quarters 2, 3, 0, 1).
+// hi*hi' + hi*lo' + lo*hi' (the dropped lo*lo' term is < 2^-20 of the product).  The tensor
+// core reads a TF32 operand from an FP32 word by dropping those 13 bits, so an FP32 tensor
+// already is its own hi part.  Weights come pre-split from packing ([2][cout][9*cin]: hi plane,
+// lo plane); activations travel as split FP32, two planes [2][B][H+2][W+2][C] (the values, then
+// their remainders lo), written by the producer of the tensor (the scatter, or the previous
+// conv's epilogue, which has the FP32 value in a register anyway), so the A remainder arrives by
+// TMA like the A tile itself.  The tensor core's FP32 accumulation is not round-to-nearest, so
+// long accumulation chains drift: the MMAs accumulate only `fold` K blocks into one TMEM buffer,
+// and reducer warps add each finished buffer into FP32 registers (round to nearest).
+
+// x - (x with its 13 low mantissa bits cleared): exact in FP32 (the cleared bits times the
+// exponent's unit); what a TF32 read of x drops.
+__device__ __forceinline__ float tf32_remainder(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float4 tf32_remainder4(float4 v) {
+  return make_float4(tf32_remainder(v.x), tf32_remainder(v.y), tf32_remainder(v.z), tf32_remainder(v.w));
+}
 
 template <int BN>
 __device__ __forceinline__ uint32_t idesc_tf32() {
@@ -348,232 +354,35 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
-struct TcArgsF32 {
-  ConvShape c;
-  int bh, bw, tiles_x, tiles_y, fold;
-  const float* ss;
-  float* out;
-};
-
-constexpr int kBK32 = 32;                        // fp32 channels per K block (128 bytes)
-constexpr uint32_t kA32Bytes = kBM * kBK32 * 4;  // 16 KiB
-
-template <int BN, int STAGES, bool S2>
-__global__ void __launch_bounds__(320, 1)
-conv3x3_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               TcArgsF32 args) {
-  constexpr uint32_t kBBytes = BN * kBK32 * 4;  // one plane
-  constexpr uint32_t kCols = 2 * BN;            // two accumulator buffers
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ unsigned s_abort;
-  if (threadIdx.x == 0) s_abort = tc_error_now();
-  __syncthreads();
-  if (s_abort != 0u) return;
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                             ~uintptr_t(1023));
-  uint8_t* sA = smem;                              // [STAGES][16K]  fp32, becomes hi
-  uint8_t* sAlo = sA + STAGES * kA32Bytes;         // [STAGES][16K]
-  uint8_t* sB = sAlo + STAGES * kA32Bytes;         // [STAGES][2][BN*128]  hi, lo
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * 2 * kBBytes);
-  uint64_t* conv = full + STAGES;
-  uint64_t* empty = conv + STAGES;
-  uint64_t* kdone = empty + STAGES;   // [2] a TMEM buffer holds a finished group of K blocks
-  uint64_t* kfree = kdone + 2;        // [2] the reducers have read that buffer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + 2);
-  float* s_ss = reinterpret_cast<float*>(tmem_slot + 4);  // [2][BN]
-
-  const ConvShape& c = args.c;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bx = blockIdx.x;
-  const int tx = bx % args.tiles_x;
-  const int ty = (bx / args.tiles_x) % args.tiles_y;
-  const int b = bx / (args.tiles_x * args.tiles_y);
-  const int n0 = blockIdx.y * BN;
-  const int oy0 = ty * args.bh, ox0 = tx * args.bw;
-  const int fold = args.fold;
-
-  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
-    s_ss[i] = args.ss[n0 + i];
-    s_ss[BN + i] = args.ss[c.cout + n0 + i];
-  }
-  if (warp == 0 && lane == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
-      mbar_init(&empty[s], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&kdone[i], 1);
-      mbar_init(&kfree[i], 128);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  const int kchunks = c.cin / kBK32;
-  const int KB = 9 * kchunks;
-  const int groups = (KB + fold - 1) / fold;
-  const int Hp2 = (c.H + 2) / 2;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) break;
-        const int tap = kb / kchunks, cc = kb % kchunks;
-        const int ky = tap / 3, kx = tap % 3;
-        mbar_expect_tx(&full[s], kA32Bytes + 2 * kBBytes);
-        if (S2)
-          tma_5d(sA + s * kA32Bytes, &tmA, &full[s], cc * kBK32, kx & 1, ox0 + (kx >> 1), ky & 1,
-                 b * Hp2 + oy0 + (ky >> 1));
-        else
-          tma_3d(sA + s * kA32Bytes, &tmA, &full[s], cc * kBK32, ox0 + kx,
-                 b * (c.H + 2) + oy0 + ky);
-        const int kk = tap * c.cin + cc * kBK32;
-        tma_3d(sB + s * 2 * kBBytes, &tmB, &full[s], kk, n0, 0);
-        tma_3d(sB + s * 2 * kBBytes + kBBytes, &tmB, &full[s], kk, n0, 1);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t id = idesc_tf32<BN>();
-      bool ok = true;
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        const int g = kb / fold, buf = g & 1;
-        const bool first = kb % fold == 0;
-        if (first && g >= 2 && !mbar_wait(&kfree[buf], (uint32_t)((g >> 1) - 1) & 1u, 16u)) break;
-        if (!mbar_wait(&conv[s], ph, 2u)) break;
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * BN);
-        const uint8_t* ahi = sA + s * kA32Bytes;
-        const uint8_t* alo = sAlo + s * kA32Bytes;
-        const uint8_t* bhi = sB + s * 2 * kBBytes;
-        const uint8_t* blo = bhi + kBBytes;
-#pragma unroll
-        for (int k = 0; k < kBK32 / 8; ++k) {
-          const uint64_t dahi = sdesc(ahi + k * 32), dalo = sdesc(alo + k * 32);
-          const uint64_t dbhi = sdesc(bhi + k * 32), dblo = sdesc(blo + k * 32);
-          mma_tf32(d, dahi, dbhi, id, (first && k == 0) ? 0u : 1u);
-          mma_tf32(d, dahi, dblo, id, 1u);
-          mma_tf32(d, dalo, dbhi, id, 1u);
-        }
-        mma_commit(&empty[s]);
-        if (kb % fold == fold - 1 || kb == KB - 1) mma_commit(&kdone[buf]);
-      }
-    }
-  } else if (warp < 6) {
-    // converters: 128 threads, 8 x 16 B of each 16 KiB A tile per thread
-    const int ct = threadIdx.x - 64;
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph, 8u)) break;
-      uint4* a = reinterpret_cast<uint4*>(sA + s * kA32Bytes);
-      uint4* lo = reinterpret_cast<uint4*>(sAlo + s * kA32Bytes);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int q = ct + 128 * i;
-        uint4 v = a[q];
-        uint4 h = make_uint4(v.x & 0xFFFFE000u, v.y & 0xFFFFE000u, v.z & 0xFFFFE000u, v.w & 0xFFFFE000u);
-        uint4 l;
-        l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
-        l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
-        l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
-        l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
-        a[q] = h;
-        lo[q] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
-    }
-  } else {
-    // reducers: fold each finished TMEM buffer into FP32 registers, then the epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
-    float acc[BN];
-#pragma unroll
-    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
-    bool ok = true;
-    for (int g = 0; g < groups && ok; ++g) {
-      const int buf = g & 1;
-      ok = mbar_wait(&kdone[buf], (uint32_t)(g >> 1) & 1u, 4u);
-      __syncwarp();
-      tc_fence_after();
-#pragma unroll
-      for (int j = 0; j < BN / 16; ++j) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + j * 16), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[j * 16 + i] += v[i];
-      }
-      tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
-    }
-    const int r = q * 32 + lane;
-    const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
-    if (ok && oy < c.Ho && ox < c.Wo) {
-      float4* dst = reinterpret_cast<float4*>(
-          args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0);
-#pragma unroll
-      for (int i = 0; i < BN / 4; ++i) {
-        const int n = 4 * i;
-        float4 t;
-        t.x = fmaxf(fmaf(acc[n + 0], s_ss[n + 0], s_ss[BN + n + 0]), 0.f);
-        t.y = fmaxf(fmaf(acc[n + 1], s_ss[n + 1], s_ss[BN + n + 1]), 0.f);
-        t.z = fmaxf(fmaf(acc[n + 2], s_ss[n + 2], s_ss[BN + n + 2]), 0.f);
-        t.w = fmaxf(fmaf(acc[n + 3], s_ss[n + 3], s_ss[BN + n + 3]), 0.f);
-        dst[i] = t;
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
-  }
-}
-
 // ---------------------------------------------------------------------------- persistent
 //
 // Persistent form of both tensor-core convs: one CTA per SM walks the output tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... (N tile innermost, so CTAs sharing an A tile run
-// side by side and the second read hits L2).  The TMA ring, the converters (3xTF32) and the
-// MMA thread run over the concatenated K blocks of all the CTA's tiles without draining, and
-// accumulation goes to two TMEM buffers in turn: while the reducer warps read one buffer (and,
-// at the end of a tile, apply BN + ReLU and store), the MMAs fill the other.  For BF16 a buffer
+// side by side and the second read hits L2).  The TMA ring and the MMA thread run over the
+// concatenated K blocks of all the CTA's tiles without draining, and
+// accumulation goes to TMEM buffers in turn (four where 512 columns hold them, else two):
+// while the reducer warps read one buffer (and, at the end of a tile, apply BN + ReLU and
+// store), the MMAs fill the next.  For BF16 a buffer
 // holds a whole tile's accumulation and a ring stage carries KPS = 2 K blocks (8 MMAs per
 // handshake); for 3xTF32 a buffer holds `fold` K blocks, which the reducers add into FP32
 // registers, and each K step is two MMAs: A_hi x [B_hi | B_lo] (N = 2 BN, the two products land
 // side by side in TMEM) and A_lo x B_hi (N = BN, into the first half); the reducers sum the
 // halves.  Loop counters advance incrementally (no division in the steady state) and shared
-// memory descriptors are built once and offset by addition.
+// memory descriptors are built once and offset by addition.  192 threads: warp 0 TMA, warp 1
+// TMEM allocation + MMA, warps 2-5 reduce and store (TMEM lane quarters 2, 3, 0, 1).
 
 struct PArgs {
   ConvShape c;
   int bh, bw, tiles_x, tiles_y, tiles_n, total, fold;
+  size_t plane;  // 3xTF32: elements from the output's value plane to its remainder plane
   const float* ss;
   void* out;
 };
 
 template <int MODE, int BN, int STAGES, int KPS, bool S2>
-__global__ void __launch_bounds__(MODE == 1 ? 320 : 192, 1)
-conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            PArgs args) {
+__global__ void __launch_bounds__(192, 1)
+conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+            const __grid_constant__ CUtensorMap tmB, PArgs args) {
   constexpr int BK = MODE == 1 ? 32 : 64;                  // channels per K block (128 B rows)
   constexpr uint32_t kA = 128 * 128;                       // A tile bytes of one K block
   constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
@@ -582,8 +391,11 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kStageA = KPS * kAK;
   constexpr uint32_t kStageB = KPS * kBK;
   constexpr int NACC = MODE == 1 ? 2 * BN : BN;            // TMEM columns per accumulator buffer
-  constexpr uint32_t kCols = 2 * NACC;
-  constexpr int kRed0 = MODE == 1 ? 6 : 2;                 // first reducer warp
+  // accumulator buffers in TMEM (512 columns): four where they fit, so that the MMAs can run
+  // up to three groups ahead of the reducers while they store a finished tile
+  constexpr int NBUF = 512 / NACC >= 4 ? 4 : 2;
+  constexpr uint32_t kCols = NBUF * NACC;
+  constexpr int kRed0 = 2;                                 // first reducer warp
   extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned s_abort;
   if (threadIdx.x == 0) s_abort = tc_error_now();
@@ -594,11 +406,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
-  uint64_t* conv = full + STAGES;
-  uint64_t* empty = conv + STAGES;
+  uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
-  uint64_t* kfree = kdone + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + 2);
+  uint64_t* kfree = kdone + NBUF;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + NBUF);
   float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);  // [cout] folded BN scale
   float* s_shift = s_scale + args.c.cout;                    // [cout] folded BN shift
 
@@ -616,16 +427,16 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NBUF; ++i) {
       mbar_init(&kdone[i], 1);
       mbar_init(&kfree[i], 128);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    if (MODE == 1) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmAlo) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
   }
   if (warp == 1) {
@@ -662,14 +473,19 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
           const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
           if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
-          mbar_expect_tx(&full[s], (uint32_t)nk * (kA + kBK));
+          mbar_expect_tx(&full[s], (uint32_t)nk * (kAK + kBK));
           for (int j = 0; j < nk; ++j) {
             uint8_t* a = sA + s * kStageA + j * kAK;
-            if (S2)
+            if (S2) {
               tma_5d(a, &tmA, &full[s], cc * BK, kx & 1, ox0 + (kx >> 1), ky & 1,
                      b * Hp2 + oy0 + (ky >> 1));
-            else
+              if (MODE == 1)
+                tma_5d(a + kA, &tmAlo, &full[s], cc * BK, kx & 1, ox0 + (kx >> 1), ky & 1,
+                       b * Hp2 + oy0 + (ky >> 1));
+            } else {
               tma_3d(a, &tmA, &full[s], cc * BK, ox0 + kx, b * (c.H + 2) + oy0 + ky);
+              if (MODE == 1) tma_3d(a + kA, &tmAlo, &full[s], cc * BK, ox0 + kx, b * (c.H + 2) + oy0 + ky);
+            }
             uint8_t* bb = sB + s * kStageB + j * kBK;
             if (MODE == 1) {
               tma_3d(bb, &tmB, &full[s], kk, n0, 0);
@@ -698,9 +514,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
         for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
           const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
-          const int buf = gg & 1;
-          if (inq == 0 && gg >= 2 && !mbar_wait(&kfree[buf], (uint32_t)((gg >> 1) - 1) & 1u, 16u)) { ok = false; break; }
-          if (!mbar_wait(MODE == 1 ? &conv[s] : &full[s], ph, 2u)) { ok = false; break; }
+          const int buf = gg & (NBUF - 1);
+          if (inq == 0 && gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, 2u)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * NACC);
           const uint64_t da = dA0 + ((uint64_t)(s * kStageA) >> 4);
@@ -733,34 +549,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
       }
     }
-  } else if (MODE == 1 && warp < kRed0) {
-    const int ct = threadIdx.x - 64;
-    int s = 0;
-    uint32_t ph = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
-      for (int kb = 0; kb < KB; ++kb) {
-        if (!mbar_wait(&full[s], ph, 8u)) { ok = false; break; }
-        uint4* a = reinterpret_cast<uint4*>(sA + s * kStageA);
-        uint4* lo = reinterpret_cast<uint4*>(sA + s * kStageA + kA);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int q = ct + 128 * i;
-          // the tensor core reads a TF32 operand from an FP32 word by dropping its 13 low
-          // mantissa bits, so the untouched tile already is A_hi; only the remainder is written
-          const uint4 v = a[q];
-          uint4 l;
-          l.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(v.x & 0xFFFFE000u));
-          l.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(v.y & 0xFFFFE000u));
-          l.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(v.z & 0xFFFFE000u));
-          l.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(v.w & 0xFFFFE000u));
-          lo[q] = l;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
-        if (++s == STAGES) { s = 0; ph ^= 1u; }
-      }
-    }
   } else if (warp >= kRed0) {
     const int q = warp & 3;  // TMEM lane quarter this warp may read
     const int r = q * 32 + lane;
@@ -779,8 +567,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int i = 0; i < BN; ++i) acc[i] = 0.f;
         for (int g = 0; g < gpt; ++g, ++gg) {
-          const int buf = gg & 1;
-          ok = mbar_wait(&kdone[buf], (uint32_t)(gg >> 1) & 1u, 4u);
+          const int buf = gg & (NBUF - 1);
+          ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
           __syncwarp();
           if (!ok) break;
           tc_fence_after();
@@ -797,7 +585,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
         }
         if (ok && in_range) {
+          // value plane and remainder plane (split FP32, the next layer's A operand)
           float4* dst = reinterpret_cast<float4*>(static_cast<float*>(args.out) + pix * c.cout + n0);
+          float4* dlo = reinterpret_cast<float4*>(static_cast<float*>(args.out) + args.plane + pix * c.cout + n0);
 #pragma unroll
           for (int i = 0; i < BN / 4; ++i) {
             const int n = n0 + 4 * i;
@@ -807,11 +597,12 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             u.z = fmaxf(fmaf(acc[4 * i + 2], s_scale[n + 2], s_shift[n + 2]), 0.f);
             u.w = fmaxf(fmaf(acc[4 * i + 3], s_scale[n + 3], s_shift[n + 3]), 0.f);
             dst[i] = u;
+            dlo[i] = tf32_remainder4(u);
           }
         }
       } else {
-        const int buf = gg & 1;
-        ok = mbar_wait(&kdone[buf], (uint32_t)(gg >> 1) & 1u, 4u);
+        const int buf = gg & (NBUF - 1);
+        ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
         __syncwarp();
         if (!ok) break;
         tc_fence_after();
@@ -1201,106 +992,13 @@ int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfl
   return fail(PP_EINVAL, "conv bf16: no kernel for tile %d", tile);
 }
 
-namespace {
-
-struct TileF32TC {
-  int bh, bw, bn, stages;
-};
-// bh*bw must be 128; stage = 32 KiB of A (fp32 + lo) + 2 x BN x 128 B of B (hi, lo).
-constexpr TileF32TC kTilesF32TC[] = {
-    {8, 16, 64, 4}, {4, 32, 64, 4}, {16, 8, 64, 4}, {2, 64, 64, 4}, {1, 128, 64, 4},
-    {8, 16, 128, 3}, {4, 32, 128, 3}, {16, 8, 128, 3},
-};
-
-template <int BN, int STAGES>
-constexpr size_t smem_bytes_f32() {
-  return 1024 + (size_t)STAGES * (2 * kA32Bytes + 2 * BN * kBK32 * 4) + (3 * STAGES + 4) * 8 + 16 +
-         2 * BN * sizeof(float);
-}
-
-template <int BN, int STAGES, bool S2>
-int launch_tf32x3(const CUtensorMap& a, const CUtensorMap& w, const TcArgsF32& args, dim3 grid,
-                  cudaStream_t s) {
-  constexpr size_t bytes = smem_bytes_f32<BN, STAGES>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tf32x3<BN, STAGES, S2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_status(e, "conv tf32x3 smem attribute");
-    attr_set = true;
-  }
-  conv3x3_tf32x3<BN, STAGES, S2><<<grid, 320, bytes, s>>>(a, w, args);
-  return cuda_status(cudaGetLastError(), "conv tf32x3 launch");
-}
-
-
-
-}  // namespace
-
-int conv_f32tc_tile_count() { return (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0])) + conv_tcp_tile_count(1); }
+int conv_f32tc_tile_count() { return conv_tcp_tile_count(1); }
 
 int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
                       float* out, int tile, cudaStream_t s) {
-  auto enc = encode_fn();
-  if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
-  if (c.cin % kBK32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
+  if (c.cin % 32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
   if (tile < 0) tile = tuned_tile(PP_F32_TC, c);
-  const int n_old = (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0]));
-  if (tile < 0 || tile >= n_old) return conv_tcp_launch(1, c, in, w_split, ss, out, tile < 0 ? -1 : tile - n_old, s);
-  if (tile < 0 || tile >= conv_f32tc_tile_count() || c.cout % kTilesF32TC[tile].bn)
-    return fail(PP_EINVAL, "conv f32 tensor: tile %d unsupported for cout %d", tile, c.cout);
-  const TileF32TC t = kTilesF32TC[tile];
-  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w_split)) & 15u)
-    return fail(PP_EINVAL, "conv f32 tensor: operands must be 16-byte aligned");
-  const int Hp = c.H + 2, Wp = c.W + 2;
-  CUtensorMap ta, tw;
-  CUresult r;
-  if (c.stride == 1) {
-    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
-    cuuint64_t strides[2] = {(cuuint64_t)c.cin * 4, (cuuint64_t)Wp * c.cin * 4};
-    cuuint32_t box[3] = {(cuuint32_t)kBK32, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
-    cuuint32_t es[3] = {1, 1, 1};
-    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(in), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
-    cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
-    cuuint64_t strides[4] = {(cuuint64_t)c.cin * 4, (cuuint64_t)c.cin * 8,
-                             (cuuint64_t)Wp * c.cin * 4, (cuuint64_t)Wp * c.cin * 8};
-    cuuint32_t box[5] = {(cuuint32_t)kBK32, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    r = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(in), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
-  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv f32 tensor: activation tensor map (%d)", (int)r);
-  {
-    const int K = 9 * c.cin;
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)c.cout, 2};
-    cuuint64_t strides[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * c.cout * 4};
-    cuuint32_t box[3] = {(cuuint32_t)kBK32, (cuuint32_t)t.bn, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    r = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(w_split), dims, strides, box,
-            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
-  if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "conv f32 tensor: weight tensor map (%d)", (int)r);
-  TcArgsF32 args;
-  args.c = c;
-  args.bh = t.bh;
-  args.bw = t.bw;
-  args.tiles_x = (c.Wo + t.bw - 1) / t.bw;
-  args.tiles_y = (c.Ho + t.bh - 1) / t.bh;
-  args.fold = 2;  // K blocks per TMEM accumulation chain (each is 3 x 4 MMAs)
-  args.ss = ss;
-  args.out = out;
-  const dim3 grid((unsigned)(args.tiles_x * args.tiles_y * c.batch), (unsigned)(c.cout / t.bn));
-  const bool s2 = c.stride == 2;
-  if (t.bn == 64 && t.stages == 4)
-    return s2 ? launch_tf32x3<64, 4, true>(ta, tw, args, grid, s) : launch_tf32x3<64, 4, false>(ta, tw, args, grid, s);
-  if (t.bn == 128 && t.stages == 3)
-    return s2 ? launch_tf32x3<128, 3, true>(ta, tw, args, grid, s) : launch_tf32x3<128, 3, false>(ta, tw, args, grid, s);
-  return fail(PP_EINVAL, "conv f32 tensor: no kernel for tile %d", tile);
+  return conv_tcp_launch(1, c, in, w_split, ss, out, tile, s);
 }
 
 namespace {
@@ -1331,7 +1029,7 @@ template <int MODE, int BN>
 constexpr size_t p_smem() {
   return 1024 + (size_t)p_stages<MODE, BN>() * p_kps<MODE, BN>() *
                     ((MODE == 1 ? 2 : 1) * 16384 + (MODE == 1 ? 2 : 1) * BN * 128) +
-         (3 * p_stages<MODE, BN>() + 4) * 8 + 16;
+         (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
 
 int num_sms() {
@@ -1346,7 +1044,8 @@ int num_sms() {
 }
 
 template <int MODE, int BN, bool S2>
-int launch_p(const CUtensorMap& a, const CUtensorMap& w, const PArgs& args, cudaStream_t s) {
+int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
+             cudaStream_t s) {
   constexpr int ST = p_stages<MODE, BN>();
   constexpr int KPS = p_kps<MODE, BN>();
   constexpr size_t bytes = p_smem<MODE, BN>() + 2 * 1024 * sizeof(float);  // + folded BN (cout <= 1024)
@@ -1358,7 +1057,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& w, const PArgs& args, cuda
     attr_set = true;
   }
   const int grid = args.total < num_sms() ? args.total : num_sms();
-  conv3x3_tcp<MODE, BN, ST, KPS, S2><<<grid, MODE == 1 ? 320 : 192, bytes, s>>>(a, w, args);
+  conv3x3_tcp<MODE, BN, ST, KPS, S2><<<grid, 192, bytes, s>>>(a, alo, w, args);
   return cuda_status(cudaGetLastError(), "persistent conv launch");
 }
 
@@ -1381,8 +1080,8 @@ int pick_tile_p(const ConvShape& c, const TileP* tiles, int n) {
 
 }  // namespace
 
-// mode 0: BF16 in/out, weights [cout][9cin] bf16; mode 1: FP32 in/out via 3xTF32, weights
-// [2][cout][9cin] fp32 (hi, lo planes).
+// mode 0: BF16 in/out, weights [cout][9cin] bf16; mode 1: split FP32 in/out ([2][B][H+2][W+2][C]:
+// values, TF32 remainders) via 3xTF32, weights [2][cout][9cin] fp32 (hi, lo planes).
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
                     void* out, int ptile, cudaStream_t s) {
   auto enc = encode_fn();
@@ -1399,24 +1098,30 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   const size_t el = mode == 1 ? 4 : 2;
   const CUtensorMapDataType dt = mode == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const int Hp = c.H + 2, Wp = c.W + 2;
-  CUtensorMap ta, tw;
-  CUresult r;
-  if (c.stride == 1) {
-    cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
-    cuuint64_t strides[2] = {(cuuint64_t)c.cin * el, (cuuint64_t)Wp * c.cin * el};
-    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
-    cuuint32_t es[3] = {1, 1, 1};
-    r = enc(&ta, dt, 3, const_cast<void*>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
-    cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
-    cuuint64_t strides[4] = {(cuuint64_t)c.cin * el, (cuuint64_t)c.cin * 2 * el,
-                             (cuuint64_t)Wp * c.cin * el, (cuuint64_t)Wp * c.cin * 2 * el};
-    cuuint32_t box[5] = {(cuuint32_t)BK, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    r = enc(&ta, dt, 5, const_cast<void*>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUtensorMap ta, talo, tw;
+  CUresult r = CUDA_SUCCESS;
+  for (int plane = 0; plane < (mode == 1 ? 2 : 1) && r == CUDA_SUCCESS; ++plane) {
+    const size_t in_plane = c.in_plane ? c.in_plane : (size_t)c.batch * Hp * Wp * c.cin;
+    void* base = static_cast<char*>(const_cast<void*>(in)) + (size_t)plane * in_plane * el;
+    CUtensorMap* m = plane ? &talo : &ta;
+    if (c.stride == 1) {
+      cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
+      cuuint64_t strides[2] = {(cuuint64_t)c.cin * el, (cuuint64_t)Wp * c.cin * el};
+      cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
+      cuuint32_t es[3] = {1, 1, 1};
+      r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      cuuint64_t dims[5] = {(cuuint64_t)c.cin, 2, (cuuint64_t)Wp / 2, 2, (cuuint64_t)(Hp / 2) * c.batch};
+      cuuint64_t strides[4] = {(cuuint64_t)c.cin * el, (cuuint64_t)c.cin * 2 * el,
+                               (cuuint64_t)Wp * c.cin * el, (cuuint64_t)Wp * c.cin * 2 * el};
+      cuuint32_t box[5] = {(cuuint32_t)BK, 1, (cuuint32_t)t.bw, 1, (cuuint32_t)t.bh};
+      cuuint32_t es[5] = {1, 1, 1, 1, 1};
+      r = enc(m, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
   }
+  if (mode != 1) talo = ta;
   if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: activation tensor map (%d)", (int)r);
   {
     const int K = 9 * c.cin;
@@ -1438,17 +1143,20 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
   args.fold = 2;
+  args.plane = c.out_plane ? c.out_plane : (size_t)c.batch * (c.Ho + 2) * (c.Wo + 2) * c.cout;
   args.ss = ss;
   args.out = out;
   const bool s2 = c.stride == 2;
+#define PP_P(M, N) return s2 ? launch_p<M, N, true>(ta, talo, tw, args, s) : launch_p<M, N, false>(ta, talo, tw, args, s)
   if (mode == 1) {
-    if (t.bn == 64) return s2 ? launch_p<1, 64, true>(ta, tw, args, s) : launch_p<1, 64, false>(ta, tw, args, s);
-    if (t.bn == 128) return s2 ? launch_p<1, 128, true>(ta, tw, args, s) : launch_p<1, 128, false>(ta, tw, args, s);
+    if (t.bn == 64) PP_P(1, 64);
+    if (t.bn == 128) PP_P(1, 128);
   } else {
-    if (t.bn == 64) return s2 ? launch_p<0, 64, true>(ta, tw, args, s) : launch_p<0, 64, false>(ta, tw, args, s);
-    if (t.bn == 128) return s2 ? launch_p<0, 128, true>(ta, tw, args, s) : launch_p<0, 128, false>(ta, tw, args, s);
-    if (t.bn == 256) return s2 ? launch_p<0, 256, true>(ta, tw, args, s) : launch_p<0, 256, false>(ta, tw, args, s);
+    if (t.bn == 64) PP_P(0, 64);
+    if (t.bn == 128) PP_P(0, 128);
+    if (t.bn == 256) PP_P(0, 256);
   }
+#undef PP_P
   return fail(PP_EINVAL, "persistent conv: no kernel for tile %d", ptile);
 }
 
@@ -1539,10 +1247,9 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   if (dtype == PP_F32_TC) {
-    const int n0 = (int)(sizeof(kTilesF32TC) / sizeof(kTilesF32TC[0]));
-    if (tile < 0 || tile >= n0 + kNPF) return PP_EINVAL;
-    if (tile < n0) { *bh = kTilesF32TC[tile].bh; *bw = kTilesF32TC[tile].bw; *bn = kTilesF32TC[tile].bn; *persistent = 0; }
-    else { const TileP& t = kTilesPF[tile - n0]; *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1; }
+    if (tile < 0 || tile >= kNPF) return PP_EINVAL;
+    const TileP& t = kTilesPF[tile];
+    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1;
     return PP_OK;
   }
   return PP_EINVAL;

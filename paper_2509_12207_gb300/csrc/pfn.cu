@@ -79,10 +79,18 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
   feat[q * 64 + lane + 32] = m1;
 }
 
-// FP32 canvas: 16 chunks of 4 channels per pixel.
+// x minus x with its 13 low mantissa bits cleared (exact in FP32): what a TF32 read drops.
+__device__ __forceinline__ float tf32_rem(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float4 tf32_rem4(float4 v) {
+  return make_float4(tf32_rem(v.x), tf32_rem(v.y), tf32_rem(v.z), tf32_rem(v.w));
+}
+
+// FP32 canvas: 16 chunks of 4 channels per pixel; with `lo`, also the TF32 remainder plane.
 __global__ void bev_scatter_f32(Geom g, int batch, const float4* __restrict__ feat,
                                 const int* __restrict__ pillar_of_cell,
-                                float4* __restrict__ canvas) {
+                                float4* __restrict__ canvas, float4* __restrict__ lo) {
   const int Wp = g.nx + 2, Hp = g.ny + 2;
   const size_t total = (size_t)batch * Hp * Wp * 16;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -99,7 +107,18 @@ __global__ void bev_scatter_f32(Geom g, int batch, const float4* __restrict__ fe
       if (p >= 0) val = feat[((size_t)b * g.P + p) * 16 + chunk];
     }
     canvas[t] = val;
+    if (lo) lo[t] = tf32_rem4(val);
   }
+}
+
+__global__ void tf32_split_kernel(const float4* __restrict__ x, float4* __restrict__ lo, size_t n4) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    lo[i] = tf32_rem4(x[i]);
+}
+
+__global__ void tf32_split_tail(const float* __restrict__ x, float* __restrict__ lo, size_t from, size_t n) {
+  const size_t i = from + threadIdx.x;
+  if (i < n) lo[i] = tf32_rem(x[i]);
 }
 
 // BF16 canvas: 8 chunks of 8 channels (16 bytes) per pixel, round to nearest even.
@@ -158,19 +177,32 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
 }
 
 int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
-                   void* canvas, int dtype, cudaStream_t s) {
+                   void* canvas, int dtype, cudaStream_t s, size_t plane) {
   const size_t pixels = (size_t)batch * (g.ny + 2) * (g.nx + 2);
-  const size_t chunks = pixels * (dtype == PP_F32 ? 16 : 8);
+  const size_t chunks = pixels * (dtype == PP_BF16 ? 8 : 16);
   size_t blocks = (chunks + 255) / 256;
   const size_t cap = (size_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
-  if (dtype == PP_F32)
-    bev_scatter_f32<<<(unsigned)blocks, 256, 0, s>>>(g, batch, (const float4*)feat,
-                                                     pillar_of_cell, (float4*)canvas);
+  if (dtype == PP_F32 || dtype == PP_F32_TC)
+    bev_scatter_f32<<<(unsigned)blocks, 256, 0, s>>>(
+        g, batch, (const float4*)feat, pillar_of_cell, (float4*)canvas,
+        dtype == PP_F32_TC ? (float4*)canvas + (plane ? plane / 4 : chunks) : nullptr);
   else
     bev_scatter_bf16<<<(unsigned)blocks, 256, 0, s>>>(g, batch, (const float4*)feat,
                                                       pillar_of_cell, (uint4*)canvas);
   return cuda_status(cudaGetLastError(), "scatter launch");
+}
+
+int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s) {
+  const size_t n4 = n / 4;
+  if (n4) {
+    size_t blocks = (n4 + 255) / 256;
+    const size_t cap = (size_t)sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+    tf32_split_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4*)x, (float4*)lo, n4);
+  }
+  if (n % 4) tf32_split_tail<<<1, 4, 0, s>>>(x, lo, n4 * 4, n);
+  return cuda_status(cudaGetLastError(), "tf32 split launch");
 }
 
 }  // namespace pp

@@ -179,10 +179,12 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   PP_ALLOC(pts_, (size_t)B_ * g.P * 32 * sizeof(float4));
   PP_ALLOC(vox_ws_, vox_workspace_bytes(g, B_, cap_));
   PP_ALLOC(feat_, (size_t)B_ * g.P * 64 * sizeof(float));
-  PP_ALLOC(canvas_, (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt);
+  // split FP32 (3xTF32 convs): every conv operand carries its TF32 remainder plane
+  const size_t planes = m->conv_dtype == PP_F32_TC ? 2 : 1;
+  PP_ALLOC(canvas_, planes * B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt);
   for (const LayerSpec& L : m->layers) {
     void* a = nullptr;
-    const size_t n = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
+    const size_t n = planes * B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
     PP_ALLOC(a, n);
     act_.push_back(a);
     // borders stay zero forever: convs write interiors only
@@ -265,11 +267,18 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
                       pts_, vw_, s, tab_dev_->src);
   if (!st) st = pfn_launch(g, n, pts_, npts_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
-  if (!st) st = scatter_launch(g, n, feat_, poc_, canvas_, m.precision, s);
+  const bool split = m.conv_dtype == PP_F32_TC;
+  if (!st)
+    st = scatter_launch(g, n, feat_, poc_, canvas_, split ? PP_F32_TC : m.precision, s,
+                        split ? (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 : 0);
   const void* x = canvas_;
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];
     ConvShape c{n, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
+    if (split) {  // planes are laid out for the unit's capacity, not for this batch
+      c.in_plane = (size_t)B_ * (L.H + 2) * (L.W + 2) * L.cin;
+      c.out_plane = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout;
+    }
     if (m.conv_dtype == PP_F32)
       st = conv_f32_launch(c, (const float*)x, (const float*)m.conv_w[l], m.conv_ss[l],
                            (float*)act_[l], -1, s);

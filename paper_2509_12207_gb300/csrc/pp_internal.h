@@ -51,12 +51,19 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,
                const int* num_pillars, const float* pfn_w, const float* scale_shift,
                float* feat, cudaStream_t s);
+// lo[i] = TF32 remainder of x[i] (x, lo 16-byte aligned when n >= 4).
+int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s);
+// PP_F32_TC: `plane` = elements between the canvas's value and remainder planes (0 = this
+// batch's plane size).
 int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
-                   void* canvas, int dtype, cudaStream_t s);
+                   void* canvas, int dtype, cudaStream_t s, size_t plane = 0);
 
 // ---- conv (conv_simt.cu, conv_tc.cu)
 struct ConvShape {
   int batch, H, W, cin, cout, stride, Ho, Wo;
+  // split FP32 (PP_F32_TC): elements between the value and remainder planes of the input and
+  // the output; 0 = this batch's plane size (planes packed for exactly `batch` frames)
+  size_t in_plane = 0, out_plane = 0;
 };
 int conv_f32_launch(const ConvShape& c, const float* in, const float* w_kn, const float* ss,
                     float* out, int tile, cudaStream_t s);

@@ -47,3 +47,11 @@ def bf16_emulated_backbone(canvas, conv_w, conv_bn, layers):
     for (_ci, _co, s), w, bn in zip(layers, conv_w, conv_bn):
         x = bf16_round(O.conv3x3_bn_relu(x, bf16_round(w), bn, s))
     return x
+
+
+def tf32_remainder(a):
+    """x - (x with its 13 low mantissa bits cleared), in float32 (exact): the part of x a TF32
+    read drops, computed from the bit pattern on the host."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    hi = (a.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    return (a - hi).astype(np.float32)

@@ -13,7 +13,7 @@ import pytest
 from oracle import pillars as O
 from pp_synth import (GEOM_FULL, GEOM_SMALL, Geometry, clustered_cloud, config_points,
                       pillar_weights, uniform_cloud, BACKBONE_SMALL)
-from tests._util import BF16_TOL, FP32_TOL, rel_err
+from tests._util import tf32_remainder, BF16_TOL, FP32_TOL, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -144,6 +144,33 @@ def test_pointnet_and_scatter(g, cfg):
         if dt == pp.PP_BF16:
             want = want.to(torch.bfloat16).float()
         assert np.array_equal(c[1:-1, 1:-1], want.numpy())
+    # split FP32 canvas (the 3xTF32 conv operand): plane 0 = the FP32 canvas, plane 1 = its
+    # TF32 remainders, border zero in both
+    f32c = pp.scatter(feat, v["pillar_of_cell"], g, dtype=pp.PP_F32)
+    split = pp.scatter(feat, v["pillar_of_cell"], g, dtype=pp.PP_F32_TC)
+    torch.cuda.synchronize()
+    assert tuple(split.shape) == (2,) + tuple(f32c.shape)
+    assert torch.equal(split[0], f32c)
+    assert np.array_equal(split[1].cpu().numpy(), tf32_remainder(f32c.cpu().numpy()))
+
+
+def test_tf32_split_exact():
+    """pp_tf32_split against the bit-pattern definition, on values that exercise every case:
+    signs, zeros, subnormals, powers of two, values whose low bits are all set, and a length
+    that leaves a tail after the 4-wide main loop."""
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(1000).astype(np.float32) * 10,
+                        np.array([0.0, -0.0, 1.0, -2.0, 1e-40, -3e-39, 2.0 ** -126, 3.4e38], np.float32),
+                        (np.arange(1, 40, dtype=np.uint32) | np.uint32(0x3F801FFF)).view(np.float32)])
+    for n in (v.size, v.size - 1, v.size - 2, 3, 1):
+        x = torch.from_numpy(v[:n].copy()).to(DEV)
+        lo = pp.tf32_split(x)
+        torch.cuda.synchronize()
+        want = tf32_remainder(v[:n])
+        assert np.array_equal(lo.cpu().numpy().view(np.uint32), want.view(np.uint32)), n
+        # plane 0 + plane 1 reproduces x exactly
+        hi = (v[:n].view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+        assert np.array_equal(hi + lo.cpu().numpy(), v[:n])
 
 
 def test_scatter_batched_bf16_rounding():
@@ -206,12 +233,13 @@ def test_conv_f32_tensor_cores(shape):
     """FP32 conv on the tensor cores (3xTF32 split) meets the FP32 tolerance on every tile."""
     B, H, W, cin, cout, s = shape
     xp, w, bn = _conv_case(B, H, W, cin, cout, s, seed=H * W + cin + 2)
-    x_d = torch.from_numpy(xp).to(DEV)
+    x_d = pp.split_f32(torch.from_numpy(xp).to(DEV))      # split FP32 operand [2, B, ...]
+    assert np.array_equal(x_d[1].cpu().numpy(), tf32_remainder(xp))
     wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_F32_TC)
     ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
     refs = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
     n_tiles = pp.conv_tile_count(pp.PP_F32_TC)
-    assert n_tiles >= 8
+    assert n_tiles >= 7
     for tile in list(range(n_tiles)) + [-1]:
         if tile >= 0 and cout % pp.conv_tile_info(pp.PP_F32_TC, tile)[2]:
             continue
@@ -219,9 +247,13 @@ def test_conv_f32_tensor_cores(shape):
         torch.cuda.synchronize()
         assert pp.device_error() == 0
         o = out.cpu().numpy()
+        # plane 1 is exactly the TF32 remainder of plane 0 (the next layer's A remainder)
+        assert np.array_equal(o[1], tf32_remainder(o[0])), tile
         for b in range(B):
-            assert rel_err(o[b, 1:-1, 1:-1], refs[b]) <= FP32_TOL, (tile, b)
-            assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
+            assert rel_err(o[0, b, 1:-1, 1:-1], refs[b]) <= FP32_TOL, (tile, b)
+            for q in (0, 1):
+                ob = o[q, b]
+                assert not ob[0].any() and not ob[-1].any() and not ob[:, 0].any() and not ob[:, -1].any()
 
 
 def _bf16(a):
@@ -285,11 +317,12 @@ def test_conv_autotune_then_library_choice(dtype):
     if dtype == pp.PP_BF16:
         x_d = _bf16(xp).to(DEV)
     else:
-        x_d = torch.from_numpy(xp).to(DEV)
+        x_d = pp.split_f32(torch.from_numpy(xp).to(DEV))
     wp = pp.pack_conv_weights(torch.from_numpy(w).to(DEV), dtype)
     ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
     Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
-    out = torch.zeros((B, Ho + 2, Wo + 2, cout), dtype=x_d.dtype, device=DEV)
+    planes = (2,) if dtype == pp.PP_F32_TC else ()
+    out = torch.zeros(planes + (B, Ho + 2, Wo + 2, cout), dtype=x_d.dtype, device=DEV)
     tile, us = pp.conv_autotune(x_d, wp, ss, cout, s, dtype, out)
     assert 0 <= tile < pp.conv_tile_count(dtype) and us > 0
     explicit = pp.conv3x3(x_d, wp, ss, cout, s, dtype=dtype, tile=tile)
@@ -297,7 +330,7 @@ def test_conv_autotune_then_library_choice(dtype):
     torch.cuda.synchronize()
     assert torch.equal(explicit, chosen)
     ref = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
-    o = chosen.float().cpu().numpy()
+    o = (chosen[0] if dtype == pp.PP_F32_TC else chosen).float().cpu().numpy()
     for b in range(B):
         tol = FP32_TOL if dtype == pp.PP_F32_TC else BF16_TOL
         assert rel_err(o[b, 1:-1, 1:-1], ref[b]) <= tol
