@@ -221,12 +221,14 @@ def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=20, tile=-1):
         ss = torch.from_numpy(pp.bn_fold(bn)).cuda()
         Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
         out = torch.zeros(planes + (batch, Ho + 2, Wo + 2, co), dtype=dt, device="cuda")
-        pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile)
+        # stream-K workspace made once, outside the captured launches (a release unit owns one)
+        ws = pp.conv_workspace(batch, H, W, ci, co, s, prec) if prec == pp.PP_F32_TC else None
+        pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile, workspace=ws)
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             for _ in range(reps):
-                pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile)
+                pp.conv3x3(x, wp, ss, co, s, dtype=prec, out=out, tile=tile, workspace=ws)
         graph.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

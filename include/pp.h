@@ -161,6 +161,22 @@ int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
 int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
                int32_t dtype, const void* in, const void* w, const float* scale_shift,
                void* out, int32_t tile, void* stream);
+/* pp_conv3x3 with a workspace for the stream-K tiles of PP_F32_TC (the K blocks of all output
+ * tiles laid end to end and cut into one equal range per SM; a tile split between SMs is
+ * finished by the last of them, from partial sums in the workspace).  workspace: device, 256-
+ * byte aligned, >= pp_conv_workspace_bytes() bytes, zero-filled before its first use; every
+ * completed launch leaves it ready for the next (a launch that failed on the device leaves it
+ * unspecified: zero it again).  Launches that share a workspace must be stream-ordered.  With
+ * workspace NULL, stream-K tiles return PP_EINVAL, and tile = -1 falls back to the same tile
+ * without stream-K.  Results of a stream-K tile differ from the plain tile's only by FP32
+ * rounding (the partial sums are added in a fixed order, so a given shape, batch and tile is
+ * bit-reproducible). */
+int pp_conv3x3_ws(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
+                  int32_t dtype, const void* in, const void* w, const float* scale_shift,
+                  void* out, int32_t tile, void* workspace, size_t workspace_bytes, void* stream);
+/* Workspace bytes pp_conv3x3_ws needs for every stream-K tile of this shape (0: none). */
+size_t pp_conv_workspace_bytes(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                               int32_t stride, int32_t dtype);
 int pp_conv_tile_count(int32_t dtype);
 /* Shape of conv tile `tile` of `dtype`: output box bh x bw pixels (bh*bw = 128 on the tensor
  * cores; CUDA-core tiles report bh = 1, bw = pixels per tile), bn output channels, and whether
@@ -168,7 +184,8 @@ int pp_conv_tile_count(int32_t dtype);
  * accumulators carried across tiles (the default for the tensor-core dtypes); 2 = the BF16
  * row-streaming kernel for 64 -> 64 channel layers (the default there: weights resident in
  * shared memory, each input row loaded once and every tap read as a row-shifted view; tile
- * reports the 128-pixel output row segment). */
+ * reports the 128-pixel output row segment); 3 = persistent with the stream-K partition (PP_F32_TC; needs a
+ * workspace, see pp_conv3x3_ws). */
 int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
                       int32_t* persistent);
 
@@ -182,6 +199,11 @@ int pp_conv_autotune(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t c
                      int32_t stride, int32_t dtype, const void* in, const void* w,
                      const float* scale_shift, void* out, int32_t reps, int32_t* best_tile,
                      float* best_us);
+/* pp_conv_autotune that also times the stream-K tiles, on `workspace` (see pp_conv3x3_ws). */
+int pp_conv_autotune_ws(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                        int32_t stride, int32_t dtype, const void* in, const void* w,
+                        const float* scale_shift, void* out, void* workspace,
+                        size_t workspace_bytes, int32_t reps, int32_t* best_tile, float* best_us);
 /* Writes the autotuned table as text ("dtype batch H W cin cout stride tile us" per line). */
 int pp_conv_tune_save(const char* path);
 /* Reads a table written by pp_conv_tune_save (host only, no GPU needed); returns the number of

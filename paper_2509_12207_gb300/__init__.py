@@ -148,6 +148,10 @@ _SIGS = {
     "pp_conv_autotune": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I,
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "pp_tf32_split": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "pp_conv3x3_ws": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P, _SZ, _P]),
+    "pp_conv_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I, _I, _I]),
+    "pp_conv_autotune_ws": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _I,
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "pp_conv_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "pp_conv_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "pp_conv_tune_clear": (None, []),
@@ -355,10 +359,25 @@ def split_f32(x, stream=None):
     return out
 
 
-def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=None, stream=None):
+def conv_workspace(B, H, W, cin, cout, stride, dtype, device="cuda"):
+    """A zeroed, 256-byte aligned device workspace for the stream-K tiles of this conv shape
+    (pp_conv_workspace_bytes), as (tensor keeping it alive, pointer, bytes); None if none is
+    needed."""
+    import torch
+    n = int(lib().pp_conv_workspace_bytes(B, H, W, cin, cout, stride, dtype))
+    if n == 0:
+        return None
+    buf = torch.zeros(n + 256, dtype=torch.uint8, device=device)
+    ptr = buf.data_ptr() + (-buf.data_ptr()) % 256
+    return buf, ptr, n
+
+
+def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=None, stream=None,
+            workspace=None):
     """x: padded NHWC [B, H+2, W+2, cin] (float32 for PP_F32, bfloat16 for PP_BF16; for
     PP_F32_TC split FP32 [2, B, H+2, W+2, cin], see split_f32).  Returns the padded output
-    [B, Ho+2, Wo+2, cout] (border zero; [2, B, ...] split FP32 for PP_F32_TC)."""
+    [B, Ho+2, Wo+2, cout] (border zero; [2, B, ...] split FP32 for PP_F32_TC).  workspace: a
+    conv_workspace() triple for the stream-K tiles (PP_F32_TC; one is made when omitted)."""
     import torch
     _need_cuda(x, w_packed, scale_shift)
     split = dtype == PP_F32_TC
@@ -369,18 +388,25 @@ def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=N
     Ho, Wo = (H - 1) // stride + 1, (W - 1) // stride + 1
     if out is None:
         out = torch.zeros(((2,) if split else ()) + (B, Ho + 2, Wo + 2, cout), dtype=x.dtype, device=x.device)
-    _check(lib().pp_conv3x3(B, H, W, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
-                            _ptr(out), tile, _stream(stream)))
+    if split and workspace is None:
+        workspace = conv_workspace(B, H, W, cin, cout, stride, dtype, x.device)
+    ws_ptr, ws_n = (workspace[1], workspace[2]) if workspace else (None, 0)
+    _check(lib().pp_conv3x3_ws(B, H, W, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
+                               _ptr(out), tile, ws_ptr, ws_n, _stream(stream)))
     return out
 
 
-def conv_autotune(x, w_packed, scale_shift, cout, stride, dtype, out, reps=5):
+def conv_autotune(x, w_packed, scale_shift, cout, stride, dtype, out, reps=5, workspace=None):
     """pp_conv_autotune on the layer shape of ``x`` (padded NHWC; split FP32 [2, B, ...] for
     PP_F32_TC) -> (best tile, us per launch)."""
     B, Hp, Wp, cin = (int(v) for v in x.shape[-4:])
     t, us = ctypes.c_int32(-1), ctypes.c_float(0)
-    _check(lib().pp_conv_autotune(B, Hp - 2, Wp - 2, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed),
-                                  _ptr(scale_shift), _ptr(out), reps, ctypes.byref(t), ctypes.byref(us)))
+    if dtype == PP_F32_TC and workspace is None:
+        workspace = conv_workspace(B, Hp - 2, Wp - 2, cin, cout, stride, dtype, x.device)
+    ws_ptr, ws_n = (workspace[1], workspace[2]) if workspace else (None, 0)
+    _check(lib().pp_conv_autotune_ws(B, Hp - 2, Wp - 2, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed),
+                                     _ptr(scale_shift), _ptr(out), ws_ptr, ws_n, reps, ctypes.byref(t),
+                                     ctypes.byref(us)))
     return int(t.value), float(us.value)
 
 

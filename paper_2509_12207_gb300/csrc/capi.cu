@@ -143,9 +143,8 @@ int pp_tf32_split(const float* x, float* lo, int64_t n, void* stream) {
   return tf32_split_launch(x, lo, (size_t)n, static_cast<cudaStream_t>(stream));
 }
 
-int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
-               int32_t dtype, const void* in, const void* w, const float* scale_shift,
-               void* out, int32_t tile, void* stream) {
+static int conv_shape(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
+                      ConvShape* c) {
   if (batch <= 0 || H <= 0 || W <= 0 || cin <= 0 || cout <= 0 || cin % 64 || cout % 64 ||
       cin > 1024 || cout > 1024 || (stride != 1 && stride != 2))
     return fail(PP_EINVAL, "conv3x3: unsupported shape (cin, cout multiples of 64, stride 1/2)");
@@ -153,13 +152,35 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
     return fail(PP_EINVAL, "conv3x3: activation too large");
   if (stride == 2 && ((H & 1) || (W & 1)))
     return fail(PP_EINVAL, "conv3x3: stride 2 needs even H and W");
+  c->batch = batch; c->H = H; c->W = W; c->cin = cin; c->cout = cout; c->stride = stride;
+  c->Ho = (H - 1) / stride + 1;
+  c->Wo = (W - 1) / stride + 1;
+  return PP_OK;
+}
+
+size_t pp_conv_workspace_bytes(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                               int32_t stride, int32_t dtype) {
+  ConvShape c;
+  if (dtype != PP_F32_TC || conv_shape(batch, H, W, cin, cout, stride, &c) != PP_OK) return 0;
+  return conv_sk_workspace_bytes(c);
+}
+
+int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
+               int32_t dtype, const void* in, const void* w, const float* scale_shift,
+               void* out, int32_t tile, void* stream) {
+  return pp_conv3x3_ws(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out, tile,
+                       nullptr, 0, stream);
+}
+
+int pp_conv3x3_ws(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t stride,
+                  int32_t dtype, const void* in, const void* w, const float* scale_shift,
+                  void* out, int32_t tile, void* workspace, size_t workspace_bytes, void* stream) {
+  ConvShape c;
+  int st = conv_shape(batch, H, W, cin, cout, stride, &c);
+  if (st) return st;
   if (!in || !w || !scale_shift || !out) return fail(PP_EINVAL, "conv3x3: NULL buffer");
   if (!aligned16(in) || !aligned16(w) || !aligned16(out))
     return fail(PP_EINVAL, "conv3x3: buffers must be 16-byte aligned");
-  ConvShape c;
-  c.batch = batch; c.H = H; c.W = W; c.cin = cin; c.cout = cout; c.stride = stride;
-  c.Ho = (H - 1) / stride + 1;
-  c.Wo = (W - 1) / stride + 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == PP_F32)
     return conv_f32_launch(c, static_cast<const float*>(in), static_cast<const float*>(w),
@@ -170,7 +191,7 @@ int pp_conv3x3(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, i
                             static_cast<__nv_bfloat16*>(out), tile, s);
   if (dtype == PP_F32_TC)
     return conv_f32tc_launch(c, static_cast<const float*>(in), static_cast<const float*>(w),
-                             scale_shift, static_cast<float*>(out), tile, s);
+                             scale_shift, static_cast<float*>(out), tile, s, workspace, workspace_bytes);
   return fail(PP_EINVAL, "conv3x3: bad dtype");
 }
 

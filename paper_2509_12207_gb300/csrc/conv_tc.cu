@@ -108,6 +108,29 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* m, uint64_t
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, const void* src, int c0, int c1,
+                                             int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(m),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The issuing thread's bulk stores have finished reading shared memory / have completed.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Named barrier `id` over `n` threads that also ANDs a predicate across them.
+__device__ __forceinline__ bool bar_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
   const uint32_t a = smem_u32(p);
@@ -377,12 +400,20 @@ struct PArgs {
   size_t plane;  // 3xTF32: elements from the output's value plane to its remainder plane
   const float* ss;
   void* out;
+  int sk;         // 3xTF32 stream-K partition (else whole tiles per CTA)
+  float* ws;      // stream-K: [2 * gridDim.x][128][BN] partial tiles
+  unsigned* sem;  // stream-K: [total] arrival counters, zero between launches
 };
 
-template <int MODE, int BN, int STAGES, int KPS, bool S2>
+// EPI_TMA: the epilogue stages the tile's output (both planes) in shared memory in the 128-byte
+// swizzled layout and one thread stores it with TMA (tmO, tmOlo: the output interiors as 4-D
+// maps, so partial tiles are clipped by the copy engine); otherwise each reducer thread stores
+// its own pixel row.
+template <int MODE, int BN, int STAGES, int KPS, bool S2, bool EPI_TMA, bool SK>
 __global__ void __launch_bounds__(192, 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
-            const __grid_constant__ CUtensorMap tmB, PArgs args) {
+            const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
+            const __grid_constant__ CUtensorMap tmOlo, PArgs args) {
   constexpr int BK = MODE == 1 ? 32 : 64;                  // channels per K block (128 B rows)
   constexpr uint32_t kA = 128 * 128;                       // A tile bytes of one K block
   constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
@@ -398,6 +429,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr int kRed0 = 2;                                 // first reducer warp
   extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned s_abort;
+  __shared__ unsigned s_arrived;  // stream-K: arrivals at the current shared tile before this CTA
   if (threadIdx.x == 0) s_abort = tc_error_now();
   __syncthreads();
   if (s_abort != 0u) return;
@@ -405,7 +437,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                                              ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
+  uint8_t* sO = sB + STAGES * kStageB;                     // EPI_TMA staging: 2 planes x BN/32 chunks x 16 KiB
+  constexpr uint32_t kStageO = EPI_TMA ? 2u * (BN / 32) * 16384u : 0u;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);
   uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
   uint64_t* kfree = kdone + NBUF;
@@ -438,6 +472,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     if (MODE == 1) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmAlo) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    if (EPI_TMA) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmO) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmOlo) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -460,18 +498,40 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     ox0 = tx * args.bw;
     n0 = nt * BN;
   };
+  // Work pieces of this CTA, i = 0, 1, ...: (tile t, K blocks [k0, k1)).  Plain: whole tiles
+  // t = blockIdx.x + i * gridDim.x.  Stream-K: the K blocks of all tiles laid end to end and cut
+  // into gridDim.x equal ranges, one per CTA; a tile cut between CTAs is finished by the CTA
+  // that completes it last (partial sums through args.ws, arrivals counted in args.sem).
+  const long W = (long)args.total * KB;
+  auto cta_start = [&](long cta) -> long { return cta * W / gridDim.x; };
+  const long r_lo = SK ? cta_start(blockIdx.x) : 0, r_hi = SK ? cta_start(blockIdx.x + 1) : 0;
+  auto piece = [&](int i, int& t, int& k0, int& k1) -> bool {
+    if (!SK) {
+      t = blockIdx.x + i * gridDim.x;
+      k0 = 0;
+      k1 = KB;
+      return t < args.total;
+    }
+    t = (int)(r_lo / KB) + i;
+    const long b0 = (long)t * KB;
+    k0 = (int)(r_lo > b0 ? r_lo - b0 : 0);
+    k1 = (int)(r_hi < b0 + KB ? r_hi - b0 : KB);
+    return b0 < r_hi && k1 > k0;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
         int b, oy0, ox0, n0;
         decode(t, b, oy0, ox0, n0);
-        int cc = 0, kx = 0, ky = 0, kk = 0;  // channel chunk, tap, K offset of the next K block
-        for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
-          const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
+        // channel chunk, tap, K offset of the next K block
+        int cc = k0 % kchunks, kx = (k0 / kchunks) % 3, ky = k0 / kchunks / 3, kk = k0 * BK;
+        for (int kb0 = k0; kb0 < k1; kb0 += KPS) {
+          const int nk = k1 - kb0 < KPS ? k1 - kb0 : KPS;
           if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
           mbar_expect_tx(&full[s], (uint32_t)nk * (kAK + kBK));
           for (int j = 0; j < nk; ++j) {
@@ -511,9 +571,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       int s = 0, gg = 0, inq = 0;  // inq: K blocks already in the current group
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
-        for (int kb0 = 0; kb0 < KB; kb0 += KPS) {
-          const int nk = KB - kb0 < KPS ? KB - kb0 : KPS;
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        for (int kb0 = k0; kb0 < k1; kb0 += KPS) {
+          const int nk = k1 - kb0 < KPS ? k1 - kb0 : KPS;
           const int buf = gg & (NBUF - 1);
           if (inq == 0 && gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
           if (!mbar_wait(&full[s], ph, 2u)) { ok = false; break; }
@@ -540,7 +601,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           }
           mma_commit(&empty[s]);
           inq += nk;
-          if (inq >= fold || kb0 + nk == KB) {
+          if (inq >= fold || kb0 + nk == k1) {
             mma_commit(&kdone[buf]);
             ++gg;
             inq = 0;
@@ -553,10 +614,11 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int q = warp & 3;  // TMEM lane quarter this warp may read
     const int r = q * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    const int gpt = (KB + fold - 1) / fold;  // accumulation groups per tile
     int gg = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < args.total && ok; t += gridDim.x) {
+    int t, k0, k1;
+    for (int pi = 0; ok && piece(pi, t, k0, k1); ++pi) {
+      const int gpt = (k1 - k0 + fold - 1) / fold;  // accumulation groups of this piece
       int b, oy0, ox0, n0;
       decode(t, b, oy0, ox0, n0);
       const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
@@ -584,7 +646,84 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tc_fence_before();
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
         }
-        if (ok && in_range) {
+        if (SK && (k0 > 0 || k1 < KB)) {
+          // Part of a tile shared with neighbouring CTAs: publish this partial sum (slot 2c for
+          // the piece a CTA starts with, 2c + 1 for the one it ends with), count the arrival,
+          // and let the last of the tile's CTAs add the partials in CTA order and finish it.
+          // slot layout [slot][BN/4][128 rows] of float4: a warp's stores and loads of one
+          // float4 column are 512 contiguous bytes
+          const long tb = (long)t * KB;
+          const int slot = 2 * blockIdx.x + (r_lo < tb ? 1 : 0);
+          float4* mine = reinterpret_cast<float4*>(args.ws) + (size_t)slot * (BN / 4) * 128 + r;
+#pragma unroll
+          for (int i = 0; i < BN / 4; ++i)
+            mine[i * 128] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+          __threadfence();
+          ok = bar_and(1, 128, ok);
+          if (!ok) break;
+          if (r == 0) s_arrived = atomicAdd(&args.sem[t], 1u);
+          bar_and(1, 128, true);
+          auto cta_of = [&](long idx) -> int {
+            long cc = idx * gridDim.x / W;
+            while (cc > 0 && cta_start(cc) > idx) --cc;
+            while (cta_start(cc + 1) <= idx) ++cc;
+            return (int)cc;
+          };
+          const int cf = cta_of(tb), cl = cta_of(tb + KB - 1);
+          if (s_arrived != (unsigned)(cl - cf)) continue;  // another CTA finishes this tile
+          __threadfence();
+          // sum every piece's partial (this CTA's too, as stored) in CTA order
+          for (int i = 0; i < BN / 4; ++i) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int cc = cf; cc <= cl; ++cc) {
+              const int sl = 2 * cc + (cta_start(cc) < tb ? 1 : 0);
+              const float4 p = __ldcg(reinterpret_cast<const float4*>(args.ws) + ((size_t)sl * (BN / 4) + i) * 128 + r);
+              v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
+            }
+            reinterpret_cast<float4*>(args.ws)[((size_t)slot * (BN / 4) + i) * 128 + r] = v;
+          }
+#pragma unroll
+          for (int i = 0; i < BN / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(args.ws)[((size_t)slot * (BN / 4) + i) * 128 + r];
+            acc[4 * i] = v.x; acc[4 * i + 1] = v.y; acc[4 * i + 2] = v.z; acc[4 * i + 3] = v.w;
+          }
+          if (r == 0) args.sem[t] = 0u;  // counters are zero again for the next launch
+        }
+        if (EPI_TMA) {
+          // the previous tile's stores must have read the staging buffer; every reducer thread
+          // takes the same decision (AND of ok), so the named barriers always match
+          if (r == 0) bulk_wait_read();
+          ok = bar_and(1, 128, ok);
+          if (!ok) break;
+#pragma unroll
+          for (int k = 0; k < BN / 32; ++k) {
+            uint8_t* hi = sO + k * 16384 + r * 128;
+            uint8_t* lo = hi + (BN / 32) * 16384;
+#pragma unroll
+            for (int qd = 0; qd < 8; ++qd) {
+              const int n = n0 + 32 * k + 4 * qd;
+              const float* a = acc + 32 * k + 4 * qd;
+              float4 u;
+              u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), 0.f);
+              u.y = fmaxf(fmaf(a[1], s_scale[n + 1], s_shift[n + 1]), 0.f);
+              u.z = fmaxf(fmaf(a[2], s_scale[n + 2], s_shift[n + 2]), 0.f);
+              u.w = fmaxf(fmaf(a[3], s_scale[n + 3], s_shift[n + 3]), 0.f);
+              const int off = ((qd ^ (r & 7)) << 4);  // 128-byte swizzle of the TMA box
+              *reinterpret_cast<float4*>(hi + off) = u;
+              *reinterpret_cast<float4*>(lo + off) = tf32_remainder4(u);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_and(1, 128, true);
+          if (r == 0) {
+#pragma unroll
+            for (int k = 0; k < BN / 32; ++k) {
+              tma_store_4d(&tmO, sO + k * 16384, n0 + 32 * k, ox0, oy0, b);
+              tma_store_4d(&tmOlo, sO + (BN / 32 + k) * 16384, n0 + 32 * k, ox0, oy0, b);
+            }
+            bulk_commit();
+          }
+        } else if (ok && in_range) {
           // value plane and remainder plane (split FP32, the next layer's A operand)
           float4* dst = reinterpret_cast<float4*>(static_cast<float*>(args.out) + pix * c.cout + n0);
           float4* dlo = reinterpret_cast<float4*>(static_cast<float*>(args.out) + args.plane + pix * c.cout + n0);
@@ -634,6 +773,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
     }
   }
+  if (EPI_TMA && warp == 4 && lane == 0) bulk_wait_all();  // the staging buffer outlives its stores
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -917,7 +1057,7 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
 
 int conv_tcp_tile_count(int mode);
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
-                    void* out, int ptile, cudaStream_t s);
+                    void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0);
 int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
                      cudaStream_t s);
 int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0) + 1; }
@@ -995,10 +1135,15 @@ int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfl
 int conv_f32tc_tile_count() { return conv_tcp_tile_count(1); }
 
 int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
-                      float* out, int tile, cudaStream_t s) {
+                      float* out, int tile, cudaStream_t s, void* ws, size_t ws_bytes) {
   if (c.cin % 32) return fail(PP_EINVAL, "conv f32 tensor: cin must be a multiple of 32");
-  if (tile < 0) tile = tuned_tile(PP_F32_TC, c);
-  return conv_tcp_launch(1, c, in, w_split, ss, out, tile, s);
+  if (tile < 0) {
+    tile = tuned_tile(PP_F32_TC, c);
+    // a stream-K choice needs a workspace; without one, the same tile without stream-K
+    const int np = conv_tcp_tile_count(1) / 2;
+    if (tile >= np && (!ws || ws_bytes < conv_sk_workspace_bytes(c))) tile -= np;
+  }
+  return conv_tcp_launch(1, c, in, w_split, ss, out, tile, s, ws, ws_bytes);
 }
 
 namespace {
@@ -1021,14 +1166,21 @@ template <int MODE, int BN>
 constexpr int p_kps() {
   return MODE == 1 ? 1 : 2;
 }
+// The 3xTF32 kernel with BN = 64 stores through a shared-memory staging tile (64 KiB: both
+// planes) by TMA, and keeps three ring stages to make room for it.
+template <int MODE, int BN>
+constexpr bool p_epi_tma() {
+  return MODE == 1 && BN == 64;
+}
 template <int MODE, int BN>
 constexpr int p_stages() {
-  return MODE == 1 ? (BN == 64 ? 4 : 3) : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+  return MODE == 1 ? 3 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
 }
 template <int MODE, int BN>
 constexpr size_t p_smem() {
   return 1024 + (size_t)p_stages<MODE, BN>() * p_kps<MODE, BN>() *
                     ((MODE == 1 ? 2 : 1) * 16384 + (MODE == 1 ? 2 : 1) * BN * 128) +
+         (p_epi_tma<MODE, BN>() ? 2 * (BN / 32) * 16384 : 0) +
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
 
@@ -1043,21 +1195,26 @@ int num_sms() {
   return n;
 }
 
-template <int MODE, int BN, bool S2>
-int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
-             cudaStream_t s) {
+template <int MODE, int BN, bool S2, bool SK>
+int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const CUtensorMap& o,
+             const CUtensorMap& olo, const PArgs& args, cudaStream_t s) {
   constexpr int ST = p_stages<MODE, BN>();
   constexpr int KPS = p_kps<MODE, BN>();
+  constexpr bool EPI = p_epi_tma<MODE, BN>();
   constexpr size_t bytes = p_smem<MODE, BN>() + 2 * 1024 * sizeof(float);  // + folded BN (cout <= 1024)
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2>,
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, EPI, SK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_status(e, "persistent conv smem attribute");
     attr_set = true;
   }
-  const int grid = args.total < num_sms() ? args.total : num_sms();
-  conv3x3_tcp<MODE, BN, ST, KPS, S2><<<grid, 192, bytes, s>>>(a, alo, w, args);
+  // stream-K: one range per CTA, never an empty one (an empty range would be counted among the
+  // CTAs that share a tile but never arrive), so at most one CTA per K block
+  const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
+  const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
+                           : (args.total < num_sms() ? args.total : num_sms());
+  conv3x3_tcp<MODE, BN, ST, KPS, S2, EPI, SK><<<grid, 192, bytes, s>>>(a, alo, w, o, olo, args);
   return cuda_status(cudaGetLastError(), "persistent conv launch");
 }
 
@@ -1083,11 +1240,14 @@ int pick_tile_p(const ConvShape& c, const TileP* tiles, int n) {
 // mode 0: BF16 in/out, weights [cout][9cin] bf16; mode 1: split FP32 in/out ([2][B][H+2][W+2][C]:
 // values, TF32 remainders) via 3xTF32, weights [2][cout][9cin] fp32 (hi, lo planes).
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
-                    void* out, int ptile, cudaStream_t s) {
+                    void* out, int ptile, cudaStream_t s, void* ws, size_t ws_bytes) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
   const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
   const int n = mode == 1 ? kNPF : kNPB;
+  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition
+  const bool sk = mode == 1 && ptile >= n;
+  if (sk) ptile -= n;
   if (ptile < 0) ptile = pick_tile_p(c, tiles, n);
   if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn)
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
@@ -1146,15 +1306,44 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.plane = c.out_plane ? c.out_plane : (size_t)c.batch * (c.Ho + 2) * (c.Wo + 2) * c.cout;
   args.ss = ss;
   args.out = out;
+  args.sk = sk ? 1 : 0;
+  args.ws = nullptr;
+  args.sem = nullptr;
+  if (sk) {
+    // counters after partial slots sized for the widest N tile, at the same offset for every
+    // tile, so that launches with different tiles can share one workspace
+    const size_t part = (size_t)2 * num_sms() * 128 * 128 * sizeof(float);
+    if (!ws || ws_bytes < part + (size_t)args.total * sizeof(unsigned) || (reinterpret_cast<uintptr_t>(ws) & 255u))
+      return fail(PP_EINVAL, "persistent conv: stream-K tile needs a 256-byte aligned workspace of %zu bytes",
+                  part + (size_t)args.total * sizeof(unsigned));
+    args.ws = static_cast<float*>(ws);
+    args.sem = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + part);
+  }
+  // output interiors as 4-D maps (channels, x, y, frame) for the TMA-store epilogue
+  CUtensorMap to = ta, tolo = ta;
+  if (mode == 1 && t.bn == 64) {
+    for (int plane = 0; plane < 2 && r == CUDA_SUCCESS; ++plane) {
+      float* base = static_cast<float*>(out) + (size_t)plane * args.plane + (size_t)(c.Wo + 3) * c.cout;
+      cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)c.Wo, (cuuint64_t)c.Ho, (cuuint64_t)c.batch};
+      cuuint64_t strides[3] = {(cuuint64_t)c.cout * 4, (cuuint64_t)(c.Wo + 2) * c.cout * 4,
+                               (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.cout * 4};
+      cuuint32_t box[4] = {32, (cuuint32_t)t.bw, (cuuint32_t)t.bh, 1};
+      cuuint32_t es[4] = {1, 1, 1, 1};
+      r = enc(plane ? &tolo : &to, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: output tensor map (%d)", (int)r);
+  }
   const bool s2 = c.stride == 2;
-#define PP_P(M, N) return s2 ? launch_p<M, N, true>(ta, talo, tw, args, s) : launch_p<M, N, false>(ta, talo, tw, args, s)
+#define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, to, tolo, args, s) : launch_p<M, N, false, K>(ta, talo, tw, to, tolo, args, s)
   if (mode == 1) {
-    if (t.bn == 64) PP_P(1, 64);
-    if (t.bn == 128) PP_P(1, 128);
+    if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
+    if (t.bn == 128) { if (sk) PP_P(1, 128, true); PP_P(1, 128, false); }
   } else {
-    if (t.bn == 64) PP_P(0, 64);
-    if (t.bn == 128) PP_P(0, 128);
-    if (t.bn == 256) PP_P(0, 256);
+    if (t.bn == 64) PP_P(0, 64, false);
+    if (t.bn == 128) PP_P(0, 128, false);
+    if (t.bn == 256) PP_P(0, 256, false);
   }
 #undef PP_P
   return fail(PP_EINVAL, "persistent conv: no kernel for tile %d", ptile);
@@ -1235,7 +1424,20 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   return cuda_status(cudaGetLastError(), "row conv launch");
 }
 
-int conv_tcp_tile_count(int mode) { return mode == 1 ? kNPF : kNPB; }
+int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF : kNPB; }
+
+// Workspace for any stream-K tile of this shape: partial tiles for two pieces per CTA at the
+// widest N tile, then one arrival counter per output tile of the narrowest.
+size_t conv_sk_workspace_bytes(const ConvShape& c) {
+  size_t tiles = 0;
+  for (int i = 0; i < kNPF; ++i) {
+    const TileP& t = kTilesPF[i];
+    if (c.cout % t.bn) continue;
+    const size_t n = (size_t)((c.Wo + t.bw - 1) / t.bw) * ((c.Ho + t.bh - 1) / t.bh) * c.batch * (c.cout / t.bn);
+    if (n > tiles) tiles = n;
+  }
+  return (size_t)2 * num_sms() * 128 * 128 * sizeof(float) + align_up(tiles * sizeof(unsigned), 256);
+}
 
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent) {
   if (dtype == PP_BF16) {
@@ -1247,9 +1449,9 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   if (dtype == PP_F32_TC) {
-    if (tile < 0 || tile >= kNPF) return PP_EINVAL;
-    const TileP& t = kTilesPF[tile];
-    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1;
+    if (tile < 0 || tile >= 2 * kNPF) return PP_EINVAL;
+    const TileP& t = kTilesPF[tile % kNPF];
+    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : 3;
     return PP_OK;
   }
   return PP_EINVAL;

@@ -190,6 +190,16 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
     // borders stay zero forever: convs write interiors only
     if ((st = cuda_status(cudaMemsetAsync(a, 0, n, s), "clear activations"))) return st;
   }
+  if (m->conv_dtype == PP_F32_TC) {
+    // one stream-K workspace, sized for the widest layer at the unit's capacity (a smaller
+    // batch needs fewer arrival counters), zeroed once; every completed conv leaves it zero
+    for (const LayerSpec& L : m->layers) {
+      ConvShape c{B_, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
+      conv_ws_bytes_ = std::max(conv_ws_bytes_, conv_sk_workspace_bytes(c));
+    }
+    PP_ALLOC(conv_ws_, conv_ws_bytes_);
+    if ((st = cuda_status(cudaMemsetAsync(conv_ws_, 0, conv_ws_bytes_, s), "clear conv workspace"))) return st;
+  }
 #undef PP_ALLOC
   if ((st = cuda_status(cudaMemsetAsync(vox_ws_, 0, 256, s), "clear vox error word"))) return st;
   if ((st = cuda_status(cudaMemsetAsync(tab_dev_, 0, sizeof(UnitTable), s), "clear unit table"))) return st;
@@ -214,8 +224,8 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
       for (size_t l = 0; l < m->layers.size() && st == PP_OK; ++l) {
         const LayerSpec& L = m->layers[l];
         int best = -1;
-        st = pp_conv_autotune(b, L.H, L.W, L.cin, L.cout, L.stride, m->conv_dtype, x, m->conv_w[l],
-                              m->conv_ss[l], act_[l], 5, &best, nullptr);
+        st = pp_conv_autotune_ws(b, L.H, L.W, L.cin, L.cout, L.stride, m->conv_dtype, x, m->conv_w[l],
+                                 m->conv_ss[l], act_[l], conv_ws_, conv_ws_bytes_, 5, &best, nullptr);
         x = act_[l];
       }
     }
@@ -284,7 +294,7 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
                            (float*)act_[l], -1, s);
     else if (m.conv_dtype == PP_F32_TC)
       st = conv_f32tc_launch(c, (const float*)x, (const float*)m.conv_w[l], m.conv_ss[l],
-                             (float*)act_[l], -1, s);
+                             (float*)act_[l], -1, s, conv_ws_, conv_ws_bytes_);
     else
       st = conv_bf16_launch(c, (const __nv_bfloat16*)x, (const __nv_bfloat16*)m.conv_w[l],
                             m.conv_ss[l], (__nv_bfloat16*)act_[l], -1, s);

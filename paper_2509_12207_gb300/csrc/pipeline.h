@@ -82,6 +82,8 @@ class Pipeline {
   VoxWork vw_{};
   float* feat_ = nullptr;
   void* canvas_ = nullptr;
+  void* conv_ws_ = nullptr;  // stream-K workspace shared by the unit's (stream-ordered) convs
+  size_t conv_ws_bytes_ = 0;
   std::vector<void*> act_;
   std::vector<cudaGraphExec_t> graphs_;
   std::vector<void*> allocs_;

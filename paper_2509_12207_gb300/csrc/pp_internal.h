@@ -71,8 +71,10 @@ int conv_f32_tile_count();
 int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w_nk,
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s);
 int conv_bf16_tile_count();
+// ws: stream-K workspace (conv_sk_workspace_bytes, zeroed once; NULL = no stream-K tiles).
 int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split, const float* ss,
-                      float* out, int tile, cudaStream_t s);
+                      float* out, int tile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0);
+size_t conv_sk_workspace_bytes(const ConvShape& c);
 int conv_f32tc_tile_count();
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent);
 // Tile the autotuner found fastest for this dtype and shape, or -1 (tune.cu).

@@ -39,6 +39,14 @@ int pp_conv_autotune(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t c
                      int32_t stride, int32_t dtype, const void* in, const void* w,
                      const float* scale_shift, void* out, int32_t reps, int32_t* best_tile,
                      float* best_us) {
+  return pp_conv_autotune_ws(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out,
+                             nullptr, 0, reps, best_tile, best_us);
+}
+
+int pp_conv_autotune_ws(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                        int32_t stride, int32_t dtype, const void* in, const void* w,
+                        const float* scale_shift, void* out, void* workspace,
+                        size_t workspace_bytes, int32_t reps, int32_t* best_tile, float* best_us) {
   if (reps <= 0 || reps > 1000 || !best_tile) return fail(PP_EINVAL, "conv_autotune: bad argument");
   const int n = pp_conv_tile_count(dtype);
   if (n <= 0) return fail(PP_EINVAL, "conv_autotune: bad dtype");
@@ -52,7 +60,8 @@ int pp_conv_autotune(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t c
   float best_t = 1e30f;
   for (int t = 0; t < n; ++t) {
     // a first plain launch validates the tile for this shape (and sets kernel attributes)
-    if (pp_conv3x3(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out, t, s) != PP_OK) {
+    if (pp_conv3x3_ws(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out, t, workspace,
+                      workspace_bytes, s) != PP_OK) {
       cudaGetLastError();
       continue;
     }
@@ -68,7 +77,8 @@ int pp_conv_autotune(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t c
     }
     int lst = PP_OK;
     for (int r = 0; r < reps && lst == PP_OK; ++r)
-      lst = pp_conv3x3(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out, t, s);
+      lst = pp_conv3x3_ws(batch, H, W, cin, cout, stride, dtype, in, w, scale_shift, out, t, workspace,
+                          workspace_bytes, s);
     const cudaError_t ce = cudaStreamEndCapture(s, &g);
     if (lst != PP_OK || ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);

@@ -239,13 +239,24 @@ def test_conv_f32_tensor_cores(shape):
     ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
     refs = [O.conv3x3_bn_relu(xp[b, 1:-1, 1:-1].astype(np.float64), w, bn, s) for b in range(B)]
     n_tiles = pp.conv_tile_count(pp.PP_F32_TC)
-    assert n_tiles >= 7
-    for tile in list(range(n_tiles)) + [-1]:
+    assert n_tiles >= 14
+    ws = pp.conv_workspace(B, H, W, cin, cout, s, pp.PP_F32_TC, DEV)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # every tile, then every tile again in reverse order on the same workspace (stream-K tiles of
+    # different widths share it, as the layers of a release unit do)
+    for tile in list(range(n_tiles)) + list(range(n_tiles - 1, -1, -1)) + [-1]:
         if tile >= 0 and cout % pp.conv_tile_info(pp.PP_F32_TC, tile)[2]:
             continue
-        out = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32_TC, tile=tile)
+        out = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32_TC, tile=tile, workspace=ws)
         torch.cuda.synchronize()
         assert pp.device_error() == 0
+        if tile >= 0 and pp.conv_tile_info(pp.PP_F32_TC, tile)[3] == 3:
+            # stream-K: bit-reproducible, and the arrival counters are left zero
+            again = pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32_TC, tile=tile, workspace=ws)
+            torch.cuda.synchronize()
+            assert torch.equal(out, again), tile
+            counters = ws[0][ws[1] - ws[0].data_ptr() + 2 * sms * 128 * 128 * 4:][: ws[2] - 2 * sms * 128 * 128 * 4]
+            assert not counters.any(), tile
         o = out.cpu().numpy()
         # plane 1 is exactly the TF32 remainder of plane 0 (the next layer's A remainder)
         assert np.array_equal(o[1], tf32_remainder(o[0])), tile
