@@ -90,6 +90,23 @@ def _conv_traffic(workload):
     return ent[0] if digest == ent[1] else None
 
 
+def _front_end_roofline(g, stages, elt, peaks):
+    """HBM roofline of the voxelise and scatter stages of one step: algorithmic bytes (per frame:
+    voxelise reads 16 B per point, reads and writes the 4-byte count of every cell, writes 32
+    float4 points plus 8 B of coordinates per kept pillar; scatter reads 256 B of features per
+    kept pillar and writes the whole padded canvas) over the stage's device time."""
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    G = g.nx * g.ny
+    canvas_px = (g.nx + 2) * (g.ny + 2)  # elt: canvas bytes per channel (8 = split FP32)
+    vox = sum(16 * n + 8 * G + (16 * 32 + 8) * p for n, p in zip(stages["_npoints"], stages["_npillars"]))
+    sca = sum(256 * p + 64 * canvas_px * elt for p in stages["_npillars"])
+    res = {"unit": "GB/s", "peak": peak, "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks else "fallback"}
+    for name, b in (("voxelize", vox), ("scatter", sca)):
+        gbs = b / (stages[name] * 1e-3) / 1e9
+        res[name] = {"bytes": int(b), "achieved": gbs, "frac": gbs / peak}
+    return res
+
+
 def _conv_flops(g, bb):
     tot = 0
     H, W = g.ny, g.nx
@@ -280,6 +297,8 @@ def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
         out[name] = e0.elapsed_time(e1) / reps
         del graph
     canvas_bytes = canvas.numel() * canvas.element_size()
+    out["_npoints"] = [int(f.shape[0]) for f in fs]
+    out["_npillars"] = [int(x) for x in v["num_pillars"].cpu()]
     return out, canvas_bytes, int(v["num_pillars"][0])
 
 
@@ -374,7 +393,9 @@ def _run_ours(a, rank, world, dist):
     layers = _time_conv_kernels(pp, torch, g, bb, w, conv_dtype, batch)
     conv_s = sum(t for t, _ in layers)
     conv_flops = sum(f for _, f in layers)
-    stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w, prec, n_frames)
+    # the scatter writes the canvas the convs read (split FP32 for the 3xTF32 convs)
+    stages, canvas_bytes, num_p = _time_stages(pp, torch, g, frames_dev, w,
+                                               pp.PP_F32_TC if conv_dtype == pp.PP_F32_TC else prec, n_frames)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
@@ -413,7 +434,9 @@ def _run_ours(a, rank, world, dist):
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames,
                      "layers_us": [round(t * 1e6, 2) for t, _ in layers],
                      "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
-        "stage_ms_per_step": {k: v for k, v in stages.items()},
+        "stage_ms_per_step": {k: v for k, v in stages.items() if not k.startswith("_")},
+        "front_end_roofline": _front_end_roofline(g, stages, {pp.PP_BF16: 2, pp.PP_F32: 4, pp.PP_F32_TC: 8}[
+            pp.PP_F32_TC if conv_dtype == pp.PP_F32_TC else prec], peaks),
         "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
                     "sched_us_per_decision": st["sched_us_per_decision"], "units": timed_units,
                     "frames_per_unit": a.steps * n_frames / max(1, timed_units)},

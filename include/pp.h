@@ -294,6 +294,10 @@ typedef struct {
                                 /* 3xTF32 split (0, default)                                   */
   int32_t autotune;             /* autotune every conv layer for each unit size at creation     */
                                 /* (pp_conv_autotune; default 1)                               */
+  int32_t stream_k;             /* let the autotuner pick stream-K tiles for 3xTF32 convs (each */
+                                /* unit then owns a workspace).  Within FP32 tolerance either  */
+                                /* way, but a frame's result is bit-identical across unit sizes */
+                                /* only without it (default 0)                                 */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,

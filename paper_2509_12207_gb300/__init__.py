@@ -60,7 +60,7 @@ class Config(ctypes.Structure):
         ("th_calib_frames", ctypes.c_int32), ("util_exempt", ctypes.c_double),
         ("early_exit", ctypes.c_int32), ("num_streams", ctypes.c_int32),
         ("max_admitted", ctypes.c_int32), ("fp32_cuda_cores", ctypes.c_int32),
-        ("autotune", ctypes.c_int32),
+        ("autotune", ctypes.c_int32), ("stream_k", ctypes.c_int32),
     ]
 
 

@@ -131,6 +131,26 @@ __device__ __forceinline__ bool bar_and(int id, int n, bool v) {
   return r != 0;
 }
 
+// Stores 32 rows of 128 bytes, row l held by lane l as v[0..7], through a 4 KiB per-warp shared
+// buffer, so that every store instruction writes four whole 128-byte lines (lane l writes bytes
+// 16 (l % 8) .. of row 4 i + l / 8) instead of 32 lines by 16 bytes.  dst_row: this lane's
+// row destination in global memory, or NULL to skip the row.  The buffer is XOR-swizzled by
+// row, so both the row writes and the transposed reads are free of bank conflicts.
+__device__ __forceinline__ void warp_rows_store(uint4* wbuf, const uint4 (&v)[8], char* dst_row, int lane) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) wbuf[lane * 8 + (j ^ (lane & 7))] = v[j];
+  __syncwarp();
+  const unsigned long long mine = reinterpret_cast<unsigned long long>(dst_row);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = 4 * i + (lane >> 3), col = lane & 7;
+    const unsigned long long d = __shfl_sync(0xffffffffu, mine, row);
+    const uint4 x = wbuf[row * 8 + (col ^ (row & 7))];
+    if (d) *reinterpret_cast<uint4*>(d + (unsigned long long)col * 16) = x;
+  }
+  __syncwarp();
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
   const uint32_t a = smem_u32(p);
@@ -438,7 +458,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
   uint8_t* sO = sB + STAGES * kStageB;                     // EPI_TMA staging: 2 planes x BN/32 chunks x 16 KiB
-  constexpr uint32_t kStageO = EPI_TMA ? 2u * (BN / 32) * 16384u : 0u;
+  constexpr uint32_t kStageO = EPI_TMA ? 2u * (BN / 32) * 16384u : 4u * 4096u;  // else 4 KiB per reducer warp
   uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);
   uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
@@ -631,7 +651,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int g = 0; g < gpt; ++g, ++gg) {
           const int buf = gg & (NBUF - 1);
           ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
-          __syncwarp();
+          ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
@@ -672,20 +692,20 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           const int cf = cta_of(tb), cl = cta_of(tb + KB - 1);
           if (s_arrived != (unsigned)(cl - cf)) continue;  // another CTA finishes this tile
           __threadfence();
-          // sum every piece's partial (this CTA's too, as stored) in CTA order
-          for (int i = 0; i < BN / 4; ++i) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int cc = cf; cc <= cl; ++cc) {
-              const int sl = 2 * cc + (cta_start(cc) < tb ? 1 : 0);
-              const float4 p = __ldcg(reinterpret_cast<const float4*>(args.ws) + ((size_t)sl * (BN / 4) + i) * 128 + r);
-              v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
-            }
-            reinterpret_cast<float4*>(args.ws)[((size_t)slot * (BN / 4) + i) * 128 + r] = v;
-          }
+          // sum every piece's partial (this CTA's too, as stored) in CTA order, one whole piece
+          // per pass so that the BN/4 loads of a pass are all in flight together
+          for (int cc = cf; cc <= cl; ++cc) {
+            const int sl = 2 * cc + (cta_start(cc) < tb ? 1 : 0);
+            const float4* src = reinterpret_cast<const float4*>(args.ws) + (size_t)sl * (BN / 4) * 128 + r;
 #pragma unroll
-          for (int i = 0; i < BN / 4; ++i) {
-            const float4 v = reinterpret_cast<const float4*>(args.ws)[((size_t)slot * (BN / 4) + i) * 128 + r];
-            acc[4 * i] = v.x; acc[4 * i + 1] = v.y; acc[4 * i + 2] = v.z; acc[4 * i + 3] = v.w;
+            for (int i = 0; i < BN / 4; ++i) {
+              const float4 p = __ldcg(src + i * 128);
+              if (cc == cf) {
+                acc[4 * i] = p.x; acc[4 * i + 1] = p.y; acc[4 * i + 2] = p.z; acc[4 * i + 3] = p.w;
+              } else {
+                acc[4 * i] += p.x; acc[4 * i + 1] += p.y; acc[4 * i + 2] += p.z; acc[4 * i + 3] += p.w;
+              }
+            }
           }
           if (r == 0) args.sem[t] = 0u;  // counters are zero again for the next launch
         }
@@ -723,26 +743,36 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             bulk_commit();
           }
-        } else if (ok && in_range) {
-          // value plane and remainder plane (split FP32, the next layer's A operand)
-          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(args.out) + pix * c.cout + n0);
-          float4* dlo = reinterpret_cast<float4*>(static_cast<float*>(args.out) + args.plane + pix * c.cout + n0);
+        } else {
+          // value plane and remainder plane (split FP32, the next layer's A operand), 32
+          // channels (128 B per pixel) at a time through the warp's transposing buffer
+          if (!ok) break;
+          uint4* wbuf = reinterpret_cast<uint4*>(sO + q * 4096);
+          float* orow = static_cast<float*>(args.out) + pix * c.cout + n0;
 #pragma unroll
-          for (int i = 0; i < BN / 4; ++i) {
-            const int n = n0 + 4 * i;
-            float4 u;
-            u.x = fmaxf(fmaf(acc[4 * i + 0], s_scale[n + 0], s_shift[n + 0]), 0.f);
-            u.y = fmaxf(fmaf(acc[4 * i + 1], s_scale[n + 1], s_shift[n + 1]), 0.f);
-            u.z = fmaxf(fmaf(acc[4 * i + 2], s_scale[n + 2], s_shift[n + 2]), 0.f);
-            u.w = fmaxf(fmaf(acc[4 * i + 3], s_scale[n + 3], s_shift[n + 3]), 0.f);
-            dst[i] = u;
-            dlo[i] = tf32_remainder4(u);
+          for (int k = 0; k < BN / 32; ++k) {
+            uint4 hv[8], lv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int n = n0 + 32 * k + 4 * j;
+              const float* a = acc + 32 * k + 4 * j;
+              float4 u;
+              u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), 0.f);
+              u.y = fmaxf(fmaf(a[1], s_scale[n + 1], s_shift[n + 1]), 0.f);
+              u.z = fmaxf(fmaf(a[2], s_scale[n + 2], s_shift[n + 2]), 0.f);
+              u.w = fmaxf(fmaf(a[3], s_scale[n + 3], s_shift[n + 3]), 0.f);
+              const float4 l = tf32_remainder4(u);
+              hv[j] = make_uint4(__float_as_uint(u.x), __float_as_uint(u.y), __float_as_uint(u.z), __float_as_uint(u.w));
+              lv[j] = make_uint4(__float_as_uint(l.x), __float_as_uint(l.y), __float_as_uint(l.z), __float_as_uint(l.w));
+            }
+            warp_rows_store(wbuf, hv, in_range ? reinterpret_cast<char*>(orow + 32 * k) : nullptr, lane);
+            warp_rows_store(wbuf, lv, in_range ? reinterpret_cast<char*>(orow + args.plane + 32 * k) : nullptr, lane);
           }
         }
       } else {
         const int buf = gg & (NBUF - 1);
         ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
-        __syncwarp();
+        ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
         if (!ok) break;
         tc_fence_after();
         __nv_bfloat16* o = static_cast<__nv_bfloat16*>(args.out) + pix * c.cout + n0;
@@ -752,7 +782,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 64), v);
           tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 64 + 32), v + 32);
           tmem_wait();
-          if (in_range) {
+          {
             uint32_t pk[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -762,9 +792,12 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
               pk[i] = *reinterpret_cast<uint32_t*>(&h);
             }
-            uint4* dst = reinterpret_cast<uint4*>(o + j * 64);
+            uint4 hv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            for (int i = 0; i < 8; ++i) hv[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            // 64 channels = 128 B per pixel, through the warp's transposing buffer
+            warp_rows_store(reinterpret_cast<uint4*>(sO + q * 4096), hv,
+                            in_range ? reinterpret_cast<char*>(o + j * 64) : nullptr, lane);
           }
         }
         tc_fence_before();
@@ -1180,7 +1213,7 @@ template <int MODE, int BN>
 constexpr size_t p_smem() {
   return 1024 + (size_t)p_stages<MODE, BN>() * p_kps<MODE, BN>() *
                     ((MODE == 1 ? 2 : 1) * 16384 + (MODE == 1 ? 2 : 1) * BN * 128) +
-         (p_epi_tma<MODE, BN>() ? 2 * (BN / 32) * 16384 : 0) +
+         (p_epi_tma<MODE, BN>() ? 2 * (BN / 32) * 16384 : 4 * 4096) +
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
 

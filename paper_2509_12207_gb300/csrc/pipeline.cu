@@ -158,7 +158,8 @@ int Pipeline::alloc(void** p, size_t n) {
   return PP_OK;
 }
 
-int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, cudaStream_t s) {
+int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, bool stream_k,
+                   cudaStream_t s) {
   m_ = m;
   B_ = max_batch;
   cap_ = cap_points;
@@ -190,7 +191,7 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
     // borders stay zero forever: convs write interiors only
     if ((st = cuda_status(cudaMemsetAsync(a, 0, n, s), "clear activations"))) return st;
   }
-  if (m->conv_dtype == PP_F32_TC) {
+  if (m->conv_dtype == PP_F32_TC && stream_k) {
     // one stream-K workspace, sized for the widest layer at the unit's capacity (a smaller
     // batch needs fewer arrival counters), zeroed once; every completed conv leaves it zero
     for (const LayerSpec& L : m->layers) {
@@ -385,7 +386,9 @@ int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** ou
   cudaStream_t s;
   int st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
   if (!st) st = p->model.upload(cfg, precision, s);
-  if (!st) st = p->pipe.init(&p->model, cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, cfg->autotune != 0, s);
+  if (!st)
+    st = p->pipe.init(&p->model, cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0, cfg->autotune != 0,
+                      cfg->stream_k != 0, s);
   if (!st) st = cuda_status(cudaStreamSynchronize(s), "pipeline init");
   cudaStreamDestroy(s);
   if (st) {

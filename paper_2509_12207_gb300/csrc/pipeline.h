@@ -44,7 +44,9 @@ struct Model {
 class Pipeline {
  public:
   // tune: autotune every conv layer for unit sizes 1..max_batch before capturing the graphs
-  int init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, cudaStream_t s);
+  // stream_k: own a stream-K workspace and let the autotuner consider stream-K tiles
+  int init(const Model* m, int max_batch, int cap_points, bool graphs, bool tune, bool stream_k,
+           cudaStream_t s);
   void release();
   // Enqueues the whole front end for `n` frames on `s` (graph or plain launches).  Frame i is
   // read in place when direct[i] (a 16-byte aligned device buffer), else staged into slot i

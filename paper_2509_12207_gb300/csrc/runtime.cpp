@@ -494,6 +494,7 @@ void pp_config_defaults(pp_config* cfg) {
   cfg->early_exit = 1;
   cfg->num_streams = 0;
   cfg->autotune = 1;
+  cfg->stream_k = 0;
 }
 
 int pp_create(const pp_config* cfg, pp_ctx** out) {
@@ -535,7 +536,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       u->precision = p;
       // the first unit of each precision tunes the conv tiles; later units reuse the table
       st = u->pipe.init(&c->models[p], cfg->max_batch, cfg->cap_points, cfg->use_graphs != 0,
-                        cfg->autotune != 0 && k == 0, c->aux);
+                        cfg->autotune != 0 && k == 0, cfg->stream_k != 0, c->aux);
       if (!st) st = cuda_status(cudaEventCreate(&u->start), "event");
       if (!st) st = cuda_status(cudaEventCreate(&u->done), "event");
       if (!st && used + u->pipe.bytes() > cfg->hbm_budget_bytes) {

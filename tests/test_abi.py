@@ -87,3 +87,28 @@ def test_tune_table_save_load(lib, tmp_path):
     assert [l for l in out.read_text().splitlines() if not l.startswith("#")] == []
     with pytest.raises(pp.PPError):
         pp.conv_tune_load(tmp_path / "missing.txt")
+
+
+def test_config_defaults_and_host_validation(lib):
+    """pp_config_defaults fills the documented defaults; host-side checks of the workspace and
+    split-FP32 entry points reject bad arguments without touching a GPU."""
+    import paper_2509_12207_gb300 as pp
+    cfg = pp.Config()
+    lib.pp_config_defaults(ctypes.byref(cfg))
+    assert cfg.autotune == 1 and cfg.stream_k == 0 and cfg.fp32_cuda_cores == 0
+    assert cfg.policy == pp.PP_POLICY_URGENCY
+    # stream-K workspaces exist only for the 3xTF32 dtype
+    assert lib.pp_conv_workspace_bytes(1, 62, 54, 256, 256, 1, pp.PP_BF16) == 0
+    assert lib.pp_conv_workspace_bytes(1, 62, 54, 256, 256, 1, pp.PP_F32_TC) > 0
+    assert lib.pp_conv_workspace_bytes(1, 62, 54, 250, 256, 1, pp.PP_F32_TC) == 0
+    assert lib.pp_tf32_split(None, None, 0, None) == pp.PP_OK
+    assert lib.pp_tf32_split(16, 16, -1, None) == pp.PP_EINVAL
+    assert lib.pp_tf32_split(16, 32, 8, None) == pp.PP_EINVAL and b"overlap" in lib.pp_last_error()
+    assert lib.pp_tf32_split(17, 4096, 8, None) == pp.PP_EINVAL and b"aligned" in lib.pp_last_error()
+    # a 3xTF32 tile index is either plain (persistent = 1) or its stream-K twin (3)
+    n = lib.pp_conv_tile_count(pp.PP_F32_TC)
+    assert n % 2 == 0
+    for t in range(n):
+        info = pp.conv_tile_info(pp.PP_F32_TC, t)
+        assert info[3] == (1 if t < n // 2 else 3)
+        assert info[:3] == pp.conv_tile_info(pp.PP_F32_TC, t % (n // 2))[:3]

@@ -75,6 +75,25 @@ def test_pipeline_batch_and_graph(prec, small_clouds):
         p.destroy()
 
 
+def test_pipeline_stream_k(small_clouds):
+    """With stream_k the autotuner may pick stream-K tiles for the 3xTF32 convs: results stay
+    within the FP32 tolerance and are bit-reproducible launch to launch."""
+    cfg, keep = pp.make_config(GEOM_SMALL, BACKBONE_SMALL, W_SMALL, max_batch=3, cap_points=150000, stream_k=1)
+    p = pp.Pipeline(cfg, pp.PP_F32)
+    try:
+        frames = [torch.from_numpy(c).to(DEV) for c in small_clouds]
+        p.run(frames)
+        torch.cuda.synchronize()
+        first = [p.output_tensor(i, 0).clone() for i in range(3)]
+        for i, c in enumerate(small_clouds):
+            _check_out(_interior(first[i]), _ref(c), pp.PP_F32)
+        p.run(frames)
+        torch.cuda.synchronize()
+        assert all(torch.equal(p.output_tensor(i, 0), first[i]) for i in range(3))
+    finally:
+        p.destroy()
+
+
 @pytest.fixture(scope="module")
 def full_frame():
     w = pillar_weights(BACKBONE_FULL, 11)
