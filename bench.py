@@ -49,7 +49,9 @@ def _args():
                     help="conv tile table: loaded (no autotuning) if the file exists, else written after "
                          "autotuning, so that a profiled run launches the same tiles as a plain one")
     ap.add_argument("--serve-sweep", default=None,
-                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed]")
+                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac]")
+    ap.add_argument("--serve-modes", default="urgency,plain",
+                    help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -458,6 +460,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     delayed launch, overlapped batched sync) with continuous batching of up to 8 frames per
     graph launch; chains BF16 (``mixed``: odd chains BF16, even FP32).  mode "plain": every
     frame launched on arrival, kernel by kernel, FP32, on its chain's default-priority stream.
+    modes "edf" / "sjf" / "hrrn" / "lcuf": the urgency mode's units and sync, released in that
+    comparison order (no early exit, reservation or delaying).
     Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
     frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
     f_a and f_d).  A frame the budget cannot admit counts as a miss."""
@@ -465,9 +469,17 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     w = pillar_weights(bb, 7)
     chains = serving_chains(n_chains, mixed=mixed)
+    others = {"edf": pp.PP_POLICY_EDF, "sjf": pp.PP_POLICY_SJF, "hrrn": pp.PP_POLICY_HRRN,
+              "lcuf": pp.PP_POLICY_LCUF}
     if mode == "urgency":
         knobs = dict(policy=pp.PP_POLICY_URGENCY, max_batch=8, use_graphs=1, max_closed=2,
                      delta_eval_us=500.0, th_urgent=0.0, th_calib_frames=64, early_exit=1, units=8)
+        prec = [c.precision for c in chains]
+    elif mode in others:
+        # the same batched, graph-launched units and batched sync, released in the comparison
+        # policy's order instead of by urgency (no early exit, reservation or delaying)
+        knobs = dict(policy=others[mode], max_batch=8, use_graphs=1, max_closed=2,
+                     delta_eval_us=500.0, th_urgent=-1.0, early_exit=0, units=8)
         prec = [c.precision for c in chains]
     else:
         knobs = dict(policy=pp.PP_POLICY_FIFO, max_batch=1, use_graphs=0, max_closed=0, early_exit=0,
@@ -575,7 +587,7 @@ def main():
             n, rate, secs = int(parts[0]), float(parts[1]), float(parts[2])
             mixed = len(parts) > 3 and parts[3] == "mixed"
             dfac = float(parts[4]) if len(parts) > 4 else 1.0
-            for mode in ("urgency", "plain"):
+            for mode in a.serve_modes.split(","):
                 out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac))
                 print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"metric": "deadline-miss ratio and p99 chain latency, urgency-served batched "

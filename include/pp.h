@@ -249,12 +249,19 @@ int pp_device_error(uint32_t* code, int32_t clear);
 /* delayed launching behind urgent units of other chains (Section 4.4.4), and batched launch  */
 /* synchronisation with overlap (Section 4.4.5).  Policy PP_POLICY_FIFO is the plain baseline:*/
 /* every frame launched on arrival on its chain's default-priority stream, kernel by kernel,  */
-/* no graph, no batching, no urgency.                                                        */
+/* no graph, no batching, no urgency.  The other policies are the textbook orders the paper */
+/* compares against (Section 5, comparison of policies; not defined there): they replace the */
+/* urgency order and its stream ranking, with no early exit, reservation or delaying:         */
+/*   PP_POLICY_EDF   earliest absolute deadline first;                                        */
+/*   PP_POLICY_SJF   shortest remaining estimate (est_gpu + est_cpu) first;                   */
+/*   PP_POLICY_HRRN  highest response ratio (waiting + estimate) / estimate first;            */
+/*   PP_POLICY_LCUF  lowest chain utilisation (estimate / period) first.                      */
 /* Times are microseconds on the host monotonic clock (pp_now_us).                           */
 /* Threading: every entry point may be called from any thread; one internal dispatcher       */
 /* thread does the rest.                                                                     */
 
-enum { PP_POLICY_FIFO = 0, PP_POLICY_URGENCY = 1 };
+enum { PP_POLICY_FIFO = 0, PP_POLICY_URGENCY = 1, PP_POLICY_EDF = 2, PP_POLICY_SJF = 3,
+       PP_POLICY_HRRN = 4, PP_POLICY_LCUF = 5 };
 enum { PP_FRAME_DONE = 0, PP_FRAME_DROPPED = 1, PP_FRAME_ERROR = 2 };
 #define PP_MAX_BLOCKS 4
 #define PP_MAX_CHAINS 64
@@ -276,7 +283,7 @@ typedef struct {
   int32_t precisions;           /* bit 0: FP32 units, bit 1: BF16 units                       */
   int32_t units;                /* units per precision; 0 = as many as the budget allows (16) */
   uint64_t hbm_budget_bytes;    /* device memory the context may hold (units + staging)       */
-  int32_t policy;               /* PP_POLICY_FIFO or PP_POLICY_URGENCY                        */
+  int32_t policy;               /* PP_POLICY_* (FIFO, URGENCY, EDF, SJF, HRRN, LCUF)          */
   int32_t use_graphs;           /* replay one CUDA graph per unit launch                      */
   double delta_eval_us;         /* batch closes when its estimated GPU time reaches this      */
   int32_t max_closed;           /* closed batches allowed in flight: 2 overlapped, 1 sync,    */
@@ -412,11 +419,14 @@ int pp_pipeline_destroy(pp_pipeline* p);
 typedef struct {
   uint64_t frame_id;
   int32_t chain_id, precision;
-  double t_arr_us, deadline_us, est_gpu_us, est_cpu_us, util;
+  double t_arr_us, deadline_us, est_gpu_us, est_cpu_us;
+  double util;                   /* GPU utilisation of the frame's kernels (delay exemption)  */
+  double period_us;              /* its chain's period (PP_POLICY_LCUF)                       */
 } pp_policy_frame;
 typedef struct {
   int32_t chain_id;
-  double ul;                     /* urgency of an active unit when it was released (1/us)     */
+  double ul;                     /* priority of an active unit when it was released           */
+                                 /* (pp_policy_priority; urgency 1/us for PP_POLICY_URGENCY)  */
 } pp_policy_active;
 typedef struct {
   int32_t policy, max_batch, max_closed, num_pri, early_exit;
@@ -433,6 +443,11 @@ int pp_policy_decide(const pp_policy_config* cfg, double t_us, const pp_policy_f
                      int32_t n_ready, const pp_policy_active* active, int32_t n_active,
                      int32_t closed_pending, pp_policy_decision* out, uint64_t* drops,
                      int32_t drops_cap);
+/* A frame's priority under cfg->policy at time t (higher = released first): URGENCY: UL = 1 /
+ * slack (-inf for slack <= 0); EDF: -deadline; SJF: -(est_gpu + est_cpu); HRRN: (t - t_arr +
+ * e) / e with e = est_gpu + est_cpu (+inf when e <= 0); LCUF: -(e / period) (-inf when the
+ * period is not positive); FIFO: -t_arr.  Stream levels rank active units by this value. */
+double pp_policy_priority(const pp_policy_config* cfg, double t_us, const pp_policy_frame* frame);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,16 @@ release units (a unit = up to ``max_batch`` frames run as one launch):
   wait for the previous batch; 1 = synchronous batched; 0 = no synchronisation);
 * the overall deadline-miss ratio (Eq. 3): mean over chains of each chain's miss ratio.
 
+The comparison policies of the paper's Section 5 (EDF, SJF, HRRN and lowest chain utilisation
+first; the paper names them without definitions) are the textbook orders: a priority value
+replaces the urgency in ordering frames and ranking active units onto stream levels
+0 .. NUM_PRI-1, without early exit, reservation or delaying:
+
+* EDF: earliest absolute deadline first (priority -deadline);
+* SJF: shortest remaining estimate e = est_gpu + est_cpu first (priority -e);
+* HRRN: highest response ratio (waited + e) / e first (+inf for e <= 0);
+* LCUF: lowest chain utilisation e / period first (priority -e / period; -inf without a period).
+
 Readings where the paper is silent (also in the design notes): urgency order breaks ties by
 (chain id, arrival time, frame id); the FIFO baseline orders by (arrival, chain id, frame id);
 rank r counts the active non-urgent units strictly more urgent than the candidate, n counts
@@ -37,6 +47,10 @@ from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
 POLICY_FIFO = 0
 POLICY_URGENCY = 1
+POLICY_EDF = 2
+POLICY_SJF = 3
+POLICY_HRRN = 4
+POLICY_LCUF = 5
 
 NONE, RELEASE, WAIT, DELAY = 0, 1, 2, 3
 
@@ -63,12 +77,13 @@ class Ready:
     est_cpu: float = 0.0            # remaining CPU estimate (us)
     precision: int = 0
     util: float = 1.0
+    period: float = 0.0             # the chain's period (us), for LCUF
 
 
 @dataclasses.dataclass
 class Active:
     chain_id: int
-    ul: float                       # urgency evaluated at release
+    ul: float                       # priority (urgency for the urgency policy) at release
 
 
 @dataclasses.dataclass
@@ -123,10 +138,37 @@ def must_delay(f: Ready, ul: float, active: Sequence[Active], cfg: PolicyConfig)
     return any(a.chain_id != f.chain_id and a.ul > cfg.th_urgent and a.ul > ul for a in active)
 
 
+def priority(f: Ready, t: float, cfg: PolicyConfig) -> float:
+    """The value a policy releases by (higher first) and ranks active units by."""
+    e = f.est_gpu + f.est_cpu
+    if cfg.policy == POLICY_URGENCY:
+        return urgency(slack(f, t))
+    if cfg.policy == POLICY_EDF:
+        return -f.deadline
+    if cfg.policy == POLICY_SJF:
+        return -e
+    if cfg.policy == POLICY_HRRN:
+        return (t - f.t_arr + e) / e if e > 0 else math.inf
+    if cfg.policy == POLICY_LCUF:
+        return -(e / f.period) if f.period > 0 else -math.inf
+    return -f.t_arr
+
+
 def order_key(f: Ready, t: float, cfg: PolicyConfig) -> tuple:
     if cfg.policy == POLICY_URGENCY:
         return (slack(f, t), f.chain_id, f.t_arr, f.frame_id)
-    return (f.t_arr, f.chain_id, f.frame_id)
+    if cfg.policy == POLICY_FIFO:
+        return (f.t_arr, f.chain_id, f.frame_id)
+    return (-priority(f, t, cfg), f.chain_id, f.t_arr, f.frame_id)
+
+
+def rank_level(p: float, active: Sequence[Active], num_pri: int) -> int:
+    """Comparison policies: the candidate's rank among all active units (strictly higher
+    priority first) spread over levels 0 .. NUM_PRI-1."""
+    if num_pri <= 1:
+        return 0
+    r = sum(1 for a in active if a.ul > p)
+    return (r * num_pri) // (len(active) + 1)
 
 
 def decide(t: float, ready: Sequence[Ready], active: Sequence[Active], closed_pending: int,
@@ -154,8 +196,10 @@ def decide(t: float, ready: Sequence[Ready], active: Sequence[Active], closed_pe
             batch.append(f.frame_id)
     if cfg.policy == POLICY_URGENCY:
         level = stream_level(ul, active, cfg)
-    else:
+    elif cfg.policy == POLICY_FIFO:
         level = max(0, cfg.num_pri - 1)
+    else:
+        level = rank_level(priority(head, t, cfg), active, cfg.num_pri)
     return Decision(RELEASE, batch, level, drops)
 
 
@@ -222,6 +266,7 @@ class SimFrame:
     precision: int = 0
     util: float = 1.0
     est: Optional[List[float]] = None   # estimates per unit (defaults to the true durations)
+    period: float = 0.0                 # the chain's period (us), for LCUF
 
 
 @dataclasses.dataclass
@@ -269,7 +314,7 @@ def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: fl
         # decisions at time t
         while True:
             rlist = [Ready(f.frame_id, f.chain_id, f.t_arr, f.deadline,
-                           sum(est[f.frame_id][nxt[f.frame_id]:]), 0.0, f.precision, f.util)
+                           sum(est[f.frame_id][nxt[f.frame_id]:]), 0.0, f.precision, f.util, f.period)
                      for f in ready.values()]
             d = decide(t, rlist, [a for a, _, _ in active.values()], gate.pending, cfg)
             for fid in d.drops:
@@ -282,8 +327,9 @@ def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: fl
                 break
             members = [(fid, nxt[fid]) for fid in d.frames]
             head = by_id[d.frames[0]]
-            ul = urgency(slack(Ready(head.frame_id, head.chain_id, head.t_arr, head.deadline,
-                                     sum(est[head.frame_id][nxt[head.frame_id]:])), t))
+            ul = priority(Ready(head.frame_id, head.chain_id, head.t_arr, head.deadline,
+                                sum(est[head.frame_id][nxt[head.frame_id]:]), 0.0, head.precision,
+                                head.util, head.period), t, cfg)
             unit = seq
             seq += 1
             active[unit] = (Active(head.chain_id, ul), members, d.level)

@@ -39,7 +39,7 @@ class Geometry(ctypes.Structure):
 
 MAX_BLOCKS = 4
 MAX_CHAINS = 64
-PP_POLICY_FIFO, PP_POLICY_URGENCY = 0, 1
+PP_POLICY_FIFO, PP_POLICY_URGENCY, PP_POLICY_EDF, PP_POLICY_SJF, PP_POLICY_HRRN, PP_POLICY_LCUF = 0, 1, 2, 3, 4, 5
 PP_FRAME_DONE, PP_FRAME_DROPPED, PP_FRAME_ERROR = 0, 1, 2
 PP_DECIDE_NONE, PP_DECIDE_RELEASE, PP_DECIDE_WAIT, PP_DECIDE_DELAY = 0, 1, 2, 3
 
@@ -103,7 +103,8 @@ class Stats(ctypes.Structure):
 class PolicyFrame(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_uint64), ("chain_id", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("t_arr_us", ctypes.c_double), ("deadline_us", ctypes.c_double),
-                ("est_gpu_us", ctypes.c_double), ("est_cpu_us", ctypes.c_double), ("util", ctypes.c_double)]
+                ("est_gpu_us", ctypes.c_double), ("est_cpu_us", ctypes.c_double), ("util", ctypes.c_double),
+                ("period_us", ctypes.c_double)]
 
 
 class PolicyActive(ctypes.Structure):
@@ -179,6 +180,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int32)]),
     "pp_pipeline_bytes": (_SZ, [_P]),
     "pp_pipeline_destroy": (ctypes.c_int, [_P]),
+    "pp_policy_priority": (ctypes.c_double, [ctypes.POINTER(PolicyConfig), ctypes.c_double,
+                                             ctypes.POINTER(PolicyFrame)]),
     "pp_policy_decide": (ctypes.c_int, [ctypes.POINTER(PolicyConfig), ctypes.c_double, ctypes.POINTER(PolicyFrame),
                                         _I, ctypes.POINTER(PolicyActive), _I, _I, ctypes.POINTER(PolicyDecision),
                                         ctypes.POINTER(ctypes.c_uint64), _I]),
@@ -648,3 +651,9 @@ def policy_decide(cfg, t_us, ready, active, closed_pending):
     _check(lib().pp_policy_decide(ctypes.byref(pc), float(t_us), rf, len(ready), ac, len(active),
                                   int(closed_pending), ctypes.byref(d), drops, len(ready)))
     return d.kind, [int(d.frames[i]) for i in range(d.n_frames)], d.level, [int(drops[i]) for i in range(d.n_drops)]
+
+
+def policy_priority(cfg, t_us, frame):
+    """pp_policy_priority: the priority of one frame (dict of PolicyFrame fields) under cfg."""
+    return float(lib().pp_policy_priority(ctypes.byref(PolicyConfig(**cfg)), float(t_us),
+                                          ctypes.byref(PolicyFrame(**frame))))

@@ -292,6 +292,22 @@ pp_policy_config policy_cfg(pp_ctx* c) {
   return p;
 }
 
+// A ready frame as the release rule sees it: one unit's estimate remains; its kernels fill the
+// GPU (utilisation 1.0, so the delay exemption never applies); its chain's period.
+pp_policy_frame policy_frame(pp_ctx* c, const Frame* f) {
+  pp_policy_frame p;
+  p.frame_id = f->id;
+  p.chain_id = f->chain;
+  p.precision = f->precision;
+  p.t_arr_us = f->t_arr;
+  p.deadline_us = f->deadline;
+  p.est_gpu_us = unit_est(c, f->precision, 1);
+  p.est_cpu_us = 0.0;
+  p.util = 1.0;
+  p.period_us = c->chains[f->chain].period_ms * 1000.0;
+  return p;
+}
+
 int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   Frame* head = c->frames[d.frames[0]];
   const int prec = head->precision;
@@ -306,8 +322,12 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   u->nf = d.n_frames;
   u->level = d.level;
   u->head_chain = head->chain;
-  const double slack = head->deadline - unit_est(c, prec, 1) - t;
-  u->ul = slack > 0 ? 1.0 / slack : -INFINITY;
+  {
+    // the unit's priority when released (urgency UL for the urgency policy)
+    const pp_policy_config pc = policy_cfg(c);
+    const pp_policy_frame hf = policy_frame(c, head);
+    u->ul = pp_policy_priority(&pc, t, &hf);
+  }
   u->est = unit_est(c, prec, d.n_frames);
   for (int i = 0; i < d.n_frames; ++i) {
     Frame* f = c->frames[d.frames[i]];
@@ -383,18 +403,7 @@ double decide_all(pp_ctx* c) {
     calibrate(c, t);
     std::vector<pp_policy_frame> rf;
     rf.reserve(c->ready.size());
-    for (Frame* f : c->ready) {
-      pp_policy_frame p;
-      p.frame_id = f->id;
-      p.chain_id = f->chain;
-      p.precision = f->precision;
-      p.t_arr_us = f->t_arr;
-      p.deadline_us = f->deadline;
-      p.est_gpu_us = unit_est(c, f->precision, 1);
-      p.est_cpu_us = 0.0;
-      p.util = 1.0;
-      rf.push_back(p);
-    }
+    for (Frame* f : c->ready) rf.push_back(policy_frame(c, f));
     std::vector<pp_policy_active> act;
     for (Unit* u : c->units)
       if (u->running) act.push_back({u->head_chain, u->ul});
@@ -502,7 +511,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (cfg->max_batch < 1 || cfg->max_batch > 8) return fail(PP_EINVAL, "create: max_batch must be 1..8");
   if (cfg->cap_points < 1 || cfg->cap_points > (1 << 24)) return fail(PP_EINVAL, "create: cap_points 1..2^24");
   if ((cfg->precisions & 3) == 0) return fail(PP_EINVAL, "create: no precision enabled");
-  if (cfg->policy != PP_POLICY_FIFO && cfg->policy != PP_POLICY_URGENCY) return fail(PP_EINVAL, "create: bad policy");
+  if (cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_LCUF) return fail(PP_EINVAL, "create: bad policy");
   if (cfg->units < 0 || cfg->units > 64 || cfg->max_closed < 0 || !(cfg->delta_eval_us >= 0) ||
       cfg->max_admitted < 0 ||
       !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0)

@@ -307,3 +307,28 @@ def test_runtime_submit_many_partial_admission():
         assert ctx.stats()["rejected"] == 2
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("policy", [pp.PP_POLICY_EDF, pp.PP_POLICY_SJF, pp.PP_POLICY_HRRN, pp.PP_POLICY_LCUF])
+def test_runtime_comparison_policies(policy, small_clouds):
+    """The comparison release orders serve every frame, with results identical to the oracle's
+    pillars and within tolerance."""
+    ctx, keep = _ctx(policy=policy, max_batch=4, th_urgent=-1.0, early_exit=0)
+    try:
+        ctx.register_chain(0, 50.0, 50.0, pp.PP_BF16)
+        ctx.register_chain(1, 200.0, 200.0, pp.PP_BF16)
+        dev = [torch.from_numpy(c).to(DEV) for c in small_clouds]
+        ids = {}
+        for i, c in enumerate(dev):
+            for chain in (0, 1):
+                rc, fid = ctx.submit(chain, c)
+                assert rc == pp.PP_OK
+                ids[fid] = i
+        res = _drain(ctx, len(ids))
+        refs = [_ref(c) for c in small_clouds]
+        for r in res:
+            assert r.status == pp.PP_FRAME_DONE
+            assert r.num_pillars == refs[ids[r.frame_id]]["vox"]["num_pillars"]
+        ctx.release_many([r.frame_id for r in res])
+    finally:
+        ctx.destroy()

@@ -228,3 +228,53 @@ def test_des_early_exit_and_batching_invariants():
     assert not fifo.dropped and len(fifo.done) == len(frames)
     assert [m[0][0] for _t, m, _l in fifo.releases] == [f.frame_id for f in
                                                         sorted(frames, key=lambda f: (f.t_arr, f.chain_id))]
+
+
+def test_comparison_policies_hand_example():
+    """Three frames with hand-computed orders.  At t = 1000 us:
+         frame  arrival  deadline  estimate  period   wait  ratio (w+e)/e  util e/P
+         A      0        5000      400       50000    1000  3.5            0.008
+         B      600      3000      100       200000   400   5.0            0.0005
+         C      900      9000      1600      100000   100   1.0625         0.016
+    EDF: B (3000), A (5000), C;  SJF: B (100), A (400), C;  HRRN: B (5.0), A (3.5), C (1.0625);
+    LCUF: B (0.0005), A (0.008), C (0.016).  FIFO: A, B, C.  A unit takes every ready frame of
+    the same precision in that order."""
+    t = 1000.0
+    ready = [S.Ready(1, 0, 0.0, 5000.0, 400.0, period=50000.0),
+             S.Ready(2, 1, 600.0, 3000.0, 100.0, period=200000.0),
+             S.Ready(3, 2, 900.0, 9000.0, 1600.0, period=100000.0)]
+    want = {S.POLICY_EDF: [2, 1, 3], S.POLICY_SJF: [2, 1, 3], S.POLICY_HRRN: [2, 1, 3],
+            S.POLICY_LCUF: [2, 1, 3], S.POLICY_FIFO: [1, 2, 3]}
+    for pol, order in want.items():
+        d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0))
+        assert d.kind == S.RELEASE and d.frames == order, pol
+    # a swap that separates the policies: make C the shortest and lowest-utilisation job
+    ready[2] = S.Ready(3, 2, 900.0, 9000.0, 50.0, period=400000.0)   # ratio (100+50)/50 = 3.0
+    got = {pol: S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0)).frames
+           for pol in (S.POLICY_EDF, S.POLICY_SJF, S.POLICY_HRRN, S.POLICY_LCUF)}
+    assert got[S.POLICY_EDF] == [2, 1, 3]        # deadlines unchanged
+    assert got[S.POLICY_SJF] == [3, 2, 1]        # 50 < 100 < 400
+    assert got[S.POLICY_HRRN] == [2, 1, 3]       # 5.0 > 3.5 > 3.0
+    assert got[S.POLICY_LCUF] == [3, 2, 1]       # 0.000125 < 0.0005 < 0.008
+
+
+def test_comparison_policies_match_sorting():
+    """On random ready sets the head each comparison policy releases is the textbook optimum:
+    min deadline, min estimate, max response ratio, min utilisation (ties: chain, arrival, id)."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        t = 1e5
+        ready = [S.Ready(i, int(rng.integers(0, 4)), t - float(rng.integers(0, 5000)),
+                         t + float(rng.integers(-100, 20000)), float(rng.integers(10, 3000)),
+                         float(rng.choice([0.0, 30.0])), 0, 1.0, float(rng.choice([5e4, 1e5, 2e5])))
+                 for i in range(int(rng.integers(1, 9)))]
+        tie = lambda f: (f.chain_id, f.t_arr, f.frame_id)
+        keys = {S.POLICY_EDF: lambda f: (f.deadline,) + tie(f),
+                S.POLICY_SJF: lambda f: (f.est_gpu + f.est_cpu,) + tie(f),
+                S.POLICY_HRRN: lambda f: (-(t - f.t_arr + f.est_gpu + f.est_cpu) / (f.est_gpu + f.est_cpu),) + tie(f),
+                S.POLICY_LCUF: lambda f: ((f.est_gpu + f.est_cpu) / f.period,) + tie(f)}
+        for pol, key in keys.items():
+            d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0, max_batch=8))
+            assert d.frames[0] == min(ready, key=key).frame_id, pol
+            assert d.drops == []                  # no early exit outside the urgency policy

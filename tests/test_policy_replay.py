@@ -27,10 +27,11 @@ def _random_state(rng):
         ready.append(dict(frame_id=int(1000 + i * 7 % 13 + 20 * i), chain_id=int(rng.integers(0, 6)),
                           precision=int(rng.integers(0, 2)), t_arr_us=t_arr, deadline_us=t_arr + D,
                           est_gpu_us=est, est_cpu_us=float(rng.choice([0.0, 50.0])),
-                          util=float(rng.choice([0.05, 0.1, 0.5, 1.0]))))
+                          util=float(rng.choice([0.05, 0.1, 0.5, 1.0])),
+                          period_us=float(rng.choice([0.0, 50000.0, 100000.0, 200000.0]))))
     active = [(int(rng.integers(0, 6)), float(rng.choice([-np.inf, 1e-5, 1e-4, 5e-4, 2e-3, 1e-2])))
               for _ in range(int(rng.integers(0, 6)))]
-    cfg = dict(policy=int(rng.integers(0, 2)), max_batch=int(rng.integers(1, 9)),
+    cfg = dict(policy=int(rng.integers(0, 6)), max_batch=int(rng.integers(1, 9)),
                max_closed=int(rng.integers(0, 3)), num_pri=int(rng.integers(1, 7)),
                early_exit=int(rng.integers(0, 2)),
                th_urgent=float(rng.choice([0.0, -1.0, 1e-4, 1e-3])), util_exempt=0.1)
@@ -42,7 +43,7 @@ def _oracle(t, ready, active, closed, cfg):
                         th_urgent=cfg["th_urgent"], util_exempt=cfg["util_exempt"],
                         early_exit=bool(cfg["early_exit"]), num_pri=cfg["num_pri"])
     rr = [S.Ready(r["frame_id"], r["chain_id"], r["t_arr_us"], r["deadline_us"], r["est_gpu_us"],
-                  r["est_cpu_us"], r["precision"], r["util"]) for r in ready]
+                  r["est_cpu_us"], r["precision"], r["util"], r["period_us"]) for r in ready]
     aa = [S.Active(c, u) for c, u in active]
     return S.decide(t, rr, aa, closed, oc)
 
@@ -50,7 +51,7 @@ def _oracle(t, ready, active, closed, cfg):
 def test_replay_random_states(pp):
     rng = np.random.default_rng(2024)
     kinds = {}
-    for _ in range(6000):
+    for _ in range(12000):
         t, ready, active, closed, cfg = _random_state(rng)
         kind, frames, level, drops = pp.policy_decide(cfg, t, ready, active, closed)
         d = _oracle(t, ready, active, closed, cfg)
@@ -100,3 +101,55 @@ def test_replay_des_trace(pp):
             assert (fr, level) == (d.frames, d.level)
         seen.add(kind)
     assert S.RELEASE in seen and S.WAIT in seen
+
+
+def test_replay_priorities(pp):
+    """pp_policy_priority agrees with the oracle's priority() for every policy, including the
+    degenerate cases (no estimate, no period, non-positive slack)."""
+    rng = np.random.default_rng(11)
+    for _ in range(3000):
+        t, ready, active, closed, cfg = _random_state(rng)
+        for r in ready[:3]:
+            if rng.random() < 0.2:
+                r["est_gpu_us"], r["est_cpu_us"] = 0.0, 0.0
+            got = pp.policy_priority(cfg, t, r)
+            f = S.Ready(r["frame_id"], r["chain_id"], r["t_arr_us"], r["deadline_us"], r["est_gpu_us"],
+                        r["est_cpu_us"], r["precision"], r["util"], r["period_us"])
+            want = S.priority(f, t, S.PolicyConfig(policy=cfg["policy"]))
+            assert got == want or (np.isnan(got) and np.isnan(want)), (cfg["policy"], r, got, want)
+
+
+@pytest.mark.parametrize("policy", [S.POLICY_EDF, S.POLICY_SJF, S.POLICY_HRRN, S.POLICY_LCUF])
+def test_replay_des_trace_other_policies(pp, policy):
+    """The comparison policies through a whole simulated run: every decision the DES takes is
+    the library's decision on the same state."""
+    rng = np.random.default_rng(9 + policy)
+    frames = []
+    for i in range(200):
+        t = float(i * 35 + rng.integers(0, 25))
+        frames.append(S.SimFrame(i, i % 5, t, t + float(rng.choice([200, 400, 900])),
+                                 [float(rng.integers(20, 150))], precision=(i % 5) % 2,
+                                 period=float([50000, 100000, 200000][i % 3])))
+    cfg = S.PolicyConfig(policy=policy, max_batch=4, delta_eval_us=150.0, max_closed=2, num_pri=6)
+    calls = []
+    orig = S.decide
+
+    def spy(t, ready, active, closed, c):
+        d = orig(t, ready, active, closed, c)
+        calls.append((t, list(ready), list(active), closed, d))
+        return d
+    S.decide = spy
+    try:
+        S.simulate(frames, cfg)
+    finally:
+        S.decide = orig
+    assert len(calls) > 200
+    pc = dict(policy=policy, max_batch=4, max_closed=2, num_pri=6, early_exit=1, th_urgent=0.0, util_exempt=0.1)
+    for t, ready, active, closed, d in calls:
+        rd = [dict(frame_id=f.frame_id, chain_id=f.chain_id, precision=f.precision, t_arr_us=f.t_arr,
+                   deadline_us=f.deadline, est_gpu_us=f.est_gpu, est_cpu_us=f.est_cpu, util=f.util,
+                   period_us=f.period) for f in ready]
+        kind, fr, level, drops = pp.policy_decide(pc, t, rd, [(a.chain_id, a.ul) for a in active], closed)
+        assert (kind, drops) == (d.kind, d.drops)
+        if kind == S.RELEASE:
+            assert (fr, level) == (d.frames, d.level)
