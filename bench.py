@@ -76,8 +76,8 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (206.5e6, "72fd56f864ae962dc6c7253f51fd32cced8094d918aa446bd7f7eec3b51ff75a"),
-    "cfg3-bf16": (84.5e6, "72fd56f864ae962dc6c7253f51fd32cced8094d918aa446bd7f7eec3b51ff75a"),
+    "cfg2-fp32": (387.8e6, "64c55a349cbce4b8ef49151f936c7289a1661d46f482566e91d848c000aa0223"),
+    "cfg3-bf16": (84.6e6, "64c55a349cbce4b8ef49151f936c7289a1661d46f482566e91d848c000aa0223"),
 }
 
 
@@ -492,31 +492,11 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
         for c, p in zip(chains, prec):
             ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
         ev = arrival_times(chains, duration_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed)
-        rejected = {}
-        slow = []  # frames slower than 5 ms: where the time went
-        t0 = pp.now_us() + 20000.0
-        i, outstanding = 0, 0
-        while i < len(ev) or outstanding:
-            now = pp.now_us()
-            while i < len(ev) and t0 + ev[i][0] * 1000.0 <= now:
-                t_ms, cid, n = ev[i]
-                t_arr = t0 + t_ms * 1000.0
-                rc, _fid = ctx.submit(cid, clouds[i % len(clouds)][:n], t_arrival_us=t_arr)
-                if rc == pp.PP_OK:
-                    outstanding += 1
-                else:
-                    rejected[cid] = rejected.get(cid, 0) + 1
-                i += 1
-            wait = 2000.0 if i >= len(ev) else max(0.0, t0 + ev[i][0] * 1000.0 - pp.now_us())
-            got = ctx.poll(256, timeout_us=int(min(wait, 2000.0)))
-            for r in got:
-                if r.t_done_us - r.t_arr_us > 5000.0 and len(slow) < 8:
-                    slow.append({"chain": r.chain_id, "status": r.status, "batch": r.batch, "level": r.level,
-                                 "t_ms": round((r.t_arr_us - t0) / 1e3, 3),
-                                 "wait_ms": round((r.t_release_us - r.t_arr_us) / 1e3, 3),
-                                 "run_ms": round((r.t_done_us - r.t_release_us) / 1e3, 3)})
-            ctx.release_many([r.frame_id for r in got])
-            outstanding -= len(got)
+        # real-time replay from the library's own load generator (pp_replay): submissions at
+        # their scheduled times, results polled and released as they complete
+        arrivals = [(20000.0 + t_ms * 1000.0, cid, i % len(clouds), n) for i, (t_ms, cid, n) in enumerate(ev)]
+        rep = ctx.replay(arrivals, clouds, timeout_us=30e6)
+        rejected = {c: r for c, r in enumerate(rep["chain_rejected"]) if r}
         st = ctx.stats()
     finally:
         ctx.destroy()
@@ -534,7 +514,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             "frames_per_s": st["done"] / duration_s, "mean_batch": st["mean_batch"],
             "delayed": st["delayed_releases"], "collisions": st["collisions"],
             "th_urgent_per_ms": st["th_urgent"] * 1e3 if st["th_urgent"] > 0 else None,
-            "sched_us_per_decision": st["sched_us_per_decision"], "slow_frames": slow}
+            "sched_us_per_decision": st["sched_us_per_decision"],
+            "submit_late_us": {"mean": rep["submit_late_us_mean"], "max": rep["submit_late_us_max"]}}
 
 
 def _serving_clouds(torch):

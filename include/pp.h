@@ -396,6 +396,29 @@ int pp_destroy(pp_ctx* ctx);
 /* Host monotonic clock in microseconds. */
 double pp_now_us(void);
 
+/* Real-time trace replay (a load generator for serving measurements; the paper has no
+ * counterpart).  Frame k arrives start + arrivals[k].t_us after the call begins (arrivals
+ * sorted by t_us) and is submitted then, from the calling thread, with t_arrival = its
+ * scheduled time and the first n_points points of clouds[cloud] (is_device_ptr: all clouds
+ * device memory, borrowed for the call; else host memory, copied at submission).  Completed
+ * frames are polled and released as they come; the call returns once every admitted frame has
+ * completed, or PP_ETIMEDOUT timeout_us after the last arrival.  A frame the budget cannot
+ * admit is counted as rejected (per chain) and not retried. */
+typedef struct {
+  double t_us;
+  int32_t chain_id, cloud;
+  int64_t n_points;
+} pp_arrival;
+typedef struct {
+  uint64_t submitted, rejected, completed, dropped;
+  uint64_t chain_rejected[PP_MAX_CHAINS];
+  double wall_s;
+  double submit_late_us_max, submit_late_us_mean;  /* submission behind its scheduled time */
+} pp_replay_stats;
+int pp_replay(pp_ctx* ctx, const pp_arrival* arrivals, int64_t n, const float* const* clouds,
+              const int64_t* cloud_points, int32_t n_clouds, int32_t is_device_ptr, double timeout_us,
+              pp_replay_stats* out);
+
 /* ---------------------------------------------------------------------------------------- */
 /* One release unit without the runtime: buffers for `max_batch` frames of one precision,    */
 /* the whole front end as plain launches or one CUDA graph per batch size.                   */

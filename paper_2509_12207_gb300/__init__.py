@@ -100,6 +100,18 @@ class Stats(ctypes.Structure):
         return d
 
 
+class Arrival(ctypes.Structure):
+    _fields_ = [("t_us", ctypes.c_double), ("chain_id", ctypes.c_int32), ("cloud", ctypes.c_int32),
+                ("n_points", ctypes.c_int64)]
+
+
+class ReplayStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("dropped", ctypes.c_uint64), ("chain_rejected", ctypes.c_uint64 * MAX_CHAINS),
+                ("wall_s", ctypes.c_double), ("submit_late_us_max", ctypes.c_double),
+                ("submit_late_us_mean", ctypes.c_double)]
+
+
 class PolicyFrame(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_uint64), ("chain_id", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("t_arr_us", ctypes.c_double), ("deadline_us", ctypes.c_double),
@@ -182,6 +194,8 @@ _SIGS = {
     "pp_pipeline_destroy": (ctypes.c_int, [_P]),
     "pp_policy_priority": (ctypes.c_double, [ctypes.POINTER(PolicyConfig), ctypes.c_double,
                                              ctypes.POINTER(PolicyFrame)]),
+    "pp_replay": (ctypes.c_int, [_P, ctypes.POINTER(Arrival), ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p),
+                                 ctypes.POINTER(ctypes.c_int64), _I, _I, ctypes.c_double, ctypes.POINTER(ReplayStats)]),
     "pp_policy_decide": (ctypes.c_int, [ctypes.POINTER(PolicyConfig), ctypes.c_double, ctypes.POINTER(PolicyFrame),
                                         _I, ctypes.POINTER(PolicyActive), _I, _I, ctypes.POINTER(PolicyDecision),
                                         ctypes.POINTER(ctypes.c_uint64), _I]),
@@ -544,6 +558,23 @@ class Context:
 
     def release(self, frame_id):
         _check(lib().pp_result_release(self.h, ctypes.c_uint64(frame_id)))
+
+    def replay(self, arrivals, clouds, timeout_us=10e6):
+        """pp_replay: ``arrivals`` = [(t_us, chain_id, cloud index, n_points)] sorted by time;
+        ``clouds`` all CUDA tensors [N, 4] (borrowed) or all host arrays.  Returns the replay
+        statistics as a dict (chain_rejected as a list)."""
+        n = len(arrivals)
+        arr = (Arrival * max(1, n))(*[Arrival(float(t), int(c), int(k), int(m)) for t, c, k, m in arrivals])
+        dev = hasattr(clouds[0], "is_cuda")
+        keep = clouds if dev else [__import__("numpy").ascontiguousarray(x, dtype="float32") for x in clouds]
+        ptrs = (ctypes.c_void_p * len(keep))(*[(_ptr(x) if dev else x.ctypes.data) for x in keep])
+        cnt = (ctypes.c_int64 * len(keep))(*[int(x.shape[0]) for x in keep])
+        st = ReplayStats()
+        _check(lib().pp_replay(self.h, arr, n, ptrs, cnt, len(keep), 1 if dev else 0, float(timeout_us),
+                               ctypes.byref(st)))
+        d = {k: getattr(st, k) for k, _ in st._fields_ if k != "chain_rejected"}
+        d["chain_rejected"] = list(st.chain_rejected)
+        return d
 
     def stats(self):
         s = Stats()

@@ -859,4 +859,67 @@ int pp_destroy(pp_ctx* c) {
   return PP_OK;
 }
 
+int pp_replay(pp_ctx* c, const pp_arrival* arr, int64_t n, const float* const* clouds,
+              const int64_t* cloud_points, int32_t n_clouds, int32_t is_device_ptr, double timeout_us,
+              pp_replay_stats* out) {
+  if (!c || !out || n < 0 || (n > 0 && (!arr || !clouds || !cloud_points)) || n_clouds <= 0 || timeout_us <= 0)
+    return fail(PP_EINVAL, "replay: bad argument");
+  for (int64_t k = 0; k < n; ++k) {
+    if (k && arr[k].t_us < arr[k - 1].t_us) return fail(PP_EINVAL, "replay: arrivals not sorted by time");
+    if (arr[k].cloud < 0 || arr[k].cloud >= n_clouds || arr[k].n_points < 0 ||
+        arr[k].n_points > cloud_points[arr[k].cloud] || arr[k].chain_id < 0 || arr[k].chain_id >= PP_MAX_CHAINS)
+      return fail(PP_EINVAL, "replay: arrival %lld names a bad chain, cloud or point count", (long long)k);
+  }
+  memset(out, 0, sizeof(*out));
+  const double t0 = now_us();
+  int64_t k = 0, outstanding = 0;
+  double late_sum = 0;
+  pp_result res[256];
+  uint64_t ids[256];
+  int st = PP_OK;
+  while (k < n || outstanding > 0) {
+    double t = now_us();
+    while (k < n && t0 + arr[k].t_us <= t) {
+      const pp_arrival& a = arr[k];
+      const double due = t0 + a.t_us;
+      const int rc = pp_submit_frame(c, a.chain_id, clouds[a.cloud], a.n_points, is_device_ptr, due, 0.0, nullptr);
+      if (rc == PP_OK) {
+        ++outstanding;
+        ++out->submitted;
+      } else if (rc == PP_EAGAIN) {
+        ++out->rejected;
+        ++out->chain_rejected[a.chain_id];
+      } else {
+        return rc;
+      }
+      const double late = now_us() - due;
+      late_sum += late;
+      out->submit_late_us_max = std::max(out->submit_late_us_max, late);
+      ++k;
+      t = now_us();
+    }
+    // wait for completions, but not past the next arrival
+    double wait = 200.0;
+    if (k < n) wait = std::min(wait, std::max(0.0, t0 + arr[k].t_us - now_us()));
+    int32_t got = 0;
+    st = pp_poll(c, res, 256, &got, (int64_t)wait);
+    for (int i = 0; i < got; ++i) {
+      ids[i] = res[i].frame_id;
+      if (res[i].status == PP_FRAME_DROPPED) ++out->dropped;
+      else ++out->completed;
+    }
+    if (got) pp_result_release_many(c, got, ids);
+    outstanding -= got;
+    if (st != PP_OK) break;
+    if (k == n && outstanding > 0 && now_us() - (t0 + (n ? arr[n - 1].t_us : 0.0)) > timeout_us) {
+      st = fail(PP_ETIMEDOUT, "replay: %lld frames still in flight %.0f us after the last arrival",
+                (long long)outstanding, timeout_us);
+      break;
+    }
+  }
+  out->wall_s = (now_us() - t0) * 1e-6;
+  out->submit_late_us_mean = n ? late_sum / (double)n : 0.0;
+  return st;
+}
+
 }  // extern "C"

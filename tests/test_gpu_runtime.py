@@ -332,3 +332,27 @@ def test_runtime_comparison_policies(policy, small_clouds):
         ctx.release_many([r.frame_id for r in res])
     finally:
         ctx.destroy()
+
+
+def test_runtime_replay_trace():
+    """pp_replay submits a timed trace from the library's own thread loop: every frame is
+    accounted for (admitted or rejected), every admitted frame completes, submissions keep to
+    the schedule, and malformed traces are rejected before anything runs."""
+    ctx, keep = _ctx(max_batch=4, max_admitted=16)
+    try:
+        ctx.register_chain(0, 20.0, 20.0, pp.PP_BF16)
+        ctx.register_chain(1, 40.0, 40.0, pp.PP_BF16)
+        clouds = [torch.from_numpy(uniform_cloud(n, 90 + n, GEOM_SMALL)).to(DEV) for n in (30000, 150000)]
+        arrivals = [(1000.0 + 500.0 * k, k % 2, k % 2, [30000, 150000][k % 2] - 7 * k) for k in range(80)]
+        rep = ctx.replay(arrivals, clouds, timeout_us=5e6)
+        assert rep["submitted"] + rep["rejected"] == 80
+        assert rep["completed"] + rep["dropped"] == rep["submitted"]
+        assert rep["submit_late_us_mean"] < 2000.0
+        st = ctx.stats()
+        assert st["done"] + st["dropped"] == rep["submitted"]
+        with pytest.raises(pp.PPError):
+            ctx.replay(list(reversed(arrivals)), clouds)          # not sorted by time
+        with pytest.raises(pp.PPError):
+            ctx.replay([(0.0, 0, 0, 40000)], clouds)              # more points than the cloud has
+    finally:
+        ctx.destroy()
