@@ -108,17 +108,6 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* m, uint64_t
       : "memory");
 }
 
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, const void* src, int c0, int c1,
-                                             int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(m),
-      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// The issuing thread's bulk stores have finished reading shared memory / have completed.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Named barrier `id` over `n` threads that also ANDs a predicate across them.
 __device__ __forceinline__ bool bar_and(int id, int n, bool v) {
   uint32_t r;
@@ -425,15 +414,10 @@ struct PArgs {
   unsigned* sem;  // stream-K: [total] arrival counters, zero between launches
 };
 
-// EPI_TMA: the epilogue stages the tile's output (both planes) in shared memory in the 128-byte
-// swizzled layout and one thread stores it with TMA (tmO, tmOlo: the output interiors as 4-D
-// maps, so partial tiles are clipped by the copy engine); otherwise each reducer thread stores
-// its own pixel row.
-template <int MODE, int BN, int STAGES, int KPS, bool S2, bool EPI_TMA, bool SK>
+template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK>
 __global__ void __launch_bounds__(192, 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
-            const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
-            const __grid_constant__ CUtensorMap tmOlo, PArgs args) {
+            const __grid_constant__ CUtensorMap tmB, PArgs args) {
   constexpr int BK = MODE == 1 ? 32 : 64;                  // channels per K block (128 B rows)
   constexpr uint32_t kA = 128 * 128;                       // A tile bytes of one K block
   constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
@@ -457,8 +441,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                                              ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
-  uint8_t* sO = sB + STAGES * kStageB;                     // EPI_TMA staging: 2 planes x BN/32 chunks x 16 KiB
-  constexpr uint32_t kStageO = EPI_TMA ? 2u * (BN / 32) * 16384u : 4u * 4096u;  // else 4 KiB per reducer warp
+  uint8_t* sO = sB + STAGES * kStageB;                     // epilogue: 4 KiB transposing buffer per reducer warp
+  constexpr uint32_t kStageO = 4u * 4096u;
   uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);
   uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
@@ -492,10 +476,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     if (MODE == 1) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmAlo) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-    if (EPI_TMA) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmO) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmOlo) : "memory");
-    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -709,41 +689,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           }
           if (r == 0) args.sem[t] = 0u;  // counters are zero again for the next launch
         }
-        if (EPI_TMA) {
-          // the previous tile's stores must have read the staging buffer; every reducer thread
-          // takes the same decision (AND of ok), so the named barriers always match
-          if (r == 0) bulk_wait_read();
-          ok = bar_and(1, 128, ok);
-          if (!ok) break;
-#pragma unroll
-          for (int k = 0; k < BN / 32; ++k) {
-            uint8_t* hi = sO + k * 16384 + r * 128;
-            uint8_t* lo = hi + (BN / 32) * 16384;
-#pragma unroll
-            for (int qd = 0; qd < 8; ++qd) {
-              const int n = n0 + 32 * k + 4 * qd;
-              const float* a = acc + 32 * k + 4 * qd;
-              float4 u;
-              u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), 0.f);
-              u.y = fmaxf(fmaf(a[1], s_scale[n + 1], s_shift[n + 1]), 0.f);
-              u.z = fmaxf(fmaf(a[2], s_scale[n + 2], s_shift[n + 2]), 0.f);
-              u.w = fmaxf(fmaf(a[3], s_scale[n + 3], s_shift[n + 3]), 0.f);
-              const int off = ((qd ^ (r & 7)) << 4);  // 128-byte swizzle of the TMA box
-              *reinterpret_cast<float4*>(hi + off) = u;
-              *reinterpret_cast<float4*>(lo + off) = tf32_remainder4(u);
-            }
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          bar_and(1, 128, true);
-          if (r == 0) {
-#pragma unroll
-            for (int k = 0; k < BN / 32; ++k) {
-              tma_store_4d(&tmO, sO + k * 16384, n0 + 32 * k, ox0, oy0, b);
-              tma_store_4d(&tmOlo, sO + (BN / 32 + k) * 16384, n0 + 32 * k, ox0, oy0, b);
-            }
-            bulk_commit();
-          }
-        } else {
+        {
           // value plane and remainder plane (split FP32, the next layer's A operand), 32
           // channels (128 B per pixel) at a time through the warp's transposing buffer
           if (!ok) break;
@@ -806,7 +752,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
     }
   }
-  if (EPI_TMA && warp == 4 && lane == 0) bulk_wait_all();  // the staging buffer outlives its stores
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -1194,26 +1139,22 @@ constexpr int kNPB = (int)(sizeof(kTilesPB) / sizeof(kTilesPB[0]));
 constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
 
 // Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
-// stage = 32 KiB A (+lo) + 2 x BN x 128 B.  Both fill ~192 KiB of shared memory.
+// stage = KPS x (32 KiB A (+lo) + 2 x BN x 128 B).  All fill ~192 KiB of shared memory.  Two K
+// blocks per stage halve the per-stage handshakes (measured on the full-size frame: 3xTF32
+// BN 64 layers 12-16 % faster with 2 stages of 2 K blocks than with 3 stages of 1).
 template <int MODE, int BN>
 constexpr int p_kps() {
-  return MODE == 1 ? 1 : 2;
-}
-// The 3xTF32 kernel with BN = 64 stores through a shared-memory staging tile (64 KiB: both
-// planes) by TMA, and keeps three ring stages to make room for it.
-template <int MODE, int BN>
-constexpr bool p_epi_tma() {
-  return MODE == 1 && BN == 64;
+  return MODE == 1 ? (BN == 64 ? 2 : 1) : 2;
 }
 template <int MODE, int BN>
 constexpr int p_stages() {
-  return MODE == 1 ? 3 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+  return MODE == 1 ? (BN == 64 ? 2 : 3) : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
 }
 template <int MODE, int BN>
 constexpr size_t p_smem() {
   return 1024 + (size_t)p_stages<MODE, BN>() * p_kps<MODE, BN>() *
                     ((MODE == 1 ? 2 : 1) * 16384 + (MODE == 1 ? 2 : 1) * BN * 128) +
-         (p_epi_tma<MODE, BN>() ? 2 * (BN / 32) * 16384 : 4 * 4096) +
+         4 * 4096 +                                   // epilogue transposing buffers
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
 
@@ -1229,15 +1170,14 @@ int num_sms() {
 }
 
 template <int MODE, int BN, bool S2, bool SK>
-int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const CUtensorMap& o,
-             const CUtensorMap& olo, const PArgs& args, cudaStream_t s) {
+int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
+             cudaStream_t s) {
   constexpr int ST = p_stages<MODE, BN>();
   constexpr int KPS = p_kps<MODE, BN>();
-  constexpr bool EPI = p_epi_tma<MODE, BN>();
   constexpr size_t bytes = p_smem<MODE, BN>() + 2 * 1024 * sizeof(float);  // + folded BN (cout <= 1024)
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, EPI, SK>,
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_status(e, "persistent conv smem attribute");
     attr_set = true;
@@ -1247,7 +1187,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  conv3x3_tcp<MODE, BN, ST, KPS, S2, EPI, SK><<<grid, 192, bytes, s>>>(a, alo, w, o, olo, args);
+  conv3x3_tcp<MODE, BN, ST, KPS, S2, SK><<<grid, 192, bytes, s>>>(a, alo, w, args);
   return cuda_status(cudaGetLastError(), "persistent conv launch");
 }
 
@@ -1352,24 +1292,8 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     args.ws = static_cast<float*>(ws);
     args.sem = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + part);
   }
-  // output interiors as 4-D maps (channels, x, y, frame) for the TMA-store epilogue
-  CUtensorMap to = ta, tolo = ta;
-  if (mode == 1 && t.bn == 64) {
-    for (int plane = 0; plane < 2 && r == CUDA_SUCCESS; ++plane) {
-      float* base = static_cast<float*>(out) + (size_t)plane * args.plane + (size_t)(c.Wo + 3) * c.cout;
-      cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)c.Wo, (cuuint64_t)c.Ho, (cuuint64_t)c.batch};
-      cuuint64_t strides[3] = {(cuuint64_t)c.cout * 4, (cuuint64_t)(c.Wo + 2) * c.cout * 4,
-                               (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.cout * 4};
-      cuuint32_t box[4] = {32, (cuuint32_t)t.bw, (cuuint32_t)t.bh, 1};
-      cuuint32_t es[4] = {1, 1, 1, 1};
-      r = enc(plane ? &tolo : &to, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    }
-    if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: output tensor map (%d)", (int)r);
-  }
   const bool s2 = c.stride == 2;
-#define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, to, tolo, args, s) : launch_p<M, N, false, K>(ta, talo, tw, to, tolo, args, s)
+#define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, args, s) : launch_p<M, N, false, K>(ta, talo, tw, args, s)
   if (mode == 1) {
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
     if (t.bn == 128) { if (sk) PP_P(1, 128, true); PP_P(1, 128, false); }
