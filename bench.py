@@ -76,8 +76,8 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (387.8e6, "64c55a349cbce4b8ef49151f936c7289a1661d46f482566e91d848c000aa0223"),
-    "cfg3-bf16": (84.6e6, "64c55a349cbce4b8ef49151f936c7289a1661d46f482566e91d848c000aa0223"),
+    "cfg2-fp32": (383.2e6, "a9b88c7f4ca23619173f4f5bc5ea632f60493b6b07bca94687643e588cf867cc"),
+    "cfg3-bf16": (84.5e6, "a9b88c7f4ca23619173f4f5bc5ea632f60493b6b07bca94687643e588cf867cc"),
 }
 
 

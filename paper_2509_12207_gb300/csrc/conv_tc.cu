@@ -395,8 +395,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 // accumulation goes to TMEM buffers in turn (four where 512 columns hold them, else two):
 // while the reducer warps read one buffer (and, at the end of a tile, apply BN + ReLU and
 // store), the MMAs fill the next.  For BF16 a buffer
-// holds a whole tile's accumulation and a ring stage carries KPS = 2 K blocks (8 MMAs per
-// handshake); for 3xTF32 a buffer holds `fold` K blocks, which the reducers add into FP32
+// holds a whole tile's accumulation and a ring stage carries KPS K blocks (p_kps: 2-4, so
+// 8-16 MMAs per handshake); for 3xTF32 a buffer holds `fold` K blocks, which the reducers add into FP32
 // registers, and each K step is two MMAs: A_hi x [B_hi | B_lo] (N = 2 BN, the two products land
 // side by side in TMEM) and A_lo x B_hi (N = BN, into the first half); the reducers sum the
 // halves.  Loop counters advance incrementally (no division in the steady state) and shared
@@ -1141,14 +1141,15 @@ constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
 // Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
 // stage = KPS x (32 KiB A (+lo) + 2 x BN x 128 B).  All fill ~192 KiB of shared memory.  Two K
 // blocks per stage halve the per-stage handshakes (measured on the full-size frame: 3xTF32
-// BN 64 layers 12-16 % faster with 2 stages of 2 K blocks than with 3 stages of 1).
+// BN 64 layers 12-16 % faster with 2 stages of 2 K blocks than with 3 stages of 1; BF16 layers
+// up to 11 % faster with 2 stages of 4 / 3 K blocks than with 4 / 3 stages of 2).
 template <int MODE, int BN>
 constexpr int p_kps() {
-  return MODE == 1 ? (BN == 64 ? 2 : 1) : 2;
+  return MODE == 1 ? (BN == 64 ? 2 : 1) : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
 }
 template <int MODE, int BN>
 constexpr int p_stages() {
-  return MODE == 1 ? (BN == 64 ? 2 : 3) : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+  return MODE == 1 ? (BN == 64 ? 2 : 3) : 2;
 }
 template <int MODE, int BN>
 constexpr size_t p_smem() {

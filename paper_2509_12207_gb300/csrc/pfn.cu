@@ -38,45 +38,49 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
   __syncthreads();
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p = blockIdx.x * kWarps + wid;
-  if (p >= num_pillars[b]) return;  // warp-uniform; no block barrier follows
-  const size_t q = (size_t)b * g.P + p;
-  const int n = npts[q];
-  const float4 v = pts[q * 32 + lane];
-  const bool valid = lane < n;
-  float sx = valid ? v.x : 0.f, sy = valid ? v.y : 0.f, sz = valid ? v.z : 0.f;
-  for (int o = 16; o; o >>= 1) {
-    sx += __shfl_xor_sync(kFull, sx, o);
-    sy += __shfl_xor_sync(kFull, sy, o);
-    sz += __shfl_xor_sync(kFull, sz, o);
-  }
-  const float inv = 1.f / (float)n;
-  const float mx = sx * inv, my = sy * inv, mz = sz * inv;
-  const int cell = coord[q];
-  const int ix = cell % g.nx, iy = cell / g.nx;
-  const float xc = g.xmin + ((float)ix + 0.5f) * g.vx;
-  const float yc = g.ymin + ((float)iy + 0.5f) * g.vy;
-  float* f = f_s[wid][lane];
-  f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
-  f[4] = v.x - mx; f[5] = v.y - my; f[6] = v.z - mz;
-  f[7] = v.x - xc; f[8] = v.y - yc;
-  __syncwarp();
-  const float s0 = sc_s[lane], s1 = sc_s[lane + 32];
-  const float h0 = sh_s[lane], h1 = sh_s[lane + 32];
-  float m0 = 0.f, m1 = 0.f;  // ReLU outputs are >= 0 and every pillar has >= 1 point
-  for (int j = 0; j < n; ++j) {
-    const float* fj = f_s[wid][j];
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      a0 = fmaf(fj[k], w_s[k][lane], a0);
-      a1 = fmaf(fj[k], w_s[k][lane + 32], a1);
+  const int np = num_pillars[b];
+  // each warp walks pillars p, p + gridDim.x * kWarps, ... (warp-uniform; no block barrier
+  // follows), so the weights staged above serve several pillars
+  for (int p = blockIdx.x * kWarps + wid; p < np; p += gridDim.x * kWarps) {
+    const size_t q = (size_t)b * g.P + p;
+    const int n = npts[q];
+    const float4 v = pts[q * 32 + lane];
+    const bool valid = lane < n;
+    float sx = valid ? v.x : 0.f, sy = valid ? v.y : 0.f, sz = valid ? v.z : 0.f;
+    for (int o = 16; o; o >>= 1) {
+      sx += __shfl_xor_sync(kFull, sx, o);
+      sy += __shfl_xor_sync(kFull, sy, o);
+      sz += __shfl_xor_sync(kFull, sz, o);
     }
-    m0 = fmaxf(m0, fmaxf(fmaf(a0, s0, h0), 0.f));
-    m1 = fmaxf(m1, fmaxf(fmaf(a1, s1, h1), 0.f));
+    const float inv = 1.f / (float)n;
+    const float mx = sx * inv, my = sy * inv, mz = sz * inv;
+    const int cell = coord[q];
+    const int ix = cell % g.nx, iy = cell / g.nx;
+    const float xc = g.xmin + ((float)ix + 0.5f) * g.vx;
+    const float yc = g.ymin + ((float)iy + 0.5f) * g.vy;
+    float* f = f_s[wid][lane];
+    f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+    f[4] = v.x - mx; f[5] = v.y - my; f[6] = v.z - mz;
+    f[7] = v.x - xc; f[8] = v.y - yc;
+    __syncwarp();
+    const float s0 = sc_s[lane], s1 = sc_s[lane + 32];
+    const float h0 = sh_s[lane], h1 = sh_s[lane + 32];
+    float m0 = 0.f, m1 = 0.f;  // ReLU outputs are >= 0 and every pillar has >= 1 point
+    for (int j = 0; j < n; ++j) {
+      const float* fj = f_s[wid][j];
+      float a0 = 0.f, a1 = 0.f;
+  #pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        a0 = fmaf(fj[k], w_s[k][lane], a0);
+        a1 = fmaf(fj[k], w_s[k][lane + 32], a1);
+      }
+      m0 = fmaxf(m0, fmaxf(fmaf(a0, s0, h0), 0.f));
+      m1 = fmaxf(m1, fmaxf(fmaf(a1, s1, h1), 0.f));
+    }
+    feat[q * 64 + lane] = m0;
+    feat[q * 64 + lane + 32] = m1;
+    __syncwarp();  // f_s[wid] is rewritten by the next pillar
   }
-  feat[q * 64 + lane] = m0;
-  feat[q * 64 + lane + 32] = m1;
 }
 
 // x minus x with its 13 low mantissa bits cleared (exact in FP32): what a TF32 read drops.
@@ -171,8 +175,12 @@ int sm_count() {
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,
                const int* num_pillars, const float* pfn_w, const float* ss, float* feat,
                cudaStream_t s) {
-  pfn_fused<<<dim3((g.P + kWarps - 1) / kWarps, batch), kWarps * 32, 0, s>>>(
-      g, pts, npts, coord, num_pillars, pfn_w, ss, feat);
+  // about 4 blocks per SM over the batch; warps loop over their pillars
+  int bx = (g.P + kWarps - 1) / kWarps;
+  const int bx_max = (4 * sm_count() + batch - 1) / batch;
+  if (bx > bx_max) bx = bx_max;
+  pfn_fused<<<dim3(bx > 0 ? bx : 1, batch), kWarps * 32, 0, s>>>(g, pts, npts, coord, num_pillars,
+                                                                pfn_w, ss, feat);
   return cuda_status(cudaGetLastError(), "pointnet launch");
 }
 

@@ -45,31 +45,34 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
                                int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, err);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x * blockDim.x >= n) return;  // whole block idle (uniform exit)
-  const size_t row = (size_t)b * cap + i;
-  int c = -1;
-  if (i < n) {
-    const float4 p = frame_src(points, srcs, b, cap)[i];
-    bool ok = p.x >= g.xmin && p.x < g.xmax && p.y >= g.ymin && p.y < g.ymax &&
-              p.z >= g.zmin && p.z < g.zmax;
-    if (ok) {
-      const float qx = floorf(__fdiv_rn(__fsub_rn(p.x, g.xmin), g.vx));
-      const float qy = floorf(__fdiv_rn(__fsub_rn(p.y, g.ymin), g.vy));
-      ok = qx >= 0.f && qx < (float)g.nx && qy >= 0.f && qy < (float)g.ny;
-      if (ok) c = (int)qy * g.nx + (int)qx;
+  const float4* src = frame_src(points, srcs, b, cap);
+  // grid-stride over the frame's points (block-uniform trip count: whole warps stay together)
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const size_t row = (size_t)b * cap + i;
+    int c = -1;
+    if (i < n) {
+      const float4 p = src[i];
+      bool ok = p.x >= g.xmin && p.x < g.xmax && p.y >= g.ymin && p.y < g.ymax &&
+                p.z >= g.zmin && p.z < g.zmax;
+      if (ok) {
+        const float qx = floorf(__fdiv_rn(__fsub_rn(p.x, g.xmin), g.vx));
+        const float qy = floorf(__fdiv_rn(__fsub_rn(p.y, g.ymin), g.vy));
+        ok = qx >= 0.f && qx < (float)g.nx && qy >= 0.f && qy < (float)g.ny;
+        if (ok) c = (int)qy * g.nx + (int)qx;
+      }
+      cell[row] = c;
     }
-    cell[row] = c;
-  }
-  const unsigned valid = __ballot_sync(kFull, c >= 0);
-  if (c >= 0) {
-    const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(valid, c);
-    const int leader = __ffs(peers) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(&cnt[(size_t)b * g.G + c], (unsigned)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    slot[row] = (int)base + __popc(peers & ((1u << lane) - 1u));
+    const unsigned valid = __ballot_sync(kFull, c >= 0);
+    if (c >= 0) {
+      const int lane = threadIdx.x & 31;
+      const unsigned peers = __match_any_sync(valid, c);
+      const int leader = __ffs(peers) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&cnt[(size_t)b * g.G + c], (unsigned)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      slot[row] = (int)base + __popc(peers & ((1u << lane) - 1u));
+    }
   }
 }
 
@@ -195,14 +198,14 @@ __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
                            const int* __restrict__ pillar_start, int* __restrict__ csr) {
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, nullptr);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const size_t row = (size_t)b * cap + i;
-  const int c = cell[row];
-  if (c < 0) return;
-  const int p = pillar_of_cell[(size_t)b * g.G + c];
-  if (p < 0) return;
-  csr[(size_t)b * cap + pillar_start[(size_t)b * g.P + p] + slot[row]] = i;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const size_t row = (size_t)b * cap + i;
+    const int c = cell[row];
+    if (c < 0) continue;
+    const int p = pillar_of_cell[(size_t)b * g.G + c];
+    if (p < 0) continue;
+    csr[(size_t)b * cap + pillar_start[(size_t)b * g.P + p] + slot[row]] = i;
+  }
 }
 
 // Ascending bitonic sort of one int per lane across a warp.
@@ -290,7 +293,18 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
                const float4* const* srcs) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
-  const dim3 pg((cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, batch);
+  // point kernels: grid-stride, about 8 blocks of 256 threads per SM over the whole batch (a
+  // grid sized for the capacity costs microseconds of empty blocks when frames are short)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  int px = (cap + 255) / 256;
+  const int px_max = (8 * sms + batch - 1) / batch;
+  if (px > px_max) px = px_max;
+  const dim3 pg(px > 0 ? px : 1, batch);
   vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, n_points, cell, w.slot, cnt, w.err);
   vox_tile_sums<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles);
   vox_scan<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles, pillar_of_cell,

@@ -356,3 +356,29 @@ def test_runtime_replay_trace():
             ctx.replay([(0.0, 0, 0, 40000)], clouds)              # more points than the cloud has
     finally:
         ctx.destroy()
+
+
+def test_runtime_batched_bf16_unit_full_workload():
+    """The 8-frame BF16 workload exactly as the bench runs it (uneven 30k-150k frames of the
+    0.32 m grid submitted together into one unit of a graph-launched, autotuned context):
+    every frame's pillars match the oracle exactly and its backbone output is within the BF16
+    tolerance (and within 8e-3 of the oracle with BF16 roundings emulated)."""
+    from pp_synth import batched_counts
+    counts = batched_counts(3)
+    clouds = [config_points(3, k, n) for k, n in enumerate(counts)]
+    ctx, keep = _ctx(max_batch=8, units=2, precisions=2, early_exit=0)
+    try:
+        ctx.register_chain(0, 10000.0, 10000.0, pp.PP_BF16)
+        dev = [torch.from_numpy(c).to(DEV) for c in clouds]
+        rc, ids = ctx.submit_many([0] * 8, dev)
+        assert rc == pp.PP_OK
+        res = {r.frame_id: r for r in _drain(ctx, 8)}
+        assert all(r.batch == 8 for r in res.values())
+        for k, fid in enumerate(ids):
+            ref = _ref(clouds[k])
+            r = res[fid]
+            assert r.num_pillars == ref["vox"]["num_pillars"]
+            _check_out(_interior(pp.result_tensor(r)), ref, pp.PP_BF16)
+        ctx.release_many(ids)
+    finally:
+        ctx.destroy()
