@@ -330,7 +330,9 @@ def _run_ours(a, rank, world, dist):
     def submit(k, host):
         fs = [(frames_host if host else frames_dev)[(k * n_frames + j) % len(frames)] for j in range(n_frames)]
         # the step's frames arrive together (one submission), so they share one release unit
-        rc, ids = ctx.submit_many([0] * n_frames, [f.numpy() for f in fs] if host else fs)
+        # host inputs are pinned tensors: borrowed, read in place by the kernels over the host
+        # link (PP_POINTS_PINNED), so the step's host->device traffic is the points themselves
+        rc, ids = ctx.submit_many([0] * n_frames, fs)
         assert rc == pp.PP_OK and len(ids) == n_frames, rc
 
     def run_steps(steps, host):

@@ -327,8 +327,16 @@ int pp_create(const pp_config* cfg, pp_ctx** out);
 int pp_register_chain(pp_ctx* ctx, int32_t chain_id, double period_ms, double rel_deadline_ms,
                       int32_t precision);
 
-/* Submits one frame of `n_points` float4 points.  is_device_ptr = 0: host memory, copied
- * before the call returns; 1: device memory, borrowed until the frame's result is polled.
+/* Where submitted points live (the is_device_ptr argument):
+ *   PP_POINTS_HOST (0)   host memory, copied into a pinned staging slot before the call returns;
+ *   PP_POINTS_DEVICE (1) device memory, borrowed until the frame's result is polled;
+ *   PP_POINTS_PINNED (2) page-locked host memory (cudaHostAlloc / cudaHostRegister, e.g. a
+ *                        pinned torch tensor), borrowed until the frame's result is polled;
+ *                        the unit's kernels read it in place over the host link, with no
+ *                        staging copy and no separate transfer.  Other host memory: PP_EINVAL. */
+enum { PP_POINTS_HOST = 0, PP_POINTS_DEVICE = 1, PP_POINTS_PINNED = 2 };
+/* Submits one frame of `n_points` float4 points (is_device_ptr: PP_POINTS_*; device and pinned
+ * points 16-byte aligned).
  * t_arrival_us / abs_deadline_us on the pp_now_us clock (abs_deadline_us <= 0: arrival +
  * the chain's deadline).  PP_EAGAIN when admitting the frame would exceed the HBM budget. */
 int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_points,

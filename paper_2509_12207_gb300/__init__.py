@@ -41,6 +41,18 @@ MAX_BLOCKS = 4
 MAX_CHAINS = 64
 PP_POLICY_FIFO, PP_POLICY_URGENCY, PP_POLICY_EDF, PP_POLICY_SJF, PP_POLICY_HRRN, PP_POLICY_LCUF = 0, 1, 2, 3, 4, 5
 PP_FRAME_DONE, PP_FRAME_DROPPED, PP_FRAME_ERROR = 0, 1, 2
+PP_POINTS_HOST, PP_POINTS_DEVICE, PP_POINTS_PINNED = 0, 1, 2
+
+
+def _points_mode(t):
+    """PP_POINTS_* for a frame: CUDA tensor -> device (borrowed), pinned CPU tensor -> pinned
+    (borrowed, read in place by the kernels), anything else -> host (copied)."""
+    if hasattr(t, "is_cuda"):
+        if t.is_cuda:
+            return PP_POINTS_DEVICE
+        if t.is_pinned():
+            return PP_POINTS_PINNED
+    return PP_POINTS_HOST
 PP_DECIDE_NONE, PP_DECIDE_RELEASE, PP_DECIDE_WAIT, PP_DECIDE_DELAY = 0, 1, 2, 3
 
 
@@ -502,14 +514,15 @@ class Context:
         _check(lib().pp_register_chain(self.h, chain_id, period_ms, deadline_ms, precision))
 
     def submit(self, chain_id, points, t_arrival_us=None, abs_deadline_us=0.0, n_points=None):
-        """points: numpy float32 [N, 4] (host; copied) or a CUDA tensor [N, 4] (device; borrowed
-        until the frame is polled).  Returns (status, frame_id); status PP_EAGAIN when not
-        admitted."""
+        """points: numpy float32 [N, 4] (host; copied), a CUDA tensor [N, 4] (device; borrowed
+        until the frame is polled) or a pinned CPU tensor (borrowed; the kernels read it in
+        place).  Returns (status, frame_id); status PP_EAGAIN when not admitted."""
         fid = ctypes.c_uint64(0)
         t = now_us() if t_arrival_us is None else t_arrival_us
-        if hasattr(points, "is_cuda"):
+        mode = _points_mode(points)
+        if mode != PP_POINTS_HOST:
             n = int(points.shape[0]) if n_points is None else n_points
-            rc = lib().pp_submit_frame(self.h, chain_id, _ptr(points), n, 1, t, abs_deadline_us, ctypes.byref(fid))
+            rc = lib().pp_submit_frame(self.h, chain_id, _ptr(points), n, mode, t, abs_deadline_us, ctypes.byref(fid))
         else:
             import numpy as np
             a = np.ascontiguousarray(points, dtype=np.float32)
@@ -522,11 +535,12 @@ class Context:
 
     def submit_many(self, chain_ids, frames, t_arrival_us=None, abs_deadlines_us=None):
         """Submits frames that arrive together (one pp_submit_frames call): ``frames`` are all
-        CUDA tensors [N, 4] (borrowed) or all host arrays (copied).  Returns (status, ids of the
-        admitted frames, in order)."""
+        CUDA tensors [N, 4] (borrowed), all pinned CPU tensors (borrowed, read in place) or all
+        host arrays (copied).  Returns (status, ids of the admitted frames, in order)."""
         n = len(frames)
         t = now_us() if t_arrival_us is None else t_arrival_us
-        dev = n > 0 and hasattr(frames[0], "is_cuda")
+        mode = _points_mode(frames[0]) if n else PP_POINTS_HOST
+        dev = mode != PP_POINTS_HOST
         keep = []
         if dev:
             ptrs = [_ptr(f) for f in frames]
@@ -540,7 +554,7 @@ class Context:
         dls = (ctypes.c_double * n)(*abs_deadlines_us) if abs_deadlines_us is not None else None
         ids = (ctypes.c_uint64 * n)()
         got = ctypes.c_int32(0)
-        rc = lib().pp_submit_frames(self.h, n, cids, parr, cnt, 1 if dev else 0, t, dls, ids, ctypes.byref(got))
+        rc = lib().pp_submit_frames(self.h, n, cids, parr, cnt, mode, t, dls, ids, ctypes.byref(got))
         if rc not in (PP_OK, PP_EAGAIN):
             _check(rc)
         return rc, [int(ids[i]) for i in range(got.value)]
@@ -565,12 +579,13 @@ class Context:
         statistics as a dict (chain_rejected as a list)."""
         n = len(arrivals)
         arr = (Arrival * max(1, n))(*[Arrival(float(t), int(c), int(k), int(m)) for t, c, k, m in arrivals])
-        dev = hasattr(clouds[0], "is_cuda")
+        mode = _points_mode(clouds[0])
+        dev = mode != PP_POINTS_HOST
         keep = clouds if dev else [__import__("numpy").ascontiguousarray(x, dtype="float32") for x in clouds]
         ptrs = (ctypes.c_void_p * len(keep))(*[(_ptr(x) if dev else x.ctypes.data) for x in keep])
         cnt = (ctypes.c_int64 * len(keep))(*[int(x.shape[0]) for x in keep])
         st = ReplayStats()
-        _check(lib().pp_replay(self.h, arr, n, ptrs, cnt, len(keep), 1 if dev else 0, float(timeout_us),
+        _check(lib().pp_replay(self.h, arr, n, ptrs, cnt, len(keep), mode, float(timeout_us),
                                ctypes.byref(st)))
         d = {k: getattr(st, k) for k, _ in st._fields_ if k != "chain_rejected"}
         d["chain_rejected"] = list(st.chain_rejected)

@@ -664,12 +664,25 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
   if (n_admitted) *n_admitted = 0;
   if (!c || n < 1 || n > kMaxSubmit || !chain_ids || !xyzr || !n_points)
     return fail(PP_EINVAL, "submit: bad argument (n 1..%d, non-NULL arrays)", kMaxSubmit);
+  if (is_device_ptr < PP_POINTS_HOST || is_device_ptr > PP_POINTS_PINNED)
+    return fail(PP_EINVAL, "submit: is_device_ptr must be PP_POINTS_HOST, _DEVICE or _PINNED");
+  const float* mapped[kMaxSubmit];  // what the kernels read: the device view of each frame
   for (int i = 0; i < n; ++i) {
     if (chain_ids[i] < 0 || chain_ids[i] >= PP_MAX_CHAINS) return fail(PP_EINVAL, "submit: bad chain");
     if (n_points[i] < 0 || n_points[i] > c->cfg.cap_points || (n_points[i] > 0 && !xyzr[i]))
       return fail(PP_EINVAL, "submit: n_points outside [0, cap_points] or NULL points");
     if (is_device_ptr && (reinterpret_cast<uintptr_t>(xyzr[i]) & 15u))
-      return fail(PP_EINVAL, "submit: device points must be 16-byte aligned");
+      return fail(PP_EINVAL, "submit: device or pinned points must be 16-byte aligned");
+    mapped[i] = xyzr[i];
+    if (is_device_ptr == PP_POINTS_PINNED && n_points[i] > 0) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, xyzr[i]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+          !at.devicePointer) {
+        cudaGetLastError();
+        return fail(PP_EINVAL, "submit: frame %d is not page-locked host memory", i);
+      }
+      mapped[i] = static_cast<const float*>(at.devicePointer);
+    }
   }
   Frame* fs[kMaxSubmit];
   int k = 0, st = PP_OK;
@@ -702,7 +715,7 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
     c->pool[p].free.pop_back();
     c->admitted[p]++;
     if (is_device_ptr) {
-      f->src = xyzr[k];
+      f->src = mapped[k];  // read in place by the unit's kernels
     } else {
       f->staging = c->staging_free.back();
       c->staging_free.pop_back();

@@ -382,3 +382,29 @@ def test_runtime_batched_bf16_unit_full_workload():
         ctx.release_many(ids)
     finally:
         ctx.destroy()
+
+
+def test_runtime_pinned_host_points(small_clouds):
+    """Page-locked host frames are borrowed and read in place by the unit's kernels (no staging
+    copy): results match the oracle exactly as device frames do; pageable memory is refused in
+    that mode."""
+    import ctypes
+    ctx, keep = _ctx(max_batch=4)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        pinned = [torch.from_numpy(c).pin_memory() for c in small_clouds]
+        rc, ids = ctx.submit_many([0] * len(pinned), pinned)
+        assert rc == pp.PP_OK
+        res = {r.frame_id: r for r in _drain(ctx, len(ids))}
+        for k, fid in enumerate(ids):
+            ref = _ref(small_clouds[k])
+            assert res[fid].num_pillars == ref["vox"]["num_pillars"]
+            _check_out(_interior(pp.result_tensor(res[fid])), ref, pp.PP_F32)
+        ctx.release_many(ids)
+        pageable = np.ascontiguousarray(small_clouds[0])
+        fid = ctypes.c_uint64(0)
+        rc = pp.lib().pp_submit_frame(ctx.h, 0, pageable.ctypes.data, 1000, pp.PP_POINTS_PINNED,
+                                      pp.now_us(), 0.0, ctypes.byref(fid))
+        assert rc == pp.PP_EINVAL and b"page-locked" in pp.lib().pp_last_error()
+    finally:
+        ctx.destroy()
