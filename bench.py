@@ -345,17 +345,23 @@ def _run_ours(a, rank, world, dist):
                 k += 1
                 inflight += n_frames
             got = ctx.poll(64, timeout_us=1000000)
-            for r in got:
+            for j, r in enumerate(got):
                 assert r.status == pp.PP_FRAME_DONE
                 if host:
-                    # D2H read of the frame's result (the last backbone layer)
-                    nbytes = r.out_c * (r.out_h + 2) * (r.out_w + 2) * (4 if r.out_dtype == pp.PP_F32 else 2)
-                    run_steps.d2h += nbytes
-                    run_steps.sink = pp.result_tensor(r).cpu()
+                    # D2H read of the frame's result (the last backbone layer) into pinned memory
+                    res = pp.result_tensor(r)
+                    run_steps.d2h += res.numel() * res.element_size()
+                    key = (j, tuple(res.shape), res.dtype)
+                    if key not in sinks:
+                        sinks[key] = torch.empty(res.shape, dtype=res.dtype, pin_memory=True)
+                    sinks[key].copy_(res, non_blocking=True)
+            if host and got:
+                torch.cuda.current_stream().synchronize()  # results read before their slots return
             ctx.release_many([r.frame_id for r in got])
             inflight -= len(got)
             done += len(got)
     run_steps.d2h = 0
+    sinks = {}
 
     def timed(host):
         run_steps(a.warmup, host)
