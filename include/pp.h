@@ -213,6 +213,38 @@ int pp_conv_tune_load(const char* path);
 /* Forgets every autotuned entry. */
 void pp_conv_tune_clear(void);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Neck and detection head (the rest of PointPillars' GPU segment; the paper runs it inside a */
+/* closed engine and does not describe it): each backbone block's output is upsampled to the  */
+/* first block's size by a transposed conv whose kernel equals its stride (no overlap) + BN + */
+/* ReLU, the upsampled maps are concatenated along channels, and a 1x1 conv with bias gives   */
+/* the per-anchor outputs.  Both run on the persistent tensor-core GEMM (dtype PP_BF16, or    */
+/* PP_F32_TC with split FP32 operands and outputs).                                            */
+/* pp_upsample: in [B][H+2][W+2][cin] -> channels [out_coff, out_coff + cout) of out          */
+/*   [B][up*H+2][up*W+2][out_c] (interior written: out[up*y+dy][up*x+dx][out_coff+co] =        */
+/*   ReLU(scale[co] * sum_ci in[y][x][ci] w[ci][co][dy][dx] + shift[co])).  cin, cout, out_c,   */
+/*   out_coff multiples of 64; scale_shift device [2][cout] (pp_bn_fold).                       */
+/* pp_head: out[B][H+2][W+2][cout_pad] = in . w^T + bias (no activation), cout_pad = cout     */
+/*   rounded up to a multiple of 64 (the extra channels are 0); scale_shift device [2][cout_pad] */
+/*   from pp_head_pack_weights (1 and the bias).                                                */
+/* The *_packed_bytes calls return 0 for a shape or dtype the GEMM does not support.           */
+/* Weights are packed on the host and copied to device memory (synchronous): pp_upsample_*    */
+/* from the ConvTranspose2d layout [cin][cout][up][up], pp_head_* from [cout][cin].  tile: a  */
+/* tile number whose pp_conv_tile_info persistent flag is 1 (its bn must divide cout), or -1  */
+/* for the library's choice.  Returns PP_EINVAL (nothing launched) for a bad shape, alignment */
+/* or tile; all pointers are device memory owned by the caller, except the host weights.     */
+size_t pp_upsample_packed_bytes(int32_t cin, int32_t cout, int32_t up, int32_t dtype);
+int pp_upsample_pack_weights(const float* w, int32_t cin, int32_t cout, int32_t up, int32_t dtype,
+                             void* w_packed);
+size_t pp_head_packed_bytes(int32_t cin, int32_t cout, int32_t dtype);
+int pp_head_pack_weights(const float* w, const float* bias, int32_t cin, int32_t cout, int32_t dtype,
+                         void* w_packed, float* scale_shift);
+int pp_upsample(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t up, int32_t dtype,
+                const void* in, const void* w_packed, const float* scale_shift, void* out, int32_t out_c,
+                int32_t out_coff, int32_t tile, void* stream);
+int pp_head(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dtype, const void* in,
+            const void* w_packed, const float* scale_shift, void* out, int32_t tile, void* stream);
+
 /* TF32 remainder plane of n floats (device): lo[i] = x[i] - (x[i] with its 13 low mantissa
  * bits cleared), exact in FP32 (the part a TF32 read of x[i] drops).  Turns an FP32 tensor into
  * the split FP32 form of PP_F32_TC (x as plane 0, lo as plane 1).  x and lo may not overlap. */

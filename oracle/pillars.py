@@ -10,7 +10,12 @@ module restates its front end step by step as this library specifies it:
    valid points;
 3. BEV scatter: each pillar's feature vector lands at its cell of a [ny][nx][C] canvas, zeros
    elsewhere;
-4. backbone: conv3x3 (zero pad 1) + BN + ReLU layers.
+4. backbone: conv3x3 (zero pad 1) + BN + ReLU layers;
+5. neck and detection head (the rest of PointPillars' GPU segment): each block's output is
+   upsampled to the first block's resolution by a transposed convolution whose kernel equals its
+   stride (no overlap), followed by BN + ReLU; the upsampled maps are concatenated along
+   channels in block order; a 1x1 convolution with bias produces the per-anchor class, box and
+   direction outputs.
 
 Readings where the specification is silent (each also listed in the design notes):
 * ranges are half-open [min, max) in x, y and z;
@@ -21,7 +26,12 @@ Readings where the specification is silent (each also listed in the design notes
   means are over the pillar's kept points, (x_c, y_c) is the pillar's cell centre
   xmin + (ix + 0.5) vx, ymin + (iy + 0.5) vy with the binary32 geometry constants;
 * BN is y = gamma (h - mean) / sqrt(var + 1e-3) + beta;
-* the max runs over the pillar's valid points only (padding slots excluded).
+* the max runs over the pillar's valid points only (padding slots excluded);
+* neck: block b is upsampled by s_b = (first block's height) / (block b's height) with a
+  transposed convolution of kernel s_b and stride s_b (PyTorch ConvTranspose2d weight layout
+  [cin][cout][s][s], no bias): out[s*y + dy, s*x + dx, co] = sum_ci in[y, x, ci] w[ci, co, dy, dx];
+* head: one 1x1 convolution (weight [cout][cin], bias [cout]) over the concatenated map; its
+  outputs are the anchors' class scores, box parameters and direction scores side by side.
 """
 from __future__ import annotations
 
@@ -155,6 +165,35 @@ def backbone(canvas: np.ndarray, conv_w: Sequence[np.ndarray], conv_bn: Sequence
             li += 1
         outs.append(x)
     return outs
+
+
+def deconv_bn_relu(x: np.ndarray, w: np.ndarray, bn: np.ndarray, s: int) -> np.ndarray:
+    """Transposed convolution with kernel = stride = s (each input pixel writes its own s x s
+    output block), then BN and ReLU.  x [H, W, cin], w [cin, cout, s, s] -> [s H, s W, cout]."""
+    H, W, _ = x.shape
+    cout = w.shape[1]
+    out = np.zeros((s * H, s * W, cout))
+    w = w.astype(np.float64)
+    for dy in range(s):
+        for dx in range(s):
+            out[dy::s, dx::s] = x @ w[:, :, dy, dx]
+    gamma, beta, mu, var = (bn[i].astype(np.float64) for i in range(4))
+    return np.maximum(gamma * (out - mu) / np.sqrt(var + BN_EPS) + beta, 0.0)
+
+
+def neck(blocks: Sequence[np.ndarray], up_w: Sequence[np.ndarray], up_bn: Sequence[np.ndarray]) -> np.ndarray:
+    """Upsample every block output to the first block's resolution and concatenate channels."""
+    H0 = blocks[0].shape[0]
+    ups = []
+    for x, w, bn in zip(blocks, up_w, up_bn):
+        s = H0 // x.shape[0]
+        ups.append(deconv_bn_relu(x, w, bn, s))
+    return np.concatenate(ups, axis=2)
+
+
+def head(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """1x1 convolution with bias: [H, W, cin] x w [cout, cin] + b [cout] -> [H, W, cout]."""
+    return x @ w.astype(np.float64).T + b.astype(np.float64)
 
 
 def frame(points: np.ndarray, g, bb, weights) -> Dict[str, object]:

@@ -173,6 +173,12 @@ _SIGS = {
     "pp_conv_autotune": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I,
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "pp_tf32_split": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "pp_upsample_packed_bytes": (_SZ, [_I, _I, _I, _I]),
+    "pp_upsample_pack_weights": (ctypes.c_int, [_P, _I, _I, _I, _I, _P]),
+    "pp_head_packed_bytes": (_SZ, [_I, _I, _I]),
+    "pp_head_pack_weights": (ctypes.c_int, [_P, _P, _I, _I, _I, _P, _P]),
+    "pp_upsample": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _I, _I, _P]),
+    "pp_head": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P]),
     "pp_conv3x3_ws": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P, _SZ, _P]),
     "pp_conv_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I, _I, _I]),
     "pp_conv_autotune_ws": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _I,
@@ -422,6 +428,54 @@ def conv3x3(x, w_packed, scale_shift, cout, stride, dtype=PP_F32, tile=-1, out=N
     ws_ptr, ws_n = (workspace[1], workspace[2]) if workspace else (None, 0)
     _check(lib().pp_conv3x3_ws(B, H, W, cin, cout, stride, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
                                _ptr(out), tile, ws_ptr, ws_n, _stream(stream)))
+    return out
+
+
+def pack_upsample_weights(w, up, dtype):
+    """Host float32 ConvTranspose2d weights [cin, cout, up, up] -> packed device weights."""
+    import numpy as np
+    import torch
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    cin, cout = int(w.shape[0]), int(w.shape[1])
+    buf = torch.empty(lib().pp_upsample_packed_bytes(cin, cout, up, dtype), dtype=torch.uint8, device="cuda")
+    _check(lib().pp_upsample_pack_weights(w.ctypes.data, cin, cout, up, dtype, _ptr(buf)))
+    return buf
+
+
+def pack_head_weights(w, b, dtype):
+    """Host float32 head weights [cout, cin] and bias [cout] -> (packed device weights, device
+    scale_shift [2, cout_pad])."""
+    import numpy as np
+    import torch
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    cout, cin = int(w.shape[0]), int(w.shape[1])
+    buf = torch.empty(lib().pp_head_packed_bytes(cin, cout, dtype), dtype=torch.uint8, device="cuda")
+    pad = (cout + 63) // 64 * 64
+    ss = torch.empty((2, pad), dtype=torch.float32, device="cuda")
+    _check(lib().pp_head_pack_weights(w.ctypes.data, b.ctypes.data, cin, cout, dtype, _ptr(buf), _ptr(ss)))
+    return buf, ss
+
+
+def upsample(x, w_packed, scale_shift, cout, up, dtype, out, out_coff=0, tile=-1, stream=None):
+    """pp_upsample of x (padded NHWC [B, H+2, W+2, cin]; split FP32 [2, B, ...] for PP_F32_TC)
+    into channels [out_coff, out_coff + cout) of ``out`` ([.., B, up H + 2, up W + 2, out_c])."""
+    B, Hp, Wp, cin = (int(v) for v in x.shape[-4:])
+    out_c = int(out.shape[-1])
+    _check(lib().pp_upsample(B, Hp - 2, Wp - 2, cin, cout, up, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
+                             _ptr(out), out_c, out_coff, tile, _stream(stream)))
+    return out
+
+
+def head(x, w_packed, scale_shift, cout, dtype, tile=-1, out=None, stream=None):
+    """pp_head of x -> [(2,) B, H+2, W+2, cout_pad] (channels >= cout are zero)."""
+    import torch
+    B, Hp, Wp, cin = (int(v) for v in x.shape[-4:])
+    pad = (cout + 63) // 64 * 64
+    if out is None:
+        out = torch.zeros(((2,) if dtype == PP_F32_TC else ()) + (B, Hp, Wp, pad), dtype=x.dtype, device=x.device)
+    _check(lib().pp_head(B, Hp - 2, Wp - 2, cin, cout, dtype, _ptr(x), _ptr(w_packed), _ptr(scale_shift),
+                         _ptr(out), tile, _stream(stream)))
     return out
 
 

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 namespace pp {
 
@@ -55,6 +56,52 @@ int tc_error_read(unsigned* code, bool clear);
 using namespace pp;
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+namespace pp {
+namespace {
+
+// float -> bf16 bits, round to nearest even (NaN kept quiet)
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (uint16_t)((u >> 16) | 0x40u);
+  const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(r >> 16);
+}
+
+// Packs a K-major GEMM weight matrix given element by element (value(n, k), n < N, k < K, rows
+// n >= n_valid zero) for `dtype` and copies it to the device: BF16 [N][K] bf16; F32_TC [2][N][K]
+// float (TF32 part, remainder).
+template <class F>
+int pack_gemm(int N, int n_valid, int K, int dtype, F value, void* dst) {
+  const size_t nk = (size_t)N * K;
+  std::vector<uint16_t> b16;
+  std::vector<float> f32;
+  if (dtype == PP_BF16) b16.assign(nk, 0); else f32.assign(2 * nk, 0.f);
+  for (int n = 0; n < n_valid; ++n)
+    for (int k = 0; k < K; ++k) {
+      const float v = value(n, k);
+      if (dtype == PP_BF16) {
+        b16[(size_t)n * K + k] = bf16_bits(v);
+      } else {
+        uint32_t u;
+        memcpy(&u, &v, 4);
+        u &= 0xFFFFE000u;
+        float hi;
+        memcpy(&hi, &u, 4);
+        f32[(size_t)n * K + k] = hi;
+        f32[nk + (size_t)n * K + k] = v - hi;
+      }
+    }
+  const cudaError_t e = dtype == PP_BF16 ? cudaMemcpy(dst, b16.data(), nk * 2, cudaMemcpyHostToDevice)
+                                         : cudaMemcpy(dst, f32.data(), 2 * nk * 4, cudaMemcpyHostToDevice);
+  return cuda_status(e, "upload packed GEMM weights");
+}
+
+int head_pad(int cout) { return (cout + 63) / 64 * 64; }
+
+}  // namespace
+}  // namespace pp
 
 extern "C" {
 
@@ -227,6 +274,72 @@ int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t
       (dtype != PP_F32 && dtype != PP_BF16 && dtype != PP_F32_TC))
     return fail(PP_EINVAL, "pack_weights: bad argument");
   return conv_pack_launch(w_oihw, cin, cout, dtype, w_packed, static_cast<cudaStream_t>(stream));
+}
+
+// ---- neck (transposed-conv upsampling) and detection head on the tensor-core GEMM
+
+size_t pp_upsample_packed_bytes(int32_t cin, int32_t cout, int32_t up, int32_t dtype) {
+  if (cin <= 0 || cin % 64 || cout <= 0 || cout % 64 || up < 1 || up > 8 ||
+      (dtype != PP_BF16 && dtype != PP_F32_TC))
+    return 0;
+  return (size_t)up * up * cout * cin * (dtype == PP_BF16 ? 2 : 8);
+}
+
+int pp_upsample_pack_weights(const float* w, int32_t cin, int32_t cout, int32_t up, int32_t dtype,
+                             void* w_packed) {
+  if (!w || !w_packed || cin <= 0 || cout <= 0 || up < 1 || up > 8 || (dtype != PP_BF16 && dtype != PP_F32_TC))
+    return fail(PP_EINVAL, "upsample_pack_weights: bad argument");
+  // GEMM column n = (dy * up + dx) * cout + co  <-  w[ci][co][dy][dx]
+  return pack_gemm(up * up * cout, up * up * cout, cin, dtype,
+                   [&](int n, int k) {
+                     const int q = n / cout, co = n % cout;
+                     return w[(((size_t)k * cout + co) * up + q / up) * up + q % up];
+                   },
+                   w_packed);
+}
+
+size_t pp_head_packed_bytes(int32_t cin, int32_t cout, int32_t dtype) {
+  if (cin <= 0 || cin % 64 || cout <= 0 || cout > 1024 || (dtype != PP_BF16 && dtype != PP_F32_TC)) return 0;
+  return (size_t)head_pad(cout) * cin * (dtype == PP_BF16 ? 2 : 8);
+}
+
+int pp_head_pack_weights(const float* w, const float* bias, int32_t cin, int32_t cout, int32_t dtype,
+                         void* w_packed, float* scale_shift) {
+  if (!w || !bias || !w_packed || !scale_shift || cin <= 0 || cout <= 0 || (dtype != PP_BF16 && dtype != PP_F32_TC))
+    return fail(PP_EINVAL, "head_pack_weights: bad argument");
+  const int np = head_pad(cout);
+  int st = pack_gemm(np, cout, cin, dtype, [&](int n, int k) { return w[(size_t)n * cin + k]; }, w_packed);
+  if (st) return st;
+  std::vector<float> ss(2 * (size_t)np, 0.f);
+  for (int n = 0; n < np; ++n) ss[n] = 1.f;
+  for (int n = 0; n < cout; ++n) ss[np + n] = bias[n];
+  return cuda_status(cudaMemcpy(scale_shift, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice), "upload head bias");
+}
+
+int pp_upsample(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t up, int32_t dtype,
+                const void* in, const void* w_packed, const float* scale_shift, void* out, int32_t out_c,
+                int32_t out_coff, int32_t tile, void* stream) {
+  if (batch <= 0 || H <= 0 || W <= 0 || cin <= 0 || cin % 64 || cout <= 0 || cout % 64 || up < 1 || up > 8 ||
+      out_c % 64 || out_coff % 64 || out_coff < 0 || out_coff + cout > out_c || cout > 1024)
+    return fail(PP_EINVAL, "upsample: unsupported shape (cin, cout, out_c, out_coff multiples of 64)");
+  if (!in || !w_packed || !scale_shift || !out) return fail(PP_EINVAL, "upsample: NULL buffer");
+  ConvShape c;
+  c.batch = batch; c.H = H; c.W = W; c.cin = cin; c.cout = up * up * cout; c.stride = 1; c.Ho = H; c.Wo = W;
+  GemmOpts g;
+  g.taps = 1; g.up = up; g.co_blk = cout; g.out_c = out_c; g.out_coff = out_coff; g.relu = 1;
+  return gemm_tc_launch(dtype, c, g, in, w_packed, scale_shift, out, tile, static_cast<cudaStream_t>(stream));
+}
+
+int pp_head(int32_t batch, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dtype, const void* in,
+            const void* w_packed, const float* scale_shift, void* out, int32_t tile, void* stream) {
+  if (batch <= 0 || H <= 0 || W <= 0 || cin <= 0 || cin % 64 || cout <= 0 || cout > 1024)
+    return fail(PP_EINVAL, "head: unsupported shape (cin multiple of 64)");
+  if (!in || !w_packed || !scale_shift || !out) return fail(PP_EINVAL, "head: NULL buffer");
+  ConvShape c;
+  c.batch = batch; c.H = H; c.W = W; c.cin = cin; c.cout = head_pad(cout); c.stride = 1; c.Ho = H; c.Wo = W;
+  GemmOpts g;
+  g.taps = 1; g.relu = 0;
+  return gemm_tc_launch(dtype, c, g, in, w_packed, scale_shift, out, tile, static_cast<cudaStream_t>(stream));
 }
 
 int pp_bn_fold(const float* bn, int32_t c, float eps, float* out) {

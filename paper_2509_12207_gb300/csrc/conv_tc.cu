@@ -406,6 +406,11 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 struct PArgs {
   ConvShape c;
   int bh, bw, tiles_x, tiles_y, tiles_n, total, fold;
+  // GEMM shape and epilogue mapping (3x3 conv: taps 9, up 1, co_blk = out_c = cout, relu 1).
+  // taps 1 = pointwise (1x1) GEMM over the centre tap.  up > 1: a transposed conv with kernel =
+  // stride = up, GEMM column n = (dy * up + dx) * co_blk + co written to output pixel
+  // (up * y + dy, up * x + dx), channel out_coff + co of an out_c-channel [Hout+2][Wout+2] map.
+  int taps, up, co_blk, out_c, out_coff, Hout, Wout, relu;
   size_t plane;  // 3xTF32: elements from the output's value plane to its remainder plane
   const float* ss;
   void* out;
@@ -449,19 +454,20 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   uint64_t* kfree = kdone + NBUF;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + NBUF);
   float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);  // [cout] folded BN scale
-  float* s_shift = s_scale + args.c.cout;                    // [cout] folded BN shift
+  float* s_shift = s_scale + args.co_blk;                    // [co_blk] folded BN shift (or bias)
 
   const ConvShape& c = args.c;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kchunks = c.cin / BK;
-  const int KB = 9 * kchunks;
+  const int KB = args.taps * kchunks;
   const int fold = MODE == 1 ? args.fold : KB;
   const int Hp2 = (c.H + 2) / 2;
 
-  for (int i = threadIdx.x; i < c.cout; i += blockDim.x) {
+  for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
     s_scale[i] = args.ss[i];
-    s_shift[i] = args.ss[c.cout + i];
+    s_shift[i] = args.ss[args.co_blk + i];
   }
+  const float lo_clamp = args.relu ? 0.f : __uint_as_float(0xff800000u);  // ReLU, or none (-inf: bias-only epilogue)
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -529,7 +535,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         int b, oy0, ox0, n0;
         decode(t, b, oy0, ox0, n0);
         // channel chunk, tap, K offset of the next K block
-        int cc = k0 % kchunks, kx = (k0 / kchunks) % 3, ky = k0 / kchunks / 3, kk = k0 * BK;
+        // pointwise GEMMs read the centre tap (the unpadded pixel) only
+        int cc = k0 % kchunks, kk = k0 * BK;
+        int kx = args.taps == 9 ? (k0 / kchunks) % 3 : 1, ky = args.taps == 9 ? k0 / kchunks / 3 : 1;
         for (int kb0 = k0; kb0 < k1; kb0 += KPS) {
           const int nk = k1 - kb0 < KPS ? k1 - kb0 : KPS;
           if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
@@ -556,7 +564,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             kk += BK;
             if (++cc == kchunks) {
               cc = 0;
-              if (++kx == 3) { kx = 0; ++ky; }
+              if (args.taps == 9 && ++kx == 3) { kx = 0; ++ky; }
             }
           }
           if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -623,7 +631,12 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       decode(t, b, oy0, ox0, n0);
       const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
       const bool in_range = oy < c.Ho && ox < c.Wo;
-      const size_t pix = ((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1;
+      // output pixel of this row for this N tile (a transposed conv spreads the N tiles of one
+      // input pixel over its up x up output block); first channel written and its BN index
+      const int qb = n0 / args.co_blk, nb = n0 - qb * args.co_blk;
+      const int opy = args.up * oy + qb / args.up, opx = args.up * ox + qb % args.up;
+      const size_t pix = ((size_t)b * (args.Hout + 2) + opy + 1) * (args.Wout + 2) + opx + 1;
+      const size_t obase = pix * args.out_c + args.out_coff + nb;
       if (MODE == 1) {
         float acc[BN];
 #pragma unroll
@@ -694,19 +707,19 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           // channels (128 B per pixel) at a time through the warp's transposing buffer
           if (!ok) break;
           uint4* wbuf = reinterpret_cast<uint4*>(sO + q * 4096);
-          float* orow = static_cast<float*>(args.out) + pix * c.cout + n0;
+          float* orow = static_cast<float*>(args.out) + obase;
 #pragma unroll
           for (int k = 0; k < BN / 32; ++k) {
             uint4 hv[8], lv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int n = n0 + 32 * k + 4 * j;
+              const int n = nb + 32 * k + 4 * j;
               const float* a = acc + 32 * k + 4 * j;
               float4 u;
-              u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), 0.f);
-              u.y = fmaxf(fmaf(a[1], s_scale[n + 1], s_shift[n + 1]), 0.f);
-              u.z = fmaxf(fmaf(a[2], s_scale[n + 2], s_shift[n + 2]), 0.f);
-              u.w = fmaxf(fmaf(a[3], s_scale[n + 3], s_shift[n + 3]), 0.f);
+              u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), lo_clamp);
+              u.y = fmaxf(fmaf(a[1], s_scale[n + 1], s_shift[n + 1]), lo_clamp);
+              u.z = fmaxf(fmaf(a[2], s_scale[n + 2], s_shift[n + 2]), lo_clamp);
+              u.w = fmaxf(fmaf(a[3], s_scale[n + 3], s_shift[n + 3]), lo_clamp);
               const float4 l = tf32_remainder4(u);
               hv[j] = make_uint4(__float_as_uint(u.x), __float_as_uint(u.y), __float_as_uint(u.z), __float_as_uint(u.w));
               lv[j] = make_uint4(__float_as_uint(l.x), __float_as_uint(l.y), __float_as_uint(l.z), __float_as_uint(l.w));
@@ -721,7 +734,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
         if (!ok) break;
         tc_fence_after();
-        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(args.out) + pix * c.cout + n0;
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(args.out) + obase;
 #pragma unroll 1
         for (int j = 0; j < BN / 64; ++j) {
           uint32_t v[64];
@@ -732,9 +745,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             uint32_t pk[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-              const int n = n0 + j * 64 + 2 * i;
-              const float a0 = fmaxf(fmaf(__uint_as_float(v[2 * i]), s_scale[n], s_shift[n]), 0.f);
-              const float a1 = fmaxf(fmaf(__uint_as_float(v[2 * i + 1]), s_scale[n + 1], s_shift[n + 1]), 0.f);
+              const int n = nb + j * 64 + 2 * i;
+              const float a0 = fmaxf(fmaf(__uint_as_float(v[2 * i]), s_scale[n], s_shift[n]), lo_clamp);
+              const float a1 = fmaxf(fmaf(__uint_as_float(v[2 * i + 1]), s_scale[n + 1], s_shift[n + 1]), lo_clamp);
               __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
               pk[i] = *reinterpret_cast<uint32_t*>(&h);
             }
@@ -1035,7 +1048,8 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
 
 int conv_tcp_tile_count(int mode);
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
-                    void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0);
+                    void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0,
+                    const GemmOpts& g = GemmOpts());
 int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
                      cudaStream_t s);
 int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0) + 1; }
@@ -1214,16 +1228,21 @@ int pick_tile_p(const ConvShape& c, const TileP* tiles, int n) {
 // mode 0: BF16 in/out, weights [cout][9cin] bf16; mode 1: split FP32 in/out ([2][B][H+2][W+2][C]:
 // values, TF32 remainders) via 3xTF32, weights [2][cout][9cin] fp32 (hi, lo planes).
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
-                    void* out, int ptile, cudaStream_t s, void* ws, size_t ws_bytes) {
+                    void* out, int ptile, cudaStream_t s, void* ws, size_t ws_bytes, const GemmOpts& g) {
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
+  const int co_blk = g.co_blk ? g.co_blk : c.cout, out_c = g.out_c ? g.out_c : co_blk;
+  if ((g.taps != 9 && g.taps != 1) || g.up < 1 || (g.taps == 1 && c.stride != 1) ||
+      g.up * g.up * co_blk != c.cout || co_blk % 64 || out_c % 64 || g.out_coff % 64 ||
+      g.out_coff + co_blk > out_c || co_blk > 1024)
+    return fail(PP_EINVAL, "persistent conv: bad GEMM options");
   const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
   const int n = mode == 1 ? kNPF : kNPB;
   // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition
   const bool sk = mode == 1 && ptile >= n;
   if (sk) ptile -= n;
   if (ptile < 0) ptile = pick_tile_p(c, tiles, n);
-  if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn)
+  if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn)
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
   const TileP t = tiles[ptile];
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
@@ -1258,7 +1277,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   if (mode != 1) talo = ta;
   if (r != CUDA_SUCCESS) return fail(PP_EDEVICE, "persistent conv: activation tensor map (%d)", (int)r);
   {
-    const int K = 9 * c.cin;
+    const int K = g.taps * c.cin;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)c.cout, (cuuint64_t)(mode == 1 ? 2 : 1)};
     cuuint64_t strides[2] = {(cuuint64_t)K * el, (cuuint64_t)K * c.cout * el};
     cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bn, 1};
@@ -1277,7 +1296,15 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
   args.fold = 2;
-  args.plane = c.out_plane ? c.out_plane : (size_t)c.batch * (c.Ho + 2) * (c.Wo + 2) * c.cout;
+  args.taps = g.taps;
+  args.up = g.up;
+  args.co_blk = co_blk;
+  args.out_c = out_c;
+  args.out_coff = g.out_coff;
+  args.Hout = g.up * c.Ho;
+  args.Wout = g.up * c.Wo;
+  args.relu = g.relu;
+  args.plane = c.out_plane ? c.out_plane : (size_t)c.batch * (args.Hout + 2) * (args.Wout + 2) * out_c;
   args.ss = ss;
   args.out = out;
   args.sk = sk ? 1 : 0;
@@ -1383,6 +1410,18 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
 }
 
 int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF : kNPB; }
+
+int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
+                   const float* ss, void* out, int tile, cudaStream_t s) {
+  if (dtype != PP_BF16 && dtype != PP_F32_TC) return fail(PP_EINVAL, "tensor-core GEMM: dtype must be BF16 or F32_TC");
+  const int mode = dtype == PP_F32_TC ? 1 : 0;
+  if (c.cin % (mode == 1 ? 32 : 64)) return fail(PP_EINVAL, "tensor-core GEMM: bad cin");
+  // tiles are numbered as for the 3x3 conv; only the persistent (non-stream-K) ones apply
+  const int first = mode == 1 ? 0 : (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
+  if (tile >= 0 && (tile < first || tile >= first + (mode == 1 ? kNPF : kNPB)))
+    return fail(PP_EINVAL, "tensor-core GEMM: tile %d is not a persistent tile", tile);
+  return conv_tcp_launch(mode, c, in, w, ss, out, tile < 0 ? -1 : tile - first, s, nullptr, 0, g);
+}
 
 // Workspace for any stream-K tile of this shape: partial tiles for two pieces per CTA at the
 // widest N tile, then one arrival counter per output tile of the narrowest.

@@ -65,6 +65,17 @@ struct ConvShape {
   // the output; 0 = this batch's plane size (planes packed for exactly `batch` frames)
   size_t in_plane = 0, out_plane = 0;
 };
+// The persistent tensor-core kernel as a general implicit GEMM (see conv_tc.cu PArgs): taps 9 =
+// 3x3 conv, 1 = pointwise; up > 1 = transposed conv with kernel = stride = up (GEMM N =
+// up * up * co_blk); output written at channel offset out_coff of an out_c-channel map; relu 0 =
+// bias-only epilogue (scale_shift = [1.., bias..]).  Zero fields take the 3x3-conv defaults.
+struct GemmOpts {
+  int taps = 9, up = 1, co_blk = 0, out_c = 0, out_coff = 0, relu = 1;
+};
+// dtype PP_BF16 (mode 0) or PP_F32_TC (mode 1, split FP32 operands); tile: persistent tile
+// index or -1 (shape heuristic).
+int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
+                   const float* ss, void* out, int tile, cudaStream_t s);
 int conv_f32_launch(const ConvShape& c, const float* in, const float* w_kn, const float* ss,
                     float* out, int tile, cudaStream_t s);
 int conv_f32_tile_count();

@@ -153,6 +153,36 @@ def pillar_weights(backbone: Backbone, seed: int = 7, cin: int = 64):
     return pfn_w, pfn_bn, conv_w, conv_bn
 
 
+NECK_CHANNELS = 128      # per upsampled block
+HEAD_OUTPUTS = 72        # 6 anchors per location x (3 class scores + 7 box parameters + 2 direction scores)
+
+
+def head_weights(backbone: Backbone, seed: int = 17, up_channels: int = NECK_CHANNELS,
+                 head_outputs: int = HEAD_OUTPUTS):
+    """Random-init weights for the neck and the detection head.
+
+    Returns ``(up_w list of [cin, up_channels, s, s], up_bn list of [4, up_channels], head_w
+    [head_outputs, n_blocks * up_channels], head_b [head_outputs])``, float32; block b's
+    upsampling stride s is the product of the strides of blocks 1..b (its map's reduction
+    relative to the first block's).
+    Weights He-normal over the fan-in (cin for the transposed convs), BN as in the backbone
+    (gamma ~ U[0.5, 1.5], beta ~ U[-0.1, 0.1], mean 0, var 1), bias ~ U[-0.1, 0.1].
+    """
+    rng = np.random.default_rng(seed)
+    up_w, up_bn = [], []
+    s = 1
+    for b, ch in enumerate(backbone.chans):
+        if b:
+            s *= backbone.strides[b]
+        up_w.append(rng.normal(0.0, np.sqrt(2.0 / ch), (ch, up_channels, s, s)).astype(np.float32))
+        up_bn.append(np.stack([rng.uniform(0.5, 1.5, up_channels), rng.uniform(-0.1, 0.1, up_channels),
+                               np.zeros(up_channels), np.ones(up_channels)]).astype(np.float32))
+    cin = up_channels * len(backbone.chans)
+    head_w = rng.normal(0.0, np.sqrt(1.0 / cin), (head_outputs, cin)).astype(np.float32)
+    head_b = rng.uniform(-0.1, 0.1, head_outputs).astype(np.float32)
+    return up_w, up_bn, head_w, head_b
+
+
 @dataclasses.dataclass(frozen=True)
 class ChainSpec:
     chain_id: int

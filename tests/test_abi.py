@@ -112,3 +112,27 @@ def test_config_defaults_and_host_validation(lib):
         info = pp.conv_tile_info(pp.PP_F32_TC, t)
         assert info[3] == (1 if t < n // 2 else 3)
         assert info[:3] == pp.conv_tile_info(pp.PP_F32_TC, t % (n // 2))[:3]
+
+
+def test_neck_head_host_validation(lib):
+    import paper_2509_12207_gb300 as pp
+    # packed sizes: [up*up*cout][cin] (BF16) or [2][up*up*cout][cin] (split FP32); the head pads
+    # its outputs to a multiple of 64
+    assert lib.pp_upsample_packed_bytes(128, 128, 2, pp.PP_BF16) == 4 * 128 * 128 * 2
+    assert lib.pp_upsample_packed_bytes(256, 128, 4, pp.PP_F32_TC) == 2 * 16 * 128 * 256 * 4
+    assert lib.pp_head_packed_bytes(384, 72, pp.PP_BF16) == 128 * 384 * 2
+    assert lib.pp_head_packed_bytes(384, 72, pp.PP_F32_TC) == 2 * 128 * 384 * 4
+    assert lib.pp_upsample_packed_bytes(100, 128, 2, pp.PP_BF16) == 0
+    assert lib.pp_upsample_packed_bytes(128, 128, 2, pp.PP_F32) == 0
+    p = 4096
+    ok = (1, 8, 8, 128, 128, 2, pp.PP_BF16, p, p, p, p, 384, 128, -1, None)
+    for i, bad in [(3, 96), (4, 100), (5, 0), (5, 9), (11, 200), (12, 32), (12, 320)]:
+        args = list(ok)
+        args[i] = bad
+        assert lib.pp_upsample(*args) == pp.PP_EINVAL, (i, bad)
+    args = list(ok)
+    args[7] = None
+    assert lib.pp_upsample(*args) == pp.PP_EINVAL and b"NULL" in lib.pp_last_error()
+    assert lib.pp_head(1, 8, 8, 100, 72, pp.PP_BF16, p, p, p, p, -1, None) == pp.PP_EINVAL
+    assert lib.pp_head(1, 8, 8, 384, 0, pp.PP_BF16, p, p, p, p, -1, None) == pp.PP_EINVAL
+    assert lib.pp_head(1, 8, 8, 384, 72, pp.PP_BF16, None, p, p, p, -1, None) == pp.PP_EINVAL

@@ -346,3 +346,104 @@ def test_conv_autotune_then_library_choice(dtype):
         tol = FP32_TOL if dtype == pp.PP_F32_TC else BF16_TOL
         assert rel_err(o[b, 1:-1, 1:-1], ref[b]) <= tol
     pp.conv_tune_clear()
+
+
+# ---- neck (transposed-conv upsampling + concatenation) and detection head
+
+def _dev_input(xp, dtype):
+    t = torch.from_numpy(xp).to(DEV)
+    return pp.split_f32(t) if dtype == pp.PP_F32_TC else t.to(torch.bfloat16)
+
+
+def _ref_input(xp, dtype):
+    """What the kernel reads: the FP32 values, or their BF16 roundings."""
+    return xp.astype(np.float64) if dtype == pp.PP_F32_TC else _bf16(xp).double().numpy()
+
+
+def _close(got, ref, dtype):
+    if dtype == pp.PP_F32_TC:
+        return rel_err(got, ref) <= FP32_TOL
+    from tests._util import max_norm_err
+    return max_norm_err(got, ref) <= BF16_TOL
+
+
+@pytest.mark.parametrize("dtype", [pp.PP_F32_TC, pp.PP_BF16])
+@pytest.mark.parametrize("up,cin,H,W", [(1, 64, 13, 37), (2, 128, 9, 21), (4, 256, 5, 11)])
+def test_upsample_into_concat(dtype, up, cin, H, W):
+    """Transposed conv (kernel = stride = up) + BN + ReLU written into its channel range of a
+    concatenated map, on every persistent tile: matches the oracle; the other channel ranges and
+    the border stay zero."""
+    B, cout, out_c, coff = 2, 128, 384, 128
+    xp, _, bn = _conv_case(B, H, W, cin, cout, 1, seed=up * 100 + cin)
+    rng = np.random.default_rng(up)
+    w = rng.normal(0, np.sqrt(2.0 / cin), (cin, cout, up, up)).astype(np.float32)
+    x_d = _dev_input(xp, dtype)
+    wp = pp.pack_upsample_weights(w, up, dtype)
+    ss = torch.from_numpy(pp.bn_fold(bn)).to(DEV)
+    xr = _ref_input(xp, dtype)
+    refs = [O.deconv_bn_relu(xr[b, 1:-1, 1:-1], w, bn, up) for b in range(B)]
+    planes = (2,) if dtype == pp.PP_F32_TC else ()
+    tdt = torch.float32 if dtype == pp.PP_F32_TC else torch.bfloat16
+    tiles = [t for t in range(pp.conv_tile_count(dtype))
+             if pp.conv_tile_info(dtype, t)[3] == 1 and cout % pp.conv_tile_info(dtype, t)[2] == 0]
+    assert tiles
+    for tile in [-1] + tiles:
+        out = torch.zeros(planes + (B, up * H + 2, up * W + 2, out_c), dtype=tdt, device=DEV)
+        pp.upsample(x_d, wp, ss, cout, up, dtype, out, out_coff=coff, tile=tile)
+        torch.cuda.synchronize()
+        assert pp.device_error() == 0
+        o = (out[0] if planes else out).float().cpu().numpy()
+        for b in range(B):
+            assert _close(o[b, 1:-1, 1:-1, coff:coff + cout], refs[b], dtype), (tile, b)
+        assert not o[:, :, :, :coff].any() and not o[:, :, :, coff + cout:].any()
+        assert not o[:, 0].any() and not o[:, -1].any() and not o[:, :, 0].any() and not o[:, :, -1].any()
+        if planes:
+            assert np.array_equal(out[1].cpu().numpy(), tf32_remainder(out[0].cpu().numpy()))
+
+
+@pytest.mark.parametrize("dtype", [pp.PP_F32_TC, pp.PP_BF16])
+def test_head_1x1(dtype):
+    """The 1x1 head with bias (no activation) over a 384-channel map: matches the oracle; the
+    channels past the 72 outputs are zero."""
+    B, H, W, cin, cout = 2, 19, 27, 384, 72
+    xp, _, _ = _conv_case(B, H, W, cin, 64, 1, seed=9)
+    rng = np.random.default_rng(10)
+    w = rng.normal(0, np.sqrt(1.0 / cin), (cout, cin)).astype(np.float32)
+    bias = rng.uniform(-0.1, 0.1, cout).astype(np.float32)
+    x_d = _dev_input(xp, dtype)
+    wp, ss = pp.pack_head_weights(w, bias, dtype)
+    xr = _ref_input(xp, dtype)
+    out = pp.head(x_d, wp, ss, cout, dtype)
+    torch.cuda.synchronize()
+    o = (out[0] if dtype == pp.PP_F32_TC else out).float().cpu().numpy()
+    assert o.shape[-1] == 128 and not o[..., cout:].any()
+    for b in range(B):
+        ref = O.head(xr[b, 1:-1, 1:-1], w, bias)
+        assert _close(o[b, 1:-1, 1:-1, :cout], ref, dtype), b
+
+
+def test_neck_head_full_size_fp32():
+    """Neck + head on the full-size frame's three block outputs (432x496 grid: 64/128/256
+    channels at 248x216, 124x108, 62x54): three transposed convs into one 384-channel map,
+    then the 72-output head, against the oracle."""
+    from pp_synth import BACKBONE_FULL, head_weights
+    up_w, up_bn, hw, hb = head_weights(BACKBONE_FULL)
+    rng = np.random.default_rng(21)
+    sizes = [(248, 216, 64), (124, 108, 128), (62, 54, 256)]
+    blocks = []
+    for (H, W, C) in sizes:
+        xp = np.zeros((1, H + 2, W + 2, C), np.float32)
+        xp[0, 1:-1, 1:-1] = np.maximum(rng.normal(size=(H, W, C)), 0).astype(np.float32)
+        blocks.append(xp)
+    neck = torch.zeros((2, 1, 250, 218, 384), device=DEV)
+    for k, (xp, w, bn) in enumerate(zip(blocks, up_w, up_bn)):
+        up = 2 ** k
+        pp.upsample(pp.split_f32(torch.from_numpy(xp).to(DEV)), pp.pack_upsample_weights(w, up, pp.PP_F32_TC),
+                    torch.from_numpy(pp.bn_fold(bn)).to(DEV), 128, up, pp.PP_F32_TC, neck, out_coff=128 * k)
+    wp, ss = pp.pack_head_weights(hw, hb, pp.PP_F32_TC)
+    out = pp.head(neck, wp, ss, 72, pp.PP_F32_TC)
+    torch.cuda.synchronize()
+    n_ref = O.neck([b[0, 1:-1, 1:-1].astype(np.float64) for b in blocks], up_w, up_bn)
+    assert rel_err(neck[0, 0, 1:-1, 1:-1].cpu().numpy(), n_ref) <= FP32_TOL
+    h_ref = O.head(n_ref, hw, hb)
+    assert rel_err(out[0, 0, 1:-1, 1:-1, :72].cpu().numpy(), h_ref) <= FP32_TOL

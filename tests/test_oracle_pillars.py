@@ -297,3 +297,39 @@ def test_conv_brute_force_loop():
                             for ci in range(cin):
                                 acc += w[co, ci, ky, kx] * x[iy, ix, ci]
                 assert abs(out[oy, ox, co] - max(acc, 0.0)) < 1e-12
+
+
+def test_neck_head_pins():
+    """Neck and head of the oracle against what fixes them independently: a transposed
+    convolution with kernel = stride is torch's conv_transpose2d (FP64, CPU; a library routine
+    for a textbook op), identity weights give nearest-neighbour upsampling, the 1x1 head is a
+    matrix product plus bias, and the neck concatenates in block order."""
+    import torch
+    rng = np.random.default_rng(4)
+    for s in (1, 2, 4):
+        x = rng.standard_normal((5, 6, 8))
+        w = rng.standard_normal((8, 3, s, s)).astype(np.float32)
+        bn = np.stack([np.ones(3), np.zeros(3), np.zeros(3), np.full(3, 1.0 - O.BN_EPS)])  # BN = identity
+        got = O.deconv_bn_relu(x, w, bn, s)
+        ref = torch.nn.functional.conv_transpose2d(torch.from_numpy(x).permute(2, 0, 1)[None],
+                                                   torch.from_numpy(w.astype(np.float64)), stride=s)
+        ref = np.maximum(ref[0].permute(1, 2, 0).numpy(), 0.0)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12), s
+    # identity transposed conv = nearest upsampling (positive inputs survive the ReLU)
+    x = rng.uniform(0.1, 1.0, (3, 4, 2))
+    w = np.zeros((2, 2, 2, 2), np.float32)
+    for c in range(2):
+        w[c, c] = 1.0
+    bn = np.stack([np.ones(2), np.zeros(2), np.zeros(2), np.full(2, 1.0 - O.BN_EPS)])
+    up = O.deconv_bn_relu(x, w, bn, 2)
+    assert np.allclose(up, np.repeat(np.repeat(x, 2, axis=0), 2, axis=1), rtol=1e-14, atol=0)
+    # head = matrix product + bias; neck = concatenation of the upsampled blocks in order
+    hw = rng.standard_normal((5, 4)).astype(np.float32)
+    hb = rng.standard_normal(5).astype(np.float32)
+    x = rng.standard_normal((3, 3, 4))
+    assert np.allclose(O.head(x, hw, hb), np.einsum("hwc,oc->hwo", x, hw.astype(np.float64)) + hb)
+    b0, b1 = rng.uniform(0.1, 1, (4, 4, 2)), rng.uniform(0.1, 1, (2, 2, 2))
+    n = O.neck([b0, b1], [w[:, :, :1, :1].copy(), w], [bn, bn])
+    assert n.shape == (4, 4, 4)
+    assert np.allclose(n[:, :, :2], b0, rtol=1e-14, atol=0)
+    assert np.allclose(n[:, :, 2:], np.repeat(np.repeat(b1, 2, 0), 2, 1), rtol=1e-14, atol=0)
