@@ -32,6 +32,8 @@ WORKLOADS = {
     "cfg3-bf16": "batched BF16: 8 frames of 30k-150k uniform points per unit, 216x248 grid, 3 conv3x3 64ch",
 }
 
+HEAD_NOTE = ", + neck (transposed convs to 128 channels each, concatenated) and 1x1 head (72 outputs)"
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -41,6 +43,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2-fp32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--head", action="store_true",
+                    help="the step also runs the neck (upsample + concat) and the detection head")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
@@ -121,20 +125,27 @@ def _conv_flops(g, bb):
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
 
-def _oracle_seconds(name, frames_to_run):
+def _oracle_seconds(name, frames_to_run, head=False):
     """Times the FP64 oracle on ``frames_to_run`` frames of the workload (this process)."""
     from oracle import pillars as O
     g, bb, _prec, _batch, _cap, frames, w = _workload(name)
+    hw = None
+    if head:
+        from pp_synth import head_weights
+        hw = head_weights(bb)
     t0 = time.perf_counter()
     for k in range(frames_to_run):
-        O.frame(frames[k % len(frames)], g, bb, w)
+        r = O.frame(frames[k % len(frames)], g, bb, w)
+        if hw is not None:
+            O.head(O.neck(r["blocks"], hw[0], hw[1]), hw[2], hw[3])
     return time.perf_counter() - t0
 
 
-def _cpu_baseline(name, n_frames=1):
+def _cpu_baseline(name, n_frames=1, head=False):
     """Runs the oracle single-threaded in a child process (BLAS pinned to one thread)."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "%s:%d" % (name, n_frames),
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                          "%s:%d:%d" % (name, n_frames, 1 if head else 0),
                           "--workload", name], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         return {"value": None, "unit": "frames/s", "cores": 1, "kind": "oracle",
@@ -261,6 +272,71 @@ def _time_conv_kernels(pp, torch, g, bb, w, prec, batch, reps=20, tile=-1):
     return per_layer
 
 
+def _time_neck_head(pp, torch, g, bb, prec, batch, reps=20):
+    """Average duration of each neck launch (one transposed conv per block into the concatenated
+    map) and of the 1x1 head, timed as the convs are (graph of `reps` launches, one replay under
+    CUDA events), with its algorithmic FLOPs and HBM bytes: the input map read once, the output
+    written once, the weights read once (elt bytes per element: 8 for split FP32, value and
+    remainder; 2 for BF16).  The head counts its real outputs (72), not its padding to 128."""
+    from pp_synth import NECK_CHANNELS, head_weights
+    up_w, up_bn, hw, hb = head_weights(bb)
+    dt = torch.bfloat16 if prec == pp.PP_BF16 else torch.float32
+    planes = (2,) if prec == pp.PP_F32_TC else ()
+    elt = 8 if prec == pp.PP_F32_TC else 2
+    sizes, H, W = [], g.ny, g.nx
+    for (ci, co, s) in bb.layers(64):
+        H, W = (H - 1) // s + 1, (W - 1) // s + 1
+        sizes.append((H, W, co))
+    blocks = [sizes[e] for e in _block_ends(bb)]
+    H0, W0 = blocks[0][:2]
+    neck_c = NECK_CHANNELS * len(blocks)
+    neck = torch.zeros(planes + (batch, H0 + 2, W0 + 2, neck_c), dtype=dt, device="cuda")
+    launches = []
+    for k, ((Hb, Wb, C), wt, bn) in enumerate(zip(blocks, up_w, up_bn)):
+        x = torch.rand((batch, Hb + 2, Wb + 2, C), device="cuda").to(dt)
+        if planes:
+            x = pp.split_f32(x)
+        up = H0 // Hb
+        wp = pp.pack_upsample_weights(wt, up, prec)
+        ss = torch.from_numpy(pp.bn_fold(bn)).cuda()
+        fn = (lambda x=x, wp=wp, ss=ss, up=up, k=k:
+              pp.upsample(x, wp, ss, NECK_CHANNELS, up, prec, neck, out_coff=k * NECK_CHANNELS))
+        byt = elt * (batch * Hb * Wb * C + batch * H0 * W0 * NECK_CHANNELS + C * up * up * NECK_CHANNELS)
+        launches.append(("upsample x%d" % up, fn, 2.0 * batch * Hb * Wb * C * up * up * NECK_CHANNELS, byt))
+    hwp, hss = pp.pack_head_weights(hw, hb, prec)
+    hout = torch.zeros(planes + (batch, H0 + 2, W0 + 2, 128), dtype=dt, device="cuda")
+    nout = hw.shape[0]
+    launches.append(("head", lambda: pp.head(neck, hwp, hss, nout, prec, out=hout),
+                     2.0 * batch * H0 * W0 * neck_c * nout,
+                     elt * (batch * H0 * W0 * (neck_c + nout) + neck_c * nout)))
+    stream = torch.cuda.current_stream()
+    out = []
+    for name, fn, flops, byt in launches:
+        fn()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                fn()
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append((name, e0.elapsed_time(e1) / reps * 1e-3, flops, byt))
+    return out
+
+
+def _block_ends(bb):
+    ends, n = [], 0
+    for c in bb.convs:
+        n += c
+        ends.append(n - 1)
+    return ends
+
+
 def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
     """Device time of the voxelise / PointNet / scatter stages for one step's batch of frames,
     each stage captured in a CUDA graph (so that only the device work is timed) and replayed."""
@@ -315,7 +391,11 @@ def _run_ours(a, rank, world, dist):
     # throughput run: no deadline pressure (early exit off, 10 s deadline), so a slow run (a
     # profiler) still completes every frame
     tuned = bool(a.tune_table) and os.path.exists(a.tune_table) and pp.conv_tune_load(a.tune_table) > 0
-    cfg, keep = pp.make_config(g, bb, w, max_batch=batch, cap_points=cap, precisions=1 << prec,
+    head = None
+    if a.head:
+        from pp_synth import head_weights
+        head = head_weights(bb)
+    cfg, keep = pp.make_config(g, bb, w, head=head, max_batch=batch, cap_points=cap, precisions=1 << prec,
                                units=max(2, a.depth), max_admitted=2 * a.depth * batch,
                                th_urgent=-1.0, early_exit=0, fp32_cuda_cores=1 if a.fp32_cuda_cores else 0,
                                autotune=0 if tuned else 1)
@@ -424,13 +504,28 @@ def _run_ours(a, rank, world, dist):
         bound, peak_note = "tensor", "bf16 dense, %s" % src
     achieved = conv_flops / conv_s / 1e12
     traffic = _conv_traffic(a.workload) if conv_dtype != pp.PP_F32 else None
+    neck_head = None
+    if conv_dtype != pp.PP_F32:
+        # pointwise GEMMs with K = 64..384: below the ridge point (FLOPs per HBM byte) of either
+        # dtype, so bound by HBM; the tensor-side figures are given beside it
+        nh = _time_neck_head(pp, torch, g, bb, conv_dtype, batch)
+        nh_s = sum(x[1] for x in nh)
+        nh_f, nh_b = sum(x[2] for x in nh), sum(x[3] for x in nh)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        neck_head = {"bound": "hbm", "achieved": nh_b / nh_s / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": nh_b / nh_s / 1e9 / hbm, "peak_source": "HBM copy, %s" % src,
+                     "ms_per_frame": nh_s * 1e3 / n_frames, "bytes_per_step": nh_b,
+                     "tflops": nh_f / nh_s / 1e12, "tensor_frac": nh_f / nh_s / 1e12 / peak,
+                     "launches": [{"kernel": k, "us": round(t * 1e6, 2), "tflops": round(f / t / 1e12, 1),
+                                   "gbs": round(b / t / 1e9)} for k, t, f, b in nh],
+                     "in_step": bool(a.head)}
     frames_done = a.steps * n_frames * world
     res = {
         "metric": "pillar frames/s", "value": frames_done / el, "unit": "frames/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOADS[a.workload], "frames_per_step": n_frames, "steps_in_flight": a.depth, "points_per_frame":
+        "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": n_frames, "steps_in_flight": a.depth, "points_per_frame":
                    [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
                          % (canvas_bytes // 2 ** 20)},
@@ -445,13 +540,15 @@ def _run_ours(a, rank, world, dist):
                      "layers_us": [round(t * 1e6, 2) for t, _ in layers],
                      "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
         "stage_ms_per_step": {k: v for k, v in stages.items() if not k.startswith("_")},
+        "neck_head": neck_head,
         "front_end_roofline": _front_end_roofline(g, stages, {pp.PP_BF16: 2, pp.PP_F32: 4, pp.PP_F32_TC: 8}[
             pp.PP_F32_TC if conv_dtype == pp.PP_F32_TC else prec], peaks),
         "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
                     "sched_us_per_decision": st["sched_us_per_decision"], "units": timed_units,
                     "frames_per_unit": a.steps * n_frames / max(1, timed_units)},
-        # per unit: 5 voxelisation kernels, PointNet, scatter, one per conv layer, result copy
-        "gpu_launches": timed_units * (5 + 1 + 1 + len(bb.layers(64)) + 1),
+        # per unit: 5 voxelisation kernels, PointNet, scatter, one per conv layer, (one per block
+        # and the head,) result copy
+        "gpu_launches": timed_units * (5 + 1 + 1 + len(bb.layers(64)) + (len(bb.convs) + 1 if a.head else 0) + 1),
         "clocks": clk,
         "num_pillars": num_p,
         "wall_s": wall,
@@ -534,19 +631,29 @@ def _serving_clouds(torch):
 def _run_reference(a):
     g, bb, prec, batch, cap, frames, w = _workload(a.workload)
     from oracle import pillars as O
+    head = None
+    if a.head:
+        from pp_synth import head_weights
+        head = head_weights(bb)
+
+    def one(pts):
+        r = O.frame(pts, g, bb, w)
+        if head is not None:
+            O.head(O.neck(r["blocks"], head[0], head[1]), head[2], head[3])
+
     for k in range(a.warmup):
-        O.frame(frames[k % len(frames)], g, bb, w)
+        one(frames[k % len(frames)])
     t0 = time.perf_counter()
     for k in range(a.steps):
         for j in range(batch):
-            O.frame(frames[(k * batch + j) % len(frames)], g, bb, w)
+            one(frames[(k * batch + j) % len(frames)])
     secs = time.perf_counter() - t0
     v = a.steps * batch / secs
     cores = os.cpu_count()
     return {"impl": "reference", "metric": "pillar frames/s", "value": v, "unit": "frames/s", "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": secs / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[a.workload], "frames_per_step": batch},
+            "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": batch},
             "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": "one full frame per step through the FP64 NumPy oracle (BLAS threads as "
                                        "installed, up to %d cores)" % cores},
@@ -556,8 +663,8 @@ def _run_reference(a):
 def main():
     a = _args()
     if a.cpu_worker:
-        name, n = a.cpu_worker.split(":")
-        print(_oracle_seconds(name, int(n)))
+        name, n, head = a.cpu_worker.split(":")
+        print(_oracle_seconds(name, int(n), head == "1"))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -600,7 +707,7 @@ def main():
         }
     if rank == 0:
         if not a.no_cpu_baseline:
-            res["cpu_baseline"] = _cpu_baseline(a.workload, 1)
+            res["cpu_baseline"] = _cpu_baseline(a.workload, 1, a.head)
         print(json.dumps(res))
     if dist is not None:
         dist.destroy_process_group()

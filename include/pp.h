@@ -337,6 +337,20 @@ typedef struct {
                                 /* unit then owns a workspace).  Within FP32 tolerance either  */
                                 /* way, but a frame's result is bit-identical across unit sizes */
                                 /* only without it (default 0)                                 */
+  /* Neck and detection head (head_outputs = 0: a unit ends at the backbone).  Block b's output
+   * is upsampled to block 0's size by a transposed conv of kernel = stride = s_b (block 0's
+   * height / block b's height, equal for the width) + BN + ReLU into up_channels channels at
+   * channel offset b * up_channels of the neck map, and the 1x1 head with bias maps that to
+   * head_outputs channels (pp_upsample / pp_head).  Tensor-core convs only (fp32_cuda_cores =
+   * 0).  Weights host float, copied by pp_create: up_w[b] [chans[b]][up_channels][s_b][s_b],
+   * up_bn[b] [4][up_channels], head_w [head_outputs][n_blocks * up_channels], head_b
+   * [head_outputs]. */
+  int32_t head_outputs;         /* 1..1024, or 0                                               */
+  int32_t up_channels;          /* multiple of 64 (default 128)                                */
+  const float* const* up_w;
+  const float* const* up_bn;
+  const float* head_w;
+  const float* head_b;
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
@@ -396,10 +410,15 @@ typedef struct {
   int32_t num_pillars;
   int32_t batch;                /* frames in the unit this frame ran in                       */
   int32_t level;                /* stream priority level it was released on (0 = highest)     */
-  const void* out_dev;          /* last backbone layer, padded NHWC [out_h+2][out_w+2][out_c] */
+  const void* out_dev;          /* last backbone layer (or the head), padded NHWC            */
+                                /* [out_h+2][out_w+2][out_c]                                  */
   int32_t out_c, out_h, out_w, out_dtype;
   const void* block_dev[PP_MAX_BLOCKS];  /* output of each block, same layout                 */
   int32_t block_c[PP_MAX_BLOCKS], block_h[PP_MAX_BLOCKS], block_w[PP_MAX_BLOCKS];
+  /* with a head (head_outputs > 0): out_dev is the head map [out_h+2][out_w+2][out_c] at block */
+  /* 0's size, out_c = head_outputs rounded up to 64 (channels past out_valid_c are 0), and the */
+  /* block outputs are not kept (block_dev NULL); without one out_valid_c = out_c.              */
+  int32_t out_valid_c;
 } pp_result;
 
 /* Drains up to `max` completed frames into out[]; waits up to timeout_us for the first one
@@ -470,7 +489,8 @@ int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** ou
 int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames,
                     const int32_t* counts, int32_t use_graph, void* stream);
 /* Device pointer to block `block`'s output for frame slot i (padded NHWC) and its shape; pass
- * block = -1 for the number of pillars (int32 device pointer, dims unset). */
+ * block = -1 for the number of pillars (int32 device pointer, dims unset), -2 for the head map
+ * and -3 for the neck map (with a head configured; for the split FP32 form the value plane). */
 int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** dev,
                        int32_t* c, int32_t* h, int32_t* w);
 size_t pp_pipeline_bytes(pp_pipeline* p);

@@ -73,6 +73,9 @@ class Config(ctypes.Structure):
         ("early_exit", ctypes.c_int32), ("num_streams", ctypes.c_int32),
         ("max_admitted", ctypes.c_int32), ("fp32_cuda_cores", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("stream_k", ctypes.c_int32),
+        ("head_outputs", ctypes.c_int32), ("up_channels", ctypes.c_int32),
+        ("up_w", ctypes.c_void_p), ("up_bn", ctypes.c_void_p),
+        ("head_w", ctypes.c_void_p), ("head_b", ctypes.c_void_p),
     ]
 
 
@@ -87,6 +90,7 @@ class Result(ctypes.Structure):
         ("out_w", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
         ("block_dev", ctypes.c_void_p * MAX_BLOCKS), ("block_c", ctypes.c_int32 * MAX_BLOCKS),
         ("block_h", ctypes.c_int32 * MAX_BLOCKS), ("block_w", ctypes.c_int32 * MAX_BLOCKS),
+        ("out_valid_c", ctypes.c_int32),
     ]
 
 
@@ -527,10 +531,11 @@ def device_error(clear: bool = True) -> int:
 
 # ------------------------------------------------------------------ runtime, pipeline, policy
 
-def make_config(geom, backbone, weights, **knobs):
+def make_config(geom, backbone, weights, head=None, **knobs):
     """Builds a pp_config (defaults from pp_config_defaults) for ``geom`` / ``backbone``
     (objects with the pp_synth Geometry/Backbone fields) and ``weights`` =
-    (pfn_w [64,9], pfn_bn [4,64], conv_w list, conv_bn list) as float32 arrays.  Returns the
+    (pfn_w [64,9], pfn_bn [4,64], conv_w list, conv_bn list) as float32 arrays; ``head`` =
+    (up_w list, up_bn list, head_w, head_b) adds the neck and the detection head.  Returns the
     config and the list of arrays it points into (keep it alive while the config is used)."""
     import numpy as np
     cfg = Config()
@@ -549,6 +554,18 @@ def make_config(geom, backbone, weights, **knobs):
     cfg.pfn_w, cfg.pfn_bn = keep[0].ctypes.data, keep[1].ctypes.data
     cfg.conv_w = ctypes.cast(arr_w, ctypes.c_void_p)
     cfg.conv_bn = ctypes.cast(arr_b, ctypes.c_void_p)
+    if head is not None:
+        up_w, up_bn, head_w, head_b = head
+        uw = [np.ascontiguousarray(w, dtype=np.float32) for w in up_w]
+        ub = [np.ascontiguousarray(b, dtype=np.float32) for b in up_bn]
+        hw, hb = np.ascontiguousarray(head_w, dtype=np.float32), np.ascontiguousarray(head_b, dtype=np.float32)
+        arr_uw = (ctypes.c_void_p * len(uw))(*[a.ctypes.data for a in uw])
+        arr_ub = (ctypes.c_void_p * len(ub))(*[a.ctypes.data for a in ub])
+        keep += uw + ub + [hw, hb, arr_uw, arr_ub]
+        cfg.head_outputs, cfg.up_channels = int(hw.shape[0]), int(uw[0].shape[1])
+        cfg.up_w = ctypes.cast(arr_uw, ctypes.c_void_p)
+        cfg.up_bn = ctypes.cast(arr_ub, ctypes.c_void_p)
+        cfg.head_w, cfg.head_b = hw.ctypes.data, hb.ctypes.data
     for k, v in knobs.items():
         if not hasattr(cfg, k):
             raise PPError(PP_EINVAL, "unknown config field %s" % k)

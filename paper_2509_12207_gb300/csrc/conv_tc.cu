@@ -1208,12 +1208,13 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
 
 // Persistent tile choice: fewest "waves" of tile work over the SMs, each tile costing its MMA
 // time plus a fixed per-tile overhead.
-int pick_tile_p(const ConvShape& c, const TileP* tiles, int n) {
+// co_blk: an N tile may not straddle a block of co_blk GEMM columns (transposed conv)
+int pick_tile_p(const ConvShape& c, const TileP* tiles, int n, int co_blk) {
   int best = -1;
   double best_cost = 1e30;
   for (int i = 0; i < n; ++i) {
     const TileP& t = tiles[i];
-    if (c.cout % t.bn) continue;
+    if (c.cout % t.bn || co_blk % t.bn) continue;
     const double tx = (c.Wo + t.bw - 1) / t.bw, ty = (c.Ho + t.bh - 1) / t.bh;
     const double total = tx * ty * c.batch * (c.cout / t.bn);
     const double per_sm = ceil(total / num_sms());
@@ -1241,7 +1242,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition
   const bool sk = mode == 1 && ptile >= n;
   if (sk) ptile -= n;
-  if (ptile < 0) ptile = pick_tile_p(c, tiles, n);
+  if (ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
   if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn)
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
   const TileP t = tiles[ptile];

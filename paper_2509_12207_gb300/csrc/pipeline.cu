@@ -122,13 +122,50 @@ int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
     conv_ss.push_back(ssd);
     if (st) return st;
   }
-  return PP_OK;
+  head_outputs = cfg->head_outputs;
+  if (head_outputs == 0) return PP_OK;
+  // neck + head
+  const int nb = (int)block_end.size();
+  if (head_outputs < 0 || head_outputs > 1024 || cfg->up_channels <= 0 || cfg->up_channels % 64 ||
+      cfg->up_channels > 1024)
+    return fail(PP_EINVAL, "config: head_outputs 0..1024, up_channels a multiple of 64 up to 1024");
+  if (conv_dtype == PP_F32) return fail(PP_EINVAL, "config: the neck and head need tensor-core convs");
+  if (!cfg->up_w || !cfg->up_bn || !cfg->head_w || !cfg->head_b) return fail(PP_EINVAL, "config: NULL head weights");
+  up_c = cfg->up_channels;
+  neck_c = nb * up_c;
+  head_c = (head_outputs + 63) / 64 * 64;
+  for (int b = 0; b < nb; ++b) {
+    const LayerSpec& L = layers[block_end[b]];
+    const int up = out_h() / L.Ho;
+    if (up < 1 || up > 8 || up * L.Ho != out_h() || up * L.Wo != out_w())
+      return fail(PP_EINVAL, "config: block %d (%d x %d) does not upsample to block 0 (%d x %d)", b, L.Ho, L.Wo,
+                  out_h(), out_w());
+    if (!cfg->up_w[b] || !cfg->up_bn[b]) return fail(PP_EINVAL, "config: NULL upsampling weights %d", b);
+    void* packed = nullptr;
+    float* ssd = nullptr;
+    st = dev_alloc(&packed, pp_upsample_packed_bytes(L.cout, up_c, up, conv_dtype));
+    if (!st) st = dev_alloc((void**)&ssd, 2 * up_c * sizeof(float));
+    if (!st) st = pp_upsample_pack_weights(cfg->up_w[b], L.cout, up_c, up, conv_dtype, packed);
+    if (!st) st = pp_bn_fold(cfg->up_bn[b], up_c, 1e-3f, ss);
+    if (!st) st = cuda_status(cudaMemcpy(ssd, ss, 2 * up_c * sizeof(float), cudaMemcpyHostToDevice), "upload up_ss");
+    up_stride.push_back(up);
+    up_w.push_back(packed);
+    up_ss.push_back(ssd);
+    if (st) return st;
+  }
+  if ((st = dev_alloc(&head_w, pp_head_packed_bytes(neck_c, head_outputs, conv_dtype)))) return st;
+  if ((st = dev_alloc((void**)&head_ss, 2 * head_c * sizeof(float)))) return st;
+  return pp_head_pack_weights(cfg->head_w, cfg->head_b, neck_c, head_outputs, conv_dtype, head_w, head_ss);
 }
 
 size_t Model::result_layout(std::vector<size_t>* block_off) const {
   const size_t elt = precision == PP_F32 ? 4 : 2;
   size_t off = 0;
   block_off->clear();
+  if (head_outputs > 0) {
+    block_off->push_back(0);
+    return align_up((size_t)(out_h() + 2) * (out_w() + 2) * head_c * elt, 256);
+  }
   for (int l : block_end) {
     const LayerSpec& L = layers[l];
     block_off->push_back(off);
@@ -142,9 +179,18 @@ void Model::release() {
   cudaFree(pfn_ss);
   for (void* p : conv_w) cudaFree(p);
   for (float* p : conv_ss) cudaFree(p);
+  for (void* p : up_w) cudaFree(p);
+  for (float* p : up_ss) cudaFree(p);
+  cudaFree(head_w);
+  cudaFree(head_ss);
   pfn_w = pfn_ss = nullptr;
+  head_w = nullptr;
+  head_ss = nullptr;
   conv_w.clear();
   conv_ss.clear();
+  up_w.clear();
+  up_ss.clear();
+  up_stride.clear();
 }
 
 int Pipeline::alloc(void** p, size_t n) {
@@ -190,6 +236,13 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
     act_.push_back(a);
     // borders stay zero forever: convs write interiors only
     if ((st = cuda_status(cudaMemsetAsync(a, 0, n, s), "clear activations"))) return st;
+  }
+  if (m->head_outputs > 0) {
+    const size_t px = planes * B_ * (m->out_h() + 2) * (m->out_w() + 2) * elt;
+    PP_ALLOC(neck_, px * m->neck_c);
+    PP_ALLOC(head_, px * m->head_c);
+    if ((st = cuda_status(cudaMemsetAsync(neck_, 0, px * m->neck_c, s), "clear neck"))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(head_, 0, px * m->head_c, s), "clear head"))) return st;
   }
   if (m->conv_dtype == PP_F32_TC && stream_k) {
     // one stream-K workspace, sized for the widest layer at the unit's capacity (a smaller
@@ -303,13 +356,47 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   }
   if (st) return st;
   ResultCopy rc{};
-  rc.nblocks = (int)m.block_end.size();
-  for (int b = 0; b < rc.nblocks; ++b) {
-    const int l = m.block_end[b];
-    const LayerSpec& L = m.layers[l];
-    rc.src[b] = static_cast<const char*>(act_[l]);
-    rc.bytes[b] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
-    rc.off[b] = res_off_[b];
+  if (m.head_outputs > 0) {
+    // neck: every block's output upsampled into its channel range of the neck map; then the head
+    const int H0 = m.out_h(), W0 = m.out_w();
+    const size_t px = (size_t)B_ * (H0 + 2) * (W0 + 2);
+    for (size_t b = 0; b < m.block_end.size() && !st; ++b) {
+      const LayerSpec& L = m.layers[m.block_end[b]];
+      const int up = m.up_stride[b];
+      ConvShape c{n, L.Ho, L.Wo, L.cout, up * up * m.up_c, 1, L.Ho, L.Wo};
+      c.in_plane = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout;
+      c.out_plane = px * m.neck_c;
+      GemmOpts o;
+      o.taps = 1;
+      o.up = up;
+      o.co_blk = m.up_c;
+      o.out_c = m.neck_c;
+      o.out_coff = (int)b * m.up_c;
+      st = gemm_tc_launch(m.conv_dtype, c, o, act_[m.block_end[b]], m.up_w[b], m.up_ss[b], neck_, -1, s);
+    }
+    if (!st) {
+      ConvShape c{n, H0, W0, m.neck_c, m.head_c, 1, H0, W0};
+      c.in_plane = px * m.neck_c;
+      c.out_plane = px * m.head_c;
+      GemmOpts o;
+      o.taps = 1;
+      o.relu = 0;
+      st = gemm_tc_launch(m.conv_dtype, c, o, neck_, m.head_w, m.head_ss, head_, -1, s);
+    }
+    if (st) return st;
+    rc.nblocks = 1;
+    rc.src[0] = static_cast<const char*>(head_);
+    rc.bytes[0] = (size_t)(H0 + 2) * (W0 + 2) * m.head_c * (m.precision == PP_F32 ? 4 : 2);
+    rc.off[0] = res_off_[0];
+  } else {
+    rc.nblocks = (int)m.block_end.size();
+    for (int b = 0; b < rc.nblocks; ++b) {
+      const int l = m.block_end[b];
+      const LayerSpec& L = m.layers[l];
+      rc.src[b] = static_cast<const char*>(act_[l]);
+      rc.bytes[b] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
+      rc.off[b] = res_off_[b];
+    }
   }
   result_copy<<<dim3(std::max(1, 8 * sms_ / n), n), 256, 0, s>>>(rc, tab_dev_);
   return cuda_status(cudaGetLastError(), "result copy");
@@ -355,6 +442,18 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
   if (st) return st;
   return cuda_status(cudaMemcpyAsync(num_host_, num_, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s),
                      "read back pillar counts");
+}
+
+const void* Pipeline::neck_out(int i) const {
+  if (!neck_) return nullptr;
+  return static_cast<const char*>(neck_) +
+         (size_t)i * (m_->out_h() + 2) * (m_->out_w() + 2) * m_->neck_c * (m_->precision == PP_F32 ? 4 : 2);
+}
+
+const void* Pipeline::head_out(int i) const {
+  if (!head_) return nullptr;
+  return static_cast<const char*>(head_) +
+         (size_t)i * (m_->out_h() + 2) * (m_->out_w() + 2) * m_->head_c * (m_->precision == PP_F32 ? 4 : 2);
 }
 
 const void* Pipeline::layer_out(int layer, int i) const {
@@ -412,6 +511,14 @@ int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** de
   if (!p || !dev || i < 0 || i >= p->pipe.max_batch()) return fail(PP_EINVAL, "pipeline_output: bad argument");
   if (block == -1) {
     *dev = p->pipe.num_pillars_dev() + i;
+    return PP_OK;
+  }
+  if (block == -2 || block == -3) {
+    if (p->model.head_outputs <= 0) return fail(PP_EINVAL, "pipeline_output: no neck or head configured");
+    *dev = block == -2 ? p->pipe.head_out(i) : p->pipe.neck_out(i);
+    if (c) *c = block == -2 ? p->model.head_c : p->model.neck_c;
+    if (h) *h = p->model.out_h();
+    if (w) *w = p->model.out_w();
     return PP_OK;
   }
   if (block < 0 || block >= (int)p->model.block_end.size()) return fail(PP_EINVAL, "pipeline_output: bad block");

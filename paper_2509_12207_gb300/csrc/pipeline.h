@@ -34,10 +34,23 @@ struct Model {
   float* pfn_ss = nullptr;       // [2][64]
   std::vector<void*> conv_w;     // packed per precision
   std::vector<float*> conv_ss;   // [2][cout]
+  // neck + head (head_outputs > 0): per block a transposed conv of kernel = stride =
+  // up_stride[b] into channels [b * up_c, (b + 1) * up_c) of the neck map, then the 1x1 head
+  int head_outputs = 0;
+  int head_c = 0;                // head_outputs rounded up to 64 (the GEMM's N)
+  int up_c = 0, neck_c = 0;      // channels per upsampled block, of the neck map
+  std::vector<int> up_stride;
+  std::vector<void*> up_w;       // packed for pp_upsample
+  std::vector<float*> up_ss;     // [2][up_c]
+  void* head_w = nullptr;        // packed for pp_head
+  float* head_ss = nullptr;      // [2][head_c]: 1 and the bias
   size_t bytes = 0;
   int upload(const pp_config* cfg, int precision, cudaStream_t s);
-  // Result slot layout: every block's padded NHWC output, each at a 256-byte aligned offset.
+  // Result slot layout: every block's padded NHWC output, each at a 256-byte aligned offset
+  // (with a head: the head map alone, one offset).
   size_t result_layout(std::vector<size_t>* block_off) const;
+  int out_h() const { return layers[block_end[0]].Ho; }  // neck / head map size (block 0's)
+  int out_w() const { return layers[block_end[0]].Wo; }
   void release();
 };
 
@@ -61,6 +74,9 @@ class Pipeline {
   int cap() const { return cap_; }
   // Output of layer `layer` (padded NHWC) for slot `i`.
   const void* layer_out(int layer, int i) const;
+  // Neck map / head map (padded NHWC, value plane) for slot `i`; NULL without a head.
+  const void* neck_out(int i) const;
+  const void* head_out(int i) const;
   const Model* model() const { return m_; }
   int* num_pillars_dev() const { return num_; }
   // pinned copy of num_pillars, written at the end of every run (valid once it completes)
@@ -87,6 +103,8 @@ class Pipeline {
   void* conv_ws_ = nullptr;  // stream-K workspace shared by the unit's (stream-ordered) convs
   size_t conv_ws_bytes_ = 0;
   std::vector<void*> act_;
+  void* neck_ = nullptr;     // [planes][B][H0+2][W0+2][neck_c]
+  void* head_ = nullptr;     // [planes][B][H0+2][W0+2][head_c]
   std::vector<cudaGraphExec_t> graphs_;
   std::vector<void*> allocs_;
   int alloc(void** p, size_t n);

@@ -202,14 +202,21 @@ void push_result(pp_ctx* c, Frame* f, int status, double t_done) {
     r.batch = u->nf;
     r.level = u->level;
     r.out_dtype = m->precision;
-    for (size_t b = 0; b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
+    if (m->head_outputs > 0) {
+      r.out_dev = base + pl.block_off[0];
+      r.out_c = m->head_c;
+      r.out_valid_c = m->head_outputs;
+      r.out_h = m->out_h();
+      r.out_w = m->out_w();
+    }
+    for (size_t b = 0; m->head_outputs == 0 && b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
       const LayerSpec& L = m->layers[m->block_end[b]];
       r.block_dev[b] = base + pl.block_off[b];
       r.block_c[b] = L.cout;
       r.block_h[b] = L.Ho;
       r.block_w[b] = L.Wo;
       r.out_dev = r.block_dev[b];
-      r.out_c = L.cout;
+      r.out_c = r.out_valid_c = L.cout;
       r.out_h = L.Ho;
       r.out_w = L.Wo;
     }
@@ -504,6 +511,8 @@ void pp_config_defaults(pp_config* cfg) {
   cfg->num_streams = 0;
   cfg->autotune = 1;
   cfg->stream_k = 0;
+  cfg->head_outputs = 0;
+  cfg->up_channels = 128;
 }
 
 int pp_create(const pp_config* cfg, pp_ctx** out) {

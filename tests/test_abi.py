@@ -136,3 +136,14 @@ def test_neck_head_host_validation(lib):
     assert lib.pp_head(1, 8, 8, 100, 72, pp.PP_BF16, p, p, p, p, -1, None) == pp.PP_EINVAL
     assert lib.pp_head(1, 8, 8, 384, 0, pp.PP_BF16, p, p, p, p, -1, None) == pp.PP_EINVAL
     assert lib.pp_head(1, 8, 8, 384, 72, pp.PP_BF16, None, p, p, p, -1, None) == pp.PP_EINVAL
+
+
+def test_config_head_defaults_and_layout(lib):
+    import ctypes
+    import paper_2509_12207_gb300 as pp
+    cfg = pp.Config()
+    lib.pp_config_defaults(ctypes.byref(cfg))
+    assert cfg.head_outputs == 0 and cfg.up_channels == 128 and not cfg.up_w and not cfg.head_w
+    # the Python mirrors end where the C structs do (fields appended last)
+    assert pp.Config.head_b.offset + ctypes.sizeof(ctypes.c_void_p) == ctypes.sizeof(pp.Config)
+    assert pp.Result.out_valid_c.offset + 4 <= ctypes.sizeof(pp.Result)

@@ -408,3 +408,87 @@ def test_runtime_pinned_host_points(small_clouds):
         assert rc == pp.PP_EINVAL and b"page-locked" in pp.lib().pp_last_error()
     finally:
         ctx.destroy()
+
+
+# ---- neck + detection head inside the release unit
+
+@pytest.fixture(scope="module")
+def full_head(full_frame):
+    """Neck/head weights for the full-size network and the oracle's neck and head maps of the
+    full-size frame."""
+    from pp_synth import head_weights
+    w, cloud, ref = full_frame
+    hw = head_weights(BACKBONE_FULL)
+    neck = O.neck(ref["blocks"], hw[0], hw[1])
+    return hw, neck, O.head(neck, hw[2], hw[3])
+
+
+def test_pipeline_neck_head_full_size_fp32(full_frame, full_head):
+    """The full-size FP32 unit with the neck and head (three transposed convs of strides 1, 2, 4
+    into one 384-channel map, then 72 outputs padded to 128): both maps match the oracle run
+    end to end from the points; the padding channels are zero."""
+    w, cloud, ref = full_frame
+    hw, neck_ref, head_ref = full_head
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, head=hw, max_batch=1, cap_points=120000)
+    p = pp.Pipeline(cfg, pp.PP_F32)
+    try:
+        p.run([torch.from_numpy(cloud).to(DEV)])
+        torch.cuda.synchronize()
+        neck = p.output_tensor(0, -3)
+        head = p.output_tensor(0, -2)
+        assert neck.shape == (250, 218, 384) and head.shape == (250, 218, 128)
+        assert rel_err(_interior(neck), neck_ref) <= FP32_TOL
+        h = _interior(head)
+        assert rel_err(h[..., :72], head_ref) <= FP32_TOL
+        assert not h[..., 72:].any()
+        for t in (neck, head):   # borders stay zero
+            assert not t[0].any() and not t[-1].any() and not t[:, 0].any() and not t[:, -1].any()
+    finally:
+        p.destroy()
+
+
+def test_pipeline_neck_head_bf16(full_frame, full_head):
+    """BF16 unit with the neck and head: each stage against the oracle applied to the unit's
+    own (BF16) input of that stage, weights unrounded; the head end to end within the BF16
+    tolerance of the FP64 oracle."""
+    w, cloud, ref = full_frame
+    hw, neck_ref, head_ref = full_head
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, head=hw, max_batch=2, cap_points=120000)
+    p = pp.Pipeline(cfg, pp.PP_BF16)
+    try:
+        p.run([torch.from_numpy(cloud).to(DEV)] * 2)
+        torch.cuda.synchronize()
+        blocks = [_interior(p.output_tensor(0, b)).astype(np.float64) for b in range(3)]
+        neck = _interior(p.output_tensor(0, -3)).astype(np.float64)
+        head = _interior(p.output_tensor(0, -2))
+        assert max_norm_err(neck, O.neck(blocks, hw[0], hw[1])) <= BF16_TOL
+        assert max_norm_err(head[..., :72], O.head(neck, hw[2], hw[3])) <= BF16_TOL
+        assert not head[..., 72:].any()
+        assert max_norm_err(head[..., :72], head_ref) <= BF16_TOL
+        assert torch.equal(p.output_tensor(0, -2), p.output_tensor(1, -2))
+    finally:
+        p.destroy()
+
+
+def test_runtime_serves_head_maps(full_frame, full_head):
+    """Through the serving runtime with a head: each result carries the head map (out_c 128,
+    out_valid_c 72, no block outputs), equal to the oracle's."""
+    w, cloud, ref = full_frame
+    hw, neck_ref, head_ref = full_head
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, head=hw, max_batch=2, cap_points=120000,
+                               precisions=1, units=1, th_urgent=-1.0)
+    ctx = pp.Context(cfg)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        rc, ids = ctx.submit_many([0, 0], [cloud, cloud])
+        assert rc == pp.PP_OK
+        res = _drain(ctx, 2)
+        for r in res:
+            assert (r.out_c, r.out_valid_c, r.out_h, r.out_w) == (128, 72, 248, 216)
+            assert not any(r.block_dev)
+            h = _interior(pp.result_tensor(r))
+            assert rel_err(h[..., :72], head_ref) <= FP32_TOL
+            assert not h[..., 72:].any()
+        ctx.release_many(ids)
+    finally:
+        ctx.destroy()
