@@ -55,7 +55,7 @@ def _args():
     ap.add_argument("--serve-sweep", default=None,
                     help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac]")
     ap.add_argument("--serve-modes", default="urgency,plain",
-                    help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf")
+                    help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf, saedf, eqdf")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -80,14 +80,19 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (383.2e6, "a9b88c7f4ca23619173f4f5bc5ea632f60493b6b07bca94687643e588cf867cc"),
-    "cfg3-bf16": (84.5e6, "a9b88c7f4ca23619173f4f5bc5ea632f60493b6b07bca94687643e588cf867cc"),
+    "cfg2-fp32": (382.3e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
+    "cfg3-bf16": (84.5e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
+}
+# the same for the neck and head launches of one step (upsamplings + head)
+NECK_HEAD_TRAFFIC = {
+    "cfg2-fp32": (250.6e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
+    "cfg3-bf16": (42.3e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
 }
 
 
-def _conv_traffic(workload):
+def _conv_traffic(workload, table=None):
     import hashlib
-    ent = CONV_TRAFFIC.get(workload)
+    ent = (CONV_TRAFFIC if table is None else table).get(workload)
     if ent is None:
         return None
     src = os.path.join(ROOT, "paper_2509_12207_gb300", "csrc", "conv_tc.cu")
@@ -514,6 +519,7 @@ def _run_ours(a, rank, world, dist):
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         neck_head = {"bound": "hbm", "achieved": nh_b / nh_s / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": nh_b / nh_s / 1e9 / hbm, "peak_source": "HBM copy, %s" % src,
+                     "traffic": _conv_traffic(a.workload, NECK_HEAD_TRAFFIC),
                      "ms_per_frame": nh_s * 1e3 / n_frames, "bytes_per_step": nh_b,
                      "tflops": nh_f / nh_s / 1e12, "tensor_frac": nh_f / nh_s / 1e12 / peak,
                      "launches": [{"kernel": k, "us": round(t * 1e6, 2), "tflops": round(f / t / 1e12, 1),
@@ -565,7 +571,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     delayed launch, overlapped batched sync) with continuous batching of up to 8 frames per
     graph launch; chains BF16 (``mixed``: odd chains BF16, even FP32).  mode "plain": every
     frame launched on arrival, kernel by kernel, FP32, on its chain's default-priority stream.
-    modes "edf" / "sjf" / "hrrn" / "lcuf": the urgency mode's units and sync, released in that
+    modes "edf" / "sjf" / "hrrn" / "lcuf" / "saedf" / "eqdf": the urgency mode's units and sync, released in that
     comparison order (no early exit, reservation or delaying).
     Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
     frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
@@ -575,7 +581,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     w = pillar_weights(bb, 7)
     chains = serving_chains(n_chains, mixed=mixed)
     others = {"edf": pp.PP_POLICY_EDF, "sjf": pp.PP_POLICY_SJF, "hrrn": pp.PP_POLICY_HRRN,
-              "lcuf": pp.PP_POLICY_LCUF}
+              "lcuf": pp.PP_POLICY_LCUF, "saedf": pp.PP_POLICY_SAEDF, "eqdf": pp.PP_POLICY_EQDF}
     if mode == "urgency":
         knobs = dict(policy=pp.PP_POLICY_URGENCY, max_batch=8, use_graphs=1, max_closed=2,
                      delta_eval_us=500.0, th_urgent=0.0, th_calib_frames=64, early_exit=1, units=8)

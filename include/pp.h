@@ -287,13 +287,16 @@ int pp_device_error(uint32_t* code, int32_t clear);
 /*   PP_POLICY_EDF   earliest absolute deadline first;                                        */
 /*   PP_POLICY_SJF   shortest remaining estimate (est_gpu + est_cpu) first;                   */
 /*   PP_POLICY_HRRN  highest response ratio (waiting + estimate) / estimate first;            */
-/*   PP_POLICY_LCUF  lowest chain utilisation (estimate / period) first.                      */
+/*   PP_POLICY_LCUF  lowest chain utilisation (estimate / period) first;                      */
+/*   PP_POLICY_SAEDF slack-aware EDF: frames that can still meet their deadline (slack >= 0)  */
+/*                   by earliest deadline, then the others by earliest deadline;             */
+/*   PP_POLICY_EQDF  earliest quasi-deadline (deadline - eqdf_lambda x estimate) first.       */
 /* Times are microseconds on the host monotonic clock (pp_now_us).                           */
 /* Threading: every entry point may be called from any thread; one internal dispatcher       */
 /* thread does the rest.                                                                     */
 
 enum { PP_POLICY_FIFO = 0, PP_POLICY_URGENCY = 1, PP_POLICY_EDF = 2, PP_POLICY_SJF = 3,
-       PP_POLICY_HRRN = 4, PP_POLICY_LCUF = 5 };
+       PP_POLICY_HRRN = 4, PP_POLICY_LCUF = 5, PP_POLICY_SAEDF = 6, PP_POLICY_EQDF = 7 };
 enum { PP_FRAME_DONE = 0, PP_FRAME_DROPPED = 1, PP_FRAME_ERROR = 2 };
 #define PP_MAX_BLOCKS 4
 #define PP_MAX_CHAINS 64
@@ -351,6 +354,7 @@ typedef struct {
   const float* const* up_bn;
   const float* head_w;
   const float* head_b;
+  double eqdf_lambda;           /* PP_POLICY_EQDF's estimate weight (default 0.5)              */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
@@ -514,6 +518,7 @@ typedef struct {
 typedef struct {
   int32_t policy, max_batch, max_closed, num_pri, early_exit;
   double th_urgent, util_exempt;
+  double eqdf_lambda;
 } pp_policy_config;
 enum { PP_DECIDE_NONE = 0, PP_DECIDE_RELEASE = 1, PP_DECIDE_WAIT = 2, PP_DECIDE_DELAY = 3 };
 typedef struct {
@@ -529,7 +534,8 @@ int pp_policy_decide(const pp_policy_config* cfg, double t_us, const pp_policy_f
 /* A frame's priority under cfg->policy at time t (higher = released first): URGENCY: UL = 1 /
  * slack (-inf for slack <= 0); EDF: -deadline; SJF: -(est_gpu + est_cpu); HRRN: (t - t_arr +
  * e) / e with e = est_gpu + est_cpu (+inf when e <= 0); LCUF: -(e / period) (-inf when the
- * period is not positive); FIFO: -t_arr.  Stream levels rank active units by this value. */
+ * period is not positive); SAEDF: -deadline, less 1e15 us when slack < 0; EQDF: -(deadline -
+ * eqdf_lambda * e); FIFO: -t_arr.  Stream levels rank active units by this value. */
 double pp_policy_priority(const pp_policy_config* cfg, double t_us, const pp_policy_frame* frame);
 
 #ifdef __cplusplus

@@ -29,7 +29,12 @@ replaces the urgency in ordering frames and ranking active units onto stream lev
 * EDF: earliest absolute deadline first (priority -deadline);
 * SJF: shortest remaining estimate e = est_gpu + est_cpu first (priority -e);
 * HRRN: highest response ratio (waited + e) / e first (+inf for e <= 0);
-* LCUF: lowest chain utilisation e / period first (priority -e / period; -inf without a period).
+* LCUF: lowest chain utilisation e / period first (priority -e / period; -inf without a period);
+* SAEDF (slack-aware EDF; reading): earliest deadline first among frames whose slack is still
+  >= 0, every frame with negative slack after them, again by deadline (priority -deadline, less
+  10^15 us for a negative slack);
+* EQDF (earliest quasi-deadline first; reading): priority -(deadline - lambda e), lambda =
+  ``eqdf_lambda`` (0 gives EDF; 1 orders by latest start time, like the urgency order).
 
 Readings where the paper is silent (also in the design notes): urgency order breaks ties by
 (chain id, arrival time, frame id); the FIFO baseline orders by (arrival, chain id, frame id);
@@ -51,6 +56,8 @@ POLICY_EDF = 2
 POLICY_SJF = 3
 POLICY_HRRN = 4
 POLICY_LCUF = 5
+POLICY_SAEDF = 6
+POLICY_EQDF = 7
 
 NONE, RELEASE, WAIT, DELAY = 0, 1, 2, 3
 
@@ -65,6 +72,7 @@ class PolicyConfig:
     util_exempt: float = 0.1
     early_exit: bool = True
     num_pri: int = 6
+    eqdf_lambda: float = 0.5        # EQDF: quasi-deadline = deadline - lambda x estimate
 
 
 @dataclasses.dataclass
@@ -151,6 +159,12 @@ def priority(f: Ready, t: float, cfg: PolicyConfig) -> float:
         return (t - f.t_arr + e) / e if e > 0 else math.inf
     if cfg.policy == POLICY_LCUF:
         return -(e / f.period) if f.period > 0 else -math.inf
+    if cfg.policy == POLICY_SAEDF:
+        # earliest deadline among frames that can still meet theirs, then the rest: the
+        # second group is pushed back by a constant far larger than any deadline
+        return -f.deadline - (1e15 if slack(f, t) < 0 else 0.0)
+    if cfg.policy == POLICY_EQDF:
+        return -(f.deadline - cfg.eqdf_lambda * e)
     return -f.t_arr
 
 

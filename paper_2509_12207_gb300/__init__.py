@@ -40,6 +40,7 @@ class Geometry(ctypes.Structure):
 MAX_BLOCKS = 4
 MAX_CHAINS = 64
 PP_POLICY_FIFO, PP_POLICY_URGENCY, PP_POLICY_EDF, PP_POLICY_SJF, PP_POLICY_HRRN, PP_POLICY_LCUF = 0, 1, 2, 3, 4, 5
+PP_POLICY_SAEDF, PP_POLICY_EQDF = 6, 7
 PP_FRAME_DONE, PP_FRAME_DROPPED, PP_FRAME_ERROR = 0, 1, 2
 PP_POINTS_HOST, PP_POINTS_DEVICE, PP_POINTS_PINNED = 0, 1, 2
 
@@ -76,6 +77,7 @@ class Config(ctypes.Structure):
         ("head_outputs", ctypes.c_int32), ("up_channels", ctypes.c_int32),
         ("up_w", ctypes.c_void_p), ("up_bn", ctypes.c_void_p),
         ("head_w", ctypes.c_void_p), ("head_b", ctypes.c_void_p),
+        ("eqdf_lambda", ctypes.c_double),
     ]
 
 
@@ -142,7 +144,8 @@ class PolicyActive(ctypes.Structure):
 class PolicyConfig(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_closed", ctypes.c_int32),
                 ("num_pri", ctypes.c_int32), ("early_exit", ctypes.c_int32),
-                ("th_urgent", ctypes.c_double), ("util_exempt", ctypes.c_double)]
+                ("th_urgent", ctypes.c_double), ("util_exempt", ctypes.c_double),
+                ("eqdf_lambda", ctypes.c_double)]
 
 
 class PolicyDecision(ctypes.Structure):

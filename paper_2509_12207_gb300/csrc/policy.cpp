@@ -9,9 +9,9 @@
 // urgent, unless the head's utilisation is below the exemption threshold.  Stream binding with
 // reservation (Section 4.4.3): level 0 for UL > TH_urgent; otherwise the urgency rank among the
 // non-urgent active units, normalised onto levels 1..NUM_PRI-1.  Frames of the head's precision
-// fill the unit up to max_batch, in order.  The comparison policies (EDF, SJF, HRRN, LCUF) only
-// change the priority that orders frames and ranks active units (levels 0..NUM_PRI-1, no
-// reservation, no delaying, no early exit).
+// fill the unit up to max_batch, in order.  The comparison policies (EDF, SJF, HRRN, LCUF,
+// SAEDF, EQDF) only change the priority that orders frames and ranks active units (levels
+// 0..NUM_PRI-1, no reservation, no delaying, no early exit).
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -36,6 +36,9 @@ double prio_of(const pp_policy_config& c, const pp_policy_frame& f, double t) {
     case PP_POLICY_SJF: return -e;
     case PP_POLICY_HRRN: return e > 0 ? (t - f.t_arr_us + e) / e : inf;
     case PP_POLICY_LCUF: return f.period_us > 0 ? -(e / f.period_us) : -inf;
+    // frames that can no longer make their deadline sort after every frame that can
+    case PP_POLICY_SAEDF: return -f.deadline_us - (slack_of(f, t) < 0 ? 1e15 : 0.0);
+    case PP_POLICY_EQDF: return -(f.deadline_us - c.eqdf_lambda * e);
     default: return -f.t_arr_us;
   }
 }
@@ -52,7 +55,7 @@ extern "C" int pp_policy_decide(const pp_policy_config* cfg, double t, const pp_
                                 int32_t closed_pending, pp_policy_decision* out, uint64_t* drops,
                                 int32_t drops_cap) {
   if (!cfg || !out || n_ready < 0 || n_active < 0 || (n_ready && !ready) || (n_active && !active) ||
-      cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_LCUF)
+      cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_EQDF)
     return PP_EINVAL;
   const pp_policy_config& c = *cfg;
   out->kind = PP_DECIDE_NONE;

@@ -296,6 +296,7 @@ pp_policy_config policy_cfg(pp_ctx* c) {
   p.early_exit = c->cfg.early_exit;
   p.th_urgent = c->th;
   p.util_exempt = c->cfg.util_exempt;
+  p.eqdf_lambda = c->cfg.eqdf_lambda;
   return p;
 }
 
@@ -513,6 +514,7 @@ void pp_config_defaults(pp_config* cfg) {
   cfg->stream_k = 0;
   cfg->head_outputs = 0;
   cfg->up_channels = 128;
+  cfg->eqdf_lambda = 0.5;
 }
 
 int pp_create(const pp_config* cfg, pp_ctx** out) {
@@ -520,7 +522,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (cfg->max_batch < 1 || cfg->max_batch > 8) return fail(PP_EINVAL, "create: max_batch must be 1..8");
   if (cfg->cap_points < 1 || cfg->cap_points > (1 << 24)) return fail(PP_EINVAL, "create: cap_points 1..2^24");
   if ((cfg->precisions & 3) == 0) return fail(PP_EINVAL, "create: no precision enabled");
-  if (cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_LCUF) return fail(PP_EINVAL, "create: bad policy");
+  if (cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_EQDF) return fail(PP_EINVAL, "create: bad policy");
+  if (!std::isfinite(cfg->eqdf_lambda)) return fail(PP_EINVAL, "create: eqdf_lambda must be finite");
   if (cfg->units < 0 || cfg->units > 64 || cfg->max_closed < 0 || !(cfg->delta_eval_us >= 0) ||
       cfg->max_admitted < 0 ||
       !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0)

@@ -144,6 +144,7 @@ def test_config_head_defaults_and_layout(lib):
     cfg = pp.Config()
     lib.pp_config_defaults(ctypes.byref(cfg))
     assert cfg.head_outputs == 0 and cfg.up_channels == 128 and not cfg.up_w and not cfg.head_w
+    assert cfg.eqdf_lambda == 0.5
     # the Python mirrors end where the C structs do (fields appended last)
-    assert pp.Config.head_b.offset + ctypes.sizeof(ctypes.c_void_p) == ctypes.sizeof(pp.Config)
+    assert pp.Config.eqdf_lambda.offset + 8 == ctypes.sizeof(pp.Config)
     assert pp.Result.out_valid_c.offset + 4 <= ctypes.sizeof(pp.Result)

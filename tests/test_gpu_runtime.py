@@ -309,7 +309,8 @@ def test_runtime_submit_many_partial_admission():
         ctx.destroy()
 
 
-@pytest.mark.parametrize("policy", [pp.PP_POLICY_EDF, pp.PP_POLICY_SJF, pp.PP_POLICY_HRRN, pp.PP_POLICY_LCUF])
+@pytest.mark.parametrize("policy", [pp.PP_POLICY_EDF, pp.PP_POLICY_SJF, pp.PP_POLICY_HRRN, pp.PP_POLICY_LCUF,
+                                    pp.PP_POLICY_SAEDF, pp.PP_POLICY_EQDF])
 def test_runtime_comparison_policies(policy, small_clouds):
     """The comparison release orders serve every frame, with results identical to the oracle's
     pillars and within tolerance."""

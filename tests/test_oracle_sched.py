@@ -258,6 +258,26 @@ def test_comparison_policies_hand_example():
     assert got[S.POLICY_LCUF] == [3, 2, 1]       # 0.000125 < 0.0005 < 0.008
 
 
+def test_saedf_eqdf_hand_example():
+    """Three frames at t = 1000 us that separate EDF, slack-aware EDF and EQDF:
+         frame  deadline  estimate  slack = d - e - t   quasi-deadline d - lambda e (0.5 / 1)
+         X      3000      100       1900                2950 / 2900
+         Y      3400      1000      1400                2900 / 2400
+         Z      1500      800       -300                1100 / 700
+    EDF: Z, X, Y.  SAEDF: X, Y (slack >= 0, by deadline), then Z.  EQDF lambda 0.5 and 1: Z, Y,
+    X; lambda 0 is EDF.  The urgency policy drops Z (negative slack) and releases Y, X."""
+    t = 1000.0
+    ready = [S.Ready(1, 0, 500.0, 3000.0, 100.0), S.Ready(2, 1, 400.0, 3400.0, 1000.0),
+             S.Ready(3, 2, 300.0, 1500.0, 800.0)]
+    cases = [(S.POLICY_EDF, 0.5, [3, 1, 2]), (S.POLICY_SAEDF, 0.5, [1, 2, 3]), (S.POLICY_EQDF, 0.5, [3, 2, 1]),
+             (S.POLICY_EQDF, 1.0, [3, 2, 1]), (S.POLICY_EQDF, 0.0, [3, 1, 2])]
+    for pol, lam, order in cases:
+        d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0, eqdf_lambda=lam))
+        assert d.kind == S.RELEASE and d.frames == order and d.drops == [], (pol, lam)
+    d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=S.POLICY_URGENCY, max_closed=0))
+    assert d.frames == [2, 1] and d.drops == [3]
+
+
 def test_comparison_policies_match_sorting():
     """On random ready sets the head each comparison policy releases is the textbook optimum:
     min deadline, min estimate, max response ratio, min utilisation (ties: chain, arrival, id)."""
@@ -273,8 +293,10 @@ def test_comparison_policies_match_sorting():
         keys = {S.POLICY_EDF: lambda f: (f.deadline,) + tie(f),
                 S.POLICY_SJF: lambda f: (f.est_gpu + f.est_cpu,) + tie(f),
                 S.POLICY_HRRN: lambda f: (-(t - f.t_arr + f.est_gpu + f.est_cpu) / (f.est_gpu + f.est_cpu),) + tie(f),
-                S.POLICY_LCUF: lambda f: ((f.est_gpu + f.est_cpu) / f.period,) + tie(f)}
+                S.POLICY_LCUF: lambda f: ((f.est_gpu + f.est_cpu) / f.period,) + tie(f),
+                S.POLICY_SAEDF: lambda f: (f.deadline - f.est_gpu - f.est_cpu - t < 0, f.deadline) + tie(f),
+                S.POLICY_EQDF: lambda f: (f.deadline - 0.5 * (f.est_gpu + f.est_cpu),) + tie(f)}
         for pol, key in keys.items():
-            d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0, max_batch=8))
+            d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0, max_batch=8, eqdf_lambda=0.5))
             assert d.frames[0] == min(ready, key=key).frame_id, pol
             assert d.drops == []                  # no early exit outside the urgency policy

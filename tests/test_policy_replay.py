@@ -31,17 +31,19 @@ def _random_state(rng):
                           period_us=float(rng.choice([0.0, 50000.0, 100000.0, 200000.0]))))
     active = [(int(rng.integers(0, 6)), float(rng.choice([-np.inf, 1e-5, 1e-4, 5e-4, 2e-3, 1e-2])))
               for _ in range(int(rng.integers(0, 6)))]
-    cfg = dict(policy=int(rng.integers(0, 6)), max_batch=int(rng.integers(1, 9)),
+    cfg = dict(policy=int(rng.integers(0, 8)), max_batch=int(rng.integers(1, 9)),
                max_closed=int(rng.integers(0, 3)), num_pri=int(rng.integers(1, 7)),
                early_exit=int(rng.integers(0, 2)),
-               th_urgent=float(rng.choice([0.0, -1.0, 1e-4, 1e-3])), util_exempt=0.1)
+               th_urgent=float(rng.choice([0.0, -1.0, 1e-4, 1e-3])), util_exempt=0.1,
+               eqdf_lambda=float(rng.choice([0.0, 0.5, 1.0, 2.0])))
     return t, ready, active, int(rng.integers(0, 4)), cfg
 
 
 def _oracle(t, ready, active, closed, cfg):
     oc = S.PolicyConfig(policy=cfg["policy"], max_batch=cfg["max_batch"], max_closed=cfg["max_closed"],
                         th_urgent=cfg["th_urgent"], util_exempt=cfg["util_exempt"],
-                        early_exit=bool(cfg["early_exit"]), num_pri=cfg["num_pri"])
+                        early_exit=bool(cfg["early_exit"]), num_pri=cfg["num_pri"],
+                        eqdf_lambda=cfg["eqdf_lambda"])
     rr = [S.Ready(r["frame_id"], r["chain_id"], r["t_arr_us"], r["deadline_us"], r["est_gpu_us"],
                   r["est_cpu_us"], r["precision"], r["util"], r["period_us"]) for r in ready]
     aa = [S.Active(c, u) for c, u in active]
@@ -115,11 +117,12 @@ def test_replay_priorities(pp):
             got = pp.policy_priority(cfg, t, r)
             f = S.Ready(r["frame_id"], r["chain_id"], r["t_arr_us"], r["deadline_us"], r["est_gpu_us"],
                         r["est_cpu_us"], r["precision"], r["util"], r["period_us"])
-            want = S.priority(f, t, S.PolicyConfig(policy=cfg["policy"]))
+            want = S.priority(f, t, S.PolicyConfig(policy=cfg["policy"], eqdf_lambda=cfg["eqdf_lambda"]))
             assert got == want or (np.isnan(got) and np.isnan(want)), (cfg["policy"], r, got, want)
 
 
-@pytest.mark.parametrize("policy", [S.POLICY_EDF, S.POLICY_SJF, S.POLICY_HRRN, S.POLICY_LCUF])
+@pytest.mark.parametrize("policy", [S.POLICY_EDF, S.POLICY_SJF, S.POLICY_HRRN, S.POLICY_LCUF,
+                                    S.POLICY_SAEDF, S.POLICY_EQDF])
 def test_replay_des_trace_other_policies(pp, policy):
     """The comparison policies through a whole simulated run: every decision the DES takes is
     the library's decision on the same state."""
@@ -144,7 +147,8 @@ def test_replay_des_trace_other_policies(pp, policy):
     finally:
         S.decide = orig
     assert len(calls) > 200
-    pc = dict(policy=policy, max_batch=4, max_closed=2, num_pri=6, early_exit=1, th_urgent=0.0, util_exempt=0.1)
+    pc = dict(policy=policy, max_batch=4, max_closed=2, num_pri=6, early_exit=1, th_urgent=0.0, util_exempt=0.1,
+              eqdf_lambda=cfg.eqdf_lambda)
     for t, ready, active, closed, d in calls:
         rd = [dict(frame_id=f.frame_id, chain_id=f.chain_id, precision=f.precision, t_arr_us=f.t_arr,
                    deadline_us=f.deadline, est_gpu_us=f.est_gpu, est_cpu_us=f.est_cpu, util=f.util,
