@@ -53,7 +53,7 @@ def _args():
                     help="conv tile table: loaded (no autotuning) if the file exists, else written after "
                          "autotuning, so that a profiled run launches the same tiles as a plain one")
     ap.add_argument("--serve-sweep", default=None,
-                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac]")
+                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac][:noise]")
     ap.add_argument("--serve-modes", default="urgency,plain",
                     help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf, saedf, eqdf")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
@@ -564,7 +564,7 @@ def _run_ours(a, rank, world, dist):
 
 # ------------------------------------------------------------------ serving (chains with deadlines)
 
-def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0):
+def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0, noise=0.0):
     """Replays periodic chains in real time against one context and returns its statistics.
 
     mode "urgency": the paper's release rules (urgency order, early exit, stream binding,
@@ -575,7 +575,9 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     comparison order (no early exit, reservation or delaying).
     Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
     frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
-    f_a and f_d).  A frame the budget cannot admit counts as a miss."""
+    f_a and f_d); ``noise``: every frame's estimate, as the policy sees it, scaled by a factor
+    drawn from 1 + U[-noise, noise) (the paper's estimation-error study).  A frame the budget
+    cannot admit counts as a miss."""
     from pp_synth import BACKBONE_SMALL, GEOM_SMALL, arrival_times, pillar_weights, serving_chains
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     w = pillar_weights(bb, 7)
@@ -597,7 +599,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
                      th_urgent=-1.0, units=16)
         prec = [pp.PP_F32] * n_chains
     need = (1 if pp.PP_F32 in prec else 0) | (2 if pp.PP_BF16 in prec else 0)
-    cfg, keep = pp.make_config(g, bb, w, cap_points=150000, precisions=need, **knobs)
+    cfg, keep = pp.make_config(g, bb, w, cap_points=150000, precisions=need, est_noise=noise,
+                               noise_seed=seed, **knobs)
     ctx = pp.Context(cfg)
     try:
         for c, p in zip(chains, prec):
@@ -619,6 +622,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             per[c.chain_id] = (m, n)
     miss = sum(m / n for m, n in per.values()) / max(1, len(per))
     return {"mode": mode, "chains": n_chains, "rate": rate, "deadline_factor": dfac, "mixed": mixed,
+            "est_noise": noise,
             "frames": len(ev),
             "done": st["done"], "dropped": st["dropped"], "rejected": sum(rejected.values()),
             "miss_ratio": miss, "lat_p50_ms": st["lat_p50_us"] / 1e3, "lat_p99_ms": st["lat_p99_us"] / 1e3,
@@ -689,8 +693,9 @@ def main():
             n, rate, secs = int(parts[0]), float(parts[1]), float(parts[2])
             mixed = len(parts) > 3 and parts[3] == "mixed"
             dfac = float(parts[4]) if len(parts) > 4 else 1.0
+            noise = float(parts[5]) if len(parts) > 5 else 0.0
             for mode in a.serve_modes.split(","):
-                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac))
+                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac, noise=noise))
                 print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"metric": "deadline-miss ratio and p99 chain latency, urgency-served batched "
                           "vs plain per-frame launches", "serving": out}))

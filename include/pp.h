@@ -355,6 +355,11 @@ typedef struct {
   const float* head_w;
   const float* head_b;
   double eqdf_lambda;           /* PP_POLICY_EQDF's estimate weight (default 0.5)              */
+  /* Estimate-noise experiment (the paper's study of urgency estimation error): every frame's   */
+  /* GPU-time estimate, as the release policy sees it, is scaled by pp_noise_factor(noise_seed, */
+  /* frame id, est_noise), drawn once per frame.  0 = off (default).                           */
+  double est_noise;             /* half-width eps of the uniform factor 1 + U[-eps, eps), < 1 */
+  uint64_t noise_seed;
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
@@ -458,6 +463,15 @@ int pp_get_stats(pp_ctx* ctx, pp_stats* out);
 int pp_destroy(pp_ctx* ctx);
 /* Host monotonic clock in microseconds. */
 double pp_now_us(void);
+/* sizeof of a public struct, by its type name ("pp_config", "pp_result", "pp_stats",
+ * "pp_geometry", "pp_arrival", "pp_replay_stats", "pp_policy_frame", "pp_policy_active",
+ * "pp_policy_config", "pp_policy_decision"); 0 for any other name.  Lets a binding check its
+ * struct mirrors against this build. */
+size_t pp_struct_size(const char* type_name);
+/* The estimate-noise factor of frame `frame_id`: 1 + eps (2u - 1) with u = the frame_id-th
+ * output of a SplitMix64 generator seeded with `seed` (Steele, Lea and Flood, OOPSLA 2014),
+ * top 53 bits scaled to [0, 1). */
+double pp_noise_factor(uint64_t seed, uint64_t frame_id, double eps);
 
 /* Real-time trace replay (a load generator for serving measurements; the paper has no
  * counterpart).  Frame k arrives start + arrivals[k].t_us after the call begins (arrivals

@@ -78,6 +78,7 @@ class Config(ctypes.Structure):
         ("up_w", ctypes.c_void_p), ("up_bn", ctypes.c_void_p),
         ("head_w", ctypes.c_void_p), ("head_b", ctypes.c_void_p),
         ("eqdf_lambda", ctypes.c_double),
+        ("est_noise", ctypes.c_double), ("noise_seed", ctypes.c_uint64),
     ]
 
 
@@ -209,6 +210,8 @@ _SIGS = {
     "pp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "pp_destroy": (ctypes.c_int, [_P]),
     "pp_now_us": (ctypes.c_double, []),
+    "pp_struct_size": (_SZ, [ctypes.c_char_p]),
+    "pp_noise_factor": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double]),
     "pp_pipeline_create": (ctypes.c_int, [ctypes.POINTER(Config), _I, ctypes.POINTER(ctypes.c_void_p)]),
     "pp_pipeline_run": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int32),
                                        _I, _P]),
@@ -679,6 +682,11 @@ class Context:
 
 def now_us() -> float:
     return float(lib().pp_now_us())
+
+
+def noise_factor(seed, frame_id, eps) -> float:
+    """pp_noise_factor: the estimate-noise factor the runtime gives frame ``frame_id``."""
+    return float(lib().pp_noise_factor(seed, frame_id, eps))
 
 
 def result_tensor(r, block=None):

@@ -78,6 +78,7 @@ struct Frame {
   int unit = -1, slot = -1;
   bool dropped = false, done = false, polled = false;
   double delay_start = -1;
+  double est_scale = 1.0;      // estimate-noise factor (1 unless the experiment is on)
 };
 
 struct Unit {
@@ -309,7 +310,7 @@ pp_policy_frame policy_frame(pp_ctx* c, const Frame* f) {
   p.precision = f->precision;
   p.t_arr_us = f->t_arr;
   p.deadline_us = f->deadline;
-  p.est_gpu_us = unit_est(c, f->precision, 1);
+  p.est_gpu_us = unit_est(c, f->precision, 1) * f->est_scale;
   p.est_cpu_us = 0.0;
   p.util = 1.0;
   p.period_us = c->chains[f->chain].period_ms * 1000.0;
@@ -389,7 +390,7 @@ void calibrate(pp_ctx* c, double t) {
   if (!c->calibrating) return;
   double mx = -INFINITY;
   for (Frame* f : c->ready) {
-    const double s = f->deadline - unit_est(c, f->precision, 1) - t;
+    const double s = f->deadline - unit_est(c, f->precision, 1) * f->est_scale - t;
     if (s > 0) mx = std::max(mx, 1.0 / s);
   }
   for (Unit* u : c->units)
@@ -492,6 +493,35 @@ extern "C" {
 
 double pp_now_us(void) { return now_us(); }
 
+size_t pp_struct_size(const char* name) {
+  if (!name) return 0;
+  static const struct {
+    const char* n;
+    size_t s;
+  } kSizes[] = {{"pp_config", sizeof(pp_config)},
+                {"pp_result", sizeof(pp_result)},
+                {"pp_stats", sizeof(pp_stats)},
+                {"pp_geometry", sizeof(pp_geometry)},
+                {"pp_arrival", sizeof(pp_arrival)},
+                {"pp_replay_stats", sizeof(pp_replay_stats)},
+                {"pp_policy_frame", sizeof(pp_policy_frame)},
+                {"pp_policy_active", sizeof(pp_policy_active)},
+                {"pp_policy_config", sizeof(pp_policy_config)},
+                {"pp_policy_decision", sizeof(pp_policy_decision)}};
+  for (const auto& e : kSizes)
+    if (strcmp(e.n, name) == 0) return e.s;
+  return 0;
+}
+
+double pp_noise_factor(uint64_t seed, uint64_t frame_id, double eps) {
+  uint64_t z = seed + frame_id * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  return 1.0 + eps * (2.0 * u - 1.0);
+}
+
 void pp_config_defaults(pp_config* cfg) {
   if (!cfg) return;
   memset(cfg, 0, sizeof(*cfg));
@@ -524,6 +554,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if ((cfg->precisions & 3) == 0) return fail(PP_EINVAL, "create: no precision enabled");
   if (cfg->policy < PP_POLICY_FIFO || cfg->policy > PP_POLICY_EQDF) return fail(PP_EINVAL, "create: bad policy");
   if (!std::isfinite(cfg->eqdf_lambda)) return fail(PP_EINVAL, "create: eqdf_lambda must be finite");
+  if (!(cfg->est_noise >= 0 && cfg->est_noise < 1)) return fail(PP_EINVAL, "create: est_noise must be in [0, 1)");
   if (cfg->units < 0 || cfg->units > 64 || cfg->max_closed < 0 || !(cfg->delta_eval_us >= 0) ||
       cfg->max_admitted < 0 ||
       !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0)
@@ -717,6 +748,7 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
       break;
     }
     f->id = c->next_id++;
+    if (c->cfg.est_noise > 0) f->est_scale = pp_noise_factor(c->cfg.noise_seed, f->id, c->cfg.est_noise);
     f->chain = chain_ids[k];
     f->precision = p;
     f->t_arr = t_arrival_us;

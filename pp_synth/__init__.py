@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "Geometry", "Backbone", "GEOM_SMALL", "GEOM_FULL", "BACKBONE_SMALL", "BACKBONE_FULL",
     "frame_seed", "uniform_cloud", "clustered_cloud", "config_points", "batched_counts",
-    "pillar_weights", "ChainSpec", "serving_chains", "arrival_times",
+    "pillar_weights", "ChainSpec", "serving_chains", "arrival_times", "splitmix64", "noise_factors",
 ]
 
 
@@ -218,3 +218,23 @@ def arrival_times(chains: Sequence[ChainSpec], duration_ms: float, rate: float =
             t += per
     ev.sort()
     return ev
+
+
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """The k-th output (k >= 1) of a SplitMix64 generator seeded with ``seed`` (Steele, Lea and
+    Flood, OOPSLA 2014): the state advances by 0x9E3779B97F4A7C15 per output and each output is
+    the state after two xor-shift-multiply rounds and a final xor-shift."""
+    z = (seed + k * 0x9E3779B97F4A7C15) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def noise_factors(seed: int, ids: Sequence[int], eps: float) -> np.ndarray:
+    """Estimate-noise factors 1 + eps (2u - 1), u = the top 53 bits of splitmix64(seed, id)
+    scaled to [0, 1): one per frame id (the estimate-error experiment's per-instance draw)."""
+    u = np.array([(splitmix64(seed, int(i)) >> 11) * 2.0 ** -53 for i in ids])
+    return 1.0 + eps * (2.0 * u - 1.0)

@@ -144,7 +144,31 @@ def test_config_head_defaults_and_layout(lib):
     cfg = pp.Config()
     lib.pp_config_defaults(ctypes.byref(cfg))
     assert cfg.head_outputs == 0 and cfg.up_channels == 128 and not cfg.up_w and not cfg.head_w
-    assert cfg.eqdf_lambda == 0.5
-    # the Python mirrors end where the C structs do (fields appended last)
-    assert pp.Config.eqdf_lambda.offset + 8 == ctypes.sizeof(pp.Config)
-    assert pp.Result.out_valid_c.offset + 4 <= ctypes.sizeof(pp.Result)
+    assert cfg.eqdf_lambda == 0.5 and cfg.est_noise == 0.0
+    # every Python struct mirror has the size of the C struct of this build
+    mirrors = {"pp_config": pp.Config, "pp_result": pp.Result, "pp_stats": pp.Stats, "pp_geometry": pp.Geometry,
+               "pp_arrival": pp.Arrival, "pp_replay_stats": pp.ReplayStats, "pp_policy_frame": pp.PolicyFrame,
+               "pp_policy_active": pp.PolicyActive, "pp_policy_config": pp.PolicyConfig,
+               "pp_policy_decision": pp.PolicyDecision}
+    for name, cls in mirrors.items():
+        assert lib.pp_struct_size(name.encode()) == ctypes.sizeof(cls), name
+    assert lib.pp_struct_size(b"pp_nothing") == 0
+
+
+def test_noise_factor_matches_splitmix64(lib):
+    """The runtime's per-frame estimate-noise factor is the published SplitMix64 sequence
+    (first outputs for seed 0 are the reference values of the generator's C source)."""
+    import paper_2509_12207_gb300 as pp
+    from pp_synth import noise_factors, splitmix64
+    assert splitmix64(0, 1) == 0xE220A8397B1DCDAF
+    assert splitmix64(0, 2) == 0x6E789E6AA1B965F4
+    assert splitmix64(0, 3) == 0x06C45D188009454F
+    ids = [1, 2, 3, 17, 1000, 123456789]
+    for seed in (0, 7, 2 ** 63 + 5):
+        want = noise_factors(seed, ids, 0.3)
+        got = [pp.noise_factor(seed, i, 0.3) for i in ids]
+        assert got == list(want)
+        assert all(0.7 <= g < 1.3 for g in got)
+    assert pp.noise_factor(5, 9, 0.0) == 1.0
+    f = noise_factors(11, range(1, 20001), 0.3)
+    assert abs(f.mean() - 1.0) < 0.01 and f.min() >= 0.7 and f.max() < 1.3

@@ -300,3 +300,29 @@ def test_comparison_policies_match_sorting():
             d = S.decide(t, ready, [], 0, S.PolicyConfig(policy=pol, max_closed=0, max_batch=8, eqdf_lambda=0.5))
             assert d.frames[0] == min(ready, key=key).frame_id, pol
             assert d.drops == []                  # no early exit outside the urgency policy
+
+
+def test_des_estimate_noise_only_moves_decisions():
+    """Estimate noise changes what the policy sees, not the work: with eps = 0 the run is
+    identical to the noiseless one; with eps = 0.3 every frame still completes or is dropped,
+    and the release trace differs."""
+    from pp_synth import noise_factors
+    import numpy as np
+    rng = np.random.default_rng(8)
+    base = []
+    for i in range(400):
+        t = float(i * 40 + rng.integers(0, 30))
+        base.append((i, i % 5, t, t + float(rng.choice([150, 300, 800])), float(rng.integers(30, 120))))
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, delta_eval_us=0.0, max_closed=0,
+                         th_urgent=-1.0, num_pri=4)
+
+    def run(eps):
+        fac = noise_factors(3, range(400), eps)
+        frames = [S.SimFrame(i, c, t, dl, [d], est=[d * fac[i]]) for (i, c, t, dl, d) in base]
+        return S.simulate(frames, cfg)
+
+    plain = S.simulate([S.SimFrame(i, c, t, dl, [d]) for (i, c, t, dl, d) in base], cfg)
+    r0, r3 = run(0.0), run(0.3)
+    assert r0.done == plain.done and r0.dropped == plain.dropped and r0.releases == plain.releases
+    assert set(r3.done) | set(r3.dropped) == set(range(400))
+    assert r3.releases != plain.releases

@@ -67,14 +67,20 @@ def test_replay_random_states(pp):
     assert set(kinds) == {S.NONE, S.RELEASE, S.WAIT, S.DELAY}, kinds
 
 
-def test_replay_des_trace(pp):
-    """Replays every decision point of a discrete-event simulation through the library."""
+@pytest.mark.parametrize("noise", [0.0, 0.3])
+def test_replay_des_trace(pp, noise):
+    """Replays every decision point of a discrete-event simulation through the library; with
+    noise, the policy sees every frame's estimate scaled by its per-frame factor 1 + U[-eps,
+    eps) while units run for the true durations (the estimation-error study)."""
+    from pp_synth import noise_factors
     rng = np.random.default_rng(5)
+    fac = noise_factors(41, range(300), noise)
     frames = []
     for i in range(300):
         t = float(i * 30 + rng.integers(0, 25))
+        d = float(rng.integers(20, 150))
         frames.append(S.SimFrame(i, i % 7, t, t + float(rng.choice([200, 400, 900])),
-                                 [float(rng.integers(20, 150))], precision=(i % 7) % 2))
+                                 [d], precision=(i % 7) % 2, est=[d * fac[i]] if noise else None))
     cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=4, delta_eval_us=150.0, max_closed=2,
                          th_urgent=1.0 / 150.0, num_pri=6)
     calls = []
