@@ -53,7 +53,8 @@ def _args():
                     help="conv tile table: loaded (no autotuning) if the file exists, else written after "
                          "autotuning, so that a profiled run launches the same tiles as a plain one")
     ap.add_argument("--serve-sweep", default=None,
-                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac][:noise]")
+                    help="run only the serving sweep: comma list of chains:rate:seconds[:mixed][:dfac][:noise]"
+                         "[:util/kernel_us/frame_us] (the last: odd chains run synthetic kernels)")
     ap.add_argument("--serve-modes", default="urgency,plain",
                     help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf, saedf, eqdf")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
@@ -564,7 +565,8 @@ def _run_ours(a, rank, world, dist):
 
 # ------------------------------------------------------------------ serving (chains with deadlines)
 
-def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0, noise=0.0):
+def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0, noise=0.0,
+           synth=None):
     """Replays periodic chains in real time against one context and returns its statistics.
 
     mode "urgency": the paper's release rules (urgency order, early exit, stream binding,
@@ -576,8 +578,11 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
     frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
     f_a and f_d); ``noise``: every frame's estimate, as the policy sees it, scaled by a factor
-    drawn from 1 + U[-noise, noise) (the paper's estimation-error study).  A frame the budget
-    cannot admit counts as a miss."""
+    drawn from 1 + U[-noise, noise) (the paper's estimation-error study).  ``synth`` = (util,
+    kernel_us, total_us): every odd chain becomes a synthetic-load chain whose frames run
+    round(total_us / kernel_us) kernels of about kernel_us on round(util x SMs) SMs (the paper's
+    kernel-utilisation and kernel-time studies).  A frame the budget cannot admit counts as a
+    miss."""
     from pp_synth import BACKBONE_SMALL, GEOM_SMALL, arrival_times, pillar_weights, serving_chains
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     w = pillar_weights(bb, 7)
@@ -603,9 +608,17 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
                                noise_seed=seed, **knobs)
     ctx = pp.Context(cfg)
     try:
+        synthetic = set()
         for c, p in zip(chains, prec):
-            ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
+            if synth is not None and c.chain_id % 2 == 1:
+                util, kus, tot = synth
+                ctx.register_synthetic_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac,
+                                             max(1, int(round(tot / kus))), kus, util)
+                synthetic.add(c.chain_id)
+            else:
+                ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
         ev = arrival_times(chains, duration_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed)
+        ev = [(t, cid, 0 if cid in synthetic else n) for t, cid, n in ev]
         # real-time replay from the library's own load generator (pp_replay): submissions at
         # their scheduled times, results polled and released as they complete
         arrivals = [(20000.0 + t_ms * 1000.0, cid, i % len(clouds), n) for i, (t_ms, cid, n) in enumerate(ev)]
@@ -622,7 +635,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             per[c.chain_id] = (m, n)
     miss = sum(m / n for m, n in per.values()) / max(1, len(per))
     return {"mode": mode, "chains": n_chains, "rate": rate, "deadline_factor": dfac, "mixed": mixed,
-            "est_noise": noise,
+            "est_noise": noise, "synthetic": None if synth is None else
+            {"util": synth[0], "kernel_us": synth[1], "frame_us": synth[2], "chains": "odd"},
             "frames": len(ev),
             "done": st["done"], "dropped": st["dropped"], "rejected": sum(rejected.values()),
             "miss_ratio": miss, "lat_p50_ms": st["lat_p50_us"] / 1e3, "lat_p99_ms": st["lat_p99_us"] / 1e3,
@@ -694,8 +708,10 @@ def main():
             mixed = len(parts) > 3 and parts[3] == "mixed"
             dfac = float(parts[4]) if len(parts) > 4 else 1.0
             noise = float(parts[5]) if len(parts) > 5 else 0.0
+            synth = tuple(float(x) for x in parts[6].split("/")) if len(parts) > 6 else None
             for mode in a.serve_modes.split(","):
-                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac, noise=noise))
+                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac, noise=noise,
+                                  synth=synth))
                 print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"metric": "deadline-miss ratio and p99 chain latency, urgency-served batched "
                           "vs plain per-frame launches", "serving": out}))

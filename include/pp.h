@@ -282,7 +282,7 @@ int pp_device_error(uint32_t* code, int32_t clear);
 /* synchronisation with overlap (Section 4.4.5).  Policy PP_POLICY_FIFO is the plain baseline:*/
 /* every frame launched on arrival on its chain's default-priority stream, kernel by kernel,  */
 /* no graph, no batching, no urgency.  The other policies are the textbook orders the paper */
-/* compares against (Section 5, comparison of policies; not defined there): they replace the */
+/* compares against (Section 6.4, comparison of policies; not defined there): they replace the */
 /* urgency order and its stream ranking, with no early exit, reservation or delaying:         */
 /*   PP_POLICY_EDF   earliest absolute deadline first;                                        */
 /*   PP_POLICY_SJF   shortest remaining estimate (est_gpu + est_cpu) first;                   */
@@ -381,6 +381,18 @@ int pp_create(const pp_config* cfg, pp_ctx** out);
  * 0 <= chain_id < PP_MAX_CHAINS. */
 int pp_register_chain(pp_ctx* ctx, int32_t chain_id, double period_ms, double rel_deadline_ms,
                       int32_t precision);
+
+/* Declares a synthetic-load chain (the paper's robustness study with custom kernels of set
+ * utilisation and execution time, Section 6.6): each of its frames runs n_kernels launches of
+ * a vector-add style kernel on round(util x SMs) CTAs (each holds an SM alone, so util is the
+ * fraction of the GPU it occupies), each launch calibrated once here to last about kernel_us.  Its frames
+ * are submitted like any other (points ignored, n_points 0), released by the same policy
+ * (utilisation util for the delay exemption; estimates from the chain's own measured
+ * durations, n_kernels x kernel_us before the first), run one per unit, and complete with no
+ * outputs (out_dev NULL, out_dtype -1).  n_kernels 1..256, kernel_us 1..100000, util (0, 1],
+ * at most 1 s of kernels per frame.  Synchronous (a few ms of calibration launches). */
+int pp_register_synthetic_chain(pp_ctx* ctx, int32_t chain_id, double period_ms, double rel_deadline_ms,
+                                int32_t n_kernels, double kernel_us, double util);
 
 /* Where submitted points live (the is_device_ptr argument):
  *   PP_POINTS_HOST (0)   host memory, copied into a pinned staging slot before the call returns;

@@ -21,7 +21,7 @@ release units (a unit = up to ``max_batch`` frames run as one launch):
   wait for the previous batch; 1 = synchronous batched; 0 = no synchronisation);
 * the overall deadline-miss ratio (Eq. 3): mean over chains of each chain's miss ratio.
 
-The comparison policies of the paper's Section 5 (EDF, SJF, HRRN and lowest chain utilisation
+The comparison policies of the paper's Section 6.4 (EDF, SJF, HRRN and lowest chain utilisation
 first; the paper names them without definitions) are the textbook orders: a priority value
 replaces the urgency in ordering frames and ranking active units onto stream levels
 0 .. NUM_PRI-1, without early exit, reservation or delaying:

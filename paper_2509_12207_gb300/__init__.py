@@ -198,6 +198,8 @@ _SIGS = {
     "pp_config_defaults": (None, [ctypes.POINTER(Config)]),
     "pp_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
     "pp_register_chain": (ctypes.c_int, [_P, _I, ctypes.c_double, ctypes.c_double, _I]),
+    "pp_register_synthetic_chain": (ctypes.c_int, [_P, _I, ctypes.c_double, ctypes.c_double, _I, ctypes.c_double,
+                                                   ctypes.c_double]),
     "pp_submit_frame": (ctypes.c_int, [_P, _I, _P, ctypes.c_int64, _I, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_uint64)]),
     "pp_poll": (ctypes.c_int, [_P, ctypes.POINTER(Result), _I, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]),
@@ -589,6 +591,12 @@ class Context:
 
     def register_chain(self, chain_id, period_ms, deadline_ms, precision):
         _check(lib().pp_register_chain(self.h, chain_id, period_ms, deadline_ms, precision))
+
+    def register_synthetic_chain(self, chain_id, period_ms, deadline_ms, n_kernels, kernel_us, util):
+        """A synthetic-load chain: each frame runs n_kernels kernels of about kernel_us on
+        round(util x SMs) SMs (submit its frames with no points)."""
+        _check(lib().pp_register_synthetic_chain(self.h, chain_id, period_ms, deadline_ms, n_kernels, kernel_us,
+                                                 util))
 
     def submit(self, chain_id, points, t_arrival_us=None, abs_deadline_us=0.0, n_points=None):
         """points: numpy float32 [N, 4] (host; copied), a CUDA tensor [N, 4] (device; borrowed

@@ -17,7 +17,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["vox.cu", "vox_static.cu", "pfn.cu", "conv_simt.cu", "conv_tc.cu", "capi.cu", "pipeline.cu", "tune.cu"]
+CUDA_SOURCES = ["vox.cu", "vox_static.cu", "pfn.cu", "conv_simt.cu", "conv_tc.cu", "capi.cu", "pipeline.cu", "tune.cu",
+                "synth.cu"]
 CXX_SOURCES = ["policy.cpp", "runtime.cpp"]
 
 

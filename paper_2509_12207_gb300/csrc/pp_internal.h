@@ -92,4 +92,18 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
 int tuned_tile(int dtype, const ConvShape& c);
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
 
+// ---- synthetic GPU load (synth.cu): kernels of set utilisation and duration
+struct SynthBuf {
+  void* ab = nullptr;  // [2][SMs][slice] float4 inputs
+  void* c = nullptr;   // [units][SMs][slice] float4 outputs, one region per synthetic unit
+  int sms = 0, units = 0;
+};
+int synth_alloc(SynthBuf* b, int units);
+void synth_free(SynthBuf* b);
+int synth_ctas(const SynthBuf& b, double util);  // round(util x SMs), 1..SMs
+// n_kernels launches of `iters` passes each with `ctas` CTAs on s, into unit `unit`'s region.
+int synth_launch(const SynthBuf& b, int unit, int ctas, int iters, int n_kernels, cudaStream_t s);
+// Passes per launch that make one launch of `ctas` CTAs last about kernel_us (synchronous).
+int synth_calibrate(const SynthBuf& b, int ctas, double kernel_us, cudaStream_t s, int* iters);
+
 }  // namespace pp

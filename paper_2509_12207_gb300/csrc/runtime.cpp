@@ -66,6 +66,8 @@ struct Lut {
 };
 
 constexpr int kMaxSubmit = PP_MAX_SUBMIT;
+constexpr int kSynth = 2;       // "precision" class of synthetic-load frames (no pillar model)
+constexpr int kSynthUnits = 4;  // units that run synthetic frames
 
 struct Frame {
   uint64_t id = 0;
@@ -94,7 +96,12 @@ struct Unit {
 struct Chain {
   bool used = false;
   double period_ms = 0, deadline_ms = 0;
-  int precision = 0;
+  int precision = 0;              // PP_F32 / PP_BF16, or kSynth for a synthetic-load chain
+  // synthetic load: n_kernels launches of synth_ctas CTAs x synth_iters passes per frame, and
+  // the chain's own duration estimates (its frames are not interchangeable with other chains')
+  int n_kernels = 0, synth_ctas = 0, synth_iters = 0;
+  double kernel_us = 0, util = 1.0;  // util: fraction of the SMs its kernels occupy
+  Lut lut;
   std::vector<cudaStream_t> streams;  // one per priority level, level 0 highest
   uint64_t frames = 0, missed = 0;
   std::vector<double> lat;
@@ -110,9 +117,11 @@ struct pp_ctx {
   int device = 0;
   int num_pri = 1, prio_greatest = 0;
   Model models[2];
-  bool have[2] = {false, false};
+  bool have[3] = {false, false, false};  // [kSynth]: synthetic-load units exist
   std::vector<Unit*> units;
-  int capacity[2] = {0, 0}, admitted[2] = {0, 0};
+  int capacity[3] = {0, 0, 0}, admitted[3] = {0, 0, 0};
+  SynthBuf synth;
+  int synth_first = -1;  // index of the first synthetic unit in `units`
   Chain chains[PP_MAX_CHAINS];
   std::map<uint64_t, Frame*> frames;
   std::vector<Frame*> ready;
@@ -126,7 +135,7 @@ struct pp_ctx {
     size_t slot_bytes = 0;
     std::vector<size_t> block_off;
     std::vector<int> free;
-  } pool[2];
+  } pool[3];                     // [kSynth] stays empty: synthetic frames have no outputs
   Lut lut[2][9];
   // batched synchronisation gate
   double open_sum = 0;
@@ -157,6 +166,15 @@ namespace {
 
 double unit_est(pp_ctx* c, int prec, int nf) {
   return c->lut[prec][nf].mean(c->lut[prec][1].mean(1000.0) * nf);
+}
+
+// GPU-time estimate of one frame alone (before any estimate noise)
+double frame_est(pp_ctx* c, const Frame* f) {
+  if (f->precision == kSynth) {
+    const Chain& ch = c->chains[f->chain];
+    return ch.lut.mean(ch.n_kernels * ch.kernel_us);
+  }
+  return unit_est(c, f->precision, 1);
 }
 
 void CUDART_CB notify_cb(void* p) {
@@ -197,31 +215,35 @@ void push_result(pp_ctx* c, Frame* f, int status, double t_done) {
     c->n_done++;
     if (t_done > c->last_done) c->last_done = t_done;
     Unit* u = c->units[f->unit];
-    const Model* m = u->pipe.model();
-    const pp_ctx::Pool& pl = c->pool[f->precision];
-    char* base = static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
     r.batch = u->nf;
     r.level = u->level;
-    r.out_dtype = m->precision;
-    if (m->head_outputs > 0) {
-      r.out_dev = base + pl.block_off[0];
-      r.out_c = m->head_c;
-      r.out_valid_c = m->head_outputs;
-      r.out_h = m->out_h();
-      r.out_w = m->out_w();
+    if (f->precision == kSynth) {
+      r.out_dtype = -1;  // synthetic load: timing only, no outputs
+    } else {
+      const Model* m = u->pipe.model();
+      const pp_ctx::Pool& pl = c->pool[f->precision];
+      char* base = static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
+      r.out_dtype = m->precision;
+      if (m->head_outputs > 0) {
+        r.out_dev = base + pl.block_off[0];
+        r.out_c = m->head_c;
+        r.out_valid_c = m->head_outputs;
+        r.out_h = m->out_h();
+        r.out_w = m->out_w();
+      }
+      for (size_t b = 0; m->head_outputs == 0 && b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
+        const LayerSpec& L = m->layers[m->block_end[b]];
+        r.block_dev[b] = base + pl.block_off[b];
+        r.block_c[b] = L.cout;
+        r.block_h[b] = L.Ho;
+        r.block_w[b] = L.Wo;
+        r.out_dev = r.block_dev[b];
+        r.out_c = r.out_valid_c = L.cout;
+        r.out_h = L.Ho;
+        r.out_w = L.Wo;
+      }
+      r.num_pillars = u->pipe.num_pillars_host()[f->slot];
     }
-    for (size_t b = 0; m->head_outputs == 0 && b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
-      const LayerSpec& L = m->layers[m->block_end[b]];
-      r.block_dev[b] = base + pl.block_off[b];
-      r.block_c[b] = L.cout;
-      r.block_h[b] = L.Ho;
-      r.block_w[b] = L.Wo;
-      r.out_dev = r.block_dev[b];
-      r.out_c = r.out_valid_c = L.cout;
-      r.out_h = L.Ho;
-      r.out_w = L.Wo;
-    }
-    r.num_pillars = u->pipe.num_pillars_host()[f->slot];
   } else {
     c->n_dropped += status == PP_FRAME_DROPPED;
   }
@@ -259,9 +281,12 @@ void reap(pp_ctx* c) {
     }
     const double t_done = q == cudaSuccess ? event_host_time(c, u->done) : now_us();
     float ms = 0;
-    if (q == cudaSuccess && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess)
-      c->lut[u->precision][u->nf].add(ms * 1000.0);
-    else
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess) {
+      if (u->precision == kSynth)
+        c->chains[u->head_chain].lut.add(ms * 1000.0);
+      else
+        c->lut[u->precision][u->nf].add(ms * 1000.0);
+    } else
       cudaGetLastError();
     for (int i = 0; i < u->nf; ++i) {
       Frame* f = c->frames[u->frames[i]];
@@ -280,6 +305,18 @@ int closed_pending(pp_ctx* c) {
   int n = 0;
   for (auto& b : c->closed) n += !b.empty();
   return n;
+}
+
+// One stream per priority level for a new chain, level 0 the highest.
+int chain_streams(pp_ctx* c, Chain* ch) {
+  for (int l = 0; l < c->num_pri; ++l) {
+    cudaStream_t s;
+    int st = cuda_status(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, c->prio_greatest + l),
+                         "chain stream");
+    if (st) return st;
+    ch->streams.push_back(s);
+  }
+  return PP_OK;
 }
 
 int free_unit(pp_ctx* c, int prec) {
@@ -301,8 +338,9 @@ pp_policy_config policy_cfg(pp_ctx* c) {
   return p;
 }
 
-// A ready frame as the release rule sees it: one unit's estimate remains; its kernels fill the
-// GPU (utilisation 1.0, so the delay exemption never applies); its chain's period.
+// A ready frame as the release rule sees it: one unit's estimate remains; its utilisation (1.0
+// for pillar frames, whose kernels fill the GPU, so the delay exemption never applies to them;
+// a synthetic chain's SM fraction); its chain's period.
 pp_policy_frame policy_frame(pp_ctx* c, const Frame* f) {
   pp_policy_frame p;
   p.frame_id = f->id;
@@ -310,9 +348,9 @@ pp_policy_frame policy_frame(pp_ctx* c, const Frame* f) {
   p.precision = f->precision;
   p.t_arr_us = f->t_arr;
   p.deadline_us = f->deadline;
-  p.est_gpu_us = unit_est(c, f->precision, 1) * f->est_scale;
+  p.est_gpu_us = frame_est(c, f) * f->est_scale;
   p.est_cpu_us = 0.0;
-  p.util = 1.0;
+  p.util = c->chains[f->chain].util;
   p.period_us = c->chains[f->chain].period_ms * 1000.0;
   return p;
 }
@@ -328,7 +366,9 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   bool direct[kMaxUnit];
   char* dsts[kMaxUnit];
   const pp_ctx::Pool& pl = c->pool[prec];
-  u->nf = d.n_frames;
+  // a synthetic frame runs alone: its chain's kernels are its own (the rest stay ready)
+  const int nf = prec == kSynth ? 1 : d.n_frames;
+  u->nf = nf;
   u->level = d.level;
   u->head_chain = head->chain;
   {
@@ -337,8 +377,8 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     const pp_policy_frame hf = policy_frame(c, head);
     u->ul = pp_policy_priority(&pc, t, &hf);
   }
-  u->est = unit_est(c, prec, d.n_frames);
-  for (int i = 0; i < d.n_frames; ++i) {
+  u->est = prec == kSynth ? frame_est(c, head) : unit_est(c, prec, nf);
+  for (int i = 0; i < nf; ++i) {
     Frame* f = c->frames[d.frames[i]];
     u->frames[i] = f->id;
     f->unit = ui;
@@ -347,7 +387,7 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     srcs[i] = f->src;
     counts[i] = (int)f->n;
     direct[i] = f->staging < 0;  // a borrowed device buffer is read in place
-    dsts[i] = static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
+    dsts[i] = f->rslot < 0 ? nullptr : static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
     if (f->delay_start >= 0) {
       c->delayed_us += t - f->delay_start;
       f->delay_start = -1;
@@ -368,13 +408,18 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   u->running = true;
   u->t_launch = t;
   int st = cuda_status(cudaEventRecord(u->start, s), "record start");
-  // the unit's graph also copies every frame's block outputs into its result slot
-  if (!st) st = u->pipe.run(d.n_frames, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s);
+  if (!st && prec == kSynth) {
+    const Chain& ch = c->chains[head->chain];
+    st = synth_launch(c->synth, ui - c->synth_first, ch.synth_ctas, ch.synth_iters, ch.n_kernels, s);
+  } else if (!st) {
+    // the unit's graph also copies every frame's block outputs into its result slot
+    st = u->pipe.run(nf, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s);
+  }
   if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
   if (!st) st = cuda_status(cudaLaunchHostFunc(s, notify_cb, c), "host notify");
   if (st) c->device_error = true;
   c->launched++;
-  c->batch_frames += d.n_frames;
+  c->batch_frames += nf;
   // batched synchronisation bookkeeping
   c->open_units.push_back(ui);
   c->open_sum += u->est;
@@ -390,7 +435,7 @@ void calibrate(pp_ctx* c, double t) {
   if (!c->calibrating) return;
   double mx = -INFINITY;
   for (Frame* f : c->ready) {
-    const double s = f->deadline - unit_est(c, f->precision, 1) * f->est_scale - t;
+    const double s = f->deadline - frame_est(c, f) * f->est_scale - t;
     if (s > 0) mx = std::max(mx, 1.0 / s);
   }
   for (Unit* u : c->units)
@@ -477,6 +522,7 @@ void destroy_units(pp_ctx* c) {
     if (c->have[p]) c->models[p].release();
   for (float* s : c->staging) cudaFreeHost(s);
   c->staging.clear();
+  synth_free(&c->synth);
   for (auto& pl : c->pool)
     if (pl.base) cudaFree(pl.base);
   for (auto& ch : c->chains)
@@ -687,17 +733,56 @@ int pp_register_chain(pp_ctx* c, int32_t chain_id, double period_ms, double rel_
   if (!c->have[precision]) return fail(PP_EINVAL, "register_chain: precision %d not enabled", precision);
   Chain& ch = c->chains[chain_id];
   if (ch.used) return fail(PP_ESTATE, "register_chain: chain %d already registered", chain_id);
-  for (int l = 0; l < c->num_pri; ++l) {
-    cudaStream_t s;
-    int st = cuda_status(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, c->prio_greatest + l),
-                         "chain stream");
-    if (st) return st;
-    ch.streams.push_back(s);
-  }
+  int st = chain_streams(c, &ch);
+  if (st) return st;
   ch.used = true;
   ch.period_ms = period_ms;
   ch.deadline_ms = rel_deadline_ms;
   ch.precision = precision;
+  return PP_OK;
+}
+
+int pp_register_synthetic_chain(pp_ctx* c, int32_t chain_id, double period_ms, double rel_deadline_ms,
+                                int32_t n_kernels, double kernel_us, double util) {
+  if (!c || chain_id < 0 || chain_id >= PP_MAX_CHAINS || !(rel_deadline_ms > 0) || !(period_ms > 0) ||
+      n_kernels < 1 || n_kernels > 256 || !(kernel_us >= 1 && kernel_us <= 100000) || !(util > 0 && util <= 1) ||
+      n_kernels * kernel_us > 1e6)
+    return fail(PP_EINVAL, "register_synthetic_chain: bad argument (1..256 kernels of 1 us..100 ms, util (0, 1], "
+                           "at most 1 s per frame)");
+  std::lock_guard<std::mutex> lk(c->mu);
+  Chain& ch = c->chains[chain_id];
+  if (ch.used) return fail(PP_ESTATE, "register_chain: chain %d already registered", chain_id);
+  int st = PP_OK;
+  if (!c->have[kSynth]) {
+    // first synthetic chain: units that run synthetic frames and their buffers
+    st = synth_alloc(&c->synth, kSynthUnits);
+    c->synth_first = (int)c->units.size();
+    for (int k = 0; k < kSynthUnits && !st; ++k) {
+      Unit* u = new (std::nothrow) Unit();
+      if (!u) { st = fail(PP_ENOMEM, "register_synthetic_chain: host allocation"); break; }
+      u->precision = kSynth;
+      st = cuda_status(cudaEventCreate(&u->start), "event");
+      if (!st) st = cuda_status(cudaEventCreate(&u->done), "event");
+      c->units.push_back(u);
+    }
+    if (st) return st;
+    c->have[kSynth] = true;
+    c->capacity[kSynth] = kMaxAdmitted;
+  }
+  const int ctas = synth_ctas(c->synth, util);
+  int iters = 1;
+  st = synth_calibrate(c->synth, ctas, kernel_us, c->aux, &iters);
+  if (!st) st = chain_streams(c, &ch);
+  if (st) return st;
+  ch.used = true;
+  ch.period_ms = period_ms;
+  ch.deadline_ms = rel_deadline_ms;
+  ch.precision = kSynth;
+  ch.n_kernels = n_kernels;
+  ch.kernel_us = kernel_us;
+  ch.synth_ctas = ctas;
+  ch.synth_iters = iters;
+  ch.util = (double)ctas / c->synth.sms;
   return PP_OK;
 }
 
@@ -736,8 +821,9 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
   for (; k < n; ++k) {
     const Chain& ch = c->chains[chain_ids[k]];
     const int p = ch.precision;
-    if (c->admitted[p] >= c->capacity[p] || c->pool[p].free.empty() ||
-        (!is_device_ptr && c->staging_free.empty())) {
+    const bool synth = p == kSynth;  // no points, no result slot, no staging
+    if (c->admitted[p] >= c->capacity[p] || (!synth && c->pool[p].free.empty()) ||
+        (!synth && !is_device_ptr && c->staging_free.empty())) {
       c->rejected += n - k;
       st = fail(PP_EAGAIN, "submit: HBM budget full");
       break;
@@ -754,10 +840,14 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
     f->t_arr = t_arrival_us;
     const double dl = abs_deadline_us ? abs_deadline_us[k] : 0.0;
     f->deadline = dl > 0 ? dl : t_arrival_us + ch.deadline_ms * 1000.0;
-    f->n = n_points[k];
+    f->n = synth ? 0 : n_points[k];
+    c->admitted[p]++;
+    if (synth) {
+      fs[k] = f;
+      continue;
+    }
     f->rslot = c->pool[p].free.back();
     c->pool[p].free.pop_back();
-    c->admitted[p]++;
     if (is_device_ptr) {
       f->src = mapped[k];  // read in place by the unit's kernels
     } else {
@@ -770,7 +860,7 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
   if (!is_device_ptr && k > 0) {
     lk.unlock();  // the copies run outside the lock; the slots are already ours
     for (int i = 0; i < k; ++i)
-      if (n_points[i] > 0) memcpy(const_cast<float*>(fs[i]->src), xyzr[i], (size_t)n_points[i] * 16);
+      if (fs[i]->n > 0) memcpy(const_cast<float*>(fs[i]->src), xyzr[i], (size_t)fs[i]->n * 16);
     lk.lock();
   }
   // the admitted frames become ready together, so one decision can batch all of them

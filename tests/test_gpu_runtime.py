@@ -493,3 +493,35 @@ def test_runtime_serves_head_maps(full_frame, full_head):
         ctx.release_many(ids)
     finally:
         ctx.destroy()
+
+
+def test_runtime_synthetic_load_chain(small_clouds):
+    """A synthetic-load chain (kernels of set duration and SM share) served beside a pillar
+    chain: its frames complete with no outputs after about n_kernels x kernel_us of device time,
+    one per unit; the pillar frames stay exact; bad arguments are refused."""
+    ctx, keep = _ctx(max_batch=4)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        ctx.register_synthetic_chain(1, 100.0, 100.0, 4, 200.0, 0.5)
+        with pytest.raises(pp.PPError):
+            ctx.register_synthetic_chain(1, 100.0, 100.0, 4, 200.0, 0.5)     # already registered
+        for bad in [(0, 200.0, 0.5), (4, 0.5, 0.5), (4, 200.0, 0.0), (4, 200.0, 1.5), (300, 200.0, 0.5)]:
+            with pytest.raises(pp.PPError):
+                ctx.register_synthetic_chain(2, 100.0, 100.0, *bad)
+        empty = np.zeros((0, 4), np.float32)
+        rc, sids = ctx.submit_many([1, 1, 1], [empty, empty, empty])
+        assert rc == pp.PP_OK and len(sids) == 3
+        rc, pids = ctx.submit_many([0, 0], small_clouds[:2])
+        assert rc == pp.PP_OK
+        res = {r.frame_id: r for r in _drain(ctx, 5)}
+        for fid in sids:
+            r = res[fid]
+            assert r.status == pp.PP_FRAME_DONE and not r.out_dev and r.out_dtype == -1 and r.batch == 1
+            assert 300.0 <= r.t_done_us - r.t_release_us <= 20000.0, r.t_done_us - r.t_release_us
+        for k, fid in enumerate(pids):
+            assert res[fid].num_pillars == _ref(small_clouds[k])["vox"]["num_pillars"]
+        st = ctx.stats()
+        assert st["chain_frames"][1] == 3 and st["chain_frames"][0] == 2
+        ctx.release_many(sids + pids)
+    finally:
+        ctx.destroy()
