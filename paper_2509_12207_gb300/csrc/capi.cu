@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -27,6 +28,14 @@ int cuda_status(cudaError_t e, const char* what) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("PP_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 
 const char* last_error() { return g_err; }
 

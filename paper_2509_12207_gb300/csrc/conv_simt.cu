@@ -28,6 +28,7 @@ conv3x3_f32(ConvShape c, const float* __restrict__ in, const float* __restrict__
   constexpr int THR = (BM / 8) * (BN / TN);
   constexpr int TX = BN / TN;  // threads along N
   static_assert(THR == 2 * BM, "A-tile loader assumes 2*BM threads");
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
 
@@ -222,13 +223,14 @@ int conv_f32_launch(const ConvShape& c, const float* in, const float* w, const f
     return fail(PP_EINVAL, "conv f32: tile %d unsupported for cout %d", tile, c.cout);
   const int bm = kTiles[tile].bm, bn = kTiles[tile].bn;
   const dim3 grid((M + bm - 1) / bm, c.cout / bn, c.batch);
+  cudaError_t e;
   switch (tile) {
-    case 0: conv3x3_f32<128, 64, 4><<<grid, 256, 0, s>>>(c, in, w, ss, out); break;
-    case 1: conv3x3_f32<64, 64, 4><<<grid, 128, 0, s>>>(c, in, w, ss, out); break;
-    case 2: conv3x3_f32<128, 128, 8><<<grid, 256, 0, s>>>(c, in, w, ss, out); break;
-    default: conv3x3_f32<64, 128, 8><<<grid, 128, 0, s>>>(c, in, w, ss, out); break;
+    case 0: e = launch_pdl(conv3x3_f32<128, 64, 4>, grid, dim3(256), 0, s, c, in, w, ss, out); break;
+    case 1: e = launch_pdl(conv3x3_f32<64, 64, 4>, grid, dim3(128), 0, s, c, in, w, ss, out); break;
+    case 2: e = launch_pdl(conv3x3_f32<128, 128, 8>, grid, dim3(256), 0, s, c, in, w, ss, out); break;
+    default: e = launch_pdl(conv3x3_f32<64, 128, 8>, grid, dim3(128), 0, s, c, in, w, ss, out); break;
   }
-  return cuda_status(cudaGetLastError(), "conv f32 launch");
+  return cuda_status(e, "conv f32 launch");
 }
 
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s) {

@@ -247,10 +247,6 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   if (threadIdx.x == 0) s_abort = tc_error_now();
   __syncthreads();
   if (s_abort != 0u) return;
-  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
-    s_ss[i] = args.ss[n0 + i];
-    s_ss[BN + i] = args.ss[c.cout + n0 + i];
-  }
   if (warp == 0) {
     if (lane == 0) {
       for (int s = 0; s < STAGES; ++s) {
@@ -273,6 +269,13 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_trigger();  // after this CTA's TMEM allocation: the next kernel may launch
+  pdl_wait();     // the previous kernel's outputs are complete and visible
+  for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+    s_ss[i] = args.ss[n0 + i];
+    s_ss[BN + i] = args.ss[c.cout + n0 + i];
+  }
+  __syncthreads();
 
   const int kchunks = c.cin / kBK;
   const int KB = 9 * kchunks;
@@ -463,10 +466,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int fold = MODE == 1 ? args.fold : KB;
   const int Hp2 = (c.H + 2) / 2;
 
-  for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
-    s_scale[i] = args.ss[i];
-    s_shift[i] = args.ss[args.co_blk + i];
-  }
   const float lo_clamp = args.relu ? 0.f : __uint_as_float(0xff800000u);  // ReLU, or none (-inf: bias-only epilogue)
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -493,6 +492,12 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();     // the previous kernel's outputs are complete and visible
+  for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
+    s_scale[i] = args.ss[i];
+    s_shift[i] = args.ss[args.co_blk + i];
+  }
+  __syncthreads();
 
   auto decode = [&](int t, int& b, int& oy0, int& ox0, int& n0) {
     const int nt = t % args.tiles_n;
@@ -581,6 +586,11 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       bool ok = true;
       int t, k0, k1;
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        {
+          // this CTA's last piece: let the next kernel launch (its CTAs take SMs as ours exit)
+          int t2, a2, b2;
+          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
+        }
         for (int kb0 = k0; kb0 < k1; kb0 += KPS) {
           const int nk = k1 - kb0 < KPS ? k1 - kb0 : KPS;
           const int buf = gg & (NBUF - 1);
@@ -822,10 +832,6 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
   const ConvShape& c = args.c;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x < 64) {
-    s_scale[threadIdx.x] = args.ss[threadIdx.x];
-    s_shift[threadIdx.x] = args.ss[64 + threadIdx.x];
-  }
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
@@ -851,6 +857,12 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();     // the previous kernel's outputs are complete and visible
+  if (threadIdx.x < 64) {
+    s_scale[threadIdx.x] = args.ss[threadIdx.x];
+    s_shift[threadIdx.x] = args.ss[64 + threadIdx.x];
+  }
+  __syncthreads();
   const int Hp = c.H + 2, Hp2 = Hp / 2;
 
   auto decode = [&](int u, int& b, int& ox0, int& r0, int& r1) {
@@ -897,6 +909,7 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       int fw = 0, fr = 0;  // ring fills waited / released so far (fill order)
       int gg = 0;
       for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+        if (u + (int)gridDim.x >= args.units) pdl_trigger();  // last unit: the next kernel may launch
         int b, ox0, r0, r1;
         decode(u, b, ox0, r0, r1);
         const int base = fw;  // fill index of this unit's first row plane
@@ -1038,8 +1051,8 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
     if (e != cudaSuccess) return cuda_status(e, "conv tc smem attribute");
     attr_set = true;
   }
-  conv3x3_tc<BN, STAGES, S2><<<grid, 128, bytes, s>>>(a, w, args);
-  return cuda_status(cudaGetLastError(), "conv tc launch");
+  return cuda_status(launch_pdl(conv3x3_tc<BN, STAGES, S2>, grid, dim3(128), bytes, s, a, w, args),
+                     "conv tc launch");
 }
 
 
@@ -1202,8 +1215,9 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  conv3x3_tcp<MODE, BN, ST, KPS, S2, SK><<<grid, 192, bytes, s>>>(a, alo, w, args);
-  return cuda_status(cudaGetLastError(), "persistent conv launch");
+  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK>, dim3(grid), dim3(192), bytes, s, a, alo, w,
+                                args),
+                     "persistent conv launch");
 }
 
 // Persistent tile choice: fewest "waves" of tile work over the SMs, each tile costing its MMA
@@ -1397,7 +1411,8 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
       if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
       attr = true;
     }
-    conv3x3_rows<true><<<grid, 192, bytes, s>>>(ta, tw, a);
+    const cudaError_t e = launch_pdl(conv3x3_rows<true>, dim3(grid), dim3(192), bytes, s, ta, tw, a);
+    if (e != cudaSuccess) return cuda_status(e, "row conv launch");
   } else {
     static bool attr = false;
     if (!attr) {
@@ -1405,9 +1420,10 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
       if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
       attr = true;
     }
-    conv3x3_rows<false><<<grid, 192, bytes, s>>>(ta, tw, a);
+    const cudaError_t e = launch_pdl(conv3x3_rows<false>, dim3(grid), dim3(192), bytes, s, ta, tw, a);
+    if (e != cudaSuccess) return cuda_status(e, "row conv launch");
   }
-  return cuda_status(cudaGetLastError(), "row conv launch");
+  return PP_OK;
 }
 
 int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF : kNPB; }

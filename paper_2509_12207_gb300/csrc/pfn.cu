@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
                                                  const float* __restrict__ pfn_w,
                                                  const float* __restrict__ ss,
                                                  float* __restrict__ feat) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   __shared__ float w_s[9][64];          // transposed: w_s[k][c] = W[c][k]
   __shared__ float sc_s[64], sh_s[64];
   __shared__ float f_s[kWarps][32][10];  // features per point (+1 pad)
@@ -95,6 +96,7 @@ __device__ __forceinline__ float4 tf32_rem4(float4 v) {
 __global__ void bev_scatter_f32(Geom g, int batch, const float4* __restrict__ feat,
                                 const int* __restrict__ pillar_of_cell,
                                 float4* __restrict__ canvas, float4* __restrict__ lo) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int Wp = g.nx + 2, Hp = g.ny + 2;
   const size_t total = (size_t)batch * Hp * Wp * 16;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -116,11 +118,13 @@ __global__ void bev_scatter_f32(Geom g, int batch, const float4* __restrict__ fe
 }
 
 __global__ void tf32_split_kernel(const float4* __restrict__ x, float4* __restrict__ lo, size_t n4) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
     lo[i] = tf32_rem4(x[i]);
 }
 
 __global__ void tf32_split_tail(const float* __restrict__ x, float* __restrict__ lo, size_t from, size_t n) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const size_t i = from + threadIdx.x;
   if (i < n) lo[i] = tf32_rem(x[i]);
 }
@@ -129,6 +133,7 @@ __global__ void tf32_split_tail(const float* __restrict__ x, float* __restrict__
 __global__ void bev_scatter_bf16(Geom g, int batch, const float4* __restrict__ feat,
                                  const int* __restrict__ pillar_of_cell,
                                  uint4* __restrict__ canvas) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int Wp = g.nx + 2, Hp = g.ny + 2;
   const size_t total = (size_t)batch * Hp * Wp * 8;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -179,9 +184,9 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
   int bx = (g.P + kWarps - 1) / kWarps;
   const int bx_max = (4 * sm_count() + batch - 1) / batch;
   if (bx > bx_max) bx = bx_max;
-  pfn_fused<<<dim3(bx > 0 ? bx : 1, batch), kWarps * 32, 0, s>>>(g, pts, npts, coord, num_pillars,
-                                                                pfn_w, ss, feat);
-  return cuda_status(cudaGetLastError(), "pointnet launch");
+  return cuda_status(launch_pdl(pfn_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, pts, npts,
+                                coord, num_pillars, pfn_w, ss, feat),
+                     "pointnet launch");
 }
 
 int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
@@ -191,14 +196,15 @@ int scatter_launch(const Geom& g, int batch, const float* feat, const int* pilla
   size_t blocks = (chunks + 255) / 256;
   const size_t cap = (size_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
+  cudaError_t e;
   if (dtype == PP_F32 || dtype == PP_F32_TC)
-    bev_scatter_f32<<<(unsigned)blocks, 256, 0, s>>>(
-        g, batch, (const float4*)feat, pillar_of_cell, (float4*)canvas,
-        dtype == PP_F32_TC ? (float4*)canvas + (plane ? plane / 4 : chunks) : nullptr);
+    e = launch_pdl(bev_scatter_f32, dim3((unsigned)blocks), dim3(256), 0, s, g, batch, (const float4*)feat,
+                   pillar_of_cell, (float4*)canvas,
+                   dtype == PP_F32_TC ? (float4*)canvas + (plane ? plane / 4 : chunks) : (float4*)nullptr);
   else
-    bev_scatter_bf16<<<(unsigned)blocks, 256, 0, s>>>(g, batch, (const float4*)feat,
-                                                      pillar_of_cell, (uint4*)canvas);
-  return cuda_status(cudaGetLastError(), "scatter launch");
+    e = launch_pdl(bev_scatter_bf16, dim3((unsigned)blocks), dim3(256), 0, s, g, batch, (const float4*)feat,
+                   pillar_of_cell, (uint4*)canvas);
+  return cuda_status(e, "scatter launch");
 }
 
 int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s) {
@@ -207,10 +213,13 @@ int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s) {
     size_t blocks = (n4 + 255) / 256;
     const size_t cap = (size_t)sm_count() * 16;
     if (blocks > cap) blocks = cap;
-    tf32_split_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4*)x, (float4*)lo, n4);
+    const cudaError_t e = launch_pdl(tf32_split_kernel, dim3((unsigned)blocks), dim3(256), 0, s, (const float4*)x,
+                                     (float4*)lo, n4);
+    if (e != cudaSuccess) return cuda_status(e, "tf32 split launch");
   }
-  if (n % 4) tf32_split_tail<<<1, 4, 0, s>>>(x, lo, n4 * 4, n);
-  return cuda_status(cudaGetLastError(), "tf32 split launch");
+  if (n % 4)
+    return cuda_status(launch_pdl(tf32_split_tail, dim3(1), dim3(4), 0, s, x, lo, n4 * 4, n), "tf32 split launch");
+  return PP_OK;
 }
 
 }  // namespace pp

@@ -25,6 +25,7 @@ struct ResultCopy {
 // Copies every frame's block outputs into its result slot (tab->dst[frame]); gridDim.y = frame.
 // Pure 16-byte streaming copy (all sizes are multiples of 128 bytes, all bases 16-byte aligned).
 __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTable* __restrict__ tab) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int f = blockIdx.y;
   char* dst = tab->dst[f];
   if (!dst) return;
@@ -398,8 +399,9 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
       rc.off[b] = res_off_[b];
     }
   }
-  result_copy<<<dim3(std::max(1, 8 * sms_ / n), n), 256, 0, s>>>(rc, tab_dev_);
-  return cuda_status(cudaGetLastError(), "result copy");
+  return cuda_status(launch_pdl(result_copy, dim3(std::max(1, 8 * sms_ / n), n), dim3(256), 0, s, rc,
+                                (const UnitTable*)tab_dev_),
+                     "result copy");
 }
 
 int Pipeline::run(int n, const float* const* frames, const int* counts, const bool* direct,

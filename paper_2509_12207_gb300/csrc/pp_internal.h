@@ -19,6 +19,42 @@ const char* last_error();
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Programmatic dependent launch.  Kernels that follow another kernel of the library in a stream
+// (or graph) are launched with programmatic stream serialisation: they may start while their
+// predecessor drains, run their prologue (shared-memory carve-up, barrier init, TMEM
+// allocation, tensor-map prefetch), and block in pdl_wait() -- which returns once the
+// predecessor grid has completed and its memory is visible -- before they touch any global data
+// a predecessor writes or reads.  Every kernel launched this way calls pdl_wait() first
+// thing after its prologue.  The persistent tensor-core kernels call pdl_trigger() from their
+// MMA thread when it starts the CTA's last tile (one-tile CTAs right after their TMEM
+// allocation): never before the CTA's own TMEM allocation, so that a dependent CTA sharing the
+// SM cannot take the columns a predecessor CTA still has to allocate; and late, so that the
+// next layer's CTAs, which hold an SM while they wait, take only SMs that are about to free up.
+// The short kernels do not trigger (a CTA's exit is its trigger): dependents launched at their
+// start held SM slots while blocked and measured slower.  PP_PDL=0 in the environment turns
+// it off (plain stream order).
+bool pdl_enabled();
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+#endif
+
 // Kernel-side copy of the geometry with derived sizes.
 struct Geom {
   float xmin, xmax, ymin, ymax, zmin, zmax, vx, vy;

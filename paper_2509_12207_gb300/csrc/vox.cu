@@ -43,6 +43,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
                                const float4* const* __restrict__ srcs,
                                const int* __restrict__ n_points, int* __restrict__ cell,
                                int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, err);
   const float4* src = frame_src(points, srcs, b, cap);
@@ -79,6 +80,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
 // Sums of (occupied, points) over one tile of kVoxTile cells; 256 threads.
 __global__ void vox_tile_sums(Geom g, const unsigned* __restrict__ cnt, int2* __restrict__ sums,
                               int ntiles) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const unsigned* c = cnt + (size_t)b * g.G;
   const int base = blockIdx.x * kVoxTile;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
                                                 int* __restrict__ pillar_start,
                                                 int* __restrict__ pillar_cnt,
                                                 int* __restrict__ num_pillars) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const unsigned* c = cnt + (size_t)b * g.G;
   const int base = blockIdx.x * kVoxTile;
@@ -196,6 +199,7 @@ __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
                            const int* __restrict__ cell, const int* __restrict__ slot,
                            const int* __restrict__ pillar_of_cell,
                            const int* __restrict__ pillar_start, int* __restrict__ csr) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, nullptr);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
                                                   const int* __restrict__ pillar_cnt,
                                                   const int* __restrict__ num_pillars,
                                                   float4* __restrict__ pts) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -305,16 +310,24 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   const int px_max = (8 * sms + batch - 1) / batch;
   if (px > px_max) px = px_max;
   const dim3 pg(px > 0 ? px : 1, batch);
+  // the count follows the memset (a plain launch); the other four follow a kernel
   vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, n_points, cell, w.slot, cnt, w.err);
-  vox_tile_sums<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles);
-  vox_scan<<<dim3(w.ntiles, batch), 256, 0, s>>>(g, cnt, w.tile_sums, w.ntiles, pillar_of_cell,
-                                                 coord, npts, w.pillar_start, w.pillar_cnt,
-                                                 num_pillars);
-  vox_bucket<<<pg, 256, 0, s>>>(g, cap, n_points, cell, w.slot, pillar_of_cell, w.pillar_start,
-                                w.csr);
-  vox_select<<<dim3((g.P + 7) / 8, batch), 256, 0, s>>>(g, cap, points, srcs, w.csr, w.pillar_start,
-                                                        w.pillar_cnt, num_pillars, pts);
-  return cuda_status(cudaGetLastError(), "voxelize launch");
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_tile_sums, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt, w.tile_sums,
+                   w.ntiles);
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_scan, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt,
+                   (const int2*)w.tile_sums, w.ntiles, pillar_of_cell, coord, npts, w.pillar_start, w.pillar_cnt,
+                   num_pillars);
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
+                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr);
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,
+                   (const int*)w.csr, (const int*)w.pillar_start, (const int*)w.pillar_cnt,
+                   (const int*)num_pillars, pts);
+  return cuda_status(e, "voxelize launch");
 }
 
 }  // namespace pp
