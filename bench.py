@@ -81,13 +81,13 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (382.3e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
-    "cfg3-bf16": (84.5e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
+    "cfg2-fp32": (383.1e6, "3f4893d5eedd50e38688a9251a2098c5f6a60818202dacb19d837ad6aab5e4d2"),
+    "cfg3-bf16": (84.5e6, "3f4893d5eedd50e38688a9251a2098c5f6a60818202dacb19d837ad6aab5e4d2"),
 }
 # the same for the neck and head launches of one step (upsamplings + head)
 NECK_HEAD_TRAFFIC = {
-    "cfg2-fp32": (250.6e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
-    "cfg3-bf16": (42.3e6, "56414cc27cecb49de00b5413518874e70c319033757a574f7c0ae8a4a56db57b"),
+    "cfg2-fp32": (250.5e6, "3f4893d5eedd50e38688a9251a2098c5f6a60818202dacb19d837ad6aab5e4d2"),
+    "cfg3-bf16": (42.3e6, "3f4893d5eedd50e38688a9251a2098c5f6a60818202dacb19d837ad6aab5e4d2"),
 }
 
 
