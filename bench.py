@@ -105,15 +105,18 @@ def _conv_traffic(workload, table=None):
 def _front_end_roofline(g, stages, elt, peaks):
     """HBM roofline of the voxelise and scatter stages of one step: algorithmic bytes (per frame:
     voxelise reads 16 B per point, reads and writes the 4-byte count of every cell, writes 32
-    float4 points plus 8 B of coordinates per kept pillar; scatter reads 256 B of features per
-    kept pillar and writes the whole padded canvas) over the stage's device time."""
+    float4 points plus 8 B of coordinates per kept pillar; the incremental scatter reads 256 B of
+    features and 4 B of coordinates per kept pillar, writes its 64 channels and 4 B of drawn list,
+    and zeroes the 64 channels of every stale cell after reading its 4-byte drawn entry and cell
+    map entry; the dense scatter writes the whole padded canvas) over the stage's device time."""
     peak = float(peaks.get("hbm_gbs", 6800.0))
     G = g.nx * g.ny
     canvas_px = (g.nx + 2) * (g.ny + 2)  # elt: canvas bytes per channel (8 = split FP32)
     vox = sum(16 * n + 8 * G + (16 * 32 + 8) * p for n, p in zip(stages["_npoints"], stages["_npillars"]))
-    sca = sum(256 * p + 64 * canvas_px * elt for p in stages["_npillars"])
+    sca = stages["_scatter_bytes"]
+    dense = sum(256 * p + 64 * canvas_px * elt for p in stages["_npillars"])
     res = {"unit": "GB/s", "peak": peak, "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks else "fallback"}
-    for name, b in (("voxelize", vox), ("scatter", sca)):
+    for name, b in (("voxelize", vox), ("scatter", sca), ("scatter_dense", dense)):
         gbs = b / (stages[name] * 1e-3) / 1e9
         res[name] = {"bytes": int(b), "achieved": gbs, "frac": gbs / peak}
     return res
@@ -345,13 +348,20 @@ def _block_ends(bb):
 
 def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
     """Device time of the voxelise / PointNet / scatter stages for one step's batch of frames,
-    each stage captured in a CUDA graph (so that only the device work is timed) and replayed."""
-    fs = [frames_dev[j % len(frames_dev)] for j in range(batch)]
-    cap = max(int(f.shape[0]) for f in fs)
-    pts = torch.zeros((batch, cap, 4), dtype=torch.float32, device="cuda")
-    for j, f in enumerate(fs):
-        pts[j, :f.shape[0]] = f
-    n = torch.tensor([int(f.shape[0]) for f in fs], dtype=torch.int32, device="cuda")
+    each stage captured in a CUDA graph (so that only the device work is timed) and replayed.
+    The scatter the release unit runs is incremental (pp_scatter_update on a canvas that keeps
+    the previous frame): it is timed alternating between this step's frames and the next
+    step's, so every update zeroes the other set's stale cells; the dense pp_scatter is timed
+    beside it."""
+    def batch_of(shift):
+        fs = [frames_dev[(j + shift) % len(frames_dev)] for j in range(batch)]
+        cap = max(int(f.shape[0]) for f in fs)
+        pts = torch.zeros((batch, cap, 4), dtype=torch.float32, device="cuda")
+        for j, f in enumerate(fs):
+            pts[j, :f.shape[0]] = f
+        return fs, pts, torch.tensor([int(f.shape[0]) for f in fs], dtype=torch.int32, device="cuda")
+
+    (fs, pts, n), (_, pts2, n2) = batch_of(0), batch_of(1)
     pfn_w = torch.from_numpy(w[0]).cuda()
     pfn_ss = torch.from_numpy(pp.bn_fold(w[1])).cuda()
     side = torch.cuda.Stream()
@@ -359,14 +369,24 @@ def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
     with torch.cuda.stream(side):
         v = pp.voxelize(pts, n, g)
         feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], pfn_w, pfn_ss, g)
+        v2 = pp.voxelize(pts2, n2, g)
+        feat2 = pp.pointnet(v2["pts"], v2["npts"], v2["coord"], v2["num_pillars"], pfn_w, pfn_ss, g)
         canvas = pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec)
+        state = pp.ScatterState(g, batch, prec)
+        pp.scatter_update(state, feat, v["coord"], v["num_pillars"], v["pillar_of_cell"])
     torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
+
+    def update_pair():
+        pp.scatter_update(state, feat2, v2["coord"], v2["num_pillars"], v2["pillar_of_cell"])
+        pp.scatter_update(state, feat, v["coord"], v["num_pillars"], v["pillar_of_cell"])
+
     out = {}
-    for name, fn in (("voxelize", lambda: pp.voxelize(pts, n, g)),
-                     ("pointnet", lambda: pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
-                                                      pfn_w, pfn_ss, g)),
-                     ("scatter", lambda: pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec))):
+    for name, fn, per in (("voxelize", lambda: pp.voxelize(pts, n, g), 1),
+                          ("pointnet", lambda: pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
+                                                           pfn_w, pfn_ss, g), 1),
+                          ("scatter", update_pair, 2),
+                          ("scatter_dense", lambda: pp.scatter(feat, v["pillar_of_cell"], g, dtype=prec), 1)):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             keep = fn()  # noqa: F841  (outputs live in the graph's pool)
@@ -378,11 +398,19 @@ def _time_stages(pp, torch, g, frames_dev, w, prec, batch, reps=20):
             graph.replay()
         e1.record()
         torch.cuda.synchronize()
-        out[name] = e0.elapsed_time(e1) / reps
+        out[name] = e0.elapsed_time(e1) / reps / per
         del graph
     canvas_bytes = canvas.numel() * canvas.element_size()
     out["_npoints"] = [int(f.shape[0]) for f in fs]
     out["_npillars"] = [int(x) for x in v["num_pillars"].cpu()]
+    # algorithmic bytes of one incremental update, averaged over the two directions
+    elt = {pp.PP_BF16: 2, pp.PP_F32: 4, pp.PP_F32_TC: 8}[prec]
+    cells = [[set(x["coord"][j, :int(x["num_pillars"][j])].cpu().tolist()) for j in range(batch)] for x in (v, v2)]
+    upd = 0
+    for new, old in ((1, 0), (0, 1)):
+        for j in range(batch):
+            upd += len(cells[new][j]) * (256 + 8 + 64 * elt) + len(cells[old][j] - cells[new][j]) * (8 + 64 * elt)
+    out["_scatter_bytes"] = upd / 2
     return out, canvas_bytes, int(v["num_pillars"][0])
 
 

@@ -142,6 +142,20 @@ int pp_pointnet(const pp_geometry* g, int32_t batch, const float* pts, const int
 int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
                const int32_t* pillar_of_cell, void* canvas, int32_t dtype, void* stream);
 
+/* Stage 3, incremental: the same canvas as pp_scatter for a canvas that persists from frame to
+ * frame (a release unit's), writing only what changes: the cells drawn for the previous frame
+ * that hold no kept pillar now are zeroed, then every kept pillar p < num_pillars[b] is written
+ * at coord[b][p] (values, TF32 remainders for PP_F32_TC, or BF16 round to nearest even), and
+ * drawn[b][0..num_pillars[b]) / drawn_num[b] are set to this frame's cells.  Traffic is about
+ * 2 x pillars x 64 x element size instead of the whole canvas.  State (device memory the caller
+ * owns): canvas, drawn int32 [B][P] and drawn_num int32 [B]; start from a zero canvas (border
+ * included) and drawn_num = 0, and pass the same three with every frame of that batch row.
+ * Afterwards the canvas equals pp_scatter's for this frame, bit for bit.  coord, num_pillars,
+ * pillar_of_cell: pp_voxelize's outputs for the frame. */
+int pp_scatter_update(const pp_geometry* g, int32_t batch, const float* feat, const int32_t* coord,
+                      const int32_t* num_pillars, const int32_t* pillar_of_cell, int32_t* drawn,
+                      int32_t* drawn_num, void* canvas, int32_t dtype, void* stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Stage 4: one backbone layer, conv3x3 (zero pad 1, stride 1 or 2, no bias) + folded BN +    */
 /* ReLU, implicit GEMM over padded NHWC.                                                     */

@@ -171,6 +171,7 @@ _SIGS = {
     "pp_voxelize_static": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_pointnet": (ctypes.c_int, [_GP, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_scatter": (ctypes.c_int, [_GP, _I, _P, _P, _P, _I, _P]),
+    "pp_scatter_update": (ctypes.c_int, [_GP, _I, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
     "pp_conv3x3": (ctypes.c_int, [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I, _P]),
     "pp_conv_tile_count": (ctypes.c_int, [_I]),
     "pp_conv_packed_bytes": (_SZ, [_I, _I, _I]),
@@ -362,6 +363,31 @@ def scatter(feat, pillar_of_cell, geom, dtype=PP_F32, stream=None):
     _check(lib().pp_scatter(ctypes.byref(g), B, _ptr(feat), _ptr(pillar_of_cell), _ptr(canvas), dtype,
                             _stream(stream)))
     return canvas
+
+
+class ScatterState:
+    """A persistent canvas for pp_scatter_update (zero canvas, drawn lists, drawn counts)."""
+
+    def __init__(self, geom, batch, dtype=PP_F32, device="cuda"):
+        import torch
+        g = Geometry.of(geom)
+        self.geom, self.dtype = geom, dtype
+        tdt = torch.bfloat16 if dtype == PP_BF16 else torch.float32
+        shape = (batch, g.ny + 2, g.nx + 2, 64)
+        self.canvas = torch.zeros(((2,) if dtype == PP_F32_TC else ()) + shape, dtype=tdt, device=device)
+        self.drawn = torch.zeros((batch, g.max_pillars), dtype=torch.int32, device=device)
+        self.drawn_num = torch.zeros((batch,), dtype=torch.int32, device=device)
+
+
+def scatter_update(state, feat, coord, num_pillars, pillar_of_cell, stream=None):
+    """pp_scatter_update on ``state`` (a ScatterState); returns its canvas."""
+    _need_cuda(feat, coord, num_pillars, pillar_of_cell)
+    g = Geometry.of(state.geom)
+    B = int(feat.shape[0])
+    _check(lib().pp_scatter_update(ctypes.byref(g), B, _ptr(feat), _ptr(coord), _ptr(num_pillars),
+                                   _ptr(pillar_of_cell), _ptr(state.drawn), _ptr(state.drawn_num),
+                                   _ptr(state.canvas), state.dtype, _stream(stream)))
+    return state.canvas
 
 
 def pack_conv_weights(w_oihw, dtype, stream=None):

@@ -190,6 +190,22 @@ int pp_scatter(const pp_geometry* g, int32_t batch, const float* feat,
                         static_cast<cudaStream_t>(stream));
 }
 
+int pp_scatter_update(const pp_geometry* g, int32_t batch, const float* feat, const int32_t* coord,
+                      const int32_t* num_pillars, const int32_t* pillar_of_cell, int32_t* drawn,
+                      int32_t* drawn_num, void* canvas, int32_t dtype, void* stream) {
+  Geom gg;
+  int st = check_geometry(g, &gg);
+  if (st) return st;
+  if (batch <= 0 || batch > 4096) return fail(PP_EINVAL, "scatter_update: batch out of range");
+  if (dtype != PP_F32 && dtype != PP_BF16 && dtype != PP_F32_TC) return fail(PP_EINVAL, "scatter_update: bad dtype");
+  if (!feat || !coord || !num_pillars || !pillar_of_cell || !drawn || !drawn_num || !canvas)
+    return fail(PP_EINVAL, "scatter_update: NULL buffer");
+  if (!aligned16(feat) || !aligned16(canvas))
+    return fail(PP_EINVAL, "scatter_update: feat and canvas must be 16-byte aligned");
+  return scatter_update_launch(gg, batch, feat, coord, num_pillars, pillar_of_cell, drawn, drawn_num, canvas, dtype,
+                               static_cast<cudaStream_t>(stream));
+}
+
 int pp_tf32_split(const float* x, float* lo, int64_t n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !lo))) return fail(PP_EINVAL, "tf32_split: bad argument");
   if (n == 0) return PP_OK;

@@ -164,6 +164,76 @@ __global__ void bev_scatter_bf16(Geom g, int batch, const float4* __restrict__ f
   }
 }
 
+// Incremental scatter into a canvas that persists across frames (see pp_scatter_update).
+// Stale cells: cells drawn for the slot's previous frame that hold no kept pillar now; each
+// thread zeroes one 16-byte chunk of one (both planes of the split FP32 form).  Cells that hold
+// a pillar now are left to canvas_write, so the two kernels never touch the same cell.
+__device__ __forceinline__ size_t canvas_pixel(const Geom& g, int b, int cell) {
+  const int iy = cell / g.nx, ix = cell - iy * g.nx;
+  return ((size_t)b * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1;
+}
+
+__global__ void canvas_clear_stale(Geom g, int batch, int chunks, const int* __restrict__ pillar_of_cell,
+                                   const int* __restrict__ drawn, const int* __restrict__ drawn_num,
+                                   uint4* __restrict__ canvas, uint4* __restrict__ lo) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  const size_t total = (size_t)batch * g.P * chunks;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t % chunks);
+    const size_t q = t / chunks;
+    const int b = (int)(q / g.P), j = (int)(q % g.P);
+    if (j >= drawn_num[b]) continue;
+    const int c = drawn[q];
+    if (pillar_of_cell[(size_t)b * g.G + c] >= 0) continue;
+    const size_t off = canvas_pixel(g, b, c) * chunks + chunk;
+    canvas[off] = make_uint4(0u, 0u, 0u, 0u);
+    if (lo) lo[off] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// Writes every kept pillar's features at its cell (FP32 value + TF32 remainder plane, or BF16
+// round to nearest even) and records the cells drawn for this frame.
+__global__ void canvas_write(Geom g, int batch, int chunks, const float4* __restrict__ feat,
+                             const int* __restrict__ coord, const int* __restrict__ num_pillars,
+                             int* __restrict__ drawn, int* __restrict__ drawn_num, uint4* __restrict__ canvas,
+                             uint4* __restrict__ lo) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  const size_t total = (size_t)batch * g.P * chunks;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t % chunks);
+    const size_t q = t / chunks;
+    const int b = (int)(q / g.P), p = (int)(q % g.P);
+    const int n = num_pillars[b];
+    if (p == 0 && chunk == 0) drawn_num[b] = n;
+    if (p >= n) continue;
+    const int c = coord[q];
+    if (chunk == 0) drawn[q] = c;
+    const size_t off = canvas_pixel(g, b, c) * chunks + chunk;
+    if (chunks == 16) {  // FP32: 4 channels per chunk
+      const float4 v = feat[q * 16 + chunk];
+      canvas[off] = *reinterpret_cast<const uint4*>(&v);
+      if (lo) {
+        const float4 r = tf32_rem4(v);
+        lo[off] = *reinterpret_cast<const uint4*>(&r);
+      }
+    } else {             // BF16: 8 channels per chunk
+      const float4 a = feat[q * 16 + chunk * 2], d = feat[q * 16 + chunk * 2 + 1];
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(a.z, a.w);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(d.x, d.y);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(d.z, d.w);
+      uint4 val;
+      val.x = *reinterpret_cast<unsigned*>(&h0);
+      val.y = *reinterpret_cast<unsigned*>(&h1);
+      val.z = *reinterpret_cast<unsigned*>(&h2);
+      val.w = *reinterpret_cast<unsigned*>(&h3);
+      canvas[off] = val;
+    }
+  }
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -205,6 +275,27 @@ int scatter_launch(const Geom& g, int batch, const float* feat, const int* pilla
     e = launch_pdl(bev_scatter_bf16, dim3((unsigned)blocks), dim3(256), 0, s, g, batch, (const float4*)feat,
                    pillar_of_cell, (uint4*)canvas);
   return cuda_status(e, "scatter launch");
+}
+
+int scatter_update_launch(const Geom& g, int batch, const float* feat, const int* coord, const int* num_pillars,
+                          const int* pillar_of_cell, int* drawn, int* drawn_num, void* canvas, int dtype,
+                          cudaStream_t s, size_t plane) {
+  const int chunks = dtype == PP_BF16 ? 8 : 16;
+  const size_t pixels = (size_t)batch * (g.ny + 2) * (g.nx + 2);
+  uint4* cv = static_cast<uint4*>(canvas);
+  // the remainder plane follows the value plane (plane: floats per plane, default this batch's)
+  uint4* lo = dtype == PP_F32_TC ? cv + (plane ? plane / 4 : pixels * 16) : nullptr;
+  const size_t work = (size_t)batch * g.P * chunks;
+  size_t blocks = (work + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  cudaError_t e = launch_pdl(canvas_clear_stale, dim3((unsigned)blocks), dim3(256), 0, s, g, batch, chunks,
+                             pillar_of_cell, (const int*)drawn, (const int*)drawn_num, cv, lo);
+  if (e == cudaSuccess)
+    e = launch_pdl(canvas_write, dim3((unsigned)blocks), dim3(256), 0, s, g, batch, chunks, (const float4*)feat,
+                   coord, num_pillars, drawn, drawn_num, cv, lo);
+  return cuda_status(e, "scatter update launch");
 }
 
 int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s) {

@@ -1,6 +1,6 @@
 // Release unit: device buffers for up to B frames, the whole pillar front end as one launch
-// sequence (voxelise -> PointNet -> scatter -> conv3x3 layers), and one CUDA graph per batch
-// size 1..B so that a unit launch costs one cudaGraphLaunch.  Per-frame point counts live in
+// sequence (voxelise -> PointNet -> incremental scatter -> conv3x3 layers), and one CUDA graph per
+// batch size 1..B so that a unit launch costs one cudaGraphLaunch.  Per-frame point counts live in
 // device memory, so a graph replays any mix of uneven frames: grids are sized for the unit's
 // capacity and blocks past a frame's count exit at once.
 #include "pipeline.h"
@@ -230,6 +230,13 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   // split FP32 (3xTF32 convs): every conv operand carries its TF32 remainder plane
   const size_t planes = m->conv_dtype == PP_F32_TC ? 2 : 1;
   PP_ALLOC(canvas_, planes * B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt);
+  PP_ALLOC(drawn_, (size_t)B_ * g.P * sizeof(int));
+  PP_ALLOC(drawn_num_, (size_t)B_ * sizeof(int));
+  // the canvas is updated in place frame after frame: it starts zero with nothing drawn
+  if ((st = cuda_status(cudaMemsetAsync(canvas_, 0, planes * B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt, s),
+                        "clear canvas")))
+    return st;
+  if ((st = cuda_status(cudaMemsetAsync(drawn_num_, 0, (size_t)B_ * sizeof(int), s), "clear drawn"))) return st;
   for (const LayerSpec& L : m->layers) {
     void* a = nullptr;
     const size_t n = planes * B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
@@ -333,9 +340,11 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
                       pts_, vw_, s, tab_dev_->src);
   if (!st) st = pfn_launch(g, n, pts_, npts_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
   const bool split = m.conv_dtype == PP_F32_TC;
+  // the canvas keeps the slot's previous frame: zero its stale cells, write the new pillars
   if (!st)
-    st = scatter_launch(g, n, feat_, poc_, canvas_, split ? PP_F32_TC : m.precision, s,
-                        split ? (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 : 0);
+    st = scatter_update_launch(g, n, feat_, coord_, num_, poc_, drawn_, drawn_num_, canvas_,
+                               split ? PP_F32_TC : m.precision, s,
+                               split ? (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 : 0);
   const void* x = canvas_;
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];

@@ -99,7 +99,9 @@ class Pipeline {
   void* vox_ws_ = nullptr;
   VoxWork vw_{};
   float* feat_ = nullptr;
-  void* canvas_ = nullptr;
+  void* canvas_ = nullptr;   // persists across runs: updated in place (pp_scatter_update)
+  int* drawn_ = nullptr;     // [B][P] cells drawn into each slot's canvas by its last frame
+  int* drawn_num_ = nullptr; // [B]
   void* conv_ws_ = nullptr;  // stream-K workspace shared by the unit's (stream-ordered) convs
   size_t conv_ws_bytes_ = 0;
   std::vector<void*> act_;

@@ -93,6 +93,12 @@ int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s);
 // batch's plane size).
 int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,
                    void* canvas, int dtype, cudaStream_t s, size_t plane = 0);
+// Incremental scatter (pp_scatter_update): zero the stale cells of the previous frame, write the
+// new pillars, record them in drawn / drawn_num.  plane: floats per plane of a split FP32 canvas
+// (0 = batch-sized).
+int scatter_update_launch(const Geom& g, int batch, const float* feat, const int* coord, const int* num_pillars,
+                          const int* pillar_of_cell, int* drawn, int* drawn_num, void* canvas, int dtype,
+                          cudaStream_t s, size_t plane = 0);
 
 // ---- conv (conv_simt.cu, conv_tc.cu)
 struct ConvShape {

@@ -191,6 +191,29 @@ def test_scatter_batched_bf16_rounding():
         assert not inner[mask].any()
 
 
+@pytest.mark.parametrize("dtype", [pp.PP_F32, pp.PP_F32_TC, pp.PP_BF16])
+def test_scatter_update_sequence_equals_dense(dtype):
+    """pp_scatter_update on one persistent canvas over a sequence of frames (overlapping and
+    disjoint pillar sets, a frame whose row has no points, the full 4000-pillar cap, a repeat)
+    gives, after every frame, exactly pp_scatter's dense canvas (bit for bit, border included)."""
+    g = GEOM_SMALL
+    seq = [(config_points(3, 2, 40000), config_points(3, 3, 120000)),
+           (config_points(3, 4, 90000), config_points(3, 3, 120000)),
+           (config_points(3, 5, 2000), np.zeros((0, 4), np.float32)),
+           (config_points(3, 6, 150000), config_points(3, 7, 30000)),
+           (config_points(3, 6, 150000), config_points(3, 7, 30000))]
+    state = pp.ScatterState(g, 2, dtype)
+    for k, clouds in enumerate(seq):
+        pts, n = _batch(list(clouds))
+        v = pp.voxelize(pts, n, g)
+        feat = torch.randn((2, g.max_pillars, 64), device=DEV) * 3
+        got = pp.scatter_update(state, feat, v["coord"], v["num_pillars"], v["pillar_of_cell"])
+        want = pp.scatter(feat, v["pillar_of_cell"], g, dtype=dtype)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want), k
+        assert torch.equal(state.drawn_num.cpu(), v["num_pillars"].cpu()), k
+
+
 # ------------------------------------------------------------------ conv
 
 def _conv_case(B, H, W, cin, cout, s, seed, density=0.5):
