@@ -86,7 +86,9 @@ const char* pp_last_error(void);
 /* captured CUDA graph can be replayed with new counts; each value must be in [0, cap_points];*/
 /* a value outside that range makes the frame empty and sets the error word in the workspace  */
 /* (reported by pp_voxelize_check).                                                          */
-/* workspace: device scratch of pp_voxelize_workspace_bytes() bytes, 256-byte aligned.        */
+/* workspace: device scratch of pp_voxelize_workspace_bytes() bytes, 256-byte aligned; its   */
+/* first 256 bytes (the error word) must be zero before the first call; the rest needs no   */
+/* initialisation.                                                                          */
 size_t pp_voxelize_workspace_bytes(const pp_geometry* g, int32_t batch, int32_t cap_points);
 int pp_voxelize(const pp_geometry* g, int32_t batch, int32_t cap_points,
                 const float* points, const int32_t* n_points,
@@ -96,6 +98,18 @@ int pp_voxelize(const pp_geometry* g, int32_t batch, int32_t cap_points,
 /* Synchronises `stream`, then reads the workspace's error word: PP_OK or PP_EINVAL (a
  * n_points value was out of range). */
 int pp_voxelize_check(const void* workspace, void* stream);
+
+/* pp_voxelize followed by pp_pointnet as a release unit runs them: the point selection is fused
+ * into the PointNet kernel (each warp picks its pillar's 32 lowest point indices and loads the
+ * points straight into registers), so there is no pts output and the gathered points never go
+ * through memory.  Arguments as for the two calls (pfn_w, scale_shift, feat as pp_pointnet's);
+ * every output, feat included, is bit-identical to pp_voxelize + pp_pointnet on the same input.
+ * Workspace: pp_voxelize_workspace_bytes(); pp_voxelize_check reads its error word. */
+int pp_voxelize_pointnet(const pp_geometry* g, int32_t batch, int32_t cap_points, const float* points,
+                         const int32_t* n_points, int32_t* cell, uint32_t* cnt, int32_t* pillar_of_cell,
+                         int32_t* coord, int32_t* npts, int32_t* num_pillars, const float* pfn_w,
+                         const float* scale_shift, float* feat, void* workspace, size_t workspace_bytes,
+                         void* stream);
 
 /* Same operation and outputs as pp_voxelize, for callers that cannot allocate device memory:
  * the paper has no counterpart; this entry point exists for deployments such as real-time

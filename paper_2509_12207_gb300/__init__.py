@@ -168,6 +168,7 @@ _SIGS = {
     "pp_voxelize_workspace_bytes": (_SZ, [_GP, _I, _I]),
     "pp_voxelize": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "pp_voxelize_check": (ctypes.c_int, [_P, _P]),
+    "pp_voxelize_pointnet": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "pp_voxelize_static": (ctypes.c_int, [_GP, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_pointnet": (ctypes.c_int, [_GP, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "pp_scatter": (ctypes.c_int, [_GP, _I, _P, _P, _P, _I, _P]),
@@ -296,14 +297,40 @@ def voxelize(points, n_points, geom, stream=None) -> Dict[str, object]:
         "pts": torch.empty((B, P, 32, 4), dtype=torch.float32, device=dev),
     }
     ws_bytes = lib().pp_voxelize_workspace_bytes(ctypes.byref(g), B, cap)
-    ws = torch.zeros(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
     off = (-ws.data_ptr()) % 256
     ws_ptr = ws.data_ptr() + off
+    ws[off:off + 256].zero_()  # the error word; the rest needs no initialisation
     s = _stream(stream)
     _check(lib().pp_voxelize(ctypes.byref(g), B, cap, _ptr(points), _ptr(n_points), _ptr(out["cell"]),
                              _ptr(out["cnt"]), _ptr(out["pillar_of_cell"]), _ptr(out["coord"]),
                              _ptr(out["npts"]), _ptr(out["num_pillars"]), _ptr(out["pts"]),
                              ws_ptr, ws_bytes, s))
+    out["_workspace"] = (ws, ws_ptr)
+    return out
+
+
+def voxelize_pointnet(points, n_points, geom, pfn_w, scale_shift, stream=None) -> Dict[str, object]:
+    """pp_voxelize_pointnet: pp_voxelize's outputs without pts, plus "feat" [B, P, 64]."""
+    import torch
+    _need_cuda(points, n_points, pfn_w, scale_shift)
+    g = Geometry.of(geom)
+    B, cap = int(points.shape[0]), int(points.shape[1])
+    dev = points.device
+    G, P = g.nx * g.ny, g.max_pillars
+    out = {k: torch.empty(shape, dtype=torch.int32, device=dev) for k, shape in
+           (("cell", (B, cap)), ("cnt", (B, G)), ("pillar_of_cell", (B, G)), ("coord", (B, P)),
+            ("npts", (B, P)), ("num_pillars", (B,)))}
+    out["feat"] = torch.empty((B, P, 64), dtype=torch.float32, device=dev)
+    ws_bytes = lib().pp_voxelize_workspace_bytes(ctypes.byref(g), B, cap)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    off = (-ws.data_ptr()) % 256
+    ws_ptr = ws.data_ptr() + off
+    ws[off:off + 256].zero_()  # the error word; the rest needs no initialisation
+    _check(lib().pp_voxelize_pointnet(ctypes.byref(g), B, cap, _ptr(points), _ptr(n_points), _ptr(out["cell"]),
+                                      _ptr(out["cnt"]), _ptr(out["pillar_of_cell"]), _ptr(out["coord"]),
+                                      _ptr(out["npts"]), _ptr(out["num_pillars"]), _ptr(pfn_w), _ptr(scale_shift),
+                                      _ptr(out["feat"]), ws_ptr, ws_bytes, _stream(stream)))
     out["_workspace"] = (ws, ws_ptr)
     return out
 

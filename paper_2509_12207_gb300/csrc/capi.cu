@@ -146,6 +146,32 @@ int pp_voxelize(const pp_geometry* g, int32_t batch, int32_t cap_points, const f
                     reinterpret_cast<float4*>(pts), w, static_cast<cudaStream_t>(stream));
 }
 
+int pp_voxelize_pointnet(const pp_geometry* g, int32_t batch, int32_t cap_points, const float* points,
+                         const int32_t* n_points, int32_t* cell, uint32_t* cnt, int32_t* pillar_of_cell,
+                         int32_t* coord, int32_t* npts, int32_t* num_pillars, const float* pfn_w,
+                         const float* scale_shift, float* feat, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+  Geom gg;
+  int st = check_geometry(g, &gg);
+  if (st) return st;
+  if (batch <= 0 || batch > 4096 || cap_points < 0 || cap_points > (1 << 27))
+    return fail(PP_EINVAL, "voxelize_pointnet: batch or cap_points out of range");
+  if (!n_points || !cnt || !pillar_of_cell || !coord || !npts || !num_pillars || !pfn_w || !scale_shift ||
+      !feat || !workspace || (cap_points > 0 && (!points || !cell)))
+    return fail(PP_EINVAL, "voxelize_pointnet: NULL buffer");
+  if (!aligned16(points) || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return fail(PP_EINVAL, "voxelize_pointnet: points need 16-byte, workspace 256-byte alignment");
+  if (workspace_bytes < vox_workspace_bytes(gg, batch, cap_points))
+    return fail(PP_EINVAL, "voxelize_pointnet: workspace too small");
+  VoxWork w = vox_carve(workspace, gg, batch, cap_points);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float4* p4 = reinterpret_cast<const float4*>(points);
+  st = vox_launch(gg, batch, cap_points, p4, n_points, cell, cnt, pillar_of_cell, coord, npts, num_pillars,
+                  nullptr, w, s);
+  if (st) return st;
+  return select_pfn_launch(gg, batch, cap_points, p4, nullptr, w, coord, num_pillars, pfn_w, scale_shift, feat, s);
+}
+
 int pp_voxelize_check(const void* workspace, void* stream) {
   if (!workspace) return fail(PP_EINVAL, "voxelize_check: NULL workspace");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

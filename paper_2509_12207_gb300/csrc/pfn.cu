@@ -5,17 +5,32 @@
 // (pillar mean by warp shuffles), then lane c owns channels c and c+32 and runs
 // Linear(9->64) + folded BN + ReLU over the valid points, keeping a running max in registers.
 // The 9x64 weights and the BN scale/shift are staged in shared memory once per block.
+// pfn_select_fused (a release unit's path): the same, with the voxeliser's point selection
+// done by the warp itself (sort of the pillar's point indices, point loaded into lane j).
 //
 // bev_scatter: a single gather pass over the whole padded canvas -- every 16-byte chunk of every
 // pixel is written exactly once (feature row of the pillar at that cell, zeros elsewhere and on
 // the border), so no separate clear is needed and all stores are coalesced 16-byte vectors.
-#include "pp_internal.h"
+#include "pillar_dev.cuh"
 
 namespace pp {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;
+
+// Stages the 9x64 weights (transposed) and the folded BN in shared memory.
+__device__ __forceinline__ void pfn_stage_weights(const float* pfn_w, const float* ss, float (*w_s)[64], float* sc_s,
+                                                  float* sh_s) {
+  for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
+    const int c = i / 9, k = i % 9;
+    w_s[k][c] = pfn_w[i];
+  }
+  if (threadIdx.x < 64) {
+    sc_s[threadIdx.x] = ss[threadIdx.x];
+    sh_s[threadIdx.x] = ss[64 + threadIdx.x];
+  }
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restrict__ pts,
                                                  const int* __restrict__ npts,
@@ -28,15 +43,7 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
   __shared__ float w_s[9][64];          // transposed: w_s[k][c] = W[c][k]
   __shared__ float sc_s[64], sh_s[64];
   __shared__ float f_s[kWarps][32][10];  // features per point (+1 pad)
-  for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
-    const int c = i / 9, k = i % 9;
-    w_s[k][c] = pfn_w[i];
-  }
-  if (threadIdx.x < 64) {
-    sc_s[threadIdx.x] = ss[threadIdx.x];
-    sh_s[threadIdx.x] = ss[64 + threadIdx.x];
-  }
-  __syncthreads();
+  pfn_stage_weights(pfn_w, ss, w_s, sc_s, sh_s);
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = num_pillars[b];
@@ -44,43 +51,44 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
   // follows), so the weights staged above serve several pillars
   for (int p = blockIdx.x * kWarps + wid; p < np; p += gridDim.x * kWarps) {
     const size_t q = (size_t)b * g.P + p;
-    const int n = npts[q];
-    const float4 v = pts[q * 32 + lane];
-    const bool valid = lane < n;
-    float sx = valid ? v.x : 0.f, sy = valid ? v.y : 0.f, sz = valid ? v.z : 0.f;
-    for (int o = 16; o; o >>= 1) {
-      sx += __shfl_xor_sync(kFull, sx, o);
-      sy += __shfl_xor_sync(kFull, sy, o);
-      sz += __shfl_xor_sync(kFull, sz, o);
-    }
-    const float inv = 1.f / (float)n;
-    const float mx = sx * inv, my = sy * inv, mz = sz * inv;
-    const int cell = coord[q];
-    const int ix = cell % g.nx, iy = cell / g.nx;
-    const float xc = g.xmin + ((float)ix + 0.5f) * g.vx;
-    const float yc = g.ymin + ((float)iy + 0.5f) * g.vy;
-    float* f = f_s[wid][lane];
-    f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
-    f[4] = v.x - mx; f[5] = v.y - my; f[6] = v.z - mz;
-    f[7] = v.x - xc; f[8] = v.y - yc;
-    __syncwarp();
-    const float s0 = sc_s[lane], s1 = sc_s[lane + 32];
-    const float h0 = sh_s[lane], h1 = sh_s[lane + 32];
-    float m0 = 0.f, m1 = 0.f;  // ReLU outputs are >= 0 and every pillar has >= 1 point
-    for (int j = 0; j < n; ++j) {
-      const float* fj = f_s[wid][j];
-      float a0 = 0.f, a1 = 0.f;
-  #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        a0 = fmaf(fj[k], w_s[k][lane], a0);
-        a1 = fmaf(fj[k], w_s[k][lane + 32], a1);
-      }
-      m0 = fmaxf(m0, fmaxf(fmaf(a0, s0, h0), 0.f));
-      m1 = fmaxf(m1, fmaxf(fmaf(a1, s1, h1), 0.f));
-    }
+    float m0, m1;
+    dev::pfn_pillar(g, pts[q * 32 + lane], npts[q], coord[q], lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
     feat[q * 64 + lane] = m0;
     feat[q * 64 + lane + 32] = m1;
-    __syncwarp();  // f_s[wid] is rewritten by the next pillar
+  }
+}
+
+// Point selection fused with PointNet (the release unit's path): each warp sorts its pillar's
+// point indices (the 32 lowest, as vox_select does), loads lane j's point straight into a
+// register and runs the pillar's PointNet, so the gathered points never go through memory.
+__global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const float4* __restrict__ points,
+                                                        const float4* const* __restrict__ srcs,
+                                                        const int* __restrict__ csr,
+                                                        const int* __restrict__ pillar_start,
+                                                        const int* __restrict__ pillar_cnt,
+                                                        const int* __restrict__ coord,
+                                                        const int* __restrict__ num_pillars,
+                                                        const float* __restrict__ pfn_w,
+                                                        const float* __restrict__ ss,
+                                                        float* __restrict__ feat) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  __shared__ float w_s[9][64];
+  __shared__ float sc_s[64], sh_s[64];
+  __shared__ float f_s[kWarps][32][10];
+  pfn_stage_weights(pfn_w, ss, w_s, sc_s, sh_s);
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int np = num_pillars[b];
+  const float4* src = dev::frame_src(points, srcs, b, cap);
+  for (int p = blockIdx.x * kWarps + wid; p < np; p += gridDim.x * kWarps) {
+    const size_t q = (size_t)b * g.P + p;
+    const int count = pillar_cnt[q];
+    const int best = dev::lowest_32(csr + (size_t)b * cap + pillar_start[q], count, lane);
+    const float4 v = lane < count ? src[best] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float m0, m1;
+    dev::pfn_pillar(g, v, count < 32 ? count : 32, coord[q], lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
+    feat[q * 64 + lane] = m0;
+    feat[q * 64 + lane + 32] = m1;
   }
 }
 
@@ -257,6 +265,18 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
   return cuda_status(launch_pdl(pfn_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, pts, npts,
                                 coord, num_pillars, pfn_w, ss, feat),
                      "pointnet launch");
+}
+
+int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
+                      const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
+                      const float* ss, float* feat, cudaStream_t s) {
+  int bx = (g.P + kWarps - 1) / kWarps;
+  const int bx_max = (4 * sm_count() + batch - 1) / batch;
+  if (bx > bx_max) bx = bx_max;
+  return cuda_status(launch_pdl(pfn_select_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, cap,
+                                points, srcs, (const int*)w.csr, (const int*)w.pillar_start,
+                                (const int*)w.pillar_cnt, coord, num_pillars, pfn_w, ss, feat),
+                     "select + pointnet launch");
 }
 
 int scatter_launch(const Geom& g, int batch, const float* feat, const int* pillar_of_cell,

@@ -1,8 +1,8 @@
 // Release unit: device buffers for up to B frames, the whole pillar front end as one launch
-// sequence (voxelise -> PointNet -> incremental scatter -> conv3x3 layers), and one CUDA graph per
-// batch size 1..B so that a unit launch costs one cudaGraphLaunch.  Per-frame point counts live in
-// device memory, so a graph replays any mix of uneven frames: grids are sized for the unit's
-// capacity and blocks past a frame's count exit at once.
+// sequence (voxelise -> point selection + PointNet -> incremental scatter -> conv3x3 layers), and
+// one CUDA graph per batch size 1..B so that a unit launch costs one cudaGraphLaunch.  Per-frame
+// point counts live in device memory, so a graph replays any mix of uneven frames: grids are
+// sized for the unit's capacity and blocks past a frame's count exit at once.
 #include "pipeline.h"
 
 #include <algorithm>
@@ -224,7 +224,6 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   PP_ALLOC(coord_, (size_t)B_ * g.P * sizeof(int));
   PP_ALLOC(npts_, (size_t)B_ * g.P * sizeof(int));
   PP_ALLOC(num_, (size_t)B_ * sizeof(int));
-  PP_ALLOC(pts_, (size_t)B_ * g.P * 32 * sizeof(float4));
   PP_ALLOC(vox_ws_, vox_workspace_bytes(g, B_, cap_));
   PP_ALLOC(feat_, (size_t)B_ * g.P * 64 * sizeof(float));
   // split FP32 (3xTF32 convs): every conv operand carries its TF32 remainder plane
@@ -336,9 +335,11 @@ void Pipeline::release() {
 int Pipeline::enqueue(int n, cudaStream_t s) {
   const Model& m = *m_;
   const Geom& g = m.g;
+  // voxelise up to the bucketing; point selection runs fused into PointNet
   int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
-                      pts_, vw_, s, tab_dev_->src);
-  if (!st) st = pfn_launch(g, n, pts_, npts_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
+                      nullptr, vw_, s, tab_dev_->src);
+  if (!st)
+    st = select_pfn_launch(g, n, cap_, points_, tab_dev_->src, vw_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
   const bool split = m.conv_dtype == PP_F32_TC;
   // the canvas keeps the slot's previous frame: zero its stale cells, write the new pillars
   if (!st)

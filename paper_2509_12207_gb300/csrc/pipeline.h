@@ -95,7 +95,6 @@ class Pipeline {
   int sms_ = 1;
   int *cell_ = nullptr, *poc_ = nullptr, *coord_ = nullptr, *npts_ = nullptr, *num_ = nullptr;
   unsigned* cnt_ = nullptr;
-  float4* pts_ = nullptr;
   void* vox_ws_ = nullptr;
   VoxWork vw_{};
   float* feat_ = nullptr;

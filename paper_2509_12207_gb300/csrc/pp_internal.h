@@ -78,6 +78,8 @@ size_t vox_workspace_bytes(const Geom& g, int batch, int cap);
 VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
 // srcs: optional device table of per-frame point pointers (frame b reads srcs[b][0..n));
 // NULL = frame b is row b of `points` ([batch][cap]).
+// pts == NULL: stop after the bucket step (the caller runs select_pfn_launch, which gathers
+// each pillar's points itself).
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
                int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
@@ -87,6 +89,11 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,
                const int* num_pillars, const float* pfn_w, const float* scale_shift,
                float* feat, cudaStream_t s);
+// Point selection + PointNet in one launch, from the voxelisation workspace (csr, pillar
+// start / count) of the same batch: feat as pfn_launch computes it, without the pts buffer.
+int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
+                      const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
+                      const float* ss, float* feat, cudaStream_t s);
 // lo[i] = TF32 remainder of x[i] (x, lo 16-byte aligned when n >= 4).
 int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s);
 // PP_F32_TC: `plane` = elements between the canvas's value and remainder planes (0 = this

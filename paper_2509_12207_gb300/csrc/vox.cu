@@ -13,16 +13,17 @@
 //   4. vox_bucket       point i -> csr[pillar_start + slot]: points grouped by kept pillar
 //   5. vox_select       one warp per pillar: the 32 smallest point indices of its group, sorted
 //                       by warp bitonic sort/merge, gathered into pts (zero padded)
+// A release unit stops after step 4: its PointNet kernel does step 5 itself (pfn.cu,
+// pfn_select_fused), so the gathered points stay in registers.
 // Nothing depends on the order in which atomics land, so the output is bit-identical across
 // runs.  The cell index follows the binary32 contract of pp.h (__fsub_rn / __fdiv_rn, floorf).
-#include "pp_internal.h"
-
-#include <climits>
+#include "pillar_dev.cuh"
 
 namespace pp {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using dev::frame_src;
+constexpr unsigned kFull = dev::kFullMask;
 
 __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap, int* err) {
   int n = n_points[b];
@@ -33,11 +34,6 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
   return n;
 }
 
-// Frame b's points: srcs[b] when a per-frame pointer table is given, else row b of the batch.
-__device__ __forceinline__ const float4* frame_src(const float4* points,
-                                                   const float4* const* srcs, int b, int cap) {
-  return srcs ? srcs[b] : points + (size_t)b * cap;
-}
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
@@ -212,30 +208,6 @@ __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
   }
 }
 
-// Ascending bitonic sort of one int per lane across a warp.
-__device__ __forceinline__ int warp_sort(int v, int lane) {
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int o = __shfl_xor_sync(kFull, v, j);
-      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-      v = keep_min ? min(v, o) : max(v, o);
-    }
-  }
-  return v;
-}
-
-// Sorts a bitonic sequence held one per lane into ascending order.
-__device__ __forceinline__ int warp_bitonic_merge(int v, int lane) {
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1) {
-    const int o = __shfl_xor_sync(kFull, v, j);
-    v = (lane & j) == 0 ? min(v, o) : max(v, o);
-  }
-  return v;
-}
-
 __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
                                                   const float4* __restrict__ points,
                                                   const float4* const* __restrict__ srcs,
@@ -252,12 +224,7 @@ __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
   const size_t q = (size_t)b * g.P + p;
   const int count = pillar_cnt[q];
   const int* seg = csr + (size_t)b * cap + pillar_start[q];
-  int best = warp_sort(lane < count ? seg[lane] : INT_MAX, lane);
-  for (int k = 32; k < count; k += 32) {
-    int v = warp_sort(k + lane < count ? seg[k + lane] : INT_MAX, lane);
-    v = __shfl_sync(kFull, v, 31 - lane);          // reversed: best ++ v is bitonic
-    best = warp_bitonic_merge(min(best, v), lane);  // lower half = 32 smallest of the union
-  }
+  const int best = dev::lowest_32(seg, count, lane);
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
   if (lane < count) out = frame_src(points, srcs, b, cap)[best];
   pts[q * 32 + lane] = out;
@@ -323,7 +290,7 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   if (e == cudaSuccess)
     e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
                    (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && pts)
     e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,
                    (const int*)w.csr, (const int*)w.pillar_start, (const int*)w.pillar_cnt,
                    (const int*)num_pillars, pts);

@@ -191,6 +191,31 @@ def test_scatter_batched_bf16_rounding():
         assert not inner[mask].any()
 
 
+def test_voxelize_pointnet_fused_equals_stages():
+    """The release unit's fused point selection + PointNet gives, bit for bit, pp_voxelize +
+    pp_pointnet's outputs (crowded clustered pillars that need the sort's merge steps, a short
+    frame, an empty row)."""
+    g = GEOM_FULL
+    w = pillar_weights(BACKBONE_SMALL, 7)
+    pfn_w = torch.from_numpy(w[0]).to(DEV)
+    ss = torch.from_numpy(pp.bn_fold(w[1])).to(DEV)
+    clouds = [clustered_cloud(120000, 5), config_points(1, 0), np.zeros((0, 4), np.float32)]
+    pts, n = _batch(clouds)
+    v = pp.voxelize(pts, n, g)
+    feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"], pfn_w, ss, g)
+    f = pp.voxelize_pointnet(pts, n, g, pfn_w, ss)
+    torch.cuda.synchronize()
+    for k in ("pillar_of_cell", "num_pillars"):
+        assert torch.equal(f[k], v[k]), k
+    for b in range(3):
+        assert torch.equal(f["cell"][b, :len(clouds[b])], v["cell"][b, :len(clouds[b])])   # rows past n unwritten
+        num = int(v["num_pillars"][b])
+        assert torch.equal(f["coord"][b, :num], v["coord"][b, :num])
+        assert torch.equal(f["npts"][b, :num], v["npts"][b, :num])
+        assert torch.equal(f["feat"][b, :num], feat[b, :num]), b
+    assert int(v["npts"][0, :int(v["num_pillars"][0])].max()) == 32   # crowded pillars were exercised
+
+
 @pytest.mark.parametrize("dtype", [pp.PP_F32, pp.PP_F32_TC, pp.PP_BF16])
 def test_scatter_update_sequence_equals_dense(dtype):
     """pp_scatter_update on one persistent canvas over a sequence of frames (overlapping and
