@@ -35,6 +35,10 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
 }
 
 
+// Points per thread per pass of the point kernels: their loads (and atomics) are issued
+// together so that one memory round trip covers several points.
+constexpr int kVoxU = 4;
+
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
                                const int* __restrict__ n_points, int* __restrict__ cell,
@@ -43,32 +47,53 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, err);
   const float4* src = frame_src(points, srcs, b, cap);
-  // grid-stride over the frame's points (block-uniform trip count: whole warps stay together)
-  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-    const int i = i0 + threadIdx.x;
-    const size_t row = (size_t)b * cap + i;
-    int c = -1;
-    if (i < n) {
-      const float4 p = src[i];
-      bool ok = p.x >= g.xmin && p.x < g.xmax && p.y >= g.ymin && p.y < g.ymax &&
-                p.z >= g.zmin && p.z < g.zmax;
-      if (ok) {
-        const float qx = floorf(__fdiv_rn(__fsub_rn(p.x, g.xmin), g.vx));
-        const float qy = floorf(__fdiv_rn(__fsub_rn(p.y, g.ymin), g.vy));
-        ok = qx >= 0.f && qx < (float)g.nx && qy >= 0.f && qy < (float)g.ny;
-        if (ok) c = (int)qy * g.nx + (int)qx;
-      }
-      cell[row] = c;
+  const int lane = threadIdx.x & 31;
+  unsigned* cnt_b = cnt + (size_t)b * g.G;
+  // grid-stride over the frame's points, kVoxU coalesced blocks of blockDim.x points per pass
+  // (block-uniform trip count: whole warps stay together)
+  for (int i0 = blockIdx.x * blockDim.x * kVoxU; i0 < n; i0 += gridDim.x * blockDim.x * kVoxU) {
+    float4 p[kVoxU];
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) {
+      const int i = i0 + u * blockDim.x + threadIdx.x;
+      p[u] = i < n ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const unsigned valid = __ballot_sync(kFull, c >= 0);
-    if (c >= 0) {
-      const int lane = threadIdx.x & 31;
-      const unsigned peers = __match_any_sync(valid, c);
-      const int leader = __ffs(peers) - 1;
-      unsigned base = 0;
-      if (lane == leader) base = atomicAdd(&cnt[(size_t)b * g.G + c], (unsigned)__popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      slot[row] = (int)base + __popc(peers & ((1u << lane) - 1u));
+    int c[kVoxU];
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) {
+      const int i = i0 + u * blockDim.x + threadIdx.x;
+      c[u] = -1;
+      if (i < n) {
+        bool ok = p[u].x >= g.xmin && p[u].x < g.xmax && p[u].y >= g.ymin && p[u].y < g.ymax &&
+                  p[u].z >= g.zmin && p[u].z < g.zmax;
+        if (ok) {
+          const float qx = floorf(__fdiv_rn(__fsub_rn(p[u].x, g.xmin), g.vx));
+          const float qy = floorf(__fdiv_rn(__fsub_rn(p[u].y, g.ymin), g.vy));
+          ok = qx >= 0.f && qx < (float)g.nx && qy >= 0.f && qy < (float)g.ny;
+          if (ok) c[u] = (int)qy * g.nx + (int)qx;
+        }
+        cell[(size_t)b * cap + i] = c[u];
+      }
+    }
+    // warp-aggregated counting: lanes with the same cell elect the lowest as leader, which adds
+    // their number to the cell's count; the old count is the group's first arrival slot
+    unsigned peers[kVoxU], base[kVoxU];
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) {
+      const unsigned valid = __ballot_sync(kFull, c[u] >= 0);
+      peers[u] = 0u;
+      base[u] = 0u;
+      if (c[u] >= 0) {
+        peers[u] = __match_any_sync(valid, c[u]);
+        if (lane == __ffs(peers[u]) - 1) base[u] = atomicAdd(&cnt_b[c[u]], (unsigned)__popc(peers[u]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) {
+      if (c[u] < 0) continue;
+      const unsigned first = __shfl_sync(peers[u], base[u], __ffs(peers[u]) - 1);
+      const int i = i0 + u * blockDim.x + threadIdx.x;
+      slot[(size_t)b * cap + i] = (int)first + __popc(peers[u] & ((1u << lane) - 1u));
     }
   }
 }
@@ -198,13 +223,21 @@ __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, nullptr);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const size_t row = (size_t)b * cap + i;
-    const int c = cell[row];
-    if (c < 0) continue;
-    const int p = pillar_of_cell[(size_t)b * g.G + c];
-    if (p < 0) continue;
-    csr[(size_t)b * cap + pillar_start[(size_t)b * g.P + p] + slot[row]] = i;
+  const size_t rb = (size_t)b * cap;
+  // kVoxU points per thread per pass, each dependent load issued for all of them at once
+  for (int i0 = blockIdx.x * blockDim.x * kVoxU; i0 < n; i0 += gridDim.x * blockDim.x * kVoxU) {
+    int c[kVoxU], sl[kVoxU], p[kVoxU];
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) {
+      const int i = i0 + u * blockDim.x + threadIdx.x;
+      c[u] = i < n ? cell[rb + i] : -1;
+      sl[u] = i < n ? slot[rb + i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) p[u] = c[u] >= 0 ? pillar_of_cell[(size_t)b * g.G + c[u]] : -1;
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u)
+      if (p[u] >= 0) csr[rb + pillar_start[(size_t)b * g.P + p[u]] + sl[u]] = i0 + u * blockDim.x + threadIdx.x;
   }
 }
 
@@ -273,7 +306,7 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       sms = 152;
   }
-  int px = (cap + 255) / 256;
+  int px = (cap + 256 * kVoxU - 1) / (256 * kVoxU);
   const int px_max = (8 * sms + batch - 1) / batch;
   if (px > px_max) px = px_max;
   const dim3 pg(px > 0 ? px : 1, batch);
