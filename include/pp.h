@@ -449,6 +449,20 @@ int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_
 int pp_submit_frames(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
                      const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
                      const double* abs_deadline_us, uint64_t* frame_ids_out, int32_t* n_admitted);
+/* pp_submit_frames with a host output buffer per frame: host_out[i] (host array of n pointers,
+ * may be NULL, entries may be NULL) is page-locked host memory of pp_result_bytes() bytes for
+ * the frame's precision, 16-byte aligned, borrowed until the frame is polled.  The unit's
+ * result copy writes the frame's final output (the out_dev map: last backbone block, or the
+ * head) there over the host link as part of the same launch, so a caller that wants its result
+ * on the host needs no copy of its own (pp_result.out_host).  Other host memory: PP_EINVAL,
+ * nothing admitted.  Ignored for synthetic-load chains. */
+int pp_submit_frames_ex(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
+                        const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
+                        const double* abs_deadline_us, void* const* host_out, uint64_t* frame_ids_out,
+                        int32_t* n_admitted);
+/* Bytes of one frame's final output (padded NHWC, out_dev's map) at `precision` (0 if that
+ * precision is not enabled). */
+size_t pp_result_bytes(pp_ctx* ctx, int32_t precision);
 
 typedef struct {
   uint64_t frame_id;
@@ -468,6 +482,9 @@ typedef struct {
   /* 0's size, out_c = head_outputs rounded up to 64 (channels past out_valid_c are 0), and the */
   /* block outputs are not kept (block_dev NULL); without one out_valid_c = out_c.              */
   int32_t out_valid_c;
+  /* frames submitted with a host output buffer (pp_submit_frames_ex): that buffer, holding a  */
+  /* copy of out_dev ([out_h+2][out_w+2][out_c]), complete when the frame is polled; else NULL */
+  const void* out_host;
 } pp_result;
 
 /* Drains up to `max` completed frames into out[]; waits up to timeout_us for the first one

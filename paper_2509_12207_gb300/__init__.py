@@ -94,6 +94,7 @@ class Result(ctypes.Structure):
         ("block_dev", ctypes.c_void_p * MAX_BLOCKS), ("block_c", ctypes.c_int32 * MAX_BLOCKS),
         ("block_h", ctypes.c_int32 * MAX_BLOCKS), ("block_w", ctypes.c_int32 * MAX_BLOCKS),
         ("out_valid_c", ctypes.c_int32),
+        ("out_host", ctypes.c_void_p),
     ]
 
 
@@ -209,6 +210,11 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int64), _I, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int32)]),
+    "pp_submit_frames_ex": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_int64), _I, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)]),
+    "pp_result_bytes": (_SZ, [_P, _I]),
     "pp_result_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "pp_result_release_many": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "pp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
@@ -671,10 +677,12 @@ class Context:
             _check(rc)
         return rc, int(fid.value)
 
-    def submit_many(self, chain_ids, frames, t_arrival_us=None, abs_deadlines_us=None):
+    def submit_many(self, chain_ids, frames, t_arrival_us=None, abs_deadlines_us=None, host_out=None):
         """Submits frames that arrive together (one pp_submit_frames call): ``frames`` are all
         CUDA tensors [N, 4] (borrowed), all pinned CPU tensors (borrowed, read in place) or all
-        host arrays (copied).  Returns (status, ids of the admitted frames, in order)."""
+        host arrays (copied).  ``host_out``: optional list of pinned CPU tensors (each at least
+        result_bytes(precision) bytes, or None) that receive each frame's outputs
+        (pp_submit_frames_ex).  Returns (status, ids of the admitted frames, in order)."""
         n = len(frames)
         t = now_us() if t_arrival_us is None else t_arrival_us
         mode = _points_mode(frames[0]) if n else PP_POINTS_HOST
@@ -692,10 +700,18 @@ class Context:
         dls = (ctypes.c_double * n)(*abs_deadlines_us) if abs_deadlines_us is not None else None
         ids = (ctypes.c_uint64 * n)()
         got = ctypes.c_int32(0)
-        rc = lib().pp_submit_frames(self.h, n, cids, parr, cnt, mode, t, dls, ids, ctypes.byref(got))
+        if host_out is None:
+            rc = lib().pp_submit_frames(self.h, n, cids, parr, cnt, mode, t, dls, ids, ctypes.byref(got))
+        else:
+            hout = (ctypes.c_void_p * n)(*[(_ptr(x) if x is not None else None) for x in host_out])
+            rc = lib().pp_submit_frames_ex(self.h, n, cids, parr, cnt, mode, t, dls, hout, ids, ctypes.byref(got))
         if rc not in (PP_OK, PP_EAGAIN):
             _check(rc)
         return rc, [int(ids[i]) for i in range(got.value)]
+
+    def result_bytes(self, precision):
+        """pp_result_bytes: size of one frame's outputs (a host output buffer) at ``precision``."""
+        return int(lib().pp_result_bytes(self.h, precision))
 
     def release_many(self, frame_ids):
         n = len(frame_ids)
@@ -748,6 +764,23 @@ def now_us() -> float:
 def noise_factor(seed, frame_id, eps) -> float:
     """pp_noise_factor: the estimate-noise factor the runtime gives frame ``frame_id``."""
     return float(lib().pp_noise_factor(seed, frame_id, eps))
+
+
+def result_host_tensor(r):
+    """A result's host copy of its final output (pp_submit_frames_ex) as a CPU tensor view
+    [h+2, w+2, c] (float32 or bfloat16; valid while the caller's buffer lives)."""
+    import numpy as np
+    import torch
+    ptr = r.out_host
+    if not ptr:
+        raise PPError(PP_ESTATE, "frame %d has no host output" % r.frame_id)
+    c, h, w = r.out_c, r.out_h, r.out_w
+    n = (h + 2) * (w + 2) * c
+    if r.out_dtype == PP_F32:
+        a = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_float)), shape=(n,))
+        return torch.from_numpy(a).view(h + 2, w + 2, c)
+    a = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_int16)), shape=(n,))
+    return torch.from_numpy(a).view(h + 2, w + 2, c).view(torch.bfloat16)
 
 
 def result_tensor(r, block=None):

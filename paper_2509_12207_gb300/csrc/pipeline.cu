@@ -17,22 +17,27 @@ namespace {
 // inside a result slot.
 struct ResultCopy {
   int nblocks;
+  int hblock;  // the block (the unit's final output) also copied to a frame's host buffer
   const char* src[PP_MAX_BLOCKS];
   size_t bytes[PP_MAX_BLOCKS];  // one slot's block output = the distance between slots
   size_t off[PP_MAX_BLOCKS];
 };
 
-// Copies every frame's block outputs into its result slot (tab->dst[frame]); gridDim.y = frame.
-// Pure 16-byte streaming copy (all sizes are multiples of 128 bytes, all bases 16-byte aligned).
+// Copies every frame's block outputs into its result slot (tab->dst[frame]) and, when the frame
+// has one, its final output (block rc.hblock) into its page-locked host buffer (tab->hdst[frame],
+// at offset 0, over the host link); gridDim.y = frame.  Pure 16-byte streaming copy (all sizes
+// are multiples of 128 bytes, all bases 16-byte aligned).
 __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTable* __restrict__ tab) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int f = blockIdx.y;
   char* dst = tab->dst[f];
+  char* hdst = tab->hdst[f];
   if (!dst) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (int b = 0; b < rc.nblocks; ++b) {
     const uint4* s = reinterpret_cast<const uint4*>(rc.src[b] + (size_t)f * rc.bytes[b]);
     uint4* d = reinterpret_cast<uint4*>(dst + rc.off[b]);
+    uint4* h = hdst && b == rc.hblock ? reinterpret_cast<uint4*>(hdst) : nullptr;
     const size_t n = rc.bytes[b] / 16;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + 3 * stride < n; i += 4 * stride) {
@@ -42,8 +47,18 @@ __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTabl
       d[i + stride] = v1;
       d[i + 2 * stride] = v2;
       d[i + 3 * stride] = v3;
+      if (h) {
+        h[i] = v0;
+        h[i + stride] = v1;
+        h[i + 2 * stride] = v2;
+        h[i + 3 * stride] = v3;
+      }
     }
-    for (; i < n; i += stride) d[i] = __ldcs(s + i);
+    for (; i < n; i += stride) {
+      const uint4 v = __ldcs(s + i);
+      d[i] = v;
+      if (h) h[i] = v;
+    }
   }
 }
 
@@ -173,6 +188,13 @@ size_t Model::result_layout(std::vector<size_t>* block_off) const {
     off += align_up((size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * elt, 256);
   }
   return off;
+}
+
+size_t Model::final_bytes() const {
+  const size_t elt = precision == PP_F32 ? 4 : 2;
+  if (head_outputs > 0) return (size_t)(out_h() + 2) * (out_w() + 2) * head_c * elt;
+  const LayerSpec& L = layers[block_end.back()];
+  return (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * elt;
 }
 
 void Model::release() {
@@ -337,9 +359,9 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   const Geom& g = m.g;
   // voxelise up to the bucketing; point selection runs fused into PointNet
   int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
-                      nullptr, vw_, s, tab_dev_->src);
+                      nullptr, vw_, s, tab_dev_->src, tab_dev_->mirror);
   if (!st)
-    st = select_pfn_launch(g, n, cap_, points_, tab_dev_->src, vw_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
+    st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
   const bool split = m.conv_dtype == PP_F32_TC;
   // the canvas keeps the slot's previous frame: zero its stale cells, write the new pillars
   if (!st)
@@ -396,11 +418,13 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
     }
     if (st) return st;
     rc.nblocks = 1;
+    rc.hblock = 0;
     rc.src[0] = static_cast<const char*>(head_);
     rc.bytes[0] = (size_t)(H0 + 2) * (W0 + 2) * m.head_c * (m.precision == PP_F32 ? 4 : 2);
     rc.off[0] = res_off_[0];
   } else {
     rc.nblocks = (int)m.block_end.size();
+    rc.hblock = rc.nblocks - 1;
     for (int b = 0; b < rc.nblocks; ++b) {
       const int l = m.block_end[b];
       const LayerSpec& L = m.layers[l];
@@ -415,7 +439,8 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
 }
 
 int Pipeline::run(int n, const float* const* frames, const int* counts, const bool* direct,
-                  char* const* dst, bool use_graph, cudaStream_t s) {
+                  char* const* dst, bool use_graph, cudaStream_t s, const bool* host_mapped,
+                  char* const* hdst) {
   if (n <= 0 || n > B_) return fail(PP_EINVAL, "pipeline run: batch %d outside 1..%d", n, B_);
   for (int i = 0; i < n; ++i) {
     if (counts[i] < 0 || counts[i] > cap_)
@@ -432,11 +457,19 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
   for (int i = 0; i < n; ++i) {
     t.counts[i] = counts[i];
     t.dst[i] = dst ? dst[i] : nullptr;
+    t.hdst[i] = hdst && t.dst[i] ? hdst[i] : nullptr;
     if (direct && direct[i]) {
       t.src[i] = reinterpret_cast<const float4*>(frames[i]);
+      t.gsrc[i] = t.src[i];
+      if (host_mapped && host_mapped[i]) {
+        // read once over the host link (coalesced); the scattered gather reads the copy
+        t.mirror[i] = points_ + (size_t)i * cap_;
+        t.gsrc[i] = t.mirror[i];
+      }
       continue;
     }
     t.src[i] = points_ + (size_t)i * cap_;
+    t.gsrc[i] = t.src[i];
     if (counts[i] > 0 &&
         (st = cuda_status(cudaMemcpyAsync(points_ + (size_t)i * cap_, frames[i],
                                           (size_t)counts[i] * sizeof(float4), cudaMemcpyDefault, s),

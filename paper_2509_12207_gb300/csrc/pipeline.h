@@ -19,8 +19,13 @@ constexpr int kMaxUnit = 8;  // frames per release unit
 struct UnitTable {
   int32_t counts[kMaxUnit];
   int32_t pad[kMaxUnit];
-  const float4* src[kMaxUnit];  // frame's points (a borrowed device buffer or a staging row)
-  char* dst[kMaxUnit];          // frame's result slot (NULL: leave outputs in the unit)
+  const float4* src[kMaxUnit];   // frame's points (a borrowed buffer, or a staging row)
+  char* dst[kMaxUnit];           // frame's result slot (NULL: leave outputs in the unit)
+  float4* mirror[kMaxUnit];      // where the first voxelise pass copies points read over the
+                                 // host link (a borrowed page-locked frame), else NULL
+  const float4* gsrc[kMaxUnit];  // where the point gather reads: the frame in device memory
+  char* hdst[kMaxUnit];          // page-locked host copy of the frame's final output (device
+                                 // view of the mapping; written over the host link), else NULL
 };
 
 struct Model {
@@ -51,6 +56,8 @@ struct Model {
   size_t result_layout(std::vector<size_t>* block_off) const;
   int out_h() const { return layers[block_end[0]].Ho; }  // neck / head map size (block 0's)
   int out_w() const { return layers[block_end[0]].Wo; }
+  // Bytes of a frame's final output (last block, or the head map), padded NHWC.
+  size_t final_bytes() const;
   void release();
 };
 
@@ -62,11 +69,17 @@ class Pipeline {
            cudaStream_t s);
   void release();
   // Enqueues the whole front end for `n` frames on `s` (graph or plain launches).  Frame i is
-  // read in place when direct[i] (a 16-byte aligned device buffer), else staged into slot i
-  // (host or device pointer, cudaMemcpyDefault).  When dst[i] is set, the blocks' outputs are
-  // copied to it (result_layout) inside the same graph.  direct / dst may be NULL.
+  // read in place when direct[i] (a 16-byte aligned device or page-locked host buffer), else
+  // staged into slot i (host or device pointer, cudaMemcpyDefault).  A direct frame with
+  // host_mapped[i] is read over the host link once, by the first voxelise pass, which copies it
+  // into slot i for the point gather.  When dst[i] is set, the blocks' outputs are copied to it
+  // (result_layout) inside the same graph.  direct / host_mapped / dst may be NULL.
+  // hdst[i] (may be NULL): a page-locked host buffer (its device view) that also receives the
+  // frame's final output (last block, or the head map), written by the same copy kernel over
+  // the host link.
   int run(int n, const float* const* frames, const int* counts, const bool* direct,
-          char* const* dst, bool use_graph, cudaStream_t s);
+          char* const* dst, bool use_graph, cudaStream_t s, const bool* host_mapped = nullptr,
+          char* const* hdst = nullptr);
   // Enqueues the kernels for slots 0..n-1 (points and counts already in place).
   int enqueue(int n, cudaStream_t s);
   size_t bytes() const { return bytes_; }

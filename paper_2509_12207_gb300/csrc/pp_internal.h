@@ -79,11 +79,12 @@ VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
 // srcs: optional device table of per-frame point pointers (frame b reads srcs[b][0..n));
 // NULL = frame b is row b of `points` ([batch][cap]).
 // pts == NULL: stop after the bucket step (the caller runs select_pfn_launch, which gathers
-// each pillar's points itself).
+// each pillar's points itself).  mirrors: device table of per-frame destinations (NULL
+// entries skip) into which the first pass copies the points it reads.
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
                int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
-               const float4* const* srcs = nullptr);
+               const float4* const* srcs = nullptr, float4* const* mirrors = nullptr);
 
 // ---- PointNet and scatter (pfn.cu)
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,

@@ -81,6 +81,9 @@ struct Frame {
   bool dropped = false, done = false, polled = false;
   double delay_start = -1;
   double est_scale = 1.0;      // estimate-noise factor (1 unless the experiment is on)
+  bool pinned = false;         // borrowed page-locked host memory (read over the host link)
+  char* hout_dev = nullptr;    // caller's page-locked result buffer: device view, host pointer
+  void* hout_host = nullptr;
 };
 
 struct Unit {
@@ -243,6 +246,7 @@ void push_result(pp_ctx* c, Frame* f, int status, double t_done) {
         r.out_w = L.Wo;
       }
       r.num_pillars = u->pipe.num_pillars_host()[f->slot];
+      r.out_host = f->hout_host;  // the final output's host copy, if the caller gave a buffer
     }
   } else {
     c->n_dropped += status == PP_FRAME_DROPPED;
@@ -363,8 +367,9 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
   Unit* u = c->units[ui];
   const float* srcs[kMaxUnit];
   int counts[kMaxUnit];
-  bool direct[kMaxUnit];
+  bool direct[kMaxUnit], host_mapped[kMaxUnit];
   char* dsts[kMaxUnit];
+  char* hdsts[kMaxUnit];
   const pp_ctx::Pool& pl = c->pool[prec];
   // a synthetic frame runs alone: its chain's kernels are its own (the rest stay ready)
   const int nf = prec == kSynth ? 1 : d.n_frames;
@@ -386,8 +391,10 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     f->t_release = t;
     srcs[i] = f->src;
     counts[i] = (int)f->n;
-    direct[i] = f->staging < 0;  // a borrowed device buffer is read in place
+    direct[i] = f->staging < 0;  // a borrowed buffer is read in place
+    host_mapped[i] = f->pinned;  // ... over the host link, once
     dsts[i] = f->rslot < 0 ? nullptr : static_cast<char*>(pl.base) + (size_t)f->rslot * pl.slot_bytes;
+    hdsts[i] = f->hout_dev;
     if (f->delay_start >= 0) {
       c->delayed_us += t - f->delay_start;
       f->delay_start = -1;
@@ -413,7 +420,7 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     st = synth_launch(c->synth, ui - c->synth_first, ch.synth_ctas, ch.synth_iters, ch.n_kernels, s);
   } else if (!st) {
     // the unit's graph also copies every frame's block outputs into its result slot
-    st = u->pipe.run(nf, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s);
+    st = u->pipe.run(nf, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s, host_mapped, hdsts);
   }
   if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
   if (!st) st = cuda_status(cudaLaunchHostFunc(s, notify_cb, c), "host notify");
@@ -789,6 +796,19 @@ int pp_register_synthetic_chain(pp_ctx* c, int32_t chain_id, double period_ms, d
 int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
                      const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
                      const double* abs_deadline_us, uint64_t* frame_ids_out, int32_t* n_admitted) {
+  return pp_submit_frames_ex(c, n, chain_ids, xyzr, n_points, is_device_ptr, t_arrival_us, abs_deadline_us,
+                             nullptr, frame_ids_out, n_admitted);
+}
+
+size_t pp_result_bytes(pp_ctx* c, int32_t precision) {
+  if (!c || (precision != PP_F32 && precision != PP_BF16) || !c->have[precision]) return 0;
+  return c->models[precision].final_bytes();
+}
+
+int pp_submit_frames_ex(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
+                        const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
+                        const double* abs_deadline_us, void* const* host_out, uint64_t* frame_ids_out,
+                        int32_t* n_admitted) {
   if (n_admitted) *n_admitted = 0;
   if (!c || n < 1 || n > kMaxSubmit || !chain_ids || !xyzr || !n_points)
     return fail(PP_EINVAL, "submit: bad argument (n 1..%d, non-NULL arrays)", kMaxSubmit);
@@ -811,6 +831,17 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
       }
       mapped[i] = static_cast<const float*>(at.devicePointer);
     }
+  }
+  char* hout[kMaxSubmit] = {nullptr};  // device views of the host output buffers
+  for (int i = 0; host_out && i < n; ++i) {
+    if (!host_out[i]) continue;
+    cudaPointerAttributes at;
+    if ((reinterpret_cast<uintptr_t>(host_out[i]) & 15u) || cudaPointerGetAttributes(&at, host_out[i]) != cudaSuccess ||
+        at.type != cudaMemoryTypeHost || !at.devicePointer) {
+      cudaGetLastError();
+      return fail(PP_EINVAL, "submit: host output %d is not 16-byte aligned page-locked host memory", i);
+    }
+    hout[i] = static_cast<char*>(at.devicePointer);
   }
   Frame* fs[kMaxSubmit];
   int k = 0, st = PP_OK;
@@ -835,6 +866,10 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
     }
     f->id = c->next_id++;
     if (c->cfg.est_noise > 0) f->est_scale = pp_noise_factor(c->cfg.noise_seed, f->id, c->cfg.est_noise);
+    if (hout[k] && !synth) {
+      f->hout_dev = hout[k];
+      f->hout_host = host_out[k];
+    }
     f->chain = chain_ids[k];
     f->precision = p;
     f->t_arr = t_arrival_us;
@@ -850,6 +885,7 @@ int pp_submit_frames(pp_ctx* c, int32_t n, const int32_t* chain_ids, const float
     c->pool[p].free.pop_back();
     if (is_device_ptr) {
       f->src = mapped[k];  // read in place by the unit's kernels
+      f->pinned = is_device_ptr == PP_POINTS_PINNED;
     } else {
       f->staging = c->staging_free.back();
       c->staging_free.pop_back();

@@ -41,12 +41,14 @@ constexpr int kVoxU = 4;
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
+                               float4* const* __restrict__ mirrors,
                                const int* __restrict__ n_points, int* __restrict__ cell,
                                int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, err);
   const float4* src = frame_src(points, srcs, b, cap);
+  float4* mirror = mirrors ? mirrors[b] : nullptr;  // copy of a frame read over the host link
   const int lane = threadIdx.x & 31;
   unsigned* cnt_b = cnt + (size_t)b * g.G;
   // grid-stride over the frame's points, kVoxU coalesced blocks of blockDim.x points per pass
@@ -57,6 +59,13 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
     for (int u = 0; u < kVoxU; ++u) {
       const int i = i0 + u * blockDim.x + threadIdx.x;
       p[u] = i < n ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (mirror) {
+#pragma unroll
+      for (int u = 0; u < kVoxU; ++u) {
+        const int i = i0 + u * blockDim.x + threadIdx.x;
+        if (i < n) mirror[i] = p[u];
+      }
     }
     int c[kVoxU];
 #pragma unroll
@@ -295,7 +304,7 @@ VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
                int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
-               const float4* const* srcs) {
+               const float4* const* srcs, float4* const* mirrors) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
   // point kernels: grid-stride, about 8 blocks of 256 threads per SM over the whole batch (a
@@ -311,7 +320,7 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   if (px > px_max) px = px_max;
   const dim3 pg(px > 0 ? px : 1, batch);
   // the count follows the memset (a plain launch); the other four follow a kernel
-  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, n_points, cell, w.slot, cnt, w.err);
+  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, mirrors, n_points, cell, w.slot, cnt, w.err);
   e = cudaGetLastError();
   if (e == cudaSuccess)
     e = launch_pdl(vox_tile_sums, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt, w.tile_sums,

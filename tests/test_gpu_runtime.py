@@ -525,3 +525,29 @@ def test_runtime_synthetic_load_chain(small_clouds):
         ctx.release_many(sids + pids)
     finally:
         ctx.destroy()
+
+
+def test_runtime_host_output_buffers(small_clouds):
+    """Frames submitted with page-locked host output buffers: when polled, each buffer holds
+    exactly the frame's final output; pageable memory is refused and admits nothing."""
+    ctx, keep = _ctx(max_batch=4)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        nbytes = ctx.result_bytes(pp.PP_F32)
+        assert nbytes > 0
+        outs = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in small_clouds]
+        dev = [torch.from_numpy(c).to(DEV) for c in small_clouds]
+        rc, ids = ctx.submit_many([0] * len(dev), dev, host_out=outs)
+        assert rc == pp.PP_OK
+        res = {r.frame_id: r for r in _drain(ctx, len(ids))}
+        for k, fid in enumerate(ids):
+            r = res[fid]
+            assert r.out_host
+            assert torch.equal(pp.result_host_tensor(r), pp.result_tensor(r).cpu())
+            _check_out(_interior(pp.result_host_tensor(r)), _ref(small_clouds[k]), pp.PP_F32)
+        ctx.release_many(ids)
+        with pytest.raises(pp.PPError):
+            ctx.submit_many([0], dev[:1], host_out=[torch.empty(nbytes, dtype=torch.uint8)])
+        assert ctx.stats()["submitted"] == len(ids)
+    finally:
+        ctx.destroy()
