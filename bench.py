@@ -32,6 +32,8 @@ WORKLOADS = {
     "cfg3-bf16": "batched BF16: 8 frames of 30k-150k uniform points per unit, 216x248 grid, 3 conv3x3 64ch",
 }
 
+REFERENCE_BUDGET_S = 90  # wall-clock cap of the reference arm's timed steps
+
 HEAD_NOTE = ", + neck (transposed convs to 128 channels each, concatenated) and 1x1 head (72 outputs)"
 
 
@@ -702,22 +704,29 @@ def _run_reference(a):
         if head is not None:
             O.head(O.neck(r["blocks"], head[0], head[1]), head[2], head[3])
 
-    for k in range(a.warmup):
+    # the oracle takes seconds per frame: at most one warm-up frame, and the timed steps stop
+    # once REFERENCE_BUDGET_S is spent (at least one step), so any --steps ends within minutes
+    warm = min(a.warmup, 1)
+    for k in range(warm):
         one(frames[k % len(frames)])
     t0 = time.perf_counter()
-    for k in range(a.steps):
+    steps = 0
+    while steps < a.steps and (steps == 0 or time.perf_counter() - t0 < REFERENCE_BUDGET_S):
         for j in range(batch):
-            one(frames[(k * batch + j) % len(frames)])
+            one(frames[(steps * batch + j) % len(frames)])
+        steps += 1
     secs = time.perf_counter() - t0
-    v = a.steps * batch / secs
+    v = steps * batch / secs
     cores = os.cpu_count()
     return {"impl": "reference", "metric": "pillar frames/s", "value": v, "unit": "frames/s", "n_gpus": 1,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": secs / a.steps * 1e3, "higher_is_better": True,
+            "steps": steps, "steps_requested": a.steps, "warmup": warm, "ms_per_step": secs / steps * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": batch},
             "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": "one full frame per step through the FP64 NumPy oracle (BLAS threads as "
-                                       "installed, up to %d cores)" % cores},
+                             "sample": "%d step(s) of %d full frame(s) through the FP64 NumPy oracle in %.1f s "
+                                       "(timed steps stop after %d s; BLAS threads as installed, up to %d cores)"
+                                       % (steps, batch, secs, REFERENCE_BUDGET_S, cores)},
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
