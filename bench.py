@@ -502,11 +502,7 @@ def _run_ours(a, rank, world, dist):
         e1.record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        el = e0.elapsed_time(e1) * 1e-3
-        if dist is not None:
-            t = torch.tensor([el], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = replica_window(dist, e0.elapsed_time(e1) * 1e-3, "cuda")
         return el, wall
 
     clocks = _Clocks(dev, enabled=not a.no_clocks)
@@ -565,9 +561,9 @@ def _run_ours(a, rank, world, dist):
                      "launches": [{"kernel": k, "us": round(t * 1e6, 2), "tflops": round(f / t / 1e12, 1),
                                    "gbs": round(b / t / 1e9)} for k, t, f, b in nh],
                      "in_step": bool(a.head)}
-    frames_done = a.steps * n_frames * world
     res = {
-        "metric": "pillar frames/s", "value": frames_done / el, "unit": "frames/s", "n_gpus": world,
+        "metric": "pillar frames/s", "value": replica_throughput(a.steps * n_frames, world, el), "unit": "frames/s",
+        "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
@@ -575,7 +571,7 @@ def _run_ours(a, rank, world, dist):
                    [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
                          % (canvas_bytes // 2 ** 20)},
-        "e2e": {"value": frames_done / e2e_el, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": replica_throughput(a.steps * n_frames, world, e2e_el), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per step, all conv launches",
@@ -600,6 +596,25 @@ def _run_ours(a, rank, world, dist):
         "wall_s": wall,
     }
     return res
+
+
+# ------------------------------------------------------------------ replicas (one process per GPU)
+
+def replica_window(dist, seconds, device="cpu"):
+    """The timed window of a multi-GPU run: the slowest rank's (all-reduce MAX over the process
+    group; the value itself without one).  Every rank processes its own frames, so the job's
+    throughput is the frames of all ranks over this window."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(frames_per_rank, world, window_s):
+    """Whole-job frames/s of `world` replicas that each processed frames_per_rank frames."""
+    return frames_per_rank * world / window_s
 
 
 # ------------------------------------------------------------------ serving (chains with deadlines)
