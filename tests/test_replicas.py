@@ -34,7 +34,7 @@ def _rank(rank, world, port, windows, out):
 def test_replica_window_is_the_slowest_rank():
     world, port = 2, _free_port()
     windows = [0.25, 0.4]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank, args=(world, port, windows, out), nprocs=world, start_method="spawn")
         got = dict(out)
