@@ -846,6 +846,11 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    if (args.c.static_w) {
+      // weights that no preceding kernel writes: fetch them while that kernel drains
+      mbar_expect_tx(wbar, 9 * kTap);
+      for (int t = 0; t < 9; ++t) tma_2d(sW + t * kTap, &tmB, wbar, t * 64, 0);
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -877,8 +882,10 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
   if (warp == 0) {
     if (lane == 0) {
-      mbar_expect_tx(wbar, 9 * kTap);
-      for (int t = 0; t < 9; ++t) tma_2d(sW + t * kTap, &tmB, wbar, t * 64, 0);
+      if (!c.static_w) {
+        mbar_expect_tx(wbar, 9 * kTap);
+        for (int t = 0; t < 9; ++t) tma_2d(sW + t * kTap, &tmB, wbar, t * 64, 0);
+      }
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;

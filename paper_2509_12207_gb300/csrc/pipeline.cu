@@ -372,6 +372,7 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];
     ConvShape c{n, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
+    c.static_w = true;  // packed once at creation
     if (split) {  // planes are laid out for the unit's capacity, not for this batch
       c.in_plane = (size_t)B_ * (L.H + 2) * (L.W + 2) * L.cin;
       c.out_plane = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout;

@@ -114,6 +114,9 @@ struct ConvShape {
   // split FP32 (PP_F32_TC): elements between the value and remainder planes of the input and
   // the output; 0 = this batch's plane size (planes packed for exactly `batch` frames)
   size_t in_plane = 0, out_plane = 0;
+  // the weights were written before the previous kernel in the stream started (a release
+  // unit's packed weights): a kernel may load them before its dependent-launch wait
+  bool static_w = false;
 };
 // The persistent tensor-core kernel as a general implicit GEMM (see conv_tc.cu PArgs): taps 9 =
 // 3x3 conv, 1 = pointwise; up > 1 = transposed conv with kernel = stride = up (GEMM N =
