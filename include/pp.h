@@ -388,6 +388,8 @@ typedef struct {
   /* frame id, est_noise), drawn once per frame.  0 = off (default).                           */
   double est_noise;             /* half-width eps of the uniform factor 1 + U[-eps, eps), < 1 */
   uint64_t noise_seed;
+  int32_t keep_blocks;          /* result slots hold every backbone block's output (1) or only */
+                                /* the last block's, the final output (0, default)            */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
@@ -476,7 +478,8 @@ typedef struct {
   const void* out_dev;          /* last backbone layer (or the head), padded NHWC            */
                                 /* [out_h+2][out_w+2][out_c]                                  */
   int32_t out_c, out_h, out_w, out_dtype;
-  const void* block_dev[PP_MAX_BLOCKS];  /* output of each block, same layout                 */
+  const void* block_dev[PP_MAX_BLOCKS];  /* output of each block kept (keep_blocks: all; else  */
+                                         /* the last block's only, others NULL), same layout   */
   int32_t block_c[PP_MAX_BLOCKS], block_h[PP_MAX_BLOCKS], block_w[PP_MAX_BLOCKS];
   /* with a head (head_outputs > 0): out_dev is the head map [out_h+2][out_w+2][out_c] at block */
   /* 0's size, out_c = head_outputs rounded up to 64 (channels past out_valid_c are 0), and the */

@@ -79,6 +79,7 @@ class Config(ctypes.Structure):
         ("head_w", ctypes.c_void_p), ("head_b", ctypes.c_void_p),
         ("eqdf_lambda", ctypes.c_double),
         ("est_noise", ctypes.c_double), ("noise_seed", ctypes.c_uint64),
+        ("keep_blocks", ctypes.c_int32),
     ]
 
 

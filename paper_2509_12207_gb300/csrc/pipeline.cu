@@ -97,6 +97,7 @@ int Model::upload(const pp_config* cfg, int prec, cudaStream_t s) {
   int st = check_geometry(&cfg->geom, &g);
   if (st) return st;
   precision = prec;
+  keep_blocks = cfg->keep_blocks != 0;
   conv_dtype = prec == PP_BF16 ? PP_BF16 : (cfg->fp32_cuda_cores ? PP_F32 : PP_F32_TC);
   layers.clear();
   block_end.clear();
@@ -182,12 +183,19 @@ size_t Model::result_layout(std::vector<size_t>* block_off) const {
     block_off->push_back(0);
     return align_up((size_t)(out_h() + 2) * (out_w() + 2) * head_c * elt, 256);
   }
-  for (int l : block_end) {
-    const LayerSpec& L = layers[l];
+  for (int b : kept_blocks()) {
+    const LayerSpec& L = layers[block_end[b]];
     block_off->push_back(off);
     off += align_up((size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * elt, 256);
   }
   return off;
+}
+
+std::vector<int> Model::kept_blocks() const {
+  std::vector<int> v;
+  if (head_outputs > 0) return v;
+  for (int b = keep_blocks ? 0 : (int)block_end.size() - 1; b < (int)block_end.size(); ++b) v.push_back(b);
+  return v;
 }
 
 size_t Model::final_bytes() const {
@@ -424,14 +432,15 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
     rc.bytes[0] = (size_t)(H0 + 2) * (W0 + 2) * m.head_c * (m.precision == PP_F32 ? 4 : 2);
     rc.off[0] = res_off_[0];
   } else {
-    rc.nblocks = (int)m.block_end.size();
-    rc.hblock = rc.nblocks - 1;
-    for (int b = 0; b < rc.nblocks; ++b) {
-      const int l = m.block_end[b];
+    const std::vector<int> kept = m.kept_blocks();
+    rc.nblocks = (int)kept.size();
+    rc.hblock = rc.nblocks - 1;  // the last block: the unit's final output
+    for (int k = 0; k < rc.nblocks; ++k) {
+      const int l = m.block_end[kept[k]];
       const LayerSpec& L = m.layers[l];
-      rc.src[b] = static_cast<const char*>(act_[l]);
-      rc.bytes[b] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
-      rc.off[b] = res_off_[b];
+      rc.src[k] = static_cast<const char*>(act_[l]);
+      rc.bytes[k] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
+      rc.off[k] = res_off_[k];
     }
   }
   return cuda_status(launch_pdl(result_copy, dim3(std::max(1, 8 * sms_ / n), n), dim3(256), 0, s, rc,

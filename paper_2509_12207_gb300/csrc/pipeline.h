@@ -51,8 +51,11 @@ struct Model {
   float* head_ss = nullptr;      // [2][head_c]: 1 and the bias
   size_t bytes = 0;
   int upload(const pp_config* cfg, int precision, cudaStream_t s);
-  // Result slot layout: every block's padded NHWC output, each at a 256-byte aligned offset
-  // (with a head: the head map alone, one offset).
+  bool keep_blocks = false;      // result slots hold every block's output (else the last one's)
+  // Blocks whose outputs a result slot holds, in order (none with a head: the head map).
+  std::vector<int> kept_blocks() const;
+  // Result slot layout: each kept block's padded NHWC output at a 256-byte aligned offset
+  // (block_off[k] for kept_blocks()[k]; with a head: the head map alone, one offset).
   size_t result_layout(std::vector<size_t>* block_off) const;
   int out_h() const { return layers[block_end[0]].Ho; }  // neck / head map size (block 0's)
   int out_w() const { return layers[block_end[0]].Wo; }

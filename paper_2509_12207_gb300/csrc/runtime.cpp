@@ -234,9 +234,11 @@ void push_result(pp_ctx* c, Frame* f, int status, double t_done) {
         r.out_h = m->out_h();
         r.out_w = m->out_w();
       }
-      for (size_t b = 0; m->head_outputs == 0 && b < m->block_end.size() && b < PP_MAX_BLOCKS; ++b) {
+      const std::vector<int> kept = m->kept_blocks();
+      for (size_t k = 0; k < kept.size(); ++k) {
+        const int b = kept[k];
         const LayerSpec& L = m->layers[m->block_end[b]];
-        r.block_dev[b] = base + pl.block_off[b];
+        r.block_dev[b] = base + pl.block_off[k];
         r.block_c[b] = L.cout;
         r.block_h[b] = L.Ho;
         r.block_w[b] = L.Wo;

@@ -123,7 +123,7 @@ def test_runtime_full_size_all_blocks(full_frame):
     the frame's result slot by the unit's graph, matches the oracle."""
     w, cloud, ref = full_frame
     cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=2, cap_points=120000,
-                               precisions=1, units=1, th_urgent=-1.0)
+                               precisions=1, units=1, th_urgent=-1.0, keep_blocks=1)
     ctx = pp.Context(cfg)
     try:
         ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
@@ -139,6 +139,19 @@ def test_runtime_full_size_all_blocks(full_frame):
                 assert rel_err(_interior(pp.result_tensor(r, b)), ref["blocks"][b]) <= FP32_TOL, b
         assert torch.equal(pp.result_tensor(res[0]), pp.result_tensor(res[1]))
         ctx.release_many([r.frame_id for r in res])
+    finally:
+        ctx.destroy()
+    # by default a result slot keeps only the final output (the last block)
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000,
+                               precisions=1, units=1, th_urgent=-1.0, autotune=0)
+    ctx = pp.Context(cfg)
+    try:
+        ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
+        rc, ids = ctx.submit_many([0], [cloud])
+        (r,) = _drain(ctx, 1)
+        assert not r.block_dev[0] and not r.block_dev[1] and r.block_dev[2] == r.out_dev
+        assert rel_err(_interior(pp.result_tensor(r)), ref["blocks"][2]) <= FP32_TOL
+        ctx.release_many(ids)
     finally:
         ctx.destroy()
 
