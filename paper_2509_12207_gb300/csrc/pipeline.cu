@@ -16,6 +16,8 @@ namespace {
 // Where the block outputs of slot 0 are, how far apart the slots lie, and where each block goes
 // inside a result slot.
 struct ResultCopy {
+  const int* num;   // [B] pillars per frame ...
+  int* num_host;    // ... copied to the unit's pinned host array (device view of the mapping)
   int nblocks;
   int hblock;  // the block (the unit's final output) also copied to a frame's host buffer
   const char* src[PP_MAX_BLOCKS];
@@ -30,6 +32,7 @@ struct ResultCopy {
 __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTable* __restrict__ tab) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int f = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) rc.num_host[f] = rc.num[f];  // over the host link
   char* dst = tab->dst[f];
   char* hdst = tab->hdst[f];
   if (!dst) return;
@@ -305,6 +308,9 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   }
   if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)B_ * sizeof(int)), "pinned pillar counts"))) return st;
   memset(num_host_, 0, (size_t)B_ * sizeof(int));
+  if ((st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void**>(&num_host_dev_), num_host_, 0),
+                        "pinned pillar counts mapping")))
+    return st;
   vw_ = vox_carve(vox_ws_, g, B_, cap_);
   if (tune) {
     // time every conv tile of every layer for each unit size on this unit's own buffers; the
@@ -398,6 +404,8 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   }
   if (st) return st;
   ResultCopy rc{};
+  rc.num = num_;
+  rc.num_host = num_host_dev_;
   if (m.head_outputs > 0) {
     // neck: every block's output upsampled into its channel range of the neck map; then the head
     const int H0 = m.out_h(), W0 = m.out_w();
@@ -494,9 +502,7 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
     st = cuda_status(cudaGraphLaunch(graphs_[n], s), "graph launch");
   else
     st = enqueue(n, s);
-  if (st) return st;
-  return cuda_status(cudaMemcpyAsync(num_host_, num_, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s),
-                     "read back pillar counts");
+  return st;  // the result copy kernel has written num_host_ (pillar counts) over the host link
 }
 
 const void* Pipeline::neck_out(int i) const {

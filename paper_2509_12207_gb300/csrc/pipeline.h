@@ -105,7 +105,8 @@ class Pipeline {
   float4* points_ = nullptr;
   UnitTable* tab_dev_ = nullptr;
   UnitTable* tab_host_ = nullptr;  // pinned; rewritten only once the previous run completed
-  int* num_host_ = nullptr;        // pinned [B]
+  int* num_host_ = nullptr;        // pinned [B], written by the unit's last kernel
+  int* num_host_dev_ = nullptr;    // its device view
   cudaEvent_t tab_ev_ = nullptr;   // after the table's H2D copy of the last run
   std::vector<size_t> res_off_;
   int sms_ = 1;

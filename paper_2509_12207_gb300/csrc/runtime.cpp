@@ -152,6 +152,7 @@ struct pp_ctx {
   cudaEvent_t ref_event = nullptr;
   double ref_host = 0;
   cudaStream_t aux = nullptr;
+  cudaStream_t notify = nullptr;  // completion callbacks, so that no unit stream waits on the host
   // stats
   uint64_t submitted = 0, n_done = 0, n_dropped = 0, n_missed = 0, rejected = 0, launched = 0;
   uint64_t batch_frames = 0, delayed = 0, collisions = 0, decisions = 0;
@@ -425,7 +426,10 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     st = u->pipe.run(nf, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s, host_mapped, hdsts);
   }
   if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
-  if (!st) st = cuda_status(cudaLaunchHostFunc(s, notify_cb, c), "host notify");
+  // wake the dispatcher at completion from a separate stream: a host function in the unit's own
+  // stream would hold back whatever is queued behind it there until the callback has run
+  if (!st) st = cuda_status(cudaStreamWaitEvent(c->notify, u->done, 0), "notify wait");
+  if (!st) st = cuda_status(cudaLaunchHostFunc(c->notify, notify_cb, c), "host notify");
   if (st) c->device_error = true;
   c->launched++;
   c->batch_frames += nf;
@@ -538,6 +542,7 @@ void destroy_units(pp_ctx* c) {
     for (cudaStream_t s : ch.streams) cudaStreamDestroy(s);
   if (c->ref_event) cudaEventDestroy(c->ref_event);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->notify) cudaStreamDestroy(c->notify);
   for (auto& kv : c->frames) delete kv.second;
   c->frames.clear();
 }
@@ -626,6 +631,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   c->num_pri = least - greatest + 1;
   if (cfg->num_streams > 0) c->num_pri = std::min(c->num_pri, cfg->num_streams);
   if (!st) st = cuda_status(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "aux stream");
+  if (!st) st = cuda_status(cudaStreamCreateWithFlags(&c->notify, cudaStreamNonBlocking), "notify stream");
   uint64_t used = 0;
   for (int p = 0; p < 2 && !st; ++p) {
     if (!(cfg->precisions & (1 << p))) continue;
@@ -1034,8 +1040,9 @@ int pp_destroy(pp_ctx* c) {
   }
   cudaGetLastError();
   if (busy) return fail(PP_ETIMEDOUT, "destroy: units still running after 10 s");
-  // every unit's completion event has fired; what may remain on a chain stream is the host
-  // notification queued after it, which touches this context: let it finish first
+  // every unit's completion event has fired; what may remain is the host notification queued
+  // after it on the notify stream, which touches this context: let it finish first
+  if (c->notify) cudaStreamSynchronize(c->notify);
   for (auto& ch : c->chains)
     for (cudaStream_t s : ch.streams) cudaStreamSynchronize(s);
   cudaGetLastError();
