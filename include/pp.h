@@ -563,7 +563,9 @@ typedef struct pp_pipeline pp_pipeline;
 int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** out);
 /* frames: host array of n pointers to each frame's points (host or device memory, copied into
  * the unit's slots on `stream`); counts: host array of n point counts.  Enqueues everything on
- * `stream` and returns without waiting. */
+ * `stream` and returns without waiting for it; a call first waits for the previous run on the
+ * same pipeline to finish (the unit's per-launch table, in page-locked host memory, is read by
+ * that run's first kernel). */
 int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames,
                     const int32_t* counts, int32_t use_graph, void* stream);
 /* Device pointer to block `block`'s output for frame slot i (padded NHWC) and its shape; pass

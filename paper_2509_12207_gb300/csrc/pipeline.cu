@@ -299,6 +299,11 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   if ((st = cuda_status(cudaMemsetAsync(tab_dev_, 0, sizeof(UnitTable), s), "clear unit table"))) return st;
   if ((st = cuda_status(cudaMallocHost(&tab_host_, sizeof(UnitTable)), "pinned unit table"))) return st;
   memset(tab_host_, 0, sizeof(UnitTable));
+  if ((st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void**>(&tab_map_), tab_host_, 0),
+                        "unit table mapping")))
+    return st;
+  // cell counts start zero; every launch's scan leaves them zero again
+  if ((st = cuda_status(cudaMemsetAsync(cnt_, 0, (size_t)B_ * g.G * sizeof(unsigned), s), "clear counts"))) return st;
   if ((st = cuda_status(cudaEventCreateWithFlags(&tab_ev_, cudaEventDisableTiming), "table event"))) return st;
   m->result_layout(&res_off_);
   {
@@ -372,8 +377,18 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   const Model& m = *m_;
   const Geom& g = m.g;
   // voxelise up to the bucketing; point selection runs fused into PointNet
+  // the unit table is read from its page-locked host copy by the first kernel, which copies it
+  // to tab_dev_ for the rest; the counts stay zero between launches
+  VoxUnitIO io;
+  io.first_counts = tab_map_->counts;
+  io.first_srcs = tab_map_->src;
+  io.first_mirrors = tab_map_->mirror;
+  io.table_src = reinterpret_cast<const uint4*>(tab_map_);
+  io.table_dst = reinterpret_cast<uint4*>(tab_dev_);
+  io.table_words = (int)(sizeof(UnitTable) / sizeof(uint4));
+  io.cnt_clean = true;
   int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
-                      nullptr, vw_, s, tab_dev_->src, tab_dev_->mirror);
+                      nullptr, vw_, s, tab_dev_->src, tab_dev_->mirror, &io);
   if (!st)
     st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
   const bool split = m.conv_dtype == PP_F32_TC;
@@ -467,7 +482,8 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
     if (direct && direct[i] && (reinterpret_cast<uintptr_t>(frames[i]) & 15u))
       return fail(PP_EINVAL, "pipeline run: frame %d is not 16-byte aligned", i);
   }
-  // the pinned table may still be in flight from the previous run on this unit
+  // the previous run on this unit reads the pinned table from its first kernel: wait for that
+  // run to finish before rewriting it (a release unit is reused only once it completed)
   int st = cuda_status(cudaEventSynchronize(tab_ev_), "unit table reuse");
   if (st) return st;
   UnitTable& t = *tab_host_;
@@ -494,14 +510,11 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
                           "stage points")))
       return st;
   }
-  st = cuda_status(cudaMemcpyAsync(tab_dev_, tab_host_, sizeof(UnitTable), cudaMemcpyHostToDevice, s),
-                   "unit table");
-  if (!st) st = cuda_status(cudaEventRecord(tab_ev_, s), "unit table event");
-  if (st) return st;
   if (use_graph && graphs_.size() > (size_t)n && graphs_[n])
     st = cuda_status(cudaGraphLaunch(graphs_[n], s), "graph launch");
   else
     st = enqueue(n, s);
+  if (!st) st = cuda_status(cudaEventRecord(tab_ev_, s), "unit table event");
   return st;  // the result copy kernel has written num_host_ (pillar counts) over the host link
 }
 

@@ -105,9 +105,10 @@ class Pipeline {
   float4* points_ = nullptr;
   UnitTable* tab_dev_ = nullptr;
   UnitTable* tab_host_ = nullptr;  // pinned; rewritten only once the previous run completed
+  UnitTable* tab_map_ = nullptr;   // its device view (read by the first kernel of a run)
   int* num_host_ = nullptr;        // pinned [B], written by the unit's last kernel
   int* num_host_dev_ = nullptr;    // its device view
-  cudaEvent_t tab_ev_ = nullptr;   // after the table's H2D copy of the last run
+  cudaEvent_t tab_ev_ = nullptr;   // after the last run (whose first kernel read the table)
   std::vector<size_t> res_off_;
   int sms_ = 1;
   int *cell_ = nullptr, *poc_ = nullptr, *coord_ = nullptr, *npts_ = nullptr, *num_ = nullptr;

@@ -78,13 +78,28 @@ size_t vox_workspace_bytes(const Geom& g, int batch, int cap);
 VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
 // srcs: optional device table of per-frame point pointers (frame b reads srcs[b][0..n));
 // NULL = frame b is row b of `points` ([batch][cap]).
+// How a release unit feeds the voxeliser (the stage entry points pass none).  Its per-launch
+// table lives in page-locked host memory: the first kernel reads its own entries there (device
+// view of the mapping) and copies the whole table to device memory for the kernels after it,
+// so that no copy precedes the unit's graph.  The unit's cell counts start at zero and the scan
+// leaves them zero again (no clearing pass).
+struct VoxUnitIO {
+  const int* first_counts = nullptr;           // host-mapped table entries the first kernel reads
+  const float4* const* first_srcs = nullptr;
+  float4* const* first_mirrors = nullptr;
+  const uint4* table_src = nullptr;            // host-mapped table ...
+  uint4* table_dst = nullptr;                  // ... copied here (table_words 16-byte words)
+  int table_words = 0;
+  bool cnt_clean = false;
+};
 // pts == NULL: stop after the bucket step (the caller runs select_pfn_launch, which gathers
 // each pillar's points itself).  mirrors: device table of per-frame destinations (NULL
 // entries skip) into which the first pass copies the points it reads.
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
                int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
-               const float4* const* srcs = nullptr, float4* const* mirrors = nullptr);
+               const float4* const* srcs = nullptr, float4* const* mirrors = nullptr,
+               const VoxUnitIO* io = nullptr);
 
 // ---- PointNet and scatter (pfn.cu)
 int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, const int* coord,

@@ -43,8 +43,12 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
                                const float4* const* __restrict__ srcs,
                                float4* const* __restrict__ mirrors,
                                const int* __restrict__ n_points, int* __restrict__ cell,
-                               int* __restrict__ slot, unsigned* __restrict__ cnt, int* err) {
+                               int* __restrict__ slot, unsigned* __restrict__ cnt, int* err,
+                               const uint4* __restrict__ table_src, uint4* __restrict__ table_dst,
+                               int table_words) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  // a release unit's per-launch table: copied from host memory for the kernels that follow
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < table_words) table_dst[threadIdx.x] = table_src[threadIdx.x];
   const int b = blockIdx.y;
   const int n = frame_points(n_points, b, cap, err);
   const float4* src = frame_src(points, srcs, b, cap);
@@ -163,7 +167,8 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
                                                 int* __restrict__ coord, int* __restrict__ npts,
                                                 int* __restrict__ pillar_start,
                                                 int* __restrict__ pillar_cnt,
-                                                int* __restrict__ num_pillars) {
+                                                int* __restrict__ num_pillars,
+                                                unsigned* __restrict__ cnt_clear) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const unsigned* c = cnt + (size_t)b * g.G;
@@ -184,6 +189,8 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
   for (int j = threadIdx.x; j < kVoxTile; j += blockDim.x) {
     const int k = base + j;
     tile[j] = k < g.G ? c[k] : 0u;
+    // a release unit's counts are left zero for its next launch (this CTA is their last reader)
+    if (cnt_clear && k < g.G) cnt_clear[(size_t)b * g.G + k] = 0u;
   }
   __syncthreads();
   pre = make_int2(0, 0);
@@ -304,8 +311,11 @@ VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
 int vox_launch(const Geom& g, int batch, int cap, const float4* points, const int* n_points,
                int* cell, unsigned* cnt, int* pillar_of_cell, int* coord, int* npts,
                int* num_pillars, float4* pts, const VoxWork& w, cudaStream_t s,
-               const float4* const* srcs, float4* const* mirrors) {
-  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
+               const float4* const* srcs, float4* const* mirrors, const VoxUnitIO* io) {
+  const VoxUnitIO none;
+  if (!io) io = &none;
+  cudaError_t e = cudaSuccess;
+  if (!io->cnt_clean) e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
   // point kernels: grid-stride, about 8 blocks of 256 threads per SM over the whole batch (a
   // grid sized for the capacity costs microseconds of empty blocks when frames are short)
@@ -319,16 +329,19 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   const int px_max = (8 * sms + batch - 1) / batch;
   if (px > px_max) px = px_max;
   const dim3 pg(px > 0 ? px : 1, batch);
-  // the count follows the memset (a plain launch); the other four follow a kernel
-  vox_cell_count<<<pg, 256, 0, s>>>(g, cap, points, srcs, mirrors, n_points, cell, w.slot, cnt, w.err);
-  e = cudaGetLastError();
+  // dependent launches throughout (the count's predecessor may also be the counts' memset)
+  // the first kernel reads the unit table's host copy (its device copy is written by this kernel)
+  e = launch_pdl(vox_cell_count, pg, dim3(256), 0, s, g, cap, points, io->first_srcs ? io->first_srcs : srcs,
+                 io->first_mirrors ? io->first_mirrors : mirrors,
+                 io->first_counts ? io->first_counts : n_points, cell, w.slot, cnt, w.err, io->table_src,
+                 io->table_dst, io->table_words);
   if (e == cudaSuccess)
     e = launch_pdl(vox_tile_sums, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt, w.tile_sums,
                    w.ntiles);
   if (e == cudaSuccess)
     e = launch_pdl(vox_scan, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt,
                    (const int2*)w.tile_sums, w.ntiles, pillar_of_cell, coord, npts, w.pillar_start, w.pillar_cnt,
-                   num_pillars);
+                   num_pillars, io->cnt_clean ? cnt : (unsigned*)nullptr);
   if (e == cudaSuccess)
     e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
                    (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr);
