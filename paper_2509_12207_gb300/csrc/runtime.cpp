@@ -770,17 +770,27 @@ int pp_register_synthetic_chain(pp_ctx* c, int32_t chain_id, double period_ms, d
   int st = PP_OK;
   if (!c->have[kSynth]) {
     // first synthetic chain: units that run synthetic frames and their buffers
+    std::vector<Unit*> added;
     st = synth_alloc(&c->synth, kSynthUnits);
-    c->synth_first = (int)c->units.size();
     for (int k = 0; k < kSynthUnits && !st; ++k) {
       Unit* u = new (std::nothrow) Unit();
       if (!u) { st = fail(PP_ENOMEM, "register_synthetic_chain: host allocation"); break; }
       u->precision = kSynth;
+      added.push_back(u);
       st = cuda_status(cudaEventCreate(&u->start), "event");
       if (!st) st = cuda_status(cudaEventCreate(&u->done), "event");
-      c->units.push_back(u);
     }
-    if (st) return st;
+    if (st) {  // leave the context as it was
+      for (Unit* u : added) {
+        if (u->start) cudaEventDestroy(u->start);
+        if (u->done) cudaEventDestroy(u->done);
+        delete u;
+      }
+      synth_free(&c->synth);
+      return st;
+    }
+    c->synth_first = (int)c->units.size();
+    c->units.insert(c->units.end(), added.begin(), added.end());
     c->have[kSynth] = true;
     c->capacity[kSynth] = kMaxAdmitted;
   }
