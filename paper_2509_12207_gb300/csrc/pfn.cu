@@ -80,15 +80,41 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = num_pillars[b];
   const float4* src = dev::frame_src(points, srcs, b, cap);
-  for (int p = blockIdx.x * kWarps + wid; p < np; p += gridDim.x * kWarps) {
+  const int* csr_b = csr + (size_t)b * cap;
+  const int stride = gridDim.x * kWarps;
+  // Software pipeline over the warp's pillars: a pillar's metadata is loaded one pillar ahead
+  // and its first 32 point indices while the previous pillar's points are in flight, so each
+  // pillar waits on one memory round trip (its points) instead of three.
+  int p = blockIdx.x * kWarps + wid;
+  int count = 0, start = 0, cell = 0, first = INT_MAX;
+  if (p < np) {
     const size_t q = (size_t)b * g.P + p;
-    const int count = pillar_cnt[q];
-    const int best = dev::lowest_32(csr + (size_t)b * cap + pillar_start[q], count, lane);
+    count = pillar_cnt[q];
+    start = pillar_start[q];
+    cell = coord[q];
+    first = lane < count ? csr_b[start + lane] : INT_MAX;
+  }
+  for (; p < np; p += stride) {
+    const size_t q = (size_t)b * g.P + p;
+    const int pn = p + stride;  // warp-uniform
+    int count_n = 0, start_n = 0, cell_n = 0;
+    if (pn < np) {
+      const size_t qn = (size_t)b * g.P + pn;
+      count_n = pillar_cnt[qn];
+      start_n = pillar_start[qn];
+      cell_n = coord[qn];
+    }
+    const int best = dev::lowest_32_from(first, csr_b + start, count, lane);
     const float4 v = lane < count ? src[best] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int first_n = pn < np && lane < count_n ? csr_b[start_n + lane] : INT_MAX;
     float m0, m1;
-    dev::pfn_pillar(g, v, count < 32 ? count : 32, coord[q], lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
+    dev::pfn_pillar(g, v, count < 32 ? count : 32, cell, lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
     feat[q * 64 + lane] = m0;
     feat[q * 64 + lane + 32] = m1;
+    count = count_n;
+    start = start_n;
+    cell = cell_n;
+    first = first_n;
   }
 }
 

@@ -42,15 +42,20 @@ __device__ __forceinline__ int warp_bitonic_merge(int v, int lane) {
 }
 
 // The 32 smallest of `count` point indices seg[0..count), ascending, one per lane (INT_MAX past
-// count): a warp sort of the first 32, then a bitonic merge with each further sorted chunk.
-__device__ __forceinline__ int lowest_32(const int* seg, int count, int lane) {
-  int best = warp_sort(lane < count ? seg[lane] : INT_MAX, lane);
+// count): a warp sort of the first 32 (`first`: lane's entry of them, already loaded), then a
+// bitonic merge with each further sorted chunk.
+__device__ __forceinline__ int lowest_32_from(int first, const int* seg, int count, int lane) {
+  int best = warp_sort(first, lane);
   for (int k = 32; k < count; k += 32) {
     int v = warp_sort(k + lane < count ? seg[k + lane] : INT_MAX, lane);
     v = __shfl_sync(kFullMask, v, 31 - lane);          // reversed: best ++ v is bitonic
     best = warp_bitonic_merge(min(best, v), lane);     // lower half = 32 smallest of the union
   }
   return best;
+}
+
+__device__ __forceinline__ int lowest_32(const int* seg, int count, int lane) {
+  return lowest_32_from(lane < count ? seg[lane] : INT_MAX, seg, count, lane);
 }
 
 // PointNet of one pillar: lane j holds point v of the pillar (valid for j < n, n >= 1) at grid
