@@ -19,7 +19,10 @@ release units (a unit = up to ``max_batch`` frames run as one launch):
   until the sum of their estimated GPU times reaches Delta_eval; the batch then closes, and no
   further launch happens while ``max_closed`` closed batches are unfinished (2 = overlapped:
   wait for the previous batch; 1 = synchronous batched; 0 = no synchronisation);
-* the overall deadline-miss ratio (Eq. 3): mean over chains of each chain's miss ratio.
+* the overall deadline-miss ratio (Eq. 3): mean over chains of each chain's miss ratio;
+* urgency-centric CPU scheduling (Section 4.3), in the DES only: CPU segments that follow a
+  chain's GPU units run on a few cores either in order of readiness (the default scheduler's
+  view) or preemptively by descending urgency, re-ranked at every event.
 
 The comparison policies of the paper's Section 6.4 (EDF, SJF, HRRN and lowest chain utilisation
 first; the paper names them without definitions) are the textbook orders: a priority value
@@ -281,6 +284,7 @@ class SimFrame:
     util: float = 1.0
     est: Optional[List[float]] = None   # estimates per unit (defaults to the true durations)
     period: float = 0.0                 # the chain's period (us), for LCUF
+    cpu: Optional[List[float]] = None   # CPU segment after each GPU unit (us; 0 = none)
 
 
 @dataclasses.dataclass
@@ -293,19 +297,35 @@ class SimResult:
 
 def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: float = 1000.0,
              unit_time: Optional[Callable[[List[float]], float]] = None,
-             servers: int = 1) -> SimResult:
+             servers: int = 1, cpu_cores: int = 1, cpu_policy: str = "fifo") -> SimResult:
     """Discrete-event simulation of the release policy.
 
     GPU model: ``servers`` identical non-preemptive servers; a released unit waits in a queue
     ordered by (stream level, release order) and runs for ``unit_time(stage durations of its
     frames)`` (default: the sum).  Decision points: frame arrival, unit completion, delay
-    wake-up.  A frame re-enters the ready set after each of its units until all are done.
+    wake-up, CPU segment completion.  A frame re-enters the ready set after each of its units
+    (and the CPU segment that follows it, if any) until all are done.
+
+    CPU model (Section 4.3; frames with ``cpu`` segments): ``cpu_cores`` cores.  ``cpu_policy``
+    "fifo": segments run in the order they became ready, to completion (the default fair
+    scheduler's view of equal tasks).  "urgency": the paper's urgency-centric CPU scheduling --
+    fixed real-time priorities by descending urgency: whenever a segment becomes ready or a core
+    frees, the ready and running segments are ranked by their frames' urgency at that moment and
+    the most urgent ones hold the cores, a less urgent running segment being preempted (its
+    remaining time resumes later).  The GPU policy's slack counts the remaining CPU time (the
+    true segment durations serve as the estimates).
     """
     if unit_time is None:
         unit_time = lambda ds: float(sum(ds))
+    if cpu_policy not in ("fifo", "urgency"):
+        raise ValueError("cpu_policy must be fifo or urgency")
     by_id = {f.frame_id: f for f in frames}
     est = {f.frame_id: (f.est if f.est is not None else list(f.stages)) for f in frames}
+    cpu = {f.frame_id: (f.cpu if f.cpu is not None else [0.0] * len(f.stages)) for f in frames}
     nxt = {f.frame_id: 0 for f in frames}
+    cpu_left: Dict[int, float] = {}                  # frame -> remaining time of its CPU segment
+    cpu_ready: List[Tuple[float, int]] = []          # (ready time, frame), waiting for a core
+    cpu_run: Dict[int, float] = {}                   # frame -> time its current run started
     arrivals = sorted(frames, key=lambda f: (f.t_arr, f.frame_id))
     ai = 0
     ready: Dict[int, SimFrame] = {}
@@ -324,11 +344,56 @@ def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: fl
             _, members, _ = active[u]
             heapq.heappush(running, (now + unit_time([by_id[fid].stages[k] for fid, k in members]), u))
 
+    def rem_cpu(fid: int) -> float:
+        k = nxt[fid]
+        return cpu_left.get(fid, 0.0) + sum(cpu[fid][k:])
+
+    def slack_of(fid: int, now: float) -> float:
+        f = by_id[fid]
+        return f.deadline - sum(est[fid][nxt[fid]:]) - rem_cpu(fid) - now
+
+    def schedule_cpu(now: float) -> None:
+        # account the time run so far, then pick who holds the cores
+        for fid, t0 in list(cpu_run.items()):
+            cpu_left[fid] -= now - t0
+            cpu_run[fid] = now
+        if cpu_policy == "fifo":
+            cpu_ready.sort()
+            while cpu_ready and len(cpu_run) < cpu_cores:
+                _, fid = cpu_ready.pop(0)
+                cpu_run[fid] = now
+            return
+        # urgency: most urgent first (least slack; ties by chain id, arrival, frame id)
+        cands = [fid for _, fid in cpu_ready] + list(cpu_run)
+        cands.sort(key=lambda fid: (slack_of(fid, now), by_id[fid].chain_id, by_id[fid].t_arr, fid))
+        hold = set(cands[:cpu_cores])
+        for fid in list(cpu_run):
+            if fid not in hold:  # preempted
+                del cpu_run[fid]
+                cpu_ready.append((now, fid))
+        cpu_ready[:] = [(tr, fid) for tr, fid in cpu_ready if fid not in hold]
+        for fid in hold:
+            cpu_run.setdefault(fid, now)
+
+    def next_cpu_end() -> Optional[Tuple[float, int]]:
+        if not cpu_run:
+            return None
+        return min((t0 + cpu_left[fid], fid) for fid, t0 in cpu_run.items())
+
+    def frame_stage_done(fid: int, now: float) -> None:
+        f = by_id[fid]
+        if nxt[fid] >= len(f.stages):
+            res.done[fid] = now
+            res.missed[fid] = now > f.deadline
+        else:
+            ready[fid] = f
+
     while True:
         # decisions at time t
         while True:
             rlist = [Ready(f.frame_id, f.chain_id, f.t_arr, f.deadline,
-                           sum(est[f.frame_id][nxt[f.frame_id]:]), 0.0, f.precision, f.util, f.period)
+                           sum(est[f.frame_id][nxt[f.frame_id]:]), rem_cpu(f.frame_id), f.precision, f.util,
+                           f.period)
                      for f in ready.values()]
             d = decide(t, rlist, [a for a, _, _ in active.values()], gate.pending, cfg)
             for fid in d.drops:
@@ -342,8 +407,8 @@ def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: fl
             members = [(fid, nxt[fid]) for fid in d.frames]
             head = by_id[d.frames[0]]
             ul = priority(Ready(head.frame_id, head.chain_id, head.t_arr, head.deadline,
-                                sum(est[head.frame_id][nxt[head.frame_id]:]), 0.0, head.precision,
-                                head.util, head.period), t, cfg)
+                                sum(est[head.frame_id][nxt[head.frame_id]:]), rem_cpu(head.frame_id),
+                                head.precision, head.util, head.period), t, cfg)
             unit = seq
             seq += 1
             active[unit] = (Active(head.chain_id, ul), members, d.level)
@@ -361,24 +426,40 @@ def simulate(frames: Sequence[SimFrame], cfg: PolicyConfig, delay_quantum_us: fl
             cands.append(running[0][0])
         if wake is not None:
             cands.append(wake)
+        ce = next_cpu_end()
+        if ce is not None:
+            cands.append(ce[0])
         if not cands:
             break
         t = max(t, min(cands))
         if wake is not None and wake <= t:
             wake = None
+        cpu_changed = False
+        while True:  # CPU segments ending by t (in end order)
+            ce = next_cpu_end()
+            if ce is None or ce[0] > t:
+                break
+            fid = ce[1]
+            del cpu_run[fid]
+            del cpu_left[fid]
+            frame_stage_done(fid, ce[0])
+            cpu_changed = True
         while running and running[0][0] <= t:
             _, u = heapq.heappop(running)
             _, members, _ = active.pop(u)
             gate.finished(u)
             for fid, k in members:
                 nxt[fid] = k + 1
-                f = by_id[fid]
-                if nxt[fid] >= len(f.stages):
-                    res.done[fid] = t
-                    res.missed[fid] = t > f.deadline
+                seg = cpu[fid][k]
+                if seg > 0:  # the CPU part that follows this GPU unit
+                    cpu_left[fid] = seg
+                    cpu_ready.append((t, fid))
+                    cpu_changed = True
                 else:
-                    ready[fid] = f
+                    frame_stage_done(fid, t)
             start_units(t)
+        if cpu_changed or cpu_run or cpu_ready:
+            schedule_cpu(t)
         while ai < len(arrivals) and arrivals[ai].t_arr <= t:
             ready[arrivals[ai].frame_id] = arrivals[ai]
             ai += 1

@@ -326,3 +326,48 @@ def test_des_estimate_noise_only_moves_decisions():
     assert r0.done == plain.done and r0.dropped == plain.dropped and r0.releases == plain.releases
     assert set(r3.done) | set(r3.dropped) == set(range(400))
     assert r3.releases != plain.releases
+
+
+def test_des_cpu_priority_hand_example():
+    """CPU segments (Section 4.3), one core.  A (chain 0, arrives 0, deadline 10000): GPU 100 us,
+    then CPU 1000 us.  B (chain 1, arrives 50, deadline 650): GPU 100 us (runs 100-200 behind A),
+    then CPU 200 us.  FIFO CPU: B waits for A's segment (core busy 100-1100) and ends at 1300 --
+    missed.  Urgency CPU priority: at 200, B's slack is 650 - 200 - 200 = 250 against A's
+    10000 - 900 - 200 = 8900, so B preempts A, runs 200-400 and is met; A resumes and ends at
+    400 + 900 = 1300."""
+    frames = [S.SimFrame(0, 0, 0.0, 10000.0, [100.0], cpu=[1000.0]),
+              S.SimFrame(1, 1, 50.0, 650.0, [100.0], cpu=[200.0])]
+    cfg = S.PolicyConfig(policy=S.POLICY_FIFO, max_batch=1, max_closed=0, th_urgent=-1.0, early_exit=False)
+    fifo = S.simulate(frames, cfg, cpu_cores=1, cpu_policy="fifo")
+    assert fifo.done == {0: 1100.0, 1: 1300.0} and fifo.missed == {0: False, 1: True}
+    urg = S.simulate(frames, cfg, cpu_cores=1, cpu_policy="urgency")
+    assert urg.done == {0: 1300.0, 1: 400.0} and urg.missed == {0: False, 1: False}
+
+
+def test_des_cpu_segments_invariants():
+    """With a core per frame the CPU policies coincide (no contention); any run completes every
+    frame no earlier than its arrival plus its GPU and CPU work; the GPU policy's slack counts the
+    remaining CPU time (an urgency run drops a frame whose CPU segment alone outlasts its
+    deadline)."""
+    import numpy as np
+    rng = np.random.default_rng(12)
+    frames = []
+    for i in range(150):
+        t = float(i * 300 + rng.integers(0, 200))
+        g = [float(rng.integers(50, 200)) for _ in range(2)]
+        c = [float(rng.integers(0, 800)), float(rng.integers(100, 900))]
+        frames.append(S.SimFrame(i, i % 6, t, t + float(rng.choice([3000, 6000, 20000])), g, cpu=c))
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=2, delta_eval_us=300.0, max_closed=2,
+                         th_urgent=-1.0, early_exit=False)
+    a = S.simulate(frames, cfg, cpu_cores=1000, cpu_policy="fifo")
+    b = S.simulate(frames, cfg, cpu_cores=1000, cpu_policy="urgency")
+    assert a.done == b.done and a.releases == b.releases
+    for cores in (1, 2, 4):
+        for pol in ("fifo", "urgency"):
+            r = S.simulate(frames, cfg, cpu_cores=cores, cpu_policy=pol)
+            assert set(r.done) == set(range(150))
+            for f in frames:
+                assert r.done[f.frame_id] >= f.t_arr + sum(f.stages) + sum(f.cpu) - 1e-9
+    late = [S.SimFrame(0, 0, 0.0, 500.0, [100.0], cpu=[600.0])]
+    r = S.simulate(late, S.PolicyConfig(policy=S.POLICY_URGENCY, max_closed=0, th_urgent=-1.0))
+    assert r.dropped == {0: 0.0}
