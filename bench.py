@@ -50,7 +50,10 @@ def _args():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
-    ap.add_argument("--depth", type=int, default=2, help="steps in flight (1 = each step waits for the last)")
+    ap.add_argument("--depth", type=int, default=3, help="steps in flight (1 = each step waits for the last)")
+    ap.add_argument("--chains", type=int, default=2,
+                    help="sensor chains the steps alternate between (a chain's units run in order on its "
+                         "own streams; units of different chains may overlap on the GPU)")
     ap.add_argument("--tune-table", default=None,
                     help="conv tile table: loaded (no autotuning) if the file exists, else written after "
                          "autotuning, so that a profiled run launches the same tiles as a plain one")
@@ -140,8 +143,10 @@ def _conv_flops(g, bb):
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
 
-def _oracle_seconds(name, frames_to_run, head=False):
-    """Times the FP64 oracle on ``frames_to_run`` frames of the workload (this process)."""
+def _oracle_seconds(name, min_s, head=False, max_frames=512):
+    """Times the FP64 oracle on the workload's frames in turn (this process) until ``min_s``
+    seconds of oracle work have run (at least one frame, at most ``max_frames``); returns
+    (frames, seconds)."""
     from oracle import pillars as O
     g, bb, _prec, _batch, _cap, frames, w = _workload(name)
     hw = None
@@ -149,23 +154,30 @@ def _oracle_seconds(name, frames_to_run, head=False):
         from pp_synth import head_weights
         hw = head_weights(bb)
     t0 = time.perf_counter()
-    for k in range(frames_to_run):
+    k = 0
+    while k < max_frames and (k == 0 or time.perf_counter() - t0 < min_s):
         r = O.frame(frames[k % len(frames)], g, bb, w)
         if hw is not None:
             O.head(O.neck(r["blocks"], hw[0], hw[1]), hw[2], hw[3])
-    return time.perf_counter() - t0
+        k += 1
+    return k, time.perf_counter() - t0
 
 
-def _cpu_baseline(name, n_frames=1, head=False):
-    """Runs the oracle single-threaded in a child process (BLAS pinned to one thread)."""
+CPU_BASELINE_S = 10.0  # seconds of oracle work in the CPU baseline sample
+
+
+def _cpu_baseline(name, head=False, min_s=CPU_BASELINE_S):
+    """Runs the oracle single-threaded in a child process (BLAS pinned to one thread) on a
+    bounded sample: whole frames until about ``min_s`` seconds of oracle work."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
-                          "%s:%d:%d" % (name, n_frames, 1 if head else 0),
+                          "%s:%g:%d" % (name, min_s, 1 if head else 0),
                           "--workload", name], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         return {"value": None, "unit": "frames/s", "cores": 1, "kind": "oracle",
                 "sample": "failed: " + out.stderr[-300:]}
-    secs = float(out.stdout.strip().splitlines()[-1])
+    n_frames, secs = out.stdout.strip().splitlines()[-1].split()
+    n_frames, secs = int(n_frames), float(secs)
     return {"value": n_frames / secs, "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": "%d full frame(s) of the workload through the FP64 NumPy oracle, one thread, %.1f s"
                       % (n_frames, secs)}
@@ -444,7 +456,8 @@ def _run_ours(a, rank, world, dist):
     ctx = pp.Context(cfg)
     if a.tune_table and not tuned:
         pp.conv_tune_save(a.tune_table)
-    ctx.register_chain(0, 10000.0, 10000.0, prec)
+    for ch in range(max(1, a.chains)):
+        ctx.register_chain(ch, 10000.0, 10000.0, prec)
     frames_dev = [torch.from_numpy(f).cuda() for f in frames]
     frames_host = [torch.from_numpy(f).pin_memory() for f in frames]
     n_frames = batch
@@ -461,7 +474,7 @@ def _run_ours(a, rank, world, dist):
         # host outputs: each frame's result lands in a pinned host buffer, written by the unit's
         # own result copy over the host link (pp_submit_frames_ex)
         sinks = [free_sinks.pop() for _ in range(n_frames)] if host else None
-        rc, ids = ctx.submit_many([0] * n_frames, fs, host_out=sinks)
+        rc, ids = ctx.submit_many([k % max(1, a.chains)] * n_frames, fs, host_out=sinks)
         assert rc == pp.PP_OK and len(ids) == n_frames, rc
         if host:
             sink_of.update(zip(ids, sinks))
@@ -567,7 +580,8 @@ def _run_ours(a, rank, world, dist):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": n_frames, "steps_in_flight": a.depth, "points_per_frame":
+        "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": n_frames, "steps_in_flight": a.depth,
+                   "chains": max(1, a.chains), "points_per_frame":
                    [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
                          % (canvas_bytes // 2 ** 20)},
@@ -748,8 +762,8 @@ def _run_reference(a):
 def main():
     a = _args()
     if a.cpu_worker:
-        name, n, head = a.cpu_worker.split(":")
-        print(_oracle_seconds(name, int(n), head == "1"))
+        name, min_s, head = a.cpu_worker.split(":")
+        print("%d %.6f" % _oracle_seconds(name, float(min_s), head == "1"))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -795,7 +809,7 @@ def main():
         }
     if rank == 0:
         if not a.no_cpu_baseline:
-            res["cpu_baseline"] = _cpu_baseline(a.workload, 1, a.head)
+            res["cpu_baseline"] = _cpu_baseline(a.workload, a.head)
         print(json.dumps(res))
     if dist is not None:
         dist.destroy_process_group()

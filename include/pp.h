@@ -429,8 +429,10 @@ int pp_register_synthetic_chain(pp_ctx* ctx, int32_t chain_id, double period_ms,
  *   PP_POINTS_DEVICE (1) device memory, borrowed until the frame's result is polled;
  *   PP_POINTS_PINNED (2) page-locked host memory (cudaHostAlloc / cudaHostRegister, e.g. a
  *                        pinned torch tensor), borrowed until the frame's result is polled;
- *                        the unit's kernels read it in place over the host link, with no
- *                        staging copy and no separate transfer.  Other host memory: PP_EINVAL. */
+ *                        no staging copy: a release unit of one frame reads it in place over
+ *                        the host link from its own kernels; a unit batching several frames
+ *                        copies it by copy engine into the unit's device point slot ahead of
+ *                        its kernels (in the unit's stream).  Other host memory: PP_EINVAL. */
 enum { PP_POINTS_HOST = 0, PP_POINTS_DEVICE = 1, PP_POINTS_PINNED = 2 };
 /* Submits one frame of `n_points` float4 points (is_device_ptr: PP_POINTS_*; device and pinned
  * points 16-byte aligned).
@@ -453,10 +455,12 @@ int pp_submit_frames(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const flo
                      const double* abs_deadline_us, uint64_t* frame_ids_out, int32_t* n_admitted);
 /* pp_submit_frames with a host output buffer per frame: host_out[i] (host array of n pointers,
  * may be NULL, entries may be NULL) is page-locked host memory of pp_result_bytes() bytes for
- * the frame's precision, 16-byte aligned, borrowed until the frame is polled.  The unit's
- * result copy writes the frame's final output (the out_dev map: last backbone block, or the
- * head) there over the host link as part of the same launch, so a caller that wants its result
- * on the host needs no copy of its own (pp_result.out_host).  Other host memory: PP_EINVAL,
+ * the frame's precision, 16-byte aligned, borrowed until the frame is polled.  The unit writes
+ * the frame's final output (the out_dev map: last backbone block, or the head) there as part of
+ * the same launch (a one-frame unit from its result copy kernel over the host link; a unit
+ * batching several frames by one copy-engine copy per frame after its kernels, in its stream),
+ * so a caller that wants its result on the host needs no copy of its own (pp_result.out_host;
+ * complete when the frame is polled).  Other host memory: PP_EINVAL,
  * nothing admitted.  Ignored for synthetic-load chains. */
 int pp_submit_frames_ex(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
                         const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,

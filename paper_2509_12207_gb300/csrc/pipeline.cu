@@ -454,6 +454,8 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
     rc.src[0] = static_cast<const char*>(head_);
     rc.bytes[0] = (size_t)(H0 + 2) * (W0 + 2) * m.head_c * (m.precision == PP_F32 ? 4 : 2);
     rc.off[0] = res_off_[0];
+    hout_off_ = rc.off[0];
+    hout_bytes_ = rc.bytes[0];
   } else {
     const std::vector<int> kept = m.kept_blocks();
     rc.nblocks = (int)kept.size();
@@ -465,6 +467,8 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
       rc.bytes[k] = (size_t)(L.Ho + 2) * (L.Wo + 2) * L.cout * (m.precision == PP_F32 ? 4 : 2);
       rc.off[k] = res_off_[k];
     }
+    hout_off_ = rc.off[rc.hblock];
+    hout_bytes_ = rc.bytes[rc.hblock];
   }
   return cuda_status(launch_pdl(result_copy, dim3(std::max(1, 8 * sms_ / n), n), dim3(256), 0, s, rc,
                                 (const UnitTable*)tab_dev_),
@@ -488,11 +492,17 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
   if (st) return st;
   UnitTable& t = *tab_host_;
   memset(&t, 0, sizeof(t));
+  // Host frames and host outputs of a unit that batches several frames move by copy engine
+  // (into the unit's point slots before its kernels, out of its result slots after them), so
+  // that the transfers overlap the kernels of other units in flight; a one-frame unit reads its
+  // points and writes its output over the host link from its own kernels (no copy on its
+  // critical path).
+  const bool ce = n > 1;
   for (int i = 0; i < n; ++i) {
     t.counts[i] = counts[i];
     t.dst[i] = dst ? dst[i] : nullptr;
-    t.hdst[i] = hdst && t.dst[i] ? hdst[i] : nullptr;
-    if (direct && direct[i]) {
+    t.hdst[i] = hdst && t.dst[i] && !ce ? hdst[i] : nullptr;
+    if (direct && direct[i] && !(host_mapped && host_mapped[i] && ce)) {
       t.src[i] = reinterpret_cast<const float4*>(frames[i]);
       t.gsrc[i] = t.src[i];
       if (host_mapped && host_mapped[i]) {
@@ -514,6 +524,11 @@ int Pipeline::run(int n, const float* const* frames, const int* counts, const bo
     st = cuda_status(cudaGraphLaunch(graphs_[n], s), "graph launch");
   else
     st = enqueue(n, s);
+  if (!st && ce && hdst && dst)
+    for (int i = 0; i < n && !st; ++i)
+      if (hdst[i] && dst[i])
+        st = cuda_status(cudaMemcpyAsync(hdst[i], dst[i] + hout_off_, hout_bytes_, cudaMemcpyDeviceToHost, s),
+                         "host output copy");
   if (!st) st = cuda_status(cudaEventRecord(tab_ev_, s), "unit table event");
   return st;  // the result copy kernel has written num_host_ (pillar counts) over the host link
 }

@@ -110,6 +110,7 @@ class Pipeline {
   int* num_host_dev_ = nullptr;    // its device view
   cudaEvent_t tab_ev_ = nullptr;   // after the last run (whose first kernel read the table)
   std::vector<size_t> res_off_;
+  size_t hout_off_ = 0, hout_bytes_ = 0;  // the final output inside a result slot
   int sms_ = 1;
   int *cell_ = nullptr, *poc_ = nullptr, *coord_ = nullptr, *npts_ = nullptr, *num_ = nullptr;
   unsigned* cnt_ = nullptr;

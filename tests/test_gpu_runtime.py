@@ -398,18 +398,38 @@ def test_runtime_batched_bf16_unit_full_workload():
         ctx.destroy()
 
 
-def test_runtime_pinned_host_points(small_clouds):
-    """Page-locked host frames are borrowed and read in place by the unit's kernels (no staging
-    copy): results match the oracle exactly as device frames do; pageable memory is refused in
-    that mode."""
+def _submit_batched_or_alone(ctx, pinned, together, **kw):
+    """Submits the frames together (one release unit batching them) or one at a time, each
+    polled before the next (one-frame units); returns (ids, results by id)."""
+    if together:
+        rc, ids = ctx.submit_many([0] * len(pinned), pinned, **kw)
+        assert rc == pp.PP_OK
+        res = {r.frame_id: r for r in _drain(ctx, len(ids))}
+        assert max(r.batch for r in res.values()) > 1  # the batched path did run
+        return ids, res
+    ids, res = [], {}
+    for k in range(len(pinned)):
+        one = {key: v[k:k + 1] for key, v in kw.items()}
+        rc, got = ctx.submit_many([0], pinned[k:k + 1], **one)
+        assert rc == pp.PP_OK and len(got) == 1
+        ids += got
+        for r in _drain(ctx, 1):
+            assert r.batch == 1
+            res[r.frame_id] = r
+    return ids, res
+
+
+@pytest.mark.parametrize("together", [True, False], ids=["batched-unit", "one-frame-units"])
+def test_runtime_pinned_host_points(small_clouds, together):
+    """Page-locked host frames are borrowed without a staging copy (a batched unit copies them by
+    copy engine, a one-frame unit reads them in place over the host link): results match the
+    oracle exactly as device frames do; pageable memory is refused in that mode."""
     import ctypes
     ctx, keep = _ctx(max_batch=4)
     try:
         ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
         pinned = [torch.from_numpy(c).pin_memory() for c in small_clouds]
-        rc, ids = ctx.submit_many([0] * len(pinned), pinned)
-        assert rc == pp.PP_OK
-        res = {r.frame_id: r for r in _drain(ctx, len(ids))}
+        ids, res = _submit_batched_or_alone(ctx, pinned, together)
         for k, fid in enumerate(ids):
             ref = _ref(small_clouds[k])
             assert res[fid].num_pillars == ref["vox"]["num_pillars"]
@@ -540,9 +560,11 @@ def test_runtime_synthetic_load_chain(small_clouds):
         ctx.destroy()
 
 
-def test_runtime_host_output_buffers(small_clouds):
-    """Frames submitted with page-locked host output buffers: when polled, each buffer holds
-    exactly the frame's final output; pageable memory is refused and admits nothing."""
+@pytest.mark.parametrize("together", [True, False], ids=["batched-unit", "one-frame-units"])
+def test_runtime_host_output_buffers(small_clouds, together):
+    """Frames submitted with page-locked host output buffers (written by copy engine for a
+    batched unit, by the result copy kernel for a one-frame unit): when polled, each buffer
+    holds exactly the frame's final output; pageable memory is refused and admits nothing."""
     ctx, keep = _ctx(max_batch=4)
     try:
         ctx.register_chain(0, 100.0, 100.0, pp.PP_F32)
@@ -550,9 +572,7 @@ def test_runtime_host_output_buffers(small_clouds):
         assert nbytes > 0
         outs = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in small_clouds]
         dev = [torch.from_numpy(c).to(DEV) for c in small_clouds]
-        rc, ids = ctx.submit_many([0] * len(dev), dev, host_out=outs)
-        assert rc == pp.PP_OK
-        res = {r.frame_id: r for r in _drain(ctx, len(ids))}
+        ids, res = _submit_batched_or_alone(ctx, dev, together, host_out=outs)
         for k, fid in enumerate(ids):
             r = res[fid]
             assert r.out_host
