@@ -282,7 +282,8 @@ int pp_tf32_split(const float* x, float* lo, int64_t n, void* stream);
  * for `dtype` (device, pp_conv_packed_bytes() bytes): PP_F32 -> [9*cin][cout] float,
  * PP_BF16 -> [cout][9*cin] bf16 (round to nearest even), PP_F32_TC -> [2][cout][9*cin] float
  * (plane 0: weight with the 13 low mantissa bits cleared, plane 1: the remainder);
- * K index = (ky*3+kx)*cin + ci. */
+ * K index = (ky*3+kx)*cin + ci.  cin and cout multiples of 64, as pp_conv3x3 takes them (else
+ * 0 bytes / PP_EINVAL: pp_conv3x3 reads 9*cin*cout weights from the buffer it is given). */
 size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype);
 int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t dtype,
                          void* w_packed, void* stream);

@@ -427,6 +427,9 @@ def scatter_update(state, feat, coord, num_pillars, pillar_of_cell, stream=None)
 def pack_conv_weights(w_oihw, dtype, stream=None):
     """w_oihw: cuda float32 [cout, cin, 3, 3] -> packed weights for pp_conv3x3."""
     import torch
+    if w_oihw.dim() != 4 or tuple(w_oihw.shape[2:]) != (3, 3):
+        raise PPError(PP_EINVAL, "pack_conv_weights: weights must be OIHW [cout, cin, 3, 3], got %s"
+                      % (tuple(w_oihw.shape),))
     _need_cuda(w_oihw)
     cout, cin = int(w_oihw.shape[0]), int(w_oihw.shape[1])
     n = lib().pp_conv_packed_bytes(cin, cout, dtype)

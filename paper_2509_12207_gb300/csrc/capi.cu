@@ -314,7 +314,7 @@ int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int
 }
 
 size_t pp_conv_packed_bytes(int32_t cin, int32_t cout, int32_t dtype) {
-  if (cin <= 0 || cout <= 0) return 0;
+  if (cin <= 0 || cout <= 0 || cin % 64 || cout % 64) return 0;
   if (dtype == PP_F32_TC) return (size_t)2 * 9 * cin * cout * 4;
   return (size_t)9 * cin * cout * (dtype == PP_F32 ? 4 : 2);
 }
@@ -324,6 +324,8 @@ int pp_conv_pack_weights(const float* w_oihw, int32_t cin, int32_t cout, int32_t
   if (!w_oihw || !w_packed || cin <= 0 || cout <= 0 ||
       (dtype != PP_F32 && dtype != PP_BF16 && dtype != PP_F32_TC))
     return fail(PP_EINVAL, "pack_weights: bad argument");
+  // the shapes pp_conv3x3 takes: a buffer packed for any other cin would be read past its end
+  if (cin % 64 || cout % 64) return fail(PP_EINVAL, "pack_weights: cin and cout must be multiples of 64");
   return conv_pack_launch(w_oihw, cin, cout, dtype, w_packed, static_cast<cudaStream_t>(stream));
 }
 

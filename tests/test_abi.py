@@ -53,6 +53,13 @@ def test_version_and_errors(lib):
     rc = lib.pp_conv3x3(1, 7, 8, 64, 64, 2, 0, 16, 16, 16, 16, -1, None)
     assert rc == pp.PP_EINVAL and b"even" in lib.pp_last_error()
     assert lib.pp_conv_packed_bytes(64, 128, 1) == 9 * 64 * 128 * 2
+    # weights are packed only for the shapes pp_conv3x3 takes (it reads 9 cin cout of them)
+    assert lib.pp_conv_packed_bytes(3, 64, 1) == 0 and lib.pp_conv_packed_bytes(64, 72, 2) == 0
+    rc = lib.pp_conv_pack_weights(16, 3, 64, 2, 16, None)
+    assert rc == pp.PP_EINVAL and b"multiples of 64" in lib.pp_last_error()
+    import torch
+    with pytest.raises(pp.PPError, match="OIHW"):
+        pp.pack_conv_weights(torch.zeros(64, 3, 3, 64), pp.PP_F32_TC)
 
 
 def test_bn_fold_matches_definition(lib):
