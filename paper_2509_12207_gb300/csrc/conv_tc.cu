@@ -1071,8 +1071,10 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
                     void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0,
                     const GemmOpts& g = GemmOpts());
 int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
-                     cudaStream_t s);
-int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0) + 1; }
+                     cudaStream_t s, int strips_per_cta = 2);
+// BF16 tiles: kTilesTC, then the persistent ones, then the row-streaming kernel with about two
+// row strips per CTA and with one (longer) strip per CTA
+int conv_bf16_tile_count() { return (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0])) + conv_tcp_tile_count(0) + 2; }
 
 int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfloat16* w,
                      const float* ss, __nv_bfloat16* out, int tile, cudaStream_t s) {
@@ -1082,7 +1084,8 @@ int conv_bf16_launch(const ConvShape& c, const __nv_bfloat16* in, const __nv_bfl
   const int n_old = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
   const int n_p = conv_tcp_tile_count(0);
   if ((tile < 0 && c.cin == 64 && c.cout == 64) || tile == n_old + n_p)
-    return conv_rows_launch(c, in, w, ss, out, s);
+    return conv_rows_launch(c, in, w, ss, out, s, 2);
+  if (tile == n_old + n_p + 1) return conv_rows_launch(c, in, w, ss, out, s, 1);
   if (tile < 0 || tile >= n_old) return conv_tcp_launch(0, c, in, w, ss, out, tile < 0 ? -1 : tile - n_old, s);
   if (tile < 0 || tile >= conv_bf16_tile_count() || c.cout % kTilesTC[tile].bn)
     return fail(PP_EINVAL, "conv bf16: tile %d unsupported for cout %d", tile, c.cout);
@@ -1357,8 +1360,12 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
 }
 
 // Row-streaming BF16 conv (64 -> 64 channels).
+// strips_per_cta: the output rows are cut into strips of rc >= 4 rows so that there are about
+// strips_per_cta strips per SM (2: a CTA runs two shorter strips; 1: one longer strip each, so
+// that the ring is filled once per CTA)
 int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const float* ss, void* out,
-                     cudaStream_t s) {
+                     cudaStream_t s, int strips_per_cta) {
+  if (strips_per_cta < 1 || strips_per_cta > 2) return fail(PP_EINVAL, "row conv: 1 or 2 strips per CTA");
   auto enc = encode_fn();
   if (!enc) return fail(PP_EDEVICE, "cuTensorMapEncodeTiled is unavailable");
   if (c.cin != 64 || c.cout != 64) return fail(PP_EINVAL, "row conv: needs 64 input and 64 output channels");
@@ -1401,7 +1408,8 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   a.nseg = (c.Wo + a.pv - 1) / a.pv;
   const int sms = num_sms();
   const long rows = (long)c.batch * a.nseg * c.Ho;
-  int rc = (int)((rows + 2L * sms - 1) / (2L * sms));
+  const long slots = (long)strips_per_cta * sms;
+  int rc = (int)((rows + slots - 1) / slots);
   if (rc < 4) rc = 4;
   if (rc > c.Ho) rc = c.Ho;
   a.rc = rc;
@@ -1463,8 +1471,8 @@ size_t conv_sk_workspace_bytes(const ConvShape& c) {
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent) {
   if (dtype == PP_BF16) {
     const int n0 = (int)(sizeof(kTilesTC) / sizeof(kTilesTC[0]));
-    if (tile < 0 || tile > n0 + kNPB) return PP_EINVAL;
-    if (tile == n0 + kNPB) { *bh = 1; *bw = 128; *bn = 64; *persistent = 2; return PP_OK; }  // row streaming
+    if (tile < 0 || tile > n0 + kNPB + 1) return PP_EINVAL;
+    if (tile >= n0 + kNPB) { *bh = 1; *bw = 128; *bn = 64; *persistent = 2; return PP_OK; }  // row streaming
     if (tile < n0) { *bh = kTilesTC[tile].bh; *bw = kTilesTC[tile].bw; *bn = kTilesTC[tile].bn; *persistent = 0; }
     else { const TileP& t = kTilesPB[tile - n0]; *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = 1; }
     return PP_OK;
