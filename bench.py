@@ -86,13 +86,13 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (383.0e6, "a84e3cb16b674c75b09aac4522a1eec9ed161a94b12d70dd28b58550d36e9072"),
-    "cfg3-bf16": (84.5e6, "a84e3cb16b674c75b09aac4522a1eec9ed161a94b12d70dd28b58550d36e9072"),
+    "cfg2-fp32": (382.5e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
+    "cfg3-bf16": (84.5e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
 }
 # the same for the neck and head launches of one step (upsamplings + head)
 NECK_HEAD_TRAFFIC = {
-    "cfg2-fp32": (250.0e6, "a84e3cb16b674c75b09aac4522a1eec9ed161a94b12d70dd28b58550d36e9072"),
-    "cfg3-bf16": (42.3e6, "a84e3cb16b674c75b09aac4522a1eec9ed161a94b12d70dd28b58550d36e9072"),
+    "cfg2-fp32": (250.3e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
+    "cfg3-bf16": (42.3e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
 }
 
 
