@@ -32,6 +32,12 @@ WORKLOADS = {
     "cfg3-bf16": "batched BF16: 8 frames of 30k-150k uniform points per unit, 216x248 grid, 3 conv3x3 64ch",
 }
 
+# (chains, steps in flight) of the throughput run: the steps alternate between the chains (a
+# chain's units run in order on its streams; units of different chains overlap on the GPU); the
+# 8-frame unit's short kernels keep more units in flight busy
+SERVING_SHAPE = {"cfg3-bf16": (3, 6)}
+SERVING_SHAPE_DEFAULT = (2, 3)
+
 REFERENCE_BUDGET_S = 90  # wall-clock cap of the reference arm's timed steps
 
 HEAD_NOTE = ", + neck (transposed convs to 128 channels each, concatenated) and 1x1 head (72 outputs)"
@@ -50,10 +56,11 @@ def _args():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
-    ap.add_argument("--depth", type=int, default=3, help="steps in flight (1 = each step waits for the last)")
-    ap.add_argument("--chains", type=int, default=2,
+    ap.add_argument("--depth", type=int, default=None,
+                    help="steps in flight (1 = each step waits for the last; default per workload)")
+    ap.add_argument("--chains", type=int, default=None,
                     help="sensor chains the steps alternate between (a chain's units run in order on its "
-                         "own streams; units of different chains may overlap on the GPU)")
+                         "own streams; units of different chains may overlap on the GPU; default per workload)")
     ap.add_argument("--tune-table", default=None,
                     help="conv tile table: loaded (no autotuning) if the file exists, else written after "
                          "autotuning, so that a profiled run launches the same tiles as a plain one")
@@ -63,7 +70,11 @@ def _args():
     ap.add_argument("--serve-modes", default="urgency,plain",
                     help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf, saedf, eqdf")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    a = ap.parse_args()
+    chains, depth = SERVING_SHAPE.get(a.workload, SERVING_SHAPE_DEFAULT)
+    a.chains = chains if a.chains is None else a.chains
+    a.depth = depth if a.depth is None else a.depth
+    return a
 
 
 def _workload(name):
