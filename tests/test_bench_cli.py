@@ -1,0 +1,54 @@
+"""bench.py's host side without a GPU: the per-workload serving shape, the CPU-baseline worker
+and the reference arm's JSON line (the oracle, timed on the host, on the small workload)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _args(*argv):
+    old = sys.argv
+    sys.argv = ["bench.py", *argv]
+    try:
+        return bench._args()
+    finally:
+        sys.argv = old
+
+
+def test_serving_shape_defaults_per_workload():
+    a = _args()
+    assert (a.workload, a.chains, a.depth) == ("cfg2-fp32", 2, 3)
+    a = _args("--workload", "cfg3-bf16")
+    assert (a.chains, a.depth) == bench.SERVING_SHAPE["cfg3-bf16"] == (3, 6)
+    a = _args("--workload", "cfg3-bf16", "--chains", "1", "--depth", "2")
+    assert (a.chains, a.depth) == (1, 2)
+    assert a.steps >= 1 and a.warmup >= 3
+
+
+def test_cpu_worker_runs_whole_frames_until_the_budget():
+    n, secs = bench._oracle_seconds("cfg1-fp32", 0.0)
+    assert n == 1 and secs > 0          # at least one frame, even with no budget
+    n, secs = bench._oracle_seconds("cfg1-fp32", 1e9, max_frames=2)
+    assert n == 2 and secs > 0          # bounded by the frame cap
+
+
+@pytest.mark.timeout(300)
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cfg1-fp32", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, cwd=ROOT, timeout=280,
+                         env=dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1"))
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "frames/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["metric"] == "pillar frames/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
