@@ -405,6 +405,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 // halves.  Loop counters advance incrementally (no division in the steady state) and shared
 // memory descriptors are built once and offset by addition.  192 threads: warp 0 TMA, warp 1
 // TMEM allocation + MMA, warps 2-5 reduce and store (TMEM lane quarters 2, 3, 0, 1).
+// HALO (3xTF32, BN 64, stride 1): a tile is 128 consecutive pixels of the output laid out over
+// the padded width W + 2 (the two padding columns of each row are computed and not stored), so
+// that for every tap the 128 input pixels are consecutive too: input pixel = output pixel +
+// ky (W + 2) + kx in the flattened padded image.  A ring stage holds 130 consecutive input
+// pixels (32 channels, value and remainder) and the weights of the three kx taps, and the MMAs
+// of tap kx read the row range from pixel kx on (a K-major 128-byte-swizzled operand may start
+// at any 128-byte row of its buffer), so one load serves three taps: 82 KiB per three K blocks
+// instead of 144 KiB, at any width.  A stage is one accumulation group (fold 3), in the order
+// ky, channel chunk, kx.
 
 struct PArgs {
   ConvShape c;
@@ -422,7 +431,7 @@ struct PArgs {
   unsigned* sem;  // stream-K: [total] arrival counters, zero between launches
 };
 
-template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK>
+template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false>
 __global__ void __launch_bounds__(192, 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
             const __grid_constant__ CUtensorMap tmB, PArgs args) {
@@ -431,7 +440,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
   constexpr uint32_t kAK = MODE == 1 ? 2 * kA : kA;        // per K block: A (+ lo)
   constexpr uint32_t kBK = MODE == 1 ? 2 * kB : kB;        // per K block: B (+ lo plane)
-  constexpr uint32_t kStageA = KPS * kAK;
+  constexpr uint32_t kHaloRow = 130 * 128;                 // HALO: one padded input row, one plane
+  constexpr uint32_t kHaloA = (kHaloRow + 1023) / 1024 * 1024;
+  static_assert(!HALO || (MODE == 1 && BN == 64 && !S2 && !SK && KPS == 3), "halo rows: 3xTF32, BN 64, stride 1");
+  constexpr uint32_t kStageA = HALO ? 2 * kHaloA : KPS * kAK;
   constexpr uint32_t kStageB = KPS * kBK;
   constexpr int NACC = MODE == 1 ? 2 * BN : BN;            // TMEM columns per accumulator buffer
   // accumulator buffers in TMEM (512 columns): four where they fit, so that the MMAs can run
@@ -531,7 +543,34 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   };
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (HALO && lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        int b, oy0, ox0, n0;
+        decode(t, b, oy0, ox0, n0);
+        for (int ky = 0; ky < 3 && ok; ++ky) {
+          for (int cc = 0; cc < kchunks; ++cc) {
+            if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
+            mbar_expect_tx(&full[s], 2u * kHaloRow + 3u * kBK);
+            uint8_t* a = sA + s * kStageA;
+            // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
+            const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
+            tma_2d(a, &tmA, &full[s], cc * BK, pix);
+            tma_2d(a + kHaloA, &tmAlo, &full[s], cc * BK, pix);
+            for (int kx = 0; kx < 3; ++kx) {
+              uint8_t* bb = sB + s * kStageB + kx * kBK;
+              const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+              tma_3d(bb, &tmB, &full[s], kk, n0, 0);
+              tma_3d(bb + kB, &tmB, &full[s], kk, n0, 1);
+            }
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+        }
+      }
+    } else if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -577,7 +616,45 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (HALO && lane == 0) {
+      const uint32_t id = idesc_tf32<2 * BN>();
+      const uint32_t id2 = idesc_tf32<BN>();
+      const uint64_t dA0 = sdesc(sA), dB0 = sdesc(sB);
+      int s = 0, gg = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        {
+          int t2, a2, b2;
+          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
+        }
+        for (int g = 0; g < 3 * kchunks; ++g) {  // one stage = one accumulation group
+          const int buf = gg & (NBUF - 1);
+          if (gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, 2u)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * NACC);
+          const uint64_t da = dA0 + ((uint64_t)(s * kStageA) >> 4);
+          const uint64_t db = dB0 + ((uint64_t)(s * kStageB) >> 4);
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // tap kx: the row from pixel kx on; K step k: 8 channels = 32 bytes into each row
+              const uint64_t a_k = da + (uint64_t)((kx * 128 + k * 32) >> 4);
+              const uint64_t b_k = db + (uint64_t)((kx * kBK + k * 32) >> 4);
+              mma_tf32(d, a_k, b_k, id, (kx == 0 && k == 0) ? 0u : 1u);     // A_hi x [B_hi|B_lo]
+              mma_tf32(d, a_k + (kHaloA >> 4), b_k, id2, 1u);               // A_lo x B_hi
+            }
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&kdone[buf]);
+          ++gg;
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+    } else if (lane == 0) {
       const uint32_t id = MODE == 1 ? idesc_tf32<2 * BN>() : idesc<BN>();
       const uint32_t id2 = idesc_tf32<BN>();
       const uint64_t dA0 = sdesc(sA), dB0 = sdesc(sB);
@@ -639,7 +716,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int gpt = (k1 - k0 + fold - 1) / fold;  // accumulation groups of this piece
       int b, oy0, ox0, n0;
       decode(t, b, oy0, ox0, n0);
-      const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
+      // HALO: output pixel ox0 + r of the image laid out over the padded width
+      const int oy = HALO ? (ox0 + r) / (c.W + 2) : oy0 + r / args.bw;
+      const int ox = HALO ? (ox0 + r) % (c.W + 2) : ox0 + r % args.bw;
       const bool in_range = oy < c.Ho && ox < c.Wo;
       // output pixel of this row for this N tile (a transposed conv spreads the N tiles of one
       // input pixel over its up x up output block); first channel written and its BN index
@@ -1067,6 +1146,7 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
 }  // namespace
 
 int conv_tcp_tile_count(int mode);
+int conv_tcp_sk_first();
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
                     void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0,
                     const GemmOpts& g = GemmOpts());
@@ -1155,8 +1235,8 @@ int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split,
   if (tile < 0) {
     tile = tuned_tile(PP_F32_TC, c);
     // a stream-K choice needs a workspace; without one, the same tile without stream-K
-    const int np = conv_tcp_tile_count(1) / 2;
-    if (tile >= np && (!ws || ws_bytes < conv_sk_workspace_bytes(c))) tile -= np;
+    const int np = conv_tcp_sk_first();
+    if (tile >= np && tile < 2 * np && (!ws || ws_bytes < conv_sk_workspace_bytes(c))) tile -= np;
   }
   return conv_tcp_launch(1, c, in, w_split, ss, out, tile, s, ws, ws_bytes);
 }
@@ -1174,6 +1254,9 @@ constexpr TileP kTilesPF[] = {{8, 16, 64}, {4, 32, 64}, {16, 8, 64}, {2, 64, 64}
                               {4, 32, 128}, {16, 8, 128}};
 constexpr int kNPB = (int)(sizeof(kTilesPB) / sizeof(kTilesPB[0]));
 constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
+// 3xTF32 tile 2 kNPF: one 128-pixel output row segment whose three kx taps share one loaded
+// 130-pixel input row (stride-1 3x3 convs)
+constexpr TileP kTileHalo = {1, 128, 64};
 
 // Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
 // stage = KPS x (32 KiB A (+lo) + 2 x BN x 128 B).  All fill ~192 KiB of shared memory.  Two K
@@ -1195,6 +1278,12 @@ constexpr size_t p_smem() {
          4 * 4096 +                                   // epilogue transposing buffers
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
+// halo-row tile (3xTF32, BN 64): 2 stages of (two 130-row planes rounded to 1 KiB, three taps
+// of B value and remainder)
+constexpr size_t kHaloStages = 2;
+constexpr size_t p_smem_halo() {
+  return 1024 + kHaloStages * (2 * 17408 + 3 * 2 * 64 * 128) + 4 * 4096 + (2 * kHaloStages + 8) * 8 + 16;
+}
 
 int num_sms() {
   static int n = 0;
@@ -1207,15 +1296,17 @@ int num_sms() {
   return n;
 }
 
-template <int MODE, int BN, bool S2, bool SK>
+template <int MODE, int BN, bool S2, bool SK, bool HALO = false>
 int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
              cudaStream_t s) {
-  constexpr int ST = p_stages<MODE, BN>();
-  constexpr int KPS = p_kps<MODE, BN>();
-  constexpr size_t bytes = p_smem<MODE, BN>() + 2 * 1024 * sizeof(float);  // + folded BN (cout <= 1024)
+  constexpr int ST = HALO ? (int)kHaloStages : p_stages<MODE, BN>();
+  constexpr int KPS = HALO ? 3 : p_kps<MODE, BN>();
+  // + folded BN (cout <= 1024)
+  constexpr size_t bytes = (HALO ? p_smem_halo() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
+  static_assert(bytes <= 227 * 1024, "persistent conv shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK>,
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_status(e, "persistent conv smem attribute");
     attr_set = true;
@@ -1225,7 +1316,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK>, dim3(grid), dim3(192), bytes, s, a, alo, w,
+  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>, dim3(grid), dim3(192), bytes, s, a, alo, w,
                                 args),
                      "persistent conv launch");
 }
@@ -1263,13 +1354,16 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     return fail(PP_EINVAL, "persistent conv: bad GEMM options");
   const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
   const int n = mode == 1 ? kNPF : kNPB;
-  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition
-  const bool sk = mode == 1 && ptile >= n;
+  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition; 2 kNPF: halo rows
+  const bool halo = mode == 1 && ptile == 2 * n;
+  if (halo && (c.stride != 1 || g.taps != 9 || g.up != 1 || c.cout % 64 || co_blk % 64))
+    return fail(PP_EINVAL, "persistent conv: the halo-row tile needs a stride-1 3x3 conv");
+  const bool sk = mode == 1 && ptile >= n && !halo;
   if (sk) ptile -= n;
-  if (ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
-  if (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn)
+  if (!halo && ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
+  if (!halo && (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn))
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
-  const TileP t = tiles[ptile];
+  const TileP t = halo ? kTileHalo : tiles[ptile];
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
     return fail(PP_EINVAL, "persistent conv: operands must be 16-byte aligned");
   const int BK = mode == 1 ? 32 : 64;
@@ -1282,7 +1376,15 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     const size_t in_plane = c.in_plane ? c.in_plane : (size_t)c.batch * Hp * Wp * c.cin;
     void* base = static_cast<char*>(const_cast<void*>(in)) + (size_t)plane * in_plane * el;
     CUtensorMap* m = plane ? &talo : &ta;
-    if (c.stride == 1) {
+    if (halo) {
+      // the flattened padded image: 130 consecutive pixels per load for 128 outputs
+      cuuint64_t dims[2] = {(cuuint64_t)c.cin, (cuuint64_t)Hp * Wp * c.batch};
+      cuuint64_t strides[1] = {(cuuint64_t)c.cin * el};
+      cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(t.bw + 2)};
+      cuuint32_t es[2] = {1, 1};
+      r = enc(m, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else if (c.stride == 1) {
       cuuint64_t dims[3] = {(cuuint64_t)c.cin, (cuuint64_t)Wp, (cuuint64_t)Hp * c.batch};
       cuuint64_t strides[2] = {(cuuint64_t)c.cin * el, (cuuint64_t)Wp * c.cin * el};
       cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)t.bw, (cuuint32_t)t.bh};
@@ -1316,11 +1418,12 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.c = c;
   args.bh = t.bh;
   args.bw = t.bw;
-  args.tiles_x = (c.Wo + t.bw - 1) / t.bw;
-  args.tiles_y = (c.Ho + t.bh - 1) / t.bh;
+  // halo-row tiles: 128-pixel runs of the output laid out over the padded width, per image
+  args.tiles_x = halo ? (c.Ho * (c.W + 2) + 127) / 128 : (c.Wo + t.bw - 1) / t.bw;
+  args.tiles_y = halo ? 1 : (c.Ho + t.bh - 1) / t.bh;
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
-  args.fold = 2;
+  args.fold = halo ? 3 : 2;  // K blocks per TMEM accumulation group (a halo stage is one group)
   args.taps = g.taps;
   args.up = g.up;
   args.co_blk = co_blk;
@@ -1348,6 +1451,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   const bool s2 = c.stride == 2;
 #define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, args, s) : launch_p<M, N, false, K>(ta, talo, tw, args, s)
   if (mode == 1) {
+    if (halo) return launch_p<1, 64, false, false, true>(ta, talo, tw, args, s);
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
     if (t.bn == 128) { if (sk) PP_P(1, 128, true); PP_P(1, 128, false); }
   } else {
@@ -1441,7 +1545,8 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   return PP_OK;
 }
 
-int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF : kNPB; }
+int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + 1 : kNPB; }
+int conv_tcp_sk_first() { return kNPF; }
 
 int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
                    const float* ss, void* out, int tile, cudaStream_t s) {
@@ -1478,9 +1583,9 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   if (dtype == PP_F32_TC) {
-    if (tile < 0 || tile >= 2 * kNPF) return PP_EINVAL;
-    const TileP& t = kTilesPF[tile % kNPF];
-    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : 3;
+    if (tile < 0 || tile > 2 * kNPF) return PP_EINVAL;
+    const TileP& t = tile == 2 * kNPF ? kTileHalo : kTilesPF[tile % kNPF];
+    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : 4;
     return PP_OK;
   }
   return PP_EINVAL;
