@@ -97,13 +97,13 @@ def _workload(name):
 # (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
 # reports null until it is captured again.
 CONV_TRAFFIC = {
-    "cfg2-fp32": (382.5e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
-    "cfg3-bf16": (84.5e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
+    "cfg2-fp32": (383.2e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
+    "cfg3-bf16": (84.6e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
 }
 # the same for the neck and head launches of one step (upsamplings + head)
 NECK_HEAD_TRAFFIC = {
-    "cfg2-fp32": (250.3e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
-    "cfg3-bf16": (42.3e6, "da13817354fa21d98d7c3432f9ef65f5b6e594d9fecb10d76d49b664ecdea182"),
+    "cfg2-fp32": (250.4e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
+    "cfg3-bf16": (42.3e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
 }
 
 
