@@ -17,7 +17,7 @@ module restates its front end step by step as this library specifies it:
    channels in block order; a 1x1 convolution with bias produces the per-anchor class, box and
    direction outputs.
 
-Readings where the specification is silent (each also listed in the design notes):
+Readings where the specification is silent:
 * ranges are half-open [min, max) in x, y and z;
 * cell index contract: ix = floor(fl32(fl32(x - xmin) / vx)) with IEEE binary32 round-to-nearest
   subtraction and division on binary32 operands; a point is kept iff it is inside all three

@@ -39,7 +39,7 @@ replaces the urgency in ordering frames and ranking active units onto stream lev
 * EQDF (earliest quasi-deadline first; reading): priority -(deadline - lambda e), lambda =
   ``eqdf_lambda`` (0 gives EDF; 1 orders by latest start time, like the urgency order).
 
-Readings where the paper is silent (also in the design notes): urgency order breaks ties by
+Readings where the paper is silent: urgency order breaks ties by
 (chain id, arrival time, frame id); the FIFO baseline orders by (arrival, chain id, frame id);
 rank r counts the active non-urgent units strictly more urgent than the candidate, n counts
 them plus the candidate, level = 1 + floor(r (NUM_PRI-1) / n); the delay rule compares against

@@ -18,6 +18,7 @@ Every frame draws from ``numpy.random.default_rng(1000 + config * 100 + frame)``
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import List, Sequence, Tuple
 
 import numpy as np
@@ -25,7 +26,8 @@ import numpy as np
 __all__ = [
     "Geometry", "Backbone", "GEOM_SMALL", "GEOM_FULL", "BACKBONE_SMALL", "BACKBONE_FULL",
     "frame_seed", "uniform_cloud", "clustered_cloud", "config_points", "batched_counts",
-    "pillar_weights", "ChainSpec", "serving_chains", "arrival_times", "splitmix64", "noise_factors",
+    "pillar_weights", "ChainSpec", "tight_chains", "serving_chains", "arrival_times", "splitmix64",
+    "noise_factors",
 ]
 
 
@@ -191,14 +193,27 @@ class ChainSpec:
     precision: int  # 0 = FP32, 1 = BF16
 
 
+def tight_chains(n_chains: int, tight: float, seed: int = 1500) -> List[int]:
+    """The chains whose deadlines are halved for a tight-deadline share ``tight`` (the paper's
+    f_tight, Section 6.2): floor(tight * n_chains + 1/2) of them, the first ones of a seeded
+    permutation of the chain ids (so a larger share keeps the chains of a smaller one)."""
+    if not 0.0 <= tight <= 1.0:
+        raise ValueError("tight must be in [0, 1]")
+    k = int(math.floor(tight * n_chains + 0.5))
+    return sorted(int(c) for c in np.random.default_rng(seed).permutation(n_chains)[:k])
+
+
 def serving_chains(n_chains: int = 11, mixed: bool = False,
-                   periods: Sequence[float] = (50.0, 100.0, 200.0)) -> List[ChainSpec]:
-    """Periodic chains: period = periods[i mod 3], deadline = period.
+                   periods: Sequence[float] = (50.0, 100.0, 200.0), tight: float = 0.0,
+                   tight_seed: int = 1500) -> List[ChainSpec]:
+    """Periodic chains: period = periods[i mod 3], deadline = period, halved for the chains
+    ``tight_chains(n_chains, tight, tight_seed)`` picks.
     ``mixed``: odd chains BF16, even chains FP32; otherwise all BF16."""
+    halved = set(tight_chains(n_chains, tight, tight_seed))
     out = []
     for i in range(n_chains):
         p = float(periods[i % len(periods)])
-        out.append(ChainSpec(i, p, p, (i % 2) if mixed else 1))
+        out.append(ChainSpec(i, p, p / 2.0 if i in halved else p, (i % 2) if mixed else 1))
     return out
 
 

@@ -371,3 +371,114 @@ def test_des_cpu_segments_invariants():
     late = [S.SimFrame(0, 0, 0.0, 500.0, [100.0], cpu=[600.0])]
     r = S.simulate(late, S.PolicyConfig(policy=S.POLICY_URGENCY, max_closed=0, th_urgent=-1.0))
     assert r.dropped == {0: 0.0}
+
+
+# ---------------------------------------------------------------- DES branches, hand-computed
+
+def _delay_case(quantum):
+    # A (chain 0) is urgent when released at t=0 (slack 50 us, UL 0.02 > TH 0.015) and holds the
+    # GPU until t=100.  B (chain 1) arrives at t=10 with slack 95 (UL 0.0105): less urgent than
+    # A, so it is delayed, and re-checked every quantum: its slack shrinks as time passes, and it
+    # is released at the first wake-up where its UL exceeds A's 0.02 (slack < 50 us):
+    #   quantum 50: wake at 60, slack 145 - 40 - 60 = 45 -> released at 60 (UL 0.022 > TH: level 0)
+    #   quantum 30: wake at 40 (slack 65, still delayed), then 70 (slack 35) -> released at 70
+    # Either way it waits in the GPU queue until A completes and runs 100..140 (deadline 145).
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, max_closed=0, th_urgent=0.015, num_pri=6)
+    frames = [S.SimFrame(0, 0, 0.0, 150.0, [100.0]), S.SimFrame(1, 1, 10.0, 145.0, [40.0])]
+    return S.simulate(frames, cfg, delay_quantum_us=quantum)
+
+
+@pytest.mark.timeout(60)
+def test_des_delay_and_wake_up_hand_example():
+    for quantum, t_rel in ((50.0, 60.0), (30.0, 70.0)):
+        r = _delay_case(quantum)
+        assert r.releases == [(0.0, [(0, 0)], 0), (t_rel, [(1, 0)], 0)], quantum
+        assert r.done == {0: 100.0, 1: 140.0} and r.missed == {0: False, 1: False}
+
+
+def test_des_gpu_queue_runs_lower_levels_first():
+    # A (level 1) holds the GPU 0..30.  C (chain 2, slack 1945, less urgent than A: rank 1 of 2
+    # -> level 1 + floor(1 * 5 / 2) = 3) is released at t=5 and queues; B (chain 1, slack 50,
+    # UL 0.02 > TH -> reserved level 0) is released at t=10 and queues behind it.  When A
+    # completes, the queue hands the GPU to the lower level first: B runs 30..70, C 70..120.
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, max_closed=0, th_urgent=0.015, num_pri=6)
+    frames = [S.SimFrame(0, 0, 0.0, 1000.0, [30.0]), S.SimFrame(1, 2, 5.0, 2000.0, [50.0]),
+              S.SimFrame(2, 1, 10.0, 100.0, [40.0])]
+    r = S.simulate(frames, cfg)
+    assert r.releases == [(0.0, [(0, 0)], 1), (5.0, [(1, 0)], 3), (10.0, [(2, 0)], 0)]
+    assert r.done == {0: 30.0, 2: 70.0, 1: 120.0}
+    assert not any(r.missed.values())
+
+
+def test_des_two_servers_hand_example():
+    # X (100 us) and Y (60 us) are released at t=0 (X first: less slack) and, with two servers,
+    # both start at once; Z (20 us) arrives at t=10, queues, and starts when Y frees its server
+    # at 60.  Levels: X alone -> 1; Y ranks behind X (1 of 2) -> 3; Z behind both (2 of 3) -> 4.
+    # With one server the same releases run back to back.
+    cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, max_closed=0, th_urgent=-1.0, num_pri=6)
+    frames = [S.SimFrame(0, 0, 0.0, 1000.0, [100.0]), S.SimFrame(1, 1, 0.0, 1000.0, [60.0]),
+              S.SimFrame(2, 2, 10.0, 1000.0, [20.0])]
+    rel = [(0.0, [(0, 0)], 1), (0.0, [(1, 0)], 3), (10.0, [(2, 0)], 4)]
+    two = S.simulate(frames, cfg, servers=2)
+    assert two.releases == rel and two.done == {0: 100.0, 1: 60.0, 2: 80.0}
+    one = S.simulate(frames, cfg, servers=1)
+    assert one.releases == rel and one.done == {0: 100.0, 1: 160.0, 2: 180.0}
+
+
+# ---------------------------------------------------------------- tight-deadline share (f_tight)
+
+def test_tight_share_halves_exactly_the_seeded_chains():
+    """Section 6.2: f_tight halves the deadlines of a share of the chains.  serving_chains halves
+    floor(f_tight n + 1/2) chains' deadlines -- the first ones of a seeded permutation, so a
+    larger share keeps a smaller one's chains -- and leaves every other deadline at its period."""
+    from pp_synth import serving_chains, tight_chains
+    for n in (10, 11, 33):
+        prev = set()
+        for share in (0.0, 0.2, 0.4, 0.7, 1.0):
+            chains = serving_chains(n, mixed=True, tight=share)
+            halved = {c.chain_id for c in chains if c.deadline_ms == c.period_ms / 2}
+            kept = {c.chain_id for c in chains if c.deadline_ms == c.period_ms}
+            assert len(halved) == math.floor(share * n + 0.5) and len(halved) + len(kept) == n
+            assert halved == set(tight_chains(n, share))
+            assert halved == set(int(c) for c in np.random.default_rng(1500).permutation(n)[:len(halved)])
+            assert prev <= halved
+            prev = halved
+    with pytest.raises(ValueError):
+        tight_chains(5, 1.5)
+
+
+def _tight_des(share, policy):
+    from pp_synth import arrival_times, serving_chains
+    chains = serving_chains(33, mixed=True, tight=share)
+    ev = arrival_times(chains, 500.0, rate=20.0, jitter_ms=0.5, seed=1400)
+    by = {c.chain_id: c for c in chains}
+    frames = [S.SimFrame(i, cid, t * 1e3, t * 1e3 + by[cid].deadline_ms * 0.01 * 1e3, [20.0 + n / 1000.0],
+                         precision=by[cid].precision, period=by[cid].period_ms * 1e3)
+              for i, (t, cid, n) in enumerate(ev)]
+    if policy == "urgency":
+        cfg = S.PolicyConfig(policy=S.POLICY_URGENCY, max_batch=1, max_closed=0, th_urgent=-1.0)
+    else:
+        cfg = S.PolicyConfig(policy=S.POLICY_FIFO, max_batch=1, max_closed=0, early_exit=False)
+    return frames, S.simulate(frames, cfg)
+
+
+def test_des_tight_share_sweep():
+    """The f_tight sweep in the DES (33 chains at 20x the paper's rates, f_d = 0.01, one GPU
+    server, ~85 % busy): each frame's deadline is its chain's (halved for the tight chains), the
+    miss ratio rises with the tight share for both the urgency rule and FIFO, and the urgency
+    rule misses no more than FIFO at any share (the paper's tight-deadline sweep)."""
+    from pp_synth import tight_chains
+    miss = {}
+    for share in (0.0, 0.4, 0.8):
+        tight = set(tight_chains(33, share))
+        for pol in ("urgency", "fifo"):
+            frames, r = _tight_des(share, pol)
+            for f in frames:
+                period_us = f.period
+                rel = (f.deadline - f.t_arr) / 0.01
+                assert math.isclose(rel, period_us / 2 if f.chain_id in tight else period_us, rel_tol=1e-9)
+            miss[share, pol] = S.miss_ratio_of(r, frames)
+    for pol in ("urgency", "fifo"):
+        assert miss[0.0, pol] < miss[0.4, pol] < miss[0.8, pol], miss
+    for share in (0.0, 0.4, 0.8):
+        assert miss[share, "urgency"] <= miss[share, "fifo"], miss
