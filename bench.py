@@ -55,6 +55,8 @@ def _args():
                     help="the step also runs the neck (upsample + concat) and the detection head")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="with the default workload, skip the 8-frame BF16 unit run reported under batched_bf16")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
     ap.add_argument("--depth", type=int, default=None,
                     help="steps in flight (1 = each step waits for the last; default per workload)")
@@ -94,8 +96,8 @@ def _workload(name):
 
 
 # DRAM bytes (read + write) of all conv launches of one step, from one-pass ncu captures
-# (profiles/traffic_*.md), valid only for the conv source they were taken on: a changed kernel
-# reports null until it is captured again.
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the sha256 of the conv source they
+# were taken on: a changed kernel reports null until it is captured again.
 CONV_TRAFFIC = {
     "cfg2-fp32": (383.2e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
     "cfg3-bf16": (84.6e6, "66563541ec5512d479f1ac7b165d18ef09f7cffc2ec9cd36b8ec5f3f07b2bac5"),
@@ -367,6 +369,30 @@ def _time_neck_head(pp, torch, g, bb, prec, batch, reps=20):
     return out
 
 
+def _measure_tf32_tflops(torch, n=8192, reps=10):
+    """Dense TF32 tensor-core rate on this GPU: torch.matmul (cuBLAS) of two n x n float32
+    matrices with TF32 allowed, 2 n^3 FLOP, best of `reps` CUDA-event-timed calls."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.rand((n, n), device="cuda")
+        b = torch.rand((n, n), device="cuda")
+        c = torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        del a, b, c
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def _block_ends(bb):
     ends, n = [], 0
     for c in bb.convs:
@@ -560,14 +586,20 @@ def _run_ours(a, rank, world, dist):
         peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # FP32 FMA lanes x 2 flops x clock
         bound, peak_note = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz (derived)" % sm_max
     elif prec == pp.PP_F32:
-        # 3xTF32: every FP32 FLOP costs three TF32 tensor FLOPs; TF32 dense = bf16 x 1.1/2.25
-        peak = bf16 * (1.1 / 2.25) / 3.0
-        bound, peak_note = "tensor", ("FP32-equivalent via 3 TF32 passes: bf16 dense %s x 1.1/2.25 "
-                                      "(nominal TF32/BF16) / 3" % src)
+        # 3xTF32: every FP32 FLOP costs three TF32 tensor FLOPs; the TF32 rate is measured here
+        # (a library GEMM), the nominal TF32/BF16 ratio applied to the measured BF16 peak is
+        # reported beside it
+        tf32 = _measure_tf32_tflops(torch)
+        peak = tf32 / 3.0
+        bound, peak_note = "tensor", ("FP32-equivalent via 3 TF32 passes: cuBLAS TF32 GEMM 8192^3 measured in this "
+                                      "run (%.1f TFLOP/s, best of 10) / 3" % tf32)
+        peak_nominal = bf16 * (1.1 / 2.25) / 3.0
     else:
         peak = bf16
         bound, peak_note = "tensor", "bf16 dense, %s" % src
     achieved = conv_flops / conv_s / 1e12
+    if prec != pp.PP_F32 or a.fp32_cuda_cores:
+        peak_nominal = None
     traffic = _conv_traffic(a.workload) if conv_dtype != pp.PP_F32 else None
     neck_head = None
     if conv_dtype != pp.PP_F32:
@@ -603,6 +635,10 @@ def _run_ours(a, rank, world, dist):
                      "kernel": "conv3x3 (%s), all layers"
                      % {pp.PP_F32: "CUDA-core FP32", pp.PP_F32_TC: "tcgen05 3xTF32", pp.PP_BF16: "tcgen05 BF16"}[conv_dtype],
                      "peak_source": peak_note,
+                     "frac_of_nominal": None if peak_nominal is None else achieved / peak_nominal,
+                     "peak_nominal": peak_nominal,
+                     "peak_nominal_source": None if peak_nominal is None else
+                     "bf16 dense %s x 1.1/2.25 (nominal TF32/BF16) / 3" % src,
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames,
                      "layers_us": [round(t * 1e6, 2) for t, _ in layers],
                      "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
@@ -645,7 +681,7 @@ def replica_throughput(frames_per_rank, world, window_s):
 # ------------------------------------------------------------------ serving (chains with deadlines)
 
 def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0, noise=0.0,
-           synth=None):
+           synth=None, tight=0.0):
     """Replays periodic chains in real time against one context and returns its statistics.
 
     mode "urgency": the paper's release rules (urgency order, early exit, stream binding,
@@ -656,7 +692,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     comparison order (no early exit, reservation or delaying).
     Periods 50/100/200 ms round robin, deadline = period, jitter +-5 ms, 30k-150k points per
     frame (config-1 geometry); arrivals scaled by ``rate``, deadlines by ``dfac`` (the paper's
-    f_a and f_d); ``noise``: every frame's estimate, as the policy sees it, scaled by a factor
+    f_a and f_d), and a seeded share ``tight`` of the chains with halved deadlines (the paper's
+    f_tight; pp_synth.tight_chains); ``noise``: every frame's estimate, as the policy sees it, scaled by a factor
     drawn from 1 + U[-noise, noise) (the paper's estimation-error study).  ``synth`` = (util,
     kernel_us, total_us): every odd chain becomes a synthetic-load chain whose frames run
     round(total_us / kernel_us) kernels of about kernel_us on round(util x SMs) SMs (the paper's
@@ -665,7 +702,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     from pp_synth import BACKBONE_SMALL, GEOM_SMALL, arrival_times, pillar_weights, serving_chains
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     w = pillar_weights(bb, 7)
-    chains = serving_chains(n_chains, mixed=mixed)
+    chains = serving_chains(n_chains, mixed=mixed, tight=tight)
     others = {"edf": pp.PP_POLICY_EDF, "sjf": pp.PP_POLICY_SJF, "hrrn": pp.PP_POLICY_HRRN,
               "lcuf": pp.PP_POLICY_LCUF, "saedf": pp.PP_POLICY_SAEDF, "eqdf": pp.PP_POLICY_EQDF}
     if mode == "urgency":
@@ -714,6 +751,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             per[c.chain_id] = (m, n)
     miss = sum(m / n for m, n in per.values()) / max(1, len(per))
     return {"mode": mode, "chains": n_chains, "rate": rate, "deadline_factor": dfac, "mixed": mixed,
+            "tight": tight, "tight_chains": [c.chain_id for c in chains if c.deadline_ms < c.period_ms],
+            "seconds": duration_s,
             "est_noise": noise, "synthetic": None if synth is None else
             {"util": synth[0], "kernel_us": synth[1], "frame_us": synth[2], "chains": "odd"},
             "frames": len(ev),
@@ -724,6 +763,51 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
             "th_urgent_per_ms": st["th_urgent"] * 1e3 if st["th_urgent"] > 0 else None,
             "sched_us_per_decision": st["sched_us_per_decision"],
             "submit_late_us": {"mean": rep["submit_late_us_mean"], "max": rep["submit_late_us_max"]}}
+
+
+def parse_sweep_item(item):
+    """One --serve-sweep point: ``chains:rate:seconds`` then, in this order and each optional,
+    ``mixed`` (any other word: all BF16), the deadline factor f_d, the estimate noise and
+    ``util/kernel_us/frame_us`` (odd chains synthetic); ``key=value`` items (dfac, noise, tight,
+    synth) may stand anywhere after the first three and override the positional ones.  tight is
+    the share of chains with halved deadlines (f_tight; default 0)."""
+    parts = item.split(":")
+    if len(parts) < 3:
+        raise ValueError("sweep point %r: need chains:rate:seconds" % item)
+    pt = {"chains": int(parts[0]), "rate": float(parts[1]), "seconds": float(parts[2]), "mixed": False,
+          "dfac": 1.0, "noise": 0.0, "synth": None, "tight": 0.0}
+    pos = []
+    for tok in parts[3:]:
+        if "=" in tok:
+            k, v = tok.split("=", 1)
+            if k not in ("dfac", "noise", "tight", "synth"):
+                raise ValueError("sweep point %r: unknown key %s" % (item, k))
+            pt[k] = tuple(float(x) for x in v.split("/")) if k == "synth" else float(v)
+        else:
+            pos.append(tok)
+    if pos:
+        pt["mixed"] = pos[0] == "mixed"
+    if len(pos) > 1 and "dfac=" not in item:
+        pt["dfac"] = float(pos[1])
+    if len(pos) > 2 and "noise=" not in item:
+        pt["noise"] = float(pos[2])
+    if len(pos) > 3 and "synth=" not in item:
+        pt["synth"] = tuple(float(x) for x in pos[3].split("/"))
+    if not 0.0 <= pt["tight"] <= 1.0:
+        raise ValueError("sweep point %r: tight must be in [0, 1]" % item)
+    return pt
+
+
+# Serving points of the default run: (key, chains, rate x, seconds, mixed, f_d, f_tight).  The
+# 11-chain point is the base load at the paper's rates; the 33-chain points are past the plain
+# per-frame path's saturation (~22k frames/s on this GPU), at the paper's default share of
+# tight-deadline chains (40 %): loose deadlines at 96x (~37k frames/s offered) and deadlines of
+# 0.5 % of the period at 64x (~25k frames/s).
+SERVING_POINTS = [
+    ("config4_11_chains_1x", 11, 1.0, 4.0, False, 1.0, 0.0),
+    ("overload_33_chains_96x_fd1_tight0.4", 33, 96.0, 8.0, True, 1.0, 0.4),
+    ("tight_33_chains_64x_fd0.005_tight0.4", 33, 64.0, 8.0, True, 0.005, 0.4),
+]
 
 
 def _serving_clouds(torch):
@@ -789,15 +873,11 @@ def main():
         clouds = _serving_clouds(torch)
         out = []
         for item in a.serve_sweep.split(","):
-            parts = item.split(":")
-            n, rate, secs = int(parts[0]), float(parts[1]), float(parts[2])
-            mixed = len(parts) > 3 and parts[3] == "mixed"
-            dfac = float(parts[4]) if len(parts) > 4 else 1.0
-            noise = float(parts[5]) if len(parts) > 5 else 0.0
-            synth = tuple(float(x) for x in parts[6].split("/")) if len(parts) > 6 else None
+            pt = parse_sweep_item(item)
             for mode in a.serve_modes.split(","):
-                out.append(_serve(pp, torch, mode, n, rate, secs, mixed, clouds=clouds, dfac=dfac, noise=noise,
-                                  synth=synth))
+                out.append(_serve(pp, torch, mode, pt["chains"], pt["rate"], pt["seconds"], pt["mixed"],
+                                  clouds=clouds, dfac=pt["dfac"], noise=pt["noise"], synth=pt["synth"],
+                                  tight=pt["tight"]))
                 print(json.dumps(out[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"metric": "deadline-miss ratio and p99 chain latency, urgency-served batched "
                           "vs plain per-frame launches", "serving": out}))
@@ -808,16 +888,24 @@ def main():
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     res = _run_ours(a, rank, world, dist)
+    if a.workload == "cfg2-fp32" and not a.no_batched and not a.head and not a.fp32_cuda_cores:
+        # the batched BF16 workload (8 frames of 30k-150k points per unit, BF16 backbone on the
+        # tensor cores) as its own timed run, reported beside the full-size FP32 frame
+        import copy
+        b = copy.copy(a)
+        b.workload, b.tune_table = "cfg3-bf16", None
+        b.chains, b.depth = SERVING_SHAPE["cfg3-bf16"]
+        sub = _run_ours(b, rank, world, dist)
+        res["batched_bf16"] = {k: sub[k] for k in (
+            "metric", "value", "unit", "ms_per_step", "dtype", "config", "e2e", "roofline", "front_end_roofline",
+            "neck_head", "stage_ms_per_step", "runtime", "gpu_launches", "clocks", "num_pillars", "wall_s")}
     if rank == 0 and not a.no_serving:
         import torch
         import paper_2509_12207_gb300 as pp
         clouds = _serving_clouds(torch)
-        res["serving"] = {
-            "config4_11_chains_1x": [_serve(pp, torch, m, 11, 1.0, 4.0, False, clouds=clouds)
-                                     for m in ("urgency", "plain")],
-            "config5_33_chains_40x": [_serve(pp, torch, m, 33, 40.0, 4.0, True, clouds=clouds)
-                                      for m in ("urgency", "plain")],
-        }
+        res["serving"] = {key: [_serve(pp, torch, m, n, rate, secs, mixed, clouds=clouds, dfac=dfac, tight=tight)
+                                for m in ("urgency", "plain")]
+                          for key, n, rate, secs, mixed, dfac, tight in SERVING_POINTS}
     if rank == 0:
         if not a.no_cpu_baseline:
             res["cpu_baseline"] = _cpu_baseline(a.workload, a.head)

@@ -52,3 +52,26 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["metric"] == "pillar frames/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_sweep_points_parse_positional_and_keyed():
+    p = bench.parse_sweep_item("33:96:8:mixed:1:tight=0.4")
+    assert (p["chains"], p["rate"], p["seconds"], p["mixed"], p["dfac"], p["tight"]) == (33, 96.0, 8.0, True, 1.0, 0.4)
+    p = bench.parse_sweep_item("33:64:3:mixed:0.005:0.1")
+    assert (p["dfac"], p["noise"], p["tight"], p["synth"]) == (0.005, 0.1, 0.0, None)
+    p = bench.parse_sweep_item("33:5:3:mixed:0.1:0:0.5/100/1000")
+    assert p["synth"] == (0.5, 100.0, 1000.0)
+    p = bench.parse_sweep_item("11:1:4:bf16:tight=1:dfac=0.5")
+    assert not p["mixed"] and p["dfac"] == 0.5 and p["tight"] == 1.0
+    for bad in ("33:96", "33:96:8:mixed:tight=1.5", "33:96:8:tightness=0.4"):
+        with pytest.raises(ValueError):
+            bench.parse_sweep_item(bad)
+
+
+def test_default_serving_points_are_past_plain_saturation_with_tight_share():
+    """The default run's overload points use the paper's default share of tight-deadline chains
+    (40 %) and replay at least 8 s each."""
+    pts = {k: v for k, *v in bench.SERVING_POINTS}
+    assert pts["config4_11_chains_1x"] == [11, 1.0, 4.0, False, 1.0, 0.0]
+    over = [v for k, v in pts.items() if k != "config4_11_chains_1x"]
+    assert over and all(n == 33 and secs >= 8.0 and tight == 0.4 for n, rate, secs, mixed, dfac, tight in over)
