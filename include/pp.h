@@ -300,6 +300,11 @@ int pp_bn_fold(const float* bn, int32_t c, float eps, float* out);
  * MMA wait timed out, bit 4: an epilogue wait timed out in the tensor-core conv; the kernel
  * that hit it skipped its stores).  Synchronous (device-wide copy).  clear != 0 resets it. */
 int pp_device_error(uint32_t* code, int32_t clear);
+/* Sets `bits` in that word, as a bounded wait that ran out would (no counterpart in the paper:
+ * a hook for testing the error path without a device fault).  Every tensor-core conv launched
+ * while it is set exits at once without writing its outputs, and a release unit that finds it
+ * set reports its frames as PP_FRAME_ERROR.  Synchronous; pp_device_error(.., 1) clears it. */
+int pp_device_error_set(uint32_t bits);
 
 /* ======================================================================================== */
 /* Serving runtime.                                                                          */
@@ -394,11 +399,16 @@ typedef struct {
   uint64_t noise_seed;
   int32_t keep_blocks;          /* result slots hold every backbone block's output (1) or only */
                                 /* the last block's, the final output (0, default)            */
+  int32_t decision_log;         /* record the first decision_log release decisions with their */
+                                /* inputs (pp_decision_log); 0 = off (default), at most 2^20   */
 } pp_config;
 
 /* Fills *cfg with defaults for the given geometry/backbone-free fields (policy urgency,
  * max_batch 8, delta_eval 500 us, max_closed 2, delay quantum 1000 us, th_urgent 0 (calibrate
- * over 64 frames), util_exempt 0.1, early_exit 1, graphs on, both precisions, budget 20 GiB). */
+ * over 64 frames), util_exempt 0.1, early_exit 1, graphs on, both precisions, budget 20 GiB).
+ * The paper's values: Delta_eval 0.5 ms and overlapped batches (Section 4.4.5), a 1 ms sleep
+ * loop and the 0.1 utilisation exemption (Section 4.4.4), TH_urgent at the 95th percentile of
+ * the highest urgency sampled (Section 4.4.3). */
 void pp_config_defaults(pp_config* cfg);
 
 typedef struct pp_ctx pp_ctx;
@@ -407,12 +417,22 @@ typedef struct pp_ctx pp_ctx;
  * holding buffers for max_batch frames), captures their graphs, carves one result slot per
  * admissible frame out of what is left of the budget, and starts the dispatcher.  A unit is
  * reusable as soon as it completes: it copies its frames' block outputs into their result
- * slots.  PP_ENOMEM if one unit per enabled precision and one result slot do not fit. */
+ * slots.  PP_ENOMEM if one unit per enabled precision and one result slot do not fit.
+ * Paper: the offline profiling stage and its lookup table of execution times (Section 4.1,
+ * Table 1) -- here every unit size is timed once at creation to seed the per-(precision,
+ * frames-per-unit) estimates, each later the mean of its last 8 measured launches (the moving
+ * average of Section 4.2).  The HBM admission budget has no counterpart in the paper.
+ * Ownership: the context owns every device buffer it allocates until pp_destroy; weights are
+ * copied.  Errors: PP_EINVAL for a bad config, PP_ENOMEM, PP_EDEVICE. */
 int pp_create(const pp_config* cfg, pp_ctx** out);
 
 /* Declares a chain.  period/deadline in milliseconds (informational/default deadline);
  * precision PP_F32 or PP_BF16 (needs that precision enabled).  Up to PP_MAX_CHAINS ids,
- * 0 <= chain_id < PP_MAX_CHAINS. */
+ * 0 <= chain_id < PP_MAX_CHAINS.  Paper: the task chain with its application-defined deadline
+ * and its period (Section 4.1; Table 2 lists chains by period, deadline and estimates).  The
+ * chain gets its own pool of streams, one per device stream priority (the per-task stream pool
+ * of Section 4.4.3).  Errors: PP_EINVAL (bad id, period, deadline or precision), PP_ESTATE
+ * (already registered), PP_EDEVICE (stream creation). */
 int pp_register_chain(pp_ctx* ctx, int32_t chain_id, double period_ms, double rel_deadline_ms,
                       int32_t precision);
 
@@ -441,7 +461,11 @@ enum { PP_POINTS_HOST = 0, PP_POINTS_DEVICE = 1, PP_POINTS_PINNED = 2 };
 /* Submits one frame of `n_points` float4 points (is_device_ptr: PP_POINTS_*; device and pinned
  * points 16-byte aligned).
  * t_arrival_us / abs_deadline_us on the pp_now_us clock (abs_deadline_us <= 0: arrival +
- * the chain's deadline).  PP_EAGAIN when admitting the frame would exceed the HBM budget. */
+ * the chain's deadline).  PP_EAGAIN when admitting the frame would exceed the HBM budget.
+ * Paper: a frame's arrival starts an instance of its chain, with t_arr and D as in Eq. 2
+ * (Section 4.2); its urgency is evaluated from then on at every release decision.  The frame
+ * (its staged points and its result slot) is the unit of admission here, which the paper does
+ * not have.  Layout: float4 (x, y, z, intensity) per point. */
 int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_points,
                     int32_t is_device_ptr, double t_arrival_us, double abs_deadline_us,
                     uint64_t* frame_id_out);
@@ -452,7 +476,11 @@ int pp_submit_frame(pp_ctx* ctx, int32_t chain_id, const float* xyzr, int64_t n_
  * meaning as in pp_submit_frame; abs_deadline_us: n deadlines, or NULL for each chain's own.
  * Frames are admitted in order until one cannot be: *n_admitted (may be NULL) receives how
  * many were, frame_ids_out (may be NULL) their ids, and the call returns PP_EAGAIN (budget
- * full) or PP_ENOMEM for the first frame left out.  Argument errors admit no frame. */
+ * full) or PP_ENOMEM for the first frame left out.  Argument errors admit no frame.
+ * Paper: arrivals as in pp_submit_frame (Section 4.2); admitting them under one lock makes
+ * them one ready set at the next decision, which may release them as one unit -- the batching
+ * of several chains' frames into one launch has no counterpart in the paper (its kernels are
+ * per task). */
 #define PP_MAX_SUBMIT 64
 int pp_submit_frames(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
                      const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
@@ -465,13 +493,15 @@ int pp_submit_frames(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const flo
  * batching several frames by one copy-engine copy per frame after its kernels, in its stream),
  * so a caller that wants its result on the host needs no copy of its own (pp_result.out_host;
  * complete when the frame is polled).  Other host memory: PP_EINVAL,
- * nothing admitted.  Ignored for synthetic-load chains. */
+ * nothing admitted.  Ignored for synthetic-load chains.  Paper: as pp_submit_frames; the
+ * output buffer (results delivered to host memory by the unit) has no counterpart in the
+ * paper. */
 int pp_submit_frames_ex(pp_ctx* ctx, int32_t n, const int32_t* chain_ids, const float* const* xyzr,
                         const int64_t* n_points, int32_t is_device_ptr, double t_arrival_us,
                         const double* abs_deadline_us, void* const* host_out, uint64_t* frame_ids_out,
                         int32_t* n_admitted);
 /* Bytes of one frame's final output (padded NHWC, out_dev's map) at `precision` (0 if that
- * precision is not enabled). */
+ * precision is not enabled).  No counterpart in the paper (a size query for host buffers). */
 size_t pp_result_bytes(pp_ctx* ctx, int32_t precision);
 
 typedef struct {
@@ -502,11 +532,17 @@ typedef struct {
  * (0 = do not wait).  *n_out = number written (0 on timeout, return PP_OK).  Output buffers
  * (the frame's result slot) stay valid until pp_result_release(frame_id), which returns the
  * slot to the budget.  A frame dropped by early exit carries no outputs (out_dev NULL) and
- * gives its slot back at once; releasing it only forgets the record. */
+ * gives its slot back at once; releasing it only forgets the record.  A frame whose unit
+ * failed on the device comes back with status PP_FRAME_ERROR (the call still returns PP_OK;
+ * pp_stats counts such units).  Paper: completion is where an active kernel's record leaves
+ * the Active Kernel Buffer (Section 4.4.2) and a batch's synchronisation point is passed
+ * (Section 4.4.5); latency and misses follow the metrics of Section 6.2. */
 int pp_poll(pp_ctx* ctx, pp_result* out, int32_t max, int32_t* n_out, int64_t timeout_us);
+/* Returns a polled frame's result slot to the HBM budget (no counterpart in the paper: its
+ * outputs are the application's).  PP_EINVAL for an unknown id, PP_ESTATE if not completed. */
 int pp_result_release(pp_ctx* ctx, uint64_t frame_id);
 /* pp_result_release for n frames under one lock; every id is tried, and the first error met
- * (unknown or not completed) is returned. */
+ * (unknown or not completed) is returned.  No counterpart in the paper, as pp_result_release. */
 int pp_result_release_many(pp_ctx* ctx, int32_t n, const uint64_t* frame_ids);
 
 typedef struct {
@@ -523,22 +559,34 @@ typedef struct {
   double th_urgent;              /* threshold in use (1/us)                                  */
   uint64_t chain_frames[PP_MAX_CHAINS], chain_missed[PP_MAX_CHAINS];
   double chain_p99_us[PP_MAX_CHAINS];
+  uint64_t device_errors;        /* units whose launch failed, whose completion event reported */
+                                 /* an error, or whose kernels found a device error word set;  */
+                                 /* their frames completed with PP_FRAME_ERROR                 */
+  uint32_t device_error_code;    /* the last nonzero device error word a unit reported (bits   */
+                                 /* of pp_device_error; bit 31: voxeliser point count)         */
+  uint64_t decisions;            /* calls of the release rule made by the dispatcher          */
 } pp_stats;
 
+/* Counters and latency percentiles so far.  overall_miss_ratio is Eq. 3 (Section 6.2): the mean
+ * over chains of each chain's missed / total instances (a dropped or failed frame is a miss);
+ * collisions as counted for Section 4.4.3.  `out` is a caller struct of sizeof(pp_stats)
+ * (pp_struct_size("pp_stats") gives this build's size). */
 int pp_get_stats(pp_ctx* ctx, pp_stats* out);
 /* Stops the dispatcher, waits (bounded, 10 s) for in-flight units, frees everything.
- * PP_ETIMEDOUT if the device did not finish in time (resources are then leaked, not freed). */
+ * PP_ETIMEDOUT if the device did not finish in time (resources are then leaked, not freed).
+ * No counterpart in the paper (its chains run for the life of the process). */
 int pp_destroy(pp_ctx* ctx);
-/* Host monotonic clock in microseconds. */
+/* Host monotonic clock in microseconds: the clock of t_arr, D and t in Eq. 2 (the paper reads
+ * clock_gettime, Section 4.2). */
 double pp_now_us(void);
 /* sizeof of a public struct, by its type name ("pp_config", "pp_result", "pp_stats",
  * "pp_geometry", "pp_arrival", "pp_replay_stats", "pp_policy_frame", "pp_policy_active",
- * "pp_policy_config", "pp_policy_decision"); 0 for any other name.  Lets a binding check its
- * struct mirrors against this build. */
+ * "pp_policy_config", "pp_policy_decision", "pp_decision_record"); 0 for any other name.  Lets a binding check its
+ * struct mirrors against this build.  No counterpart in the paper (ABI versioning). */
 size_t pp_struct_size(const char* type_name);
 /* The estimate-noise factor of frame `frame_id`: 1 + eps (2u - 1) with u = the frame_id-th
  * output of a SplitMix64 generator seeded with `seed` (Steele, Lea and Flood, OOPSLA 2014),
- * top 53 bits scaled to [0, 1). */
+ * top 53 bits scaled to [0, 1).  Paper: the urgency-estimation error study of Section 6.6. */
 double pp_noise_factor(uint64_t seed, uint64_t frame_id, double eps);
 
 /* Real-time trace replay (a load generator for serving measurements; the paper has no
@@ -566,21 +614,29 @@ int pp_replay(pp_ctx* ctx, const pp_arrival* arrivals, int64_t n, const float* c
 
 /* ---------------------------------------------------------------------------------------- */
 /* One release unit without the runtime: buffers for `max_batch` frames of one precision,    */
-/* the whole front end as plain launches or one CUDA graph per batch size.                   */
+/* the whole front end as plain launches or one CUDA graph per batch size.  Paper: the GPU    */
+/* segment of a 3D-perception chain (PointPillars, Section 6.1, Table 4), run as the work of   */
+/* one release; the pipeline object itself has no counterpart in the paper.                  */
 typedef struct pp_pipeline pp_pipeline;
+/* Creates one unit for `precision` (PP_F32 / PP_BF16) from cfg's geometry, backbone, weights
+ * and max_batch, tunes its conv tiles (cfg->autotune) and captures its graphs (cfg->use_graphs).
+ * Section 6.1, Table 4 (the PointPillars segment).  Errors: PP_EINVAL, PP_ENOMEM, PP_EDEVICE. */
 int pp_pipeline_create(const pp_config* cfg, int32_t precision, pp_pipeline** out);
 /* frames: host array of n pointers to each frame's points (host or device memory, copied into
  * the unit's slots on `stream`); counts: host array of n point counts.  Enqueues everything on
  * `stream` and returns without waiting for it; a call first waits for the previous run on the
  * same pipeline to finish (the unit's per-launch table, in page-locked host memory, is read by
- * that run's first kernel). */
+ * that run's first kernel).  Section 6.1, Table 4 (one release of the chain's GPU segment). */
 int pp_pipeline_run(pp_pipeline* p, int32_t n, const float* const* frames,
                     const int32_t* counts, int32_t use_graph, void* stream);
 /* Device pointer to block `block`'s output for frame slot i (padded NHWC) and its shape; pass
  * block = -1 for the number of pillars (int32 device pointer, dims unset), -2 for the head map
- * and -3 for the neck map (with a head configured; for the split FP32 form the value plane). */
+ * and -3 for the neck map (with a head configured; for the split FP32 form the value plane).
+ * Pointers belong to the pipeline (valid until the next run or pp_pipeline_destroy).  No
+ * counterpart in the paper (output access). */
 int pp_pipeline_output(pp_pipeline* p, int32_t i, int32_t block, const void** dev,
                        int32_t* c, int32_t* h, int32_t* w);
+/* Device bytes the pipeline holds; frees it.  No counterpart in the paper. */
 size_t pp_pipeline_bytes(pp_pipeline* p);
 int pp_pipeline_destroy(pp_pipeline* p);
 
@@ -609,18 +665,53 @@ typedef struct {
   int32_t kind, level, n_frames, n_drops;
   uint64_t frames[8];            /* released frame ids (kind RELEASE), most urgent first     */
 } pp_policy_decision;
-/* drops: caller array of drops_cap entries receiving the ids of frames to drop (early exit);
- * n_drops counts them all even if more than drops_cap. */
+/* One decision of the release rule at time t_us, as the dispatcher takes it: drop frames whose
+ * slack is negative (early chain exit, Section 4.3; urgency policy only); WAIT while
+ * closed_pending >= max_closed (batched launching with overlap, Section 4.4.5); order the rest
+ * by least slack, i.e. highest UL of Eq. 2 (Section 4.2; the comparison policies of Section 6.4
+ * by their own keys); DELAY while another chain's active unit is above TH_urgent and more
+ * urgent than the head (Section 4.4.4); otherwise RELEASE the head and up to max_batch - 1
+ * further frames of its precision at stream level 0 if UL > TH_urgent, else its normalised
+ * rank among the active non-urgent units (Section 4.4.3).  Pure function of its arguments
+ * (host arrays; nothing retained).
+ * drops: caller array of drops_cap entries receiving the ids of frames to drop (early exit);
+ * n_drops counts them all even if more than drops_cap.  PP_EINVAL for a bad argument. */
 int pp_policy_decide(const pp_policy_config* cfg, double t_us, const pp_policy_frame* ready,
                      int32_t n_ready, const pp_policy_active* active, int32_t n_active,
                      int32_t closed_pending, pp_policy_decision* out, uint64_t* drops,
                      int32_t drops_cap);
-/* A frame's priority under cfg->policy at time t (higher = released first): URGENCY: UL = 1 /
+/* A frame's priority under cfg->policy at time t (higher = released first; Eq. 2 and the
+ * comparison policies of Section 6.4): URGENCY: UL = 1 /
  * slack (-inf for slack <= 0); EDF: -deadline; SJF: -(est_gpu + est_cpu); HRRN: (t - t_arr +
  * e) / e with e = est_gpu + est_cpu (+inf when e <= 0); LCUF: -(e / period) (-inf when the
  * period is not positive); SAEDF: -deadline, less 1e15 us when slack < 0; EQDF: -(deadline -
  * eqdf_lambda * e); FIFO: -t_arr.  Stream levels rank active units by this value. */
 double pp_policy_priority(const pp_policy_config* cfg, double t_us, const pp_policy_frame* frame);
+
+/* Decision log (pp_config.decision_log > 0; the paper has no counterpart: it lets every release
+ * decision a serving run took be replayed against an independent restatement of the rule).
+ * Record k holds the inputs the dispatcher passed to pp_policy_decide -- the time, the rule's
+ * configuration as it stood (th_urgent as calibrated), the ready frames as the rule saw them
+ * (estimates with any estimate noise applied), the active units and the closed batches pending
+ * -- and the decision it returned.  Its ready frames are ready[ready_off .. ready_off +
+ * n_ready), its active units active[active_off .. + n_active), its drops drops[drops_off ..
+ * + decision.n_drops).  launched: for a RELEASE, 1 if the unit was launched, 0 if no unit of
+ * that precision was free (the frames stayed ready). */
+typedef struct {
+  double t_us;
+  pp_policy_config cfg;
+  int32_t closed_pending, n_ready, n_active, launched;
+  int64_t ready_off, active_off, drops_off;
+  pp_policy_decision decision;
+} pp_decision_record;
+/* Copies the log.  With recs == NULL only the sizes are written (n_recs, n_ready, n_active,
+ * n_drops; each pointer may be NULL); otherwise every array must hold the sizes a previous
+ * query returned (max_* entries; PP_EINVAL if one is too small) and is filled.  The log stops
+ * growing at pp_config.decision_log records; reading it does not clear it. */
+int pp_decision_log(pp_ctx* ctx, pp_decision_record* recs, int32_t max_recs, pp_policy_frame* ready,
+                    int64_t max_ready, pp_policy_active* active, int64_t max_active, uint64_t* drops,
+                    int64_t max_drops, int32_t* n_recs, int64_t* n_ready, int64_t* n_active,
+                    int64_t* n_drops);
 
 #ifdef __cplusplus
 }

@@ -79,7 +79,7 @@ class Config(ctypes.Structure):
         ("head_w", ctypes.c_void_p), ("head_b", ctypes.c_void_p),
         ("eqdf_lambda", ctypes.c_double),
         ("est_noise", ctypes.c_double), ("noise_seed", ctypes.c_uint64),
-        ("keep_blocks", ctypes.c_int32),
+        ("keep_blocks", ctypes.c_int32), ("decision_log", ctypes.c_int32),
     ]
 
 
@@ -111,6 +111,8 @@ class Stats(ctypes.Structure):
         ("sched_us_per_decision", ctypes.c_double), ("th_urgent", ctypes.c_double),
         ("chain_frames", ctypes.c_uint64 * MAX_CHAINS), ("chain_missed", ctypes.c_uint64 * MAX_CHAINS),
         ("chain_p99_us", ctypes.c_double * MAX_CHAINS),
+        ("device_errors", ctypes.c_uint64), ("device_error_code", ctypes.c_uint32),
+        ("decisions", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -156,6 +158,13 @@ class PolicyDecision(ctypes.Structure):
                 ("n_drops", ctypes.c_int32), ("frames", ctypes.c_uint64 * 8)]
 
 
+class DecisionRecord(ctypes.Structure):
+    _fields_ = [("t_us", ctypes.c_double), ("cfg", PolicyConfig), ("closed_pending", ctypes.c_int32),
+                ("n_ready", ctypes.c_int32), ("n_active", ctypes.c_int32), ("launched", ctypes.c_int32),
+                ("ready_off", ctypes.c_int64), ("active_off", ctypes.c_int64), ("drops_off", ctypes.c_int64),
+                ("decision", PolicyDecision)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 _P = ctypes.c_void_p
@@ -199,6 +208,12 @@ _SIGS = {
     "pp_conv_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "pp_conv_tune_clear": (None, []),
     "pp_device_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), _I]),
+    "pp_device_error_set": (ctypes.c_int, [ctypes.c_uint32]),
+    "pp_decision_log": (ctypes.c_int, [_P, ctypes.POINTER(DecisionRecord), _I, ctypes.POINTER(PolicyFrame),
+                                       ctypes.c_int64, ctypes.POINTER(PolicyActive), ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "pp_config_defaults": (None, [ctypes.POINTER(Config)]),
     "pp_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
     "pp_register_chain": (ctypes.c_int, [_P, _I, ctypes.c_double, ctypes.c_double, _I]),
@@ -600,6 +615,11 @@ def device_error(clear: bool = True) -> int:
     return int(v.value)
 
 
+def device_error_set(bits: int) -> None:
+    """pp_device_error_set: sets bits of the sticky device error word (a test hook)."""
+    _check(lib().pp_device_error_set(int(bits)))
+
+
 # ------------------------------------------------------------------ runtime, pipeline, policy
 
 def make_config(geom, backbone, weights, head=None, **knobs):
@@ -748,6 +768,35 @@ class Context:
         d = {k: getattr(st, k) for k, _ in st._fields_ if k != "chain_rejected"}
         d["chain_rejected"] = list(st.chain_rejected)
         return d
+
+    def decision_log(self):
+        """pp_decision_log: every logged release decision as a dict with the time ``t_us``, the
+        rule's configuration ``cfg`` (dict of PolicyConfig fields), ``closed_pending``,
+        ``ready`` (list of dicts of PolicyFrame fields), ``active`` (list of (chain_id, ul)),
+        ``launched`` and the decision (``kind``, ``frames``, ``level``, ``drops``)."""
+        nr, nf, na, nd = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        L = lib()
+        _check(L.pp_decision_log(self.h, None, 0, None, 0, None, 0, None, 0, ctypes.byref(nr), ctypes.byref(nf),
+                                 ctypes.byref(na), ctypes.byref(nd)))
+        recs = (DecisionRecord * max(1, nr.value))()
+        rf = (PolicyFrame * max(1, nf.value))()
+        ac = (PolicyActive * max(1, na.value))()
+        dr = (ctypes.c_uint64 * max(1, nd.value))()
+        _check(L.pp_decision_log(self.h, recs, len(recs), rf, len(rf), ac, len(ac), dr, len(dr), ctypes.byref(nr),
+                                 ctypes.byref(nf), ctypes.byref(na), ctypes.byref(nd)))
+        out = []
+        for k in range(nr.value):
+            r = recs[k]
+            d = r.decision
+            out.append({
+                "t_us": r.t_us, "cfg": {n: getattr(r.cfg, n) for n, _ in PolicyConfig._fields_},
+                "closed_pending": r.closed_pending, "launched": r.launched,
+                "ready": [{n: getattr(rf[r.ready_off + i], n) for n, _ in PolicyFrame._fields_}
+                          for i in range(r.n_ready)],
+                "active": [(ac[r.active_off + i].chain_id, ac[r.active_off + i].ul) for i in range(r.n_active)],
+                "kind": d.kind, "frames": [int(d.frames[i]) for i in range(d.n_frames)], "level": d.level,
+                "drops": [int(dr[r.drops_off + i]) for i in range(d.n_drops)]})
+        return out
 
     def stats(self):
         s = Stats()

@@ -46,7 +46,10 @@ def _compile(src: str, nvcc: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if not _stale(obj, src):
         return obj
-    flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # host code: no contraction of a*b+c into one fused operation, so that the release rule's
+    # floating-point keys come out the same on x86 and Arm (gcc contracts by default on Arm)
+    flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE,
+             "-I", CSRC]
     if src.endswith(".cu"):
         cmd = [nvcc] + ARCH + flags + ["-lineinfo", "-c", src, "-o", obj]
     else:

@@ -58,7 +58,36 @@ int check_geometry(const pp_geometry* g, Geom* out) {
   return PP_OK;
 }
 
-int tc_error_read(unsigned* code, bool clear);
+int device_sms() {
+  constexpr int kDev = 64;
+  static std::atomic<int> cache[kDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  int n = dev < kDev ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 152;
+  }
+  if (dev < kDev) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+int smem_attr_once(const void* func, int bytes, std::atomic<uint64_t>* done, const char* what) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+  if (bit && (done->load(std::memory_order_acquire) & bit)) return PP_OK;
+  // setting it twice (two threads racing here) is harmless
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  if (bit) done->fetch_or(bit, std::memory_order_acq_rel);
+  return PP_OK;
+}
 
 }  // namespace pp
 
@@ -406,6 +435,8 @@ int pp_bn_fold(const float* bn, int32_t c, float eps, float* out) {
   }
   return PP_OK;
 }
+
+int pp_device_error_set(uint32_t bits) { return tc_error_set(bits); }
 
 int pp_device_error(uint32_t* code, int32_t clear) {
   if (!code) return fail(PP_EINVAL, "device_error: NULL");

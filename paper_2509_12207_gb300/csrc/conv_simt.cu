@@ -187,14 +187,7 @@ struct TileF32 {
 constexpr TileF32 kTiles[] = {{128, 64}, {64, 64}, {128, 128}, {64, 128}};
 
 int sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 152;
-  }
-  return n;
+  return device_sms();
 }
 
 }  // namespace

@@ -19,6 +19,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 namespace pp {
@@ -1130,13 +1131,10 @@ template <int BN, int STAGES, bool S2>
 int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, dim3 grid,
               cudaStream_t s) {
   constexpr size_t bytes = smem_bytes<BN, STAGES>();
-  static bool attr_set = false;  // per instantiation, set once (same device for the process)
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc<BN, STAGES, S2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_status(e, "conv tc smem attribute");
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};  // per instantiation: devices configured
+  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tc<BN, STAGES, S2>), (int)bytes, &attr_set,
+                              "conv tc smem attribute"))
+    return st;
   return cuda_status(launch_pdl(conv3x3_tc<BN, STAGES, S2>, grid, dim3(128), bytes, s, a, w, args),
                      "conv tc launch");
 }
@@ -1286,14 +1284,7 @@ constexpr size_t p_smem_halo() {
 }
 
 int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 152;
-  }
-  return n;
+  return device_sms();
 }
 
 template <int MODE, int BN, bool S2, bool SK, bool HALO = false>
@@ -1304,13 +1295,10 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   // + folded BN (cout <= 1024)
   constexpr size_t bytes = (HALO ? p_smem_halo() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
   static_assert(bytes <= 227 * 1024, "persistent conv shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_status(e, "persistent conv smem attribute");
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_set{0};  // per instantiation: devices configured
+  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>),
+                              (int)bytes, &attr_set, "persistent conv smem attribute"))
+    return st;
   // stream-K: one range per CTA, never an empty one (an empty range would be counted among the
   // CTAs that share a tile but never arrive), so at most one CTA per K block
   const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
@@ -1524,21 +1512,17 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   constexpr size_t bytes = 1024 + 9 * 64 * 128 + 8 * 128 * 128 + (2 * 8 + 5) * 8 + 16 + 2 * 64 * 4;
   const int grid = a.units < sms ? a.units : sms;
   if (c.stride == 2) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(conv3x3_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_rows<true>), (int)bytes, &attr,
+                                "row conv smem attribute"))
+      return st;
     const cudaError_t e = launch_pdl(conv3x3_rows<true>, dim3(grid), dim3(192), bytes, s, ta, tw, a);
     if (e != cudaSuccess) return cuda_status(e, "row conv launch");
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(conv3x3_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (e != cudaSuccess) return cuda_status(e, "row conv smem attribute");
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_rows<false>), (int)bytes, &attr,
+                                "row conv smem attribute"))
+      return st;
     const cudaError_t e = launch_pdl(conv3x3_rows<false>, dim3(grid), dim3(192), bytes, s, ta, tw, a);
     if (e != cudaSuccess) return cuda_status(e, "row conv launch");
   }
@@ -1589,6 +1573,34 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   return PP_EINVAL;
+}
+
+int tc_error_set(unsigned bits) {
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_status(e, "read device error word");
+  v |= bits;
+  e = cudaMemcpyToSymbol(g_tc_error, &v, sizeof(unsigned));
+  return cuda_status(e, "set device error word");
+}
+
+int tc_error_address(const unsigned** out) {
+  // the symbol's device address differs per device: looked up with that device current, once
+  constexpr int kDev = 64;
+  static std::atomic<const unsigned*> addr[kDev];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "current device");
+  const unsigned* p = dev < kDev ? addr[dev].load(std::memory_order_acquire) : nullptr;
+  if (!p) {
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_tc_error);
+    if (e != cudaSuccess) return cuda_status(e, "device error word address");
+    p = static_cast<const unsigned*>(q);
+    if (dev < kDev) addr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return PP_OK;
 }
 
 int tc_error_read(unsigned* code, bool clear) {

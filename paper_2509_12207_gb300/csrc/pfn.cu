@@ -269,14 +269,7 @@ __global__ void canvas_write(Geom g, int batch, int chunks, const float4* __rest
 }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 152;
-  }
-  return n;
+  return device_sms();
 }
 
 }  // namespace

@@ -18,6 +18,9 @@ namespace {
 struct ResultCopy {
   const int* num;   // [B] pillars per frame ...
   int* num_host;    // ... copied to the unit's pinned host array (device view of the mapping)
+  int err_at;       // num_host[err_at] receives the device error words (B, the capacity)
+  const unsigned* tc_err;  // the tensor-core conv's sticky error word
+  const int* vox_err;      // the voxeliser's sticky error word
   int nblocks;
   int hblock;  // the block (the unit's final output) also copied to a frame's host buffer
   const char* src[PP_MAX_BLOCKS];
@@ -32,7 +35,11 @@ struct ResultCopy {
 __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTable* __restrict__ tab) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int f = blockIdx.y;
-  if (blockIdx.x == 0 && threadIdx.x == 0) rc.num_host[f] = rc.num[f];  // over the host link
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rc.num_host[f] = rc.num[f];  // over the host link
+    // every conv of this run has completed: its error word says whether one skipped its stores
+    if (f == 0) rc.num_host[rc.err_at] = (int)((*rc.tc_err & 0x7fffffffu) | (*rc.vox_err ? 0x80000000u : 0u));
+  }
   char* dst = tab->dst[f];
   char* hdst = tab->hdst[f];
   if (!dst) return;
@@ -311,8 +318,9 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
     cudaGetDevice(&dev);
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return st;
   }
-  if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)B_ * sizeof(int)), "pinned pillar counts"))) return st;
-  memset(num_host_, 0, (size_t)B_ * sizeof(int));
+  if ((st = cuda_status(cudaMallocHost(&num_host_, (size_t)(B_ + 1) * sizeof(int)), "pinned pillar counts"))) return st;
+  memset(num_host_, 0, (size_t)(B_ + 1) * sizeof(int));
+  if ((st = tc_error_address(&tc_err_))) return st;
   if ((st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void**>(&num_host_dev_), num_host_, 0),
                         "pinned pillar counts mapping")))
     return st;
@@ -421,6 +429,9 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   ResultCopy rc{};
   rc.num = num_;
   rc.num_host = num_host_dev_;
+  rc.err_at = B_;
+  rc.tc_err = tc_err_;
+  rc.vox_err = vw_.err;
   if (m.head_outputs > 0) {
     // neck: every block's output upsampled into its channel range of the neck map; then the head
     const int H0 = m.out_h(), W0 = m.out_w();

@@ -97,6 +97,11 @@ class Pipeline {
   int* num_pillars_dev() const { return num_; }
   // pinned copy of num_pillars, written at the end of every run (valid once it completes)
   const int* num_pillars_host() const { return num_host_; }
+  // The device error words as the run's last kernel saw them (valid once the run completes):
+  // the tensor-core conv's sticky word (a bounded wait ran out: that conv skipped its stores)
+  // in the low 31 bits, bit 31 for the voxeliser's (a point count outside [0, capacity]).
+  // Nonzero means the run's outputs are not to be trusted.
+  unsigned device_error_host() const { return (unsigned)num_host_[B_]; }
 
  private:
   const Model* m_ = nullptr;
@@ -106,7 +111,9 @@ class Pipeline {
   UnitTable* tab_dev_ = nullptr;
   UnitTable* tab_host_ = nullptr;  // pinned; rewritten only once the previous run completed
   UnitTable* tab_map_ = nullptr;   // its device view (read by the first kernel of a run)
-  int* num_host_ = nullptr;        // pinned [B], written by the unit's last kernel
+  int* num_host_ = nullptr;        // pinned [B + 1], written by the unit's last kernel: the
+                                   // pillar counts, then the device error words
+  const unsigned* tc_err_ = nullptr;  // device address of the tensor-core conv's error word
   int* num_host_dev_ = nullptr;    // its device view
   cudaEvent_t tab_ev_ = nullptr;   // after the last run (whose first kernel read the table)
   std::vector<size_t> res_off_;

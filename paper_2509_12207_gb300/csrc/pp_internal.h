@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "pp.h"
 
 namespace pp {
@@ -18,6 +20,19 @@ void clear_error();
 const char* last_error();
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// SM count of the current device, looked up once per device (152 if the query fails).
+int device_sms();
+// Sets the dynamic shared-memory limit of kernel `func` to `bytes` on the current device, once
+// per device: `done` is the caller's per-kernel set of devices already configured (bit d for
+// device d; devices from 64 on are configured on every call).  Thread-safe.
+int smem_attr_once(const void* func, int bytes, std::atomic<uint64_t>* done, const char* what);
+
+// The tensor-core conv's sticky device error word (conv_tc.cu): read (and optionally clear) it,
+// set bits in it, or get its device address on the current device (for kernels that copy it).
+int tc_error_read(unsigned* code, bool clear);
+int tc_error_set(unsigned bits);
+int tc_error_address(const unsigned** out);
 
 // Programmatic dependent launch.  Kernels that follow another kernel of the library in a stream
 // (or graph) are launched with programmatic stream serialisation: they may start while their

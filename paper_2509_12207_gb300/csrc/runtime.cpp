@@ -90,6 +90,7 @@ struct Unit {
   Pipeline pipe;
   int precision = 0;
   bool busy = false, running = false;
+  bool failed = false;  // the launch itself failed: its frames complete with PP_FRAME_ERROR
   int nf = 0, level = 0, head_chain = 0;
   uint64_t frames[8] = {0};
   cudaEvent_t start = nullptr, done = nullptr;
@@ -163,7 +164,14 @@ struct pp_ctx {
   std::condition_variable cv_work, cv_done;
   std::thread dispatcher;
   std::atomic<bool> stop{false};
-  bool device_error = false;
+  uint64_t device_errors = 0;      // units whose launch or device work failed
+  unsigned device_error_code = 0;  // the last nonzero device error word a unit reported
+  // decision log (cfg.decision_log > 0): every release decision the dispatcher takes, with the
+  // inputs it took it on, until the log holds cfg.decision_log records
+  std::vector<pp_decision_record> log;
+  std::vector<pp_policy_frame> log_ready;
+  std::vector<pp_policy_active> log_active;
+  std::vector<uint64_t> log_drops;
 };
 
 namespace {
@@ -282,13 +290,22 @@ void reap(pp_ctx* c) {
     if (q == cudaErrorNotReady) continue;
     u->running = false;
     u->busy = false;
-    if (q != cudaSuccess) {
-      cudaGetLastError();
-      c->device_error = true;
+    if (q != cudaSuccess) cudaGetLastError();
+    // a unit failed if its launch did, if its event reports an error, or if its last kernel
+    // saw a device error word set (a conv whose bounded wait ran out skipped its stores, and
+    // every conv after it exits at once): its frames' outputs are not to be trusted
+    unsigned code = 0;
+    if (!u->failed && q == cudaSuccess && u->precision != kSynth) code = u->pipe.device_error_host();
+    const bool ok = !u->failed && q == cudaSuccess && code == 0;
+    u->failed = false;
+    if (!ok) {
+      c->device_errors++;
+      if (code) c->device_error_code = code;
     }
     const double t_done = q == cudaSuccess ? event_host_time(c, u->done) : now_us();
     float ms = 0;
-    if (q == cudaSuccess && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess) {
+    // only a unit that ran to completion feeds the estimate table
+    if (ok && cudaEventElapsedTime(&ms, u->start, u->done) == cudaSuccess) {
       if (u->precision == kSynth)
         c->chains[u->head_chain].lut.add(ms * 1000.0);
       else
@@ -298,7 +315,7 @@ void reap(pp_ctx* c) {
     for (int i = 0; i < u->nf; ++i) {
       Frame* f = c->frames[u->frames[i]];
       free_staging(c, f);
-      push_result(c, f, q == cudaSuccess ? PP_FRAME_DONE : PP_FRAME_ERROR, t_done);
+      push_result(c, f, ok ? PP_FRAME_DONE : PP_FRAME_ERROR, t_done);
     }
     // batch gate: closed batches finish in launch order
     const int id = (int)ui;
@@ -425,14 +442,38 @@ int launch_unit(pp_ctx* c, const pp_policy_decision& d, double t) {
     // the unit's graph also copies every frame's block outputs into its result slot
     st = u->pipe.run(nf, srcs, counts, direct, dsts, c->cfg.use_graphs != 0, s, host_mapped, hdsts);
   }
-  if (!st) st = cuda_status(cudaEventRecord(u->done, s), "record done");
-  // wake the dispatcher at completion from a separate stream: a host function in the unit's own
-  // stream would hold back whatever is queued behind it there until the callback has run
-  if (!st) st = cuda_status(cudaStreamWaitEvent(c->notify, u->done, 0), "notify wait");
-  if (!st) st = cuda_status(cudaLaunchHostFunc(c->notify, notify_cb, c), "host notify");
-  if (st) c->device_error = true;
+  // the completion event is recorded even after a failed launch, so that reap() sees this
+  // launch's end (not an earlier one's) and the unit is not reused while work it did enqueue
+  // may still run; the frames then complete with PP_FRAME_ERROR
+  const int rec = cuda_status(cudaEventRecord(u->done, s), "record done");
+  if (!st) st = rec;
+  u->failed = st != 0;
+  if (u->failed) {
+    cudaGetLastError();
+    if (rec) {
+      // not even the event could be recorded: nothing of this launch can be waited for, so
+      // finish its frames now (the unit stays out of use: its stream may hold work)
+      u->running = false;
+      u->failed = false;
+      c->device_errors++;
+      for (int i = 0; i < nf; ++i) {
+        Frame* f = c->frames[u->frames[i]];
+        free_staging(c, f);
+        push_result(c, f, PP_FRAME_ERROR, t);
+      }
+      return 0;
+    }
+  } else {
+    // wake the dispatcher at completion from a separate stream: a host function in the unit's
+    // own stream would hold back whatever is queued behind it there until the callback has run
+    // (without it the dispatcher still looks every 500 us while a unit runs)
+    if (cudaStreamWaitEvent(c->notify, u->done, 0) != cudaSuccess ||
+        cudaLaunchHostFunc(c->notify, notify_cb, c) != cudaSuccess)
+      cudaGetLastError();
+  }
   c->launched++;
   c->batch_frames += nf;
+  if (u->failed) return 0;  // no estimate accounting for a launch that did not happen
   // batched synchronisation bookkeeping
   c->open_units.push_back(ui);
   c->open_sum += u->est;
@@ -477,8 +518,28 @@ double decide_all(pp_ctx* c) {
     pp_policy_config pc = policy_cfg(c);
     pp_policy_decision d;
     std::vector<uint64_t> drops(rf.size() + 1);
-    pp_policy_decide(&pc, t, rf.data(), (int)rf.size(), act.data(), (int)act.size(),
-                     closed_pending(c), &d, drops.data(), (int)drops.size());
+    const int pend = closed_pending(c);
+    pp_policy_decide(&pc, t, rf.data(), (int)rf.size(), act.data(), (int)act.size(), pend, &d,
+                     drops.data(), (int)drops.size());
+    pp_decision_record* rec = nullptr;
+    if ((int64_t)c->log.size() < (int64_t)c->cfg.decision_log) {
+      pp_decision_record r;
+      memset(&r, 0, sizeof(r));
+      r.t_us = t;
+      r.cfg = pc;
+      r.closed_pending = pend;
+      r.n_ready = (int)rf.size();
+      r.n_active = (int)act.size();
+      r.ready_off = (int64_t)c->log_ready.size();
+      r.active_off = (int64_t)c->log_active.size();
+      r.drops_off = (int64_t)c->log_drops.size();
+      r.decision = d;
+      c->log_ready.insert(c->log_ready.end(), rf.begin(), rf.end());
+      c->log_active.insert(c->log_active.end(), act.begin(), act.end());
+      c->log_drops.insert(c->log_drops.end(), drops.begin(), drops.begin() + d.n_drops);
+      c->log.push_back(r);
+      rec = &c->log.back();
+    }
     for (int i = 0; i < d.n_drops; ++i) {
       Frame* f = c->frames[drops[i]];
       c->ready.erase(std::remove(c->ready.begin(), c->ready.end(), f), c->ready.end());
@@ -491,6 +552,7 @@ double decide_all(pp_ctx* c) {
     c->decisions++;
     if (d.kind == PP_DECIDE_RELEASE) {
       if (launch_unit(c, d, t)) return 200.0;  // no free unit
+      if (rec) rec->launched = 1;
       c->sched_us += now_us() - t;
       continue;
     }
@@ -567,7 +629,8 @@ size_t pp_struct_size(const char* name) {
                 {"pp_policy_frame", sizeof(pp_policy_frame)},
                 {"pp_policy_active", sizeof(pp_policy_active)},
                 {"pp_policy_config", sizeof(pp_policy_config)},
-                {"pp_policy_decision", sizeof(pp_policy_decision)}};
+                {"pp_policy_decision", sizeof(pp_policy_decision)},
+                {"pp_decision_record", sizeof(pp_decision_record)}};
   for (const auto& e : kSizes)
     if (strcmp(e.n, name) == 0) return e.s;
   return 0;
@@ -617,7 +680,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (!(cfg->est_noise >= 0 && cfg->est_noise < 1)) return fail(PP_EINVAL, "create: est_noise must be in [0, 1)");
   if (cfg->units < 0 || cfg->units > 64 || cfg->max_closed < 0 || !(cfg->delta_eval_us >= 0) ||
       cfg->max_admitted < 0 ||
-      !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0)
+      !(cfg->delay_quantum_us > 0) || cfg->th_calib_frames < 0 || cfg->decision_log < 0 ||
+      cfg->decision_log > (1 << 20))
     return fail(PP_EINVAL, "create: bad runtime knob");
   pp_ctx* c = new (std::nothrow) pp_ctx();
   if (!c) return fail(PP_ENOMEM, "create: host allocation");
@@ -953,7 +1017,7 @@ int pp_poll(pp_ctx* c, pp_result* out, int32_t max, int32_t* n_out, int64_t time
     ++n;
   }
   *n_out = n;
-  return c->device_error ? fail(PP_EDEVICE, "a unit failed on the device") : PP_OK;
+  return PP_OK;  // a failed unit's frames carry PP_FRAME_ERROR; pp_stats counts the failures
 }
 
 int pp_result_release_many(pp_ctx* c, int32_t n, const uint64_t* frame_ids) {
@@ -1032,6 +1096,32 @@ int pp_get_stats(pp_ctx* c, pp_stats* s) {
   s->collisions = c->collisions;
   s->sched_us_per_decision = c->decisions ? c->sched_us / (double)c->decisions : 0.0;
   s->th_urgent = c->th;
+  s->device_errors = c->device_errors;
+  s->device_error_code = c->device_error_code;
+  s->decisions = c->decisions;
+  return PP_OK;
+}
+
+int pp_decision_log(pp_ctx* c, pp_decision_record* recs, int32_t max_recs, pp_policy_frame* ready,
+                    int64_t max_ready, pp_policy_active* active, int64_t max_active, uint64_t* drops,
+                    int64_t max_drops, int32_t* n_recs, int64_t* n_ready, int64_t* n_active,
+                    int64_t* n_drops) {
+  if (!c) return fail(PP_EINVAL, "decision_log: NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (n_recs) *n_recs = (int32_t)c->log.size();
+  if (n_ready) *n_ready = (int64_t)c->log_ready.size();
+  if (n_active) *n_active = (int64_t)c->log_active.size();
+  if (n_drops) *n_drops = (int64_t)c->log_drops.size();
+  if (!recs) return PP_OK;
+  if (max_recs < (int64_t)c->log.size() || max_ready < (int64_t)c->log_ready.size() ||
+      max_active < (int64_t)c->log_active.size() || max_drops < (int64_t)c->log_drops.size() ||
+      (!c->log_ready.empty() && !ready) || (!c->log_active.empty() && !active) ||
+      (!c->log_drops.empty() && !drops))
+    return fail(PP_EINVAL, "decision_log: arrays smaller than the log");
+  std::copy(c->log.begin(), c->log.end(), recs);
+  std::copy(c->log_ready.begin(), c->log_ready.end(), ready);
+  std::copy(c->log_active.begin(), c->log_active.end(), active);
+  std::copy(c->log_drops.begin(), c->log_drops.end(), drops);
   return PP_OK;
 }
 

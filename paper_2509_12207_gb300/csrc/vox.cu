@@ -319,12 +319,7 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
   // point kernels: grid-stride, about 8 blocks of 256 threads per SM over the whole batch (a
   // grid sized for the capacity costs microseconds of empty blocks when frames are short)
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 152;
-  }
+  const int sms = device_sms();
   int px = (cap + 256 * kVoxU - 1) / (256 * kVoxU);
   const int px_max = (8 * sms + batch - 1) / batch;
   if (px > px_max) px = px_max;

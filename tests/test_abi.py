@@ -161,10 +161,37 @@ def test_config_head_defaults_and_layout(lib):
     mirrors = {"pp_config": pp.Config, "pp_result": pp.Result, "pp_stats": pp.Stats, "pp_geometry": pp.Geometry,
                "pp_arrival": pp.Arrival, "pp_replay_stats": pp.ReplayStats, "pp_policy_frame": pp.PolicyFrame,
                "pp_policy_active": pp.PolicyActive, "pp_policy_config": pp.PolicyConfig,
-               "pp_policy_decision": pp.PolicyDecision}
+               "pp_policy_decision": pp.PolicyDecision, "pp_decision_record": pp.DecisionRecord}
     for name, cls in mirrors.items():
         assert lib.pp_struct_size(name.encode()) == ctypes.sizeof(cls), name
     assert lib.pp_struct_size(b"pp_nothing") == 0
+
+
+def test_runtime_declarations_cite_the_paper():
+    """Every entry point of the serving runtime (from the runtime banner of include/pp.h on) is
+    preceded by a comment that names the passage it restates (a Section, Eq. or Table) or says
+    that the paper has no counterpart; a declaration right after another with no comment of its
+    own shares that one's."""
+    src = open(os.path.join(ROOT, "include", "pp.h")).read()
+    body = src[src.index("Serving runtime."):]
+    cite = re.compile(r"(Section \d|Eq\. \d|Table \d|no counterpart in the paper|the paper has no counterpart)",
+                      re.I)
+    prev, last_ok, seen, missing = 0, False, [], []
+    for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(pp_\w+)\s*\(", body, flags=re.M):
+        seg = body[prev:m.start()]
+        comments = "\n".join(re.findall(r"/\*.*?\*/", seg, flags=re.S))
+        text = " ".join(re.sub(r"/\*|\*/|^\s*\*", " ", comments, flags=re.M).split())
+        ok = bool(cite.search(text)) if comments else last_ok
+        last_ok = ok
+        seen.append(m.group(1))
+        if not ok:
+            missing.append(m.group(1))
+        prev = body.index(";", m.end()) + 1
+    for name in ("pp_create", "pp_register_chain", "pp_submit_frame", "pp_submit_frames", "pp_submit_frames_ex",
+                 "pp_poll", "pp_result_release", "pp_result_release_many", "pp_get_stats", "pp_destroy",
+                 "pp_policy_decide", "pp_decision_log"):
+        assert name in seen, name
+    assert not missing, missing
 
 
 def test_noise_factor_matches_splitmix64(lib):

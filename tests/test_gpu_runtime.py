@@ -481,6 +481,33 @@ def test_pipeline_neck_head_full_size_fp32(full_frame, full_head):
         p.destroy()
 
 
+def test_pipeline_full_size_bf16_blocks(full_frame):
+    """The full-size frame through a BF16 unit, block by block: each block output within the
+    BF16 tolerance of the FP64 oracle (unrounded weights), and of the oracle's block applied to
+    the unit's own (BF16) input of that block, so that one block's error cannot hide behind
+    another's."""
+    w, cloud, ref = full_frame
+    cfg, keep = pp.make_config(GEOM_FULL, BACKBONE_FULL, w, max_batch=1, cap_points=120000)
+    p = pp.Pipeline(cfg, pp.PP_BF16)
+    try:
+        p.run([torch.from_numpy(cloud).to(DEV)])
+        torch.cuda.synchronize()
+        assert p.num_pillars(0) == ref["vox"]["num_pillars"]
+        blocks = [_interior(p.output_tensor(0, b)).astype(np.float64) for b in range(3)]
+    finally:
+        p.destroy()
+    layers = BACKBONE_FULL.layers(64)
+    ends = list(np.cumsum(BACKBONE_FULL.convs) - 1)
+    x, start = ref["canvas"], 0
+    for b, end in enumerate(ends):
+        assert max_norm_err(blocks[b], ref["blocks"][b]) <= BF16_TOL, b
+        r = x
+        for l in range(start, end + 1):
+            r = O.conv3x3_bn_relu(r, w[2][l], w[3][l], layers[l][2])
+        assert max_norm_err(blocks[b], r) <= BF16_TOL, b
+        x, start = blocks[b], end + 1
+
+
 def test_pipeline_neck_head_bf16(full_frame, full_head):
     """BF16 unit with the neck and head: each stage against the oracle applied to the unit's
     own (BF16) input of that stage, weights unrounded; the head end to end within the BF16

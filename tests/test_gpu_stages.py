@@ -350,7 +350,11 @@ def test_conv_bf16(shape):
             assert not o[b, 0].any() and not o[b, -1].any() and not o[b, :, 0].any() and not o[b, :, -1].any()
 
 
-def test_frame_config1_fp32_end_to_end():
+@pytest.mark.parametrize("dtype", [pp.PP_F32, pp.PP_F32_TC], ids=["cuda-cores", "3xtf32"])
+def test_frame_config1_fp32_end_to_end(dtype):
+    """The 20k-point frame through the stage entry points, the convs on CUDA cores (PP_F32) and
+    on the tensor cores (PP_F32_TC: split FP32 operands, 3xTF32 products, the default FP32
+    path), every layer's output against the FP64 oracle."""
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     cloud = config_points(1, 0)
     weights = pillar_weights(bb, 7)
@@ -360,14 +364,21 @@ def test_frame_config1_fp32_end_to_end():
     v = pp.voxelize(pts, n, g)
     feat = pp.pointnet(v["pts"], v["npts"], v["coord"], v["num_pillars"],
                        torch.from_numpy(pfn_w).to(DEV), torch.from_numpy(pp.bn_fold(pfn_bn)).to(DEV), g)
-    x = pp.scatter(feat, v["pillar_of_cell"], g, dtype=pp.PP_F32)
+    x = pp.scatter(feat, v["pillar_of_cell"], g, dtype=dtype)
+    outs = []
     for (ci, co, s), w, bn in zip(bb.layers(64), conv_w, conv_bn):
-        x = pp.conv3x3(x, pp.pack_conv_weights(torch.from_numpy(w).to(DEV), pp.PP_F32),
-                       torch.from_numpy(pp.bn_fold(bn)).to(DEV), co, s, dtype=pp.PP_F32)
+        x = pp.conv3x3(x, pp.pack_conv_weights(torch.from_numpy(w).to(DEV), dtype),
+                       torch.from_numpy(pp.bn_fold(bn)).to(DEV), co, s, dtype=dtype)
+        outs.append(x[0] if dtype == pp.PP_F32_TC else x)   # value plane of split FP32
     torch.cuda.synchronize()
-    got = x[0, 1:-1, 1:-1].cpu().numpy()
+    got = outs[-1][0, 1:-1, 1:-1].cpu().numpy()
     assert got.shape == ref["blocks"][-1].shape
     assert rel_err(got, ref["blocks"][-1]) <= FP32_TOL
+    # every layer, each against the oracle's layer on the same (oracle) input chain
+    r = ref["canvas"]
+    for (ci, co, s), w, bn, o in zip(bb.layers(64), conv_w, conv_bn, outs):
+        r = O.conv3x3_bn_relu(r, w, bn, s)
+        assert rel_err(o[0, 1:-1, 1:-1].cpu().numpy(), r) <= FP32_TOL, (ci, co, s)
 
 
 @pytest.mark.parametrize("dtype", [pp.PP_BF16, pp.PP_F32_TC])
