@@ -71,6 +71,10 @@ def _args():
                          "[:util/kernel_us/frame_us] (the last: odd chains run synthetic kernels)")
     ap.add_argument("--serve-modes", default="urgency,plain",
                     help="release policies of the sweep: urgency, plain, edf, sjf, hrrn, lcuf, saedf, eqdf")
+    ap.add_argument("--profile-conv", default=None,
+                    help="LAYER:TILE[:REPS] -- launch only backbone layer LAYER of the workload (0-based, its input "
+                         "random) with conv tile TILE, REPS times (default 3), and exit: a short process for a "
+                         "profiler to capture one conv kernel")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     a = ap.parse_args()
     chains, depth = SERVING_SHAPE.get(a.workload, SERVING_SHAPE_DEFAULT)
@@ -391,6 +395,35 @@ def _measure_tf32_tflops(torch, n=8192, reps=10):
         return 2.0 * n ** 3 / best / 1e12
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def _profile_conv(a):
+    """--profile-conv: one backbone layer of the workload, launched REPS times with one tile
+    (split FP32 operands for the FP32 workloads, BF16 otherwise), on random input."""
+    import torch
+    import paper_2509_12207_gb300 as pp
+    g, bb, prec, batch, _cap, _frames, w = _workload(a.workload)
+    parts = a.profile_conv.split(":")
+    layer, tile = int(parts[0]), int(parts[1])
+    reps = int(parts[2]) if len(parts) > 2 else 3
+    dt = pp.PP_BF16 if prec == pp.PP_BF16 else pp.PP_F32_TC
+    H, W = g.ny, g.nx
+    layers = bb.layers(64)
+    for ci, co, st in layers[:layer]:
+        H, W = (H - 1) // st + 1, (W - 1) // st + 1
+    ci, co, st = layers[layer]
+    x = torch.rand((batch, H + 2, W + 2, ci), device="cuda")
+    x[:, 0] = 0; x[:, -1] = 0; x[:, :, 0] = 0; x[:, :, -1] = 0
+    x = pp.split_f32(x) if dt == pp.PP_F32_TC else x.to(torch.bfloat16)
+    wp = pp.pack_conv_weights(torch.from_numpy(w[2][layer]).cuda(), dt)
+    ss = torch.from_numpy(pp.bn_fold(w[3][layer])).cuda()
+    for _ in range(reps):
+        out = pp.conv3x3(x, wp, ss, co, st, dtype=dt, tile=tile)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_conv": {"workload": a.workload, "layer": layer, "cin": ci, "cout": co, "stride": st,
+                                       "H": H, "W": W, "batch": batch, "tile": tile,
+                                       "tile_info": pp.conv_tile_info(dt, tile), "reps": reps,
+                                       "out_shape": list(out.shape)}}))
 
 
 def _block_ends(bb):
@@ -862,6 +895,9 @@ def main():
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.profile_conv:
+        _profile_conv(a)
+        return
     if a.impl == "reference":
         if rank == 0:
             print(json.dumps(_run_reference(a)))

@@ -415,6 +415,11 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 // at any 128-byte row of its buffer), so one load serves three taps: 82 KiB per three K blocks
 // instead of 144 KiB, at any width.  A stage is one accumulation group (fold 3), in the order
 // ky, channel chunk, kx.
+// HALO with BN 128: the three kx taps' weights (value and remainder, 32 KiB each) no longer fit
+// beside two A stages, so A and B have rings of their own: an A slot holds one (ky, chunk)
+// input range (34 KiB), a B slot one tap (32 KiB); the MMAs of a group wait for the A slot once
+// and for each tap's B slot in turn, and free each B slot after its tap and the A slot after
+// the third.  130 KiB of TMA per three K blocks instead of 192 KiB for the plain BN 128 tile.
 
 struct PArgs {
   ConvShape c;
@@ -443,9 +448,13 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kBK = MODE == 1 ? 2 * kB : kB;        // per K block: B (+ lo plane)
   constexpr uint32_t kHaloRow = 130 * 128;                 // HALO: one padded input row, one plane
   constexpr uint32_t kHaloA = (kHaloRow + 1023) / 1024 * 1024;
-  static_assert(!HALO || (MODE == 1 && BN == 64 && !S2 && !SK && KPS == 3), "halo rows: 3xTF32, BN 64, stride 1");
+  static_assert(!HALO || (MODE == 1 && (BN == 64 || BN == 128) && !S2 && !SK && KPS == 3),
+                "halo rows: 3xTF32, BN 64 or 128, stride 1");
+  constexpr bool kSplit = HALO && BN == 128;               // A and B in separate rings
+  constexpr int NB = kSplit ? 4 : 0;                       // B ring slots (one tap each)
   constexpr uint32_t kStageA = HALO ? 2 * kHaloA : KPS * kAK;
   constexpr uint32_t kStageB = KPS * kBK;
+  constexpr uint32_t kBRegion = kSplit ? (uint32_t)NB * kBK : (uint32_t)STAGES * kStageB;
   constexpr int NACC = MODE == 1 ? 2 * BN : BN;            // TMEM columns per accumulator buffer
   // accumulator buffers in TMEM (512 columns): four where they fit, so that the MMAs can run
   // up to three groups ahead of the reducers while they store a finished tile
@@ -462,13 +471,15 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                                              ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
-  uint8_t* sO = sB + STAGES * kStageB;                     // epilogue: 4 KiB transposing buffer per reducer warp
+  uint8_t* sO = sB + kBRegion;                             // epilogue: 4 KiB transposing buffer per reducer warp
   constexpr uint32_t kStageO = 4u * 4096u;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);  // (split rings: the A ring's)
   uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
   uint64_t* kfree = kdone + NBUF;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(kfree + NBUF);
+  uint64_t* fullB = kfree + NBUF;                          // split rings: the B ring's
+  uint64_t* emptyB = fullB + NB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(emptyB + NB);
   float* s_scale = reinterpret_cast<float*>(tmem_slot + 4);  // [cout] folded BN scale
   float* s_shift = s_scale + args.co_blk;                    // [co_blk] folded BN shift (or bias)
 
@@ -488,6 +499,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(&kdone[i], 1);
       mbar_init(&kfree[i], 128);
+    }
+    for (int i = 0; i < NB; ++i) {
+      mbar_init(&fullB[i], 1);
+      mbar_init(&emptyB[i], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -544,7 +559,37 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   };
 
   if (warp == 0) {
-    if (HALO && lane == 0) {
+    if (kSplit && lane == 0) {
+      int sa = 0, sb = 0;
+      uint32_t pa = 0, pb = 0;
+      bool ok = true;
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        int b, oy0, ox0, n0;
+        decode(t, b, oy0, ox0, n0);
+        for (int ky = 0; ky < 3 && ok; ++ky) {
+          for (int cc = 0; cc < kchunks && ok; ++cc) {
+            if (!mbar_wait(&empty[sa], pa ^ 1u, 1u)) { ok = false; break; }
+            mbar_expect_tx(&full[sa], 2u * kHaloRow);
+            uint8_t* a = sA + sa * kStageA;
+            // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
+            const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
+            tma_2d(a, &tmA, &full[sa], cc * BK, pix);
+            tma_2d(a + kHaloA, &tmAlo, &full[sa], cc * BK, pix);
+            if (++sa == STAGES) { sa = 0; pa ^= 1u; }
+            for (int kx = 0; kx < 3; ++kx) {
+              if (!mbar_wait(&emptyB[sb], pb ^ 1u, 1u)) { ok = false; break; }
+              mbar_expect_tx(&fullB[sb], kBK);
+              uint8_t* bb = sB + sb * kBK;
+              const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+              tma_3d(bb, &tmB, &fullB[sb], kk, n0, 0);
+              tma_3d(bb + kB, &tmB, &fullB[sb], kk, n0, 1);
+              if (++sb == NB) { sb = 0; pb ^= 1u; }
+            }
+          }
+        }
+      }
+    } else if (HALO && lane == 0) {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -617,7 +662,49 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
     }
   } else if (warp == 1) {
-    if (HALO && lane == 0) {
+    if (kSplit && lane == 0) {
+      const uint32_t id = idesc_tf32<2 * BN>();
+      const uint32_t id2 = idesc_tf32<BN>();
+      const uint64_t dA0 = sdesc(sA), dB0 = sdesc(sB);
+      int sa = 0, sb = 0, gg = 0;
+      uint32_t pa = 0, pb = 0;
+      bool ok = true;
+      int t, k0, k1;
+      for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
+        {
+          int t2, a2, b2;
+          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
+        }
+        for (int g = 0; g < 3 * kchunks; ++g) {  // one A slot = one accumulation group
+          const int buf = gg & (NBUF - 1);
+          if (gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
+          if (!mbar_wait(&full[sa], pa, 2u)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * NACC);
+          const uint64_t da = dA0 + ((uint64_t)(sa * kStageA) >> 4);
+          for (int kx = 0; kx < 3; ++kx) {
+            if (!mbar_wait(&fullB[sb], pb, 2u)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t db = dB0 + ((uint64_t)(sb * kBK) >> 4);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // tap kx: the row from pixel kx on; K step k: 8 channels = 32 bytes into each row
+              const uint64_t a_k = da + (uint64_t)((kx * 128 + k * 32) >> 4);
+              const uint64_t b_k = db + (uint64_t)((k * 32) >> 4);
+              mma_tf32(d, a_k, b_k, id, (kx == 0 && k == 0) ? 0u : 1u);     // A_hi x [B_hi|B_lo]
+              mma_tf32(d, a_k + (kHaloA >> 4), b_k, id2, 1u);               // A_lo x B_hi
+            }
+            mma_commit(&emptyB[sb]);
+            if (++sb == NB) { sb = 0; pb ^= 1u; }
+          }
+          if (!ok) break;
+          mma_commit(&empty[sa]);
+          mma_commit(&kdone[buf]);
+          ++gg;
+          if (++sa == STAGES) { sa = 0; pa ^= 1u; }
+        }
+      }
+    } else if (HALO && lane == 0) {
       const uint32_t id = idesc_tf32<2 * BN>();
       const uint32_t id2 = idesc_tf32<BN>();
       const uint64_t dA0 = sdesc(sA), dB0 = sdesc(sB);
@@ -1252,9 +1339,11 @@ constexpr TileP kTilesPF[] = {{8, 16, 64}, {4, 32, 64}, {16, 8, 64}, {2, 64, 64}
                               {4, 32, 128}, {16, 8, 128}};
 constexpr int kNPB = (int)(sizeof(kTilesPB) / sizeof(kTilesPB[0]));
 constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
-// 3xTF32 tile 2 kNPF: one 128-pixel output row segment whose three kx taps share one loaded
-// 130-pixel input row (stride-1 3x3 convs)
+// 3xTF32 tiles 2 kNPF and 2 kNPF + 1: 128 consecutive output pixels (over the padded width)
+// whose three kx taps share one loaded 130-pixel input range (stride-1 3x3 convs), 64 or 128
+// output channels
 constexpr TileP kTileHalo = {1, 128, 64};
+constexpr TileP kTileHalo128 = {1, 128, 128};
 
 // Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
 // stage = KPS x (32 KiB A (+lo) + 2 x BN x 128 B).  All fill ~192 KiB of shared memory.  Two K
@@ -1276,11 +1365,16 @@ constexpr size_t p_smem() {
          4 * 4096 +                                   // epilogue transposing buffers
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
-// halo-row tile (3xTF32, BN 64): 2 stages of (two 130-row planes rounded to 1 KiB, three taps
-// of B value and remainder)
+// halo tile (3xTF32), BN 64: 2 stages of (two 130-row planes rounded to 1 KiB, three taps of
+// B value and remainder); BN 128: an A ring of 2 slots (two 130-row planes) and a B ring of 4
+// slots (one tap, value and remainder), with their own full/empty barriers
 constexpr size_t kHaloStages = 2;
+constexpr size_t kHaloBSlots = 4;
+template <int BN>
 constexpr size_t p_smem_halo() {
-  return 1024 + kHaloStages * (2 * 17408 + 3 * 2 * 64 * 128) + 4 * 4096 + (2 * kHaloStages + 8) * 8 + 16;
+  return BN == 64 ? 1024 + kHaloStages * (2 * 17408 + 3 * 2 * 64 * 128) + 4 * 4096 + (2 * kHaloStages + 8) * 8 + 16
+                  : 1024 + kHaloStages * 2 * 17408 + kHaloBSlots * 2 * BN * 128 + 4 * 4096 +
+                        (2 * kHaloStages + 8 + 2 * kHaloBSlots) * 8 + 16;
 }
 
 int num_sms() {
@@ -1293,7 +1387,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   constexpr int ST = HALO ? (int)kHaloStages : p_stages<MODE, BN>();
   constexpr int KPS = HALO ? 3 : p_kps<MODE, BN>();
   // + folded BN (cout <= 1024)
-  constexpr size_t bytes = (HALO ? p_smem_halo() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
+  constexpr size_t bytes = (HALO ? p_smem_halo<BN>() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
   static_assert(bytes <= 227 * 1024, "persistent conv shared memory");
   static std::atomic<uint64_t> attr_set{0};  // per instantiation: devices configured
   if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>),
@@ -1342,16 +1436,19 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     return fail(PP_EINVAL, "persistent conv: bad GEMM options");
   const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
   const int n = mode == 1 ? kNPF : kNPB;
-  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition; 2 kNPF: halo rows
-  const bool halo = mode == 1 && ptile == 2 * n;
-  if (halo && (c.stride != 1 || g.taps != 9 || g.up != 1 || c.cout % 64 || co_blk % 64))
-    return fail(PP_EINVAL, "persistent conv: the halo-row tile needs a stride-1 3x3 conv");
+  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition; 2 kNPF, 2 kNPF + 1:
+  // halo tiles of 64 / 128 output channels
+  const bool halo = mode == 1 && (ptile == 2 * n || ptile == 2 * n + 1);
+  const int halo_bn = ptile == 2 * n + 1 ? 128 : 64;
+  if (halo && (c.stride != 1 || g.taps != 9 || g.up != 1 || c.cout % halo_bn || co_blk % halo_bn))
+    return fail(PP_EINVAL, "persistent conv: the halo tile needs a stride-1 3x3 conv with cout a multiple of %d",
+                halo_bn);
   const bool sk = mode == 1 && ptile >= n && !halo;
   if (sk) ptile -= n;
   if (!halo && ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
   if (!halo && (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn))
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
-  const TileP t = halo ? kTileHalo : tiles[ptile];
+  const TileP t = halo ? (halo_bn == 128 ? kTileHalo128 : kTileHalo) : tiles[ptile];
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
     return fail(PP_EINVAL, "persistent conv: operands must be 16-byte aligned");
   const int BK = mode == 1 ? 32 : 64;
@@ -1439,6 +1536,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   const bool s2 = c.stride == 2;
 #define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, args, s) : launch_p<M, N, false, K>(ta, talo, tw, args, s)
   if (mode == 1) {
+    if (halo && t.bn == 128) return launch_p<1, 128, false, false, true>(ta, talo, tw, args, s);
     if (halo) return launch_p<1, 64, false, false, true>(ta, talo, tw, args, s);
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
     if (t.bn == 128) { if (sk) PP_P(1, 128, true); PP_P(1, 128, false); }
@@ -1529,7 +1627,7 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   return PP_OK;
 }
 
-int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + 1 : kNPB; }
+int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + 2 : kNPB; }
 int conv_tcp_sk_first() { return kNPF; }
 
 int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
@@ -1567,8 +1665,8 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   if (dtype == PP_F32_TC) {
-    if (tile < 0 || tile > 2 * kNPF) return PP_EINVAL;
-    const TileP& t = tile == 2 * kNPF ? kTileHalo : kTilesPF[tile % kNPF];
+    if (tile < 0 || tile > 2 * kNPF + 1) return PP_EINVAL;
+    const TileP& t = tile == 2 * kNPF ? kTileHalo : tile == 2 * kNPF + 1 ? kTileHalo128 : kTilesPF[tile % kNPF];
     *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : 4;
     return PP_OK;
   }

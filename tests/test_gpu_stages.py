@@ -254,7 +254,8 @@ def _conv_case(B, H, W, cin, cout, s, seed, density=0.5):
 
 SHAPES = [(2, 20, 18, 64, 64, 1), (2, 20, 18, 64, 64, 2), (1, 34, 46, 128, 128, 1),
           (1, 26, 30, 64, 128, 2), (1, 14, 10, 256, 256, 1), (1, 16, 18, 128, 256, 2),
-          (3, 9, 17, 64, 64, 1), (2, 22, 300, 64, 64, 1), (2, 24, 300, 64, 64, 2)]
+          (3, 9, 17, 64, 64, 1), (2, 22, 300, 64, 64, 1), (2, 24, 300, 64, 64, 2),
+          (3, 80, 98, 128, 128, 1)]   # more 128-pixel halo tiles (189) than SMs: CTAs walk several
 
 
 @pytest.mark.parametrize("shape", SHAPES)
