@@ -325,10 +325,6 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
                         "pinned pillar counts mapping")))
     return st;
   vw_ = vox_carve(vox_ws_, g, B_, cap_);
-  // the tile sums start zero too (each launch's bucket pass leaves them zero again)
-  if ((st = cuda_status(cudaMemsetAsync(vw_.tile_sums, 0, (size_t)B_ * vw_.ntiles * sizeof(int2), s),
-                        "clear tile sums")))
-    return st;
   if (tune) {
     // time every conv tile of every layer for each unit size on this unit's own buffers; the
     // launches below (and the captured graphs) then use the fastest

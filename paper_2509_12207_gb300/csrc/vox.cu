@@ -4,14 +4,10 @@
 // stage, made deterministic: pillars are the occupied cells in ascending cell order (at most
 // P), and each keeps its 32 lowest-index points in ascending index order.
 //
-// Four launches per batch (five for grids of more than kFoldTiles tiles), gridDim.y = frame:
+// Five launches per batch, gridDim.y = frame:
 //   1. vox_cell_count   cell per point; warp-aggregated atomic count per cell, which also hands
-//                       each point an arrival slot inside its cell (order arbitrary); each
-//                       block also sums, per tile of 2048 cells, the points it counted and the
-//                       cells it made occupied (the group whose atomic found the count at zero),
-//                       and adds those sums to the tile's (occupied cells, points) once
-//   2. (vox_tile_sums   the same sums from the final counts, for grids too large to keep a
-//                       block's sums in shared memory)
+//                       each point an arrival slot inside its cell (order arbitrary)
+//   2. vox_tile_sums    per tile of 2048 cells: (occupied cells, points)
 //   3. vox_scan         exclusive scans over cells -> pillar id (rank of occupied cell, kept if
 //                       < P), pillar's first point offset; writes coord / npts / num_pillars
 //   4. vox_bucket       point i -> csr[pillar_start + slot]: points grouped by kept pillar
@@ -42,8 +38,6 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
 // Points per thread per pass of the point kernels: their loads (and atomics) are issued
 // together so that one memory round trip covers several points.
 constexpr int kVoxU = 4;
-// Grids of at most this many tiles per frame get their tile sums from the count kernel.
-constexpr int kFoldTiles = 1024;
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
@@ -51,12 +45,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
                                const int* __restrict__ n_points, int* __restrict__ cell,
                                int* __restrict__ slot, unsigned* __restrict__ cnt, int* err,
                                const uint4* __restrict__ table_src, uint4* __restrict__ table_dst,
-                               int table_words, int2* __restrict__ tile_sums, int ntiles) {
-  // per-tile sums of this block's points (tile_sums != NULL): points counted, cells occupied
-  __shared__ int s_pts[kFoldTiles], s_occ[kFoldTiles];
-  if (tile_sums)
-    for (int j = threadIdx.x; j < ntiles; j += blockDim.x) s_pts[j] = s_occ[j] = 0;
-  __syncthreads();
+                               int table_words) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   // a release unit's per-launch table: copied from host memory for the kernels that follow
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < table_words) table_dst[threadIdx.x] = table_src[threadIdx.x];
@@ -109,14 +98,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
       base[u] = 0u;
       if (c[u] >= 0) {
         peers[u] = __match_any_sync(valid, c[u]);
-        if (lane == __ffs(peers[u]) - 1) {
-          base[u] = atomicAdd(&cnt_b[c[u]], (unsigned)__popc(peers[u]));
-          if (tile_sums) {
-            const int t = c[u] / kVoxTile;
-            atomicAdd(&s_pts[t], __popc(peers[u]));
-            if (base[u] == 0u) atomicAdd(&s_occ[t], 1);  // this group occupied the cell
-          }
-        }
+        if (lane == __ffs(peers[u]) - 1) base[u] = atomicAdd(&cnt_b[c[u]], (unsigned)__popc(peers[u]));
       }
     }
 #pragma unroll
@@ -125,15 +107,6 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
       const unsigned first = __shfl_sync(peers[u], base[u], __ffs(peers[u]) - 1);
       const int i = i0 + u * blockDim.x + threadIdx.x;
       slot[(size_t)b * cap + i] = (int)first + __popc(peers[u] & ((1u << lane) - 1u));
-    }
-  }
-  if (tile_sums) {
-    __syncthreads();  // the loop's trip count is block-uniform: every thread gets here
-    for (int j = threadIdx.x; j < ntiles; j += blockDim.x) {
-      if (s_pts[j] == 0) continue;
-      int2* d = tile_sums + (size_t)b * ntiles + j;
-      atomicAdd(&d->x, s_occ[j]);
-      atomicAdd(&d->y, s_pts[j]);
     }
   }
 }
@@ -262,13 +235,9 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
 __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
                            const int* __restrict__ cell, const int* __restrict__ slot,
                            const int* __restrict__ pillar_of_cell,
-                           const int* __restrict__ pillar_start, int* __restrict__ csr,
-                           int2* __restrict__ sums_clear, int ntiles) {
+                           const int* __restrict__ pillar_start, int* __restrict__ csr) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
-  // the scan (the tile sums' last reader) has completed: leave them zero for the next count
-  if (sums_clear && blockIdx.x == 0)
-    for (int j = threadIdx.x; j < ntiles; j += blockDim.x) sums_clear[(size_t)b * ntiles + j] = make_int2(0, 0);
   const int n = frame_points(n_points, b, cap, nullptr);
   const size_t rb = (size_t)b * cap;
   // kVoxU points per thread per pass, each dependent load issued for all of them at once
@@ -346,13 +315,8 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   const VoxUnitIO none;
   if (!io) io = &none;
   cudaError_t e = cudaSuccess;
-  // tile sums from the count kernel (they start at zero: the previous launch's bucket pass
-  // leaves them so, or the memset below), else from their own pass over the final counts
-  const bool fold = w.ntiles <= kFoldTiles;
   if (!io->cnt_clean) e = cudaMemsetAsync(cnt, 0, (size_t)batch * g.G * sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_status(e, "memset cnt");
-  if (fold && !io->cnt_clean) e = cudaMemsetAsync(w.tile_sums, 0, (size_t)batch * w.ntiles * sizeof(int2), s);
-  if (e != cudaSuccess) return cuda_status(e, "memset tile sums");
   // point kernels: grid-stride, about 8 blocks of 256 threads per SM over the whole batch (a
   // grid sized for the capacity costs microseconds of empty blocks when frames are short)
   const int sms = device_sms();
@@ -365,8 +329,8 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
   e = launch_pdl(vox_cell_count, pg, dim3(256), 0, s, g, cap, points, io->first_srcs ? io->first_srcs : srcs,
                  io->first_mirrors ? io->first_mirrors : mirrors,
                  io->first_counts ? io->first_counts : n_points, cell, w.slot, cnt, w.err, io->table_src,
-                 io->table_dst, io->table_words, fold ? w.tile_sums : (int2*)nullptr, w.ntiles);
-  if (e == cudaSuccess && !fold)
+                 io->table_dst, io->table_words);
+  if (e == cudaSuccess)
     e = launch_pdl(vox_tile_sums, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt, w.tile_sums,
                    w.ntiles);
   if (e == cudaSuccess)
@@ -375,8 +339,7 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
                    num_pillars, io->cnt_clean ? cnt : (unsigned*)nullptr);
   if (e == cudaSuccess)
     e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
-                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr, fold ? w.tile_sums : (int2*)nullptr,
-                   w.ntiles);
+                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr);
   if (e == cudaSuccess && pts)
     e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,
                    (const int*)w.csr, (const int*)w.pillar_start, (const int*)w.pillar_cnt,
