@@ -682,9 +682,10 @@ def _run_ours(a, rank, world, dist):
         "runtime": {"lat_p50_us": st["lat_p50_us"], "lat_p99_us": st["lat_p99_us"],
                     "sched_us_per_decision": st["sched_us_per_decision"], "units": timed_units,
                     "frames_per_unit": a.steps * n_frames / max(1, timed_units)},
-        # per unit: 5 voxelisation kernels, PointNet, scatter, one per conv layer, (one per block
-        # and the head,) result copy
-        "gpu_launches": timed_units * (5 + 1 + 1 + len(bb.layers(64)) + (len(bb.convs) + 1 if a.head else 0) + 1),
+        # per unit: 4 voxelisation kernels (count, tile sums, scan, bucket + stale canvas cells),
+        # point selection + PointNet + canvas write, one per conv layer, (one per block and the
+        # head,) result copy
+        "gpu_launches": timed_units * (4 + 1 + len(bb.layers(64)) + (len(bb.convs) + 1 if a.head else 0) + 1),
         "clocks": clk,
         "num_pillars": num_p,
         "wall_s": wall,

@@ -415,11 +415,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 // at any 128-byte row of its buffer), so one load serves three taps: 82 KiB per three K blocks
 // instead of 144 KiB, at any width.  A stage is one accumulation group (fold 3), in the order
 // ky, channel chunk, kx.
-// HALO with BN 128: the three kx taps' weights (value and remainder, 32 KiB each) no longer fit
-// beside two A stages, so A and B have rings of their own: an A slot holds one (ky, chunk)
-// input range (34 KiB), a B slot one tap (32 KiB); the MMAs of a group wait for the A slot once
-// and for each tap's B slot in turn, and free each B slot after its tap and the A slot after
-// the third.  130 KiB of TMA per three K blocks instead of 192 KiB for the plain BN 128 tile.
+// HALO with NBS > 0 (split rings): A and B have rings of their own -- STAGES A slots, each one
+// (ky, chunk) input range (34 KiB), and NBS B slots, each one tap's weights (value and
+// remainder: 16 KiB at BN 64, 32 KiB at BN 128); the MMAs of a group wait for the A slot once and
+// for each tap's B slot in turn, and free each B slot after its tap and the A slot after the
+// third.  With BN 128 this is what makes three taps fit at all (130 KiB of TMA per three K
+// blocks instead of 192 KiB for the plain BN 128 tile); with either BN a deeper ring than the
+// unified stage allows: a stage is held from its TMA issue until its MMAs complete, so the
+// ring's depth, not its bytes, sets how much of that round trip is hidden.
 
 struct PArgs {
   ConvShape c;
@@ -437,7 +440,7 @@ struct PArgs {
   unsigned* sem;  // stream-K: [total] arrival counters, zero between launches
 };
 
-template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false>
+template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false, int NBS = 0>
 __global__ void __launch_bounds__(192, 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
             const __grid_constant__ CUtensorMap tmB, PArgs args) {
@@ -450,8 +453,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kHaloA = (kHaloRow + 1023) / 1024 * 1024;
   static_assert(!HALO || (MODE == 1 && (BN == 64 || BN == 128) && !S2 && !SK && KPS == 3),
                 "halo rows: 3xTF32, BN 64 or 128, stride 1");
-  constexpr bool kSplit = HALO && BN == 128;               // A and B in separate rings
-  constexpr int NB = kSplit ? 4 : 0;                       // B ring slots (one tap each)
+  static_assert(NBS == 0 || HALO, "split rings: halo tiles only");
+  static_assert(!HALO || BN == 64 || NBS > 0, "a unified halo stage holds three taps of BN 64 only");
+  constexpr bool kSplit = HALO && NBS > 0;                 // A and B in separate rings
+  constexpr int NB = kSplit ? NBS : 0;                     // B ring slots (one tap each)
   constexpr uint32_t kStageA = HALO ? 2 * kHaloA : KPS * kAK;
   constexpr uint32_t kStageB = KPS * kBK;
   constexpr uint32_t kBRegion = kSplit ? (uint32_t)NB * kBK : (uint32_t)STAGES * kStageB;
@@ -1339,11 +1344,9 @@ constexpr TileP kTilesPF[] = {{8, 16, 64}, {4, 32, 64}, {16, 8, 64}, {2, 64, 64}
                               {4, 32, 128}, {16, 8, 128}};
 constexpr int kNPB = (int)(sizeof(kTilesPB) / sizeof(kTilesPB[0]));
 constexpr int kNPF = (int)(sizeof(kTilesPF) / sizeof(kTilesPF[0]));
-// 3xTF32 tiles 2 kNPF and 2 kNPF + 1: 128 consecutive output pixels (over the padded width)
-// whose three kx taps share one loaded 130-pixel input range (stride-1 3x3 convs), 64 or 128
-// output channels
-constexpr TileP kTileHalo = {1, 128, 64};
-constexpr TileP kTileHalo128 = {1, 128, 128};
+// 3xTF32 tiles from 2 kNPF on: 128 consecutive output pixels (over the padded width) whose three
+// kx taps share one loaded 130-pixel input range (stride-1 3x3 convs); their output channels and
+// ring shapes are listed with the shared-memory sizes below (kHalo)
 
 // Ring depth and K blocks per stage.  BF16 stage = KPS x (16 KiB A + BN x 128 B); 3xTF32
 // stage = KPS x (32 KiB A (+lo) + 2 x BN x 128 B).  All fill ~192 KiB of shared memory.  Two K
@@ -1365,32 +1368,36 @@ constexpr size_t p_smem() {
          4 * 4096 +                                   // epilogue transposing buffers
          (2 * p_stages<MODE, BN>() + 8) * 8 + 16;  // full/empty per stage, kdone/kfree x 4
 }
-// halo tile (3xTF32), BN 64: 2 stages of (two 130-row planes rounded to 1 KiB, three taps of
-// B value and remainder); BN 128: an A ring of 2 slots (two 130-row planes) and a B ring of 4
-// slots (one tap, value and remainder), with their own full/empty barriers
-constexpr size_t kHaloStages = 2;
-constexpr size_t kHaloBSlots = 4;
-template <int BN>
+// halo tiles (3xTF32): NB = 0: ST unified stages of (two 130-row planes rounded to 1 KiB, three
+// taps of B value and remainder), BN 64 only; NB > 0: an A ring of ST slots (two 130-row planes)
+// and a B ring of NB slots (one tap, value and remainder), with their own full/empty barriers
+template <int BN, int ST, int NB>
 constexpr size_t p_smem_halo() {
-  return BN == 64 ? 1024 + kHaloStages * (2 * 17408 + 3 * 2 * 64 * 128) + 4 * 4096 + (2 * kHaloStages + 8) * 8 + 16
-                  : 1024 + kHaloStages * 2 * 17408 + kHaloBSlots * 2 * BN * 128 + 4 * 4096 +
-                        (2 * kHaloStages + 8 + 2 * kHaloBSlots) * 8 + 16;
+  return NB == 0 ? 1024 + (size_t)ST * (2 * 17408 + 3 * 2 * BN * 128) + 4 * 4096 + (2 * ST + 8) * 8 + 16
+                 : 1024 + (size_t)ST * 2 * 17408 + (size_t)NB * 2 * BN * 128 + 4 * 4096 + (2 * ST + 8 + 2 * NB) * 8 +
+                       16;
 }
+// The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots; 0 = unified stages)
+struct HaloVariant {
+  int bn, stages, bslots;
+};
+constexpr HaloVariant kHalo[] = {{64, 2, 0}, {128, 2, 4}, {64, 3, 5}, {128, 3, 3}};
+constexpr int kNHalo = (int)(sizeof(kHalo) / sizeof(kHalo[0]));
 
 int num_sms() {
   return device_sms();
 }
 
-template <int MODE, int BN, bool S2, bool SK, bool HALO = false>
+template <int MODE, int BN, bool S2, bool SK, bool HALO = false, int HST = 2, int NBS = 0>
 int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
              cudaStream_t s) {
-  constexpr int ST = HALO ? (int)kHaloStages : p_stages<MODE, BN>();
+  constexpr int ST = HALO ? HST : p_stages<MODE, BN>();
   constexpr int KPS = HALO ? 3 : p_kps<MODE, BN>();
   // + folded BN (cout <= 1024)
-  constexpr size_t bytes = (HALO ? p_smem_halo<BN>() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
+  constexpr size_t bytes = (HALO ? p_smem_halo<BN, HST, NBS>() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
   static_assert(bytes <= 227 * 1024, "persistent conv shared memory");
   static std::atomic<uint64_t> attr_set{0};  // per instantiation: devices configured
-  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>),
+  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>),
                               (int)bytes, &attr_set, "persistent conv smem attribute"))
     return st;
   // stream-K: one range per CTA, never an empty one (an empty range would be counted among the
@@ -1398,8 +1405,8 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO>, dim3(grid), dim3(192), bytes, s, a, alo, w,
-                                args),
+  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>, dim3(grid), dim3(192), bytes, s, a,
+                                alo, w, args),
                      "persistent conv launch");
 }
 
@@ -1436,10 +1443,11 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     return fail(PP_EINVAL, "persistent conv: bad GEMM options");
   const TileP* tiles = mode == 1 ? kTilesPF : kTilesPB;
   const int n = mode == 1 ? kNPF : kNPB;
-  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition; 2 kNPF, 2 kNPF + 1:
-  // halo tiles of 64 / 128 output channels
-  const bool halo = mode == 1 && (ptile == 2 * n || ptile == 2 * n + 1);
-  const int halo_bn = ptile == 2 * n + 1 ? 128 : 64;
+  // 3xTF32 tiles kNPF..2 kNPF-1: the same tiles with the stream-K partition; 2 kNPF + i: halo
+  // variant kHalo[i]
+  const bool halo = mode == 1 && ptile >= 2 * n && ptile < 2 * n + kNHalo;
+  const HaloVariant hv = halo ? kHalo[ptile - 2 * n] : kHalo[0];
+  const int halo_bn = hv.bn;
   if (halo && (c.stride != 1 || g.taps != 9 || g.up != 1 || c.cout % halo_bn || co_blk % halo_bn))
     return fail(PP_EINVAL, "persistent conv: the halo tile needs a stride-1 3x3 conv with cout a multiple of %d",
                 halo_bn);
@@ -1448,7 +1456,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   if (!halo && ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
   if (!halo && (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn))
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
-  const TileP t = halo ? (halo_bn == 128 ? kTileHalo128 : kTileHalo) : tiles[ptile];
+  const TileP t = halo ? TileP{1, 128, halo_bn} : tiles[ptile];
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
     return fail(PP_EINVAL, "persistent conv: operands must be 16-byte aligned");
   const int BK = mode == 1 ? 32 : 64;
@@ -1536,8 +1544,14 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   const bool s2 = c.stride == 2;
 #define PP_P(M, N, K) return s2 ? launch_p<M, N, true, K>(ta, talo, tw, args, s) : launch_p<M, N, false, K>(ta, talo, tw, args, s)
   if (mode == 1) {
-    if (halo && t.bn == 128) return launch_p<1, 128, false, false, true>(ta, talo, tw, args, s);
-    if (halo) return launch_p<1, 64, false, false, true>(ta, talo, tw, args, s);
+    if (halo) {
+      switch (ptile - 2 * n) {
+        case 0: return launch_p<1, 64, false, false, true, 2, 0>(ta, talo, tw, args, s);
+        case 1: return launch_p<1, 128, false, false, true, 2, 4>(ta, talo, tw, args, s);
+        case 2: return launch_p<1, 64, false, false, true, 3, 5>(ta, talo, tw, args, s);
+        default: return launch_p<1, 128, false, false, true, 3, 3>(ta, talo, tw, args, s);
+      }
+    }
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
     if (t.bn == 128) { if (sk) PP_P(1, 128, true); PP_P(1, 128, false); }
   } else {
@@ -1627,7 +1641,7 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
   return PP_OK;
 }
 
-int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + 2 : kNPB; }
+int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + kNHalo : kNPB; }
 int conv_tcp_sk_first() { return kNPF; }
 
 int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
@@ -1665,8 +1679,8 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
     return PP_OK;
   }
   if (dtype == PP_F32_TC) {
-    if (tile < 0 || tile > 2 * kNPF + 1) return PP_EINVAL;
-    const TileP& t = tile == 2 * kNPF ? kTileHalo : tile == 2 * kNPF + 1 ? kTileHalo128 : kTilesPF[tile % kNPF];
+    if (tile < 0 || tile >= 2 * kNPF + kNHalo) return PP_EINVAL;
+    const TileP t = tile >= 2 * kNPF ? TileP{1, 128, kHalo[tile - 2 * kNPF].bn} : kTilesPF[tile % kNPF];
     *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : 4;
     return PP_OK;
   }

@@ -18,6 +18,35 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// x minus x with its 13 low mantissa bits cleared (exact in FP32): what a TF32 read drops.
+__device__ __forceinline__ float tf32_rem(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// One pillar's features (lane c holds channels c and c + 32) into its canvas pixel: FP32 (chunks
+// 16) as two 128-byte rows per plane, the TF32 remainder plane beside it when lo != NULL; BF16
+// (chunks 8) rounded to nearest even, lane l packing channels 2l and 2l + 1 (one 128-byte row).
+// The values and roundings are those of canvas_write on the same features.
+__device__ __forceinline__ void canvas_put(size_t pix, int chunks, float m0, float m1, int lane,
+                                           uint4* __restrict__ canvas, uint4* __restrict__ lo) {
+  if (chunks == 16) {
+    float* cv = reinterpret_cast<float*>(canvas) + pix * 64;
+    cv[lane] = m0;
+    cv[lane + 32] = m1;
+    if (lo) {
+      float* lv = reinterpret_cast<float*>(lo) + pix * 64;
+      lv[lane] = tf32_rem(m0);
+      lv[lane + 32] = tf32_rem(m1);
+    }
+  } else {
+    const int s0 = (2 * lane) & 31, s1 = (2 * lane + 1) & 31;
+    const float a0 = __shfl_sync(0xffffffffu, m0, s0), a1 = __shfl_sync(0xffffffffu, m0, s1);
+    const float b0 = __shfl_sync(0xffffffffu, m1, s0), b1 = __shfl_sync(0xffffffffu, m1, s1);
+    __nv_bfloat162 h = __floats2bfloat162_rn(lane < 16 ? a0 : b0, lane < 16 ? a1 : b1);
+    reinterpret_cast<unsigned*>(canvas)[pix * 32 + lane] = *reinterpret_cast<unsigned*>(&h);
+  }
+}
+
 // Stages the 9x64 weights (transposed) and the folded BN in shared memory.
 __device__ __forceinline__ void pfn_stage_weights(const float* pfn_w, const float* ss, float (*w_s)[64], float* sc_s,
                                                   float* sh_s) {
@@ -70,7 +99,9 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
                                                         const int* __restrict__ num_pillars,
                                                         const float* __restrict__ pfn_w,
                                                         const float* __restrict__ ss,
-                                                        float* __restrict__ feat) {
+                                                        float* __restrict__ feat, int chunks,
+                                                        int* __restrict__ drawn, int* __restrict__ drawn_num,
+                                                        uint4* __restrict__ canvas, uint4* __restrict__ lo) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   __shared__ float w_s[9][64];
   __shared__ float sc_s[64], sh_s[64];
@@ -79,6 +110,8 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = num_pillars[b];
+  // the bucket pass has read the previous frame's drawn list: this frame's replaces it
+  if (canvas && blockIdx.x == 0 && threadIdx.x == 0) drawn_num[b] = np;
   const float4* src = dev::frame_src(points, srcs, b, cap);
   const int* csr_b = csr + (size_t)b * cap;
   const int stride = gridDim.x * kWarps;
@@ -109,8 +142,14 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
     const int first_n = pn < np && lane < count_n ? csr_b[start_n + lane] : INT_MAX;
     float m0, m1;
     dev::pfn_pillar(g, v, count < 32 ? count : 32, cell, lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
-    feat[q * 64 + lane] = m0;
-    feat[q * 64 + lane + 32] = m1;
+    if (feat) {
+      feat[q * 64 + lane] = m0;
+      feat[q * 64 + lane + 32] = m1;
+    }
+    if (canvas) {
+      canvas_put(dev::canvas_pixel(g, b, cell), chunks, m0, m1, lane, canvas, lo);
+      if (lane == 0) drawn[q] = cell;
+    }
     count = count_n;
     start = start_n;
     cell = cell_n;
@@ -118,10 +157,6 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
   }
 }
 
-// x minus x with its 13 low mantissa bits cleared (exact in FP32): what a TF32 read drops.
-__device__ __forceinline__ float tf32_rem(float x) {
-  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-}
 __device__ __forceinline__ float4 tf32_rem4(float4 v) {
   return make_float4(tf32_rem(v.x), tf32_rem(v.y), tf32_rem(v.z), tf32_rem(v.w));
 }
@@ -202,10 +237,7 @@ __global__ void bev_scatter_bf16(Geom g, int batch, const float4* __restrict__ f
 // Stale cells: cells drawn for the slot's previous frame that hold no kept pillar now; each
 // thread zeroes one 16-byte chunk of one (both planes of the split FP32 form).  Cells that hold
 // a pillar now are left to canvas_write, so the two kernels never touch the same cell.
-__device__ __forceinline__ size_t canvas_pixel(const Geom& g, int b, int cell) {
-  const int iy = cell / g.nx, ix = cell - iy * g.nx;
-  return ((size_t)b * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1;
-}
+using dev::canvas_pixel;
 
 __global__ void canvas_clear_stale(Geom g, int batch, int chunks, const int* __restrict__ pillar_of_cell,
                                    const int* __restrict__ drawn, const int* __restrict__ drawn_num,
@@ -288,13 +320,15 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
 
 int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
                       const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
-                      const float* ss, float* feat, cudaStream_t s) {
+                      const float* ss, float* feat, cudaStream_t s, int chunks, int* drawn, int* drawn_num,
+                      uint4* canvas, uint4* lo) {
   int bx = (g.P + kWarps - 1) / kWarps;
   const int bx_max = (4 * sm_count() + batch - 1) / batch;
   if (bx > bx_max) bx = bx_max;
   return cuda_status(launch_pdl(pfn_select_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, cap,
                                 points, srcs, (const int*)w.csr, (const int*)w.pillar_start,
-                                (const int*)w.pillar_cnt, coord, num_pillars, pfn_w, ss, feat),
+                                (const int*)w.pillar_cnt, coord, num_pillars, pfn_w, ss, feat, chunks, drawn,
+                                drawn_num, canvas, lo),
                      "select + pointnet launch");
 }
 

@@ -101,5 +101,11 @@ __device__ __forceinline__ void pfn_pillar(const Geom& g, float4 v, int n, int c
   __syncwarp();  // f_w is rewritten by the next pillar
 }
 
+// Padded canvas pixel [b][iy + 1][ix + 1] of cell `cell` = iy * nx + ix of frame b.
+__device__ __forceinline__ size_t canvas_pixel(const Geom& g, int b, int cell) {
+  const int iy = cell / g.nx, ix = cell - iy * g.nx;
+  return ((size_t)b * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1;
+}
+
 }  // namespace dev
 }  // namespace pp

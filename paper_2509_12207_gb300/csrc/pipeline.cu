@@ -265,7 +265,6 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
   PP_ALLOC(npts_, (size_t)B_ * g.P * sizeof(int));
   PP_ALLOC(num_, (size_t)B_ * sizeof(int));
   PP_ALLOC(vox_ws_, vox_workspace_bytes(g, B_, cap_));
-  PP_ALLOC(feat_, (size_t)B_ * g.P * 64 * sizeof(float));
   // split FP32 (3xTF32 convs): every conv operand carries its TF32 remainder plane
   const size_t planes = m->conv_dtype == PP_F32_TC ? 2 : 1;
   PP_ALLOC(canvas_, planes * B_ * (g.ny + 2) * (g.nx + 2) * 64 * elt);
@@ -395,16 +394,24 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   io.table_dst = reinterpret_cast<uint4*>(tab_dev_);
   io.table_words = (int)(sizeof(UnitTable) / sizeof(uint4));
   io.cnt_clean = true;
+  // the canvas keeps each slot's previous frame: the bucket pass zeroes its stale cells, the
+  // point selection + PointNet pass writes every kept pillar's features straight into its cell
+  // (the incremental scatter of pp_scatter_update, without a feature buffer or launches of its
+  // own)
+  const bool split = m.conv_dtype == PP_F32_TC;
+  const int chunks = m.precision == PP_BF16 ? 8 : 16;
+  uint4* cv = static_cast<uint4*>(canvas_);
+  uint4* cv_lo = split ? cv + (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 16 : nullptr;
+  io.canvas = cv;
+  io.canvas_lo = cv_lo;
+  io.canvas_chunks = chunks;
+  io.drawn = drawn_;
+  io.drawn_num = drawn_num_;
   int st = vox_launch(g, n, cap_, points_, tab_dev_->counts, cell_, cnt_, poc_, coord_, npts_, num_,
                       nullptr, vw_, s, tab_dev_->src, tab_dev_->mirror, &io);
   if (!st)
-    st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, feat_, s);
-  const bool split = m.conv_dtype == PP_F32_TC;
-  // the canvas keeps the slot's previous frame: zero its stale cells, write the new pillars
-  if (!st)
-    st = scatter_update_launch(g, n, feat_, coord_, num_, poc_, drawn_, drawn_num_, canvas_,
-                               split ? PP_F32_TC : m.precision, s,
-                               split ? (size_t)B_ * (g.ny + 2) * (g.nx + 2) * 64 : 0);
+    st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, nullptr, s,
+                           chunks, drawn_, drawn_num_, cv, cv_lo);
   const void* x = canvas_;
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];

@@ -123,7 +123,6 @@ class Pipeline {
   unsigned* cnt_ = nullptr;
   void* vox_ws_ = nullptr;
   VoxWork vw_{};
-  float* feat_ = nullptr;
   void* canvas_ = nullptr;   // persists across runs: updated in place (pp_scatter_update)
   int* drawn_ = nullptr;     // [B][P] cells drawn into each slot's canvas by its last frame
   int* drawn_num_ = nullptr; // [B]

@@ -106,6 +106,14 @@ struct VoxUnitIO {
   uint4* table_dst = nullptr;                  // ... copied here (table_words 16-byte words)
   int table_words = 0;
   bool cnt_clean = false;
+  // a release unit's persistent canvas (canvas != NULL): the bucket pass also zeroes the cells
+  // drawn for each slot's previous frame (drawn / drawn_num) that hold no kept pillar now, in
+  // `canvas_chunks` 16-byte chunks per pixel (both planes of the split FP32 form, lo != NULL)
+  uint4* canvas = nullptr;
+  uint4* canvas_lo = nullptr;
+  int canvas_chunks = 0;
+  const int* drawn = nullptr;
+  const int* drawn_num = nullptr;
 };
 // pts == NULL: stop after the bucket step (the caller runs select_pfn_launch, which gathers
 // each pillar's points itself).  mirrors: device table of per-frame destinations (NULL
@@ -122,9 +130,14 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
                float* feat, cudaStream_t s);
 // Point selection + PointNet in one launch, from the voxelisation workspace (csr, pillar
 // start / count) of the same batch: feat as pfn_launch computes it, without the pts buffer.
+// With `canvas` (a release unit): each pillar's 64 features also go straight to its cell of the
+// persistent canvas (FP32 value + TF32 remainder plane `lo`, or BF16 round to nearest even, in
+// `chunks` 16-byte chunks per pixel), its cell to drawn[b][p] and the pillar count to
+// drawn_num[b]; feat may then be NULL.
 int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
                       const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
-                      const float* ss, float* feat, cudaStream_t s);
+                      const float* ss, float* feat, cudaStream_t s, int chunks = 0, int* drawn = nullptr,
+                      int* drawn_num = nullptr, uint4* canvas = nullptr, uint4* lo = nullptr);
 // lo[i] = TF32 remainder of x[i] (x, lo 16-byte aligned when n >= 4).
 int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s);
 // PP_F32_TC: `plane` = elements between the canvas's value and remainder planes (0 = this

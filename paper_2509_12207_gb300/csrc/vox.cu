@@ -139,28 +139,12 @@ __global__ void vox_tile_sums(Geom g, const unsigned* __restrict__ cnt, int2* __
   }
 }
 
-// Exclusive block scan of a pair of ints over 256 threads; returns the prefix, sets *total.
-__device__ __forceinline__ int2 block_scan2(int2 v, int2* total) {
-  __shared__ int2 warp_tot[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int2 inc = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int a = __shfl_up_sync(kFull, inc.x, o);
-    const int c = __shfl_up_sync(kFull, inc.y, o);
-    if (lane >= o) { inc.x += a; inc.y += c; }
-  }
-  if (lane == 31) warp_tot[wid] = inc;
-  __syncthreads();
-  int2 off = make_int2(0, 0), tot = make_int2(0, 0);
-  for (int w = 0; w < 8; ++w) {
-    if (w < wid) { off.x += warp_tot[w].x; off.y += warp_tot[w].y; }
-    tot.x += warp_tot[w].x; tot.y += warp_tot[w].y;
-  }
-  __syncthreads();
-  *total = tot;
-  return make_int2(off.x + inc.x - v.x, off.y + inc.y - v.y);
-}
-
+// Pillar ranks over one tile of kVoxTile cells, 256 threads: warp w owns the 256 consecutive
+// cells from base + 256 w as 8 rows of 32 (lane l takes cell 32 i + l of row i), so every load
+// and store of a row is one coalesced 128-byte line.  A cell's rank (pillar id, kept if < P) is
+// the number of occupied cells before it in the frame and its first point offset the number of
+// points before it: the preceding tiles' sums, plus the preceding warps' totals in this tile,
+// plus a warp scan along the rows.
 __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restrict__ cnt,
                                                 const int2* __restrict__ sums, int ntiles,
                                                 int* __restrict__ pillar_of_cell,
@@ -172,9 +156,8 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const unsigned* c = cnt + (size_t)b * g.G;
-  const int base = blockIdx.x * kVoxTile;
-  __shared__ unsigned tile[kVoxTile];
-  __shared__ int2 pre_red[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ int2 pre_red[8], warp_tot[8];
   // prefix of the preceding tiles' sums
   int2 pre = make_int2(0, 0);
   for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) {
@@ -185,49 +168,67 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
     pre.x += __shfl_xor_sync(kFull, pre.x, o);
     pre.y += __shfl_xor_sync(kFull, pre.y, o);
   }
-  if ((threadIdx.x & 31) == 0) pre_red[threadIdx.x >> 5] = pre;
-  for (int j = threadIdx.x; j < kVoxTile; j += blockDim.x) {
-    const int k = base + j;
-    tile[j] = k < g.G ? c[k] : 0u;
-    // a release unit's counts are left zero for its next launch (this CTA is their last reader)
-    if (cnt_clear && k < g.G) cnt_clear[(size_t)b * g.G + k] = 0u;
-  }
-  __syncthreads();
-  pre = make_int2(0, 0);
-  for (int w = 0; w < 8; ++w) { pre.x += pre_red[w].x; pre.y += pre_red[w].y; }
-  // 8 consecutive cells per thread
+  if (lane == 0) pre_red[wid] = pre;
+  const int wbase = blockIdx.x * kVoxTile + wid * 256;
   unsigned v[8];
-  int2 loc = make_int2(0, 0);
+  int2 tot = make_int2(0, 0);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    v[j] = tile[threadIdx.x * 8 + j];
-    loc.x += v[j] != 0u;
-    loc.y += (int)v[j];
+  for (int i = 0; i < 8; ++i) {
+    const int k = wbase + 32 * i + lane;
+    v[i] = k < g.G ? c[k] : 0u;
+    tot.x += v[i] != 0u;
+    tot.y += (int)v[i];
   }
-  int2 tot;
-  int2 ex = block_scan2(loc, &tot);
-  int rank = pre.x + ex.x, start = pre.y + ex.y;
+  // a release unit's counts are left zero for its next launch (this CTA is their last reader)
+  if (cnt_clear) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int k = base + threadIdx.x * 8 + j;
-    if (k >= g.G) break;
-    int pid = -1;
-    if (v[j] != 0u) {
-      if (rank < g.P) {
-        pid = rank;
-        const size_t q = (size_t)b * g.P + rank;
-        coord[q] = k;
-        npts[q] = v[j] < 32u ? (int)v[j] : 32;
-        pillar_start[q] = start;
-        pillar_cnt[q] = (int)v[j];
-      }
-      ++rank;
-      start += (int)v[j];
+    for (int i = 0; i < 8; ++i) {
+      const int k = wbase + 32 * i + lane;
+      if (k < g.G) cnt_clear[(size_t)b * g.G + k] = 0u;
     }
-    pillar_of_cell[(size_t)b * g.G + k] = pid;
+  }
+  for (int o = 16; o; o >>= 1) {
+    tot.x += __shfl_xor_sync(kFull, tot.x, o);
+    tot.y += __shfl_xor_sync(kFull, tot.y, o);
+  }
+  if (lane == 0) warp_tot[wid] = tot;
+  __syncthreads();
+  int2 before = make_int2(0, 0), tile = make_int2(0, 0);
+  pre = make_int2(0, 0);
+  for (int w = 0; w < 8; ++w) {
+    pre.x += pre_red[w].x; pre.y += pre_red[w].y;
+    tile.x += warp_tot[w].x; tile.y += warp_tot[w].y;
+    if (w < wid) { before.x += warp_tot[w].x; before.y += warp_tot[w].y; }
+  }
+  int rank = pre.x + before.x, start = pre.y + before.y;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = wbase + 32 * i + lane;
+    const int occ = v[i] != 0u ? 1 : 0, pts = (int)v[i];
+    int io = occ, ip = pts;  // inclusive scan along the row
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kFull, io, o);
+      const int d = __shfl_up_sync(kFull, ip, o);
+      if (lane >= o) { io += a; ip += d; }
+    }
+    if (k < g.G) {
+      const int r = rank + io - occ;
+      int pid = -1;
+      if (occ && r < g.P) {
+        pid = r;
+        const size_t q = (size_t)b * g.P + r;
+        coord[q] = k;
+        npts[q] = pts < 32 ? pts : 32;
+        pillar_start[q] = start + ip - pts;
+        pillar_cnt[q] = pts;
+      }
+      pillar_of_cell[(size_t)b * g.G + k] = pid;
+    }
+    rank += __shfl_sync(kFull, io, 31);
+    start += __shfl_sync(kFull, ip, 31);
   }
   if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) {
-    const int all = pre.x + tot.x;
+    const int all = pre.x + tile.x;
     num_pillars[b] = all < g.P ? all : g.P;
   }
 }
@@ -235,9 +236,25 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
 __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
                            const int* __restrict__ cell, const int* __restrict__ slot,
                            const int* __restrict__ pillar_of_cell,
-                           const int* __restrict__ pillar_start, int* __restrict__ csr) {
+                           const int* __restrict__ pillar_start, int* __restrict__ csr, int chunks,
+                           const int* __restrict__ drawn, const int* __restrict__ drawn_num,
+                           uint4* __restrict__ canvas, uint4* __restrict__ lo) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
+  if (canvas) {
+    // a release unit's canvas: zero the cells drawn for this slot's previous frame that hold no
+    // kept pillar now (the scan has completed, so pillar_of_cell is this frame's); the cells
+    // that do hold one are rewritten by the PointNet pass that follows, never touched here
+    const size_t work = (size_t)drawn_num[b] * chunks;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < work; t += (size_t)gridDim.x * blockDim.x) {
+      const int j = (int)(t / chunks), chunk = (int)(t % chunks);
+      const int c = drawn[(size_t)b * g.P + j];
+      if (pillar_of_cell[(size_t)b * g.G + c] >= 0) continue;
+      const size_t off = dev::canvas_pixel(g, b, c) * chunks + chunk;
+      canvas[off] = make_uint4(0u, 0u, 0u, 0u);
+      if (lo) lo[off] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
   const int n = frame_points(n_points, b, cap, nullptr);
   const size_t rb = (size_t)b * cap;
   // kVoxU points per thread per pass, each dependent load issued for all of them at once
@@ -339,7 +356,8 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
                    num_pillars, io->cnt_clean ? cnt : (unsigned*)nullptr);
   if (e == cudaSuccess)
     e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
-                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr);
+                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr, io->canvas_chunks, io->drawn,
+                   io->drawn_num, io->canvas, io->canvas_lo);
   if (e == cudaSuccess && pts)
     e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,
                    (const int*)w.csr, (const int*)w.pillar_start, (const int*)w.pillar_cnt,

@@ -75,6 +75,29 @@ def test_pipeline_batch_and_graph(prec, small_clouds):
         p.destroy()
 
 
+@pytest.mark.parametrize("prec", [pp.PP_F32, pp.PP_BF16])
+def test_pipeline_canvas_follows_frame_sequences(prec):
+    """A release unit keeps each slot's canvas from frame to frame: the bucket pass zeroes the
+    cells the slot's previous frame drew that hold no pillar now, and the PointNet pass writes
+    the new pillars.  Slots run different frames in turn (overlapping and disjoint cells, an
+    empty frame, fewer frames than before) and every output matches the oracle of its own
+    frame, so no stale pillar survives."""
+    clouds = [uniform_cloud(n, 300 + i, GEOM_SMALL) for i, n in enumerate((60000, 20000, 150000, 0, 90000))]
+    refs = [_ref(c) for c in clouds]
+    cfg, keep = pp.make_config(GEOM_SMALL, BACKBONE_SMALL, W_SMALL, max_batch=2, cap_points=150000)
+    p = pp.Pipeline(cfg, prec)
+    try:
+        dev = [torch.from_numpy(c).to(DEV) if len(c) else torch.zeros((0, 4), device=DEV) for c in clouds]
+        for seq in ([0, 1], [2, 3], [1], [4, 0], [3, 2], [0]):
+            p.run([dev[i] for i in seq])
+            torch.cuda.synchronize()
+            for slot, i in enumerate(seq):
+                assert p.num_pillars(slot) == refs[i]["vox"]["num_pillars"], (seq, slot)
+                _check_out(_interior(p.output_tensor(slot, 0)), refs[i], prec)
+    finally:
+        p.destroy()
+
+
 def test_pipeline_stream_k(small_clouds):
     """With stream_k the autotuner may pick stream-K tiles for the 3xTF32 convs: results stay
     within the FP32 tolerance and are bit-reproducible launch to launch."""
