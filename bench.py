@@ -715,7 +715,7 @@ def replica_throughput(frames_per_rank, world, window_s):
 # ------------------------------------------------------------------ serving (chains with deadlines)
 
 def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds=None, dfac=1.0, noise=0.0,
-           synth=None, tight=0.0):
+           synth=None, tight=0.0, warmup_s=1.0):
     """Replays periodic chains in real time against one context and returns its statistics.
 
     mode "urgency": the paper's release rules (urgency order, early exit, stream binding,
@@ -732,7 +732,8 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     kernel_us, total_us): every odd chain becomes a synthetic-load chain whose frames run
     round(total_us / kernel_us) kernels of about kernel_us on round(util x SMs) SMs (the paper's
     kernel-utilisation and kernel-time studies).  A frame the budget cannot admit counts as a
-    miss."""
+    miss.  The statistics exclude a warm-up replay of ``warmup_s`` seconds at the same load
+    (another seed), run to completion on the same context first."""
     from pp_synth import BACKBONE_SMALL, GEOM_SMALL, arrival_times, pillar_weights, serving_chains
     g, bb = GEOM_SMALL, BACKBONE_SMALL
     w = pillar_weights(bb, 7)
@@ -767,6 +768,11 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
                 synthetic.add(c.chain_id)
             else:
                 ctx.register_chain(c.chain_id, c.period_ms, c.deadline_ms * dfac, p)
+        if warmup_s > 0:
+            wev = arrival_times(chains, warmup_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed + 7)
+            ctx.replay([(20000.0 + t_ms * 1000.0, cid, i % len(clouds), 0 if cid in synthetic else n)
+                        for i, (t_ms, cid, n) in enumerate(wev)], clouds, timeout_us=30e6)
+            ctx.stats_reset()
         ev = arrival_times(chains, duration_s * 1000.0, rate=rate, jitter_ms=5.0, seed=seed)
         ev = [(t, cid, 0 if cid in synthetic else n) for t, cid, n in ev]
         # real-time replay from the library's own load generator (pp_replay): submissions at
@@ -786,7 +792,7 @@ def _serve(pp, torch, mode, n_chains, rate, duration_s, mixed, seed=1400, clouds
     miss = sum(m / n for m, n in per.values()) / max(1, len(per))
     return {"mode": mode, "chains": n_chains, "rate": rate, "deadline_factor": dfac, "mixed": mixed,
             "tight": tight, "tight_chains": [c.chain_id for c in chains if c.deadline_ms < c.period_ms],
-            "seconds": duration_s,
+            "seconds": duration_s, "warmup_s": warmup_s,
             "est_noise": noise, "synthetic": None if synth is None else
             {"util": synth[0], "kernel_us": synth[1], "frame_us": synth[2], "chains": "odd"},
             "frames": len(ev),

@@ -574,6 +574,11 @@ typedef struct {
  * collisions as counted for Section 4.4.3.  `out` is a caller struct of sizeof(pp_stats)
  * (pp_struct_size("pp_stats") gives this build's size). */
 int pp_get_stats(pp_ctx* ctx, pp_stats* out);
+/* Starts the statistics afresh (counters, latency samples, per-chain counts, the decision count;
+ * the estimate table, TH_urgent and every frame in flight are kept): a measurement that excludes
+ * a warm-up phase.  The paper evaluates after its chains have run in (Section 6.1); no
+ * counterpart as an entry point. */
+int pp_stats_reset(pp_ctx* ctx);
 /* Stops the dispatcher, waits (bounded, 10 s) for in-flight units, frees everything.
  * PP_ETIMEDOUT if the device did not finish in time (resources are then leaked, not freed).
  * No counterpart in the paper (its chains run for the life of the process). */

@@ -234,6 +234,7 @@ _SIGS = {
     "pp_result_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "pp_result_release_many": (ctypes.c_int, [_P, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "pp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "pp_stats_reset": (ctypes.c_int, [_P]),
     "pp_destroy": (ctypes.c_int, [_P]),
     "pp_now_us": (ctypes.c_double, []),
     "pp_struct_size": (_SZ, [ctypes.c_char_p]),
@@ -802,6 +803,10 @@ class Context:
         s = Stats()
         _check(lib().pp_get_stats(self.h, ctypes.byref(s)))
         return s.as_dict()
+
+    def stats_reset(self):
+        """pp_stats_reset: the statistics start afresh (frames in flight and estimates kept)."""
+        _check(lib().pp_stats_reset(self.h))
 
     def destroy(self):
         if self.h:

@@ -324,7 +324,10 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   const int r = warp * 32 + lane;
   const int oy = oy0 + r / args.bw, ox = ox0 + r % args.bw;
   const bool store = ok && oy < c.Ho && ox < c.Wo;
-  __nv_bfloat16* o = args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0;
+  char* fdst = c.frame_dst ? c.frame_dst[b] : nullptr;  // the frame's result slot, if any
+  __nv_bfloat16* o = fdst ? reinterpret_cast<__nv_bfloat16*>(fdst + c.frame_off) +
+                                ((size_t)(oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0
+                          : args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * c.cout + n0;
 #pragma unroll 1
   for (int j = 0; j < BN / 16; ++j) {
     float v[16];
@@ -819,6 +822,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int opy = args.up * oy + qb / args.up, opx = args.up * ox + qb % args.up;
       const size_t pix = ((size_t)b * (args.Hout + 2) + opy + 1) * (args.Wout + 2) + opx + 1;
       const size_t obase = pix * args.out_c + args.out_coff + nb;
+      // a release unit's last layer writes the frame's result slot directly
+      char* fdst = c.frame_dst ? c.frame_dst[b] : nullptr;
+      const size_t fbase = ((size_t)(opy + 1) * (args.Wout + 2) + opx + 1) * args.out_c + args.out_coff + nb;
       if (MODE == 1) {
         float acc[BN];
 #pragma unroll
@@ -889,7 +895,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           // channels (128 B per pixel) at a time through the warp's transposing buffer
           if (!ok) break;
           uint4* wbuf = reinterpret_cast<uint4*>(sO + q * 4096);
-          float* orow = static_cast<float*>(args.out) + obase;
+          float* orow = fdst ? reinterpret_cast<float*>(fdst + c.frame_off) + fbase
+                             : static_cast<float*>(args.out) + obase;
 #pragma unroll
           for (int k = 0; k < BN / 32; ++k) {
             uint4 hv[8], lv[8];
@@ -907,7 +914,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               lv[j] = make_uint4(__float_as_uint(l.x), __float_as_uint(l.y), __float_as_uint(l.z), __float_as_uint(l.w));
             }
             warp_rows_store(wbuf, hv, in_range ? reinterpret_cast<char*>(orow + 32 * k) : nullptr, lane);
-            warp_rows_store(wbuf, lv, in_range ? reinterpret_cast<char*>(orow + args.plane + 32 * k) : nullptr, lane);
+            if (!c.skip_lo)
+              warp_rows_store(wbuf, lv, in_range ? reinterpret_cast<char*>(orow + args.plane + 32 * k) : nullptr, lane);
           }
         }
       } else {
@@ -916,7 +924,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
         if (!ok) break;
         tc_fence_after();
-        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(args.out) + obase;
+        __nv_bfloat16* o = fdst ? reinterpret_cast<__nv_bfloat16*>(fdst + c.frame_off) + fbase
+                                : static_cast<__nv_bfloat16*>(args.out) + obase;
 #pragma unroll 1
         for (int j = 0; j < BN / 64; ++j) {
           uint32_t v[64];
@@ -1171,8 +1180,10 @@ conv3x3_rows(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
             pk[i] = *reinterpret_cast<uint32_t*>(&h);
           }
+          char* fdst = c.frame_dst ? c.frame_dst[b] : nullptr;  // the frame's result slot, if any
           uint4* dst = reinterpret_cast<uint4*>(
-              args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * 64);
+              fdst ? reinterpret_cast<__nv_bfloat16*>(fdst + c.frame_off) + ((size_t)(oy + 1) * (c.Wo + 2) + ox + 1) * 64
+                   : args.out + (((size_t)b * (c.Ho + 2) + oy + 1) * (c.Wo + 2) + ox + 1) * 64);
 #pragma unroll
           for (int i = 0; i < 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
         }

@@ -19,6 +19,8 @@ struct ResultCopy {
   const int* num;   // [B] pillars per frame ...
   int* num_host;    // ... copied to the unit's pinned host array (device view of the mapping)
   int err_at;       // num_host[err_at] receives the device error words (B, the capacity)
+  int direct;       // block written into the result slots by the last conv itself (-1: none):
+                    // not copied; its host copy (hblock) is read from the slot
   const unsigned* tc_err;  // the tensor-core conv's sticky error word
   const int* vox_err;      // the voxeliser's sticky error word
   int nblocks;
@@ -45,18 +47,24 @@ __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTabl
   if (!dst) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (int b = 0; b < rc.nblocks; ++b) {
-    const uint4* s = reinterpret_cast<const uint4*>(rc.src[b] + (size_t)f * rc.bytes[b]);
-    uint4* d = reinterpret_cast<uint4*>(dst + rc.off[b]);
+    const bool direct = b == rc.direct;
     uint4* h = hdst && b == rc.hblock ? reinterpret_cast<uint4*>(hdst) : nullptr;
+    if (direct && !h) continue;  // already in the slot, nothing to send to the host
+    const uint4* s = direct ? reinterpret_cast<const uint4*>(dst + rc.off[b])
+                            : reinterpret_cast<const uint4*>(rc.src[b] + (size_t)f * rc.bytes[b]);
+    // a direct block only goes to the host (its slot is the source)
+    uint4* d = direct ? nullptr : reinterpret_cast<uint4*>(dst + rc.off[b]);
     const size_t n = rc.bytes[b] / 16;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + 3 * stride < n; i += 4 * stride) {
       const uint4 v0 = __ldcs(s + i), v1 = __ldcs(s + i + stride);
       const uint4 v2 = __ldcs(s + i + 2 * stride), v3 = __ldcs(s + i + 3 * stride);
-      d[i] = v0;
-      d[i + stride] = v1;
-      d[i + 2 * stride] = v2;
-      d[i + 3 * stride] = v3;
+      if (d) {
+        d[i] = v0;
+        d[i + stride] = v1;
+        d[i + 2 * stride] = v2;
+        d[i + 3 * stride] = v3;
+      }
       if (h) {
         h[i] = v0;
         h[i + stride] = v1;
@@ -66,7 +74,7 @@ __global__ void __launch_bounds__(256) result_copy(ResultCopy rc, const UnitTabl
     }
     for (; i < n; i += stride) {
       const uint4 v = __ldcs(s + i);
-      d[i] = v;
+      if (d) d[i] = v;
       if (h) h[i] = v;
     }
   }
@@ -413,10 +421,20 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
     st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, nullptr, s,
                            chunks, drawn_, drawn_num_, cv, cv_lo);
   const void* x = canvas_;
+  // without a head the last layer's output is the frames' result: its tensor-core epilogue
+  // writes it straight into each frame's result slot (the unit table's dst; frames without a
+  // slot fall back to the unit's buffer), and a split FP32 last layer skips the remainder plane
+  // no later layer would read
+  const bool direct = m.head_outputs == 0 && m.conv_dtype != PP_F32;
   for (size_t l = 0; l < m.layers.size() && !st; ++l) {
     const LayerSpec& L = m.layers[l];
     ConvShape c{n, L.H, L.W, L.cin, L.cout, L.stride, L.Ho, L.Wo};
     c.static_w = true;  // packed once at creation
+    if (direct && l + 1 == m.layers.size()) {
+      c.frame_dst = tab_dev_->dst;
+      c.frame_off = res_off_.back();
+      c.skip_lo = split;
+    }
     if (split) {  // planes are laid out for the unit's capacity, not for this batch
       c.in_plane = (size_t)B_ * (L.H + 2) * (L.W + 2) * L.cin;
       c.out_plane = (size_t)B_ * (L.Ho + 2) * (L.Wo + 2) * L.cout;
@@ -437,6 +455,7 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
   rc.num = num_;
   rc.num_host = num_host_dev_;
   rc.err_at = B_;
+  rc.direct = -1;
   rc.tc_err = tc_err_;
   rc.vox_err = vw_.err;
   if (m.head_outputs > 0) {
@@ -487,6 +506,7 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
     }
     hout_off_ = rc.off[rc.hblock];
     hout_bytes_ = rc.bytes[rc.hblock];
+    if (direct) rc.direct = rc.hblock;  // the last block, written by the last conv
   }
   return cuda_status(launch_pdl(result_copy, dim3(std::max(1, 8 * sms_ / n), n), dim3(256), 0, s, rc,
                                 (const UnitTable*)tab_dev_),

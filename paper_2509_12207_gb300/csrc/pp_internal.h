@@ -160,6 +160,14 @@ struct ConvShape {
   // the weights were written before the previous kernel in the stream started (a release
   // unit's packed weights): a kernel may load them before its dependent-launch wait
   bool static_w = false;
+  // a release unit's last layer: frame b's output goes to frame_dst[b] + frame_off (its result
+  // slot, a padded [Ho+2][Wo+2][cout] map whose border stays zero) when that entry is non-NULL,
+  // else to the output buffer as usual; frame_dst is a device array of batch pointers (the
+  // unit table's), read when the epilogue runs.  skip_lo: split FP32 output without its
+  // remainder plane (no later layer reads it).  Tensor-core convs only.
+  char* const* frame_dst = nullptr;
+  size_t frame_off = 0;
+  bool skip_lo = false;
 };
 // The persistent tensor-core kernel as a general implicit GEMM (see conv_tc.cu PArgs): taps 9 =
 // 3x3 conv, 1 = pointwise; up > 1 = transposed conv with kernel = stride = up (GEMM N =

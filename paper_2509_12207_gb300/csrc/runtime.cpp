@@ -749,6 +749,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       if (!pl.slot_bytes) continue;
       if (n < 1) st = fail(PP_ENOMEM, "create: no room for a result slot in the budget");
       if (!st) st = cuda_status(cudaMalloc(&pl.base, pl.slot_bytes * (size_t)n), "result pool");
+      // zero once: the last conv writes a slot's interior directly, so its border must stay zero
+      if (!st) st = cuda_status(cudaMemsetAsync(pl.base, 0, pl.slot_bytes * (size_t)n, c->aux), "clear result pool");
       for (int i = 0; i < n && !st; ++i) pl.free.push_back(n - 1 - i);
       c->capacity[p] = n;
       used += pl.slot_bytes * (size_t)n;
@@ -1099,6 +1101,23 @@ int pp_get_stats(pp_ctx* c, pp_stats* s) {
   s->device_errors = c->device_errors;
   s->device_error_code = c->device_error_code;
   s->decisions = c->decisions;
+  return PP_OK;
+}
+
+int pp_stats_reset(pp_ctx* c) {
+  if (!c) return fail(PP_EINVAL, "stats_reset: NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->submitted = c->n_done = c->n_dropped = c->n_missed = c->rejected = c->launched = 0;
+  c->batch_frames = c->delayed = c->collisions = c->decisions = 0;
+  c->delayed_us = c->sched_us = 0;
+  c->first_arr = c->last_done = -1;
+  c->lat_all.clear();
+  c->device_errors = 0;
+  c->device_error_code = 0;
+  for (Chain& ch : c->chains) {
+    ch.frames = ch.missed = 0;
+    ch.lat.clear();
+  }
   return PP_OK;
 }
 

@@ -201,3 +201,27 @@ def test_unit_reports_device_error_word():
         ctx.release_many([r.frame_id for r in good])
     finally:
         ctx.destroy()
+
+
+def test_stats_reset_starts_afresh():
+    """pp_stats_reset zeroes the counters and latency samples (a warm-up excluded from a
+    measurement) while the context keeps serving: frames after it are counted from zero."""
+    ctx, keep = _ctx(units=1, precisions=2)
+    try:
+        ctx.register_chain(0, 50.0, 50.0, pp.PP_BF16)
+        cloud = uniform_cloud(40000, 9, GEOM_SMALL)
+        for _ in range(3):
+            assert ctx.submit(0, cloud)[0] == pp.PP_OK
+        ctx.release_many([r.frame_id for r in _drain(ctx, 3)])
+        assert ctx.stats()["done"] == 3
+        ctx.stats_reset()
+        st = ctx.stats()
+        assert st["done"] == st["submitted"] == st["missed"] == 0 and st["lat_p99_us"] == 0.0
+        assert st["chain_frames"][0] == 0 and st["decisions"] == 0
+        for _ in range(2):
+            assert ctx.submit(0, cloud)[0] == pp.PP_OK
+        ctx.release_many([r.frame_id for r in _drain(ctx, 2)])
+        st = ctx.stats()
+        assert st["done"] == st["submitted"] == st["chain_frames"][0] == 2 and st["lat_p99_us"] > 0
+    finally:
+        ctx.destroy()
