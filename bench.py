@@ -33,10 +33,13 @@ WORKLOADS = {
 }
 
 # (chains, steps in flight) of the throughput run: the steps alternate between the chains (a
-# chain's units run in order on its streams; units of different chains overlap on the GPU); the
-# 8-frame unit's short kernels keep more units in flight busy
-SERVING_SHAPE = {"cfg3-bf16": (3, 6)}
-SERVING_SHAPE_DEFAULT = (2, 3)
+# chain's units run in order on its streams; units of different chains overlap on the GPU).
+# Measured: full-size frame 2,470 frames/s at 3 x 4 and 4 x 4 against 2,344 at 2 x 3 and
+# 2,333-2,383 at 4 x 6, 6 x 6, 8 x 8 (a unit's front end then overlaps another's convolutions
+# without queueing so deep that units contend); the 8-frame unit's short kernels keep more in
+# flight busy
+SERVING_SHAPE = {"cfg3-bf16": (3, 6), "cfg1-fp32": (2, 3)}
+SERVING_SHAPE_DEFAULT = (4, 4)
 
 REFERENCE_BUDGET_S = 90  # wall-clock cap of the reference arm's timed steps
 

@@ -23,7 +23,9 @@ def _args(*argv):
 
 def test_serving_shape_defaults_per_workload():
     a = _args()
-    assert (a.workload, a.chains, a.depth) == ("cfg2-fp32", 2, 3)
+    assert (a.workload, a.chains, a.depth) == ("cfg2-fp32", 4, 4)
+    a = _args("--workload", "cfg1-fp32")
+    assert (a.chains, a.depth) == bench.SERVING_SHAPE["cfg1-fp32"]
     a = _args("--workload", "cfg3-bf16")
     assert (a.chains, a.depth) == bench.SERVING_SHAPE["cfg3-bf16"] == (3, 6)
     a = _args("--workload", "cfg3-bf16", "--chains", "1", "--depth", "2")
