@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
                                                         const float* __restrict__ ss,
                                                         float* __restrict__ feat, int chunks,
                                                         int* __restrict__ drawn, int* __restrict__ drawn_num,
-                                                        uint4* __restrict__ canvas, uint4* __restrict__ lo) {
+                                                        uint4* __restrict__ canvas, uint4* __restrict__ lo,
+                                                        unsigned* __restrict__ cnt_zero) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   __shared__ float w_s[9][64];
   __shared__ float sc_s[64], sh_s[64];
@@ -150,6 +151,8 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
       canvas_put(dev::canvas_pixel(g, b, cell), chunks, m0, m1, lane, canvas, lo);
       if (lane == 0) drawn[q] = cell;
     }
+    // a release unit's count array: the kept cell's entry (its bucket lookup) back to zero
+    if (cnt_zero && lane == 0) cnt_zero[(size_t)b * g.G + cell] = 0u;
     count = count_n;
     start = start_n;
     cell = cell_n;
@@ -321,14 +324,14 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
 int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
                       const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
                       const float* ss, float* feat, cudaStream_t s, int chunks, int* drawn, int* drawn_num,
-                      uint4* canvas, uint4* lo) {
+                      uint4* canvas, uint4* lo, unsigned* cnt_zero) {
   int bx = (g.P + kWarps - 1) / kWarps;
   const int bx_max = (4 * sm_count() + batch - 1) / batch;
   if (bx > bx_max) bx = bx_max;
   return cuda_status(launch_pdl(pfn_select_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, cap,
                                 points, srcs, (const int*)w.csr, (const int*)w.pillar_start,
                                 (const int*)w.pillar_cnt, coord, num_pillars, pfn_w, ss, feat, chunks, drawn,
-                                drawn_num, canvas, lo),
+                                drawn_num, canvas, lo, cnt_zero),
                      "select + pointnet launch");
 }
 

@@ -419,7 +419,7 @@ int Pipeline::enqueue(int n, cudaStream_t s) {
                       nullptr, vw_, s, tab_dev_->src, tab_dev_->mirror, &io);
   if (!st)
     st = select_pfn_launch(g, n, cap_, points_, tab_dev_->gsrc, vw_, coord_, num_, m.pfn_w, m.pfn_ss, nullptr, s,
-                           chunks, drawn_, drawn_num_, cv, cv_lo);
+                           chunks, drawn_, drawn_num_, cv, cv_lo, cnt_);
   const void* x = canvas_;
   // without a head the last layer's output is the frames' result: its tensor-core epilogue
   // writes it straight into each frame's result slot (the unit table's dst; frames without a

@@ -105,6 +105,9 @@ struct VoxUnitIO {
   const uint4* table_src = nullptr;            // host-mapped table ...
   uint4* table_dst = nullptr;                  // ... copied here (table_words 16-byte words)
   int table_words = 0;
+  // the counts start zero (no memset); the scan then leaves each kept cell's pillar start + 1
+  // there for the bucket pass (a dropped cell's count back at zero), and the PointNet pass
+  // (select_pfn_launch's cnt_zero) zeroes the kept cells' entries again for the next launch
   bool cnt_clean = false;
   // a release unit's persistent canvas (canvas != NULL): the bucket pass also zeroes the cells
   // drawn for each slot's previous frame (drawn / drawn_num) that hold no kept pillar now, in
@@ -130,6 +133,8 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
                float* feat, cudaStream_t s);
 // Point selection + PointNet in one launch, from the voxelisation workspace (csr, pillar
 // start / count) of the same batch: feat as pfn_launch computes it, without the pts buffer.
+// cnt_zero (a release unit whose count array the scan turned into the bucket's lookup): each
+// kept pillar's cell entry is set back to zero.
 // With `canvas` (a release unit): each pillar's 64 features also go straight to its cell of the
 // persistent canvas (FP32 value + TF32 remainder plane `lo`, or BF16 round to nearest even, in
 // `chunks` 16-byte chunks per pixel), its cell to drawn[b][p] and the pillar count to
@@ -137,7 +142,8 @@ int pfn_launch(const Geom& g, int batch, const float4* pts, const int* npts, con
 int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, const float4* const* srcs,
                       const VoxWork& w, const int* coord, const int* num_pillars, const float* pfn_w,
                       const float* ss, float* feat, cudaStream_t s, int chunks = 0, int* drawn = nullptr,
-                      int* drawn_num = nullptr, uint4* canvas = nullptr, uint4* lo = nullptr);
+                      int* drawn_num = nullptr, uint4* canvas = nullptr, uint4* lo = nullptr,
+                      unsigned* cnt_zero = nullptr);
 // lo[i] = TF32 remainder of x[i] (x, lo 16-byte aligned when n >= 4).
 int tf32_split_launch(const float* x, float* lo, size_t n, cudaStream_t s);
 // PP_F32_TC: `plane` = elements between the canvas's value and remainder planes (0 = this

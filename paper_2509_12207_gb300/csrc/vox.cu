@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
                                                 int* __restrict__ pillar_start,
                                                 int* __restrict__ pillar_cnt,
                                                 int* __restrict__ num_pillars,
-                                                unsigned* __restrict__ cnt_clear) {
+                                                unsigned* __restrict__ cnt_starts) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
   const unsigned* c = cnt + (size_t)b * g.G;
@@ -178,14 +178,6 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
     v[i] = k < g.G ? c[k] : 0u;
     tot.x += v[i] != 0u;
     tot.y += (int)v[i];
-  }
-  // a release unit's counts are left zero for its next launch (this CTA is their last reader)
-  if (cnt_clear) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int k = wbase + 32 * i + lane;
-      if (k < g.G) cnt_clear[(size_t)b * g.G + k] = 0u;
-    }
   }
   for (int o = 16; o; o >>= 1) {
     tot.x += __shfl_xor_sync(kFull, tot.x, o);
@@ -223,6 +215,10 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
         pillar_cnt[q] = pts;
       }
       pillar_of_cell[(size_t)b * g.G + k] = pid;
+      // a release unit: the count becomes the bucket pass's lookup -- a kept cell's first point
+      // offset + 1, zero for a cell the pillar cap dropped (this CTA is the count's last
+      // reader; the PointNet pass zeroes the kept cells' entries for the next launch)
+      if (cnt_starts && occ) cnt_starts[(size_t)b * g.G + k] = pid >= 0 ? (unsigned)(start + ip - pts) + 1u : 0u;
     }
     rank += __shfl_sync(kFull, io, 31);
     start += __shfl_sync(kFull, ip, 31);
@@ -236,7 +232,8 @@ __global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restri
 __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
                            const int* __restrict__ cell, const int* __restrict__ slot,
                            const int* __restrict__ pillar_of_cell,
-                           const int* __restrict__ pillar_start, int* __restrict__ csr, int chunks,
+                           const int* __restrict__ pillar_start, int* __restrict__ csr,
+                           const unsigned* __restrict__ cnt_starts, int chunks,
                            const int* __restrict__ drawn, const int* __restrict__ drawn_num,
                            uint4* __restrict__ canvas, uint4* __restrict__ lo) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
@@ -265,6 +262,17 @@ __global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
       const int i = i0 + u * blockDim.x + threadIdx.x;
       c[u] = i < n ? cell[rb + i] : -1;
       sl[u] = i < n ? slot[rb + i] : 0;
+    }
+    if (cnt_starts) {
+      // a release unit: one lookup per point, the cell's first point offset + 1 left by the
+      // scan (0: the cell was dropped by the pillar cap)
+      unsigned st[kVoxU];
+#pragma unroll
+      for (int u = 0; u < kVoxU; ++u) st[u] = c[u] >= 0 ? cnt_starts[(size_t)b * g.G + c[u]] : 0u;
+#pragma unroll
+      for (int u = 0; u < kVoxU; ++u)
+        if (st[u]) csr[rb + (st[u] - 1u) + sl[u]] = i0 + u * blockDim.x + threadIdx.x;
+      continue;
     }
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) p[u] = c[u] >= 0 ? pillar_of_cell[(size_t)b * g.G + c[u]] : -1;
@@ -356,7 +364,8 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
                    num_pillars, io->cnt_clean ? cnt : (unsigned*)nullptr);
   if (e == cudaSuccess)
     e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
-                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr, io->canvas_chunks, io->drawn,
+                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr,
+                   io->cnt_clean ? cnt : (unsigned*)nullptr, io->canvas_chunks, io->drawn,
                    io->drawn_num, io->canvas, io->canvas_lo);
   if (e == cudaSuccess && pts)
     e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,
