@@ -61,6 +61,9 @@ def _args():
     ap.add_argument("--no-batched", action="store_true",
                     help="with the default workload, skip the 8-frame BF16 unit run reported under batched_bf16")
     ap.add_argument("--fp32-cuda-cores", action="store_true", help="FP32 convs on CUDA cores instead of 3xTF32")
+    ap.add_argument("--stream-k", action="store_true",
+                    help="let the autotuner also time the stream-K 3xTF32 conv tiles (config stream_k; "
+                         "bit-reproducible here because every unit of the FP32 workloads holds one frame)")
     ap.add_argument("--depth", type=int, default=None,
                     help="steps in flight (1 = each step waits for the last; default per workload)")
     ap.add_argument("--chains", type=int, default=None,
@@ -552,7 +555,7 @@ def _run_ours(a, rank, world, dist):
     cfg, keep = pp.make_config(g, bb, w, head=head, max_batch=batch, cap_points=cap, precisions=1 << prec,
                                units=max(2, a.depth), max_admitted=2 * a.depth * batch,
                                th_urgent=-1.0, early_exit=0, fp32_cuda_cores=1 if a.fp32_cuda_cores else 0,
-                               autotune=0 if tuned else 1)
+                               autotune=0 if tuned else 1, stream_k=1 if a.stream_k else 0)
     ctx = pp.Context(cfg)
     if a.tune_table and not tuned:
         pp.conv_tune_save(a.tune_table)
@@ -687,7 +690,8 @@ def _run_ours(a, rank, world, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pp.PP_F32 else "bf16", "data": "synthetic",
         "config": {"workload": WORKLOADS[a.workload] + (HEAD_NOTE if a.head else ""), "frames_per_step": n_frames, "steps_in_flight": a.depth,
-                   "chains": max(1, a.chains), "points_per_frame":
+                   "chains": max(1, a.chains), "conv_stream_k": a.stream_k and prec == pp.PP_F32
+                   and not a.fp32_cuda_cores, "points_per_frame":
                    [int(f.shape[0]) for f in frames], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "per-frame working set (~%d MB canvas + activations) exceeds the 129 MB L2"
                          % (canvas_bytes // 2 ** 20)},

@@ -454,7 +454,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kBK = MODE == 1 ? 2 * kB : kB;        // per K block: B (+ lo plane)
   constexpr uint32_t kHaloRow = 130 * 128;                 // HALO: one padded input row, one plane
   constexpr uint32_t kHaloA = (kHaloRow + 1023) / 1024 * 1024;
-  static_assert(!HALO || (MODE == 1 && (BN == 64 || BN == 128) && !S2 && !SK && KPS == 3),
+  static_assert(!HALO || (MODE == 1 && (BN == 64 || BN == 128) && !S2 && KPS == 3),
                 "halo rows: 3xTF32, BN 64 or 128, stride 1");
   static_assert(NBS == 0 || HALO, "split rings: halo tiles only");
   static_assert(!HALO || BN == 64 || NBS > 0, "a unified halo stage holds three taps of BN 64 only");
@@ -494,7 +494,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const ConvShape& c = args.c;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kchunks = c.cin / BK;
-  const int KB = args.taps * kchunks;
+  // work units of one tile: K blocks, or for the halo tiles accumulation groups (one ky and one
+  // channel chunk, the three kx taps of one loaded input range), ky outer, chunk inner
+  const int KB = HALO ? 3 * kchunks : args.taps * kchunks;
   const int fold = MODE == 1 ? args.fold : KB;
   const int Hp2 = (c.H + 2) / 2;
 
@@ -575,25 +577,24 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
         int b, oy0, ox0, n0;
         decode(t, b, oy0, ox0, n0);
-        for (int ky = 0; ky < 3 && ok; ++ky) {
-          for (int cc = 0; cc < kchunks && ok; ++cc) {
-            if (!mbar_wait(&empty[sa], pa ^ 1u, 1u)) { ok = false; break; }
-            mbar_expect_tx(&full[sa], 2u * kHaloRow);
-            uint8_t* a = sA + sa * kStageA;
-            // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
-            const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
-            tma_2d(a, &tmA, &full[sa], cc * BK, pix);
-            tma_2d(a + kHaloA, &tmAlo, &full[sa], cc * BK, pix);
-            if (++sa == STAGES) { sa = 0; pa ^= 1u; }
-            for (int kx = 0; kx < 3; ++kx) {
-              if (!mbar_wait(&emptyB[sb], pb ^ 1u, 1u)) { ok = false; break; }
-              mbar_expect_tx(&fullB[sb], kBK);
-              uint8_t* bb = sB + sb * kBK;
-              const int kk = (ky * 3 + kx) * c.cin + cc * BK;
-              tma_3d(bb, &tmB, &fullB[sb], kk, n0, 0);
-              tma_3d(bb + kB, &tmB, &fullB[sb], kk, n0, 1);
-              if (++sb == NB) { sb = 0; pb ^= 1u; }
-            }
+        for (int gi = k0; gi < k1 && ok; ++gi) {
+          const int ky = gi / kchunks, cc = gi % kchunks;
+          if (!mbar_wait(&empty[sa], pa ^ 1u, 1u)) { ok = false; break; }
+          mbar_expect_tx(&full[sa], 2u * kHaloRow);
+          uint8_t* a = sA + sa * kStageA;
+          // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
+          const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
+          tma_2d(a, &tmA, &full[sa], cc * BK, pix);
+          tma_2d(a + kHaloA, &tmAlo, &full[sa], cc * BK, pix);
+          if (++sa == STAGES) { sa = 0; pa ^= 1u; }
+          for (int kx = 0; kx < 3; ++kx) {
+            if (!mbar_wait(&emptyB[sb], pb ^ 1u, 1u)) { ok = false; break; }
+            mbar_expect_tx(&fullB[sb], kBK);
+            uint8_t* bb = sB + sb * kBK;
+            const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+            tma_3d(bb, &tmB, &fullB[sb], kk, n0, 0);
+            tma_3d(bb + kB, &tmB, &fullB[sb], kk, n0, 1);
+            if (++sb == NB) { sb = 0; pb ^= 1u; }
           }
         }
       }
@@ -605,23 +606,22 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
         int b, oy0, ox0, n0;
         decode(t, b, oy0, ox0, n0);
-        for (int ky = 0; ky < 3 && ok; ++ky) {
-          for (int cc = 0; cc < kchunks; ++cc) {
-            if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
-            mbar_expect_tx(&full[s], 2u * kHaloRow + 3u * kBK);
-            uint8_t* a = sA + s * kStageA;
-            // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
-            const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
-            tma_2d(a, &tmA, &full[s], cc * BK, pix);
-            tma_2d(a + kHaloA, &tmAlo, &full[s], cc * BK, pix);
-            for (int kx = 0; kx < 3; ++kx) {
-              uint8_t* bb = sB + s * kStageB + kx * kBK;
-              const int kk = (ky * 3 + kx) * c.cin + cc * BK;
-              tma_3d(bb, &tmB, &full[s], kk, n0, 0);
-              tma_3d(bb + kB, &tmB, &full[s], kk, n0, 1);
-            }
-            if (++s == STAGES) { s = 0; ph ^= 1u; }
+        for (int gi = k0; gi < k1 && ok; ++gi) {
+          const int ky = gi / kchunks, cc = gi % kchunks;
+          if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
+          mbar_expect_tx(&full[s], 2u * kHaloRow + 3u * kBK);
+          uint8_t* a = sA + s * kStageA;
+          // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
+          const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
+          tma_2d(a, &tmA, &full[s], cc * BK, pix);
+          tma_2d(a + kHaloA, &tmAlo, &full[s], cc * BK, pix);
+          for (int kx = 0; kx < 3; ++kx) {
+            uint8_t* bb = sB + s * kStageB + kx * kBK;
+            const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+            tma_3d(bb, &tmB, &full[s], kk, n0, 0);
+            tma_3d(bb + kB, &tmB, &full[s], kk, n0, 1);
           }
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
         }
       }
     } else if (lane == 0) {
@@ -679,11 +679,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       bool ok = true;
       int t, k0, k1;
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
-        {
-          int t2, a2, b2;
-          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
-        }
-        for (int g = 0; g < 3 * kchunks; ++g) {  // one A slot = one accumulation group
+        for (int g = k0; g < k1; ++g) {  // one A slot = one accumulation group
           const int buf = gg & (NBUF - 1);
           if (gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
           if (!mbar_wait(&full[sa], pa, 2u)) { ok = false; break; }
@@ -721,11 +717,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       bool ok = true;
       int t, k0, k1;
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
-        {
-          int t2, a2, b2;
-          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
-        }
-        for (int g = 0; g < 3 * kchunks; ++g) {  // one stage = one accumulation group
+        for (int g = k0; g < k1; ++g) {  // one stage = one accumulation group
           const int buf = gg & (NBUF - 1);
           if (gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
           if (!mbar_wait(&full[s], ph, 2u)) { ok = false; break; }
@@ -759,11 +751,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       bool ok = true;
       int t, k0, k1;
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
-        {
-          // this CTA's last piece: let the next kernel launch (its CTAs take SMs as ours exit)
-          int t2, a2, b2;
-          if (!piece(i + 1, t2, a2, b2)) pdl_trigger();
-        }
         for (int kb0 = k0; kb0 < k1; kb0 += KPS) {
           const int nk = k1 - kb0 < KPS ? k1 - kb0 : KPS;
           const int buf = gg & (NBUF - 1);
@@ -802,6 +789,14 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
     }
   } else if (warp >= kRed0) {
+    // The next kernel may launch once this CTA's last accumulation has been read out of TMEM:
+    // its CTAs then take SMs as ours exit.  Launched earlier, they would sit on the SMs this
+    // grid leaves free, waiting for it to end, where kernels of other streams (units of other
+    // chains, at other priorities) could run.
+    auto last_piece_trigger = [&](int pi) {
+      int t2, a2, b2;
+      if (warp == kRed0 && lane == 0 && !piece(pi + 1, t2, a2, b2)) pdl_trigger();
+    };
     const int q = warp & 3;  // TMEM lane quarter this warp may read
     const int r = q * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
@@ -847,6 +842,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tc_fence_before();
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
         }
+        last_piece_trigger(pi);
         if (SK && (k0 > 0 || k1 < KB)) {
           // Part of a tile shared with neighbouring CTAs: publish this partial sum (slot 2c for
           // the piece a CTA starts with, 2c + 1 for the one it ends with), count the arrival,
@@ -923,6 +919,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
         ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
         if (!ok) break;
+        last_piece_trigger(pi);
         tc_fence_after();
         __nv_bfloat16* o = fdst ? reinterpret_cast<__nv_bfloat16*>(fdst + c.frame_off) + fbase
                                 : static_cast<__nv_bfloat16*>(args.out) + obase;
@@ -1247,7 +1244,7 @@ int launch_tc(const CUtensorMap& a, const CUtensorMap& w, const TcArgs& args, di
 }  // namespace
 
 int conv_tcp_tile_count(int mode);
-int conv_tcp_sk_first();
+int conv_tcp_sk_twin(int tile);
 int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w, const float* ss,
                     void* out, int ptile, cudaStream_t s, void* ws = nullptr, size_t ws_bytes = 0,
                     const GemmOpts& g = GemmOpts());
@@ -1336,8 +1333,7 @@ int conv_f32tc_launch(const ConvShape& c, const float* in, const float* w_split,
   if (tile < 0) {
     tile = tuned_tile(PP_F32_TC, c);
     // a stream-K choice needs a workspace; without one, the same tile without stream-K
-    const int np = conv_tcp_sk_first();
-    if (tile >= np && tile < 2 * np && (!ws || ws_bytes < conv_sk_workspace_bytes(c))) tile -= np;
+    if (!ws || ws_bytes < conv_sk_workspace_bytes(c)) tile = conv_tcp_sk_twin(tile);
   }
   return conv_tcp_launch(1, c, in, w_split, ss, out, tile, s, ws, ws_bytes);
 }
@@ -1388,11 +1384,17 @@ constexpr size_t p_smem_halo() {
                  : 1024 + (size_t)ST * 2 * 17408 + (size_t)NB * 2 * BN * 128 + 4 * 4096 + (2 * ST + 8 + 2 * NB) * 8 +
                        16;
 }
-// The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots; 0 = unified stages)
+// The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots (0 = unified
+// stages), stream-K).  The stream-K ones cut the accumulation groups of all tiles into one equal
+// range per SM, as the stream-K twins of the plain tiles cut their K blocks; each is listed
+// after its whole-tile twin, kNHaloSK entries back.
 struct HaloVariant {
   int bn, stages, bslots;
+  bool sk;
 };
-constexpr HaloVariant kHalo[] = {{64, 2, 0}, {128, 2, 4}, {64, 3, 5}, {128, 3, 3}};
+constexpr HaloVariant kHalo[] = {{64, 2, 0, false}, {128, 2, 4, false}, {64, 3, 5, false}, {128, 3, 3, false},
+                                 {64, 2, 0, true},  {128, 2, 4, true}};
+constexpr int kNHaloSK = 2;
 constexpr int kNHalo = (int)(sizeof(kHalo) / sizeof(kHalo[0]));
 
 int num_sms() {
@@ -1412,8 +1414,9 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
                               (int)bytes, &attr_set, "persistent conv smem attribute"))
     return st;
   // stream-K: one range per CTA, never an empty one (an empty range would be counted among the
-  // CTAs that share a tile but never arrive), so at most one CTA per K block
-  const long kblocks = (long)args.total * 9 * (args.c.cin / (MODE == 1 ? 32 : 64));
+  // CTAs that share a tile but never arrive), so at most one CTA per K block (per accumulation
+  // group for the halo tiles)
+  const long kblocks = (long)args.total * (HALO ? 3 : 9) * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
   return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>, dim3(grid), dim3(192), bytes, s, a,
@@ -1462,8 +1465,8 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   if (halo && (c.stride != 1 || g.taps != 9 || g.up != 1 || c.cout % halo_bn || co_blk % halo_bn))
     return fail(PP_EINVAL, "persistent conv: the halo tile needs a stride-1 3x3 conv with cout a multiple of %d",
                 halo_bn);
-  const bool sk = mode == 1 && ptile >= n && !halo;
-  if (sk) ptile -= n;
+  const bool sk = mode == 1 && ptile >= n && (!halo || hv.sk);
+  if (sk && !halo) ptile -= n;
   if (!halo && ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
   if (!halo && (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn))
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
@@ -1527,7 +1530,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.tiles_y = halo ? 1 : (c.Ho + t.bh - 1) / t.bh;
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
-  args.fold = halo ? 3 : 2;  // K blocks per TMEM accumulation group (a halo stage is one group)
+  args.fold = halo ? 1 : 2;  // work units per TMEM accumulation group (a halo unit is one group)
   args.taps = g.taps;
   args.up = g.up;
   args.co_blk = co_blk;
@@ -1560,7 +1563,9 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
         case 0: return launch_p<1, 64, false, false, true, 2, 0>(ta, talo, tw, args, s);
         case 1: return launch_p<1, 128, false, false, true, 2, 4>(ta, talo, tw, args, s);
         case 2: return launch_p<1, 64, false, false, true, 3, 5>(ta, talo, tw, args, s);
-        default: return launch_p<1, 128, false, false, true, 3, 3>(ta, talo, tw, args, s);
+        case 3: return launch_p<1, 128, false, false, true, 3, 3>(ta, talo, tw, args, s);
+        case 4: return launch_p<1, 64, false, true, true, 2, 0>(ta, talo, tw, args, s);
+        default: return launch_p<1, 128, false, true, true, 2, 4>(ta, talo, tw, args, s);
       }
     }
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
@@ -1653,7 +1658,18 @@ int conv_rows_launch(const ConvShape& c, const void* in, const void* w, const fl
 }
 
 int conv_tcp_tile_count(int mode) { return mode == 1 ? 2 * kNPF + kNHalo : kNPB; }
-int conv_tcp_sk_first() { return kNPF; }
+// the tile to launch instead of stream-K tile `tile` when there is no workspace (the tile itself
+// if it is not a stream-K one)
+int conv_tcp_sk_twin(int tile) {
+  if (tile >= kNPF && tile < 2 * kNPF) return tile - kNPF;
+  const int h = tile - 2 * kNPF;
+  if (h >= 0 && h < kNHalo && kHalo[h].sk)
+    for (int i = 0; i < kNHalo; ++i)
+      if (!kHalo[i].sk && kHalo[i].bn == kHalo[h].bn && kHalo[i].stages == kHalo[h].stages &&
+          kHalo[i].bslots == kHalo[h].bslots)
+        return 2 * kNPF + i;
+  return tile;
+}
 
 int gemm_tc_launch(int dtype, const ConvShape& c, const GemmOpts& g, const void* in, const void* w,
                    const float* ss, void* out, int tile, cudaStream_t s) {
@@ -1677,6 +1693,11 @@ size_t conv_sk_workspace_bytes(const ConvShape& c) {
     const size_t n = (size_t)((c.Wo + t.bw - 1) / t.bw) * ((c.Ho + t.bh - 1) / t.bh) * c.batch * (c.cout / t.bn);
     if (n > tiles) tiles = n;
   }
+  if (c.stride == 1 && c.cout % 64 == 0) {
+    // halo tiles: 128-pixel runs of the output over the padded width, 64 channels at the narrowest
+    const size_t n = ((size_t)c.Ho * (c.W + 2) + 127) / 128 * c.batch * (c.cout / 64);
+    if (n > tiles) tiles = n;
+  }
   return (size_t)2 * num_sms() * 128 * 128 * sizeof(float) + align_up(tiles * sizeof(unsigned), 256);
 }
 
@@ -1692,7 +1713,8 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
   if (dtype == PP_F32_TC) {
     if (tile < 0 || tile >= 2 * kNPF + kNHalo) return PP_EINVAL;
     const TileP t = tile >= 2 * kNPF ? TileP{1, 128, kHalo[tile - 2 * kNPF].bn} : kTilesPF[tile % kNPF];
-    *bh = t.bh; *bw = t.bw; *bn = t.bn; *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : 4;
+    *bh = t.bh; *bw = t.bw; *bn = t.bn;
+    *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : kHalo[tile - 2 * kNPF].sk ? 5 : 4;
     return PP_OK;
   }
   return PP_EINVAL;
