@@ -1385,16 +1385,14 @@ constexpr size_t p_smem_halo() {
                        16;
 }
 // The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots (0 = unified
-// stages), stream-K).  The stream-K ones cut the accumulation groups of all tiles into one equal
-// range per SM, as the stream-K twins of the plain tiles cut their K blocks; each is listed
-// after its whole-tile twin, kNHaloSK entries back.
+// stages), stream-K).  The stream-K ones (last) cut the accumulation groups of all tiles into
+// one equal range per SM, as the stream-K twins of the plain tiles cut their K blocks.
 struct HaloVariant {
   int bn, stages, bslots;
   bool sk;
 };
 constexpr HaloVariant kHalo[] = {{64, 2, 0, false}, {128, 2, 4, false}, {64, 3, 5, false}, {128, 3, 3, false},
                                  {64, 2, 0, true},  {128, 2, 4, true}};
-constexpr int kNHaloSK = 2;
 constexpr int kNHalo = (int)(sizeof(kHalo) / sizeof(kHalo[0]));
 
 int num_sms() {
