@@ -113,10 +113,10 @@ def _workload(name):
 # were taken on: a changed kernel reports null until it is captured again.
 CONV_TRAFFIC = {
     # per distinct layer shape, one launch each (bench.py --profile-conv LAYER:TILE with the
-    # tuned tile), summed over the step's layers: full-size frame 118.3 + 3 x 28.3 + 28.6 + 5 x 15.4
-    # + 16.5 + 5 x 12.1 MB; 8-frame unit 56.3 + 2 x 14.3 MB
-    "cfg2-fp32": (385.8e6, "2f3bd6668692e09ff7382d6b77d23b9a3b902a53fd5232676afbdcb9164506fe"),
-    "cfg3-bf16": (84.9e6, "2f3bd6668692e09ff7382d6b77d23b9a3b902a53fd5232676afbdcb9164506fe"),
+    # tuned tile), summed over the step's layers: full-size frame 119.1 + 3 x 28.3 + 28.6 + 5 x 15.4
+    # + 16.6 + 5 x 12.1 MB; 8-frame unit 56.4 + 2 x 14.3 MB
+    "cfg2-fp32": (386.9e6, "5e7a5a1e5ac133c24b848aeae39a1dae2fa5eb724765f72d27edad3d69b72b03"),
+    "cfg3-bf16": (85.0e6, "5e7a5a1e5ac133c24b848aeae39a1dae2fa5eb724765f72d27edad3d69b72b03"),
 }
 # the same for the neck and head launches of one step (upsamplings + head); not re-captured on the
 # current conv source, so reported as null
