@@ -707,6 +707,13 @@ def _run_ours(a, rank, world, dist):
                      "peak_nominal_source": None if peak_nominal is None else
                      "bf16 dense %s x 1.1/2.25 (nominal TF32/BF16) / 3" % src,
                      "conv_ms_per_frame": conv_s * 1e3 / n_frames,
+                     "timing": "each layer alone on the GPU: a CUDA graph of 20 launches replayed once under CUDA "
+                               "events on its stream, after the timed region",
+                     # the same FLOPs over the step's device time, which also holds the front end: in
+                     # the timed steps the units of several chains overlap on the GPU, so this can
+                     # exceed the per-layer figure above
+                     "in_step": {"tflops": conv_flops / (el / a.steps) / 1e12,
+                                 "frac": conv_flops / (el / a.steps) / 1e12 / peak},
                      "layers_us": [round(t * 1e6, 2) for t, _ in layers],
                      "layers_tflops": [round(f / t / 1e12, 1) for t, f in layers]},
         "stage_ms_per_step": {k: v for k, v in stages.items() if not k.startswith("_")},
