@@ -880,10 +880,10 @@ def parse_sweep_item(item):
 
 
 # Serving points of the default run: (key, chains, rate x, seconds, mixed, f_d, f_tight).  The
-# 11-chain point is the base load at the paper's rates; the 33-chain points are past the plain
-# per-frame path's saturation (~22k frames/s on this GPU), at the paper's default share of
-# tight-deadline chains (40 %): loose deadlines at 96x (~37k frames/s offered) and deadlines of
-# 0.5 % of the period at 64x (~25k frames/s).
+# 11-chain point is the base load at the paper's rates; the 33-chain points take the paper's
+# default share of tight-deadline chains (40 %): loose deadlines at 96x (~37k frames/s offered,
+# past the plain per-frame path's saturation near 28k frames/s on this GPU) and deadlines of
+# 0.5 % of the period at 64x (~25k frames/s, where the deadlines rather than the load decide).
 SERVING_POINTS = [
     ("config4_11_chains_1x", 11, 1.0, 4.0, False, 1.0, 0.0),
     ("overload_33_chains_96x_fd1_tight0.4", 33, 96.0, 8.0, True, 1.0, 0.4),
