@@ -443,8 +443,21 @@ struct PArgs {
   unsigned* sem;  // stream-K: [total] arrival counters, zero between launches
 };
 
+// Reducer warps of the persistent conv: eight for the BN 64 halo tiles (two per TMEM lane
+// quarter, each owning half of the tile's columns, so that the accumulation groups are drained
+// and the last tile's epilogue is written by two warps per scheduler), four otherwise (where
+// eight 4 KiB transposing buffers would not fit beside the rings).
+template <int MODE, int BN, bool HALO>
+__host__ __device__ constexpr int p_red_warps() {
+  return MODE == 1 && HALO && BN == 64 ? 8 : 4;
+}
+template <int MODE, int BN, bool HALO>
+__host__ __device__ constexpr int p_threads() {
+  return 64 + 32 * p_red_warps<MODE, BN, HALO>();
+}
+
 template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false, int NBS = 0>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(p_threads<MODE, BN, HALO>(), 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
             const __grid_constant__ CUtensorMap tmB, PArgs args) {
   constexpr int BK = MODE == 1 ? 32 : 64;                  // channels per K block (128 B rows)
@@ -469,6 +482,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr int NBUF = 512 / NACC >= 4 ? 4 : 2;
   constexpr uint32_t kCols = NBUF * NACC;
   constexpr int kRed0 = 2;                                 // first reducer warp
+  constexpr int kRW = p_red_warps<MODE, BN, HALO>();       // reducer warps
+  constexpr int kRT = 32 * kRW;                            // reducer threads
+  constexpr int BNW = BN * 4 / kRW;                        // columns of the tile per reducer warp
   extern __shared__ uint8_t smem_raw[];
   __shared__ unsigned s_abort;
   __shared__ unsigned s_arrived;  // stream-K: arrivals at the current shared tile before this CTA
@@ -480,7 +496,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * kStageA;
   uint8_t* sO = sB + kBRegion;                             // epilogue: 4 KiB transposing buffer per reducer warp
-  constexpr uint32_t kStageO = 4u * 4096u;
+  constexpr uint32_t kStageO = (uint32_t)kRW * 4096u;
   uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageO);  // (split rings: the A ring's)
   uint64_t* empty = full + STAGES;
   uint64_t* kdone = empty + STAGES;
@@ -508,7 +524,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(&kdone[i], 1);
-      mbar_init(&kfree[i], 128);
+      mbar_init(&kfree[i], kRT);
     }
     for (int i = 0; i < NB; ++i) {
       mbar_init(&fullB[i], 1);
@@ -530,12 +546,6 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  pdl_wait();     // the previous kernel's outputs are complete and visible
-  for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
-    s_scale[i] = args.ss[i];
-    s_shift[i] = args.ss[args.co_blk + i];
-  }
-  __syncthreads();
 
   auto decode = [&](int t, int& b, int& oy0, int& ox0, int& n0) {
     const int nt = t % args.tiles_n;
@@ -568,9 +578,51 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     return b0 < r_hi && k1 > k0;
   };
 
+  // Weights and folded BN written before the previous kernel started (a release unit's,
+  // packed at creation) are fetched while that kernel drains: the scale/shift table, and for
+  // the halo tiles the weight taps of the first stages (B slots) of this CTA's first piece, so
+  // that only the input rows wait for the dependent-launch release.  npre: stages (unified
+  // halo stages) or B slots (split rings) already loaded that way.
+  int npre = 0;
+  if (c.static_w) {
+    for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
+      s_scale[i] = args.ss[i];
+      s_shift[i] = args.ss[args.co_blk + i];
+    }
+    int t, k0, k1;
+    if (HALO && piece(0, t, k0, k1)) {
+      int b, oy0, ox0, n0;
+      decode(t, b, oy0, ox0, n0);
+      npre = kSplit ? (NB < 3 * (k1 - k0) ? NB : 3 * (k1 - k0)) : (STAGES < k1 - k0 ? STAGES : k1 - k0);
+      if (warp == 0 && lane == 0) {
+        for (int f = 0; f < npre; ++f) {
+          const int gi = k0 + (kSplit ? f / 3 : f);
+          const int ky = gi / kchunks, cc = gi % kchunks;
+          for (int kx = kSplit ? f % 3 : 0; kx < (kSplit ? f % 3 + 1 : 3); ++kx) {
+            uint64_t* bar = kSplit ? &fullB[f] : &full[f];
+            uint8_t* bb = kSplit ? sB + f * kBK : sB + f * kStageB + kx * kBK;
+            if (kSplit) mbar_expect_tx(bar, kBK);
+            else if (kx == 0) mbar_expect_tx(bar, 2u * kHaloRow + 3u * kBK);
+            const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+            tma_3d(bb, &tmB, bar, kk, n0, 0);
+            tma_3d(bb + kB, &tmB, bar, kk, n0, 1);
+          }
+        }
+      }
+    }
+  }
+  pdl_wait();     // the previous kernel's outputs are complete and visible
+  if (!c.static_w) {
+    for (int i = threadIdx.x; i < args.co_blk; i += blockDim.x) {
+      s_scale[i] = args.ss[i];
+      s_shift[i] = args.ss[args.co_blk + i];
+    }
+  }
+  __syncthreads();
+
   if (warp == 0) {
     if (kSplit && lane == 0) {
-      int sa = 0, sb = 0;
+      int sa = 0, sb = 0, fb = 0;  // fb: B fills so far
       uint32_t pa = 0, pb = 0;
       bool ok = true;
       int t, k0, k1;
@@ -588,18 +640,20 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tma_2d(a + kHaloA, &tmAlo, &full[sa], cc * BK, pix);
           if (++sa == STAGES) { sa = 0; pa ^= 1u; }
           for (int kx = 0; kx < 3; ++kx) {
-            if (!mbar_wait(&emptyB[sb], pb ^ 1u, 1u)) { ok = false; break; }
-            mbar_expect_tx(&fullB[sb], kBK);
-            uint8_t* bb = sB + sb * kBK;
-            const int kk = (ky * 3 + kx) * c.cin + cc * BK;
-            tma_3d(bb, &tmB, &fullB[sb], kk, n0, 0);
-            tma_3d(bb + kB, &tmB, &fullB[sb], kk, n0, 1);
+            if (fb++ >= npre) {  // (the first npre were loaded before the dependent-launch wait)
+              if (!mbar_wait(&emptyB[sb], pb ^ 1u, 1u)) { ok = false; break; }
+              mbar_expect_tx(&fullB[sb], kBK);
+              uint8_t* bb = sB + sb * kBK;
+              const int kk = (ky * 3 + kx) * c.cin + cc * BK;
+              tma_3d(bb, &tmB, &fullB[sb], kk, n0, 0);
+              tma_3d(bb + kB, &tmB, &fullB[sb], kk, n0, 1);
+            }
             if (++sb == NB) { sb = 0; pb ^= 1u; }
           }
         }
       }
     } else if (HALO && lane == 0) {
-      int s = 0;
+      int s = 0, fs = 0;  // fs: stage fills so far
       uint32_t ph = 0;
       bool ok = true;
       int t, k0, k1;
@@ -608,14 +662,16 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         decode(t, b, oy0, ox0, n0);
         for (int gi = k0; gi < k1 && ok; ++gi) {
           const int ky = gi / kchunks, cc = gi % kchunks;
+          // the first npre stages have their weights (and the byte count) in already
+          const bool pre = fs++ < npre;
           if (!mbar_wait(&empty[s], ph ^ 1u, 1u)) { ok = false; break; }
-          mbar_expect_tx(&full[s], 2u * kHaloRow + 3u * kBK);
+          if (!pre) mbar_expect_tx(&full[s], 2u * kHaloRow + 3u * kBK);
           uint8_t* a = sA + s * kStageA;
           // flattened padded input pixels pix .. pix + 129 (ox0: the tile's first output pixel)
           const int pix = (b * (c.H + 2) + ky) * (c.W + 2) + ox0;
           tma_2d(a, &tmA, &full[s], cc * BK, pix);
           tma_2d(a + kHaloA, &tmAlo, &full[s], cc * BK, pix);
-          for (int kx = 0; kx < 3; ++kx) {
+          for (int kx = 0; kx < 3 && !pre; ++kx) {
             uint8_t* bb = sB + s * kStageB + kx * kBK;
             const int kk = (ky * 3 + kx) * c.cin + cc * BK;
             tma_3d(bb, &tmB, &full[s], kk, n0, 0);
@@ -799,6 +855,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     };
     const int q = warp & 3;  // TMEM lane quarter this warp may read
     const int r = q * 32 + lane;
+    const int h0 = ((warp - kRed0) >> 2) * BNW;  // first of this warp's BNW columns of the tile
+    const bool lead = threadIdx.x == kRed0 * 32;  // one reducer thread for the CTA's arrivals
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     int gg = 0;
     bool ok = true;
@@ -821,9 +879,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       char* fdst = c.frame_dst ? c.frame_dst[b] : nullptr;
       const size_t fbase = ((size_t)(opy + 1) * (args.Wout + 2) + opx + 1) * args.out_c + args.out_coff + nb;
       if (MODE == 1) {
-        float acc[BN];
+        float acc[BNW];
 #pragma unroll
-        for (int i = 0; i < BN; ++i) acc[i] = 0.f;
+        for (int i = 0; i < BNW; ++i) acc[i] = 0.f;
         for (int g = 0; g < gpt; ++g, ++gg) {
           const int buf = gg & (NBUF - 1);
           ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
@@ -831,10 +889,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
-          for (int j = 0; j < BN / 32; ++j) {
+          for (int j = 0; j < BNW / 32; ++j) {
             uint32_t v[32], w[32];
-            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + j * 32), v);
-            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + BN + j * 32), w);
+            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + h0 + j * 32), v);
+            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + BN + h0 + j * 32), w);
             tmem_wait();
 #pragma unroll
             for (int i = 0; i < 32; ++i) acc[j * 32 + i] += __uint_as_float(v[i]) + __uint_as_float(w[i]);
@@ -851,15 +909,15 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           // float4 column are 512 contiguous bytes
           const long tb = (long)t * KB;
           const int slot = 2 * blockIdx.x + (r_lo < tb ? 1 : 0);
-          float4* mine = reinterpret_cast<float4*>(args.ws) + (size_t)slot * (BN / 4) * 128 + r;
+          float4* mine = reinterpret_cast<float4*>(args.ws) + ((size_t)slot * (BN / 4) + h0 / 4) * 128 + r;
 #pragma unroll
-          for (int i = 0; i < BN / 4; ++i)
+          for (int i = 0; i < BNW / 4; ++i)
             mine[i * 128] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
           __threadfence();
-          ok = bar_and(1, 128, ok);
+          ok = bar_and(1, kRT, ok);
           if (!ok) break;
-          if (r == 0) s_arrived = atomicAdd(&args.sem[t], 1u);
-          bar_and(1, 128, true);
+          if (lead) s_arrived = atomicAdd(&args.sem[t], 1u);
+          bar_and(1, kRT, true);
           auto cta_of = [&](long idx) -> int {
             long cc = idx * gridDim.x / W;
             while (cc > 0 && cta_start(cc) > idx) --cc;
@@ -873,9 +931,9 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           // per pass so that the BN/4 loads of a pass are all in flight together
           for (int cc = cf; cc <= cl; ++cc) {
             const int sl = 2 * cc + (cta_start(cc) < tb ? 1 : 0);
-            const float4* src = reinterpret_cast<const float4*>(args.ws) + (size_t)sl * (BN / 4) * 128 + r;
+            const float4* src = reinterpret_cast<const float4*>(args.ws) + ((size_t)sl * (BN / 4) + h0 / 4) * 128 + r;
 #pragma unroll
-            for (int i = 0; i < BN / 4; ++i) {
+            for (int i = 0; i < BNW / 4; ++i) {
               const float4 p = __ldcg(src + i * 128);
               if (cc == cf) {
                 acc[4 * i] = p.x; acc[4 * i + 1] = p.y; acc[4 * i + 2] = p.z; acc[4 * i + 3] = p.w;
@@ -884,21 +942,21 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               }
             }
           }
-          if (r == 0) args.sem[t] = 0u;  // counters are zero again for the next launch
+          if (lead) args.sem[t] = 0u;  // counters are zero again for the next launch
         }
         {
           // value plane and remainder plane (split FP32, the next layer's A operand), 32
           // channels (128 B per pixel) at a time through the warp's transposing buffer
           if (!ok) break;
-          uint4* wbuf = reinterpret_cast<uint4*>(sO + q * 4096);
-          float* orow = fdst ? reinterpret_cast<float*>(fdst + c.frame_off) + fbase
-                             : static_cast<float*>(args.out) + obase;
+          uint4* wbuf = reinterpret_cast<uint4*>(sO + (warp - kRed0) * 4096);
+          float* orow = (fdst ? reinterpret_cast<float*>(fdst + c.frame_off) + fbase
+                              : static_cast<float*>(args.out) + obase) + h0;
 #pragma unroll
-          for (int k = 0; k < BN / 32; ++k) {
+          for (int k = 0; k < BNW / 32; ++k) {
             uint4 hv[8], lv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int n = nb + 32 * k + 4 * j;
+              const int n = nb + h0 + 32 * k + 4 * j;
               const float* a = acc + 32 * k + 4 * j;
               float4 u;
               u.x = fmaxf(fmaf(a[0], s_scale[n + 0], s_shift[n + 0]), lo_clamp);
@@ -1380,9 +1438,10 @@ constexpr size_t p_smem() {
 // and a B ring of NB slots (one tap, value and remainder), with their own full/empty barriers
 template <int BN, int ST, int NB>
 constexpr size_t p_smem_halo() {
-  return NB == 0 ? 1024 + (size_t)ST * (2 * 17408 + 3 * 2 * BN * 128) + 4 * 4096 + (2 * ST + 8) * 8 + 16
-                 : 1024 + (size_t)ST * 2 * 17408 + (size_t)NB * 2 * BN * 128 + 4 * 4096 + (2 * ST + 8 + 2 * NB) * 8 +
-                       16;
+  return NB == 0 ? 1024 + (size_t)ST * (2 * 17408 + 3 * 2 * BN * 128) + p_red_warps<1, BN, true>() * 4096 +
+                       (2 * ST + 8) * 8 + 16
+                 : 1024 + (size_t)ST * 2 * 17408 + (size_t)NB * 2 * BN * 128 + p_red_warps<1, BN, true>() * 4096 +
+                       (2 * ST + 8 + 2 * NB) * 8 + 16;
 }
 // The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots (0 = unified
 // stages), stream-K).  The stream-K ones (last) cut the accumulation groups of all tiles into
@@ -1417,7 +1476,8 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * (HALO ? 3 : 9) * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>, dim3(grid), dim3(192), bytes, s, a,
+  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>, dim3(grid),
+                                dim3(p_threads<MODE, BN, HALO>()), bytes, s, a,
                                 alo, w, args),
                      "persistent conv launch");
 }

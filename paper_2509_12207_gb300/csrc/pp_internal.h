@@ -163,8 +163,9 @@ struct ConvShape {
   // split FP32 (PP_F32_TC): elements between the value and remainder planes of the input and
   // the output; 0 = this batch's plane size (planes packed for exactly `batch` frames)
   size_t in_plane = 0, out_plane = 0;
-  // the weights were written before the previous kernel in the stream started (a release
-  // unit's packed weights): a kernel may load them before its dependent-launch wait
+  // the weights and the folded BN scale/shift were written before the previous kernel in the
+  // stream started (a release unit's, packed at creation): a kernel may load them before its
+  // dependent-launch wait
   bool static_w = false;
   // a release unit's last layer: frame b's output goes to frame_dst[b] + frame_off (its result
   // slot, a padded [Ho+2][Wo+2][cout] map whose border stays zero) when that entry is non-NULL,
