@@ -17,10 +17,14 @@ __device__ __forceinline__ const float4* frame_src(const float4* points, const f
   return srcs ? srcs[b] : points + (size_t)b * cap;
 }
 
-// Ascending bitonic sort of one int per lane across a warp.
-__device__ __forceinline__ int warp_sort(int v, int lane) {
+// Ascending bitonic sort of one int per lane across a warp.  With `upto` < 32 (warp-uniform)
+// the network stops after its merges of width `upto` (rounded up to a power of two): lanes
+// 0..upto-1 are then sorted among themselves, which is the whole sort when every lane from
+// `upto` on holds INT_MAX (a pillar of at most `upto` points).
+__device__ __forceinline__ int warp_sort(int v, int lane, int upto = 32) {
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
+    if (k >= 2 * upto && k > 2) break;  // blocks of k / 2 >= upto lanes are sorted already
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       const int o = __shfl_xor_sync(kFullMask, v, j);
@@ -45,7 +49,7 @@ __device__ __forceinline__ int warp_bitonic_merge(int v, int lane) {
 // count): a warp sort of the first 32 (`first`: lane's entry of them, already loaded), then a
 // bitonic merge with each further sorted chunk.
 __device__ __forceinline__ int lowest_32_from(int first, const int* seg, int count, int lane) {
-  int best = warp_sort(first, lane);
+  int best = warp_sort(first, lane, count);
   for (int k = 32; k < count; k += 32) {
     int v = warp_sort(k + lane < count ? seg[k + lane] : INT_MAX, lane);
     v = __shfl_sync(kFullMask, v, 31 - lane);          // reversed: best ++ v is bitonic
