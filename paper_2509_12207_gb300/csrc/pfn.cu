@@ -1,10 +1,12 @@
 // PointNet (PFN) over pillars and the BEV scatter, batched over frames (PointPillars front end
 // of the paper's 3D-perception chains, Section 6 / Table 4).
 //
-// pfn_fused: one warp per pillar.  Lane j builds the 9 features of point j into shared memory
-// (pillar mean by warp shuffles), then lane c owns channels c and c+32 and runs
-// Linear(9->64) + folded BN + ReLU over the valid points, keeping a running max in registers.
-// The 9x64 weights and the BN scale/shift are staged in shared memory once per block.
+// pfn_fused: one warp per pillar.  The pillar's means come from a warp butterfly over lane j =
+// point j; lane c owns channels c and c+32 and runs Linear(9->64) + folded BN + ReLU over the
+// valid points (each point broadcast by shuffles), keeping a running max in registers.  The
+// linear layer is evaluated regrouped (dev::PfnLane): the five offset features are affine in
+// the point with per-pillar constants, so a point costs four FMAs per channel.  The regrouped
+// weights are staged in shared memory once per block and held in registers by each lane.
 // pfn_select_fused (a release unit's path): the same, with the voxeliser's point selection
 // done by the warp itself (sort of the pillar's point indices, point loaded into lane j).
 //
@@ -47,17 +49,13 @@ __device__ __forceinline__ void canvas_put(size_t pix, int chunks, float m0, flo
   }
 }
 
-// Stages the 9x64 weights (transposed) and the folded BN in shared memory.
-__device__ __forceinline__ void pfn_stage_weights(const float* pfn_w, const float* ss, float (*w_s)[64], float* sc_s,
-                                                  float* sh_s) {
-  for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
-    const int c = i / 9, k = i % 9;
-    w_s[k][c] = pfn_w[i];
-  }
-  if (threadIdx.x < 64) {
-    sc_s[threadIdx.x] = ss[threadIdx.x];
-    sh_s[threadIdx.x] = ss[64 + threadIdx.x];
-  }
+// Stages the regrouped PointNet weights (dev::pfn_combine, one row per channel) and the table
+// of 1 / n for n = 1..32 in shared memory; each lane then keeps its two channels' weights in
+// registers (dev::pfn_lane).
+__device__ __forceinline__ void pfn_stage_weights(const float* pfn_w, const float* ss,
+                                                  float (*comb)[dev::kPfnComb], float* inv_s) {
+  if (threadIdx.x < 64) dev::pfn_combine(pfn_w, ss, threadIdx.x, comb[threadIdx.x]);
+  if (threadIdx.x < 33) inv_s[threadIdx.x] = threadIdx.x ? 1.f / (float)threadIdx.x : 0.f;
   __syncthreads();
 }
 
@@ -69,10 +67,10 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
                                                  const float* __restrict__ ss,
                                                  float* __restrict__ feat) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
-  __shared__ float w_s[9][64];          // transposed: w_s[k][c] = W[c][k]
-  __shared__ float sc_s[64], sh_s[64];
-  __shared__ float f_s[kWarps][32][10];  // features per point (+1 pad)
-  pfn_stage_weights(pfn_w, ss, w_s, sc_s, sh_s);
+  __shared__ float comb[64][dev::kPfnComb];
+  __shared__ float inv_s[33];
+  pfn_stage_weights(pfn_w, ss, comb, inv_s);
+  const dev::PfnLane L = dev::pfn_lane(comb, threadIdx.x & 31);
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = num_pillars[b];
@@ -81,7 +79,8 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
   for (int p = blockIdx.x * kWarps + wid; p < np; p += gridDim.x * kWarps) {
     const size_t q = (size_t)b * g.P + p;
     float m0, m1;
-    dev::pfn_pillar(g, pts[q * 32 + lane], npts[q], coord[q], lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
+    const int n = npts[q];
+    dev::pfn_pillar(g, pts[q * 32 + lane], n, coord[q], lane, L, inv_s[n], m0, m1);
     feat[q * 64 + lane] = m0;
     feat[q * 64 + lane + 32] = m1;
   }
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
 // Point selection fused with PointNet (the release unit's path): each warp sorts its pillar's
 // point indices (the 32 lowest, as vox_select does), loads lane j's point straight into a
 // register and runs the pillar's PointNet, so the gathered points never go through memory.
-__global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const float4* __restrict__ points,
+__global__ void __launch_bounds__(256, 4) pfn_select_fused(Geom g, int cap, const float4* __restrict__ points,
                                                         const float4* const* __restrict__ srcs,
                                                         const int* __restrict__ csr,
                                                         const int* __restrict__ pillar_start,
@@ -104,10 +103,10 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
                                                         uint4* __restrict__ canvas, uint4* __restrict__ lo,
                                                         unsigned* __restrict__ cnt_zero) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
-  __shared__ float w_s[9][64];
-  __shared__ float sc_s[64], sh_s[64];
-  __shared__ float f_s[kWarps][32][10];
-  pfn_stage_weights(pfn_w, ss, w_s, sc_s, sh_s);
+  __shared__ float comb[64][dev::kPfnComb];
+  __shared__ float inv_s[33];
+  pfn_stage_weights(pfn_w, ss, comb, inv_s);
+  const dev::PfnLane L = dev::pfn_lane(comb, threadIdx.x & 31);
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = num_pillars[b];
@@ -116,47 +115,61 @@ __global__ void __launch_bounds__(256) pfn_select_fused(Geom g, int cap, const f
   const float4* src = dev::frame_src(points, srcs, b, cap);
   const int* csr_b = csr + (size_t)b * cap;
   const int stride = gridDim.x * kWarps;
-  // Software pipeline over the warp's pillars: a pillar's metadata is loaded one pillar ahead
-  // and its first 32 point indices while the previous pillar's points are in flight, so each
-  // pillar waits on one memory round trip (its points) instead of three.
+  // Software pipeline over the warp's pillars p, p + stride, ...: in the iteration of pillar p
+  // the warp loads the metadata of pillar p + 3 and the first 32 point indices of pillar p + 2,
+  // sorts the indices of pillar p + 1 and starts its point gather, then runs pillar p's
+  // PointNet on the points gathered one iteration earlier, so every load has a whole
+  // iteration's work to arrive in.
+  auto meta = [&](int pp, int& cnt, int& st, int& cl) {
+    cnt = 0; st = 0; cl = 0;
+    if (pp < np) {
+      const size_t q = (size_t)b * g.P + pp;
+      cnt = pillar_cnt[q];
+      st = pillar_start[q];
+      cl = coord[q];
+    }
+  };
+  auto firsts = [&](int pp, int cnt, int st) { return pp < np && lane < cnt ? csr_b[st + lane] : INT_MAX; };
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   int p = blockIdx.x * kWarps + wid;
-  int count = 0, start = 0, cell = 0, first = INT_MAX;
+  int c0, s0, l0, c1, s1, l1, c2, s2, l2;  // metadata of pillars p, p + stride, p + 2 stride
+  meta(p, c0, s0, l0);
+  meta(p + stride, c1, s1, l1);
+  meta(p + 2 * stride, c2, s2, l2);
+  int f1 = firsts(p + stride, c1, s1);
+  float4 v0 = zero;
   if (p < np) {
-    const size_t q = (size_t)b * g.P + p;
-    count = pillar_cnt[q];
-    start = pillar_start[q];
-    cell = coord[q];
-    first = lane < count ? csr_b[start + lane] : INT_MAX;
+    const int best = dev::lowest_32_from(firsts(p, c0, s0), csr_b + s0, c0, lane);
+    if (lane < c0) v0 = src[best];
   }
   for (; p < np; p += stride) {
     const size_t q = (size_t)b * g.P + p;
-    const int pn = p + stride;  // warp-uniform
-    int count_n = 0, start_n = 0, cell_n = 0;
-    if (pn < np) {
-      const size_t qn = (size_t)b * g.P + pn;
-      count_n = pillar_cnt[qn];
-      start_n = pillar_start[qn];
-      cell_n = coord[qn];
+    int c3, s3, l3;
+    meta(p + 3 * stride, c3, s3, l3);
+    const int f2 = firsts(p + 2 * stride, c2, s2);
+    float4 v1 = zero;
+    if (p + stride < np) {  // warp-uniform
+      const int best = dev::lowest_32_from(f1, csr_b + s1, c1, lane);
+      if (lane < c1) v1 = src[best];
     }
-    const int best = dev::lowest_32_from(first, csr_b + start, count, lane);
-    const float4 v = lane < count ? src[best] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int first_n = pn < np && lane < count_n ? csr_b[start_n + lane] : INT_MAX;
     float m0, m1;
-    dev::pfn_pillar(g, v, count < 32 ? count : 32, cell, lane, f_s[wid], w_s, sc_s, sh_s, m0, m1);
+    const int n0 = c0 < 32 ? c0 : 32;
+    dev::pfn_pillar(g, v0, n0, l0, lane, L, inv_s[n0], m0, m1);
     if (feat) {
       feat[q * 64 + lane] = m0;
       feat[q * 64 + lane + 32] = m1;
     }
     if (canvas) {
-      canvas_put(dev::canvas_pixel(g, b, cell), chunks, m0, m1, lane, canvas, lo);
-      if (lane == 0) drawn[q] = cell;
+      canvas_put(dev::canvas_pixel(g, b, l0), chunks, m0, m1, lane, canvas, lo);
+      if (lane == 0) drawn[q] = l0;
     }
     // a release unit's count array: the kept cell's entry (its bucket lookup) back to zero
-    if (cnt_zero && lane == 0) cnt_zero[(size_t)b * g.G + cell] = 0u;
-    count = count_n;
-    start = start_n;
-    cell = cell_n;
-    first = first_n;
+    if (cnt_zero && lane == 0) cnt_zero[(size_t)b * g.G + l0] = 0u;
+    c0 = c1; s0 = s1; l0 = l1;
+    c1 = c2; s1 = s2; l1 = l2;
+    c2 = c3; s2 = s3; l2 = l3;
+    f1 = f2;
+    v0 = v1;
   }
 }
 

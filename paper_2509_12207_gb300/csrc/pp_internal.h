@@ -85,7 +85,10 @@ struct VoxWork {
   int* csr;          // [B][cap] point indices grouped by kept pillar
   int* pillar_start; // [B][P]
   int* pillar_cnt;   // [B][P]
+  int2* tile_sums;   // [B][ntiles] (occupied cells, points) per tile of cells
+  int ntiles;
 };
+constexpr int kVoxTile = 2048;        // cells per scan tile (256 threads x 8)
 size_t vox_workspace_bytes(const Geom& g, int batch, int cap);
 VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap);
 // srcs: optional device table of per-frame point pointers (frame b reads srcs[b][0..n));

@@ -4,16 +4,16 @@
 // stage, made deterministic: pillars are the occupied cells in ascending cell order (at most
 // P), and each keeps its 32 lowest-index points in ascending index order.
 //
-// Three launches per batch (gridDim.y = frame):
+// Five launches per batch, gridDim.y = frame:
 //   1. vox_cell_count   cell per point; warp-aggregated atomic count per cell, which also hands
 //                       each point an arrival slot inside its cell (order arbitrary)
-//   2. vox_rank         one thread-block cluster per frame: exclusive scans over cells -> pillar
-//                       id (rank of occupied cell, kept if < P), pillar's first point offset;
-//                       coord / npts / num_pillars; then point i -> csr[pillar_start + slot]
-//                       (points grouped by kept pillar)
-//   3. vox_select       one warp per pillar: the 32 smallest point indices of its group, sorted
+//   2. vox_tile_sums    per tile of 2048 cells: (occupied cells, points)
+//   3. vox_scan         exclusive scans over cells -> pillar id (rank of occupied cell, kept if
+//                       < P), pillar's first point offset; writes coord / npts / num_pillars
+//   4. vox_bucket       point i -> csr[pillar_start + slot]: points grouped by kept pillar
+//   5. vox_select       one warp per pillar: the 32 smallest point indices of its group, sorted
 //                       by warp bitonic sort/merge, gathered into pts (zero padded)
-// A release unit stops after step 2: its PointNet kernel does step 3 itself (pfn.cu,
+// A release unit stops after step 4: its PointNet kernel does step 5 itself (pfn.cu,
 // pfn_select_fused), so the gathered points stay in registers.
 // Nothing depends on the order in which atomics land, so the output is bit-identical across
 // runs.  The cell index follows the binary32 contract of pp.h (__fsub_rn / __fdiv_rn, floorf).
@@ -38,12 +38,6 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
 // Points per thread per pass of the point kernels: their loads (and atomics) are issued
 // together so that one memory round trip covers several points.
 constexpr int kVoxU = 4;
-
-// The rank kernel: one cluster of kRankCluster CTAs (the portable maximum) per frame,
-// kRankThreads threads per CTA.
-constexpr int kRankCluster = 8;
-constexpr int kRankThreads = 1024;
-constexpr int kRankWarps = kRankThreads / 32;
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
@@ -99,7 +93,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
     // their number to the cell's count; the old count is the group's first arrival slot.  A
     // lane's peers (the lanes holding its cell) come from one ballot per bit of the cell index:
     // the lanes that agree with it on every bit.  That is the set __match_any_sync returns, at
-    // a fraction of its cost when the 32 cells are mostly distinct.
+    // a lower cost when the 32 cells are mostly distinct.
     unsigned peers[kVoxU], base[kVoxU];
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) {
@@ -126,66 +120,73 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   }
 }
 
-// Thread-block cluster helpers: a barrier over all threads of the cluster whose arrive has
-// release and whose wait has acquire semantics at cluster scope (every global and shared write
-// of the cluster before it is visible to every thread of the cluster after it), and a load of a
-// 32-bit word from the shared memory of CTA `rank` of the cluster.
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ int cluster_ld_s32(const int* local, unsigned rank) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
-  unsigned remote;
-  int v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(a), "r"(rank));
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(remote) : "memory");
-  return v;
-}
-
-// Pillar ranks and point buckets of one frame per thread-block cluster of kRankCluster CTAs
-// (blockIdx.x = the CTA's rank in the cluster, blockIdx.y = frame), kRankThreads threads each.
-// CTA r owns the cells [r S, (r + 1) S) (S = kRankWarps x rows x 32) and warp w of it the
-// `rows` x 32 consecutive cells from r S + 32 rows w, lane l taking cell 32 i + l of row i, so
-// every count load, count store and pillar-id store of a row is one coalesced 128-byte line.
-//   1. each CTA totals (occupied cells, points) over its cells and publishes them in shared
-//      memory; cluster barrier;
-//   2. a CTA's prefix is the sum of the totals of the CTAs before it (read over distributed
-//      shared memory), a warp's adds the earlier warps' totals; a warp scan along each row then
-//      gives every cell its rank (pillar id, kept if < P) and its first point offset: the
-//      pillar's coord / npts / start / count, pillar_of_cell, num_pillars (last CTA); in a
-//      release unit (cnt_starts) the count becomes the bucket pass's lookup -- a kept cell's
-//      first point offset + 1, zero for a cell the pillar cap dropped (the PointNet pass zeroes
-//      the kept cells' entries for the next launch); cluster barrier;
-//   3. the cluster's threads walk the frame's points: point i of a kept pillar goes to
-//      csr[start + slot], and, in a release unit, the cells drawn for the slot's previous frame
-//      that hold no kept pillar now are zeroed on the canvas (the cells that do hold one are
-//      rewritten by the PointNet pass that follows).
-// Every thread of the cluster passes both barriers (no early exit), and no CTA touches another
-// CTA's shared memory after the second, so none exits while a peer may still read it.
-__global__ void __cluster_dims__(kRankCluster, 1, 1) __launch_bounds__(kRankThreads)
-vox_rank(Geom g, int cap, int rows, const int* __restrict__ n_points, const int* __restrict__ cell,
-         const int* __restrict__ slot, unsigned* __restrict__ cnt, int* __restrict__ pillar_of_cell,
-         int* __restrict__ coord, int* __restrict__ npts, int* __restrict__ pillar_start,
-         int* __restrict__ pillar_cnt, int* __restrict__ num_pillars, int* __restrict__ csr,
-         int cnt_starts, int chunks, const int* __restrict__ drawn, const int* __restrict__ drawn_num,
-         uint4* __restrict__ canvas, uint4* __restrict__ lo) {
-  __shared__ int2 warp_tot[kRankWarps];
-  __shared__ int cta_occ, cta_pts;
-  __shared__ int2 pre_s;
+// Sums of (occupied, points) over one tile of kVoxTile cells; 256 threads.
+__global__ void vox_tile_sums(Geom g, const unsigned* __restrict__ cnt, int2* __restrict__ sums,
+                              int ntiles) {
   pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
   const int b = blockIdx.y;
-  const unsigned r = blockIdx.x;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned* c = cnt + (size_t)b * g.G;
-  const long long wbase = ((long long)r * kRankWarps + wid) * rows * 32;
-  // 1. totals
-  int2 tot = make_int2(0, 0);
-#pragma unroll 4
-  for (int i = 0; i < rows; ++i) {
-    const long long k = wbase + 32 * i + lane;
+  const unsigned* c = cnt + (size_t)b * g.G;
+  const int base = blockIdx.x * kVoxTile;
+  int occ = 0, pts = 0;
+  for (int j = threadIdx.x; j < kVoxTile; j += blockDim.x) {
+    const int k = base + j;
     const unsigned v = k < g.G ? c[k] : 0u;
-    tot.x += v != 0u;
-    tot.y += (int)v;
+    occ += v != 0u;
+    pts += (int)v;
+  }
+  for (int o = 16; o; o >>= 1) {
+    occ += __shfl_xor_sync(kFull, occ, o);
+    pts += __shfl_xor_sync(kFull, pts, o);
+  }
+  __shared__ int2 red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_int2(occ, pts);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int2 t = make_int2(0, 0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t.x += red[w].x; t.y += red[w].y; }
+    sums[(size_t)b * ntiles + blockIdx.x] = t;
+  }
+}
+
+// Pillar ranks over one tile of kVoxTile cells, 256 threads: warp w owns the 256 consecutive
+// cells from base + 256 w as 8 rows of 32 (lane l takes cell 32 i + l of row i), so every load
+// and store of a row is one coalesced 128-byte line.  A cell's rank (pillar id, kept if < P) is
+// the number of occupied cells before it in the frame and its first point offset the number of
+// points before it: the preceding tiles' sums, plus the preceding warps' totals in this tile,
+// plus a warp scan along the rows.
+__global__ void __launch_bounds__(256) vox_scan(Geom g, const unsigned* __restrict__ cnt,
+                                                const int2* __restrict__ sums, int ntiles,
+                                                int* __restrict__ pillar_of_cell,
+                                                int* __restrict__ coord, int* __restrict__ npts,
+                                                int* __restrict__ pillar_start,
+                                                int* __restrict__ pillar_cnt,
+                                                int* __restrict__ num_pillars,
+                                                unsigned* __restrict__ cnt_starts) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  const int b = blockIdx.y;
+  const unsigned* c = cnt + (size_t)b * g.G;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ int2 pre_red[8], warp_tot[8];
+  // prefix of the preceding tiles' sums
+  int2 pre = make_int2(0, 0);
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) {
+    const int2 s = sums[(size_t)b * ntiles + t];
+    pre.x += s.x; pre.y += s.y;
+  }
+  for (int o = 16; o; o >>= 1) {
+    pre.x += __shfl_xor_sync(kFull, pre.x, o);
+    pre.y += __shfl_xor_sync(kFull, pre.y, o);
+  }
+  if (lane == 0) pre_red[wid] = pre;
+  const int wbase = blockIdx.x * kVoxTile + wid * 256;
+  unsigned v[8];
+  int2 tot = make_int2(0, 0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = wbase + 32 * i + lane;
+    v[i] = k < g.G ? c[k] : 0u;
+    tot.x += v[i] != 0u;
+    tot.y += (int)v[i];
   }
   for (int o = 16; o; o >>= 1) {
     tot.x += __shfl_xor_sync(kFull, tot.x, o);
@@ -193,33 +194,18 @@ vox_rank(Geom g, int cap, int rows, const int* __restrict__ n_points, const int*
   }
   if (lane == 0) warp_tot[wid] = tot;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int2 t = make_int2(0, 0);
-    for (int w = 0; w < kRankWarps; ++w) { t.x += warp_tot[w].x; t.y += warp_tot[w].y; }
-    cta_occ = t.x;
-    cta_pts = t.y;
+  int2 before = make_int2(0, 0), tile = make_int2(0, 0);
+  pre = make_int2(0, 0);
+  for (int w = 0; w < 8; ++w) {
+    pre.x += pre_red[w].x; pre.y += pre_red[w].y;
+    tile.x += warp_tot[w].x; tile.y += warp_tot[w].y;
+    if (w < wid) { before.x += warp_tot[w].x; before.y += warp_tot[w].y; }
   }
-  cluster_sync_all();
-  // 2. ranks
-  if (wid == 0) {
-    int2 pre = make_int2(0, 0);
-    if ((unsigned)lane < r) {
-      pre.x = cluster_ld_s32(&cta_occ, (unsigned)lane);
-      pre.y = cluster_ld_s32(&cta_pts, (unsigned)lane);
-    }
-    for (int o = 16; o; o >>= 1) {
-      pre.x += __shfl_xor_sync(kFull, pre.x, o);
-      pre.y += __shfl_xor_sync(kFull, pre.y, o);
-    }
-    if (lane == 0) pre_s = pre;
-  }
-  __syncthreads();
-  int rank = pre_s.x, start = pre_s.y;
-  for (int w = 0; w < wid; ++w) { rank += warp_tot[w].x; start += warp_tot[w].y; }
-  for (int i = 0; i < rows; ++i) {
-    const long long k = wbase + 32 * i + lane;
-    const unsigned v = k < g.G ? c[k] : 0u;
-    const int occ = v != 0u ? 1 : 0, pts = (int)v;
+  int rank = pre.x + before.x, start = pre.y + before.y;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = wbase + 32 * i + lane;
+    const int occ = v[i] != 0u ? 1 : 0, pts = (int)v[i];
     int io = occ, ip = pts;  // inclusive scan along the row
     for (int o = 1; o < 32; o <<= 1) {
       const int a = __shfl_up_sync(kFull, io, o);
@@ -227,36 +213,50 @@ vox_rank(Geom g, int cap, int rows, const int* __restrict__ n_points, const int*
       if (lane >= o) { io += a; ip += d; }
     }
     if (k < g.G) {
-      const int rk = rank + io - occ;
+      const int r = rank + io - occ;
       int pid = -1;
-      if (occ && rk < g.P) {
-        pid = rk;
-        const size_t q = (size_t)b * g.P + rk;
-        coord[q] = (int)k;
+      if (occ && r < g.P) {
+        pid = r;
+        const size_t q = (size_t)b * g.P + r;
+        coord[q] = k;
         npts[q] = pts < 32 ? pts : 32;
         pillar_start[q] = start + ip - pts;
         pillar_cnt[q] = pts;
       }
       pillar_of_cell[(size_t)b * g.G + k] = pid;
-      if (cnt_starts && occ) c[k] = pid >= 0 ? (unsigned)(start + ip - pts) + 1u : 0u;
+      // a release unit: the count becomes the bucket pass's lookup -- a kept cell's first point
+      // offset + 1, zero for a cell the pillar cap dropped (this CTA is the count's last
+      // reader; the PointNet pass zeroes the kept cells' entries for the next launch)
+      if (cnt_starts && occ) cnt_starts[(size_t)b * g.G + k] = pid >= 0 ? (unsigned)(start + ip - pts) + 1u : 0u;
     }
     rank += __shfl_sync(kFull, io, 31);
     start += __shfl_sync(kFull, ip, 31);
   }
-  if (r == kRankCluster - 1 && threadIdx.x == 0) {
-    const int all = pre_s.x + cta_occ;
+  if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) {
+    const int all = pre.x + tile.x;
     num_pillars[b] = all < g.P ? all : g.P;
   }
-  cluster_sync_all();
-  // 3. buckets (and a release unit's stale canvas cells)
-  const int tid = (int)(r * kRankThreads + threadIdx.x), nth = kRankCluster * kRankThreads;
+}
+
+__global__ void vox_bucket(Geom g, int cap, const int* __restrict__ n_points,
+                           const int* __restrict__ cell, const int* __restrict__ slot,
+                           const int* __restrict__ pillar_of_cell,
+                           const int* __restrict__ pillar_start, int* __restrict__ csr,
+                           const unsigned* __restrict__ cnt_starts, int chunks,
+                           const int* __restrict__ drawn, const int* __restrict__ drawn_num,
+                           uint4* __restrict__ canvas, uint4* __restrict__ lo) {
+  pdl_wait();  // predecessor's outputs complete and visible (exiting lets the next kernel launch)
+  const int b = blockIdx.y;
   if (canvas) {
+    // a release unit's canvas: zero the cells drawn for this slot's previous frame that hold no
+    // kept pillar now (the scan has completed, so pillar_of_cell is this frame's); the cells
+    // that do hold one are rewritten by the PointNet pass that follows, never touched here
     const size_t work = (size_t)drawn_num[b] * chunks;
-    for (size_t t = tid; t < work; t += nth) {
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < work; t += (size_t)gridDim.x * blockDim.x) {
       const int j = (int)(t / chunks), chunk = (int)(t % chunks);
-      const int cc = drawn[(size_t)b * g.P + j];
-      if (pillar_of_cell[(size_t)b * g.G + cc] >= 0) continue;
-      const size_t off = dev::canvas_pixel(g, b, cc) * chunks + chunk;
+      const int c = drawn[(size_t)b * g.P + j];
+      if (pillar_of_cell[(size_t)b * g.G + c] >= 0) continue;
+      const size_t off = dev::canvas_pixel(g, b, c) * chunks + chunk;
       canvas[off] = make_uint4(0u, 0u, 0u, 0u);
       if (lo) lo[off] = make_uint4(0u, 0u, 0u, 0u);
     }
@@ -264,30 +264,30 @@ vox_rank(Geom g, int cap, int rows, const int* __restrict__ n_points, const int*
   const int n = frame_points(n_points, b, cap, nullptr);
   const size_t rb = (size_t)b * cap;
   // kVoxU points per thread per pass, each dependent load issued for all of them at once
-  for (int i0 = tid; i0 < n; i0 += nth * kVoxU) {
-    int cl[kVoxU], sl[kVoxU];
+  for (int i0 = blockIdx.x * blockDim.x * kVoxU; i0 < n; i0 += gridDim.x * blockDim.x * kVoxU) {
+    int c[kVoxU], sl[kVoxU], p[kVoxU];
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) {
-      const int i = i0 + u * nth;
-      cl[u] = i < n ? cell[rb + i] : -1;
+      const int i = i0 + u * blockDim.x + threadIdx.x;
+      c[u] = i < n ? cell[rb + i] : -1;
       sl[u] = i < n ? slot[rb + i] : 0;
     }
     if (cnt_starts) {
-      // one lookup per point: the cell's first point offset + 1 (0: dropped by the pillar cap)
+      // a release unit: one lookup per point, the cell's first point offset + 1 left by the
+      // scan (0: the cell was dropped by the pillar cap)
       unsigned st[kVoxU];
 #pragma unroll
-      for (int u = 0; u < kVoxU; ++u) st[u] = cl[u] >= 0 ? c[cl[u]] : 0u;
+      for (int u = 0; u < kVoxU; ++u) st[u] = c[u] >= 0 ? cnt_starts[(size_t)b * g.G + c[u]] : 0u;
 #pragma unroll
       for (int u = 0; u < kVoxU; ++u)
-        if (st[u]) csr[rb + (st[u] - 1u) + sl[u]] = i0 + u * nth;
-    } else {
-      int pp[kVoxU];
-#pragma unroll
-      for (int u = 0; u < kVoxU; ++u) pp[u] = cl[u] >= 0 ? pillar_of_cell[(size_t)b * g.G + cl[u]] : -1;
-#pragma unroll
-      for (int u = 0; u < kVoxU; ++u)
-        if (pp[u] >= 0) csr[rb + pillar_start[(size_t)b * g.P + pp[u]] + sl[u]] = i0 + u * nth;
+        if (st[u]) csr[rb + (st[u] - 1u) + sl[u]] = i0 + u * blockDim.x + threadIdx.x;
+      continue;
     }
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u) p[u] = c[u] >= 0 ? pillar_of_cell[(size_t)b * g.G + c[u]] : -1;
+#pragma unroll
+    for (int u = 0; u < kVoxU; ++u)
+      if (p[u] >= 0) csr[rb + pillar_start[(size_t)b * g.P + p[u]] + sl[u]] = i0 + u * blockDim.x + threadIdx.x;
   }
 }
 
@@ -316,15 +316,18 @@ __global__ void __launch_bounds__(256) vox_select(Geom g, int cap,
 }  // namespace
 
 size_t vox_workspace_bytes(const Geom& g, int batch, int cap) {
+  const int ntiles = (g.G + kVoxTile - 1) / kVoxTile;
   size_t s = 256;                                            // err
   s += align_up((size_t)batch * cap * sizeof(int), 256) * 2;  // slot, csr
   s += align_up((size_t)batch * g.P * sizeof(int), 256) * 2;  // pillar_start, pillar_cnt
+  s += align_up((size_t)batch * ntiles * sizeof(int2), 256);
   return s;
 }
 
 VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
   VoxWork w;
   char* p = static_cast<char*>(ws);
+  w.ntiles = (g.G + kVoxTile - 1) / kVoxTile;
   w.err = reinterpret_cast<int*>(p);
   p += 256;
   w.slot = reinterpret_cast<int*>(p);
@@ -334,6 +337,8 @@ VoxWork vox_carve(void* ws, const Geom& g, int batch, int cap) {
   w.pillar_start = reinterpret_cast<int*>(p);
   p += align_up((size_t)batch * g.P * sizeof(int), 256);
   w.pillar_cnt = reinterpret_cast<int*>(p);
+  p += align_up((size_t)batch * g.P * sizeof(int), 256);
+  w.tile_sums = reinterpret_cast<int2*>(p);
   return w;
 }
 
@@ -359,13 +364,17 @@ int vox_launch(const Geom& g, int batch, int cap, const float4* points, const in
                  io->first_mirrors ? io->first_mirrors : mirrors,
                  io->first_counts ? io->first_counts : n_points, cell, w.slot, cnt, w.err, io->table_src,
                  io->table_dst, io->table_words);
-  // one cluster per frame; each warp's rows of 32 cells cover the frame's cells
-  const long long per_row = (long long)kRankCluster * kRankWarps * 32;
-  const int rows = (int)((g.G + per_row - 1) / per_row);
   if (e == cudaSuccess)
-    e = launch_pdl(vox_rank, dim3(kRankCluster, batch), dim3(kRankThreads), 0, s, g, cap, rows, n_points,
-                   (const int*)cell, (const int*)w.slot, cnt, pillar_of_cell, coord, npts, w.pillar_start,
-                   w.pillar_cnt, num_pillars, w.csr, io->cnt_clean ? 1 : 0, io->canvas_chunks, io->drawn,
+    e = launch_pdl(vox_tile_sums, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt, w.tile_sums,
+                   w.ntiles);
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_scan, dim3(w.ntiles, batch), dim3(256), 0, s, g, (const unsigned*)cnt,
+                   (const int2*)w.tile_sums, w.ntiles, pillar_of_cell, coord, npts, w.pillar_start, w.pillar_cnt,
+                   num_pillars, io->cnt_clean ? cnt : (unsigned*)nullptr);
+  if (e == cudaSuccess)
+    e = launch_pdl(vox_bucket, pg, dim3(256), 0, s, g, cap, n_points, (const int*)cell, (const int*)w.slot,
+                   (const int*)pillar_of_cell, (const int*)w.pillar_start, w.csr,
+                   io->cnt_clean ? cnt : (unsigned*)nullptr, io->canvas_chunks, io->drawn,
                    io->drawn_num, io->canvas, io->canvas_lo);
   if (e == cudaSuccess && pts)
     e = launch_pdl(vox_select, dim3((g.P + 7) / 8, batch), dim3(256), 0, s, g, cap, points, srcs,

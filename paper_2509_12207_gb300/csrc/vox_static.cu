@@ -1,6 +1,6 @@
 // pp_voxelize_static: pp_voxelize for callers that cannot allocate device memory.
 //
-// Its scratch (arrival slots, grouped point indices, per-pillar offsets, error
+// Its scratch (arrival slots, grouped point indices, per-pillar offsets, tile sums, error
 // word) lives in one file-scope __device__ array of fixed size instead of a caller workspace.
 // Every GPU that loads the library holds that array until the process exits.  Host code must
 // not use the array's name as a device address (on the host it names a host-side shadow), so
