@@ -113,10 +113,10 @@ def _workload(name):
 # were taken on: a changed kernel reports null until it is captured again.
 CONV_TRAFFIC = {
     # per distinct layer shape, one launch each (bench.py --profile-conv LAYER:TILE with the
-    # tuned tile), summed over the step's layers: full-size frame 119.1 + 3 x 28.3 + 28.6 + 5 x 15.4
-    # + 16.6 + 5 x 12.1 MB; 8-frame unit 56.4 + 2 x 14.3 MB
-    "cfg2-fp32": (386.9e6, "5e7a5a1e5ac133c24b848aeae39a1dae2fa5eb724765f72d27edad3d69b72b03"),
-    "cfg3-bf16": (85.0e6, "5e7a5a1e5ac133c24b848aeae39a1dae2fa5eb724765f72d27edad3d69b72b03"),
+    # tuned tile), summed over the step's layers: full-size frame 118.96 + 3 x 28.29 + 28.56 +
+    # 5 x 15.44 + 16.49 + 5 x 12.11 MB; 8-frame unit 56.29 + 2 x 14.30 MB
+    "cfg2-fp32": (386.64e6, "c9df04e78d97fa2336bbb90f8a4dd01a9a6f64e86c624e2e2d014d0c03ee68b8"),
+    "cfg3-bf16": (84.90e6, "c9df04e78d97fa2336bbb90f8a4dd01a9a6f64e86c624e2e2d014d0c03ee68b8"),
 }
 # the same for the neck and head launches of one step (upsamplings + head); not re-captured on the
 # current conv source, so reported as null

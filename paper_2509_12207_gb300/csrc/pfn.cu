@@ -19,6 +19,9 @@ namespace pp {
 namespace {
 
 constexpr int kWarps = 8;
+// Resident blocks per SM of the fused selection + PointNet kernel: its registers (launch
+// bounds) and its grid are both sized for this many, so the grid is one wave.
+constexpr int kSelectBlocksPerSM = 3;
 
 // x minus x with its 13 low mantissa bits cleared (exact in FP32): what a TF32 read drops.
 __device__ __forceinline__ float tf32_rem(float x) {
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
 // Point selection fused with PointNet (the release unit's path): each warp sorts its pillar's
 // point indices (the 32 lowest, as vox_select does), loads lane j's point straight into a
 // register and runs the pillar's PointNet, so the gathered points never go through memory.
-__global__ void __launch_bounds__(256, 4) pfn_select_fused(Geom g, int cap, const float4* __restrict__ points,
+__global__ void __launch_bounds__(256, kSelectBlocksPerSM) pfn_select_fused(Geom g, int cap, const float4* __restrict__ points,
                                                         const float4* const* __restrict__ srcs,
                                                         const int* __restrict__ csr,
                                                         const int* __restrict__ pillar_start,
@@ -339,7 +342,7 @@ int select_pfn_launch(const Geom& g, int batch, int cap, const float4* points, c
                       const float* ss, float* feat, cudaStream_t s, int chunks, int* drawn, int* drawn_num,
                       uint4* canvas, uint4* lo, unsigned* cnt_zero) {
   int bx = (g.P + kWarps - 1) / kWarps;
-  const int bx_max = (4 * sm_count() + batch - 1) / batch;
+  const int bx_max = (kSelectBlocksPerSM * sm_count() + batch - 1) / batch;
   if (bx > bx_max) bx = bx_max;
   return cuda_status(launch_pdl(pfn_select_fused, dim3(bx > 0 ? bx : 1, batch), dim3(kWarps * 32), 0, s, g, cap,
                                 points, srcs, (const int*)w.csr, (const int*)w.pillar_start,

@@ -50,9 +50,20 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   // a release unit's per-launch table: copied from host memory for the kernels that follow
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < table_words) table_dst[threadIdx.x] = table_src[threadIdx.x];
   const int b = blockIdx.y;
-  const int n = frame_points(n_points, b, cap, err);
-  const float4* src = frame_src(points, srcs, b, cap);
-  float4* mirror = mirrors ? mirrors[b] : nullptr;  // copy of a frame read over the host link
+  // the frame's count and pointers: one thread per block reads them (in a release unit from
+  // page-locked host memory, where each read crosses the host link) and shares them
+  __shared__ int s_n;
+  __shared__ const float4* s_src;
+  __shared__ float4* s_mirror;
+  if (threadIdx.x == 0) {
+    s_n = frame_points(n_points, b, cap, err);
+    s_src = frame_src(points, srcs, b, cap);
+    s_mirror = mirrors ? mirrors[b] : nullptr;
+  }
+  __syncthreads();
+  const int n = s_n;
+  const float4* src = s_src;
+  float4* mirror = s_mirror;  // copy of a frame read over the host link
   const int lane = threadIdx.x & 31;
   unsigned* cnt_b = cnt + (size_t)b * g.G;
   const int cell_bits = g.G > 1 ? 32 - __clz(g.G - 1) : 1;  // bits of the largest cell index
