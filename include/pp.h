@@ -216,11 +216,14 @@ int pp_conv_tile_count(int32_t dtype);
  * for about two strips per SM, or one longer strip each); 3 = persistent with the stream-K
  * partition (PP_F32_TC; needs a workspace, see pp_conv3x3_ws); 4 = persistent over runs of
  * 128 consecutive output pixels (the output laid out over the padded width) whose three kx taps
- * share one loaded 130-pixel input range (PP_F32_TC, the last six tiles: 64 and 128 output
+ * share one loaded 130-pixel input range (PP_F32_TC, the six tiles before the last: 64 and 128 output
  * channels, then the same with deeper rings; stride 1 and cout a multiple of bn only, PP_EINVAL
  * otherwise); 5 = the first two of those with the stream-K partition (the accumulation groups of
  * one ky and one 32-channel chunk of all tiles cut into one equal range per SM; needs a
- * workspace like 3). */
+ * workspace like 3); 6 = persistent over runs of 126 consecutive output pixels (bw = 126) with
+ * the three kx taps' 64 output channels side by side in the MMA's N dimension and the kx shift
+ * applied to the accumulator rows (PP_F32_TC, the last tile; stride 1 and cout a multiple of
+ * 64 only, PP_EINVAL otherwise). */
 int pp_conv_tile_info(int32_t dtype, int32_t tile, int32_t* bh, int32_t* bw, int32_t* bn,
                       int32_t* persistent);
 

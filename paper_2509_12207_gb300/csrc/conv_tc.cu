@@ -426,6 +426,20 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
 // blocks instead of 192 KiB for the plain BN 128 tile); with either BN a deeper ring than the
 // unified stage allows: a stage is held from its TMA issue until its MMAs complete, so the
 // ring's depth, not its bytes, sets how much of that round trip is hidden.
+// HALO with KXN (kx folded into N; BN 64, unified stages): the three kx taps' weights are
+// stacked along N (B = 192 rows: the value taps kx = 0, 1, 2, then the remainder taps), and
+// the A operand is the stage's input range from its first pixel on, unshifted.  A K step is
+// three MMAs of N = 192 -- A_hi x B_hi, A_hi x B_lo, A_lo x B_hi, all into one 192-column
+// accumulator -- so that accumulator row j holds, for each tap kx, the products of input pixel
+// p0 + j with that tap's weights; output pixel p0 + i takes tap kx from row i + kx.  A tile is
+// 126 output pixels (rows 126 and 127 only feed the rows before them).  Per K step the MMAs
+// read 30 KiB of operands for 288 tensor cycles (106 B per clock) where the shifted-A halo
+// tile reads 14 KiB per 96 (149 B per clock, above the ~128 B per clock that shared memory
+// serves): the N = 64 MMAs of the shifted form run at 0.66 of the tensor rate, N = 192 at the
+// full rate.  The reducer warps of a lane quarter split the output channels (0-31 and 32-63),
+// each holding its channels' columns of all three taps; at the tile's end a warp adds tap 1
+// from the next row and tap 2 from the row after (warp shuffles; the next lane quarter's first
+// two rows through shared memory).
 
 struct PArgs {
   ConvShape c;
@@ -456,7 +470,8 @@ __host__ __device__ constexpr int p_threads() {
   return 64 + 32 * p_red_warps<MODE, BN, HALO>();
 }
 
-template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false, int NBS = 0>
+template <int MODE, int BN, int STAGES, int KPS, bool S2, bool SK, bool HALO = false, int NBS = 0,
+          bool KXN = false>
 __global__ void __launch_bounds__(p_threads<MODE, BN, HALO>(), 1)
 conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
             const __grid_constant__ CUtensorMap tmB, PArgs args) {
@@ -465,22 +480,27 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t kB = BN * 128;                        // B tile bytes of one K block, one plane
   constexpr uint32_t kAK = MODE == 1 ? 2 * kA : kA;        // per K block: A (+ lo)
   constexpr uint32_t kBK = MODE == 1 ? 2 * kB : kB;        // per K block: B (+ lo plane)
-  constexpr uint32_t kHaloRow = 130 * 128;                 // HALO: one padded input row, one plane
+  constexpr uint32_t kHaloRow = (KXN ? 128 : 130) * 128;   // HALO: one padded input row, one plane
   constexpr uint32_t kHaloA = (kHaloRow + 1023) / 1024 * 1024;
   static_assert(!HALO || (MODE == 1 && (BN == 64 || BN == 128) && !S2 && KPS == 3),
                 "halo rows: 3xTF32, BN 64 or 128, stride 1");
   static_assert(NBS == 0 || HALO, "split rings: halo tiles only");
   static_assert(!HALO || BN == 64 || NBS > 0, "a unified halo stage holds three taps of BN 64 only");
+  static_assert(!KXN || (HALO && BN == 64 && NBS == 0 && !SK), "kx in N: the unified BN 64 halo tile");
   constexpr bool kSplit = HALO && NBS > 0;                 // A and B in separate rings
   constexpr int NB = kSplit ? NBS : 0;                     // B ring slots (one tap each)
   constexpr uint32_t kStageA = HALO ? 2 * kHaloA : KPS * kAK;
   constexpr uint32_t kStageB = KPS * kBK;
   constexpr uint32_t kBRegion = kSplit ? (uint32_t)NB * kBK : (uint32_t)STAGES * kStageB;
-  constexpr int NACC = MODE == 1 ? 2 * BN : BN;            // TMEM columns per accumulator buffer
+  // unified halo stage: where tap kx's value and remainder weights go (KXN: the three value
+  // taps stacked, then the three remainder taps)
+  auto b_hi = [](int kx) -> uint32_t { return KXN ? (uint32_t)kx * kB : (uint32_t)kx * kBK; };
+  auto b_lo = [](int kx) -> uint32_t { return KXN ? 3u * kB + (uint32_t)kx * kB : (uint32_t)kx * kBK + kB; };
+  constexpr int NACC = KXN ? 3 * BN : MODE == 1 ? 2 * BN : BN;  // TMEM columns per accumulator buffer
   // accumulator buffers in TMEM (512 columns): four where they fit, so that the MMAs can run
   // up to three groups ahead of the reducers while they store a finished tile
   constexpr int NBUF = 512 / NACC >= 4 ? 4 : 2;
-  constexpr uint32_t kCols = NBUF * NACC;
+  constexpr uint32_t kCols = KXN ? 512 : NBUF * NACC;      // (an allocation is a power of two)
   constexpr int kRed0 = 2;                                 // first reducer warp
   constexpr int kRW = p_red_warps<MODE, BN, HALO>();       // reducer warps
   constexpr int kRT = 32 * kRW;                            // reducer threads
@@ -600,12 +620,12 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           const int ky = gi / kchunks, cc = gi % kchunks;
           for (int kx = kSplit ? f % 3 : 0; kx < (kSplit ? f % 3 + 1 : 3); ++kx) {
             uint64_t* bar = kSplit ? &fullB[f] : &full[f];
-            uint8_t* bb = kSplit ? sB + f * kBK : sB + f * kStageB + kx * kBK;
+            uint8_t* bb = kSplit ? sB + f * kBK : sB + f * kStageB;
             if (kSplit) mbar_expect_tx(bar, kBK);
             else if (kx == 0) mbar_expect_tx(bar, 2u * kHaloRow + 3u * kBK);
             const int kk = (ky * 3 + kx) * c.cin + cc * BK;
-            tma_3d(bb, &tmB, bar, kk, n0, 0);
-            tma_3d(bb + kB, &tmB, bar, kk, n0, 1);
+            tma_3d(bb + (kSplit ? 0u : b_hi(kx)), &tmB, bar, kk, n0, 0);
+            tma_3d(bb + (kSplit ? kB : b_lo(kx)), &tmB, bar, kk, n0, 1);
           }
         }
       }
@@ -672,10 +692,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tma_2d(a, &tmA, &full[s], cc * BK, pix);
           tma_2d(a + kHaloA, &tmAlo, &full[s], cc * BK, pix);
           for (int kx = 0; kx < 3 && !pre; ++kx) {
-            uint8_t* bb = sB + s * kStageB + kx * kBK;
+            uint8_t* bb = sB + s * kStageB;
             const int kk = (ky * 3 + kx) * c.cin + cc * BK;
-            tma_3d(bb, &tmB, &full[s], kk, n0, 0);
-            tma_3d(bb + kB, &tmB, &full[s], kk, n0, 1);
+            tma_3d(bb + b_hi(kx), &tmB, &full[s], kk, n0, 0);
+            tma_3d(bb + b_lo(kx), &tmB, &full[s], kk, n0, 1);
           }
           if (++s == STAGES) { s = 0; ph ^= 1u; }
         }
@@ -781,15 +801,29 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           const uint32_t d = tmem + (uint32_t)(buf * NACC);
           const uint64_t da = dA0 + ((uint64_t)(s * kStageA) >> 4);
           const uint64_t db = dB0 + ((uint64_t)(s * kStageB) >> 4);
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
+          if (KXN) {
+            const uint32_t id3 = idesc_tf32<3 * BN>();
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              // tap kx: the row from pixel kx on; K step k: 8 channels = 32 bytes into each row
-              const uint64_t a_k = da + (uint64_t)((kx * 128 + k * 32) >> 4);
-              const uint64_t b_k = db + (uint64_t)((kx * kBK + k * 32) >> 4);
-              mma_tf32(d, a_k, b_k, id, (kx == 0 && k == 0) ? 0u : 1u);     // A_hi x [B_hi|B_lo]
-              mma_tf32(d, a_k + (kHaloA >> 4), b_k, id2, 1u);               // A_lo x B_hi
+              // K step k: 8 channels = 32 bytes into each row; the three taps side by side in N
+              const uint64_t a_k = da + (uint64_t)((k * 32) >> 4);
+              const uint64_t bh = db + (uint64_t)((b_hi(0) + k * 32) >> 4);
+              const uint64_t bl = db + (uint64_t)((b_lo(0) + k * 32) >> 4);
+              mma_tf32(d, a_k, bh, id3, k == 0 ? 0u : 1u);                 // A_hi x B_hi
+              mma_tf32(d, a_k, bl, id3, 1u);                               // A_hi x B_lo
+              mma_tf32(d, a_k + (kHaloA >> 4), bh, id3, 1u);               // A_lo x B_hi
+            }
+          } else {
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                // tap kx: the row from pixel kx on; K step k: 8 channels = 32 bytes into each row
+                const uint64_t a_k = da + (uint64_t)((kx * 128 + k * 32) >> 4);
+                const uint64_t b_k = db + (uint64_t)((b_hi(kx) + k * 32) >> 4);
+                mma_tf32(d, a_k, b_k, id, (kx == 0 && k == 0) ? 0u : 1u);     // A_hi x [B_hi|B_lo]
+                mma_tf32(d, a_k + (kHaloA >> 4), b_k, id2, 1u);               // A_lo x B_hi
+              }
             }
           }
           mma_commit(&empty[s]);
@@ -868,7 +902,8 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       // HALO: output pixel ox0 + r of the image laid out over the padded width
       const int oy = HALO ? (ox0 + r) / (c.W + 2) : oy0 + r / args.bw;
       const int ox = HALO ? (ox0 + r) % (c.W + 2) : ox0 + r % args.bw;
-      const bool in_range = oy < c.Ho && ox < c.Wo;
+      // (KXN: rows 126 and 127 of the accumulator only feed taps 1 and 2 of the rows before)
+      const bool in_range = oy < c.Ho && ox < c.Wo && (!KXN || r < 126);
       // output pixel of this row for this N tile (a transposed conv spreads the N tiles of one
       // input pixel over its up x up output block); first channel written and its BN index
       const int qb = n0 / args.co_blk, nb = n0 - qb * args.co_blk;
@@ -879,28 +914,70 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       char* fdst = c.frame_dst ? c.frame_dst[b] : nullptr;
       const size_t fbase = ((size_t)(opy + 1) * (args.Wout + 2) + opx + 1) * args.out_c + args.out_coff + nb;
       if (MODE == 1) {
-        float acc[BNW];
+        // KXN: this warp's BNW channels of tap kx at acc[kx * BNW ...] (three taps); else one
+        constexpr int NT = KXN ? 3 : 1;
+        float acc[NT * BNW];
 #pragma unroll
-        for (int i = 0; i < BNW; ++i) acc[i] = 0.f;
+        for (int i = 0; i < NT * BNW; ++i) acc[i] = 0.f;
         for (int g = 0; g < gpt; ++g, ++gg) {
           const int buf = gg & (NBUF - 1);
           ok = mbar_wait(&kdone[buf], (uint32_t)(gg / NBUF) & 1u, 4u);
           ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the epilogue shuffles need all lanes
           if (!ok) break;
           tc_fence_after();
+          if (KXN) {
 #pragma unroll
-          for (int j = 0; j < BNW / 32; ++j) {
-            uint32_t v[32], w[32];
-            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + h0 + j * 32), v);
-            tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + BN + h0 + j * 32), w);
-            tmem_wait();
+            for (int t = 0; t < 3; ++t) {
+              uint32_t v[32];
+              tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + t * BN + h0), v);
+              tmem_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[j * 32 + i] += __uint_as_float(v[i]) + __uint_as_float(w[i]);
+              for (int i = 0; i < 32; ++i) acc[t * BNW + i] += __uint_as_float(v[i]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < BNW / 32; ++j) {
+              uint32_t v[32], w[32];
+              tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + h0 + j * 32), v);
+              tmem_ld32_nowait(trow + (uint32_t)(buf * NACC + BN + h0 + j * 32), w);
+              tmem_wait();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) acc[j * 32 + i] += __uint_as_float(v[i]) + __uint_as_float(w[i]);
+            }
           }
           tc_fence_before();
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&kfree[buf])) : "memory");
         }
         last_piece_trigger(pi);
+        if (KXN) {
+          // output row r = tap 0 of row r + tap 1 of row r + 1 + tap 2 of row r + 2: the rows
+          // above come by shuffles; lane 31 (tap 1) and lanes 30, 31 (tap 2) take theirs from
+          // the first two rows of the next lane quarter, which the warp holding the same
+          // channels there publishes in its transposing buffer (quarter 3 has none: its lanes
+          // 30 and 31 are rows 126 and 127, not outputs)
+          static_assert(!KXN || BNW == 32, "kx in N: 32 channels per reducer warp");
+          float* mine = reinterpret_cast<float*>(sO + (warp - kRed0) * 4096);
+          if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mine[i] = acc[BNW + i];
+          }
+          if (lane < 2) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mine[32 + 32 * lane + i] = acc[2 * BNW + i];
+          }
+          ok = bar_and(1, kRT, ok);
+          const int hk = (warp - kRed0) >> 2;
+          const float* next = reinterpret_cast<const float*>(sO + (4 * hk + ((q + 1 + 4 - kRed0) & 3)) * 4096);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            float t1 = __shfl_down_sync(0xffffffffu, acc[BNW + i], 1);
+            float t2 = __shfl_down_sync(0xffffffffu, acc[2 * BNW + i], 2);
+            if (q < 3 && lane == 31) t1 = next[i];
+            if (q < 3 && lane >= 30) t2 = next[32 + 32 * (lane - 30) + i];
+            acc[i] = (acc[i] + t1) + t2;
+          }
+          bar_and(1, kRT, true);  // the buffers are the stores' transposing buffers next
+        }
         if (SK && (k0 > 0 || k1 < KB)) {
           // Part of a tile shared with neighbouring CTAs: publish this partial sum (slot 2c for
           // the piece a CTA starts with, 2c + 1 for the one it ends with), count the arrival,
@@ -1444,21 +1521,25 @@ constexpr size_t p_smem_halo() {
                        (2 * ST + 8 + 2 * NB) * 8 + 16;
 }
 // The halo variants, tiles 2 kNPF + i: (output channels, A stages, B slots (0 = unified
-// stages), stream-K).  The stream-K ones (last) cut the accumulation groups of all tiles into
-// one equal range per SM, as the stream-K twins of the plain tiles cut their K blocks.
+// stages), stream-K, kx folded into N).  The stream-K ones cut the accumulation groups of all
+// tiles into one equal range per SM, as the stream-K twins of the plain tiles cut their K
+// blocks.  The kx-in-N one (last) computes 126 output pixels per tile.
 struct HaloVariant {
   int bn, stages, bslots;
-  bool sk;
+  bool sk, kxn;
 };
-constexpr HaloVariant kHalo[] = {{64, 2, 0, false}, {128, 2, 4, false}, {64, 3, 5, false}, {128, 3, 3, false},
-                                 {64, 2, 0, true},  {128, 2, 4, true}};
+constexpr HaloVariant kHalo[] = {{64, 2, 0, false, false}, {128, 2, 4, false, false}, {64, 3, 5, false, false},
+                                 {128, 3, 3, false, false}, {64, 2, 0, true, false},  {128, 2, 4, true, false},
+                                 {64, 2, 0, false, true}};
+// output pixels per halo tile
+constexpr int halo_bw(const HaloVariant& v) { return v.kxn ? 126 : 128; }
 constexpr int kNHalo = (int)(sizeof(kHalo) / sizeof(kHalo[0]));
 
 int num_sms() {
   return device_sms();
 }
 
-template <int MODE, int BN, bool S2, bool SK, bool HALO = false, int HST = 2, int NBS = 0>
+template <int MODE, int BN, bool S2, bool SK, bool HALO = false, int HST = 2, int NBS = 0, bool KXN = false>
 int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w, const PArgs& args,
              cudaStream_t s) {
   constexpr int ST = HALO ? HST : p_stages<MODE, BN>();
@@ -1467,7 +1548,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   constexpr size_t bytes = (HALO ? p_smem_halo<BN, HST, NBS>() : p_smem<MODE, BN>()) + 2 * 1024 * sizeof(float);
   static_assert(bytes <= 227 * 1024, "persistent conv shared memory");
   static std::atomic<uint64_t> attr_set{0};  // per instantiation: devices configured
-  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>),
+  if (int st = smem_attr_once(reinterpret_cast<const void*>(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS, KXN>),
                               (int)bytes, &attr_set, "persistent conv smem attribute"))
     return st;
   // stream-K: one range per CTA, never an empty one (an empty range would be counted among the
@@ -1476,7 +1557,7 @@ int launch_p(const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& w,
   const long kblocks = (long)args.total * (HALO ? 3 : 9) * (args.c.cin / (MODE == 1 ? 32 : 64));
   const int grid = SK ? (int)(kblocks < num_sms() ? kblocks : num_sms())
                            : (args.total < num_sms() ? args.total : num_sms());
-  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS>, dim3(grid),
+  return cuda_status(launch_pdl(conv3x3_tcp<MODE, BN, ST, KPS, S2, SK, HALO, NBS, KXN>, dim3(grid),
                                 dim3(p_threads<MODE, BN, HALO>()), bytes, s, a,
                                 alo, w, args),
                      "persistent conv launch");
@@ -1528,7 +1609,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   if (!halo && ptile < 0) ptile = pick_tile_p(c, tiles, n, co_blk);
   if (!halo && (ptile < 0 || ptile >= n || c.cout % tiles[ptile].bn || co_blk % tiles[ptile].bn))
     return fail(PP_EINVAL, "persistent conv: tile %d unsupported for cout %d", ptile, c.cout);
-  const TileP t = halo ? TileP{1, 128, halo_bn} : tiles[ptile];
+  const TileP t = halo ? TileP{1, halo_bw(hv), halo_bn} : tiles[ptile];
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(w)) & 15u)
     return fail(PP_EINVAL, "persistent conv: operands must be 16-byte aligned");
   const int BK = mode == 1 ? 32 : 64;
@@ -1542,7 +1623,7 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
     void* base = static_cast<char*>(const_cast<void*>(in)) + (size_t)plane * in_plane * el;
     CUtensorMap* m = plane ? &talo : &ta;
     if (halo) {
-      // the flattened padded image: 130 consecutive pixels per load for 128 outputs
+      // the flattened padded image: bw + 2 consecutive pixels per load for bw outputs
       cuuint64_t dims[2] = {(cuuint64_t)c.cin, (cuuint64_t)Hp * Wp * c.batch};
       cuuint64_t strides[1] = {(cuuint64_t)c.cin * el};
       cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(t.bw + 2)};
@@ -1583,8 +1664,8 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.c = c;
   args.bh = t.bh;
   args.bw = t.bw;
-  // halo-row tiles: 128-pixel runs of the output laid out over the padded width, per image
-  args.tiles_x = halo ? (c.Ho * (c.W + 2) + 127) / 128 : (c.Wo + t.bw - 1) / t.bw;
+  // halo-row tiles: runs of bw output pixels laid out over the padded width, per image
+  args.tiles_x = halo ? (c.Ho * (c.W + 2) + t.bw - 1) / t.bw : (c.Wo + t.bw - 1) / t.bw;
   args.tiles_y = halo ? 1 : (c.Ho + t.bh - 1) / t.bh;
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
@@ -1623,7 +1704,8 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
         case 2: return launch_p<1, 64, false, false, true, 3, 5>(ta, talo, tw, args, s);
         case 3: return launch_p<1, 128, false, false, true, 3, 3>(ta, talo, tw, args, s);
         case 4: return launch_p<1, 64, false, true, true, 2, 0>(ta, talo, tw, args, s);
-        default: return launch_p<1, 128, false, true, true, 2, 4>(ta, talo, tw, args, s);
+        case 5: return launch_p<1, 128, false, true, true, 2, 4>(ta, talo, tw, args, s);
+        default: return launch_p<1, 64, false, false, true, 2, 0, true>(ta, talo, tw, args, s);
       }
     }
     if (t.bn == 64) { if (sk) PP_P(1, 64, true); PP_P(1, 64, false); }
@@ -1770,9 +1852,10 @@ int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persi
   }
   if (dtype == PP_F32_TC) {
     if (tile < 0 || tile >= 2 * kNPF + kNHalo) return PP_EINVAL;
-    const TileP t = tile >= 2 * kNPF ? TileP{1, 128, kHalo[tile - 2 * kNPF].bn} : kTilesPF[tile % kNPF];
+    const HaloVariant* hv = tile >= 2 * kNPF ? &kHalo[tile - 2 * kNPF] : nullptr;
+    const TileP t = hv ? TileP{1, halo_bw(*hv), hv->bn} : kTilesPF[tile % kNPF];
     *bh = t.bh; *bw = t.bw; *bn = t.bn;
-    *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : kHalo[tile - 2 * kNPF].sk ? 5 : 4;
+    *persistent = tile < kNPF ? 1 : tile < 2 * kNPF ? 3 : hv->sk ? 5 : hv->kxn ? 6 : 4;
     return PP_OK;
   }
   return PP_EINVAL;

@@ -113,18 +113,20 @@ def test_config_defaults_and_host_validation(lib):
     assert lib.pp_tf32_split(16, 32, 8, None) == pp.PP_EINVAL and b"overlap" in lib.pp_last_error()
     assert lib.pp_tf32_split(17, 4096, 8, None) == pp.PP_EINVAL and b"aligned" in lib.pp_last_error()
     # a 3xTF32 tile index is plain (persistent = 1), its stream-K twin (3), or, last, one of the
-    # six halo tiles (runs of 128 output pixels): 64 / 128 channels with a unified ring or split
-    # A and B rings, the same with deeper split rings (4), then the first two with the stream-K
-    # partition over accumulation groups (5)
+    # seven halo tiles: runs of 128 output pixels with 64 / 128 channels and a unified ring or
+    # split A and B rings, the same with deeper split rings (4), the first two with the stream-K
+    # partition over accumulation groups (5), then runs of 126 pixels with the three kx taps in
+    # the MMA's N dimension (6)
     n = lib.pp_conv_tile_count(pp.PP_F32_TC)
-    npl = (n - 6) // 2
+    npl = (n - 7) // 2
     for t in range(n):
         info = pp.conv_tile_info(pp.PP_F32_TC, t)
-        assert info[3] == (1 if t < npl else 3 if t < 2 * npl else 4 if t < n - 2 else 5)
+        assert info[3] == (1 if t < npl else 3 if t < 2 * npl else 4 if t < n - 3 else 5 if t < n - 1 else 6)
         if t < 2 * npl:
             assert info[:3] == pp.conv_tile_info(pp.PP_F32_TC, t % npl)[:3]
-    assert [pp.conv_tile_info(pp.PP_F32_TC, n - 6 + i) for i in range(6)] == [
-        (1, 128, 64, 4), (1, 128, 128, 4), (1, 128, 64, 4), (1, 128, 128, 4), (1, 128, 64, 5), (1, 128, 128, 5)]
+    assert [pp.conv_tile_info(pp.PP_F32_TC, n - 7 + i) for i in range(7)] == [
+        (1, 128, 64, 4), (1, 128, 128, 4), (1, 128, 64, 4), (1, 128, 128, 4), (1, 128, 64, 5), (1, 128, 128, 5),
+        (1, 126, 64, 6)]
     with pytest.raises(pp.PPError):
         pp.conv_tile_info(pp.PP_F32_TC, n)
 

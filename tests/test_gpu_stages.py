@@ -297,7 +297,7 @@ def test_conv_f32_tensor_cores(shape):
     for tile in list(range(n_tiles)) + list(range(n_tiles - 1, -1, -1)) + [-1]:
         if tile >= 0 and cout % pp.conv_tile_info(pp.PP_F32_TC, tile)[2]:
             continue
-        if tile >= 0 and pp.conv_tile_info(pp.PP_F32_TC, tile)[3] in (4, 5) and s != 1:
+        if tile >= 0 and pp.conv_tile_info(pp.PP_F32_TC, tile)[3] in (4, 5, 6) and s != 1:
             with pytest.raises(pp.PPError, match="stride-1"):  # the halo-row tile is stride 1 only
                 pp.conv3x3(x_d, wp, ss, cout, s, dtype=pp.PP_F32_TC, tile=tile, workspace=ws)
             continue
