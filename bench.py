@@ -113,10 +113,10 @@ def _workload(name):
 # were taken on: a changed kernel reports null until it is captured again.
 CONV_TRAFFIC = {
     # per distinct layer shape, one launch each (bench.py --profile-conv LAYER:TILE with the
-    # tuned tile), summed over the step's layers: full-size frame 118.96 + 3 x 28.29 + 28.56 +
-    # 5 x 15.44 + 16.49 + 5 x 12.11 MB; 8-frame unit 56.29 + 2 x 14.30 MB
-    "cfg2-fp32": (386.64e6, "c9df04e78d97fa2336bbb90f8a4dd01a9a6f64e86c624e2e2d014d0c03ee68b8"),
-    "cfg3-bf16": (84.90e6, "c9df04e78d97fa2336bbb90f8a4dd01a9a6f64e86c624e2e2d014d0c03ee68b8"),
+    # tuned tile), summed over the step's layers: full-size frame 118.78 + 3 x 28.26 + 28.45 +
+    # 5 x 15.44 + 16.61 + 5 x 12.11 MB; 8-frame unit 56.38 + 2 x 14.31 MB
+    "cfg2-fp32": (386.37e6, "f5f28c322f42a6db8be3c246b70d5514f0c8b3c7b5763d815db16edcb294b783"),
+    "cfg3-bf16": (85.00e6, "f5f28c322f42a6db8be3c246b70d5514f0c8b3c7b5763d815db16edcb294b783"),
 }
 # the same for the neck and head launches of one step (upsamplings + head); not re-captured on the
 # current conv source, so reported as null
