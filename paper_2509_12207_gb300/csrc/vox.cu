@@ -38,6 +38,8 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
 // Points per thread per pass of the point kernels: their loads (and atomics) are issued
 // together so that one memory round trip covers several points.
 constexpr int kVoxU = 4;
+// Slots of the per-warp table of the count kernel's no-repeated-cell test (a power of two).
+constexpr int kVoxTab = 1024;
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
@@ -67,6 +69,7 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   const int lane = threadIdx.x & 31;
   unsigned* cnt_b = cnt + (size_t)b * g.G;
   const int cell_bits = g.G > 1 ? 32 - __clz(g.G - 1) : 1;  // bits of the largest cell index
+  __shared__ unsigned char s_tab[8][kVoxTab];                   // per warp (256 threads)
   // grid-stride over the frame's points, kVoxU coalesced blocks of blockDim.x points per pass
   // (block-uniform trip count: whole warps stay together)
   for (int i0 = blockIdx.x * blockDim.x * kVoxU; i0 < n; i0 += gridDim.x * blockDim.x * kVoxU) {
@@ -104,15 +107,29 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
     // their number to the cell's count; the old count is the group's first arrival slot.  A
     // lane's peers (the lanes holding its cell) come from one ballot per bit of the cell index:
     // the lanes that agree with it on every bit.  That is the set __match_any_sync returns, at
-    // a lower cost when the 32 cells are mostly distinct.
+    // a lower cost when the 32 cells are mostly distinct.  First a cheap exact test: every
+    // lane writes its lane number into a per-warp table slot chosen by the low bits of its
+    // cell and reads the slot back; if no lane reads another's number, no two lanes share a
+    // cell (nor a slot), every lane is its own group and the ballots are skipped.
     unsigned peers[kVoxU], base[kVoxU];
+    unsigned char* tab = s_tab[threadIdx.x >> 5];
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) {
-      unsigned pm = __ballot_sync(kFull, c[u] >= 0);
-      for (int k = 0; k < cell_bits; ++k) {
-        const unsigned bit = (unsigned)(c[u] >> k) & 1u;
-        const unsigned on = __ballot_sync(kFull, bit);
-        pm &= bit ? on : ~on;
+      const unsigned valid = __ballot_sync(kFull, c[u] >= 0);
+      const int slot_h = c[u] & (kVoxTab - 1);
+      if (c[u] >= 0) tab[slot_h] = (unsigned char)lane;
+      __syncwarp();
+      const bool clash = c[u] >= 0 && tab[slot_h] != (unsigned char)lane;
+      const unsigned clashes = __ballot_sync(kFull, clash);
+      __syncwarp();  // every lane's read of the table before any lane's next write
+      unsigned pm = valid & (1u << lane);
+      if (clashes) {
+        pm = valid;
+        for (int k = 0; k < cell_bits; ++k) {
+          const unsigned bit = (unsigned)(c[u] >> k) & 1u;
+          const unsigned on = __ballot_sync(kFull, bit);
+          pm &= bit ? on : ~on;
+        }
       }
       peers[u] = 0u;
       base[u] = 0u;
