@@ -55,6 +55,7 @@ int check_geometry(const pp_geometry* g, Geom* out) {
   out->nx = g->nx; out->ny = g->ny;
   out->G = g->nx * g->ny;
   out->P = g->max_pillars;
+  out->nx_magic = g->nx > 1 ? UINT64_MAX / (uint64_t)g->nx + 1u : 0u;
   return PP_OK;
 }
 

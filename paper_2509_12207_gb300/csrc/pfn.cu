@@ -28,26 +28,17 @@ __device__ __forceinline__ float tf32_rem(float x) {
   return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
-// One pillar's features (lane c holds channels c and c + 32) into its canvas pixel: FP32 (chunks
-// 16) as two 128-byte rows per plane, the TF32 remainder plane beside it when lo != NULL; BF16
-// (chunks 8) rounded to nearest even, lane l packing channels 2l and 2l + 1 (one 128-byte row).
+// One pillar's features (lane c holds channels 2c and 2c + 1) into its canvas pixel: FP32 (chunks
+// 16) as one 256-byte row per plane, the TF32 remainder plane beside it when lo != NULL; BF16
+// (chunks 8) rounded to nearest even, one 128-byte row.
 // The values and roundings are those of canvas_write on the same features.
 __device__ __forceinline__ void canvas_put(size_t pix, int chunks, float m0, float m1, int lane,
                                            uint4* __restrict__ canvas, uint4* __restrict__ lo) {
   if (chunks == 16) {
-    float* cv = reinterpret_cast<float*>(canvas) + pix * 64;
-    cv[lane] = m0;
-    cv[lane + 32] = m1;
-    if (lo) {
-      float* lv = reinterpret_cast<float*>(lo) + pix * 64;
-      lv[lane] = tf32_rem(m0);
-      lv[lane + 32] = tf32_rem(m1);
-    }
+    reinterpret_cast<float2*>(canvas)[pix * 32 + lane] = make_float2(m0, m1);
+    if (lo) reinterpret_cast<float2*>(lo)[pix * 32 + lane] = make_float2(tf32_rem(m0), tf32_rem(m1));
   } else {
-    const int s0 = (2 * lane) & 31, s1 = (2 * lane + 1) & 31;
-    const float a0 = __shfl_sync(0xffffffffu, m0, s0), a1 = __shfl_sync(0xffffffffu, m0, s1);
-    const float b0 = __shfl_sync(0xffffffffu, m1, s0), b1 = __shfl_sync(0xffffffffu, m1, s1);
-    __nv_bfloat162 h = __floats2bfloat162_rn(lane < 16 ? a0 : b0, lane < 16 ? a1 : b1);
+    __nv_bfloat162 h = __floats2bfloat162_rn(m0, m1);
     reinterpret_cast<unsigned*>(canvas)[pix * 32 + lane] = *reinterpret_cast<unsigned*>(&h);
   }
 }
@@ -84,8 +75,7 @@ __global__ void __launch_bounds__(256) pfn_fused(Geom g, const float4* __restric
     float m0, m1;
     const int n = npts[q];
     dev::pfn_pillar(g, pts[q * 32 + lane], n, coord[q], lane, L, inv_s[n], m0, m1);
-    feat[q * 64 + lane] = m0;
-    feat[q * 64 + lane + 32] = m1;
+    reinterpret_cast<float2*>(feat)[q * 32 + lane] = make_float2(m0, m1);
   }
 }
 
@@ -159,8 +149,7 @@ __global__ void __launch_bounds__(256, kSelectBlocksPerSM) pfn_select_fused(Geom
     const int n0 = c0 < 32 ? c0 : 32;
     dev::pfn_pillar(g, v0, n0, l0, lane, L, inv_s[n0], m0, m1);
     if (feat) {
-      feat[q * 64 + lane] = m0;
-      feat[q * 64 + lane + 32] = m1;
+      reinterpret_cast<float2*>(feat)[q * 32 + lane] = make_float2(m0, m1);
     }
     if (canvas) {
       canvas_put(dev::canvas_pixel(g, b, l0), chunks, m0, m1, lane, canvas, lo);

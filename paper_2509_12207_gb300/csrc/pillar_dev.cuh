@@ -11,6 +11,13 @@ namespace dev {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// cell / nx for a cell index 0 <= cell < 2^31: the high word of cell times
+// g.nx_magic = ceil(2^64 / nx) (nx >= 2; Lemire, Kaser and Kurz, "Faster remainder by direct
+// computation", 2019: exact for every 32-bit dividend), set with the geometry on the host.
+__device__ __forceinline__ int nx_div(const Geom& g, int cell) {
+  return g.nx > 1 ? (int)__umul64hi(g.nx_magic, (uint64_t)(unsigned)cell) : cell;
+}
+
 // Frame b's points: srcs[b] when a per-frame pointer table is given, else row b of the batch.
 __device__ __forceinline__ const float4* frame_src(const float4* points, const float4* const* srcs, int b,
                                                    int cap) {
@@ -62,7 +69,7 @@ __device__ __forceinline__ int lowest_32(const int* seg, int count, int lane) {
   return lowest_32_from(lane < count ? seg[lane] : INT_MAX, seg, count, lane);
 }
 
-// PointNet weights of lane c's two channels (c and c + 32), BN folded in: with BN scale s,
+// PointNet weights of lane c's two channels (2c and 2c + 1), BN folded in: with BN scale s,
 // shift h and weight rows w[0..8] over the features (x, y, z, r, x - x_mean, y - y_mean,
 // z - z_mean, x - x_centre, y - y_centre), a channel's pre-activation is
 //   s (w . f) + h = ax x + ay y + az z + ar r + (h - m4 x_mean - m5 y_mean - m6 z_mean
@@ -97,7 +104,7 @@ __device__ __forceinline__ PfnLane pfn_lane(const float (*comb)[kPfnComb], int l
   PfnLane L;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float* t = comb[lane + 32 * i];
+    const float* t = comb[2 * lane + i];
     L.ax[i] = t[0]; L.ay[i] = t[1]; L.az[i] = t[2]; L.ar[i] = t[3];
     L.m4[i] = t[4]; L.m5[i] = t[5]; L.m6[i] = t[6]; L.m7[i] = t[7]; L.m8[i] = t[8];
     L.h[i] = t[9];
@@ -106,7 +113,7 @@ __device__ __forceinline__ PfnLane pfn_lane(const float (*comb)[kPfnComb], int l
 }
 
 // PointNet of one pillar: lane j holds point v of the pillar (valid for j < n, n >= 1) at grid
-// cell `cell`; lane c returns channels c and c + 32: the max over the valid points of
+// cell `cell`; lane c returns channels 2c and 2c + 1: the max over the valid points of
 // ReLU(s (W . f) + h) for the 9 features f of the point (x, y, z, r, offsets to the mean of the
 // valid points, x/y offsets to the cell centre), evaluated in the regrouped form of PfnLane.
 // inv_n: 1 / n (table in shared memory).
@@ -125,7 +132,7 @@ __device__ __forceinline__ void pfn_pillar(const Geom& g, float4 v, int n, int c
   const float mx = __shfl_sync(kFullMask, sx, 0) * inv_n;
   const float my = __shfl_sync(kFullMask, sy, 0) * inv_n;
   const float mz = __shfl_sync(kFullMask, sz, 0) * inv_n;
-  const int iy = cell / g.nx, ix = cell - iy * g.nx;
+  const int iy = nx_div(g, cell), ix = cell - iy * g.nx;
   const float xc = g.xmin + ((float)ix + 0.5f) * g.vx;
   const float yc = g.ymin + ((float)iy + 0.5f) * g.vy;
   float c[2];
@@ -146,7 +153,7 @@ __device__ __forceinline__ void pfn_pillar(const Geom& g, float4 v, int n, int c
 
 // Padded canvas pixel [b][iy + 1][ix + 1] of cell `cell` = iy * nx + ix of frame b.
 __device__ __forceinline__ size_t canvas_pixel(const Geom& g, int b, int cell) {
-  const int iy = cell / g.nx, ix = cell - iy * g.nx;
+  const int iy = nx_div(g, cell), ix = cell - iy * g.nx;
   return ((size_t)b * (g.ny + 2) + iy + 1) * (g.nx + 2) + ix + 1;
 }
 

@@ -74,6 +74,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 struct Geom {
   float xmin, xmax, ymin, ymax, zmin, zmax, vx, vy;
   int nx, ny, G, P;
+  uint64_t nx_magic;  // ceil(2^64 / nx) for nx >= 2 (cell / nx by one multiply-high), else 0
 };
 
 int check_geometry(const pp_geometry* g, Geom* out);
