@@ -794,8 +794,14 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       int t, k0, k1;
       for (int i = 0; ok && piece(i, t, k0, k1); ++i) {
         for (int g = k0; g < k1; ++g) {  // one stage = one accumulation group
+          // KXN: args.fold groups per accumulation buffer (12 MMAs each into one column block;
+          // two groups give a buffer the 24 accumulations the shifted-A tile gives one group),
+          // dividing the reducers' TMEM reads; a tile's last buffer may hold fewer
+          const int gl = KXN ? (g - k0) % args.fold : 0;
+          const bool fresh = gl == 0;
+          const bool close = !KXN || gl == args.fold - 1 || g + 1 == k1;
           const int buf = gg & (NBUF - 1);
-          if (gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
+          if (fresh && gg >= NBUF && !mbar_wait(&kfree[buf], (uint32_t)(gg / NBUF - 1) & 1u, 16u)) { ok = false; break; }
           if (!mbar_wait(&full[s], ph, 2u)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * NACC);
@@ -809,7 +815,7 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               const uint64_t a_k = da + (uint64_t)((k * 32) >> 4);
               const uint64_t bh = db + (uint64_t)((b_hi(0) + k * 32) >> 4);
               const uint64_t bl = db + (uint64_t)((b_lo(0) + k * 32) >> 4);
-              mma_tf32(d, a_k, bh, id3, k == 0 ? 0u : 1u);                 // A_hi x B_hi
+              mma_tf32(d, a_k, bh, id3, (fresh && k == 0) ? 0u : 1u);      // A_hi x B_hi
               mma_tf32(d, a_k, bl, id3, 1u);                               // A_hi x B_lo
               mma_tf32(d, a_k + (kHaloA >> 4), bh, id3, 1u);               // A_lo x B_hi
             }
@@ -827,8 +833,10 @@ conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
           }
           mma_commit(&empty[s]);
-          mma_commit(&kdone[buf]);
-          ++gg;
+          if (close) {
+            mma_commit(&kdone[buf]);
+            ++gg;
+          }
           if (++s == STAGES) { s = 0; ph ^= 1u; }
         }
       }
@@ -1533,6 +1541,8 @@ constexpr HaloVariant kHalo[] = {{64, 2, 0, false, false}, {128, 2, 4, false, fa
                                  {64, 2, 0, false, true}};
 // output pixels per halo tile
 constexpr int halo_bw(const HaloVariant& v) { return v.kxn ? 126 : 128; }
+// accumulation groups per TMEM buffer of the kx-in-N tile
+constexpr int kKxnFold = 2;
 constexpr int kNHalo = (int)(sizeof(kHalo) / sizeof(kHalo[0]));
 
 int num_sms() {
@@ -1669,7 +1679,9 @@ int conv_tcp_launch(int mode, const ConvShape& c, const void* in, const void* w,
   args.tiles_y = halo ? 1 : (c.Ho + t.bh - 1) / t.bh;
   args.tiles_n = c.cout / t.bn;
   args.total = args.tiles_x * args.tiles_y * c.batch * args.tiles_n;
-  args.fold = halo ? 1 : 2;  // work units per TMEM accumulation group (a halo unit is one group)
+  // work units per TMEM accumulation buffer (a halo unit is one group; the kx-in-N tile takes
+  // two groups per buffer)
+  args.fold = halo ? (hv.kxn ? kKxnFold : 1) : 2;
   args.taps = g.taps;
   args.up = g.up;
   args.co_blk = co_blk;
