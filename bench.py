@@ -113,10 +113,10 @@ def _workload(name):
 # were taken on: a changed kernel reports null until it is captured again.
 CONV_TRAFFIC = {
     # per distinct layer shape, one launch each (bench.py --profile-conv LAYER:TILE with the
-    # tuned tile), summed over the step's layers: full-size frame 118.78 + 3 x 28.26 + 28.45 +
-    # 5 x 15.44 + 16.61 + 5 x 12.11 MB; 8-frame unit 56.38 + 2 x 14.31 MB
-    "cfg2-fp32": (386.37e6, "f5f28c322f42a6db8be3c246b70d5514f0c8b3c7b5763d815db16edcb294b783"),
-    "cfg3-bf16": (85.00e6, "f5f28c322f42a6db8be3c246b70d5514f0c8b3c7b5763d815db16edcb294b783"),
+    # tuned tile), summed over the step's layers: full-size frame 119.10 + 3 x 28.30 + 28.57 +
+    # 5 x 15.44 + 16.61 + 5 x 12.11 MB; 8-frame unit 56.40 + 2 x 14.30 MB
+    "cfg2-fp32": (386.96e6, "85903ed2da2377408ed2145782c910963e4bc0278d0b31c7742d9d7985a06fc3"),
+    "cfg3-bf16": (85.01e6, "85903ed2da2377408ed2145782c910963e4bc0278d0b31c7742d9d7985a06fc3"),
 }
 # the same for the neck and head launches of one step (upsamplings + head); not re-captured on the
 # current conv source, so reported as null

@@ -333,18 +333,20 @@ int Pipeline::init(const Model* m, int max_batch, int cap_points, bool graphs, b
     return st;
   vw_ = vox_carve(vox_ws_, g, B_, cap_);
   if (tune) {
-    // time every conv tile of every layer for each unit size on this unit's own buffers; the
-    // launches below (and the captured graphs) then use the fastest
+    // time every conv tile of every layer at the largest unit size on this unit's own buffers
+    // and use the fastest for every unit size: the tiles differ in their accumulation order,
+    // and one tile per layer keeps a frame's result bit-identical whatever the number of
+    // frames its unit carries.  The launches below (and the captured graphs) then use it.
     if ((st = cuda_status(cudaStreamSynchronize(s), "pre-tune sync"))) return st;
-    for (int b = 1; b <= B_ && st == PP_OK; ++b) {
-      const void* x = canvas_;
-      for (size_t l = 0; l < m->layers.size() && st == PP_OK; ++l) {
-        const LayerSpec& L = m->layers[l];
-        int best = -1;
-        st = pp_conv_autotune_ws(b, L.H, L.W, L.cin, L.cout, L.stride, m->conv_dtype, x, m->conv_w[l],
-                                 m->conv_ss[l], act_[l], conv_ws_, conv_ws_bytes_, 5, &best, nullptr);
-        x = act_[l];
-      }
+    const void* x = canvas_;
+    for (size_t l = 0; l < m->layers.size() && st == PP_OK; ++l) {
+      const LayerSpec& L = m->layers[l];
+      int best = -1;
+      st = pp_conv_autotune_ws(B_, L.H, L.W, L.cin, L.cout, L.stride, m->conv_dtype, x, m->conv_w[l],
+                               m->conv_ss[l], act_[l], conv_ws_, conv_ws_bytes_, 5, &best, nullptr);
+      for (int b = 1; b < B_ && st == PP_OK; ++b)
+        tune_record(m->conv_dtype, b, L.H, L.W, L.cin, L.cout, L.stride, best);
+      x = act_[l];
     }
     if (st) return st;
   }

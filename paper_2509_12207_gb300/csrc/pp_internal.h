@@ -202,6 +202,8 @@ int conv_f32tc_tile_count();
 int conv_tc_tile_info(int dtype, int tile, int* bh, int* bw, int* bn, int* persistent);
 // Tile the autotuner found fastest for this dtype and shape, or -1 (tune.cu).
 int tuned_tile(int dtype, const ConvShape& c);
+// Records `tile` as the library's choice for this (dtype, layer shape) without timing it.
+void tune_record(int dtype, int batch, int H, int W, int cin, int cout, int stride, int tile);
 int conv_pack_launch(const float* w_oihw, int cin, int cout, int dtype, void* dst, cudaStream_t s);
 
 // ---- synthetic GPU load (synth.cu): kernels of set utilisation and duration

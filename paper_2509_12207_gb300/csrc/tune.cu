@@ -29,6 +29,11 @@ int tuned_tile(int dtype, const ConvShape& c) {
   return it == g_table.end() ? -1 : it->second.tile;
 }
 
+void tune_record(int dtype, int batch, int H, int W, int cin, int cout, int stride, int tile) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_table[Key(dtype, batch, H, W, cin, cout, stride)] = Entry{tile, 0.f};
+}
+
 }  // namespace pp
 
 using namespace pp;
