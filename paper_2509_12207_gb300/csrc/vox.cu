@@ -38,8 +38,9 @@ __device__ __forceinline__ int frame_points(const int* n_points, int b, int cap,
 // Points per thread per pass of the point kernels: their loads (and atomics) are issued
 // together so that one memory round trip covers several points.
 constexpr int kVoxU = 4;
-// Slots of the per-warp table of the count kernel's no-repeated-cell test (a power of two).
-constexpr int kVoxTab = 1024;
+// 32-bit words of the per-warp bit table of the count kernel's no-repeated-cell test (a power
+// of two): 16,384 bits, so that 32 distinct cells share a bit with probability ~3 %.
+constexpr int kVoxTabWords = 512;
 
 __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ points,
                                const float4* const* __restrict__ srcs,
@@ -69,7 +70,10 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
   const int lane = threadIdx.x & 31;
   unsigned* cnt_b = cnt + (size_t)b * g.G;
   const int cell_bits = g.G > 1 ? 32 - __clz(g.G - 1) : 1;  // bits of the largest cell index
-  __shared__ unsigned char s_tab[8][kVoxTab];                   // per warp (256 threads)
+  __shared__ __align__(16) unsigned s_tab[8][kVoxTabWords];    // per warp (256 threads)
+  unsigned* tab = s_tab[threadIdx.x >> 5];
+  for (int i = lane; i < kVoxTabWords / 4; i += 32) reinterpret_cast<uint4*>(tab)[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
   // grid-stride over the frame's points, kVoxU coalesced blocks of blockDim.x points per pass
   // (block-uniform trip count: whole warps stay together)
   for (int i0 = blockIdx.x * blockDim.x * kVoxU; i0 < n; i0 += gridDim.x * blockDim.x * kVoxU) {
@@ -108,20 +112,22 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
     // lane's peers (the lanes holding its cell) come from one ballot per bit of the cell index:
     // the lanes that agree with it on every bit.  That is the set __match_any_sync returns, at
     // a lower cost when the 32 cells are mostly distinct.  First a cheap exact test: every
-    // lane writes its lane number into a per-warp table slot chosen by the low bits of its
-    // cell and reads the slot back; if no lane reads another's number, no two lanes share a
-    // cell (nor a slot), every lane is its own group and the ballots are skipped.
+    // lane sets the bit of a per-warp bit table chosen by the low bits of its cell with an
+    // atomic OR that returns the word's old value; a lane that finds its bit already set
+    // shares it with another lane (the same cell, or another cell with the same low bits).
+    // If no lane does, no two lanes share a cell, every lane is its own group and the ballots
+    // are skipped.  The lanes then clear the words they set.
     unsigned peers[kVoxU], base[kVoxU];
-    unsigned char* tab = s_tab[threadIdx.x >> 5];
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) {
       const unsigned valid = __ballot_sync(kFull, c[u] >= 0);
-      const int slot_h = c[u] & (kVoxTab - 1);
-      if (c[u] >= 0) tab[slot_h] = (unsigned char)lane;
-      __syncwarp();
-      const bool clash = c[u] >= 0 && tab[slot_h] != (unsigned char)lane;
+      const int word = (c[u] >> 5) & (kVoxTabWords - 1);
+      const unsigned bitm = 1u << (c[u] & 31);
+      const bool clash = c[u] >= 0 && (atomicOr(&tab[word], bitm) & bitm) != 0u;
       const unsigned clashes = __ballot_sync(kFull, clash);
-      __syncwarp();  // every lane's read of the table before any lane's next write
+      __syncwarp();  // every lane's atomic on the table before any lane clears a word
+      if (c[u] >= 0) tab[word] = 0u;
+      __syncwarp();  // the table clear before the next group's atomics
       unsigned pm = valid & (1u << lane);
       if (clashes) {
         pm = valid;
@@ -138,12 +144,14 @@ __global__ void vox_cell_count(Geom g, int cap, const float4* __restrict__ point
         if (lane == __ffs(pm) - 1) base[u] = atomicAdd(&cnt_b[c[u]], (unsigned)__popc(pm));
       }
     }
+    // each lane reads its group leader's old count with one whole-warp indexed shuffle (a
+    // shuffle over each group's own mask would split the warp into one pass per group)
 #pragma unroll
     for (int u = 0; u < kVoxU; ++u) {
-      if (c[u] < 0) continue;
-      const unsigned first = __shfl_sync(peers[u], base[u], __ffs(peers[u]) - 1);
+      const int leader = peers[u] ? __ffs(peers[u]) - 1 : lane;
+      const unsigned first = __shfl_sync(kFull, base[u], leader);
       const int i = i0 + u * blockDim.x + threadIdx.x;
-      slot[(size_t)b * cap + i] = (int)first + __popc(peers[u] & ((1u << lane) - 1u));
+      if (c[u] >= 0) slot[(size_t)b * cap + i] = (int)first + __popc(peers[u] & ((1u << lane) - 1u));
     }
   }
 }
