@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--head", action="store_true",
                     help="the step also runs the neck (upsample + concat) and the detection head")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiling runs)")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi samples of the timed region "
+                         "(bench_clocks_<pid>.csv; default: the system temporary directory)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="with the default workload, skip the 8-frame BF16 unit run reported under batched_bf16")
@@ -230,9 +233,10 @@ class _Clocks:
     Always stopped by the caller (try/finally); the child also dies with this process and is
     killed by a watchdog after `max_s` seconds."""
 
-    def __init__(self, gpu_index, enabled=True, max_s=600.0):
+    def __init__(self, gpu_index, enabled=True, max_s=600.0, out_dir=None):
+        import tempfile
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
         if not enabled:
             return
         try:
@@ -621,7 +625,7 @@ def _run_ours(a, rank, world, dist):
         el = replica_window(dist, e0.elapsed_time(e1) * 1e-3, "cuda")
         return el, wall
 
-    clocks = _Clocks(dev, enabled=not a.no_clocks)
+    clocks = _Clocks(dev, enabled=not a.no_clocks, out_dir=a.clocks_dir)
     try:
         el, wall = timed(host=False)
     finally:
