@@ -77,3 +77,20 @@ def test_default_serving_points_are_past_plain_saturation_with_tight_share():
     assert pts["config4_11_chains_1x"] == [11, 1.0, 4.0, False, 1.0, 0.0]
     over = [v for k, v in pts.items() if k != "config4_11_chains_1x"]
     assert over and all(n == 33 and secs >= 8.0 and tight == 0.4 for n, rate, secs, mixed, dfac, tight in over)
+
+
+def test_clock_samples_go_to_the_chosen_directory(tmp_path):
+    """The timed region's nvidia-smi samples are written under --clocks-dir (default: the system
+    temporary directory), never into the source tree; without nvidia-smi the line says so."""
+    a = _args("--clocks-dir", str(tmp_path))
+    assert a.clocks_dir == str(tmp_path)
+    assert _args().clocks_dir is None
+    c = bench._Clocks(0, enabled=True, max_s=5.0, out_dir=str(tmp_path))
+    try:
+        assert os.path.dirname(c.path) == str(tmp_path) and os.path.exists(c.path)
+    finally:
+        r = c.stop()
+    assert set(r) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+    d = bench._Clocks(0, enabled=False)
+    assert not os.path.commonpath([d.path, ROOT]) == ROOT
+    d.stop()
